@@ -1,0 +1,465 @@
+/*
+ * dg_oracle.c -- plain, slow, FP64 CPU oracle for the weighted symmetric interior
+ * penalty (WSIPG) DG operator of Muething, Piatkowski & Bastian (arXiv 1711.10885).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is used by the test suite, by the
+ * smoke check and by the CPU-baseline leg of the benchmark.  The product path
+ * (the CUDA library) never links, loads or calls it, and it shares no code,
+ * headers or tables with the library.
+ *
+ * What it computes (Sec. 2, eq. blf and the right hand side functional l_h):
+ *   (A u)_i = a_h(u, phi_i),   F_i = l_h(phi_i)
+ * for every basis function phi_i of the DG space Q_k on an axis-parallel
+ * uniform cuboid mesh, by DIRECT quadrature: at every quadrature point the
+ * finite element function and its gradient are summed over all (k+1)^3 basis
+ * functions, and every integral is accumulated point by point for every test
+ * function.  No sum factorisation, no 1D factorisation reuse (Sec. 3 is the
+ * method being checked; this is the definition it must reproduce).
+ *
+ * Readings of the paper taken here (each also listed in the design notes):
+ *  - weighted average {v}_w = w- v- + w+ v+ (the printed minus sign
+ *    contradicts w- + w+ = 1 and the convex-average definition it cites);
+ *  - orthonormal shifted Legendre basis on the reference interval [0,1]:
+ *    theta_j(x) = sqrt(2j+1) P_j(2x-1)  ("L2-orthogonal Legendre", Sec. 2);
+ *  - tensor Gauss-Legendre rule with m points per direction (Sec. 3.1);
+ *  - scalar diffusion D_T * I constant per cell, constant b and c (Problem A);
+ *  - penalty gamma_F = <delta-,delta+> * sigma * |F| / min(|T-|,|T+|) where the
+ *    caller passes sigma (the paper's alpha*p*(p+d-1), or 2k(k+1));
+ *    on boundary faces <delta-,delta+> -> delta- and min|T| -> |T-|;
+ *  - every boundary face is Dirichlet; interior faces are oriented from the
+ *    cell with the lower index along the face normal (T-) to the upper (T+);
+ *  - upwind tie b_nu = 0 takes the u- branch (value 0 either way).
+ *
+ * Layouts (shared with the library only as a documented interface):
+ *   cells lexicographic, x fastest: cell = ix + nx*(iy + ny*iz);
+ *   DOF within a cell: J = j1 + n*(j2 + n*j3), n = k+1 (x-degree fastest);
+ *   volume quadrature points within a cell: q = i1 + m*(i2 + m*i3);
+ *   boundary side s = 2*dir + (0 lower | 1 upper); its faces enumerate the
+ *   cells of that boundary layer lexicographically in the two tangential
+ *   cell indices (lower axis fastest), and the m*m face points of each face
+ *   with the lower tangential axis fastest.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* 1D ingredients                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Legendre polynomial P_j(t) and derivative on [-1,1] by the three-term
+ * (Bonnet) recurrence; returns values for j = 0..jmax. */
+static void legendre_all(int jmax, double t, double* P, double* dP) {
+  P[0] = 1.0;
+  dP[0] = 0.0;
+  if (jmax >= 1) {
+    P[1] = t;
+    dP[1] = 1.0;
+  }
+  for (int j = 1; j < jmax; ++j) {
+    P[j + 1] = ((2.0 * j + 1.0) * t * P[j] - j * P[j - 1]) / (j + 1.0);
+    /* P'_{j+1} = P'_{j-1} + (2j+1) P_j */
+    dP[j + 1] = dP[j - 1] + (2.0 * j + 1.0) * P[j];
+  }
+}
+
+/* Gauss-Legendre rule with m points on [0,1] (ascending), Sec. 3.1.  Newton
+ * iteration on P_m from the Chebyshev-like initial guesses. */
+int oracle_gauss_legendre(int m, double* x, double* w) {
+  if (m < 1 || m > 64) return -1;
+  double P[66], dP[66];
+  for (int i = 0; i < m; ++i) {
+    double t = -cos(M_PI * (i + 0.75) / (m + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      legendre_all(m, t, P, dP);
+      double dt = P[m] / dP[m];
+      t -= dt;
+      if (fabs(dt) < 1e-17) break;
+    }
+    legendre_all(m, t, P, dP);
+    x[i] = 0.5 * (1.0 + t);
+    w[i] = 1.0 / ((1.0 - t * t) * dP[m] * dP[m]); /* = (2/((1-t^2)P'^2)) / 2 */
+  }
+  return 0;
+}
+
+/* Orthonormal shifted Legendre basis on [0,1] and its derivative, j = 0..k. */
+void oracle_basis_1d(int k, double x, double* val, double* der) {
+  double P[66], dP[66];
+  legendre_all(k, 2.0 * x - 1.0, P, dP);
+  for (int j = 0; j <= k; ++j) {
+    double s = sqrt(2.0 * j + 1.0);
+    val[j] = s * P[j];
+    der[j] = 2.0 * s * dP[j];
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Problem description                                                 */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int n[3];            /* cells per direction                               */
+  double lo[3], hi[3]; /* domain [lo, hi]                                    */
+  int k;               /* polynomial degree; n = k+1 shape functions / dir   */
+  int m;               /* Gauss points per direction                         */
+  const double* D;     /* [ncells] scalar diffusion per cell                 */
+  double b[3];         /* constant velocity                                  */
+  double c;            /* reaction                                           */
+  double sigma;        /* penalty factor, gamma = <d-,d+> sigma |F|/min|T|   */
+} oracle_problem;
+
+/* Full 3D tables at one set of points: phi[p*nb + J], grad[(p*nb + J)*3 + r]
+ * are the reference-cube basis values and reference gradients. */
+typedef struct {
+  int np, nb;
+  double* phi;
+  double* grad;
+  double* wgt; /* quadrature weight per point (reference measure) */
+} table3d;
+
+static void table_free(table3d* t) {
+  free(t->phi);
+  free(t->grad);
+  free(t->wgt);
+}
+
+/* Points given by three per-axis coordinate lists; point p = a + na*(b + nb_*c)
+ * enumerates axis0 fastest.  A face is an axis list with one fixed entry. */
+static int table_build(int k, const double* ax[3], const double* aw[3], const int na[3], table3d* t) {
+  int n = k + 1;
+  t->nb = n * n * n;
+  t->np = na[0] * na[1] * na[2];
+  t->phi = (double*)malloc(sizeof(double) * t->np * t->nb);
+  t->grad = (double*)malloc(sizeof(double) * t->np * t->nb * 3);
+  t->wgt = (double*)malloc(sizeof(double) * t->np);
+  if (!t->phi || !t->grad || !t->wgt) return -1;
+  double v[3][66], d[3][66];
+  for (int p2 = 0; p2 < na[2]; ++p2)
+    for (int p1 = 0; p1 < na[1]; ++p1)
+      for (int p0 = 0; p0 < na[0]; ++p0) {
+        int p = p0 + na[0] * (p1 + na[1] * p2);
+        oracle_basis_1d(k, ax[0][p0], v[0], d[0]);
+        oracle_basis_1d(k, ax[1][p1], v[1], d[1]);
+        oracle_basis_1d(k, ax[2][p2], v[2], d[2]);
+        t->wgt[p] = aw[0][p0] * aw[1][p1] * aw[2][p2];
+        for (int j3 = 0; j3 < n; ++j3)
+          for (int j2 = 0; j2 < n; ++j2)
+            for (int j1 = 0; j1 < n; ++j1) {
+              int J = j1 + n * (j2 + n * j3);
+              size_t o = (size_t)p * t->nb + J;
+              t->phi[o] = v[0][j1] * v[1][j2] * v[2][j3];
+              t->grad[o * 3 + 0] = d[0][j1] * v[1][j2] * v[2][j3];
+              t->grad[o * 3 + 1] = v[0][j1] * d[1][j2] * v[2][j3];
+              t->grad[o * 3 + 2] = v[0][j1] * v[1][j2] * d[2][j3];
+            }
+      }
+  return 0;
+}
+
+typedef struct {
+  table3d vol;
+  table3d face[6]; /* face s = 2*dir + side, side 0 at xi_dir = 0, side 1 at 1 */
+  double h[3], vol_T;
+  double area[3]; /* |F| of a face normal to dir */
+  int ncell;
+} oracle_ctx;
+
+static int ctx_build(const oracle_problem* pr, oracle_ctx* cx) {
+  memset(cx, 0, sizeof(*cx));
+  int m = pr->m;
+  double* x = (double*)malloc(sizeof(double) * m);
+  double* w = (double*)malloc(sizeof(double) * m);
+  if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
+  static const double zero = 0.0, one = 1.0, unitw = 1.0;
+  const double* ax[3] = {x, x, x};
+  const double* aw[3] = {w, w, w};
+  int na[3] = {m, m, m};
+  if (table_build(pr->k, ax, aw, na, &cx->vol)) return -1;
+  for (int dir = 0; dir < 3; ++dir)
+    for (int side = 0; side < 2; ++side) {
+      const double* fx[3] = {x, x, x};
+      const double* fw[3] = {w, w, w};
+      int fn[3] = {m, m, m};
+      fx[dir] = side ? &one : &zero;
+      fw[dir] = &unitw;
+      fn[dir] = 1;
+      if (table_build(pr->k, fx, fw, fn, &cx->face[2 * dir + side])) return -1;
+    }
+  free(x);
+  free(w);
+  for (int r = 0; r < 3; ++r) cx->h[r] = (pr->hi[r] - pr->lo[r]) / pr->n[r];
+  cx->vol_T = cx->h[0] * cx->h[1] * cx->h[2];
+  for (int r = 0; r < 3; ++r) cx->area[r] = cx->vol_T / cx->h[r];
+  cx->ncell = pr->n[0] * pr->n[1] * pr->n[2];
+  return 0;
+}
+
+static void ctx_free(oracle_ctx* cx) {
+  table_free(&cx->vol);
+  for (int s = 0; s < 6; ++s) table_free(&cx->face[s]);
+}
+
+/* u and physical gradient of the FE function with coefficients zc at point p of table t */
+static void eval_fe(const table3d* t, int p, const double* zc, const double h[3], double* u, double g[3]) {
+  double uu = 0, g0 = 0, g1 = 0, g2 = 0;
+  const double* ph = t->phi + (size_t)p * t->nb;
+  const double* gr = t->grad + (size_t)p * t->nb * 3;
+  for (int J = 0; J < t->nb; ++J) {
+    uu += zc[J] * ph[J];
+    g0 += zc[J] * gr[3 * J + 0];
+    g1 += zc[J] * gr[3 * J + 1];
+    g2 += zc[J] * gr[3 * J + 2];
+  }
+  *u = uu;
+  /* S_T = diag(1/h) maps reference to physical gradients (Sec. 3.2) */
+  g[0] = g0 / h[0];
+  g[1] = g1 / h[1];
+  g[2] = g2 / h[2];
+}
+
+static double upwind(double um, double up, double bnu) { return bnu >= 0.0 ? um * bnu : up * bnu; }
+
+static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+static void cell_coords(const oracle_problem* pr, int cell, int ic[3]) {
+  ic[0] = cell % pr->n[0];
+  ic[1] = (cell / pr->n[0]) % pr->n[1];
+  ic[2] = cell / (pr->n[0] * pr->n[1]);
+}
+
+static int cell_index(const oracle_problem* pr, const int ic[3]) {
+  return ic[0] + pr->n[0] * (ic[1] + pr->n[1] * ic[2]);
+}
+
+/* a_h(u, phi_i) for all test functions phi_i supported on one cell: the
+ * cell's volume term plus every face of the cell (eq. blf). */
+static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const double* u, int cell, double* y) {
+  const int nb = cx->vol.nb;
+  const double* zc = u + (size_t)cell * nb;
+  const double* h = cx->h;
+  const double DT = pr->D[cell];
+  for (int i = 0; i < nb; ++i) y[i] = 0.0;
+
+  /* volume: (D grad u - b u, grad v)_T + (c u, v)_T */
+  for (int p = 0; p < cx->vol.np; ++p) {
+    double uq, g[3];
+    eval_fe(&cx->vol, p, zc, h, &uq, g);
+    double dx = cx->vol.wgt[p] * cx->vol_T; /* Delta_T * w_i */
+    double fl[3];
+    for (int r = 0; r < 3; ++r) fl[r] = DT * g[r] - pr->b[r] * uq;
+    const double* ph = cx->vol.phi + (size_t)p * nb;
+    const double* gr = cx->vol.grad + (size_t)p * nb * 3;
+    for (int i = 0; i < nb; ++i) {
+      double gv0 = gr[3 * i] / h[0], gv1 = gr[3 * i + 1] / h[1], gv2 = gr[3 * i + 2] / h[2];
+      y[i] += dx * (fl[0] * gv0 + fl[1] * gv1 + fl[2] * gv2 + pr->c * uq * ph[i]);
+    }
+  }
+
+  int ic[3];
+  cell_coords(pr, cell, ic);
+  for (int dir = 0; dir < 3; ++dir)
+    for (int side = 0; side < 2; ++side) {
+      const table3d* ft = &cx->face[2 * dir + side]; /* this cell's trace at the face */
+      int nic[3] = {ic[0], ic[1], ic[2]};
+      nic[dir] += side ? 1 : -1;
+      int interior = nic[dir] >= 0 && nic[dir] < pr->n[dir];
+      double dF = cx->area[dir];
+      if (interior) {
+        /* T- is the lower cell along dir, nu = +e_dir from T- to T+ */
+        int nbr = cell_index(pr, nic);
+        const double* zn = u + (size_t)nbr * nb;
+        const table3d* nt = &cx->face[2 * dir + (1 - side)]; /* neighbour's trace */
+        int this_is_minus = side == 1;
+        double Dm = this_is_minus ? DT : pr->D[nbr];
+        double Dp = this_is_minus ? pr->D[nbr] : DT;
+        double wm = Dp / (Dm + Dp), wp = Dm / (Dm + Dp); /* delta = nu^T D nu = D */
+        double gam = harmonic(Dm, Dp) * pr->sigma * dF / cx->vol_T;
+        double bnu = pr->b[dir];
+        for (int p = 0; p < ft->np; ++p) {
+          double us, gs[3], un, gn[3];
+          eval_fe(ft, p, zc, h, &us, gs);
+          eval_fe(nt, p, zn, h, &un, gn);
+          double um = this_is_minus ? us : un, up = this_is_minus ? un : us;
+          double dnum = this_is_minus ? gs[dir] : gn[dir]; /* nu . grad u- */
+          double dnup = this_is_minus ? gn[dir] : gs[dir];
+          double jump_u = um - up;
+          double avg_flux = wm * Dm * dnum + wp * Dp * dnup; /* nu . {D grad u}_w */
+          double phi_flux = upwind(um, up, bnu);
+          double dx = ft->wgt[p] * dF;
+          const double* ph = ft->phi + (size_t)p * nb;
+          const double* gr = ft->grad + (size_t)p * nb * 3;
+          for (int i = 0; i < nb; ++i) {
+            double v = ph[i], dv = gr[3 * i + dir] / h[dir];
+            /* jump and weighted average of the test function supported on this cell */
+            double jump_v = this_is_minus ? v : -v;
+            double avg_dv = this_is_minus ? wm * Dm * dv : wp * Dp * dv;
+            y[i] += dx * (phi_flux * jump_v - avg_flux * jump_v - avg_dv * jump_u + gam * jump_u * jump_v);
+          }
+        }
+      } else {
+        /* Dirichlet boundary face, nu = outward normal */
+        double sgn = side ? 1.0 : -1.0;
+        double bnu = sgn * pr->b[dir];
+        double gam = DT * pr->sigma * dF / cx->vol_T;
+        for (int p = 0; p < ft->np; ++p) {
+          double us, gs[3];
+          eval_fe(ft, p, zc, h, &us, gs);
+          double dnu = sgn * gs[dir];
+          double dx = ft->wgt[p] * dF;
+          const double* ph = ft->phi + (size_t)p * nb;
+          const double* gr = ft->grad + (size_t)p * nb * 3;
+          for (int i = 0; i < nb; ++i) {
+            double v = ph[i], dnv = sgn * gr[3 * i + dir] / h[dir];
+            y[i] += dx * (upwind(us, 0.0, bnu) * v - DT * dnu * v - DT * dnv * us + gam * us * v);
+          }
+        }
+      }
+    }
+}
+
+static int fill_problem(oracle_problem* pr, const int* n, const double* lo, const double* hi, int k, int m,
+                        const double* D, const double* b, double c, double sigma) {
+  for (int r = 0; r < 3; ++r) {
+    pr->n[r] = n[r];
+    pr->lo[r] = lo[r];
+    pr->hi[r] = hi[r];
+    pr->b[r] = b[r];
+    if (n[r] < 1 || !(hi[r] > lo[r])) return -1;
+  }
+  if (k < 0 || k > 20 || m < 1 || m > 40) return -1;
+  pr->k = k;
+  pr->m = m;
+  pr->D = D;
+  pr->c = c;
+  pr->sigma = sigma;
+  return 0;
+}
+
+/* y = A u restricted to the listed cells (cells == NULL: all cells, in order).
+ * y holds ncell_out blocks of (k+1)^3 values, one per listed cell. */
+int oracle_apply(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
+                 double c, double sigma, const double* u, double* y, const int* cells, int ncells_out) {
+  oracle_problem pr;
+  oracle_ctx cx;
+  if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
+  if (ctx_build(&pr, &cx)) return -2;
+  int nb = cx.vol.nb;
+  int count = cells ? ncells_out : cx.ncell;
+  for (int t = 0; t < count; ++t) {
+    int cell = cells ? cells[t] : t;
+    if (cell < 0 || cell >= cx.ncell) {
+      ctx_free(&cx);
+      return -3;
+    }
+    apply_cell(&pr, &cx, u, cell, y + (size_t)t * nb);
+  }
+  ctx_free(&cx);
+  return 0;
+}
+
+/* F_i = l_h(phi_i): (f, v)_T from f given at the volume quadrature points
+ * (f_qp: [ncells][m^3], NULL means f = 0) plus the Dirichlet terms
+ * -(Phi(0,g,b_nu), v)_F - (nu . D grad v, g)_F + gamma_F (g, v)_F from g given
+ * at the boundary face points (g_qp[s]: side s array, NULL means g = 0). */
+int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
+               double c, double sigma, const double* f_qp, const double* const* g_qp, double* F) {
+  oracle_problem pr;
+  oracle_ctx cx;
+  if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
+  if (ctx_build(&pr, &cx)) return -2;
+  int nb = cx.vol.nb, npv = cx.vol.np;
+  const double* h = cx.h;
+  for (int cell = 0; cell < cx.ncell; ++cell) {
+    double* y = F + (size_t)cell * nb;
+    for (int i = 0; i < nb; ++i) y[i] = 0.0;
+    if (f_qp) {
+      for (int p = 0; p < npv; ++p) {
+        double fx = f_qp[(size_t)cell * npv + p] * cx.vol.wgt[p] * cx.vol_T;
+        const double* ph = cx.vol.phi + (size_t)p * nb;
+        for (int i = 0; i < nb; ++i) y[i] += fx * ph[i];
+      }
+    }
+    int ic[3];
+    cell_coords(&pr, cell, ic);
+    for (int dir = 0; dir < 3; ++dir)
+      for (int side = 0; side < 2; ++side) {
+        int s = 2 * dir + side;
+        int on_boundary = side ? ic[dir] == pr.n[dir] - 1 : ic[dir] == 0;
+        if (!on_boundary || !g_qp || !g_qp[s]) continue;
+        /* face index within the boundary layer: tangential cell indices, lower axis fastest */
+        int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+        int fidx = ic[ta] + pr.n[ta] * ic[tb];
+        const table3d* ft = &cx.face[s];
+        double sgn = side ? 1.0 : -1.0;
+        double bnu = sgn * pr.b[dir];
+        double DT = pr.D[cell];
+        double dF = cx.area[dir];
+        double gam = DT * pr.sigma * dF / cx.vol_T;
+        for (int p = 0; p < ft->np; ++p) {
+          double g = g_qp[s][(size_t)fidx * ft->np + p];
+          double dx = ft->wgt[p] * dF;
+          const double* ph = ft->phi + (size_t)p * nb;
+          const double* gr = ft->grad + (size_t)p * nb * 3;
+          for (int i = 0; i < nb; ++i) {
+            double v = ph[i], dnv = sgn * gr[3 * i + dir] / h[dir];
+            y[i] += dx * (-upwind(0.0, g, bnu) * v - DT * dnv * g + gam * g * v);
+          }
+        }
+      }
+  }
+  ctx_free(&cx);
+  return 0;
+}
+
+/* Physical coordinates of the volume quadrature points: xyz[(cell*m^3 + q)*3 + r]. */
+int oracle_volume_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
+  double* x = (double*)malloc(sizeof(double) * m);
+  double* w = (double*)malloc(sizeof(double) * m);
+  if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
+  double h[3];
+  for (int r = 0; r < 3; ++r) h[r] = (hi[r] - lo[r]) / n[r];
+  size_t o = 0;
+  for (int iz = 0; iz < n[2]; ++iz)
+    for (int iy = 0; iy < n[1]; ++iy)
+      for (int ix = 0; ix < n[0]; ++ix)
+        for (int i3 = 0; i3 < m; ++i3)
+          for (int i2 = 0; i2 < m; ++i2)
+            for (int i1 = 0; i1 < m; ++i1) {
+              xyz[o++] = lo[0] + h[0] * (ix + x[i1]);
+              xyz[o++] = lo[1] + h[1] * (iy + x[i2]);
+              xyz[o++] = lo[2] + h[2] * (iz + x[i3]);
+            }
+  free(x);
+  free(w);
+  return 0;
+}
+
+/* Physical coordinates of the boundary face points of side s = 2*dir + side:
+ * xyz[(face*m^2 + p)*3 + r], faces and points ordered as documented above. */
+int oracle_face_points(const int* n, const double* lo, const double* hi, int m, int s, double* xyz) {
+  if (s < 0 || s > 5) return -1;
+  double* x = (double*)malloc(sizeof(double) * m);
+  double* w = (double*)malloc(sizeof(double) * m);
+  if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
+  int dir = s / 2, side = s % 2;
+  int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+  double h[3];
+  for (int r = 0; r < 3; ++r) h[r] = (hi[r] - lo[r]) / n[r];
+  size_t o = 0;
+  for (int cb = 0; cb < n[tb]; ++cb)
+    for (int ca = 0; ca < n[ta]; ++ca)
+      for (int pb = 0; pb < m; ++pb)
+        for (int pa = 0; pa < m; ++pa) {
+          double p[3];
+          p[dir] = side ? hi[dir] : lo[dir];
+          p[ta] = lo[ta] + h[ta] * (ca + x[pa]);
+          p[tb] = lo[tb] + h[tb] * (cb + x[pb]);
+          xyz[o++] = p[0];
+          xyz[o++] = p[1];
+          xyz[o++] = p[2];
+        }
+  free(x);
+  free(w);
+  return 0;
+}

@@ -1,0 +1,131 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module only draws random numbers and describes workloads; it holds none of
+the method's arithmetic.  Everything is generated with
+``numpy.random.default_rng(seed)`` and handed to both the CUDA library and the
+oracle as plain arrays, so the two sides never need a common generator.
+
+Workloads (Problem A of Sec. 5.1: axis-parallel cells, per-cell constant
+coefficients, q = 2p i.e. m = k+1 Gauss points per direction):
+
+* ``unit_cube_q3_8``  -- 8^3 cells on [0,1]^3, k = 3, D = 1, b = (1, .5, .25),
+  c = 1, penalty 2k(k+1)/h, Dirichlet g = 0, f = 1, u ~ U[-1,1] (seed 0).
+* ``unit_cube_q7_32`` -- 32^3 cells, k = 7, D_T = exp(N(0,1)) per cell (seed 1),
+  same b, c, f, g, u ~ U[-1,1] (seed 2).
+* ``unit_cube_q5_48`` -- 48^3 cells, k = 5, log-normal D (sigma 1, seed 3),
+  f = a sum of 8 seeded sine modes (seed 4).
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+B_DEFAULT = (1.0, 0.5, 0.25)
+C_DEFAULT = 1.0
+
+
+@dataclass
+class Workload:
+    name: str
+    n: tuple
+    k: int
+    D: np.ndarray
+    b: tuple = B_DEFAULT
+    c: float = C_DEFAULT
+    u: np.ndarray | None = None
+    f_kind: str = "one"          # "one" (f = 1), "zero" or "sines"
+    f_params: dict = field(default_factory=dict)
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+
+    @property
+    def ncell(self):
+        return int(np.prod(self.n))
+
+    @property
+    def nb(self):
+        return (self.k + 1) ** 3
+
+    @property
+    def ndof(self):
+        return self.ncell * self.nb
+
+
+def log_normal_D(ncell: int, sigma: float, seed: int) -> np.ndarray:
+    """Per-cell diffusion D_T = exp(sigma * N(0,1)), i.i.d."""
+    return np.exp(sigma * np.random.default_rng(seed).standard_normal(ncell))
+
+
+def uniform_u(ndof: int, seed: int) -> np.ndarray:
+    """DG coefficient vector with i.i.d. U[-1,1] entries."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, ndof)
+
+
+def sine_modes(seed: int, count: int = 8) -> dict:
+    """Parameters of f(x) = sum_l a_l sin(2 pi n_l . x + phi_l): a ~ N(0,1), n in {1..4}^3, phi ~ U[0, 2pi)."""
+    rng = np.random.default_rng(seed)
+    return {"a": rng.standard_normal(count), "n": rng.integers(1, 5, size=(count, 3)),
+            "phi": rng.uniform(0.0, 2.0 * np.pi, count)}
+
+
+def eval_sines(params: dict, xyz: np.ndarray) -> np.ndarray:
+    """Evaluate the sine-mode source at points xyz[..., 3]."""
+    arg = 2.0 * np.pi * (xyz @ params["n"].T.astype(np.float64)) + params["phi"]
+    return np.sin(arg) @ params["a"]
+
+
+def f_at(w: Workload, xyz: np.ndarray) -> np.ndarray:
+    """Source term f at the given quadrature point coordinates xyz[..., 3]."""
+    if w.f_kind == "one":
+        return np.ones(xyz.shape[:-1])
+    if w.f_kind == "zero":
+        return np.zeros(xyz.shape[:-1])
+    if w.f_kind == "sines":
+        return eval_sines(w.f_params, xyz)
+    raise ValueError(w.f_kind)
+
+
+def unit_cube_q3_8() -> Workload:
+    w = Workload("unit_cube_q3_8", (8, 8, 8), 3, np.ones(512))
+    w.u = uniform_u(w.ndof, 0)
+    return w
+
+
+def unit_cube_q7_32() -> Workload:
+    n = (32, 32, 32)
+    w = Workload("unit_cube_q7_32", n, 7, log_normal_D(32 ** 3, 1.0, 1))
+    w.u = uniform_u(w.ndof, 2)
+    return w
+
+
+def unit_cube_q5_48(with_u: bool = True) -> Workload:
+    w = Workload("unit_cube_q5_48", (48, 48, 48), 5, log_normal_D(48 ** 3, 1.0, 3), f_kind="sines",
+                 f_params=sine_modes(4))
+    if with_u:
+        w.u = uniform_u(w.ndof, 5)
+    return w
+
+
+def small_case(n=(3, 2, 4), k=2, sigma_D=1.0, seed=7, b=B_DEFAULT, c=C_DEFAULT, f_kind="one") -> Workload:
+    """Small anisotropic-count mesh for fast parity checks: seeded D and u."""
+    ncell = int(np.prod(n))
+    w = Workload(f"small_{n}_{k}", tuple(n), k, log_normal_D(ncell, sigma_D, seed), b=tuple(b), c=c, f_kind=f_kind)
+    w.u = uniform_u(w.ndof, seed + 1)
+    return w
+
+
+def batch_problems(count: int = 64, seed: int = 5, nmin: int = 4, nmax: int = 24, kmin: int = 2, kmax: int = 8):
+    """Many uneven problems: n ~ U{nmin..nmax}, k ~ U{kmin..kmax} per problem, log-normal D, U[-1,1] u."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(nmin, nmax + 1, size=count)
+    ks = rng.integers(kmin, kmax + 1, size=count)
+    out = []
+    for i in range(count):
+        n = int(ns[i])
+        k = int(ks[i])
+        w = Workload(f"batch{i}", (n, n, n), k, log_normal_D(n ** 3, 1.0, 1000 + i))
+        w.u = uniform_u(w.ndof, 2000 + i)
+        out.append(w)
+    return out

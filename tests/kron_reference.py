@@ -1,0 +1,132 @@
+"""Independent closed form of the WSIPG operator for the oracle pins (test helper).
+
+On an axis-parallel uniform mesh with a per-cell constant scalar D, constant b
+and c, every integrand of eq. blf (Sec. 2) is a tensor product of 1D
+polynomials.  With the orthonormal 1D basis the tangential factors are
+identities, so the whole operator is a sum of Kronecker products of small 1D
+matrices.  The 1D entries here are EXACT polynomial integrals and end-point
+values from ``numpy.polynomial`` -- no quadrature rule and none of the oracle's
+tables -- and the matrix is assembled densely cell by cell and face by face.
+It is a second, structurally different computation of a_h(phi_j, phi_i); it
+shares nothing with the oracle except the documented layouts.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+from numpy.polynomial import legendre as npleg
+
+
+def theta(k: int):
+    """Orthonormal shifted Legendre polynomials on [0,1] as numpy Legendre series objects."""
+    return [np.sqrt(2 * j + 1) * npleg.Legendre.basis(j, domain=[0.0, 1.0]) for j in range(k + 1)]
+
+
+def _integral01(p):
+    P = p.integ()
+    return P(1.0) - P(0.0)
+
+
+def matrices_1d(k: int):
+    th = theta(k)
+    dth = [t.deriv() for t in th]
+    n = k + 1
+    M = np.array([[_integral01(th[i] * th[j]) for j in range(n)] for i in range(n)])
+    S = np.array([[_integral01(dth[i] * dth[j]) for j in range(n)] for i in range(n)])
+    C = np.array([[_integral01(dth[i] * th[j]) for j in range(n)] for i in range(n)])  # test' * trial
+    e0 = np.array([t(0.0) for t in th])
+    e1 = np.array([t(1.0) for t in th])
+    d0 = np.array([t(0.0) for t in dth])
+    d1 = np.array([t(1.0) for t in dth])
+    return dict(M=M, S=S, C=C, e0=e0, e1=e1, d0=d0, d1=d1)
+
+
+def _embed(mat1d, q, n):
+    """Kronecker product acting on index j_q of J = j1 + n j2 + n^2 j3, identity on the others."""
+    eye = np.eye(n)
+    mats = [eye, eye, eye]
+    mats[q] = mat1d
+    # J = j1 + n*(j2 + n*j3): j3 slowest, so kron(order z, y, x)
+    return np.kron(mats[2], np.kron(mats[1], mats[0]))
+
+
+def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1)):
+    """Dense A with A[(T,I),(S,J)] = a_h(phi_{S,J}, phi_{T,I}) (row = test function)."""
+    n = tuple(int(v) for v in n)
+    nb1 = k + 1
+    nb = nb1 ** 3
+    ncell = n[0] * n[1] * n[2]
+    h = [(hi[r] - lo[r]) / n[r] for r in range(3)]
+    volT = h[0] * h[1] * h[2]
+    mt = matrices_1d(k)
+    A = np.zeros((ncell * nb, ncell * nb))
+
+    def cid(ix, iy, iz):
+        return ix + n[0] * (iy + n[1] * iz)
+
+    def blk(t, s):
+        return (slice(t * nb, (t + 1) * nb), slice(s * nb, (s + 1) * nb))
+
+    for iz in range(n[2]):
+        for iy in range(n[1]):
+            for ix in range(n[0]):
+                T = cid(ix, iy, iz)
+                DT = D[T]
+                V = c * volT * np.eye(nb)
+                for r in range(3):
+                    V += DT * volT / h[r] ** 2 * _embed(mt["S"], r, nb1)
+                    V -= b[r] * volT / h[r] * _embed(mt["C"], r, nb1)
+                A[blk(T, T)] += V
+
+    e0, e1, d0, d1 = mt["e0"], mt["e1"], mt["d0"], mt["d1"]
+    for q in range(3):
+        area = volT / h[q]
+        hq = h[q]
+        for iz in range(n[2]):
+            for iy in range(n[1]):
+                for ix in range(n[0]):
+                    ic = [ix, iy, iz]
+                    T = cid(*ic)
+                    # interior face to the upper neighbour along q: T- = T, T+ = neighbour
+                    if ic[q] + 1 < n[q]:
+                        jc = list(ic)
+                        jc[q] += 1
+                        P = cid(*jc)
+                        Dm, Dp = D[T], D[P]
+                        wm, wp = Dp / (Dm + Dp), Dm / (Dm + Dp)
+                        gam = 2 * Dm * Dp / (Dm + Dp) * sigma / hq
+                        bq = b[q]
+                        # trace functionals (rows: test index, cols: trial index), 1D along q
+                        up_m = np.outer(e1, e1) * bq if bq >= 0 else np.zeros((nb1, nb1))
+                        up_p = np.outer(e1, e0) * bq if bq < 0 else np.zeros((nb1, nb1))
+                        # test in T-: jump(phi) = e1_i
+                        mm = up_m - wm * Dm / hq * np.outer(e1, d1) - wm * Dm / hq * np.outer(d1, e1) \
+                            + gam * np.outer(e1, e1)
+                        mp = up_p - wp * Dp / hq * np.outer(e1, d0) + wm * Dm / hq * np.outer(d1, e0) \
+                            - gam * np.outer(e1, e0)
+                        # test in T+: jump(phi) = -e0_i
+                        up_m2 = -np.outer(e0, e1) * bq if bq >= 0 else np.zeros((nb1, nb1))
+                        up_p2 = -np.outer(e0, e0) * bq if bq < 0 else np.zeros((nb1, nb1))
+                        pm = up_m2 + wm * Dm / hq * np.outer(e0, d1) - wp * Dp / hq * np.outer(d0, e1) \
+                            - gam * np.outer(e0, e1)
+                        pp = up_p2 + wp * Dp / hq * np.outer(e0, d0) + wp * Dp / hq * np.outer(d0, e0) \
+                            + gam * np.outer(e0, e0)
+                        A[blk(T, T)] += area * _embed(mm, q, nb1)
+                        A[blk(T, P)] += area * _embed(mp, q, nb1)
+                        A[blk(P, T)] += area * _embed(pm, q, nb1)
+                        A[blk(P, P)] += area * _embed(pp, q, nb1)
+                    # Dirichlet faces
+                    for side in (0, 1):
+                        on_b = (ic[q] == 0) if side == 0 else (ic[q] == n[q] - 1)
+                        if not on_b:
+                            continue
+                        DT = D[T]
+                        gam = DT * sigma / hq
+                        sgn = 1.0 if side else -1.0
+                        ev = e1 if side else e0
+                        dv = sgn * (d1 if side else d0) / hq  # nu . grad of the 1D factor
+                        bnu = sgn * b[q]
+                        mat = (bnu * np.outer(ev, ev) if bnu >= 0 else 0.0) - DT * np.outer(ev, dv) \
+                            - DT * np.outer(dv, ev) + gam * np.outer(ev, ev)
+                        A[blk(T, T)] += area * _embed(mat, q, nb1)
+    return A
