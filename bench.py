@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free DG operator (one JSON line on rank 0).
+
+A step is one FP64 residual evaluation r = A u - F (Algorithm 1 of Sec. 3.6 plus
+the right hand side) on the 32^3-cell, Q_7 unit-cube workload with per-cell
+log-normal diffusion (16.8 M DOF), inputs resident in HBM.  The vectors (u, r:
+134 MB each) and the work buffers (335 MB) are larger than the 129 MB L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (direct quadrature, single thread)
+on a bounded sample of the same workload's cells on the host cores.
+Multi-GPU runs are independent replicas (one problem per rank, weak scaling):
+the operator application needs no data-path collective.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# FP64 peak of one GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz (unit counts and max clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+# DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
+# kernels as they were when profiled, keyed by the sha256 of the kernel source at that time.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_1711_10885_gb300", "csrc", "dg_kernels.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """CPU oracle on bounded samples of the workload's cells (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1711_10885_gb300 import inputs
+    oracle.build()
+    w = inputs.unit_cube_q7_32()
+    pr = oracle.Problem(w.n, w.k, w.D, b=w.b, c=w.c)
+    # size one step's sample so that warmup + steps take about two minutes
+    t0 = time.perf_counter()
+    oracle.apply(pr, w.u, cells=list(range(8)))
+    per_cell = (time.perf_counter() - t0) / 8
+    budget_s = 120.0 / max(1, args.steps + args.warmup)
+    cells_per_step = int(max(8, min(w.ncell, budget_s / per_cell)))
+    rng = np.random.default_rng(99)
+    for _ in range(args.warmup):
+        oracle.apply(pr, w.u, cells=rng.choice(w.ncell, cells_per_step, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply(pr, w.u, cells=rng.choice(w.ncell, cells_per_step, replace=False))
+    dt = time.perf_counter() - t0
+    mdofs = args.steps * cells_per_step * w.nb / dt / 1e6
+    sample = f"{cells_per_step} random cells of the 32^3 Q7 workload per step (A u on those cells)"
+    line = {"metric": "DG FP64 residual apply throughput, 32^3 cells Q7 (16.8M DOF)", "value": mdofs,
+            "unit": "MDOF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "unit_cube_q7_32", "cells": [32, 32, 32], "k": 7, "dofs": w.ndof},
+            "impl": "reference",
+            "cpu_baseline": {"value": mdofs, "unit": "MDOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mdofs, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, seconds=15.0):
+    """Oracle (single thread, direct quadrature) on a bounded sample of the same workload's cells."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    pr = oracle.Problem(w.n, w.k, w.D, b=w.b, c=w.c)
+    t0 = time.perf_counter()
+    oracle.apply(pr, w.u, cells=list(range(8)))
+    per_cell = (time.perf_counter() - t0) / 8
+    count = int(max(16, min(w.ncell, seconds / per_cell)))
+    cells = np.random.default_rng(7).choice(w.ncell, count, replace=False)
+    t0 = time.perf_counter()
+    oracle.apply(pr, w.u, cells=cells)
+    dt = time.perf_counter() - t0
+    return {"value": count * w.nb / dt / 1e6, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"A u on {count} random cells of the 32^3 Q7 workload ({dt:.1f} s, one thread)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1711_10885_gb300 import dg, flops, inputs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    w = inputs.unit_cube_q7_32()
+    op = dg.operator_for(w)
+    u = torch.tensor(w.u, device=dev)
+    r = torch.empty_like(u)
+    N = w.k + 1
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        op.apply_residual(u, r)
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        op.apply_residual(u, r)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    # per-kernel durations on the launching stream (same kernels, same launch configuration)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    for i in range(args.steps):
+        ev[3 * i].record(stream)
+        op.apply_stage(0, u, r, residual=True)
+        ev[3 * i + 1].record(stream)
+        op.apply_stage(1, u, r, residual=True)
+        ev[3 * i + 2].record(stream)
+    barrier()
+    cell_ms = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps)) / args.steps
+    face_ms = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps)) / args.steps
+    clocks = sampler.stop() if sampler else None
+
+    # end to end through the C ABI with host buffers: H2D of u, apply, D2H of r
+    u_h = torch.tensor(w.u).pin_memory()
+    r_h = torch.empty_like(u_h).pin_memory()
+    for _ in range(2):
+        u.copy_(u_h, non_blocking=True)
+        op.apply_residual(u, r)
+        r_h.copy_(r, non_blocking=True)
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(e2e_steps):
+        u.copy_(u_h, non_blocking=True)
+        op.apply_residual(u, r)
+        r_h.copy_(r, non_blocking=True)
+    e3.record(stream)
+    barrier()
+    e2e_ms = e2.elapsed_time(e3) / e2e_steps
+
+    # other precisions / operations of the same path, reported alongside
+    extra = {}
+    for name, fn, x in (("jacobian_f64", op.apply_jacobian, u), ("residual_f32", op.apply_residual, u.float())):
+        y = torch.empty_like(x)
+        for _ in range(3):
+            fn(x, y)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(20):
+            fn(x, y)
+        b.record(stream)
+        b.synchronize()
+        extra[name + "_mdofs"] = w.ndof * 20 / (a.elapsed_time(b) * 1e-3) / 1e6
+
+    if ws > 1:
+        t = torch.tensor([ms, e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+
+    mdofs = ws * w.ndof * args.steps / (ms * 1e-3) / 1e6
+    cell_fl = flops.cell_kernel_flops(N) * w.ncell
+    face_fl = flops.face_kernel_flops(N, w.n, residual=True) * w.ncell
+    dominant = ("dg_cell_kernel", cell_fl, cell_ms) if cell_ms >= face_ms else ("dg_face_kernel", face_fl, face_ms)
+    achieved = dominant[1] / (dominant[2] * 1e-3) / 1e12
+    src_hash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get((dominant[0], src_hash))
+    line = {
+        "metric": "DG FP64 residual apply throughput, 32^3 cells Q7 (16.8M DOF)",
+        "value": mdofs, "unit": "MDOF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "unit_cube_q7_32", "cells": [32, 32, 32], "k": 7, "dofs": w.ndof,
+                   "D": "log-normal sigma 1 per cell", "b": list(w.b), "c": w.c, "penalty": "2k(k+1)/h",
+                   "l2": "inputs larger than L2 (u, r 134 MB; work 335 MB), no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "kernel": dominant[0], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (unit counts and max clock)",
+                     "flops_per_launch": dominant[1]},
+        "kernels_ms": {"dg_cell_kernel": cell_ms, "dg_face_kernel": face_ms},
+        "executed_flops_per_dof": (cell_fl + face_fl) / w.ndof,
+        "paper_flopdof": flops.paper_flopdof(w.k),
+        "fp64_tflops_executed": (cell_fl + face_fl) / (ms / args.steps * 1e-3) / 1e12,
+        "e2e": {"value": ws * w.ndof / (e2e_ms * 1e-3) / 1e6, "unit": "MDOF/s", "h2d_bytes_per_step": 8 * w.ndof,
+                "d2h_bytes_per_step": 8 * w.ndof},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "extra": extra,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    op.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * dg.h -- C ABI of the GB300 matrix-free DG operator library (libdg.so).
+ *
+ * The library applies the weighted symmetric interior penalty (WSIPG) DG
+ * operator of Muething, Piatkowski & Bastian, "High-performance
+ * Implementation of Matrix-free High-order Discontinuous Galerkin Methods"
+ * (arXiv 1711.10885), for the stationary convection-diffusion-reaction problem
+ *     -div(D grad u) + div(b u) + c u = f  in Omega,   u = g on dOmega
+ * (Sec. 2, eq. modelproblem without the time derivative) on an axis-parallel,
+ * uniform cuboid mesh with the tensor-product space Q_k (Sec. 3.1) and the
+ * (k+1)^3-point Gauss-Legendre rule (Problem A of Sec. 5.1: q = 2p).
+ *
+ * Numbering and layouts (all arrays are plain, contiguous, C order):
+ *   cells      cell = ix + nx*(iy + ny*iz)                       (x fastest)
+ *   DOFs       vector[cell*(k+1)^3 + J],  J = j1 + n*(j2 + n*j3), n = k+1,
+ *              coefficients of the ORTHONORMAL shifted Legendre basis on the
+ *              reference cell [0,1]^3: phi_J = theta_j1 theta_j2 theta_j3,
+ *              theta_j(x) = sqrt(2j+1) P_j(2x-1)  (the "L2-orthogonal
+ *              Legendre" basis of Sec. 2; the mass matrix is |T| I).
+ *   vol. pts   f_qp[cell*m^3 + q],  q = i1 + m*(i2 + m*i3), m = k+1.
+ *   faces      boundary side s = 2*dir + (0: lower, 1: upper), dir 0=x,1=y,2=z;
+ *              face f of side s = c_a + n_a*c_b over the two tangential cell
+ *              indices (a < b); its m^2 points p = p_a + m*p_b.
+ *
+ * Operator (Sec. 2, eq. blf):  (A u)_i = a_h(u, phi_i).  Right hand side
+ * F_i = l_h(phi_i) with f and Dirichlet data g.  Residual r = A u - F.
+ * Jacobian application y = A z (the problem is linear, so this is the
+ * operator without f and g).  Readings where the paper is ambiguous:
+ * weighted average {v}_w = w- v- + w+ v+; penalty
+ *   gamma_F = <D-,D+> * sigma * |F| / min(|T-|,|T+|),  <a,b> = 2ab/(a+b),
+ * with the caller's sigma (dg_penalty_sigma gives the two conventions);
+ * boundary faces use D- and |T-|; all boundary faces are Dirichlet; interior
+ * faces are oriented from the lower-index cell T- to T+ along the axis.
+ *
+ * Ownership: the caller owns every vector it passes (device pointers for the
+ * *_dev arguments, in layout above, 8-byte (FP64) or 4-byte (FP32) elements,
+ * input and output must not alias).  The library owns the handle and all
+ * memory reachable from it (tables, coefficients, right hand side, work
+ * buffers) and frees it in dg_destroy.  Host pointers passed to dg_setup are
+ * read during the call only.
+ *
+ * Streams: every `stream` argument is a cudaStream_t passed as void* (NULL =
+ * legacy default stream).  Apply calls are asynchronous on that stream.
+ *
+ * Errors: every call returns DG_OK (0) or a negative DG_ERR_* code and never
+ * aborts; dg_last_error() returns a message for the calling thread's last
+ * failure.  Calls on one handle must not run concurrently from several host
+ * threads (the handle's work buffers are shared by its applies).
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DG_OK = 0,
+  DG_ERR_INVALID_ARG = -1, /* bad size, degree, coefficient or pointer         */
+  DG_ERR_CUDA = -2,        /* a CUDA runtime call failed (message has details) */
+  DG_ERR_OOM = -3,         /* device allocation failed                         */
+  DG_ERR_NOT_CONVERGED = -4,
+  DG_ERR_TIMEOUT = -5,
+  DG_ERR_NAN = -6
+};
+
+enum { DG_F64 = 0, DG_F32 = 1 };
+
+#define DG_MAX_DEGREE 10
+
+typedef struct dg_handle dg_handle;
+
+/* Axis-parallel uniform cuboid mesh [lo, hi] with n[d] cells per axis (Sec. 2, maps mu_T are
+ * translations plus axis scalings: S_T = diag(1/h), Delta_T = h_x h_y h_z, Sec. 3.2). */
+typedef struct {
+  double lo[3], hi[3];
+  int32_t n[3];
+} dg_mesh;
+
+/* Coefficients of eq. modelproblem: D = D_T * I constant per cell (D_cell[ncells] on the host,
+ * or NULL to use D_const everywhere; every D_T must be finite and > 0), constant velocity b,
+ * constant reaction c, and the penalty factor sigma of gamma_F (see above). */
+typedef struct {
+  const double* D_cell;
+  double D_const;
+  double b[3];
+  double c;
+  double sigma;
+} dg_coeffs;
+
+/* Dirichlet data g at the boundary face points: g_qp[s] is a host array of
+ * (faces of side s) * (k+1)^2 values, or NULL for g = 0 on that side. */
+typedef struct {
+  const double* g_qp[6];
+} dg_bc;
+
+/* Penalty factor sigma for degree k.  mode 0: 2k(k+1) (the benchmark convention "2k(k+1)/h"
+ * for D = 1); mode 1: alpha*k*(k+d-1) with alpha = 2, d = 3, as printed in Sec. 2. */
+double dg_penalty_sigma(int32_t k, int32_t mode);
+
+/* Build a handle for degree k in [1, DG_MAX_DEGREE] (k = 0 is rejected: the paper's penalty
+ * p(p+d-1) vanishes).  f_qp: host array [ncells][(k+1)^3] of f at the volume points, or NULL
+ * (f = 0).  bc may be NULL (g = 0).  Computes the right hand side F = l_h(phi_i) (Sec. 2) on
+ * the device.  Synchronises `stream` before returning. */
+int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* coeffs, const dg_bc* bc, const double* f_qp,
+             void* stream, dg_handle** out);
+
+int dg_destroy(dg_handle* h);
+
+/* Sizes of the handle's problem: number of cells, DOFs per cell, total DOFs. */
+int dg_sizes(const dg_handle* h, int64_t* ncells, int32_t* dofs_per_cell, int64_t* ndofs);
+
+/* Physical coordinates of the quadrature points, written to a host array:
+ * which = 0: volume points [ncells][(k+1)^3][3]; which = 1+s: boundary side s
+ * [faces][(k+1)^2][3].  Use them to sample f and g for dg_setup. */
+int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz_host);
+
+/* y = A z: matrix-free application of eq. blf by sum factorisation (Algorithm 1 of Sec. 3.6:
+ * volume terms, interior faces, boundary faces).  precision DG_F64 (double vectors) or DG_F32
+ * (float vectors, the same algorithm in single precision). */
+int dg_apply_jacobian(dg_handle* h, const void* z_dev, void* y_dev, int32_t precision, void* stream);
+
+/* r = A u - F (residual evaluation, Sec. 1 and Sec. 2), same precisions as above. */
+int dg_apply_residual(dg_handle* h, const void* u_dev, void* r_dev, int32_t precision, void* stream);
+
+/* One of the two kernels of an apply, for per-kernel timing and profiling.  stage 0 runs the
+ * cell kernel (volume terms and face traces, Algorithm 1 steps 1-3 and the evaluation halves of
+ * steps 4 and 8) from `in` into the handle's work buffers; stage 1 runs the face kernel (face
+ * fluxes, lifting and the final contraction, the integration halves of steps 4-10) from the work
+ * buffers into `out`, subtracting F when `residual` is non-zero.  Stage 0 followed by stage 1 on
+ * the same stream is exactly dg_apply_jacobian (residual = 0) or dg_apply_residual (residual = 1).
+ * The pointer a stage does not use is ignored. */
+int dg_apply_stage(dg_handle* h, int32_t stage, const void* in, void* out, int32_t precision, int32_t residual,
+                   void* stream);
+
+/* Copy the right hand side F = l_h(phi_i) into F_dev (device, given precision). */
+int dg_rhs(dg_handle* h, void* F_dev, int32_t precision, void* stream);
+
+/* Message for the calling thread's last error ("" if none). */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

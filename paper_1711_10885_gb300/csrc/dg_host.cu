@@ -1,0 +1,411 @@
+// dg_host.cu -- C ABI entry points: setup (1D tables, coefficients, right hand side), apply, teardown.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace dgi {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+}
+
+// P_j(2x-1) and its x-derivative for j = 0..jmax (three-term recurrence, differentiated term by term)
+static void shifted_legendre(int jmax, double x, double* p, double* dp) {
+  const double t = 2.0 * x - 1.0;
+  p[0] = 1.0;
+  dp[0] = 0.0;
+  if (jmax >= 1) {
+    p[1] = t;
+    dp[1] = 2.0;
+  }
+  for (int j = 1; j < jmax; ++j) {
+    p[j + 1] = ((2 * j + 1) * t * p[j] - j * p[j - 1]) / (j + 1);
+    dp[j + 1] = ((2 * j + 1) * (2.0 * p[j] + t * dp[j]) - j * dp[j - 1]) / (j + 1);
+  }
+}
+
+// Gauss-Legendre nodes/weights on [0,1] (Sec. 3.1) and the 1D matrices of the kernels.
+static void build_tables(int N, Tables1D* tb) {
+  tb->N = N;
+  double p[MAXN + 2], dp[MAXN + 2];
+  for (int i = 0; i < N; ++i) {
+    double x = 0.5 * (1.0 - std::cos(M_PI * (i + 0.75) / (N + 0.5)));
+    for (int it = 0; it < 60; ++it) {
+      shifted_legendre(N, x, p, dp);
+      const double dx = p[N] / dp[N];
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    shifted_legendre(N, x, p, dp);
+    tb->xi[i] = x;
+    tb->w[i] = 1.0 / (x * (1.0 - x) * dp[N] * dp[N]);
+  }
+  // theta_j(x) = sqrt(2j+1) P_j(2x-1): values / derivatives at the nodes and at the end points
+  double th[MAXN][MAXN], dth[MAXN][MAXN], te[2][MAXN], dte[2][MAXN];
+  for (int i = 0; i < N; ++i) {
+    shifted_legendre(N - 1, tb->xi[i], p, dp);
+    for (int j = 0; j < N; ++j) {
+      th[i][j] = std::sqrt(2.0 * j + 1.0) * p[j];
+      dth[i][j] = std::sqrt(2.0 * j + 1.0) * dp[j];
+    }
+  }
+  for (int s = 0; s < 2; ++s) {
+    shifted_legendre(N - 1, (double)s, p, dp);
+    for (int j = 0; j < N; ++j) {
+      te[s][j] = std::sqrt(2.0 * j + 1.0) * p[j];
+      dte[s][j] = std::sqrt(2.0 * j + 1.0) * dp[j];
+    }
+  }
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) tb->A[i][j] = th[i][j];
+  // Lagrange basis on the Gauss points through the orthonormal expansion
+  //   l_l(x) = sum_j theta_j(x) theta_j(xi_l) w_l   (exact: the N-point rule integrates degree 2N-1)
+  for (int l = 0; l < N; ++l) {
+    for (int i = 0; i < N; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < N; ++j) acc += dth[i][j] * th[l][j];
+      tb->Dt[i][l] = acc * tb->w[l];
+    }
+    for (int s = 0; s < 2; ++s) {
+      double av = 0.0, ad = 0.0;
+      for (int j = 0; j < N; ++j) {
+        av += te[s][j] * th[l][j];
+        ad += dte[s][j] * th[l][j];
+      }
+      tb->L[s][l] = av * tb->w[l];
+      tb->P[s][l] = ad * tb->w[l];
+    }
+  }
+}
+
+__global__ void cast_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+static int cast_launch(const double* a, float* b, int64_t n, cudaStream_t s) {
+  const int64_t blocks64 = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(blocks64 > 152 * 32 ? 152 * 32 : (blocks64 > 0 ? blocks64 : 1));
+  cast_f64_to_f32<<<blocks, 256, 0, s>>>(a, b, n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "cast kernel");
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+static void free_buffers(Buffers& b) {
+  cudaFree(b.D);
+  cudaFree(b.fc);
+  cudaFree(b.F);
+  b = Buffers();
+}
+
+}  // namespace dgi
+
+using namespace dgi;
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+double dg_penalty_sigma(int32_t k, int32_t mode) {
+  if (mode == 1) return 2.0 * k * (k + 2);  // alpha p (p + d - 1), alpha = 2, d = 3
+  return 2.0 * k * (k + 1);
+}
+
+int dg_destroy(dg_handle* h) {
+  if (!h) return DG_OK;
+  free_buffers(h->p64);
+  free_buffers(h->p32);
+  cudaFree(h->work_V);
+  cudaFree(h->work_tr);
+  delete h;
+  return DG_OK;
+}
+
+int dg_sizes(const dg_handle* h, int64_t* ncells, int32_t* dofs_per_cell, int64_t* ndofs) {
+  if (!h) {
+    set_error("dg_sizes: null handle");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (ncells) *ncells = h->ncell;
+  if (dofs_per_cell) *dofs_per_cell = h->N * h->N * h->N;
+  if (ndofs) *ndofs = h->ncell * h->N * h->N * h->N;
+  return DG_OK;
+}
+
+int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* bc, const double* f_qp,
+             void* stream, dg_handle** out) {
+  if (!out) {
+    set_error("dg_setup: out is null");
+    return DG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (!mesh || !co) {
+    set_error("dg_setup: mesh and coefficients are required");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (k < 1 || k > DG_MAX_DEGREE) {
+    set_error("dg_setup: degree k must be in [1, " + std::to_string(DG_MAX_DEGREE) + "]");
+    return DG_ERR_INVALID_ARG;
+  }
+  int64_t ncell = 1;
+  for (int r = 0; r < 3; ++r) {
+    if (mesh->n[r] < 1 || !std::isfinite(mesh->lo[r]) || !std::isfinite(mesh->hi[r]) ||
+        !(mesh->hi[r] > mesh->lo[r])) {
+      set_error("dg_setup: each axis needs n >= 1 and finite lo < hi");
+      return DG_ERR_INVALID_ARG;
+    }
+    ncell *= mesh->n[r];
+  }
+  if (ncell > (int64_t)1 << 30) {
+    set_error("dg_setup: too many cells");
+    return DG_ERR_INVALID_ARG;
+  }
+  for (int r = 0; r < 3; ++r)
+    if (!std::isfinite(co->b[r])) {
+      set_error("dg_setup: velocity must be finite");
+      return DG_ERR_INVALID_ARG;
+    }
+  if (!std::isfinite(co->c) || !std::isfinite(co->sigma) || co->sigma < 0) {
+    set_error("dg_setup: c must be finite and sigma finite and >= 0");
+    return DG_ERR_INVALID_ARG;
+  }
+  std::vector<double> D(ncell);
+  for (int64_t i = 0; i < ncell; ++i) {
+    D[i] = co->D_cell ? co->D_cell[i] : co->D_const;
+    if (!finite_pos(D[i])) {
+      set_error("dg_setup: every D_T must be finite and > 0 (cell " + std::to_string(i) + ")");
+      return DG_ERR_INVALID_ARG;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dg_handle* h = new (std::nothrow) dg_handle();
+  if (!h) {
+    set_error("dg_setup: host allocation failed");
+    return DG_ERR_OOM;
+  }
+  cudaGetDevice(&h->device);
+  h->k = k;
+  h->N = k + 1;
+  h->ncell = ncell;
+  for (int r = 0; r < 3; ++r) {
+    h->n[r] = mesh->n[r];
+    h->lo[r] = mesh->lo[r];
+    h->hi[r] = mesh->hi[r];
+    h->h[r] = (mesh->hi[r] - mesh->lo[r]) / mesh->n[r];
+    h->b[r] = co->b[r];
+  }
+  h->c = co->c;
+  h->sigma = co->sigma;
+  build_tables(h->N, &h->tab);
+
+  const int N = h->N;
+  const int64_t nb = (int64_t)N * N * N;
+  const int64_t ndof = ncell * nb;
+  // face coefficients per cell and face (Sec. 2: weights w+- = delta-+/(delta- + delta+), gamma_F)
+  std::vector<double> fc(ncell * 18);
+  for (int64_t cell = 0; cell < ncell; ++cell) {
+    int ic[3] = {(int)(cell % h->n[0]), (int)((cell / h->n[0]) % h->n[1]), (int)(cell / ((int64_t)h->n[0] * h->n[1]))};
+    const int64_t strides[3] = {1, h->n[0], (int64_t)h->n[0] * h->n[1]};
+    for (int dir = 0; dir < 3; ++dir)
+      for (int side = 0; side < 2; ++side) {
+        double* c3 = &fc[(cell * 6 + 2 * dir + side) * 3];
+        const double hq = h->h[dir];
+        const double Do = D[cell];
+        const bool boundary = side ? ic[dir] == h->n[dir] - 1 : ic[dir] == 0;
+        if (boundary) {
+          c3[0] = Do / hq;
+          c3[1] = 0.0;
+          c3[2] = Do * h->sigma / hq;  // delta- sigma |F| / |T-|
+        } else {
+          const double Dn = D[side ? cell + strides[dir] : cell - strides[dir]];
+          const double sum = Do + Dn;
+          c3[0] = (Dn / sum) * Do / hq;  // w_own D_own / h
+          c3[1] = (Do / sum) * Dn / hq;  // w_nbr D_nbr / h
+          c3[2] = (2.0 * Do * Dn / sum) * h->sigma / hq;
+        }
+      }
+  }
+  std::vector<float> D32(D.begin(), D.end()), fc32(fc.begin(), fc.end());
+
+  int rc = DG_OK;
+  cudaError_t e = cudaSuccess;
+  double* gdev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+#define DG_TRY(call, what)            \
+  do {                                \
+    e = (call);                       \
+    if (e != cudaSuccess) {           \
+      rc = cuda_fail(e, what);        \
+      goto fail;                      \
+    }                                 \
+  } while (0)
+  {
+    DG_TRY(cudaMalloc(&h->p64.D, ncell * sizeof(double)), "cudaMalloc(D)");
+    DG_TRY(cudaMalloc(&h->p32.D, ncell * sizeof(float)), "cudaMalloc(D32)");
+    DG_TRY(cudaMalloc(&h->p64.fc, ncell * 18 * sizeof(double)), "cudaMalloc(fc)");
+    DG_TRY(cudaMalloc(&h->p32.fc, ncell * 18 * sizeof(float)), "cudaMalloc(fc32)");
+    DG_TRY(cudaMalloc(&h->p64.F, ndof * sizeof(double)), "cudaMalloc(F)");
+    DG_TRY(cudaMalloc(&h->p32.F, ndof * sizeof(float)), "cudaMalloc(F32)");
+    DG_TRY(cudaMalloc(&h->work_V, ndof * sizeof(double)), "cudaMalloc(work V)");
+    DG_TRY(cudaMalloc(&h->work_tr, ncell * 12 * N * N * sizeof(double)), "cudaMalloc(work traces)");
+    DG_TRY(cudaMemcpyAsync(h->p64.D, D.data(), ncell * sizeof(double), cudaMemcpyHostToDevice, s), "copy D");
+    DG_TRY(cudaMemcpyAsync(h->p32.D, D32.data(), ncell * sizeof(float), cudaMemcpyHostToDevice, s), "copy D32");
+    DG_TRY(cudaMemcpyAsync(h->p64.fc, fc.data(), ncell * 18 * sizeof(double), cudaMemcpyHostToDevice, s), "copy fc");
+    DG_TRY(cudaMemcpyAsync(h->p32.fc, fc32.data(), ncell * 18 * sizeof(float), cudaMemcpyHostToDevice, s),
+           "copy fc32");
+    // right hand side: f at the volume points goes through the work buffer
+    if (f_qp) {
+      DG_TRY(cudaMemcpyAsync(h->work_V, f_qp, ndof * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
+    } else {
+      DG_TRY(cudaMemsetAsync(h->work_V, 0, ndof * sizeof(double), s), "memset f");
+    }
+    int64_t gsize[6];
+    for (int sd = 0; sd < 6; ++sd) {
+      const int dir = sd / 2, ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+      gsize[sd] = (int64_t)h->n[ta] * h->n[tb] * N * N;
+      if (bc && bc->g_qp[sd]) {
+        DG_TRY(cudaMalloc(&gdev[sd], gsize[sd] * sizeof(double)), "cudaMalloc(g)");
+        DG_TRY(cudaMemcpyAsync(gdev[sd], bc->g_qp[sd], gsize[sd] * sizeof(double), cudaMemcpyHostToDevice, s),
+               "copy g");
+      }
+    }
+    rc = launch_rhs_f64(h, static_cast<const double*>(h->work_V), gdev, static_cast<double*>(h->p64.F), s);
+    if (rc == DG_OK) rc = cast_launch(static_cast<const double*>(h->p64.F), static_cast<float*>(h->p32.F), ndof, s);
+    e = cudaStreamSynchronize(s);
+    for (int sd = 0; sd < 6; ++sd) {
+      cudaFree(gdev[sd]);
+      gdev[sd] = nullptr;
+    }
+    if (rc != DG_OK) goto fail;
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "dg_setup synchronize");
+      goto fail;
+    }
+  }
+#undef DG_TRY
+  *out = h;
+  return DG_OK;
+fail:
+  cudaStreamSynchronize(s);
+  for (int sd = 0; sd < 6; ++sd) cudaFree(gdev[sd]);
+  dg_destroy(h);
+  return rc;
+}
+
+int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
+  if (!h || !xyz || which < 0 || which > 6) {
+    set_error("dg_quadrature_points: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  const int N = h->N;
+  const double* x = h->tab.xi;
+  size_t o = 0;
+  if (which == 0) {
+    for (int iz = 0; iz < h->n[2]; ++iz)
+      for (int iy = 0; iy < h->n[1]; ++iy)
+        for (int ix = 0; ix < h->n[0]; ++ix)
+          for (int i3 = 0; i3 < N; ++i3)
+            for (int i2 = 0; i2 < N; ++i2)
+              for (int i1 = 0; i1 < N; ++i1) {
+                xyz[o++] = h->lo[0] + h->h[0] * (ix + x[i1]);
+                xyz[o++] = h->lo[1] + h->h[1] * (iy + x[i2]);
+                xyz[o++] = h->lo[2] + h->h[2] * (iz + x[i3]);
+              }
+    return DG_OK;
+  }
+  const int sd = which - 1, dir = sd / 2, side = sd % 2;
+  const int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+  for (int cb = 0; cb < h->n[tb]; ++cb)
+    for (int ca = 0; ca < h->n[ta]; ++ca)
+      for (int pb = 0; pb < N; ++pb)
+        for (int pa = 0; pa < N; ++pa) {
+          double pt[3];
+          pt[dir] = side ? h->hi[dir] : h->lo[dir];
+          pt[ta] = h->lo[ta] + h->h[ta] * (ca + x[pa]);
+          pt[tb] = h->lo[tb] + h->h[tb] * (cb + x[pb]);
+          xyz[o++] = pt[0];
+          xyz[o++] = pt[1];
+          xyz[o++] = pt[2];
+        }
+  return DG_OK;
+}
+
+static int check_apply(dg_handle* h, const void* in, void* out, int32_t precision, const char* name) {
+  if (!h || !in || !out) {
+    set_error(std::string(name) + ": null handle or vector");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (in == out) {
+    set_error(std::string(name) + ": input and output must not alias");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (precision != DG_F64 && precision != DG_F32) {
+    set_error(std::string(name) + ": precision must be DG_F64 or DG_F32");
+    return DG_ERR_INVALID_ARG;
+  }
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) {
+    set_error(std::string(name) + ": current device differs from the handle's device");
+    return DG_ERR_INVALID_ARG;
+  }
+  return DG_OK;
+}
+
+int dg_apply_jacobian(dg_handle* h, const void* z, void* y, int32_t precision, void* stream) {
+  if (int rc = check_apply(h, z, y, precision, "dg_apply_jacobian")) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == DG_F64)
+    return launch_apply_f64(h, static_cast<const double*>(z), static_cast<double*>(y), 0, 3, s);
+  return launch_apply_f32(h, static_cast<const float*>(z), static_cast<float*>(y), 0, 3, s);
+}
+
+int dg_apply_residual(dg_handle* h, const void* u, void* r, int32_t precision, void* stream) {
+  if (int rc = check_apply(h, u, r, precision, "dg_apply_residual")) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == DG_F64)
+    return launch_apply_f64(h, static_cast<const double*>(u), static_cast<double*>(r), 1, 3, s);
+  return launch_apply_f32(h, static_cast<const float*>(u), static_cast<float*>(r), 1, 3, s);
+}
+
+int dg_apply_stage(dg_handle* h, int32_t stage, const void* in, void* out, int32_t precision, int32_t residual,
+                   void* stream) {
+  if (stage != 0 && stage != 1) {
+    set_error("dg_apply_stage: stage must be 0 (cell kernel) or 1 (face kernel)");
+    return DG_ERR_INVALID_ARG;
+  }
+  // stage 0 reads `in` only, stage 1 writes `out` only; the unused pointer may be anything non-null
+  if (int rc = check_apply(h, stage == 0 ? in : (const void*)h, stage == 1 ? out : (void*)h, precision,
+                           "dg_apply_stage"))
+    return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int mode = residual ? 1 : 0, stages = stage == 0 ? 1 : 2;
+  if (precision == DG_F64)
+    return launch_apply_f64(h, static_cast<const double*>(in), static_cast<double*>(out), mode, stages, s);
+  return launch_apply_f32(h, static_cast<const float*>(in), static_cast<float*>(out), mode, stages, s);
+}
+
+int dg_rhs(dg_handle* h, void* F, int32_t precision, void* stream) {
+  if (!h || !F || (precision != DG_F64 && precision != DG_F32)) {
+    set_error("dg_rhs: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  const int64_t ndof = h->ncell * h->N * h->N * h->N;
+  const void* src = precision == DG_F64 ? h->p64.F : h->p32.F;
+  const size_t bytes = ndof * (precision == DG_F64 ? sizeof(double) : sizeof(float));
+  cudaError_t e = cudaMemcpyAsync(F, src, bytes, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DG_OK : cuda_fail(e, "dg_rhs copy");
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// dg_internal.h -- host-side state of a dg_handle and the per-precision launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dg.h"
+
+namespace dgi {
+
+constexpr int MAXN = DG_MAX_DEGREE + 1;
+
+// 1D tables in FP64 for n = m = N points/modes (Sec. 3.1), computed once per handle
+struct Tables1D {
+  int N;
+  double xi[MAXN], w[MAXN];      // Gauss-Legendre nodes / weights on [0,1]
+  double A[MAXN][MAXN];          // A[i][j] = theta_j(xi_i)
+  double Dt[MAXN][MAXN];         // Dt[i][l] = l_l'(xi_i)
+  double L[2][MAXN], P[2][MAXN]; // l_l(s), l_l'(s) for s = 0, 1
+};
+
+struct Buffers {
+  void* D = nullptr;       // per-cell diffusion            [ncell]
+  void* fc = nullptr;      // per-cell face coefficients    [ncell][6][3]
+  void* F = nullptr;       // right hand side               [ncell][N^3]
+};
+
+}  // namespace dgi
+
+struct dg_handle {
+  int k = 0, N = 0;
+  int n[3] = {0, 0, 0};
+  int64_t ncell = 0;
+  double lo[3], hi[3], h[3];
+  double b[3] = {0, 0, 0};
+  double c = 0, sigma = 0;
+  dgi::Tables1D tab;
+  dgi::Buffers p64, p32;   // FP64 and FP32 copies of the coefficient data
+  void* work_V = nullptr;  // point-space residual scratch [ncell][N^3] (sized for FP64)
+  void* work_tr = nullptr; // face trace scratch [ncell][6][2][N^2] (sized for FP64)
+  int device = 0;
+};
+
+namespace dgi {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// mode 0: y = A z, mode 1: y = A z - F; stages: bit 0 cell kernel, bit 1 face kernel (3 = full apply)
+int launch_apply_f64(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s);
+int launch_apply_f32(const dg_handle* h, const float* z, float* y, int mode, int stages, cudaStream_t s);
+// F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null)
+int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s);
+
+}  // namespace dgi

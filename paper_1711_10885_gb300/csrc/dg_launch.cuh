@@ -1,0 +1,151 @@
+// dg_launch.cuh -- template launchers shared by the per-precision translation units.
+#pragma once
+
+#include "dg_internal.h"
+#include "dg_kernels.cuh"
+
+namespace dgi {
+
+template <int N, typename T>
+dgk::Tab<N, T> make_tab(const Tables1D& t) {
+  dgk::Tab<N, T> r;
+  for (int i = 0; i < N; ++i) {
+    r.w[i] = (T)t.w[i];
+    for (int j = 0; j < N; ++j) {
+      r.A[i][j] = (T)t.A[i][j];
+      r.Dt[i][j] = (T)t.Dt[i][j];
+      r.DtW[i][j] = (T)(t.w[i] * t.Dt[i][j]);
+    }
+    for (int s = 0; s < 2; ++s) {
+      r.L[s][i] = (T)t.L[s][i];
+      r.P[s][i] = (T)t.P[s][i];
+    }
+  }
+  return r;
+}
+
+template <typename T>
+dgk::Geo<T> make_geo(const dg_handle* h) {
+  dgk::Geo<T> g;
+  const double vol = h->h[0] * h->h[1] * h->h[2];
+  for (int r = 0; r < 3; ++r) {
+    g.n[r] = h->n[r];
+    g.area[r] = (T)(vol / h->h[r]);
+    g.alpha[r] = (T)(vol / (h->h[r] * h->h[r]));
+    g.beta[r] = (T)(-h->b[r] * vol / h->h[r]);
+    g.b[r] = (T)h->b[r];
+  }
+  g.ncell = (int)h->ncell;
+  g.vol = (T)vol;
+  g.creact = (T)(h->c * vol);
+  return g;
+}
+
+template <int N, typename T>
+size_t cell_smem() {
+  return 2 * (size_t)dgk::Launch<N>::CPB * dgk::Lay<N>::CS * sizeof(T);
+}
+template <int N, typename T>
+size_t face_smem() {
+  return (size_t)dgk::Launch<N>::CPB * dgk::Lay<N>::CS * sizeof(T);
+}
+
+template <int N, typename T>
+int set_smem_attrs() {
+  static bool done = false;  // per (N, T) instantiation; attributes are per function
+  if (done) return 0;
+  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cell_smem<N, T>());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel)");
+  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)face_smem<N, T>());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
+  done = true;
+  return 0;
+}
+
+// stages: bit 0 = cell kernel (z -> work buffers), bit 1 = face kernel (work buffers -> y)
+template <int N, typename T>
+int apply_n(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStream_t s) {
+  if (int rc = set_smem_attrs<N, T>()) return rc;
+  const Buffers& bf = sizeof(T) == 8 ? h->p64 : h->p32;
+  const auto tb = make_tab<N, T>(h->tab);
+  const auto geo = make_geo<T>(h);
+  const int cpb = dgk::Launch<N>::CPB;
+  const unsigned grid = (unsigned)((h->ncell + cpb - 1) / cpb);
+  T* V = static_cast<T*>(h->work_V);
+  T* tr = static_cast<T*>(h->work_tr);
+  if (stages & 1)
+    dgk::dg_cell_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, cell_smem<N, T>(), s>>>(
+        tb, geo, z, static_cast<const T*>(bf.D), V, tr);
+  dgk::FaceArgs<T> fa;
+  fa.V = V;
+  fa.traces = tr;
+  fa.fc = static_cast<const T*>(bf.fc);
+  fa.F = mode == 1 ? static_cast<const T*>(bf.F) : nullptr;
+  for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
+  fa.y = y;
+  fa.mode = mode;
+  if (stages & 2) dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");
+  return 0;
+}
+
+template <int N, typename T>
+int rhs_n(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_t s) {
+  if (int rc = set_smem_attrs<N, T>()) return rc;
+  const Buffers& bf = sizeof(T) == 8 ? h->p64 : h->p32;
+  const auto tb = make_tab<N, T>(h->tab);
+  const auto geo = make_geo<T>(h);
+  const int cpb = dgk::Launch<N>::CPB;
+  const unsigned grid = (unsigned)((h->ncell + cpb - 1) / cpb);
+  dgk::FaceArgs<T> fa;
+  fa.V = f;
+  fa.traces = nullptr;
+  fa.fc = static_cast<const T*>(bf.fc);
+  fa.F = nullptr;
+  for (int i = 0; i < 6; ++i) fa.g[i] = g[i];
+  fa.y = F;
+  fa.mode = 2;
+  dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "rhs kernel launch");
+  return 0;
+}
+
+template <typename T>
+int apply_dispatch(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStream_t s) {
+  switch (h->N) {
+    case 2: return apply_n<2, T>(h, z, y, mode, stages, s);
+    case 3: return apply_n<3, T>(h, z, y, mode, stages, s);
+    case 4: return apply_n<4, T>(h, z, y, mode, stages, s);
+    case 5: return apply_n<5, T>(h, z, y, mode, stages, s);
+    case 6: return apply_n<6, T>(h, z, y, mode, stages, s);
+    case 7: return apply_n<7, T>(h, z, y, mode, stages, s);
+    case 8: return apply_n<8, T>(h, z, y, mode, stages, s);
+    case 9: return apply_n<9, T>(h, z, y, mode, stages, s);
+    case 10: return apply_n<10, T>(h, z, y, mode, stages, s);
+    case 11: return apply_n<11, T>(h, z, y, mode, stages, s);
+    default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
+  }
+}
+
+template <typename T>
+int rhs_dispatch(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_t s) {
+  switch (h->N) {
+    case 2: return rhs_n<2, T>(h, f, g, F, s);
+    case 3: return rhs_n<3, T>(h, f, g, F, s);
+    case 4: return rhs_n<4, T>(h, f, g, F, s);
+    case 5: return rhs_n<5, T>(h, f, g, F, s);
+    case 6: return rhs_n<6, T>(h, f, g, F, s);
+    case 7: return rhs_n<7, T>(h, f, g, F, s);
+    case 8: return rhs_n<8, T>(h, f, g, F, s);
+    case 9: return rhs_n<9, T>(h, f, g, F, s);
+    case 10: return rhs_n<10, T>(h, f, g, F, s);
+    case 11: return rhs_n<11, T>(h, f, g, F, s);
+    default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace dgi

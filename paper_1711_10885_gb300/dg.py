@@ -1,0 +1,240 @@
+"""Thin Python binding of libdg.so (argument marshalling only).
+
+Every step of the operator runs in the CUDA library; this module turns torch
+tensors into device pointers and a stream into a ``cudaStream_t`` and calls the
+C ABI declared in ``include/dg.h`` under the same names.  There is no CPU or
+PyTorch fallback: if the compiled library is missing, importing fails loudly.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdg.so")
+
+DG_OK = 0
+DG_F64 = 0
+DG_F32 = 1
+DG_MAX_DEGREE = 10
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dg error {code}: {msg}")
+        self.code = code
+
+
+class dg_mesh(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("n", ctypes.c_int32 * 3)]
+
+
+class dg_coeffs(ctypes.Structure):
+    _fields_ = [("D_cell", _dp), ("D_const", ctypes.c_double), ("b", ctypes.c_double * 3),
+                ("c", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class dg_bc(ctypes.Structure):
+    _fields_ = [("g_qp", _dp * 6)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdg.so not built ({LIB_PATH}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.dg_last_error.restype = ctypes.c_char_p
+    lib.dg_penalty_sigma.restype = ctypes.c_double
+    lib.dg_penalty_sigma.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.dg_setup.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int32, ctypes.POINTER(dg_coeffs),
+                             ctypes.POINTER(dg_bc), _dp, vp, ctypes.POINTER(vp)]
+    lib.dg_destroy.argtypes = [vp]
+    lib.dg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_int64)]
+    lib.dg_quadrature_points.argtypes = [vp, ctypes.c_int32, _dp]
+    lib.dg_apply_jacobian.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.dg_apply_residual.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.dg_rhs.argtypes = [vp, vp, ctypes.c_int32, vp]
+    lib.dg_apply_stage.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32, ctypes.c_int32, vp]
+    return lib
+
+
+lib = _load()
+
+# C-ABI symbols declared in include/dg.h (checked by the CPU test suite)
+EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadrature_points", "dg_apply_jacobian",
+            "dg_apply_residual", "dg_rhs", "dg_last_error", "dg_apply_stage"]
+
+
+def check(rc):
+    if rc != DG_OK:
+        raise DGError(rc, lib.dg_last_error().decode())
+    return rc
+
+
+def dg_penalty_sigma(k: int, mode: int = 0) -> float:
+    return lib.dg_penalty_sigma(k, mode)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _prec(t):
+    import torch
+    if t.dtype == torch.float64:
+        return DG_F64
+    if t.dtype == torch.float32:
+        return DG_F32
+    raise TypeError("vectors must be float64 or float32")
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Operator:
+    """A dg_handle: mesh, degree, coefficients and right hand side (dg_setup), freed by close()."""
+
+    def __init__(self, n, k, D=1.0, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0),
+                 hi=(1.0, 1.0, 1.0), f_qp=None, g_qp=None, stream=None):
+        mesh = dg_mesh()
+        for r in range(3):
+            mesh.lo[r], mesh.hi[r], mesh.n[r] = float(lo[r]), float(hi[r]), int(n[r])
+        co = dg_coeffs()
+        self.ncell = int(np.prod([int(v) for v in n]))
+        Darr = np.asarray(D, dtype=np.float64)
+        self._D = None
+        if Darr.ndim == 0:
+            co.D_cell = _dp()
+            co.D_const = float(Darr)
+        else:
+            self._D = _f64(Darr).reshape(-1)
+            if self._D.size != self.ncell:
+                raise ValueError("D must have one value per cell")
+            co.D_cell = self._D.ctypes.data_as(_dp)
+            co.D_const = 0.0
+        for r in range(3):
+            co.b[r] = float(b[r])
+        co.c = float(c)
+        co.sigma = float(sigma) if sigma is not None else dg_penalty_sigma(int(k), 0)
+        keep = []
+        bcp = None
+        if g_qp is not None:
+            bc = dg_bc()
+            for s in range(6):
+                if g_qp[s] is None:
+                    bc.g_qp[s] = _dp()
+                else:
+                    a = _f64(g_qp[s]).reshape(-1)
+                    keep.append(a)
+                    bc.g_qp[s] = a.ctypes.data_as(_dp)
+            bcp = ctypes.byref(bc)
+        fptr = None
+        if f_qp is not None:
+            fa = _f64(f_qp).reshape(-1)
+            keep.append(fa)
+            fptr = fa.ctypes.data_as(_dp)
+        h = ctypes.c_void_p()
+        check(lib.dg_setup(ctypes.byref(mesh), int(k), ctypes.byref(co), bcp, fptr, _stream_ptr(stream),
+                           ctypes.byref(h)))
+        self.h = h
+        self.k = int(k)
+        self.n = tuple(int(v) for v in n)
+        nc, dpc, nd = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        check(lib.dg_sizes(h, ctypes.byref(nc), ctypes.byref(dpc), ctypes.byref(nd)))
+        self.dofs_per_cell = dpc.value
+        self.ndof = nd.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def quadrature_points(self, which: int = 0) -> np.ndarray:
+        m = self.k + 1
+        if which == 0:
+            shape = (self.ncell, m ** 3, 3)
+        else:
+            d = (which - 1) // 2
+            ta, tb = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+            shape = (self.n[ta] * self.n[tb], m ** 2, 3)
+        out = np.empty(shape, dtype=np.float64)
+        check(lib.dg_quadrature_points(self.h, int(which), out.ctypes.data_as(_dp)))
+        return out
+
+    def _vec_check(self, *ts):
+        for t in ts:
+            if not t.is_cuda or not t.is_contiguous() or t.numel() != self.ndof:
+                raise ValueError("vectors must be contiguous CUDA tensors with ndof entries")
+
+    def apply_jacobian(self, z, y=None, stream=None):
+        """y = A z (dg_apply_jacobian)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(z)
+        self._vec_check(z, y)
+        if z.dtype != y.dtype:
+            raise TypeError("z and y must have the same dtype")
+        check(lib.dg_apply_jacobian(self.h, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(y.data_ptr()), _prec(z),
+                                    _stream_ptr(stream)))
+        return y
+
+    def apply_residual(self, u, r=None, stream=None):
+        """r = A u - F (dg_apply_residual)."""
+        import torch
+        if r is None:
+            r = torch.empty_like(u)
+        self._vec_check(u, r)
+        if u.dtype != r.dtype:
+            raise TypeError("u and r must have the same dtype")
+        check(lib.dg_apply_residual(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(r.data_ptr()), _prec(u),
+                                    _stream_ptr(stream)))
+        return r
+
+    def apply_stage(self, stage, x, y, residual=False, stream=None):
+        """One kernel of an apply (dg_apply_stage): stage 0 cell kernel from x, stage 1 face kernel into y."""
+        self._vec_check(x, y)
+        check(lib.dg_apply_stage(self.h, int(stage), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                 _prec(x), int(bool(residual)), _stream_ptr(stream)))
+        return y
+
+    def rhs(self, dtype=None, stream=None):
+        """F = l_h(phi_i) (dg_rhs)."""
+        import torch
+        dtype = dtype or torch.float64
+        F = torch.empty(self.ndof, dtype=dtype, device="cuda")
+        check(lib.dg_rhs(self.h, ctypes.c_void_p(F.data_ptr()), _prec(F), _stream_ptr(stream)))
+        return F
+
+
+def operator_for(w, stream=None, sigma=None):
+    """Build an Operator for an inputs.Workload, with f sampled at the library's own quadrature points."""
+    import numpy as np
+    from . import inputs
+    m3 = (w.k + 1) ** 3
+    if w.f_kind == "zero":
+        f = None
+    elif w.f_kind == "one":
+        f = np.ones(w.ncell * m3)
+    else:
+        probe = Operator(w.n, w.k, w.D, b=w.b, c=w.c, sigma=sigma, lo=w.lo, hi=w.hi, stream=stream)
+        f = inputs.f_at(w, probe.quadrature_points(0))
+        probe.close()
+    return Operator(w.n, w.k, w.D, b=w.b, c=w.c, sigma=sigma, lo=w.lo, hi=w.hi, f_qp=f, stream=stream)

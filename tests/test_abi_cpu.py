@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads, exports every
+function that include/dg.h declares, and rejects invalid arguments before touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1711_10885_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(dg_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["dg_setup", "dg_apply_residual", "dg_apply_jacobian", "dg_destroy", "dg_last_error"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    from paper_1711_10885_gb300 import dg
+    assert set(dg.EXPORTED) <= set(declared_functions())
+
+
+def test_penalty_conventions(lib):
+    lib.dg_penalty_sigma.restype = ctypes.c_double
+    lib.dg_penalty_sigma.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    assert lib.dg_penalty_sigma(3, 0) == 24.0  # 2k(k+1): 24/h for k = 3 and D = 1
+    assert lib.dg_penalty_sigma(7, 1) == 2.0 * 7 * 9  # alpha p (p + d - 1), alpha = 2
+
+
+def test_setup_rejects_invalid_arguments_on_host():
+    from paper_1711_10885_gb300 import dg
+    mesh = dg.dg_mesh()
+    for r in range(3):
+        mesh.lo[r], mesh.hi[r], mesh.n[r] = 0.0, 1.0, 2
+    co = dg.dg_coeffs()
+    co.D_const, co.c, co.sigma = 1.0, 1.0, 4.0
+    h = ctypes.c_void_p()
+
+    def setup(k, mesh=mesh, co=co):
+        return dg.lib.dg_setup(ctypes.byref(mesh), k, ctypes.byref(co), None, None, None, ctypes.byref(h))
+
+    assert setup(0) == -1 and b"degree" in dg.lib.dg_last_error()
+    assert setup(11) == -1
+    bad = dg.dg_coeffs()
+    bad.D_const, bad.c, bad.sigma = -1.0, 1.0, 4.0
+    assert setup(2, co=bad) == -1 and b"D_T" in dg.lib.dg_last_error()
+    bad.D_const = float("nan")
+    assert setup(2, co=bad) == -1
+    bad.D_const, bad.sigma = 1.0, float("inf")
+    assert setup(2, co=bad) == -1
+    m2 = dg.dg_mesh()
+    for r in range(3):
+        m2.lo[r], m2.hi[r], m2.n[r] = 0.0, 1.0, 2
+    m2.n[1] = 0
+    assert setup(2, mesh=m2) == -1
+    m2.n[1], m2.hi[2] = 2, 0.0
+    assert setup(2, mesh=m2) == -1
+    assert dg.lib.dg_setup(ctypes.byref(mesh), 2, ctypes.byref(co), None, None, None, None) == -1
+    assert h.value is None
