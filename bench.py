@@ -162,6 +162,24 @@ def cpu_baseline(w, seconds=15.0):
             "sample": f"A u on {count} random cells of the 32^3 Q7 workload ({dt:.1f} s, one thread)"}
 
 
+def run_profile(args):
+    """Minimal launch sequence for profilers: W + K residual applies on the bench workload."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, inputs
+    torch.cuda.set_device(0)
+    w = inputs.unit_cube_q7_32()
+    op = dg.operator_for(w)
+    u = torch.tensor(w.u, device="cuda")
+    r = torch.empty_like(u)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup + args.steps):
+        op.apply_residual(u, r)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
+    op.close()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -303,11 +321,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run warmup + steps residual applies (for ncu launch lists and captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
     else:
         run_ours(args)
 
