@@ -38,17 +38,25 @@ static void shifted_legendre(int jmax, double x, double* p, double* dp) {
 static void build_tables(int N, Tables1D* tb) {
   tb->N = N;
   double p[MAXN + 2], dp[MAXN + 2];
-  for (int i = 0; i < N; ++i) {
+  // Newton on P_N(2x-1) for the lower half of the nodes; the rule is symmetric about 1/2, and the
+  // kernels rely on that symmetry exactly (even-odd form), so the upper half is mirrored
+  for (int i = 0; i < (N + 1) / 2; ++i) {
     double x = 0.5 * (1.0 - std::cos(M_PI * (i + 0.75) / (N + 0.5)));
-    for (int it = 0; it < 60; ++it) {
-      shifted_legendre(N, x, p, dp);
-      const double dx = p[N] / dp[N];
-      x -= dx;
-      if (std::fabs(dx) < 1e-16) break;
+    if (2 * i + 1 == N) {
+      x = 0.5;
+    } else {
+      for (int it = 0; it < 60; ++it) {
+        shifted_legendre(N, x, p, dp);
+        const double dx = p[N] / dp[N];
+        x -= dx;
+        if (std::fabs(dx) < 1e-16) break;
+      }
     }
     shifted_legendre(N, x, p, dp);
     tb->xi[i] = x;
     tb->w[i] = 1.0 / (x * (1.0 - x) * dp[N] * dp[N]);
+    tb->xi[N - 1 - i] = 1.0 - x;
+    tb->w[N - 1 - i] = tb->w[i];
   }
   // theta_j(x) = sqrt(2j+1) P_j(2x-1): values / derivatives at the nodes and at the end points
   double th[MAXN][MAXN], dth[MAXN][MAXN], te[2][MAXN], dte[2][MAXN];

@@ -24,33 +24,50 @@
 // the cell tensor held in shared memory, with the 1D matrices as kernel
 // parameters (constant bank, broadcast to the warp).  The rotation between
 // directions is implicit: the next pass reads lines along the next axis.
+//
+// Every 1D operator is applied in even-odd form: the Gauss points are symmetric
+// about 1/2 and theta_j(1-x) = (-1)^j theta_j(x), so each N x N matrix splits into
+// two half-size blocks acting on the symmetric and antisymmetric parts of the
+// line.  That is the same product with about 40 % fewer FP64 operations, which
+// is what bounds these kernels on GB300 (FP64 issue rate, not memory).
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace dgk {
 
-// 1D tables for n = m = N: basis at the Gauss points, collocation derivative, face extrapolation.
+// 1D tables for n = m = N (Sec. 3.1), in even-odd form.  H = floor(N/2) point pairs, C = ceil(N/2).
 template <int N, typename T>
 struct Tab {
-  T A[N][N];    // A[i][j] = theta_j(xi_i)
-  T Dt[N][N];   // Dt[i][l] = l_l'(xi_i)   (Lagrange basis on the Gauss points)
-  T DtW[N][N];  // DtW[i][l] = w_i * Dt[i][l]
-  T w[N];       // Gauss weights on [0,1]
-  T L[2][N];    // L[s][l] = l_l(s),  s = 0, 1 (face at xi = s)
-  T P[2][N];    // P[s][l] = l_l'(s)
+  static constexpr int H = N / 2, C = (N + 1) / 2;
+  // basis at the points A[i][j] = theta_j(xi_i): AE[i][e] = A[i][2e] (i < C), AO[i][o] = A[i][2o+1] (i < H)
+  T AE[C][C];
+  T AO[C][H];
+  // collocation derivative M[i][l] = l_l'(xi_i) (Lagrange basis on the Gauss points) and the weighted
+  // transpose B[l][i] = w_i M[i][l]; both satisfy X[N-1-i][N-1-l] = -X[i][l].  Half blocks:
+  //   XHm[i][l] = (X[i][l] - X[i][N-1-l]) / 2  (i < C, l < H),  XHp[i][l] = (X[i][l] + X[i][N-1-l]) / 2  (i < H, l < C)
+  T DHm[C][H];
+  T DHp[H][C];
+  T BHm[C][H];
+  T BHp[H][C];
+  // face extrapolation from a point line: value/derivative at xi = 1 are LS.s + LD.d and PS.s + PD.d,
+  // at xi = 0 they are LS.s - LD.d and -PS.s + PD.d (s, d: symmetric / antisymmetric parts)
+  T LS[C], LD[H], PS[C], PD[H];
+  T w[N];     // Gauss weights on [0,1]
+  T L[2][N];  // L[s][l] = l_l(s): lift of a face value onto the normal line
+  T P[2][N];  // P[s][l] = l_l'(s): lift of a face normal-derivative weight
 };
 
 template <typename T>
 struct Geo {
   int n[3];
   int ncell;
-  T vol;      // |T| = h_x h_y h_z
-  T area[3];  // |F| of a face normal to axis r
-  T alpha[3]; // |T| / h_r^2       (times D_T: diffusion weight of d_r u)
-  T beta[3];  // -b_r |T| / h_r    (convection weight of u)
-  T b[3];     // velocity
-  T creact;   // c |T|
+  T vol;       // |T| = h_x h_y h_z
+  T area[3];   // |F| of a face normal to axis r
+  T alpha[3];  // |T| / h_r^2       (times D_T: diffusion weight of d_r u)
+  T beta[3];   // -b_r |T| / h_r    (convection weight of u)
+  T b[3];      // velocity
+  T creact;    // c |T|
 };
 
 // shared-memory tensor of one cell: element (i1,i2,i3) at i1 + (N+1)*(i2 + N*i3)
@@ -78,38 +95,95 @@ __device__ __forceinline__ void store_line(T* s, int base, int st, const T (&x)[
   for (int l = 0; l < N; ++l) s[base + l * st] = x[l];
 }
 
-// y[i] = sum_j M[i][j] x[j]
+// symmetric / antisymmetric parts of a point line: s[i] = x[i] + x[N-1-i], d[i] = x[i] - x[N-1-i]
+// (i < H); for odd N the middle point goes to s[H] = x[H] unchanged.
 template <int N, typename T>
-__device__ __forceinline__ void mv(const T (&M)[N][N], const T (&x)[N], T (&y)[N]) {
+__device__ __forceinline__ void split_sd(const T (&x)[N], T (&s)[(N + 1) / 2], T (&d)[N / 2 > 0 ? N / 2 : 1]) {
+  constexpr int H = N / 2;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    T acc = M[i][0] * x[0];
+  for (int i = 0; i < H; ++i) {
+    s[i] = x[i] + x[N - 1 - i];
+    d[i] = x[i] - x[N - 1 - i];
+  }
+  if (N & 1) s[H] = x[H];
+}
+
+// modal -> points along one line: y[i] = sum_j theta_j(xi_i) x[j]   (eq. evalfe, one direction)
+template <int N, typename T>
+__device__ __forceinline__ void eo_fwd(const Tab<N, T>& tb, const T (&x)[N], T (&y)[N]) {
+  constexpr int H = N / 2, C = (N + 1) / 2;
+  T e[C], o[H];
 #pragma unroll
-    for (int j = 1; j < N; ++j) acc = fma(M[i][j], x[j], acc);
-    y[i] = acc;
+  for (int i = 0; i < C; ++i) {
+    T acc = tb.AE[i][0] * x[0];
+#pragma unroll
+    for (int k = 1; k < C; ++k) acc = fma(tb.AE[i][k], x[2 * k], acc);
+    e[i] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T acc = tb.AO[i][0] * x[1];
+#pragma unroll
+    for (int k = 1; k < H; ++k) acc = fma(tb.AO[i][k], x[2 * k + 1], acc);
+    o[i] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    y[i] = e[i] + o[i];
+    y[N - 1 - i] = e[i] - o[i];
+  }
+  if (N & 1) y[H] = e[H];
+}
+
+// points -> modal along one line: y[j] = sum_i theta_j(xi_i) x[i]   (test functions, eq. evalblf)
+template <int N, typename T>
+__device__ __forceinline__ void eo_bwd(const Tab<N, T>& tb, const T (&x)[N], T (&y)[N]) {
+  constexpr int H = N / 2, C = (N + 1) / 2;
+  T s[C], d[H > 0 ? H : 1];
+  split_sd<N, T>(x, s, d);
+#pragma unroll
+  for (int k = 0; k < C; ++k) {
+    T acc = tb.AE[0][k] * s[0];
+#pragma unroll
+    for (int i = 1; i < C; ++i) acc = fma(tb.AE[i][k], s[i], acc);
+    y[2 * k] = acc;
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    T acc = tb.AO[0][k] * d[0];
+#pragma unroll
+    for (int i = 1; i < H; ++i) acc = fma(tb.AO[i][k], d[i], acc);
+    y[2 * k + 1] = acc;
   }
 }
-// y[j] = y0[j] + sum_i M[i][j] x[i]
+
+// points -> points with a centro-antisymmetric matrix X given by its half blocks (Hm, Hp), from the
+// split parts (s, d) of the input line: out[i] = Gp[i] + Gm[i], out[N-1-i] = Gp[i] - Gm[i].
 template <int N, typename T>
-__device__ __forceinline__ void mvt_acc(const T (&M)[N][N], const T (&x)[N], T (&y)[N]) {
+__device__ __forceinline__ void eo_anti(const T (&Hm)[(N + 1) / 2][N / 2], const T (&Hp)[N / 2][(N + 1) / 2],
+                                        const T (&s)[(N + 1) / 2], const T (&d)[N / 2], T (&out)[N]) {
+  constexpr int H = N / 2, C = (N + 1) / 2;
+  T gp[C], gm[H];
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    T acc = y[j];
+  for (int i = 0; i < C; ++i) {
+    T acc = Hm[i][0] * d[0];
 #pragma unroll
-    for (int i = 0; i < N; ++i) acc = fma(M[i][j], x[i], acc);
-    y[j] = acc;
+    for (int l = 1; l < H; ++l) acc = fma(Hm[i][l], d[l], acc);
+    gp[i] = acc;
   }
-}
-// y[j] = sum_i M[i][j] x[i]
-template <int N, typename T>
-__device__ __forceinline__ void mvt(const T (&M)[N][N], const T (&x)[N], T (&y)[N]) {
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    T acc = M[0][j] * x[0];
+  for (int i = 0; i < H; ++i) {
+    T acc = Hp[i][0] * s[0];
 #pragma unroll
-    for (int i = 1; i < N; ++i) acc = fma(M[i][j], x[i], acc);
-    y[j] = acc;
+    for (int l = 1; l < C; ++l) acc = fma(Hp[i][l], s[l], acc);
+    gm[i] = acc;
   }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    out[i] = gp[i] + gm[i];
+    out[N - 1 - i] = gp[i] - gm[i];
+  }
+  if (N & 1) out[H] = gp[H];
 }
 
 template <int N>
@@ -143,6 +217,45 @@ __device__ __forceinline__ void gstore_cells(T* __restrict__ g, const T* sbuf, i
   }
 }
 
+// One derivative pass along axis `dir` for the line u (values at the points) owned by this thread:
+// v (+)= B [ w_perp (sa d_r u + sb u) ] and the two face traces of this line.
+template <int N, typename T, bool FIRST>
+__device__ __forceinline__ void deriv_line(const Tab<N, T>& tb, const T (&u)[N], T (&v)[N], T sa, T sb, T sc,
+                                           T* __restrict__ tr, int NN, int t) {
+  constexpr int H = N / 2, C = (N + 1) / 2;
+  T s[C], d[H > 0 ? H : 1], gr[N], X[N];
+  split_sd<N, T>(u, s, d);
+  eo_anti<N, T>(tb.DHm, tb.DHp, s, d, gr);  // d u / d xi_r at the points (reference derivative)
+#pragma unroll
+  for (int i = 0; i < N; ++i) X[i] = fma(sa, gr[i], sb * u[i]);  // eq. gauss_points, times w_perp
+  T xs[C], xd[H > 0 ? H : 1], c[N];
+  split_sd<N, T>(X, xs, xd);
+  eo_anti<N, T>(tb.BHm, tb.BHp, xs, xd, c);  // sum_i w_i l_l'(xi_i) X[i]
+  if (FIRST) {
+#pragma unroll
+    for (int l = 0; l < N; ++l) v[l] = fma(sc * tb.w[l], u[l], c[l]);  // + c |T| w u (reaction)
+  } else {
+#pragma unroll
+    for (int l = 0; l < N; ++l) v[l] += c[l];
+  }
+  // traces at xi_r = 1 and 0 (value, reference normal derivative), Sec. 3.4
+  T t1 = T(0), t2 = T(0), q1 = T(0), q2 = T(0);
+#pragma unroll
+  for (int l = 0; l < C; ++l) {
+    t1 = fma(tb.LS[l], s[l], t1);
+    q1 = fma(tb.PS[l], s[l], q1);
+  }
+#pragma unroll
+  for (int l = 0; l < H; ++l) {
+    t2 = fma(tb.LD[l], d[l], t2);
+    q2 = fma(tb.PD[l], d[l], q2);
+  }
+  tr[0 * NN + t] = t1 - t2;   // face xi = 0: u
+  tr[1 * NN + t] = q2 - q1;   // face xi = 0: du/dxi
+  tr[2 * NN + t] = t1 + t2;   // face xi = 1: u
+  tr[3 * NN + t] = q1 + q2;   // face xi = 1: du/dxi
+}
+
 // ---------------------------------------------------------------------------------------------
 // Kernel 1: modal -> points, volume integrand, point-space residual V, face traces
 // ---------------------------------------------------------------------------------------------
@@ -165,57 +278,47 @@ dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
   gload_cells<N>(sU, z, cell0, here);
   __syncthreads();
 
-  // Sec. 3.3, eq. evalfe: u at the Gauss points, one axis at a time (x, then y, then z)
+  // Sec. 3.3, eq. evalfe: u at the Gauss points, axis x then y ...
 #pragma unroll
-  for (int dir = 0; dir < 3; ++dir) {
+  for (int dir = 0; dir < 2; ++dir) {
     if (active) {
       T x[N], y[N];
       const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
       load_line<N>(U, bs, st, x);
-      mv<N>(tb.A, x, y);
+      eo_fwd<N, T>(tb, x, y);
       store_line<N>(U, bs, st, y);
     }
     __syncthreads();
   }
 
-  // Sec. 3.2, eqs. evalblf / gauss_points: per axis r, V += Dt_r^T [w (alpha_r D d_r u + beta_r u)]
-  // and the six face traces (value and reference normal derivative) from the same lines.
   const T DT = active ? Dcell[cell] : T(0);
   const int a = t % N, b = t / N;
   const T wperp = tb.w[a] * tb.w[b];
+  T* trc = traces + (size_t)cell * 12 * NN;
+  // ... then z, kept in registers for the z derivative pass (Sec. 3.2, eqs. evalblf / gauss_points):
+  // V = c|T| w u + B_z [w (alpha_z D d_z u + beta_z u)], traces on the two z faces
+  if (active) {
+    T x[N], u[N], v[N];
+    const int bs = Lay<N>::base(2, t), st = Lay<N>::stride(2);
+    load_line<N>(U, bs, st, x);
+    eo_fwd<N, T>(tb, x, u);
+    store_line<N>(U, bs, st, u);
+    deriv_line<N, T, true>(tb, u, v, wperp * (DT * g.alpha[2]), wperp * g.beta[2], wperp * g.creact, trc + 8 * NN,
+                           NN, t);
+    store_line<N>(V, bs, st, v);
+  }
+  __syncthreads();
+  // x and y derivative passes accumulate into V
 #pragma unroll
-  for (int dir = 0; dir < 3; ++dir) {
+  for (int dir = 0; dir < 2; ++dir) {
     if (active) {
-      T u[N], gr[N], X[N], v[N];
+      T u[N], v[N];
       const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
       load_line<N>(U, bs, st, u);
-      mv<N>(tb.Dt, u, gr);
-      const T sa = wperp * (DT * g.alpha[dir]);
-      const T sb = wperp * g.beta[dir];
-#pragma unroll
-      for (int i = 0; i < N; ++i) X[i] = fma(sa, gr[i], sb * u[i]);
-      if (dir == 0) {
-        const T sc = wperp * g.creact;
-#pragma unroll
-        for (int l = 0; l < N; ++l) v[l] = (sc * tb.w[l]) * u[l];
-      } else {
-        load_line<N>(V, bs, st, v);
-      }
-      mvt_acc<N>(tb.DtW, X, v);
+      load_line<N>(V, bs, st, v);
+      deriv_line<N, T, false>(tb, u, v, wperp * (DT * g.alpha[dir]), wperp * g.beta[dir], T(0),
+                              trc + 4 * dir * NN, NN, t);
       store_line<N>(V, bs, st, v);
-      // traces at xi_dir = 0 and 1: field 0 = u, field 1 = d u / d xi_dir (reference)
-      T* tr = traces + ((size_t)cell * 6 + 2 * dir) * 2 * NN;
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        T tv = T(0), td = T(0);
-#pragma unroll
-        for (int l = 0; l < N; ++l) {
-          tv = fma(tb.L[s][l], u[l], tv);
-          td = fma(tb.P[s][l], u[l], td);
-        }
-        tr[(2 * s + 0) * NN + t] = tv;
-        tr[(2 * s + 1) * NN + t] = td;
-      }
     }
     __syncthreads();
   }
@@ -239,6 +342,61 @@ struct FaceArgs {
   int mode;
 };
 
+// face test weights of this thread's face point on face (dir, s): value weight Vf and normal-derivative
+// weight Wf (eq. blf: interior upwind, consistency, symmetry and penalty terms, or the Dirichlet terms;
+// mode 2: the Dirichlet terms of l_h)
+template <int N, typename T>
+__device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>& fa, int cell, const int (&ic)[3],
+                                             int dir, int s, int t, T wf, T& Vf, T& Wf) {
+  constexpr int NN = N * N;
+  const int face = 2 * dir + s;
+  const bool boundary = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
+  const T* c3 = fa.fc + ((size_t)cell * 6 + face) * 3;
+  const T bq = g.b[dir];
+  Vf = T(0);
+  Wf = T(0);
+  if (fa.mode == 2) {
+    // -(Phi(0,g,b_nu), v) - (nu.D grad v, g) + gamma (g, v)
+    const T* gs = fa.g[face];
+    if (boundary && gs != nullptr) {
+      const int ta = dir == 0 ? 1 : 0, tbx = dir == 2 ? 1 : 2;
+      const int fidx = ic[ta] + g.n[ta] * ic[tbx];
+      const T gv = gs[(size_t)fidx * NN + t];
+      const T sgn = s ? T(1) : T(-1);
+      const T bnu = sgn * bq;
+      const T phi = bnu >= T(0) ? T(0) : bnu * gv;
+      Vf = wf * (c3[2] * gv - phi);
+      Wf = -wf * sgn * c3[0] * gv;
+    }
+    return;
+  }
+  const T* tro = fa.traces + ((size_t)cell * 6 + face) * 2 * NN;
+  const T uo = tro[t], dO = tro[NN + t];
+  if (!boundary) {
+    const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
+    const int nb = s ? cell + nstride : cell - nstride;
+    const T* trn = fa.traces + ((size_t)nb * 6 + (2 * dir + 1 - s)) * 2 * NN;
+    const T un = trn[t], dn = trn[NN + t];
+    const T ao = c3[0], an = c3[1], gam = c3[2];
+    // the own cell is T- for s = 1 and T+ for s = 0; nu = +e_dir
+    const T um = s ? uo : un, up = s ? un : uo;
+    const T jump = um - up;
+    const T avg = fma(ao, dO, an * dn);          // nu . {D grad u}_w
+    const T phi = bq * (bq >= T(0) ? um : up);   // upwind flux Phi(u-, u+, b_nu)
+    const T H = fma(gam, jump, phi - avg);        // Phi - nu.{D grad u}_w + gamma [[u]]
+    Vf = s ? wf * H : -wf * H;                    // times [[v]] = +v (T-) or -v (T+)
+    Wf = -wf * ao * jump;                         // -nu.{D grad v}_w [[u]]
+  } else {
+    // Phi(u,0,b_nu) v - (nu.D grad u) v - (nu.D grad v) u + gamma u v, nu = outward normal
+    const T sgn = s ? T(1) : T(-1);
+    const T bnu = sgn * bq;
+    const T phi = bnu >= T(0) ? bnu * uo : T(0);
+    const T aD = c3[0];
+    Vf = wf * (phi - sgn * aD * dO + c3[2] * uo);
+    Wf = -wf * sgn * aD * uo;
+  }
+}
+
 template <int N, typename T>
 __global__ void __launch_bounds__(Launch<N>::THREADS)
 dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g,
@@ -255,15 +413,12 @@ dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
 
   gload_cells<N>(sV, fa.V, cell0, here);
   __syncthreads();
+  const int a = t % N, b = t / N;
   if (fa.mode == 2 && active) {
     // (f, v)_T: scale f by the quadrature weight Delta_T w_i (Sec. 3.1)
-    const int a = t % N, b = t / N;
     const T wz = g.vol * tb.w[a] * tb.w[b];
 #pragma unroll
-    for (int l = 0; l < N; ++l) {
-      const int e = Lay<N>::idx(l, a, b);
-      V[e] *= wz * tb.w[l];
-    }
+    for (int l = 0; l < N; ++l) V[Lay<N>::idx(l, a, b)] *= wz * tb.w[l];
   }
   __syncthreads();
 
@@ -271,79 +426,43 @@ dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
   ic[0] = cell % g.n[0];
   ic[1] = (cell / g.n[0]) % g.n[1];
   ic[2] = cell / (g.n[0] * g.n[1]);
-  const int a = t % N, b = t / N;
+  const T wab = tb.w[a] * tb.w[b];
+  // lift the face weights onto the normal lines, x then y then z (Sec. 3.4, normal direction last):
+  // v_l += l_l(s) Vf + l_l'(s) Wf; the z pass continues with the first transposed contraction
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     if (active) {
       const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
       T v[N];
       load_line<N>(V, bs, st, v);
-      const T wf = g.area[dir] * tb.w[a] * tb.w[b];
-      const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
-      const T bq = g.b[dir];
+      const T wf = g.area[dir] * wab;
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        const int face = 2 * dir + s;
-        const bool boundary = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
-        const T* c3 = fa.fc + ((size_t)cell * 6 + face) * 3;
-        T Vf = T(0), Wf = T(0);
-        if (fa.mode == 2) {
-          // Dirichlet terms of l_h: -(Phi(0,g,b_nu), v) - (nu.D grad v, g) + gamma (g, v)
-          const T* gs = fa.g[face];
-          if (boundary && gs != nullptr) {
-            const int ta = dir == 0 ? 1 : 0, tbx = dir == 2 ? 1 : 2;
-            const int fidx = ic[ta] + g.n[ta] * ic[tbx];
-            const T gv = gs[(size_t)fidx * NN + t];
-            const T sgn = s ? T(1) : T(-1);
-            const T bnu = sgn * bq;
-            const T phi = bnu >= T(0) ? T(0) : bnu * gv;
-            Vf = wf * (c3[2] * gv - phi);
-            Wf = -wf * sgn * c3[0] * gv;
-          }
-        } else {
-          const T* tro = fa.traces + ((size_t)cell * 6 + face) * 2 * NN;
-          const T uo = tro[t], dO = tro[NN + t];
-          if (!boundary) {
-            const int nb = s ? cell + nstride : cell - nstride;
-            const T* trn = fa.traces + ((size_t)nb * 6 + (2 * dir + 1 - s)) * 2 * NN;
-            const T un = trn[t], dn = trn[NN + t];
-            const T ao = c3[0], an = c3[1], gam = c3[2];
-            // eq. blf on an interior face; the own cell is T- for s = 1 and T+ for s = 0
-            const T um = s ? uo : un, up = s ? un : uo;
-            const T jump = um - up;
-            const T avg = fma(ao, dO, an * dn);            // nu . {D grad u}_w
-            const T phi = bq * (bq >= T(0) ? um : up);     // upwind flux
-            const T H = fma(gam, jump, phi - avg);          // Phi - avg + gamma [[u]]
-            Vf = s ? wf * H : -wf * H;                     // times [[v]] = +-v
-            Wf = -wf * ao * jump;                          // -nu.{D grad v}_w [[u]]
-          } else {
-            // Dirichlet face: Phi(u,0,b_nu) v - (nu.D grad u) v - (nu.D grad v) u + gamma u v
-            const T sgn = s ? T(1) : T(-1);
-            const T bnu = sgn * bq;
-            const T phi = bnu >= T(0) ? bnu * uo : T(0);
-            const T aD = c3[0];
-            Vf = wf * (phi - sgn * aD * dO + c3[2] * uo);
-            Wf = -wf * sgn * aD * uo;
-          }
-        }
-        // lift onto the normal line: v_l += l_l(s) Vf + l_l'(s) Wf  (Sec. 3.4, normal direction last)
+        T Vf, Wf;
+        face_weights<N, T>(g, fa, cell, ic, dir, s, t, wf, Vf, Wf);
 #pragma unroll
         for (int l = 0; l < N; ++l) v[l] = fma(tb.L[s][l], Vf, fma(tb.P[s][l], Wf, v[l]));
       }
-      store_line<N>(V, bs, st, v);
+      if (dir == 2) {
+        T y[N];
+        eo_bwd<N, T>(tb, v, y);
+        store_line<N>(V, bs, st, y);
+      } else {
+        store_line<N>(V, bs, st, v);
+      }
     }
     __syncthreads();
   }
 
-  // Sec. 3.2: test functions, A^T along z, y, x
+  // Sec. 3.2: test functions, A^T along y and x
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) {
-    const int dir = 2 - dd;
+  for (int dd = 0; dd < 2; ++dd) {
+    const int dir = 1 - dd;
     if (active) {
       T x[N], y[N];
       const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
       load_line<N>(V, bs, st, x);
-      mvt<N>(tb.A, x, y);
+      eo_bwd<N, T>(tb, x, y);
       store_line<N>(V, bs, st, y);
     }
     __syncthreads();

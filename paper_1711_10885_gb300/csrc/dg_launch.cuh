@@ -8,14 +8,35 @@ namespace dgi {
 
 template <int N, typename T>
 dgk::Tab<N, T> make_tab(const Tables1D& t) {
+  constexpr int H = N / 2, C = (N + 1) / 2;
   dgk::Tab<N, T> r;
+  // B[o][i] = w_i Dt[i][o]: the weighted transposed collocation derivative
+  double B[MAXN][MAXN];
+  for (int o = 0; o < N; ++o)
+    for (int i = 0; i < N; ++i) B[o][i] = t.w[i] * t.Dt[i][o];
+  for (int i = 0; i < C; ++i) {
+    for (int k = 0; k < C; ++k) r.AE[i][k] = (T)t.A[i][2 * k];
+    for (int k = 0; k < H; ++k) r.AO[i][k] = (T)t.A[i][2 * k + 1];
+    for (int l = 0; l < H; ++l) {
+      r.DHm[i][l] = (T)(0.5 * (t.Dt[i][l] - t.Dt[i][N - 1 - l]));
+      r.BHm[i][l] = (T)(0.5 * (B[i][l] - B[i][N - 1 - l]));
+    }
+  }
+  for (int i = 0; i < H; ++i)
+    for (int l = 0; l < C; ++l) {
+      r.DHp[i][l] = (T)(0.5 * (t.Dt[i][l] + t.Dt[i][N - 1 - l]));
+      r.BHp[i][l] = (T)(0.5 * (B[i][l] + B[i][N - 1 - l]));
+    }
+  for (int l = 0; l < C; ++l) {
+    r.LS[l] = (T)(0.5 * (t.L[1][l] + t.L[1][N - 1 - l]));
+    r.PS[l] = (T)(0.5 * (t.P[1][l] + t.P[1][N - 1 - l]));
+  }
+  for (int l = 0; l < H; ++l) {
+    r.LD[l] = (T)(0.5 * (t.L[1][l] - t.L[1][N - 1 - l]));
+    r.PD[l] = (T)(0.5 * (t.P[1][l] - t.P[1][N - 1 - l]));
+  }
   for (int i = 0; i < N; ++i) {
     r.w[i] = (T)t.w[i];
-    for (int j = 0; j < N; ++j) {
-      r.A[i][j] = (T)t.A[i][j];
-      r.Dt[i][j] = (T)t.Dt[i][j];
-      r.DtW[i][j] = (T)(t.w[i] * t.Dt[i][j]);
-    }
     for (int s = 0; s < 2; ++s) {
       r.L[s][i] = (T)t.L[s][i];
       r.P[s][i] = (T)t.P[s][i];

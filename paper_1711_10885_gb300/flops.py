@@ -17,31 +17,52 @@ def paper_flopdof(p: int, d: int = 3) -> float:
     return vol + face
 
 
-def _mv(N):
-    return N * (2 * N - 1)  # one mul and N-1 fma per output
+def _halves(N):
+    return N // 2, (N + 1) // 2
+
+
+def eo_fwd_flops(N):
+    """Modal -> points on one line in even-odd form (mul + fma chains, then the +/- recombination)."""
+    H, C = _halves(N)
+    return C * (2 * C - 1) + H * (2 * H - 1) + 2 * H
+
+
+def eo_bwd_flops(N):
+    H, C = _halves(N)
+    return 2 * H + C * (2 * C - 1) + H * (2 * H - 1)
+
+
+def eo_anti_flops(N):
+    """Centro-antisymmetric N x N point operator from the split parts of its input."""
+    H, C = _halves(N)
+    return C * (2 * H - 1) + H * (2 * C - 1) + 2 * H
+
+
+def deriv_line_flops(N, first):
+    H, C = _halves(N)
+    split = 2 * H
+    flux = 3 * N  # sa * grad + sb * u
+    acc = 3 * N if first else N  # reaction (mul + fma) on the first pass, else add
+    traces = 4 * N + 4
+    return split + eo_anti_flops(N) + flux + split + eo_anti_flops(N) + acc + traces
 
 
 def cell_kernel_flops(N: int) -> float:
     """Executed FP operations of dg_cell_kernel for one cell (n = m = N)."""
     NN = N * N
-    fwd = 3 * NN * _mv(N)
-    per_dir_line = _mv(N) + 3 * N + 2 * N * N + 8 * N + 3  # Dt u, flux, Dt^T acc, 4 traces, scalars
-    deriv = 3 * NN * per_dir_line + NN * (2 * N + 1)  # + reaction init on the x pass
-    return fwd + deriv + NN  # wperp
+    fwd = 3 * NN * eo_fwd_flops(N)
+    deriv = NN * (deriv_line_flops(N, True) + 2 * deriv_line_flops(N, False))
+    scalars = NN * (1 + 3 * 3 + 1)  # wperp; sa (2) and sb (1) per pass; sc once
+    return fwd + deriv + scalars
 
 
 def face_kernel_flops(N: int, n=(1, 1, 1), residual: bool = True) -> float:
     """Executed FP operations of dg_face_kernel, averaged per cell for an n[0] x n[1] x n[2] mesh."""
     NN = N * N
-    ncell = n[0] * n[1] * n[2]
-    nbound = 2 * (n[1] * n[2] + n[0] * n[2] + n[0] * n[1])  # boundary face-sides
-    face_sides = 6 * ncell
-    interior_pt = 11  # jump, avg (mul+fma), upwind, H (sub+fma), V, W (2 mul), sign
-    boundary_pt = 10
-    pointwise = NN * (interior_pt * (face_sides - nbound) + boundary_pt * nbound) / ncell
-    lift = 3 * NN * (2 + 2 * 4 * N)  # wf, and 2 fma per point per side
-    back = 3 * NN * _mv(N)
-    return pointwise + lift + back + (N ** 3 if residual else 0)
+    per_point = 11  # face weights: jump, average (mul+fma), upwind, H (sub+fma), V, W (2 mul), sign
+    lift = 3 * NN * (1 + 2 * (per_point + 4 * N))  # wf, then per side the weights and 2 fma per point
+    back = 3 * NN * eo_bwd_flops(N)
+    return NN + lift + back + (N ** 3 if residual else 0)
 
 
 def apply_flops_per_dof(k: int, n=(1, 1, 1), residual: bool = True) -> float:
