@@ -138,6 +138,57 @@ int dg_apply_stage(dg_handle* h, int32_t stage, const void* in, void* out, int32
 /* Copy the right hand side F = l_h(phi_i) into F_dev (device, given precision). */
 int dg_rhs(dg_handle* h, void* F_dev, int32_t precision, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Solvers.  The paper measures operator application only and leaves solvers to future work
+ * (Sec. 1, Sec. 6); the solvers below use that operator as their only access to A.
+ * --------------------------------------------------------------------------------------------- */
+
+enum { DG_SOLVE_FP64 = 0, DG_SOLVE_MIXED = 1 };
+enum { DG_PRECOND_NONE = 0, DG_PRECOND_BLOCK_JACOBI = 1 };
+
+typedef struct {
+  int32_t mode;           /* DG_SOLVE_FP64: FGMRES(restart) in FP64 on the FP64 operator.
+                             DG_SOLVE_MIXED: FGMRES(outer_restart) in FP64 (true residual, defect update
+                             and orthogonalisation in FP64) whose preconditioner is one cycle of an FP32
+                             FGMRES(restart) on the FP32 operator, stopped at inner_rtol.             */
+  int32_t preconditioner; /* DG_PRECOND_NONE or DG_PRECOND_BLOCK_JACOBI (FP64 blocks in FP64 mode, FP32
+                             blocks inside the FP32 inner solve); needs dg_precond_setup first        */
+  int32_t restart;        /* FGMRES restart length (inner length in MIXED mode), 1..60, 0 = 30        */
+  int32_t outer_restart;  /* MIXED: outer restart length, 1..60, 0 = 10                               */
+  int32_t max_iterations; /* cap on (outer) iterations, 0 = 10000                                      */
+  double rtol;            /* stop when ||b - A x||_2 <= rtol ||b||_2, checked on the FP64 residual     */
+  double inner_rtol;      /* MIXED: relative residual reduction of each inner solve, in (0, 1)         */
+} dg_solve_opts;
+
+typedef struct {
+  int32_t status;           /* DG_OK or the returned error code                                    */
+  int32_t iterations;       /* FGMRES iterations (outer iterations in MIXED mode)                    */
+  int32_t inner_iterations; /* FP32 inner iterations (MIXED), else equal to iterations              */
+  int32_t applies_f64;      /* FP64 operator applications                                           */
+  int32_t applies_f32;      /* FP32 operator applications                                           */
+  double rel_residual;      /* final ||b - A x||_2 / ||b||_2 (true FP64 residual at exit)           */
+  double seconds;           /* wall time of the call                                                */
+} dg_solve_stats;
+
+/* Build the block-Jacobi preconditioner (kind = DG_PRECOND_BLOCK_JACOBI): for every cell the
+ * diagonal block A_TT ((k+1)^3 x (k+1)^3: the cell's volume term plus the self-coupling of its
+ * faces) is assembled on the device by running the operator's own kernels on unit vectors, then
+ * inverted in a batch (Gauss-Jordan, partial pivoting) and kept in FP64 and FP32.  Memory:
+ * ncells * (k+1)^6 * 12 bytes, owned by the handle.  Requires (k+1)^3 <= 512.  Returns
+ * DG_ERR_NAN if a block is singular.  Synchronises `stream`. */
+int dg_precond_setup(dg_handle* h, int32_t kind, void* stream);
+
+/* z = M^{-1} r with the block-Jacobi preconditioner (r, z device vectors of the given precision). */
+int dg_precond_apply(dg_handle* h, const void* r_dev, void* z_dev, int32_t precision, void* stream);
+
+/* Solve A x = b (b_dev NULL: b = F, the right hand side of dg_setup) with FGMRES; x_dev holds the
+ * initial guess and receives the solution (FP64, device).  Fills *stats (may be NULL).  Returns
+ * DG_OK when the FP64 relative residual reached opts->rtol, DG_ERR_NOT_CONVERGED when the iteration
+ * cap was hit first, DG_ERR_NAN on a non-finite residual.  Synchronises `stream` (once per Arnoldi
+ * step).  Workspace is allocated on first use and kept by the handle. */
+int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_opts* opts, dg_solve_stats* stats,
+             void* stream);
+
 /* Message for the calling thread's last error ("" if none). */
 const char* dg_last_error(void);
 

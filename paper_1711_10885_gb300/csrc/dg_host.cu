@@ -137,6 +137,10 @@ int dg_destroy(dg_handle* h) {
   free_buffers(h->p32);
   cudaFree(h->work_V);
   cudaFree(h->work_tr);
+  cudaFree(h->bj64);
+  cudaFree(h->bj32);
+  cudaFree(h->ws);
+  if (h->ws_host) cudaFreeHost(h->ws_host);
   delete h;
   return DG_OK;
 }

@@ -41,6 +41,13 @@ struct dg_handle {
   void* work_V = nullptr;  // point-space residual scratch [ncell][N^3] (sized for FP64)
   void* work_tr = nullptr; // face trace scratch [ncell][6][2][N^2] (sized for FP64)
   int device = 0;
+  // block-Jacobi preconditioner: per cell (A_TT^{-1})^T, row-major [ncell][N^3][N^3], FP64 and FP32
+  void* bj64 = nullptr;
+  void* bj32 = nullptr;
+  // Krylov workspace (grown on demand, freed by dg_destroy)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* ws_host = nullptr;  // pinned host staging for reduction results
 };
 
 namespace dgi {
@@ -51,6 +58,11 @@ int cuda_fail(cudaError_t e, const char* what);
 // mode 0: y = A z, mode 1: y = A z - F; stages: bit 0 cell kernel, bit 1 face kernel (3 = full apply)
 int launch_apply_f64(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s);
 int launch_apply_f32(const dg_handle* h, const float* z, float* y, int mode, int stages, cudaStream_t s);
+int launch_diag_blocks_f64(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr,
+                           cudaStream_t s);
+// block-Jacobi application z = M r (precision by type), M from dg_precond_setup
+int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s);
+int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 // F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null)
 int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s);
 

@@ -259,23 +259,39 @@ __device__ __forceinline__ void deriv_line(const Tab<N, T>& tb, const T (&u)[N],
 // ---------------------------------------------------------------------------------------------
 // Kernel 1: modal -> points, volume integrand, point-space residual V, face traces
 // ---------------------------------------------------------------------------------------------
-template <int N, typename T>
+// Diagonal-block mode (SELF = true): "virtual cell" vc = (cell - cell_base) * N^3 + j stands for the unit
+// vector e_j supported on one real cell, with every neighbour's contribution zero; the outputs are indexed
+// by vc.  This assembles the cell's diagonal block A_TT column by column with the operator's own code.
+struct SelfArgs {
+  int nvirt;      // number of virtual cells in this launch
+  int cell_base;  // first real cell of the chunk
+};
+
+template <int N, typename T, bool SELF = false>
 __global__ void __launch_bounds__(Launch<N>::THREADS)
 dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g, const T* __restrict__ z,
-               const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces) {
-  constexpr int NN = N * N, CPB = Launch<N>::CPB, CS = Lay<N>::CS;
+               const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces, SelfArgs sa_) {
+  constexpr int NN = N * N, N3 = N * N * N, CPB = Launch<N>::CPB, CS = Lay<N>::CS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sU = reinterpret_cast<T*>(smem_raw);
   T* sV = sU + CPB * CS;
   const int cell0 = blockIdx.x * CPB;
-  const int here = min(CPB, g.ncell - cell0);
+  const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
   const bool active = lc < here;
-  const int cell = cell0 + lc;
+  const int cell = cell0 + lc;                                 // output index (virtual in SELF mode)
+  const int rcell = SELF ? sa_.cell_base + cell / N3 : cell;   // real cell (coefficients)
   T* U = sU + lc * CS;
   T* V = sV + lc * CS;
 
-  gload_cells<N>(sU, z, cell0, here);
+  if (SELF) {
+    for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+      const int c = e / N3, r = e - c * N3;
+      sU[c * CS + r % N + Lay<N>::LS * (r / N)] = (r == (cell0 + c) % N3) ? T(1) : T(0);
+    }
+  } else {
+    gload_cells<N>(sU, z, cell0, here);
+  }
   __syncthreads();
 
   // Sec. 3.3, eq. evalfe: u at the Gauss points, axis x then y ...
@@ -291,7 +307,7 @@ dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
     __syncthreads();
   }
 
-  const T DT = active ? Dcell[cell] : T(0);
+  const T DT = active ? Dcell[rcell] : T(0);
   const int a = t % N, b = t / N;
   const T wperp = tb.w[a] * tb.w[b];
   T* trc = traces + (size_t)cell * 12 * NN;
@@ -345,9 +361,9 @@ struct FaceArgs {
 // face test weights of this thread's face point on face (dir, s): value weight Vf and normal-derivative
 // weight Wf (eq. blf: interior upwind, consistency, symmetry and penalty terms, or the Dirichlet terms;
 // mode 2: the Dirichlet terms of l_h)
-template <int N, typename T>
-__device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>& fa, int cell, const int (&ic)[3],
-                                             int dir, int s, int t, T wf, T& Vf, T& Wf) {
+template <int N, typename T, bool SELF>
+__device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>& fa, int cell, int tcell,
+                                             const int (&ic)[3], int dir, int s, int t, T wf, T& Vf, T& Wf) {
   constexpr int NN = N * N;
   const int face = 2 * dir + s;
   const bool boundary = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
@@ -370,13 +386,17 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>&
     }
     return;
   }
-  const T* tro = fa.traces + ((size_t)cell * 6 + face) * 2 * NN;
+  const T* tro = fa.traces + ((size_t)tcell * 6 + face) * 2 * NN;
   const T uo = tro[t], dO = tro[NN + t];
   if (!boundary) {
-    const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
-    const int nb = s ? cell + nstride : cell - nstride;
-    const T* trn = fa.traces + ((size_t)nb * 6 + (2 * dir + 1 - s)) * 2 * NN;
-    const T un = trn[t], dn = trn[NN + t];
+    T un = T(0), dn = T(0);  // the neighbour contributes nothing to a diagonal block
+    if (!SELF) {
+      const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
+      const int nb = s ? cell + nstride : cell - nstride;
+      const T* trn = fa.traces + ((size_t)nb * 6 + (2 * dir + 1 - s)) * 2 * NN;
+      un = trn[t];
+      dn = trn[NN + t];
+    }
     const T ao = c3[0], an = c3[1], gam = c3[2];
     // the own cell is T- for s = 1 and T+ for s = 0; nu = +e_dir
     const T um = s ? uo : un, up = s ? un : uo;
@@ -397,18 +417,19 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>&
   }
 }
 
-template <int N, typename T>
+template <int N, typename T, bool SELF = false>
 __global__ void __launch_bounds__(Launch<N>::THREADS)
 dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g,
-               const __grid_constant__ FaceArgs<T> fa) {
-  constexpr int NN = N * N, CPB = Launch<N>::CPB, CS = Lay<N>::CS;
+               const __grid_constant__ FaceArgs<T> fa, SelfArgs sa_) {
+  constexpr int NN = N * N, N3 = N * N * N, CPB = Launch<N>::CPB, CS = Lay<N>::CS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sV = reinterpret_cast<T*>(smem_raw);
   const int cell0 = blockIdx.x * CPB;
-  const int here = min(CPB, g.ncell - cell0);
+  const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
   const bool active = lc < here;
-  const int cell = cell0 + lc;
+  const int vcell = cell0 + lc;                                // output / trace index
+  const int cell = SELF ? sa_.cell_base + vcell / N3 : vcell;  // real cell
   T* V = sV + lc * CS;
 
   gload_cells<N>(sV, fa.V, cell0, here);
@@ -439,7 +460,7 @@ dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         T Vf, Wf;
-        face_weights<N, T>(g, fa, cell, ic, dir, s, t, wf, Vf, Wf);
+        face_weights<N, T, SELF>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf, Wf);
 #pragma unroll
         for (int l = 0; l < N; ++l) v[l] = fma(tb.L[s][l], Vf, fma(tb.P[s][l], Wf, v[l]));
       }
@@ -468,7 +489,6 @@ dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
     __syncthreads();
   }
   // write out (minus F for the residual)
-  constexpr int N3 = N * N * N;
   const int total = here * N3;
   T* dst = fa.y + (size_t)cell0 * N3;
   const T* Fs = fa.F ? fa.F + (size_t)cell0 * N3 : nullptr;

@@ -86,6 +86,20 @@ int set_smem_attrs() {
 }
 
 // stages: bit 0 = cell kernel (z -> work buffers), bit 1 = face kernel (work buffers -> y)
+template <int N>
+int set_self_smem_attrs() {
+  static bool done = false;
+  if (done) return 0;
+  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, double, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<N, double>());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel self)");
+  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)face_smem<N, double>());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel self)");
+  done = true;
+  return 0;
+}
+
 template <int N, typename T>
 int apply_n(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStream_t s) {
   if (int rc = set_smem_attrs<N, T>()) return rc;
@@ -98,7 +112,7 @@ int apply_n(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStre
   T* tr = static_cast<T*>(h->work_tr);
   if (stages & 1)
     dgk::dg_cell_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, cell_smem<N, T>(), s>>>(
-        tb, geo, z, static_cast<const T*>(bf.D), V, tr);
+        tb, geo, z, static_cast<const T*>(bf.D), V, tr, dgk::SelfArgs{0, 0});
   dgk::FaceArgs<T> fa;
   fa.V = V;
   fa.traces = tr;
@@ -107,7 +121,9 @@ int apply_n(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStre
   for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
   fa.y = y;
   fa.mode = mode;
-  if (stages & 2) dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa);
+  if (stages & 2)
+    dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa,
+                                                                                      dgk::SelfArgs{0, 0});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");
   return 0;
@@ -129,10 +145,58 @@ int rhs_n(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_
   for (int i = 0; i < 6; ++i) fa.g[i] = g[i];
   fa.y = F;
   fa.mode = 2;
-  dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa);
+  dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa,
+                                                                                    dgk::SelfArgs{0, 0});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rhs kernel launch");
   return 0;
+}
+
+// Diagonal blocks of cells [cell_base, cell_base + ncells): column j of block c is written to
+// out[(c * N^3 + j) * N^3 + i], i.e. each block is stored as A_TT^T in row-major order.
+template <int N>
+int diag_blocks_n(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr, cudaStream_t s) {
+  if (int rc = set_smem_attrs<N, double>()) return rc;
+  if (int rc = set_self_smem_attrs<N>()) return rc;
+  constexpr int N3 = N * N * N;
+  const auto tb = make_tab<N, double>(h->tab);
+  const auto geo = make_geo<double>(h);
+  const int cpb = dgk::Launch<N>::CPB;
+  const int nvirt = ncells * N3;
+  const unsigned grid = (unsigned)((nvirt + cpb - 1) / cpb);
+  const dgk::SelfArgs sa{nvirt, cell_base};
+  dgk::dg_cell_kernel<N, double, true><<<grid, dgk::Launch<N>::THREADS, cell_smem<N, double>(), s>>>(
+      tb, geo, nullptr, static_cast<const double*>(h->p64.D), V, tr, sa);
+  dgk::FaceArgs<double> fa;
+  fa.V = V;
+  fa.traces = tr;
+  fa.fc = static_cast<const double*>(h->p64.fc);
+  fa.F = nullptr;
+  for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
+  fa.y = out;
+  fa.mode = 0;
+  dgk::dg_face_kernel<N, double, true><<<grid, dgk::Launch<N>::THREADS, face_smem<N, double>(), s>>>(tb, geo, fa,
+                                                                                                    sa);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "diagonal block kernel launch");
+  return 0;
+}
+
+inline int diag_blocks_dispatch(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr,
+                                cudaStream_t s) {
+  switch (h->N) {
+    case 2: return diag_blocks_n<2>(h, out, cell_base, ncells, V, tr, s);
+    case 3: return diag_blocks_n<3>(h, out, cell_base, ncells, V, tr, s);
+    case 4: return diag_blocks_n<4>(h, out, cell_base, ncells, V, tr, s);
+    case 5: return diag_blocks_n<5>(h, out, cell_base, ncells, V, tr, s);
+    case 6: return diag_blocks_n<6>(h, out, cell_base, ncells, V, tr, s);
+    case 7: return diag_blocks_n<7>(h, out, cell_base, ncells, V, tr, s);
+    case 8: return diag_blocks_n<8>(h, out, cell_base, ncells, V, tr, s);
+    case 9: return diag_blocks_n<9>(h, out, cell_base, ncells, V, tr, s);
+    case 10: return diag_blocks_n<10>(h, out, cell_base, ncells, V, tr, s);
+    case 11: return diag_blocks_n<11>(h, out, cell_base, ncells, V, tr, s);
+    default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
+  }
 }
 
 template <typename T>

@@ -8,4 +8,8 @@ int launch_apply_f64(const dg_handle* h, const double* z, double* y, int mode, i
 int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s) {
   return rhs_dispatch<double>(h, f, g, F, s);
 }
+int launch_diag_blocks_f64(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr,
+                           cudaStream_t s) {
+  return diag_blocks_dispatch(h, out, cell_base, ncells, V, tr, s);
+}
 }  // namespace dgi

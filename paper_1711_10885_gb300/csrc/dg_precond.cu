@@ -1,0 +1,240 @@
+// dg_precond.cu -- block-Jacobi preconditioner: per-cell diagonal blocks A_TT of the operator,
+// inverted in a batch (Gauss-Jordan with partial pivoting), applied as a batched matrix-vector product.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "dg_internal.h"
+
+namespace dgi {
+
+// In-place Gauss-Jordan inversion with partial (row) pivoting of one n x n row-major block per CTA.
+// SMEM: the block is staged in shared memory; otherwise it is updated in global memory.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) gj_invert(double* __restrict__ blocks, int n, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sA = reinterpret_cast<double*>(smem_raw);
+  __shared__ double fcol[512];
+  __shared__ int perm[512];
+  __shared__ double red_v[8];
+  __shared__ int red_i[8];
+  __shared__ int s_piv;
+  __shared__ double s_d;
+  double* g = blocks + (size_t)blockIdx.x * n * n;
+  double* A = SMEM ? sA : g;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (SMEM) {
+    for (int e = tid; e < n * n; e += nt) A[e] = g[e];
+    __syncthreads();
+  }
+  for (int p = 0; p < n; ++p) {
+    // pivot: argmax_{i >= p} |A[i][p]| (ties: smallest i)
+    double bv = -1.0;
+    int bi = p;
+    for (int i = p + tid; i < n; i += nt) {
+      const double v = fabs(A[(size_t)i * n + p]);
+      if (v > bv) {
+        bv = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if ((tid & 31) == 0) {
+      red_v[tid >> 5] = bv;
+      red_i[tid >> 5] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double v = red_v[0];
+      int i0 = red_i[0];
+      for (int k = 1; k < (nt >> 5); ++k)
+        if (red_v[k] > v || (red_v[k] == v && red_i[k] < i0)) {
+          v = red_v[k];
+          i0 = red_i[k];
+        }
+      s_piv = i0;
+      perm[p] = i0;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != p)
+      for (int k = tid; k < n; k += nt) {
+        const double t = A[(size_t)p * n + k];
+        A[(size_t)p * n + k] = A[(size_t)piv * n + k];
+        A[(size_t)piv * n + k] = t;
+      }
+    __syncthreads();
+    if (tid == 0) {
+      const double a = A[(size_t)p * n + p];
+      if (a == 0.0 || !isfinite(a)) {
+        atomicAdd(status, 1);
+        s_d = 0.0;
+      } else {
+        s_d = 1.0 / a;
+      }
+    }
+    __syncthreads();
+    const double d = s_d;
+    for (int k = tid; k < n; k += nt) A[(size_t)p * n + k] = (k == p ? 1.0 : A[(size_t)p * n + k]) * d;
+    for (int i = tid; i < n; i += nt) fcol[i] = (i == p) ? 0.0 : A[(size_t)i * n + p];
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, k = e - i * n;
+      if (i != p) A[e] = (k == p ? 0.0 : A[e]) - fcol[i] * A[(size_t)p * n + k];
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int p = n - 1; p >= 0; --p) {
+    const int piv = perm[p];
+    if (piv != p)
+      for (int i = tid; i < n; i += nt) {
+        const double t = A[(size_t)i * n + p];
+        A[(size_t)i * n + p] = A[(size_t)i * n + piv];
+        A[(size_t)i * n + piv] = t;
+      }
+    __syncthreads();
+  }
+  if (SMEM)
+    for (int e = tid; e < n * n; e += nt) g[e] = A[e];
+}
+
+// z_T = A_TT^{-1} r_T with the stored (A_TT^{-1})^T: z_i = sum_j M[j][i] r_j  (one CTA per cell)
+template <typename T>
+__global__ void __launch_bounds__(256) bj_apply(const T* __restrict__ M, const T* __restrict__ r, T* __restrict__ z,
+                                                int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* rs = reinterpret_cast<T*>(smem_raw);
+  const size_t cell = blockIdx.x;
+  const T* Mc = M + cell * n * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = r[cell * n + j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T acc = T(0);
+    for (int j = 0; j < n; ++j) acc = fma(Mc[(size_t)j * n + i], rs[j], acc);
+    z[cell * n + i] = acc;
+  }
+}
+
+__global__ void cast_blocks(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s) {
+  const int n = h->N * h->N * h->N;
+  const int threads = n >= 256 ? 256 : ((n + 31) / 32) * 32;
+  bj_apply<double><<<(unsigned)h->ncell, threads, n * sizeof(double), s>>>(static_cast<const double*>(h->bj64), r, z, n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply");
+}
+
+int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
+  const int n = h->N * h->N * h->N;
+  const int threads = n >= 256 ? 256 : ((n + 31) / 32) * 32;
+  bj_apply<float><<<(unsigned)h->ncell, threads, n * sizeof(float), s>>>(static_cast<const float*>(h->bj32), r, z, n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply");
+}
+
+}  // namespace dgi
+
+using namespace dgi;
+
+extern "C" {
+
+int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
+  if (!h || kind != 1) {
+    set_error("dg_precond_setup: kind must be 1 (block-Jacobi)");
+    return DG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int N = h->N, n = N * N * N;
+  if (n > 512) {
+    set_error("dg_precond_setup: block-Jacobi supports (k+1)^3 <= 512");
+    return DG_ERR_INVALID_ARG;
+  }
+  const size_t nblk = (size_t)h->ncell * n * n;
+  cudaError_t e;
+  if (!h->bj64) {
+    e = cudaMalloc(&h->bj64, nblk * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(block-Jacobi FP64)");
+  }
+  if (!h->bj32) {
+    e = cudaMalloc(&h->bj32, nblk * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(block-Jacobi FP32)");
+  }
+  // assemble in chunks of cells: each chunk needs (cells * n) virtual cells of work buffers
+  int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(h->ncell, h->ncell / n));
+  double *V = nullptr, *tr = nullptr;
+  const size_t nvirt = (size_t)chunk * n;
+  e = cudaMalloc(&V, nvirt * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&tr, nvirt * 12 * N * N * sizeof(double));
+  int* status = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  int rc = DG_OK;
+  if (e != cudaSuccess) rc = cuda_fail(e, "block-Jacobi setup buffers");
+  for (int64_t c0 = 0; rc == DG_OK && c0 < h->ncell; c0 += chunk) {
+    const int nc = (int)std::min<int64_t>(chunk, h->ncell - c0);
+    rc = launch_diag_blocks_f64(h, static_cast<double*>(h->bj64) + (size_t)c0 * n * n, (int)c0, nc, V, tr, s);
+  }
+  if (rc == DG_OK) {
+    const size_t smem = (size_t)n * n * sizeof(double);
+    if (smem <= 200 * 1024) {
+      e = cudaFuncSetAttribute(gj_invert<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        gj_invert<true><<<(unsigned)h->ncell, 256, smem, s>>>(static_cast<double*>(h->bj64), n, status);
+        e = cudaGetLastError();
+      }
+    } else {
+      gj_invert<false><<<(unsigned)h->ncell, 256, 0, s>>>(static_cast<double*>(h->bj64), n, status);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      cast_blocks<<<152 * 8, 256, 0, s>>>(static_cast<const double*>(h->bj64), static_cast<float*>(h->bj32), nblk);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "block inversion");
+  }
+  int bad = 0;
+  if (rc == DG_OK) {
+    e = cudaMemcpyAsync(&bad, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "block-Jacobi setup");
+  } else {
+    cudaStreamSynchronize(s);
+  }
+  cudaFree(V);
+  cudaFree(tr);
+  cudaFree(status);
+  if (rc == DG_OK && bad) {
+    set_error("dg_precond_setup: " + std::to_string(bad) + " singular diagonal block(s)");
+    rc = DG_ERR_NAN;
+  }
+  return rc;
+}
+
+int dg_precond_apply(dg_handle* h, const void* r, void* z, int32_t precision, void* stream) {
+  if (!h || !r || !z || r == z || (precision != DG_F64 && precision != DG_F32)) {
+    set_error("dg_precond_apply: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (!h->bj64) {
+    set_error("dg_precond_apply: call dg_precond_setup first");
+    return DG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == DG_F64) return precond_bj_f64(h, static_cast<const double*>(r), static_cast<double*>(z), s);
+  return precond_bj_f32(h, static_cast<const float*>(r), static_cast<float*>(z), s);
+}
+
+}  // extern "C"

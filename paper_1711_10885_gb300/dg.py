@@ -43,6 +43,27 @@ class dg_bc(ctypes.Structure):
     _fields_ = [("g_qp", _dp * 6)]
 
 
+DG_SOLVE_FP64 = 0
+DG_SOLVE_MIXED = 1
+DG_PRECOND_NONE = 0
+DG_PRECOND_BLOCK_JACOBI = 1
+
+
+class dg_solve_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("preconditioner", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("outer_restart", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("inner_rtol", ctypes.c_double)]
+
+
+class dg_solve_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
+                ("applies_f64", ctypes.c_int32), ("applies_f32", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libdg.so not built ({LIB_PATH}); run __graft_entry__.build() first")
@@ -61,6 +82,9 @@ def _load():
     lib.dg_apply_residual.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
     lib.dg_rhs.argtypes = [vp, vp, ctypes.c_int32, vp]
     lib.dg_apply_stage.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32, ctypes.c_int32, vp]
+    lib.dg_precond_setup.argtypes = [vp, ctypes.c_int32, vp]
+    lib.dg_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.dg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(dg_solve_opts), ctypes.POINTER(dg_solve_stats), vp]
     return lib
 
 
@@ -68,7 +92,8 @@ lib = _load()
 
 # C-ABI symbols declared in include/dg.h (checked by the CPU test suite)
 EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadrature_points", "dg_apply_jacobian",
-            "dg_apply_residual", "dg_rhs", "dg_last_error", "dg_apply_stage"]
+            "dg_apply_residual", "dg_rhs", "dg_last_error", "dg_apply_stage", "dg_precond_setup",
+            "dg_precond_apply", "dg_solve"]
 
 
 def check(rc):
@@ -214,6 +239,39 @@ class Operator:
         check(lib.dg_apply_stage(self.h, int(stage), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                  _prec(x), int(bool(residual)), _stream_ptr(stream)))
         return y
+
+    def precond_setup(self, kind=DG_PRECOND_BLOCK_JACOBI, stream=None):
+        """Assemble and invert the per-cell diagonal blocks (dg_precond_setup)."""
+        check(lib.dg_precond_setup(self.h, int(kind), _stream_ptr(stream)))
+
+    def precond_apply(self, r, z=None, stream=None):
+        """z = M^{-1} r with the block-Jacobi preconditioner (dg_precond_apply)."""
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        self._vec_check(r, z)
+        check(lib.dg_precond_apply(self.h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()), _prec(r),
+                                   _stream_ptr(stream)))
+        return z
+
+    def solve(self, x, b=None, mode=DG_SOLVE_FP64, preconditioner=DG_PRECOND_BLOCK_JACOBI, restart=30,
+              outer_restart=10, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True):
+        """Solve A x = b (b = F when None) in place on the FP64 tensor x (dg_solve); returns the stats dict."""
+        import torch
+        if x.dtype != torch.float64:
+            raise TypeError("x must be float64")
+        self._vec_check(x)
+        if b is not None:
+            self._vec_check(b)
+        o = dg_solve_opts(mode, preconditioner, restart, outer_restart, max_iterations, rtol, inner_rtol)
+        st = dg_solve_stats()
+        rc = lib.dg_solve(self.h, ctypes.c_void_p(b.data_ptr()) if b is not None else None,
+                          ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
+        if raise_on_error:
+            check(rc)
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
 
     def rhs(self, dtype=None, stream=None):
         """F = l_h(phi_i) (dg_rhs)."""

@@ -1,0 +1,111 @@
+"""GPU tests of the block-Jacobi preconditioner and the FGMRES solvers against the FP64 oracle.
+
+The diagonal blocks are pinned to the oracle (A e_j restricted to the cell, with e_j supported on
+that cell); solutions are pinned to a dense LU solve of the oracle-assembled matrix.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_10885_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_10885_gb300 import dg as _dg
+    return _dg
+
+
+def oracle_problem(w):
+    return oracle.Problem(w.n, w.k, w.D, b=w.b, c=w.c, lo=w.lo, hi=w.hi)
+
+
+def oracle_matrix(pr):
+    N = pr.ndof
+    A = np.empty((N, N))
+    e = np.zeros(N)
+    for j in range(N):
+        e[j] = 1.0
+        A[:, j] = oracle.apply(pr, e)
+        e[j] = 0.0
+    return A
+
+
+@pytest.mark.parametrize("n,k", [((3, 2, 2), 2), ((2, 2, 3), 3), ((1, 1, 2), 4), ((2, 1, 1), 1)])
+def test_block_jacobi_matches_oracle_blocks(dg, n, k):
+    w = inputs.small_case(n=n, k=k, seed=31 + k, b=(0.7, -0.4, 0.2))
+    pr = oracle_problem(w)
+    A = oracle_matrix(pr)
+    nb = w.nb
+    op = dg.operator_for(w)
+    op.precond_setup()
+    rng = np.random.default_rng(3)
+    r = rng.uniform(-1, 1, w.ndof)
+    z64 = op.precond_apply(torch.tensor(r, device="cuda")).cpu().numpy()
+    z32 = op.precond_apply(torch.tensor(r, device="cuda").float()).cpu().numpy()
+    z_ref = np.empty_like(r)
+    for c in range(w.ncell):
+        sl = slice(c * nb, (c + 1) * nb)
+        z_ref[sl] = np.linalg.solve(A[sl, sl], r[sl])
+    assert np.max(np.abs(z64 - z_ref)) <= 1e-10 * np.max(np.abs(z_ref))
+    assert np.max(np.abs(z32 - z_ref)) <= 1e-3 * np.max(np.abs(z_ref))
+    op.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp64_bj", "mixed_bj", "mixed"])
+def test_fgmres_solution_matches_dense_solve(dg, mode):
+    w = inputs.small_case(n=(3, 2, 2), k=2, seed=8, b=(1.0, 0.5, 0.25), f_kind="sines")
+    w.f_params = inputs.sine_modes(9)
+    pr = oracle_problem(w)
+    A = oracle_matrix(pr)
+    F = oracle.rhs(pr, inputs.f_at(w, oracle.volume_points(pr)), None)
+    x_ref = np.linalg.solve(A, F)
+    op = dg.operator_for(w)
+    pc = dg.DG_PRECOND_BLOCK_JACOBI if mode.endswith("bj") else dg.DG_PRECOND_NONE
+    if pc:
+        op.precond_setup()
+    x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    m = dg.DG_SOLVE_MIXED if mode.startswith("mixed") else dg.DG_SOLVE_FP64
+    st = op.solve(x, mode=m, preconditioner=pc, rtol=1e-12, restart=20, outer_restart=8, inner_rtol=1e-2)
+    assert st["rc"] == 0 and st["rel_residual"] <= 1e-12
+    xs = x.cpu().numpy()
+    # field error bound: ||x - x*|| <= cond(A) * rtol * ||x*||; checked directly against the LU solution
+    assert np.max(np.abs(xs - x_ref)) <= 1e-9 * np.max(np.abs(x_ref)), st
+    # the true residual with the oracle operator
+    assert np.linalg.norm(A @ xs - F) <= 1e-11 * np.linalg.norm(F)
+    if m == dg.DG_SOLVE_MIXED:
+        assert st["applies_f32"] > st["applies_f64"]
+    op.close()
+
+
+def test_mixed_and_fp64_solutions_agree(dg):
+    w = inputs.small_case(n=(4, 4, 4), k=3, seed=12, f_kind="sines")
+    w.f_params = inputs.sine_modes(13)
+    op = dg.operator_for(w)
+    op.precond_setup()
+    x64 = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    xmx = torch.zeros_like(x64)
+    s1 = op.solve(x64, mode=dg.DG_SOLVE_FP64, rtol=1e-13)
+    s2 = op.solve(xmx, mode=dg.DG_SOLVE_MIXED, rtol=1e-13, inner_rtol=1e-3)
+    diff = (torch.max(torch.abs(x64 - xmx)) / torch.max(torch.abs(x64))).item()
+    assert diff <= 1e-10, (diff, s1, s2)
+    op.close()
+
+
+def test_solver_errors(dg):
+    w = inputs.small_case(n=(2, 2, 2), k=2)
+    op = dg.operator_for(w)
+    x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    with pytest.raises(dg.DGError):  # block-Jacobi not set up
+        op.solve(x, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI)
+    with pytest.raises(dg.DGError):  # restart too long
+        op.solve(x, preconditioner=dg.DG_PRECOND_NONE, restart=100)
+    st = op.solve(x, preconditioner=dg.DG_PRECOND_NONE, max_iterations=2, rtol=1e-14, raise_on_error=False)
+    assert st["rc"] == -4 and st["status"] == -4  # DG_ERR_NOT_CONVERGED
+    op.close()
