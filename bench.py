@@ -183,6 +183,56 @@ def run_profile(args):
     op.close()
 
 
+def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10):
+    """Mixed-precision vs plain FP64 block-Jacobi FGMRES on the 48^3 Q5 workload (sine source, log-normal D)."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, inputs
+    w = inputs.unit_cube_q5_48(with_u=False)
+    op = dg.operator_for(w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op.precond_setup()
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    out = {"workload": "unit_cube_q5_48", "dofs": w.ndof, "rtol": rtol, "precond_setup_s": setup_s}
+    xs = {}
+    for name, mode in (("fp64", dg.DG_SOLVE_FP64), ("mixed", dg.DG_SOLVE_MIXED)):
+        x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.solve(x, mode=mode, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=rtol, restart=restart,
+                      outer_restart=outer_restart, inner_rtol=inner_rtol, raise_on_error=False)
+        torch.cuda.synchronize()
+        st["wall_s"] = time.perf_counter() - t0
+        out[name] = st
+        xs[name] = x
+    out["field_diff_mixed_vs_fp64"] = float((xs["mixed"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
+    # operator throughput at this size
+    for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        u = torch.rand(w.ndof, dtype=dt, device="cuda")
+        y = torch.empty_like(u)
+        for _ in range(3):
+            op.apply_jacobian(u, y)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            op.apply_jacobian(u, y)
+        b.record()
+        b.synchronize()
+        out[f"apply_{prec}_mdofs"] = w.ndof * 20 / (a.elapsed_time(b) * 1e-3) / 1e6
+        r = torch.empty_like(u)
+        a.record()
+        for _ in range(20):
+            op.precond_apply(u, r)
+        b.record()
+        b.synchronize()
+        out[f"block_jacobi_{prec}_ms"] = a.elapsed_time(b) / 20
+    op.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -324,6 +374,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-only", action="store_true", help="print the mixed vs FP64 solve comparison only")
     ap.add_argument("--profile", action="store_true",
                     help="only run warmup + steps residual applies (for ncu launch lists and captures)")
     args = ap.parse_args()
@@ -333,6 +384,10 @@ def main():
         run_reference(args)
     elif args.profile:
         run_profile(args)
+    elif args.solve_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(solve_benchmark()), flush=True)
     else:
         run_ours(args)
 
