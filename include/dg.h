@@ -189,6 +189,41 @@ int dg_precond_apply(dg_handle* h, const void* r_dev, void* z_dev, int32_t preci
 int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_opts* opts, dg_solve_stats* stats,
              void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Allocation-free Jacobian application.  The paper has no counterpart of this entry point.
+ *
+ * dg_setup obtains its tables, coefficients and work buffers from cudaMalloc.  Some callers cannot
+ * allocate device memory at the point where they apply the operator: a host application that owns
+ * all device memory through its own pool and forbids other allocators, or a latency-critical loop
+ * where cudaMalloc, which can synchronise the whole device, is not allowed after start-up.
+ * dg_apply_jacobian_static serves them.  It computes y = A z in FP64 exactly like
+ * dg_apply_jacobian (same kernels, same operator), and it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Its work space (point-space residual, face traces, face coefficients) is a fixed device array
+ * of DG_STATIC_SCRATCH_BYTES inside libdg.so.  Every GPU that loads the library holds this array
+ * until the process exits.  A problem needs
+ *     256-byte-rounded ncells*(k+1)^3*8  +  ncells*12*(k+1)^2*8  +  ncells*18*8  bytes,
+ * for example at most about 3200 cells at k = 7 or 15000 cells at k = 3.  Larger problems are
+ * rejected with DG_ERR_INVALID_ARG and a message; use dg_setup / dg_apply_jacobian for them.
+ *
+ * Arguments: the mesh and degree as in dg_setup; D_dev is a device array of ncells diffusion
+ * values (finite, > 0, not checked on the device); b, c and sigma are as in dg_coeffs.  z_dev and
+ * y_dev are FP64 device vectors in the DOF layout above and must not alias.  The call is
+ * asynchronous on `stream`.
+ *
+ * Set-up: the first call on each device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current, so make this first call before any stream
+ * capture.  Sharing: all calls in the process use the same array, and a call leaves its contents
+ * behind.  Every byte a call reads has been written earlier in that call, so nothing has to start
+ * at zero.  Calls whose kernels overlap on the GPU (different streams or host threads without
+ * ordering) race on the array and give wrong results; order them on one stream.
+ * --------------------------------------------------------------------------------------------- */
+#define DG_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+int dg_apply_jacobian_static(const dg_mesh* mesh, int32_t k, const double* D_dev, const double b[3], double c,
+                             double sigma, const double* z_dev, double* y_dev, void* stream);
+
 /* Message for the calling thread's last error ("" if none). */
 const char* dg_last_error(void);
 

@@ -35,7 +35,7 @@ static void shifted_legendre(int jmax, double x, double* p, double* dp) {
 }
 
 // Gauss-Legendre nodes/weights on [0,1] (Sec. 3.1) and the 1D matrices of the kernels.
-static void build_tables(int N, Tables1D* tb) {
+void build_tables(int N, Tables1D* tb) {
   tb->N = N;
   double p[MAXN + 2], dp[MAXN + 2];
   // Newton on P_N(2x-1) for the lower half of the nodes; the rule is symmetric about 1/2, and the

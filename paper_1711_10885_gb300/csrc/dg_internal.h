@@ -53,6 +53,8 @@ struct dg_handle {
 namespace dgi {
 
 void set_error(const std::string& msg);
+// Gauss-Legendre nodes/weights and the 1D matrices for N = k+1 (host, FP64)
+void build_tables(int N, Tables1D* tb);
 int cuda_fail(cudaError_t e, const char* what);
 
 // mode 0: y = A z, mode 1: y = A z - F; stages: bit 0 cell kernel, bit 1 face kernel (3 = full apply)
