@@ -233,6 +233,48 @@ def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10):
     return out
 
 
+def batch_benchmark(reps=20):
+    """64 uneven problems (n ~ U{4..24}, k ~ U{2..8}, seed 5): one graph launch vs the standalone applies."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, inputs
+    ws = inputs.batch_problems(64, seed=5)
+    ops = [dg.operator_for(w) for w in ws]
+    xs = [torch.tensor(w.u, device="cuda") for w in ws]
+    ys = [torch.empty_like(x) for x in xs]
+    t0 = time.perf_counter()
+    batch = dg.Batch(ops)
+    tune_s = time.perf_counter() - t0
+    dofs = sum(w.ndof for w in ws)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def standalone():
+        for op, x, y in zip(ops, xs, ys):
+            op.apply_jacobian(x, y)
+
+    ms_batch = timed(lambda: batch.apply(xs, ys))
+    ms_alone = timed(standalone)
+    out = {"problems": len(ws), "dofs": dofs, "graph_launch_ms": ms_batch, "standalone_sum_ms": ms_alone,
+           "batch_mdofs": dofs / (ms_batch * 1e-3) / 1e6, "standalone_mdofs": dofs / (ms_alone * 1e-3) / 1e6,
+           "speedup": ms_alone / ms_batch, "autotune_s": tune_s,
+           "cells_per_cta": {k: batch.tuning(k)["cells_per_cta"] for k in sorted({w.k for w in ws})}}
+    batch.close()
+    for op in ops:
+        op.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -359,6 +401,8 @@ def run_ours(args):
         "clocks": clocks,
         "extra": extra,
     }
+    if ws == 1 and not args.no_batch:
+        line["batch"] = batch_benchmark()
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -374,6 +418,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--solve-only", action="store_true", help="print the mixed vs FP64 solve comparison only")
     ap.add_argument("--profile", action="store_true",
                     help="only run warmup + steps residual applies (for ncu launch lists and captures)")

@@ -190,6 +190,33 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
              void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Batched application of many uneven problems.  The paper applies one operator per process
+ * (Sec. 5); a batch runs the applies of many handles (different meshes and degrees 1..8, FP64) in
+ * one CUDA graph launch: each of the two kernels of Algorithm 1's split (cell kernel, face kernel)
+ * runs as one persistent kernel that takes tiles of cells of all problems from a work queue
+ * (heaviest tiles first).  At creation an autotuner times, per degree, two cells-per-CTA choices
+ * (so two CTA thread layouts) on that degree's problems and keeps the faster.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct dg_batch dg_batch;
+
+/* Create a batch over `count` handles (not owned: they must outlive the batch, and must not be
+ * applied on their own while a batch apply that uses them is in flight, since the batch uses their
+ * work buffers).  Runs the autotuner on `stream` and synchronises it. */
+int dg_batch_create(dg_handle* const* handles, int32_t count, void* stream, dg_batch** out);
+
+/* For every problem i: out_dev[i] = A_i in_dev[i] (residual = 0) or A_i in_dev[i] - F_i (residual = 1),
+ * FP64 device vectors, as one graph launch on `stream`.  The first call captures the graph; later
+ * calls with the same vectors and mode launch it directly (no host synchronisation). */
+int dg_batch_apply(dg_batch* b, const double* const* in_dev, double* const* out_dev, int32_t residual,
+                   void* stream);
+
+/* Autotuner result for degree k: chosen cells per CTA, and the measured time (ms) of the two
+ * candidates (full and half cells per CTA) on that degree's problems. */
+int dg_batch_tuning(const dg_batch* b, int32_t k, int32_t* cells_per_cta, float* ms_candidates);
+
+int dg_batch_destroy(dg_batch* b);
+
+/* ---------------------------------------------------------------------------------------------
  * Allocation-free Jacobian application.  The paper has no counterpart of this entry point.
  *
  * dg_setup obtains its tables, coefficients and work buffers from cudaMalloc.  Some callers cannot

@@ -267,20 +267,19 @@ struct SelfArgs {
   int cell_base;  // first real cell of the chunk
 };
 
-template <int N, typename T, bool SELF = false>
-__global__ void __launch_bounds__(Launch<N>::THREADS)
-dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g, const T* __restrict__ z,
-               const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces, SelfArgs sa_) {
-  constexpr int NN = N * N, N3 = N * N * N, CPB = Launch<N>::CPB, CS = Lay<N>::CS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Cell-kernel work on one tile of `here` consecutive cells starting at cell0 (virtual cells in SELF mode),
+// run by all threads of the CTA (blockDim.x >= CPB * N^2; threads beyond that only help with copies).
+template <int N, typename T, bool SELF, int CPB>
+__device__ __forceinline__ void cell_tile(const Tab<N, T>& tb, const Geo<T>& g, const T* __restrict__ z,
+                                          const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces,
+                                          int cell0, int here, int cell_base, unsigned char* smem_raw) {
+  constexpr int NN = N * N, N3 = N * N * N, CS = Lay<N>::CS;
   T* sU = reinterpret_cast<T*>(smem_raw);
   T* sV = sU + CPB * CS;
-  const int cell0 = blockIdx.x * CPB;
-  const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
   const bool active = lc < here;
   const int cell = cell0 + lc;                                 // output index (virtual in SELF mode)
-  const int rcell = SELF ? sa_.cell_base + cell / N3 : cell;   // real cell (coefficients)
+  const int rcell = SELF ? cell_base + cell / N3 : cell;       // real cell (coefficients)
   T* U = sU + lc * CS;
   T* V = sV + lc * CS;
 
@@ -339,6 +338,16 @@ dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
     __syncthreads();
   }
   gstore_cells<N>(Vout, sV, cell0, here);
+}
+
+template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB>
+__global__ void __launch_bounds__(CPB * N * N)
+dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g, const T* __restrict__ z,
+               const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces, SelfArgs sa_) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * CPB;
+  const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
+  cell_tile<N, T, SELF, CPB>(tb, g, z, Dcell, Vout, traces, cell0, here, sa_.cell_base, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -417,19 +426,16 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>&
   }
 }
 
-template <int N, typename T, bool SELF = false>
-__global__ void __launch_bounds__(Launch<N>::THREADS)
-dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g,
-               const __grid_constant__ FaceArgs<T> fa, SelfArgs sa_) {
-  constexpr int NN = N * N, N3 = N * N * N, CPB = Launch<N>::CPB, CS = Lay<N>::CS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Face-kernel work on one tile of `here` consecutive cells starting at cell0 (see cell_tile).
+template <int N, typename T, bool SELF, int CPB>
+__device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, const FaceArgs<T>& fa, int cell0,
+                                          int here, int cell_base, unsigned char* smem_raw) {
+  constexpr int NN = N * N, N3 = N * N * N, CS = Lay<N>::CS;
   T* sV = reinterpret_cast<T*>(smem_raw);
-  const int cell0 = blockIdx.x * CPB;
-  const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
   const bool active = lc < here;
   const int vcell = cell0 + lc;                                // output / trace index
-  const int cell = SELF ? sa_.cell_base + vcell / N3 : vcell;  // real cell
+  const int cell = SELF ? cell_base + vcell / N3 : vcell;      // real cell
   T* V = sV + lc * CS;
 
   gload_cells<N>(sV, fa.V, cell0, here);
@@ -499,6 +505,16 @@ dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
     if (fa.mode == 1) val -= Fs[e];
     dst[e] = val;
   }
+}
+
+template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB>
+__global__ void __launch_bounds__(CPB * N * N)
+dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g,
+               const __grid_constant__ FaceArgs<T> fa, SelfArgs sa_) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * CPB;
+  const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
+  face_tile<N, T, SELF, CPB>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
 }
 
 }  // namespace dgk

@@ -85,6 +85,10 @@ def _load():
     lib.dg_precond_setup.argtypes = [vp, ctypes.c_int32, vp]
     lib.dg_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
     lib.dg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(dg_solve_opts), ctypes.POINTER(dg_solve_stats), vp]
+    lib.dg_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.dg_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, vp]
+    lib.dg_batch_tuning.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
+    lib.dg_batch_destroy.argtypes = [vp]
     return lib
 
 
@@ -93,7 +97,8 @@ lib = _load()
 # C-ABI symbols declared in include/dg.h (checked by the CPU test suite)
 EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadrature_points", "dg_apply_jacobian",
             "dg_apply_residual", "dg_rhs", "dg_last_error", "dg_apply_stage", "dg_precond_setup",
-            "dg_precond_apply", "dg_solve"]
+            "dg_precond_apply", "dg_solve", "dg_batch_create", "dg_batch_apply", "dg_batch_tuning",
+            "dg_batch_destroy"]
 
 
 def check(rc):
@@ -280,6 +285,43 @@ class Operator:
         F = torch.empty(self.ndof, dtype=dtype, device="cuda")
         check(lib.dg_rhs(self.h, ctypes.c_void_p(F.data_ptr()), _prec(F), _stream_ptr(stream)))
         return F
+
+
+class Batch:
+    """Many Operators applied in one graph launch (dg_batch_create / dg_batch_apply)."""
+
+    def __init__(self, ops, stream=None):
+        self.ops = list(ops)
+        arr = (ctypes.c_void_p * len(self.ops))(*[o.h.value for o in self.ops])
+        b = ctypes.c_void_p()
+        check(lib.dg_batch_create(arr, len(self.ops), _stream_ptr(stream), ctypes.byref(b)))
+        self.b = b
+
+    def apply(self, xs, ys, residual=False, stream=None):
+        n = len(self.ops)
+        for op, x, y in zip(self.ops, xs, ys):
+            op._vec_check(x, y)
+        ins = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        outs = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        check(lib.dg_batch_apply(self.b, ins, outs, int(bool(residual)), _stream_ptr(stream)))
+        return ys
+
+    def tuning(self, k):
+        cpb = ctypes.c_int32()
+        ms = (ctypes.c_float * 2)()
+        check(lib.dg_batch_tuning(self.b, int(k), ctypes.byref(cpb), ms))
+        return {"cells_per_cta": cpb.value, "ms_full": ms[0], "ms_half": ms[1]}
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib.dg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def operator_for(w, stream=None, sigma=None):
