@@ -144,7 +144,11 @@ int dg_rhs(dg_handle* h, void* F_dev, int32_t precision, void* stream);
  * --------------------------------------------------------------------------------------------- */
 
 enum { DG_SOLVE_FP64 = 0, DG_SOLVE_MIXED = 1 };
-enum { DG_PRECOND_NONE = 0, DG_PRECOND_BLOCK_JACOBI = 1 };
+/* DG_PRECOND_MLP: z = network(r); DG_PRECOND_BJ_MLP: z = block-Jacobi(r) + network(r), the network
+ * trained on the part of the error that block-Jacobi misses (needs dg_precond_setup). */
+enum { DG_PRECOND_NONE = 0, DG_PRECOND_BLOCK_JACOBI = 1, DG_PRECOND_MLP = 2, DG_PRECOND_BJ_MLP = 3 };
+
+typedef struct dg_mlp dg_mlp; /* learned per-element preconditioner, see below */
 
 typedef struct {
   int32_t mode;           /* DG_SOLVE_FP64: FGMRES(restart) in FP64 on the FP64 operator.
@@ -158,6 +162,14 @@ typedef struct {
   int32_t max_iterations; /* cap on (outer) iterations, 0 = 10000                                      */
   double rtol;            /* stop when ||b - A x||_2 <= rtol ||b||_2, checked on the FP64 residual     */
   double inner_rtol;      /* MIXED: relative residual reduction of each inner solve, in (0, 1)         */
+  const dg_mlp* mlp;      /* DG_PRECOND_MLP: the trained network (degree must match the handle)       */
+  int32_t mlp_placement;  /* MLP modes: 0 = the network acts in every preconditioner application;
+                             1 = only on the first direction of each (outer) FGMRES cycle, whose input is
+                             the true residual r/||r|| like its training data; the other directions use
+                             block-Jacobi (DG_PRECOND_BJ_MLP) or none (DG_PRECOND_MLP)              */
+  double fallback_ratio;  /* DG_PRECOND_MLP: if one inner cycle (MIXED) or restart cycle (FP64) reduces
+                             its residual by less than this factor (e.g. 0.5), the rest of the solve
+                             uses block-Jacobi when dg_precond_setup was called; 0 = never          */
 } dg_solve_opts;
 
 typedef struct {
@@ -168,6 +180,7 @@ typedef struct {
   int32_t applies_f32;      /* FP32 operator applications                                           */
   double rel_residual;      /* final ||b - A x||_2 / ||b||_2 (true FP64 residual at exit)           */
   double seconds;           /* wall time of the call                                                */
+  int32_t fallback;         /* 1 if an MLP-preconditioned solve switched to block-Jacobi            */
 } dg_solve_stats;
 
 /* Build the block-Jacobi preconditioner (kind = DG_PRECOND_BLOCK_JACOBI): for every cell the
@@ -188,6 +201,65 @@ int dg_precond_apply(dg_handle* h, const void* r_dev, void* z_dev, int32_t preci
  * step).  Workspace is allocated on first use and kept by the handle. */
 int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_opts* opts, dg_solve_stats* stats,
              void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned per-element preconditioner.  The paper has no solver or preconditioner (Sec. 1, Sec. 6
+ * leave them to future work); this network is trained on (residual, error) pairs produced by the
+ * solver above on the operator above, and used as the preconditioner M inside FGMRES.
+ *
+ * For a cell T with residual block r_T ((k+1)^3 values) the network input is
+ *   x = [r_T / s, log D_T, log D of the 6 face neighbours (x-, x+, y-, y+, z-, z+; the cell's own
+ *        value where the neighbour is missing)],  s = ||r_T||_2,  zero-padded to kin_padded,
+ * two ReLU layers of 256 units, and an output layer of (k+1)^3 units; the correction is
+ *   z_T = s * t_scale * y(x),
+ * which makes the preconditioner positively homogeneous in r.  Weights are FP32 masters rounded to
+ * BF16 for the forward GEMMs (tensor cores, FP32 accumulation); the backward pass and Adam run in
+ * FP32.  Rows of X are BF16 [rows][kin_padded]; targets T are FP32 [rows][(k+1)^3].
+ * --------------------------------------------------------------------------------------------- */
+typedef struct {
+  int32_t epochs;   /* passes over the rows                    */
+  int32_t batch;    /* rows per Adam step (rows / batch steps)   */
+  double lr;        /* Adam step size (beta1 0.9, beta2 0.999)   */
+} dg_mlp_train_opts;
+
+typedef struct {
+  double first_epoch_loss; /* mean squared error over the first epoch  */
+  double last_epoch_loss;  /* mean squared error over the last epoch   */
+  int64_t steps;           /* Adam steps taken by this network so far  */
+} dg_mlp_train_stats;
+
+/* New network for degree k in [1, 7], He-uniform weights from `seed`, zero biases, t_scale 1. */
+int dg_mlp_create(int32_t k, uint64_t seed, dg_mlp** out);
+int dg_mlp_destroy(dg_mlp* m);
+int dg_mlp_dims(const dg_mlp* m, int32_t* k, int32_t* kin, int32_t* kin_padded, int32_t* out_padded,
+                int64_t* nparam);
+/* Parameter block (FP32, nparam values: W1 [256][kin_padded], b1, W2 [256][256], b2,
+ * W3 [out_padded][256], b3 at the offsets of dg_mlp_param_offsets).  direction 0: copy weights to
+ * host; 1: copy weights from host (BF16 copy refreshed, t_scale set if non-NULL); 2: copy the
+ * gradient of the last dg_mlp_loss_grad / training step to host.  Synchronous. */
+int dg_mlp_params(dg_mlp* m, float* host, int32_t direction, float* t_scale);
+int dg_mlp_param_offsets(const dg_mlp* m, int64_t* offsets6);
+int dg_mlp_set_target_scale(dg_mlp* m, float t_scale);
+/* Feature rows X (device, BF16) and scales s * t_scale (device) for the listed cells of the handle's
+ * mesh (cells_dev = NULL: all cells in order, rows = ncells), from the residual r_dev (device, given
+ * precision). */
+int dg_mlp_features(const dg_mlp* m, const dg_handle* h, const void* r_dev, int32_t precision,
+                    const int32_t* cells_dev, int64_t rows, void* X_dev, float* scale_dev, void* stream);
+/* Y = network(X) for `rows` rows: Y device FP32 [rows][out_padded]. */
+int dg_mlp_forward(const dg_mlp* m, const void* X_dev, int64_t rows, float* Y_dev, void* stream);
+/* Mean squared error of network(X) against T and its gradient (kept in the network). */
+int dg_mlp_loss_grad(dg_mlp* m, const void* X_dev, const float* T_dev, int64_t rows, double* loss, void* stream);
+/* Adam training on the rows in order (batches of opts->batch rows); synchronises `stream`. */
+int dg_mlp_train(dg_mlp* m, const void* X_dev, const float* T_dev, int64_t rows, const dg_mlp_train_opts* opts,
+                 dg_mlp_train_stats* stats, void* stream);
+/* The preconditioner: z = M(r) for every cell of the handle (r, z device vectors, given precision). */
+int dg_mlp_apply(dg_mlp* m, const dg_handle* h, const void* r_dev, void* z_dev, int32_t precision, void* stream);
+/* z += M(r): the network's correction added to z (used with block-Jacobi in DG_PRECOND_BJ_MLP). */
+int dg_mlp_apply_add(dg_mlp* m, const dg_handle* h, const void* r_dev, void* z_dev, int32_t precision,
+                     void* stream);
+/* Checkpoint: weights, Adam moments and step count, t_scale (binary, host file). */
+int dg_mlp_save(const dg_mlp* m, const char* path);
+int dg_mlp_load(const char* path, dg_mlp** out);
 
 /* ---------------------------------------------------------------------------------------------
  * Batched application of many uneven problems.  The paper applies one operator per process

@@ -1,0 +1,831 @@
+// dg_mlp.cu -- per-element MLP preconditioner: feature gather, fused BF16 tensor-core forward pass,
+// FP32 backward pass, Adam, and the preconditioner application z = M(r) used inside FGMRES.
+//
+// Network (per cell T): x = [r_T / s, log D_T, log D of the 6 face neighbours (own value where there is
+// no neighbour)], s = ||r_T||_2;  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3 (256 hidden
+// units each); the correction is z_T = s * t_scale * y.  Weights are kept in FP32 (master copy, Adam
+// moments) and rounded to BF16 for the forward GEMMs; accumulation is FP32.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "dg_internal.h"
+
+namespace dgm {
+
+constexpr int HID = 256;
+constexpr int ROWS = 64;      // rows (cells) per CTA in the forward kernel
+constexpr int FWD_THREADS = 256;
+
+struct Dims {
+  int nb;    // (k+1)^3
+  int kin;   // nb + 7
+  int kinp;  // kin rounded up to 16
+  int outp;  // nb rounded up to 16
+};
+
+inline Dims dims_for(int k) {
+  Dims d;
+  d.nb = (k + 1) * (k + 1) * (k + 1);
+  d.kin = d.nb + 7;
+  d.kinp = (d.kin + 15) / 16 * 16;
+  d.outp = (d.nb + 15) / 16 * 16;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// One warp computes a 16 x (8 * NT) block of C = A(16 x K, shared memory, row stride lda elements)
+// times W^T (W: row-major [n][K] in global memory, rows n0 .. n0 + 8 NT - 1).
+template <int NT>
+__device__ __forceinline__ void warp_gemm(const __nv_bfloat16* As, int lda, const __nv_bfloat16* __restrict__ W,
+                                          int ldw, int n0, int K, float (&acc)[NT][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    a[0] = *reinterpret_cast<const uint32_t*>(As + g * lda + k0 + tig * 2);
+    a[1] = *reinterpret_cast<const uint32_t*>(As + (g + 8) * lda + k0 + tig * 2);
+    a[2] = *reinterpret_cast<const uint32_t*>(As + g * lda + k0 + 8 + tig * 2);
+    a[3] = *reinterpret_cast<const uint32_t*>(As + (g + 8) * lda + k0 + 8 + tig * 2);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const __nv_bfloat16* wr = W + (size_t)(n0 + 8 * j + g) * ldw + k0 + tig * 2;
+      const uint32_t b0 = __ldg(reinterpret_cast<const unsigned int*>(wr));
+      const uint32_t b1 = __ldg(reinterpret_cast<const unsigned int*>(wr + 8));
+      mma_bf16(acc[j], a, b0, b1);
+    }
+  }
+}
+
+struct FwdArgs {
+  const __nv_bfloat16* X;  // [rows][kinp]
+  const __nv_bfloat16* W1; // [HID][kinp]
+  const float* b1;
+  const __nv_bfloat16* W2; // [HID][HID]
+  const float* b2;
+  const __nv_bfloat16* W3; // [outp][HID]
+  const float* b3;
+  __nv_bfloat16* H1;       // optional [rows][HID] (training)
+  __nv_bfloat16* H2;       // optional [rows][HID]
+  float* Y;                // optional [rows][outp]
+  // preconditioner output (optional): z[cell * nb + j] = scale[row] * y[row][j]
+  const float* scale;
+  void* z;
+  int z_is_f64;
+  int z_accumulate;  // z += ... instead of z = ...
+  int64_t rows;
+  int kinp, outp, nb;
+};
+
+// Output layer on 8 NT columns starting at c0 for this warp's 16 rows, with the bias and either the
+// raw output Y or the scaled preconditioner output z.
+template <int NT>
+__device__ __forceinline__ void layer3_chunk(const FwdArgs& a, const __nv_bfloat16* As, int lda, int c0, int rA,
+                                             int rB, int64_t row0, int here) {
+  const int tig = (threadIdx.x & 31) & 3;
+  float acc[NT][4];
+  warp_gemm<NT>(As, lda, a.W3, HID, c0, HID, acc);
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int col = c0 + 8 * j + 2 * tig;
+    const float y0 = acc[j][0] + a.b3[col], y1 = acc[j][1] + a.b3[col + 1];
+    const float y2 = acc[j][2] + a.b3[col], y3 = acc[j][3] + a.b3[col + 1];
+    if (a.Y) {
+      if (rA < here) {
+        a.Y[(row0 + rA) * a.outp + col] = y0;
+        a.Y[(row0 + rA) * a.outp + col + 1] = y1;
+      }
+      if (rB < here) {
+        a.Y[(row0 + rB) * a.outp + col] = y2;
+        a.Y[(row0 + rB) * a.outp + col + 1] = y3;
+      }
+    }
+    if (a.z) {
+      const float vals[4] = {y0, y1, y2, y3};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = q < 2 ? rA : rB, cc = col + (q & 1);
+        if (r < here && cc < a.nb) {
+          const float v = a.scale[row0 + r] * vals[q];
+          const size_t zi = (size_t)(row0 + r) * a.nb + cc;
+          if (a.z_is_f64) {
+            double* zp = static_cast<double*>(a.z) + zi;
+            *zp = a.z_accumulate ? *zp + (double)v : (double)v;
+          } else {
+            float* zp = static_cast<float*>(a.z) + zi;
+            *zp = a.z_accumulate ? *zp + v : v;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Fused 3-layer forward pass for 64 rows per CTA: 8 warps = 4 row tiles x 2 column halves.
+__global__ void __launch_bounds__(FWD_THREADS) mlp_forward(const FwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldx = a.kinp + 8, ldh = HID + 8;
+  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  __nv_bfloat16* H1s = Xs + ROWS * ldx;
+  __nv_bfloat16* H2s = H1s + ROWS * ldh;
+  const int64_t row0 = (int64_t)blockIdx.x * ROWS;
+  const int here = (int)min((int64_t)ROWS, a.rows - row0);
+  // stage X (rows beyond `here` are zero)
+  for (int e = threadIdx.x; e < ROWS * a.kinp / 2; e += blockDim.x) {
+    const int r = e / (a.kinp / 2), c2 = e - r * (a.kinp / 2);
+    uint32_t v = 0;
+    if (r < here) v = *reinterpret_cast<const uint32_t*>(a.X + (row0 + r) * a.kinp + 2 * c2);
+    *reinterpret_cast<uint32_t*>(Xs + r * ldx + 2 * c2) = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+  const int mt = warp & 3, nh = warp >> 2;
+  const int rA = 16 * mt + g, rB = rA + 8;
+  // layer 1 and 2: 16 x 128 per warp
+#pragma unroll 1
+  for (int layer = 0; layer < 2; ++layer) {
+    const __nv_bfloat16* As = layer == 0 ? Xs : H1s;
+    const int lda = layer == 0 ? ldx : ldh;
+    const int K = layer == 0 ? a.kinp : HID;
+    const __nv_bfloat16* W = layer == 0 ? a.W1 : a.W2;
+    const float* bias = layer == 0 ? a.b1 : a.b2;
+    __nv_bfloat16* Hs = layer == 0 ? H1s : H2s;
+    __nv_bfloat16* Hg = layer == 0 ? a.H1 : a.H2;
+    float acc[16][4];
+    warp_gemm<16>(As + 16 * mt * lda, lda, W, K, 128 * nh, K, acc);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int col = 128 * nh + 8 * j + 2 * tig;
+      const float bb0 = bias[col], bb1 = bias[col + 1];
+      const uint32_t lo = pack_bf16(fmaxf(acc[j][0] + bb0, 0.f), fmaxf(acc[j][1] + bb1, 0.f));
+      const uint32_t hi = pack_bf16(fmaxf(acc[j][2] + bb0, 0.f), fmaxf(acc[j][3] + bb1, 0.f));
+      *reinterpret_cast<uint32_t*>(Hs + rA * ldh + col) = lo;
+      *reinterpret_cast<uint32_t*>(Hs + rB * ldh + col) = hi;
+      if (Hg) {
+        if (rA < here) *reinterpret_cast<uint32_t*>(Hg + (row0 + rA) * HID + col) = lo;
+        if (rB < here) *reinterpret_cast<uint32_t*>(Hg + (row0 + rB) * HID + col) = hi;
+      }
+    }
+    __syncthreads();
+  }
+  // layer 3: outp columns, split in halves between the two warp columns, up to 128 columns at a time
+  const int half = a.outp / 2;
+  for (int c0 = nh * half; c0 < (nh + 1) * half; c0 += 128) {
+    const int ntiles = min(128, (nh + 1) * half - c0) / 8;  // outp is a multiple of 16
+    switch (ntiles) {
+#define L3(NT) \
+  case NT:     \
+    layer3_chunk<NT>(a, H2s + 16 * mt * ldh, ldh, c0, rA, rB, row0, here); \
+    break;
+      L3(1) L3(2) L3(3) L3(4) L3(5) L3(6) L3(7) L3(8) L3(9) L3(10) L3(11) L3(12) L3(13) L3(14) L3(15) L3(16)
+#undef L3
+      default:
+        break;
+    }
+  }
+}
+
+// Feature rows for cells: X[row] = [r_T / s, log D (own, x-, x+, y-, y+, z-, z+), 0 ...] in BF16, and
+// scale[row] = s * t_scale (s = ||r_T||_2; a zero residual gives a zero row and scale 0).
+template <typename T>
+__global__ void mlp_features(const T* __restrict__ r, const double* __restrict__ D, int nx, int ny, int nz,
+                             const int* __restrict__ cells, int64_t nrows, int nb, int kinp, float t_scale,
+                             __nv_bfloat16* __restrict__ X, float* __restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = warp0; row < nrows; row += nwarps) {
+    const int64_t cell = cells ? cells[row] : row;
+    const T* rc = r + cell * nb;
+    float ss = 0.f;
+    for (int j = lane; j < nb; j += 32) {
+      const float v = (float)rc[j];
+      ss = fmaf(v, v, ss);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const float s = sqrtf(ss);
+    const float inv = s > 0.f ? 1.f / s : 0.f;
+    __nv_bfloat16* xr = X + row * kinp;
+    for (int j = lane; j < nb; j += 32) xr[j] = __float2bfloat16_rn((float)rc[j] * inv);
+    if (lane < 7) {
+      const int ic[3] = {(int)(cell % nx), (int)((cell / nx) % ny), (int)(cell / ((int64_t)nx * ny))};
+      int64_t c = cell;
+      if (lane > 0) {
+        const int dir = (lane - 1) / 2, up = (lane - 1) & 1;
+        const int n[3] = {nx, ny, nz};
+        const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+        const bool inside = up ? ic[dir] + 1 < n[dir] : ic[dir] > 0;
+        if (inside) c = up ? cell + st[dir] : cell - st[dir];
+      }
+      xr[nb + lane] = __float2bfloat16_rn((float)log(D[c]));
+    }
+    for (int j = nb + 7 + lane; j < kinp; j += 32) xr[j] = __float2bfloat16_rn(0.f);
+    if (lane == 0) scale[row] = s * t_scale;
+  }
+}
+
+// ---- backward pass (FP32 SIMT) ----
+
+// C[M x N] (+)= sum_k A(m,k) B(k,n) with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) sgemm(int M, int N, int K, const TA* __restrict__ A, int64_t sam,
+                                             int64_t sak, const TB* __restrict__ B, int64_t sbk, int64_t sbn,
+                                             float* __restrict__ C, int ldc, int accumulate) {
+  __shared__ float As[16][64 + 1];
+  __shared__ float Bs[16][64 + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int kk = e / 64, mm = e % 64;
+      const int gm = m0 + mm, gk = k0 + kk, gn = n0 + mm;
+      As[kk][mm] = (gm < M && gk < K) ? (float)A[gm * sam + gk * sak] : 0.f;
+      Bs[kk][mm] = (gn < N && gk < K) ? (float)B[gk * sbk + gn * sbn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+      if (gm < M && gn < N) C[(size_t)gm * ldc + gn] = accumulate ? C[(size_t)gm * ldc + gn] + acc[i][j] : acc[i][j];
+    }
+}
+
+// dY = 2 (Y - T) / (rows * nb) on the nb real outputs (zero on the padding); loss partials per block
+__global__ void loss_grad(const float* __restrict__ Y, const float* __restrict__ T, int64_t rows, int nb, int outp,
+                          float* __restrict__ dY, double* __restrict__ loss_part) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  const float inv = 2.f / (float)((double)rows * nb);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * outp; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / outp;
+    const int c = (int)(e - r * outp);
+    float d = 0.f;
+    if (c < nb) {
+      d = Y[e] - T[r * nb + c];
+      acc += (double)d * d;
+    }
+    dY[e] = d * inv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    loss_part[blockIdx.x] = t;
+  }
+}
+
+// dZ = dH * (H > 0)
+__global__ void relu_back(float* __restrict__ dH, const __nv_bfloat16* __restrict__ H, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!(__bfloat162float(H[i]) > 0.f)) dH[i] = 0.f;
+}
+
+// db[c] = sum_r dZ[r][c]  (one thread per column, fixed order)
+__global__ void col_sum(const float* __restrict__ dZ, int64_t rows, int cols, float* __restrict__ db) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float acc = 0.f;
+  for (int64_t r = 0; r < rows; ++r) acc += dZ[r * cols + c];
+  db[c] = acc;
+}
+
+__global__ void adam_step(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                          float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                          float c2, __nv_bfloat16* __restrict__ wh) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wh) wh[i] = __float2bfloat16_rn(wi);
+  }
+}
+
+__global__ void to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
+}
+
+}  // namespace dgm
+
+// Parameters: one FP32 master block [W1 | b1 | W2 | b2 | W3 | b3] with its Adam moments, and BF16
+// copies of W1, W2, W3 (biases stay FP32 in the forward pass).
+struct dg_mlp {
+  int k = 0;
+  dgm::Dims d;
+  float t_scale = 1.f;
+  int64_t nparam = 0;
+  int64_t off[6] = {};   // offsets of W1, b1, W2, b2, W3, b3 in the FP32 block
+  float* w = nullptr;    // FP32 master
+  float* g = nullptr;    // gradient
+  float* m = nullptr;
+  float* v = nullptr;
+  __nv_bfloat16* wh = nullptr;  // BF16 copy of the whole block (only W1, W2, W3 are read)
+  int64_t adam_t = 0;
+  // training / inference scratch (grown on demand)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+namespace dgi {
+bool mlp_matches(const dg_mlp* m, const dg_handle* h) { return m && h && m->d.nb == h->N * h->N * h->N; }
+}  // namespace dgi
+
+namespace {
+
+using namespace dgi;
+
+int cfail(cudaError_t e, const char* what) { return e == cudaSuccess ? 0 : cuda_fail(e, what); }
+
+size_t fwd_smem(const dgm::Dims& d) {
+  return ((size_t)dgm::ROWS * (d.kinp + 8) + 2 * (size_t)dgm::ROWS * (dgm::HID + 8)) * sizeof(__nv_bfloat16);
+}
+
+int ensure_ws(dg_mlp* m, size_t bytes) {
+  if (m->ws_bytes >= bytes) return 0;
+  cudaFree(m->ws);
+  m->ws = nullptr;
+  m->ws_bytes = 0;
+  if (int rc = cfail(cudaMalloc(&m->ws, bytes), "cudaMalloc(MLP workspace)")) return rc;
+  m->ws_bytes = bytes;
+  return 0;
+}
+
+dgm::FwdArgs fwd_args(const dg_mlp* m, const __nv_bfloat16* X, int64_t rows) {
+  dgm::FwdArgs a{};
+  a.X = X;
+  a.W1 = m->wh + m->off[0];
+  a.b1 = m->w + m->off[1];
+  a.W2 = m->wh + m->off[2];
+  a.b2 = m->w + m->off[3];
+  a.W3 = m->wh + m->off[4];
+  a.b3 = m->w + m->off[5];
+  a.rows = rows;
+  a.kinp = m->d.kinp;
+  a.outp = m->d.outp;
+  a.nb = m->d.nb;
+  return a;
+}
+
+int launch_forward(const dg_mlp* m, const dgm::FwdArgs& a, cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = fwd_smem(m->d);
+  if (!attr || smem > 48 * 1024) {
+    if (int rc = cfail(cudaFuncSetAttribute(dgm::mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)std::max<size_t>(smem, 48 * 1024)),
+                       "MLP forward smem"))
+      return rc;
+    attr = true;
+  }
+  const unsigned grid = (unsigned)((a.rows + dgm::ROWS - 1) / dgm::ROWS);
+  if (grid == 0) return 0;
+  dgm::mlp_forward<<<grid, dgm::FWD_THREADS, smem, s>>>(a);
+  return cfail(cudaGetLastError(), "MLP forward");
+}
+
+template <typename TA, typename TB>
+int gemm(int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn, float* C,
+         int ldc, cudaStream_t s) {
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  dgm::sgemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, 0);
+  return cfail(cudaGetLastError(), "MLP backward GEMM");
+}
+
+// loss and gradient (into m->g) of one batch: X bf16 [rows][kinp], T fp32 [rows][nb]
+int loss_and_grad(dg_mlp* m, const __nv_bfloat16* X, const float* T, int64_t rows, double* loss, cudaStream_t s) {
+  const dgm::Dims& d = m->d;
+  const int H = dgm::HID;
+  // scratch: H1, H2 (bf16), Y, dY (f32 rows x outp), dH (f32 rows x H), loss partials
+  const size_t nbh = (size_t)rows * H * sizeof(__nv_bfloat16);
+  const size_t nY = (size_t)rows * d.outp * sizeof(float);
+  const size_t ndH = (size_t)rows * H * sizeof(float);
+  const int lblocks = 256;
+  const size_t bytes = 2 * nbh + 2 * nY + 2 * ndH + lblocks * sizeof(double) + 1024;
+  if (int rc = ensure_ws(m, bytes)) return rc;
+  unsigned char* p = static_cast<unsigned char*>(m->ws);
+  auto* H1 = reinterpret_cast<__nv_bfloat16*>(p);
+  auto* H2 = reinterpret_cast<__nv_bfloat16*>(p + nbh);
+  auto* Y = reinterpret_cast<float*>(p + 2 * nbh);
+  auto* dY = reinterpret_cast<float*>(p + 2 * nbh + nY);
+  auto* dH = reinterpret_cast<float*>(p + 2 * nbh + 2 * nY);
+  auto* dH1 = reinterpret_cast<float*>(p + 2 * nbh + 2 * nY + ndH);
+  auto* lp = reinterpret_cast<double*>(p + 2 * nbh + 2 * nY + 2 * ndH);
+  dgm::FwdArgs a = fwd_args(m, X, rows);
+  a.H1 = H1;
+  a.H2 = H2;
+  a.Y = Y;
+  if (int rc = launch_forward(m, a, s)) return rc;
+  dgm::loss_grad<<<lblocks, 256, 0, s>>>(Y, T, rows, d.nb, d.outp, dY, lp);
+  float* g = m->g;
+  const __nv_bfloat16* W2 = m->wh + m->off[2];
+  const __nv_bfloat16* W3 = m->wh + m->off[4];
+  int rc = 0;
+  // layer 3: dW3[o][h] = sum_r dY[r][o] H2[r][h]; db3; dH2 = dY W3
+  rc = gemm<float, __nv_bfloat16>(d.outp, H, (int)rows, dY, 1, d.outp, H2, H, 1, g + m->off[4], H, s);
+  if (!rc) {
+    dgm::col_sum<<<(d.outp + 127) / 128, 128, 0, s>>>(dY, rows, d.outp, g + m->off[5]);
+    rc = gemm<float, __nv_bfloat16>((int)rows, H, d.outp, dY, d.outp, 1, W3, H, 1, dH, H, s);
+  }
+  // layer 2
+  if (!rc) {
+    dgm::relu_back<<<1024, 256, 0, s>>>(dH, H2, (int64_t)rows * H);
+    rc = gemm<float, __nv_bfloat16>(H, H, (int)rows, dH, 1, H, H1, H, 1, g + m->off[2], H, s);
+  }
+  if (!rc) {
+    dgm::col_sum<<<(H + 127) / 128, 128, 0, s>>>(dH, rows, H, g + m->off[3]);
+    rc = gemm<float, __nv_bfloat16>((int)rows, H, H, dH, H, 1, W2, H, 1, dH1, H, s);  // dH1 = dZ2 W2
+  }
+  // layer 1
+  if (!rc) {
+    dgm::relu_back<<<1024, 256, 0, s>>>(dH1, H1, (int64_t)rows * H);
+    rc = gemm<float, __nv_bfloat16>(H, d.kinp, (int)rows, dH1, 1, H, X, d.kinp, 1, g + m->off[0], d.kinp, s);
+  }
+  if (!rc) {
+    dgm::col_sum<<<(H + 127) / 128, 128, 0, s>>>(dH1, rows, H, g + m->off[1]);
+    rc = cfail(cudaGetLastError(), "MLP backward");
+  }
+  if (!rc && loss) {
+    std::vector<double> h(lblocks);
+    rc = cfail(cudaMemcpyAsync(h.data(), lp, lblocks * sizeof(double), cudaMemcpyDeviceToHost, s), "loss copy");
+    if (!rc) rc = cfail(cudaStreamSynchronize(s), "loss sync");
+    double t = 0;
+    for (double x : h) t += x;
+    *loss = t / ((double)rows * d.nb);
+  }
+  return rc;
+}
+
+void free_mlp(dg_mlp* m) {
+  if (!m) return;
+  cudaFree(m->w);
+  cudaFree(m->g);
+  cudaFree(m->m);
+  cudaFree(m->v);
+  cudaFree(m->wh);
+  cudaFree(m->ws);
+  delete m;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_mlp_create(int32_t k, uint64_t seed, dg_mlp** out) {
+  if (!out || k < 1 || k > 7) {
+    set_error("dg_mlp_create: degree must be in [1, 7]");
+    return DG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  dg_mlp* m = new dg_mlp();
+  m->k = k;
+  m->d = dgm::dims_for(k);
+  const int H = dgm::HID;
+  // layer 3 keeps a full HID x HID-sized backing so the backward pass can reuse its buffers
+  const int64_t sizes[6] = {(int64_t)H * m->d.kinp, H, (int64_t)H * H, H, (int64_t)m->d.outp * H, m->d.outp};
+  int64_t o = 0;
+  for (int i = 0; i < 6; ++i) {
+    m->off[i] = o;
+    o += (sizes[i] + 63) / 64 * 64;
+  }
+  m->nparam = o;
+  // He-uniform initialisation on the real fan-in; padding rows/columns start at zero
+  std::vector<float> w(o, 0.f);
+  std::mt19937_64 rng(seed);
+  auto init = [&](int64_t off, int rows, int cols, int fan_in, int real_rows, int real_cols) {
+    const float lim = std::sqrt(6.f / (float)fan_in);
+    std::uniform_real_distribution<float> u(-lim, lim);
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) w[off + (int64_t)r * cols + c] = (r < real_rows && c < real_cols) ? u(rng) : 0.f;
+  };
+  init(m->off[0], H, m->d.kinp, m->d.kin, H, m->d.kin);
+  init(m->off[2], H, H, H, H, H);
+  init(m->off[4], m->d.outp, H, H, m->d.nb, H);
+  int rc = cfail(cudaMalloc(&m->w, o * sizeof(float)), "cudaMalloc(MLP)");
+  if (!rc) rc = cfail(cudaMalloc(&m->g, o * sizeof(float)), "cudaMalloc(MLP grad)");
+  if (!rc) rc = cfail(cudaMalloc(&m->m, o * sizeof(float)), "cudaMalloc(MLP m)");
+  if (!rc) rc = cfail(cudaMalloc(&m->v, o * sizeof(float)), "cudaMalloc(MLP v)");
+  if (!rc) rc = cfail(cudaMalloc(&m->wh, o * sizeof(__nv_bfloat16)), "cudaMalloc(MLP bf16)");
+  if (!rc) rc = cfail(cudaMemcpy(m->w, w.data(), o * sizeof(float), cudaMemcpyHostToDevice), "MLP upload");
+  if (!rc) rc = cfail(cudaMemset(m->m, 0, o * sizeof(float)), "MLP memset");
+  if (!rc) rc = cfail(cudaMemset(m->v, 0, o * sizeof(float)), "MLP memset");
+  if (!rc) rc = cfail(cudaMemset(m->g, 0, o * sizeof(float)), "MLP memset");
+  if (!rc) {
+    dgm::to_bf16<<<256, 256>>>(m->w, m->wh, o);
+    rc = cfail(cudaDeviceSynchronize(), "MLP init");
+  }
+  if (rc) {
+    free_mlp(m);
+    return rc;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_mlp_destroy(dg_mlp* m) {
+  free_mlp(m);
+  return DG_OK;
+}
+
+int dg_mlp_dims(const dg_mlp* m, int32_t* k, int32_t* kin, int32_t* kin_padded, int32_t* out_padded,
+                int64_t* nparam) {
+  if (!m) {
+    set_error("dg_mlp_dims: null");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (k) *k = m->k;
+  if (kin) *kin = m->d.kin;
+  if (kin_padded) *kin_padded = m->d.kinp;
+  if (out_padded) *out_padded = m->d.outp;
+  if (nparam) *nparam = m->nparam;
+  return DG_OK;
+}
+
+int dg_mlp_params(dg_mlp* m, float* host, int32_t direction, float* t_scale) {
+  // direction 0: device -> host (weights), 1: host -> device (weights, BF16 copy refreshed),
+  // 2: device -> host (last gradient)
+  if (!m || !host || direction < 0 || direction > 2) {
+    set_error("dg_mlp_params: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  const size_t bytes = m->nparam * sizeof(float);
+  int rc = 0;
+  if (direction == 0) rc = cfail(cudaMemcpy(host, m->w, bytes, cudaMemcpyDeviceToHost), "MLP download");
+  if (direction == 2) rc = cfail(cudaMemcpy(host, m->g, bytes, cudaMemcpyDeviceToHost), "MLP grad download");
+  if (direction == 1) {
+    rc = cfail(cudaMemcpy(m->w, host, bytes, cudaMemcpyHostToDevice), "MLP upload");
+    if (!rc) {
+      dgm::to_bf16<<<256, 256>>>(m->w, m->wh, m->nparam);
+      rc = cfail(cudaDeviceSynchronize(), "MLP bf16 refresh");
+    }
+    if (!rc && t_scale) m->t_scale = *t_scale;
+  } else if (t_scale) {
+    *t_scale = m->t_scale;
+  }
+  return rc;
+}
+
+int dg_mlp_param_offsets(const dg_mlp* m, int64_t* offsets6) {
+  if (!m || !offsets6) {
+    set_error("dg_mlp_param_offsets: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 6; ++i) offsets6[i] = m->off[i];
+  return DG_OK;
+}
+
+int dg_mlp_features(const dg_mlp* m, const dg_handle* h, const void* r, int32_t precision, const int32_t* cells,
+                    int64_t rows, void* X, float* scale, void* stream) {
+  if (!m || !h || !r || !X || !scale || (precision != DG_F64 && precision != DG_F32) ||
+      h->N * h->N * h->N != m->d.nb) {
+    set_error("dg_mlp_features: bad arguments or degree mismatch");
+    return DG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = cells ? rows : h->ncell;
+  auto* Xb = static_cast<__nv_bfloat16*>(X);
+  if (precision == DG_F64)
+    dgm::mlp_features<double><<<152 * 8, 256, 0, s>>>(static_cast<const double*>(r), static_cast<const double*>(h->p64.D),
+                                                      h->n[0], h->n[1], h->n[2], cells, n, m->d.nb, m->d.kinp,
+                                                      m->t_scale, Xb, scale);
+  else
+    dgm::mlp_features<float><<<152 * 8, 256, 0, s>>>(static_cast<const float*>(r), static_cast<const double*>(h->p64.D),
+                                                     h->n[0], h->n[1], h->n[2], cells, n, m->d.nb, m->d.kinp,
+                                                     m->t_scale, Xb, scale);
+  return cfail(cudaGetLastError(), "MLP features");
+}
+
+int dg_mlp_forward(const dg_mlp* m, const void* X, int64_t rows, float* Y, void* stream) {
+  if (!m || !X || !Y || rows < 0) {
+    set_error("dg_mlp_forward: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  dgm::FwdArgs a = fwd_args(m, static_cast<const __nv_bfloat16*>(X), rows);
+  a.Y = Y;
+  return launch_forward(m, a, static_cast<cudaStream_t>(stream));
+}
+
+int dg_mlp_loss_grad(dg_mlp* m, const void* X, const float* T, int64_t rows, double* loss, void* stream) {
+  if (!m || !X || !T || rows < 1) {
+    set_error("dg_mlp_loss_grad: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  return loss_and_grad(m, static_cast<const __nv_bfloat16*>(X), T, rows, loss, static_cast<cudaStream_t>(stream));
+}
+
+int dg_mlp_train(dg_mlp* m, const void* X, const float* T, int64_t rows, const dg_mlp_train_opts* o,
+                 dg_mlp_train_stats* st, void* stream) {
+  if (!m || !X || !T || !o || rows < 1 || o->batch < 1 || o->epochs < 1 || !(o->lr > 0)) {
+    set_error("dg_mlp_train: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto* Xb = static_cast<const __nv_bfloat16*>(X);
+  const int64_t nbatch = rows / o->batch;
+  if (nbatch < 1) {
+    set_error("dg_mlp_train: fewer rows than one batch");
+    return DG_ERR_INVALID_ARG;
+  }
+  double first = -1, last = 0;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int ep = 0; ep < o->epochs; ++ep) {
+    double sum = 0;
+    for (int64_t bi = 0; bi < nbatch; ++bi) {
+      double loss = 0;
+      const int64_t r0 = bi * o->batch;
+      int rc = loss_and_grad(m, Xb + r0 * m->d.kinp, T + r0 * m->d.nb, o->batch, &loss, s);
+      if (rc) return rc;
+      if (!std::isfinite(loss)) {
+        set_error("dg_mlp_train: non-finite loss");
+        return DG_ERR_NAN;
+      }
+      sum += loss;
+      ++m->adam_t;
+      const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
+      dgm::adam_step<<<512, 256, 0, s>>>(m->w, m->g, m->m, m->v, m->nparam, (float)o->lr, b1, b2, eps, c1, c2, m->wh);
+      if ((rc = cfail(cudaGetLastError(), "Adam step"))) return rc;
+    }
+    const double mean = sum / nbatch;
+    if (ep == 0) first = mean;
+    last = mean;
+  }
+  if (st) {
+    st->first_epoch_loss = first;
+    st->last_epoch_loss = last;
+    st->steps = m->adam_t;
+  }
+  return cfail(cudaStreamSynchronize(s), "dg_mlp_train sync");
+}
+
+int dg_mlp_set_target_scale(dg_mlp* m, float t_scale) {
+  if (!m || !(t_scale > 0) || !std::isfinite(t_scale)) {
+    set_error("dg_mlp_set_target_scale: scale must be finite and > 0");
+    return DG_ERR_INVALID_ARG;
+  }
+  m->t_scale = t_scale;
+  return DG_OK;
+}
+
+}  // extern "C"
+
+namespace dgi {
+int mlp_apply_impl(dg_mlp* m, const dg_handle* h, const void* r, void* z, int32_t precision, int accumulate,
+                   cudaStream_t s);
+}
+
+extern "C" {
+
+int dg_mlp_apply(dg_mlp* m, const dg_handle* h, const void* r, void* z, int32_t precision, void* stream) {
+  return dgi::mlp_apply_impl(m, h, r, z, precision, 0, static_cast<cudaStream_t>(stream));
+}
+
+int dg_mlp_apply_add(dg_mlp* m, const dg_handle* h, const void* r, void* z, int32_t precision, void* stream) {
+  return dgi::mlp_apply_impl(m, h, r, z, precision, 1, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+int dgi::mlp_apply_impl(dg_mlp* m, const dg_handle* h, const void* r, void* z, int32_t precision, int accumulate,
+                        cudaStream_t s) {
+  void* stream = s;
+  if (!m || !h || !r || !z || r == z || (precision != DG_F64 && precision != DG_F32) ||
+      h->N * h->N * h->N != m->d.nb) {
+    set_error("dg_mlp_apply: bad arguments or degree mismatch");
+    return DG_ERR_INVALID_ARG;
+  }
+  const int64_t rows = h->ncell;
+  const size_t bx = (size_t)rows * m->d.kinp * sizeof(__nv_bfloat16);
+  const size_t bytes = (bx + 255) / 256 * 256 + rows * sizeof(float);
+  // the preconditioner keeps its own buffer (not the training workspace, which may be larger)
+  if (int rc = ensure_ws(m, bytes)) return rc;
+  auto* X = static_cast<__nv_bfloat16*>(m->ws);
+  auto* scale = reinterpret_cast<float*>(static_cast<unsigned char*>(m->ws) + (bx + 255) / 256 * 256);
+  if (int rc = dg_mlp_features(m, h, r, precision, nullptr, rows, X, scale, stream)) return rc;
+  dgm::FwdArgs a = fwd_args(m, X, rows);
+  a.scale = scale;
+  a.z = z;
+  a.z_is_f64 = precision == DG_F64;
+  a.z_accumulate = accumulate;
+  return launch_forward(m, a, s);
+}
+
+extern "C" {
+
+int dg_mlp_save(const dg_mlp* m, const char* path) {
+  if (!m || !path) {
+    set_error("dg_mlp_save: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  std::vector<float> w(m->nparam), mm(m->nparam), vv(m->nparam);
+  int rc = cfail(cudaMemcpy(w.data(), m->w, m->nparam * sizeof(float), cudaMemcpyDeviceToHost), "save");
+  if (!rc) rc = cfail(cudaMemcpy(mm.data(), m->m, m->nparam * sizeof(float), cudaMemcpyDeviceToHost), "save");
+  if (!rc) rc = cfail(cudaMemcpy(vv.data(), m->v, m->nparam * sizeof(float), cudaMemcpyDeviceToHost), "save");
+  if (rc) return rc;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("dg_mlp_save: cannot open ") + path);
+    return DG_ERR_INVALID_ARG;
+  }
+  const char magic[8] = {'D', 'G', 'M', 'L', 'P', '0', '1', 0};
+  int64_t hdr[3] = {m->k, m->nparam, m->adam_t};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int64_t), 3, f) == 3 &&
+            std::fwrite(&m->t_scale, sizeof(float), 1, f) == 1 &&
+            std::fwrite(w.data(), sizeof(float), m->nparam, f) == (size_t)m->nparam &&
+            std::fwrite(mm.data(), sizeof(float), m->nparam, f) == (size_t)m->nparam &&
+            std::fwrite(vv.data(), sizeof(float), m->nparam, f) == (size_t)m->nparam;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    set_error("dg_mlp_save: write failed");
+    return DG_ERR_INVALID_ARG;
+  }
+  return DG_OK;
+}
+
+int dg_mlp_load(const char* path, dg_mlp** out) {
+  if (!path || !out) {
+    set_error("dg_mlp_load: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("dg_mlp_load: cannot open ") + path);
+    return DG_ERR_INVALID_ARG;
+  }
+  char magic[8];
+  int64_t hdr[3];
+  float ts = 1.f;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "DGMLP01", 8) == 0 &&
+            std::fread(hdr, sizeof(int64_t), 3, f) == 3 && std::fread(&ts, sizeof(float), 1, f) == 1;
+  dg_mlp* m = nullptr;
+  if (ok && dg_mlp_create((int32_t)hdr[0], 0, &m) == DG_OK && m->nparam == hdr[1]) {
+    std::vector<float> w(m->nparam), mm(m->nparam), vv(m->nparam);
+    ok = std::fread(w.data(), sizeof(float), m->nparam, f) == (size_t)m->nparam &&
+         std::fread(mm.data(), sizeof(float), m->nparam, f) == (size_t)m->nparam &&
+         std::fread(vv.data(), sizeof(float), m->nparam, f) == (size_t)m->nparam;
+    if (ok) {
+      ok = cudaMemcpy(m->w, w.data(), m->nparam * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(m->m, mm.data(), m->nparam * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(m->v, vv.data(), m->nparam * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+      if (ok) {
+        dgm::to_bf16<<<256, 256>>>(m->w, m->wh, m->nparam);
+        ok = cudaDeviceSynchronize() == cudaSuccess;
+      }
+      m->t_scale = ts;
+      m->adam_t = hdr[2];
+    }
+  } else {
+    ok = false;
+  }
+  std::fclose(f);
+  if (!ok) {
+    free_mlp(m);
+    set_error("dg_mlp_load: bad or truncated file");
+    return DG_ERR_INVALID_ARG;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+}  // extern "C"

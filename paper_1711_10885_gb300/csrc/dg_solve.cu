@@ -14,6 +14,10 @@
 
 namespace dgi {
 
+bool mlp_matches(const dg_mlp* m, const dg_handle* h);
+int mlp_apply_impl(dg_mlp* m, const dg_handle* h, const void* r, void* z, int32_t precision, int accumulate,
+                   cudaStream_t s);
+
 namespace {
 
 struct Ctx {
@@ -85,7 +89,9 @@ struct Result {
 // V: (m+1) n, Z: m n (ignored without M).  x holds the initial guess unless x0_zero.
 template <typename T>
 int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, bool x0_zero, T* V, T* Z, int m,
-           double tol_abs, int maxit, int max_cycles, bool true_residual_check, Result* out) {
+           double tol_abs, int maxit, int max_cycles, bool true_residual_check, Result* out,
+           const std::function<void(double, double)>& cycle_hook = {},
+           const std::function<int(const T*, T*)>& M0 = {}) {
   const size_t n = c.n;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hv(m + 2), h2(m + 2), y(m);
   Result r;
@@ -120,10 +126,16 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     bool est_conv = false;
     for (int j = 0; j < m; ++j) {
       T* vj = V + (size_t)j * n;
-      T* zj = M ? Z + (size_t)j * n : vj;
+      T* zj = (M || M0) ? Z + (size_t)j * n : vj;
       T* w = V + (size_t)(j + 1) * n;
-      if (M)
+      if (j == 0 && M0) {
+        if (int rc = M0(vj, zj)) return rc;
+      } else if (M) {
         if (int rc = M(vj, zj)) return rc;
+      } else if (M0) {
+        if (int rc = cuda_check(cudaMemcpyAsync(zj, vj, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s), "copy v"))
+          return rc;
+      }
       if (int rc = apply_A<T>(c, zj, w)) return rc;
       // classical Gram-Schmidt, twice
       if (int rc = dots<T>(c, V, j + 1, w, hv.data())) return rc;
@@ -176,9 +188,10 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     if (int rc = cuda_check(cudaMemcpyAsync(c.ydev, c.hhost, jend * sizeof(double), cudaMemcpyHostToDevice, c.s),
                             "y copy"))
       return rc;
-    const T* basis = M ? Z : V;
+    const T* basis = (M || M0) ? Z : V;
     dgb::lincomb_add<T, T><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(basis, n, jend, c.ydev, x, n);
     if (int rc = cuda_check(cudaStreamSynchronize(c.s), "solution update")) return rc;
+    if (cycle_hook) cycle_hook(beta, r.res);
     if (est_conv && !true_residual_check) {
       r.converged = true;
       break;
@@ -220,19 +233,38 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   const int m = o->restart > 0 ? o->restart : 30;
   const int mo = o->outer_restart > 0 ? o->outer_restart : 10;
   if (m > 60 || mo > 60 || (o->mode != DG_SOLVE_FP64 && o->mode != DG_SOLVE_MIXED) ||
-      (o->preconditioner != DG_PRECOND_NONE && o->preconditioner != DG_PRECOND_BLOCK_JACOBI) ||
+      (o->preconditioner != DG_PRECOND_NONE && o->preconditioner != DG_PRECOND_BLOCK_JACOBI &&
+       o->preconditioner != DG_PRECOND_MLP && o->preconditioner != DG_PRECOND_BJ_MLP) ||
       !(o->rtol > 0) || (o->mode == DG_SOLVE_MIXED && !(o->inner_rtol > 0 && o->inner_rtol < 1))) {
     set_error("dg_solve: bad options (restart <= 60, mode, preconditioner, rtol > 0, 0 < inner_rtol < 1)");
     return DG_ERR_INVALID_ARG;
   }
-  if (o->preconditioner == DG_PRECOND_BLOCK_JACOBI && !h->bj64) {
+  if ((o->preconditioner == DG_PRECOND_BLOCK_JACOBI || o->preconditioner == DG_PRECOND_BJ_MLP) && !h->bj64) {
     set_error("dg_solve: block-Jacobi requested but dg_precond_setup was not called");
+    return DG_ERR_INVALID_ARG;
+  }
+  if ((o->preconditioner == DG_PRECOND_MLP || o->preconditioner == DG_PRECOND_BJ_MLP) && !mlp_matches(o->mlp, h)) {
+    set_error("dg_solve: DG_PRECOND_MLP / DG_PRECOND_BJ_MLP need opts->mlp for the handle's degree");
     return DG_ERR_INVALID_ARG;
   }
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
-  const bool pc = o->preconditioner == DG_PRECOND_BLOCK_JACOBI;
+  const bool pc = o->preconditioner != DG_PRECOND_NONE;
+  // MLP preconditioner, with a switch to block-Jacobi when a cycle stagnates (if blocks exist)
+  bool use_mlp = o->preconditioner == DG_PRECOND_MLP || o->preconditioner == DG_PRECOND_BJ_MLP;
+  const bool with_bj = o->preconditioner == DG_PRECOND_BJ_MLP;
+  // placement 1: the network only acts on the first direction of each (outer) FGMRES cycle, where the
+  // direction is the true residual r / ||r|| -- the kind of input it was trained on
+  const bool first_only = use_mlp && o->mlp_placement == 1;
+  int fallback = 0;
+  dg_mlp* mlp = const_cast<dg_mlp*>(o->mlp);
+  auto maybe_fallback = [&](double start, double end) {
+    if (use_mlp && o->fallback_ratio > 0 && h->bj64 && start > 0 && end > o->fallback_ratio * start) {
+      use_mlp = false;
+      fallback = 1;
+    }
+  };
   // workspace: reductions, r/b copy, FP64 basis (V, Z), FP32 basis for the inner solve
   const size_t small = (size_t)dgb::RED_BLOCKS * 64 + 128;
   size_t v64 = 0, v32 = 0;
@@ -271,10 +303,26 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   Result res;
   int inner_total = 0;
   if (o->mode == DG_SOLVE_FP64) {
-    std::function<int(const double*, double*)> M;
-    if (pc) M = [&](const double* r, double* z) { return precond_bj_f64(h, r, z, s); };
+    std::function<int(const double*, double*)> M, M0;
+    if (pc && !first_only)
+      M = [&](const double* r, double* z) {
+        if (!use_mlp) return precond_bj_f64(h, r, z, s);
+        if (!with_bj) return mlp_apply_impl(mlp, h, r, z, DG_F64, 0, s);
+        int e2 = precond_bj_f64(h, r, z, s);
+        return e2 ? e2 : mlp_apply_impl(mlp, h, r, z, DG_F64, 1, s);
+      };
+    if (first_only) {
+      if (with_bj) M = [&](const double* r, double* z) { return precond_bj_f64(h, r, z, s); };
+      M0 = [&](const double* r, double* z) {
+        if (!use_mlp) return M ? M(r, z) : cuda_check(cudaMemcpyAsync(z, r, n * sizeof(double),
+                                                                      cudaMemcpyDeviceToDevice, s), "copy");
+        if (!with_bj) return mlp_apply_impl(mlp, h, r, z, DG_F64, 0, s);
+        int e2 = precond_bj_f64(h, r, z, s);
+        return e2 ? e2 : mlp_apply_impl(mlp, h, r, z, DG_F64, 1, s);
+      };
+    }
     rc = fgmres<double>(c, M, bcopy, x_dev, false, V64, V64 + (size_t)(m + 1) * n, m, tol, maxit, 1 << 20, true,
-                        &res);
+                        &res, maybe_fallback, M0);
     inner_total = res.iterations;
   } else {
     // inner FP32 FGMRES(m) on the FP32 operator, x0 = 0, one cycle or until inner_rtol: z = P(v)
@@ -283,7 +331,16 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     float* rhs32 = Z32 + (pc ? (size_t)m * n : 0);
     float* e32 = rhs32 + n;
     std::function<int(const float*, float*)> M32;
-    if (pc) M32 = [&](const float* r, float* z) { return precond_bj_f32(h, r, z, s); };
+    if (pc)
+      M32 = [&](const float* r, float* z) {
+        if (!use_mlp || first_only) return with_bj || !use_mlp ? precond_bj_f32(h, r, z, s)
+                                                             : cuda_check(cudaMemcpyAsync(z, r, n * sizeof(float),
+                                                                                          cudaMemcpyDeviceToDevice, s),
+                                                                          "copy");
+        if (!with_bj) return mlp_apply_impl(mlp, h, r, z, DG_F32, 0, s);
+        int e2 = precond_bj_f32(h, r, z, s);
+        return e2 ? e2 : mlp_apply_impl(mlp, h, r, z, DG_F32, 1, s);
+      };
     std::function<int(const double*, double*)> P = [&](const double* v, double* z) -> int {
       dgb::scale_copy<double, float><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, s>>>(v, rhs32, 1.0, n);
       cudaMemsetAsync(e32, 0, n * sizeof(float), s);
@@ -293,12 +350,20 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       if (rc2) return rc2;
       rc2 = fgmres<float>(c, M32, rhs32, e32, true, V32, Z32, m, o->inner_rtol * std::sqrt(vn2), m, 1, false, &ri);
       if (rc2) return rc2;
+      maybe_fallback(ri.beta0, ri.res);
       inner_total += ri.iterations;
       dgb::scale_copy<float, double><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, s>>>(e32, z, 1.0, n);
       return cuda_check(cudaGetLastError(), "inner solve casts");
     };
+    std::function<int(const double*, double*)> P0;
+    if (first_only)
+      P0 = [&](const double* v, double* z) -> int {
+        // the inner solve, plus the network's correction of the true residual direction
+        if (int rc2 = P(v, z)) return rc2;
+        return use_mlp ? mlp_apply_impl(mlp, h, v, z, DG_F64, 1, s) : 0;
+      };
     rc = fgmres<double>(c, P, bcopy, x_dev, false, V64, V64 + (size_t)(mo + 1) * n, mo, tol, maxit, 1 << 20, true,
-                        &res);
+                        &res, {}, P0);
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) {
@@ -309,6 +374,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     st->applies_f32 = c.applies32;
     st->rel_residual = res.res / (bnorm > 0 ? bnorm : 1.0);
     st->seconds = secs;
+    st->fallback = fallback;
   }
   if (rc) return rc;
   if (!res.converged) {

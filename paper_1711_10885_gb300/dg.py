@@ -47,18 +47,30 @@ DG_SOLVE_FP64 = 0
 DG_SOLVE_MIXED = 1
 DG_PRECOND_NONE = 0
 DG_PRECOND_BLOCK_JACOBI = 1
+DG_PRECOND_MLP = 2
+DG_PRECOND_BJ_MLP = 3
 
 
 class dg_solve_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("preconditioner", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("outer_restart", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("rtol", ctypes.c_double),
-                ("inner_rtol", ctypes.c_double)]
+                ("inner_rtol", ctypes.c_double), ("mlp", ctypes.c_void_p), ("mlp_placement", ctypes.c_int32),
+                ("fallback_ratio", ctypes.c_double)]
+
+
+class dg_mlp_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double)]
+
+
+class dg_mlp_train_stats(ctypes.Structure):
+    _fields_ = [("first_epoch_loss", ctypes.c_double), ("last_epoch_loss", ctypes.c_double),
+                ("steps", ctypes.c_int64)]
 
 
 class dg_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
                 ("applies_f64", ctypes.c_int32), ("applies_f32", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("fallback", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +101,21 @@ def _load():
     lib.dg_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, vp]
     lib.dg_batch_tuning.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
     lib.dg_batch_destroy.argtypes = [vp]
+    lib.dg_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(vp)]
+    lib.dg_mlp_destroy.argtypes = [vp]
+    lib.dg_mlp_dims.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int32)] * 4 + [ctypes.POINTER(ctypes.c_int64)]
+    lib.dg_mlp_params.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+    lib.dg_mlp_param_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.dg_mlp_set_target_scale.argtypes = [vp, ctypes.c_float]
+    lib.dg_mlp_features.argtypes = [vp, vp, vp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp]
+    lib.dg_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.dg_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp]
+    lib.dg_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(dg_mlp_train_opts),
+                                 ctypes.POINTER(dg_mlp_train_stats), vp]
+    lib.dg_mlp_apply.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp]
+    lib.dg_mlp_apply_add.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp]
+    lib.dg_mlp_save.argtypes = [vp, ctypes.c_char_p]
+    lib.dg_mlp_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
     return lib
 
 
@@ -98,7 +125,9 @@ lib = _load()
 EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadrature_points", "dg_apply_jacobian",
             "dg_apply_residual", "dg_rhs", "dg_last_error", "dg_apply_stage", "dg_precond_setup",
             "dg_precond_apply", "dg_solve", "dg_batch_create", "dg_batch_apply", "dg_batch_tuning",
-            "dg_batch_destroy"]
+            "dg_batch_destroy", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_dims", "dg_mlp_params",
+            "dg_mlp_param_offsets", "dg_mlp_set_target_scale", "dg_mlp_features", "dg_mlp_forward", "dg_mlp_loss_grad",
+            "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load"]
 
 
 def check(rc):
@@ -260,7 +289,8 @@ class Operator:
         return z
 
     def solve(self, x, b=None, mode=DG_SOLVE_FP64, preconditioner=DG_PRECOND_BLOCK_JACOBI, restart=30,
-              outer_restart=10, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True):
+              outer_restart=10, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True,
+              mlp=None, fallback_ratio=0.0, mlp_placement=0):
         """Solve A x = b (b = F when None) in place on the FP64 tensor x (dg_solve); returns the stats dict."""
         import torch
         if x.dtype != torch.float64:
@@ -268,7 +298,8 @@ class Operator:
         self._vec_check(x)
         if b is not None:
             self._vec_check(b)
-        o = dg_solve_opts(mode, preconditioner, restart, outer_restart, max_iterations, rtol, inner_rtol)
+        o = dg_solve_opts(mode, preconditioner, restart, outer_restart, max_iterations, rtol, inner_rtol,
+                          mlp.m.value if mlp is not None else None, int(mlp_placement), fallback_ratio)
         st = dg_solve_stats()
         rc = lib.dg_solve(self.h, ctypes.c_void_p(b.data_ptr()) if b is not None else None,
                           ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
@@ -285,6 +316,104 @@ class Operator:
         F = torch.empty(self.ndof, dtype=dtype, device="cuda")
         check(lib.dg_rhs(self.h, ctypes.c_void_p(F.data_ptr()), _prec(F), _stream_ptr(stream)))
         return F
+
+
+class MLP:
+    """Learned per-element preconditioner network (dg_mlp_*)."""
+
+    def __init__(self, k=None, seed=0, path=None):
+        m = ctypes.c_void_p()
+        if path is not None:
+            check(lib.dg_mlp_load(str(path).encode(), ctypes.byref(m)))
+        else:
+            check(lib.dg_mlp_create(int(k), int(seed), ctypes.byref(m)))
+        self.m = m
+        k_, kin, kinp, outp = (ctypes.c_int32() for _ in range(4))
+        npar = ctypes.c_int64()
+        check(lib.dg_mlp_dims(m, ctypes.byref(k_), ctypes.byref(kin), ctypes.byref(kinp), ctypes.byref(outp),
+                              ctypes.byref(npar)))
+        self.k, self.kin, self.kinp, self.outp, self.nparam = k_.value, kin.value, kinp.value, outp.value, npar.value
+        self.nb = (self.k + 1) ** 3
+        offs = (ctypes.c_int64 * 6)()
+        check(lib.dg_mlp_param_offsets(m, offs))
+        self.offsets = list(offs)
+
+    def close(self):
+        if getattr(self, "m", None):
+            lib.dg_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        ts = ctypes.c_float()
+        check(lib.dg_mlp_params(self.m, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0, ctypes.byref(ts)))
+        return out, ts.value
+
+    def set_params(self, p, t_scale=None):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        ts = ctypes.c_float(t_scale) if t_scale is not None else None
+        check(lib.dg_mlp_params(self.m, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1,
+                                ctypes.byref(ts) if ts is not None else None))
+
+    def grad(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        check(lib.dg_mlp_params(self.m, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 2, None))
+        return out
+
+    def set_target_scale(self, t):
+        check(lib.dg_mlp_set_target_scale(self.m, float(t)))
+
+    def features(self, op, r, cells=None, stream=None):
+        import torch
+        rows = op.ncell if cells is None else cells.numel()
+        X = torch.empty((rows, self.kinp), dtype=torch.bfloat16, device=r.device)
+        sc = torch.empty(rows, dtype=torch.float32, device=r.device)
+        cp = ctypes.c_void_p(cells.data_ptr()) if cells is not None else None
+        check(lib.dg_mlp_features(self.m, op.h, ctypes.c_void_p(r.data_ptr()), _prec(r), cp, rows,
+                                  ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(sc.data_ptr()), _stream_ptr(stream)))
+        return X, sc
+
+    def forward(self, X, stream=None):
+        import torch
+        Y = torch.empty((X.shape[0], self.outp), dtype=torch.float32, device=X.device)
+        check(lib.dg_mlp_forward(self.m, ctypes.c_void_p(X.data_ptr()), X.shape[0], ctypes.c_void_p(Y.data_ptr()),
+                                 _stream_ptr(stream)))
+        return Y
+
+    def loss_grad(self, X, T, stream=None):
+        loss = ctypes.c_double()
+        check(lib.dg_mlp_loss_grad(self.m, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()), X.shape[0],
+                                   ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def train(self, X, T, epochs=10, batch=256, lr=1e-3, stream=None):
+        o = dg_mlp_train_opts(int(epochs), int(batch), float(lr))
+        st = dg_mlp_train_stats()
+        check(lib.dg_mlp_train(self.m, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()), X.shape[0],
+                               ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream)))
+        return {"first_epoch_loss": st.first_epoch_loss, "last_epoch_loss": st.last_epoch_loss, "steps": st.steps}
+
+    def apply(self, op, r, z=None, stream=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        check(lib.dg_mlp_apply(self.m, op.h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()), _prec(r),
+                               _stream_ptr(stream)))
+        return z
+
+    def apply_add(self, op, r, z, stream=None):
+        check(lib.dg_mlp_apply_add(self.m, op.h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                   _prec(r), _stream_ptr(stream)))
+        return z
+
+    def save(self, path):
+        check(lib.dg_mlp_save(self.m, str(path).encode()))
 
 
 class Batch:

@@ -1,0 +1,178 @@
+"""GPU tests of the learned preconditioner: feature rows, forward pass and gradients against the FP64
+MLP reference (oracle/mlp.py), training, checkpointing, and what the trained network gains inside
+FGMRES over block-Jacobi alone, with the block-Jacobi fallback."""
+
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import mlp as om
+from paper_1711_10885_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_10885_gb300 import dg as _dg
+    return _dg
+
+
+def _random_params(mlp, rng):
+    p = np.zeros(mlp.nparam, dtype=np.float32)
+    o, H = mlp.offsets, 256
+    W1 = np.zeros((H, mlp.kinp), np.float32)
+    W1[:, :mlp.kin] = rng.standard_normal((H, mlp.kin)) / np.sqrt(mlp.kin)
+    W3 = np.zeros((mlp.outp, H), np.float32)
+    W3[:mlp.nb] = rng.standard_normal((mlp.nb, H)) / np.sqrt(H)
+    b3 = np.zeros(mlp.outp, np.float32)
+    b3[:mlp.nb] = rng.standard_normal(mlp.nb) * 0.1
+    p[o[0]:o[0] + W1.size] = W1.ravel()
+    p[o[1]:o[1] + H] = rng.standard_normal(H) * 0.1
+    p[o[2]:o[2] + H * H] = (rng.standard_normal((H, H)) / np.sqrt(H)).ravel()
+    p[o[3]:o[3] + H] = rng.standard_normal(H) * 0.1
+    p[o[4]:o[4] + W3.size] = W3.ravel()
+    p[o[5]:o[5] + mlp.outp] = b3
+    return p
+
+
+def _rows(mlp, rng, n):
+    X = np.zeros((n, mlp.kinp), np.float32)
+    X[:, :mlp.kin] = rng.standard_normal((n, mlp.kin))
+    return om.bf16_round(X)
+
+
+def test_feature_rows(dg):
+    w = inputs.small_case(n=(3, 4, 2), k=2, seed=3, sigma_D=1.5)
+    op = dg.operator_for(w)
+    mlp = dg.MLP(2, seed=1)
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(w.ndof)
+    r[:w.nb] = 0.0  # a cell with zero residual gives a zero row
+    X, s = mlp.features(op, torch.tensor(r, device="cuda"))
+    X = X.float().cpu().numpy()
+    s = s.cpu().numpy()
+    logD = np.log(w.D)
+    nx, ny, nz = w.n
+    for c in range(w.ncell):
+        ic = [c % nx, (c // nx) % ny, c // (nx * ny)]
+        nbr = [c]
+        for d, st, nn in ((0, 1, nx), (1, nx, ny), (2, nx * ny, nz)):
+            nbr.append(c - st if ic[d] > 0 else c)
+            nbr.append(c + st if ic[d] < nn - 1 else c)
+        row, sr = om.features(r[c * w.nb:(c + 1) * w.nb], logD[nbr], mlp.kinp)
+        assert abs(s[c] - sr) <= 1e-6 * max(sr, 1e-30)
+        ref = om.bf16_round(row)
+        assert np.max(np.abs(X[c] - ref)) <= 2 ** -7 * np.max(np.abs(ref)), c
+    op.close()
+    mlp.close()
+
+
+@pytest.mark.parametrize("k,rows", [(4, 300), (2, 77), (7, 65)])
+def test_forward_matches_oracle(dg, k, rows):
+    rng = np.random.default_rng(k)
+    mlp = dg.MLP(k, seed=0)
+    p = _random_params(mlp, rng)
+    mlp.set_params(p)
+    X = _rows(mlp, rng, rows)
+    Y = mlp.forward(torch.tensor(X, dtype=torch.bfloat16, device="cuda")).cpu().numpy()
+    W = om.unpack(p, mlp.offsets, mlp.kinp, mlp.outp)
+    y_ref, _, _ = om.forward(X, *W, bf16_hidden=True)
+    err = np.linalg.norm(Y[:, :mlp.nb] - y_ref[:, :mlp.nb]) / np.linalg.norm(y_ref[:, :mlp.nb])
+    assert err <= 2e-3, err
+    mlp.close()
+
+
+def test_gradient_matches_oracle(dg):
+    rng = np.random.default_rng(7)
+    mlp = dg.MLP(4, seed=0)
+    p = _random_params(mlp, rng)
+    mlp.set_params(p)
+    X = _rows(mlp, rng, 200)
+    T = rng.standard_normal((200, mlp.nb)).astype(np.float32)
+    loss = mlp.loss_grad(torch.tensor(X, dtype=torch.bfloat16, device="cuda"), torch.tensor(T, device="cuda"))
+    g = mlp.grad()
+    W = om.unpack(p, mlp.offsets, mlp.kinp, mlp.outp)
+    loss_ref, g_ref = om.loss_and_grad(X, T, *W, nb=mlp.nb, bf16_hidden=True)
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref
+    gW = om.unpack(g, mlp.offsets, mlp.kinp, mlp.outp)
+    for name, a, b in zip(["W1", "b1", "W2", "b2", "W3", "b3"], gW, g_ref):
+        err = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert err <= 2e-2, (name, err)
+    mlp.close()
+
+
+def test_training_reduces_loss_and_checkpoint_round_trips(dg):
+    rng = np.random.default_rng(11)
+    mlp = dg.MLP(3, seed=2)
+    X = _rows(mlp, rng, 2048)
+    A = rng.standard_normal((mlp.nb, mlp.kin)) / np.sqrt(mlp.kin)
+    T = np.tanh(X[:, :mlp.kin] @ A.T).astype(np.float32)
+    Xt = torch.tensor(X, dtype=torch.bfloat16, device="cuda")
+    st = mlp.train(Xt, torch.tensor(T, device="cuda"), epochs=15, batch=128, lr=2e-3)
+    assert st["last_epoch_loss"] < 0.3 * st["first_epoch_loss"], st
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "net.bin")
+        mlp.save(path)
+        m2 = dg.MLP(path=path)
+        p1, t1 = mlp.params()
+        p2, t2 = m2.params()
+        assert np.array_equal(p1, p2) and t1 == t2
+        assert torch.equal(mlp.forward(Xt), m2.forward(Xt))
+        m2.close()
+    mlp.close()
+
+
+def test_preconditioner_apply_is_scaled_forward(dg):
+    w = inputs.small_case(n=(4, 3, 3), k=4, seed=9)
+    op = dg.operator_for(w)
+    mlp = dg.MLP(4, seed=3)
+    mlp.set_target_scale(2.5)
+    r = torch.randn(w.ndof, dtype=torch.float64, device="cuda")
+    z = mlp.apply(op, r)
+    X, s = mlp.features(op, r)
+    Y = mlp.forward(X)
+    ref = (Y[:, :w.nb] * s[:, None]).double().reshape(-1)
+    assert torch.allclose(z, ref, rtol=1e-6, atol=0)
+    z32 = mlp.apply(op, r.float())
+    assert torch.max(torch.abs(z32.double() - z)).item() <= 1e-2 * torch.max(torch.abs(z)).item()
+    op.close()
+    mlp.close()
+
+
+def test_learned_preconditioner_gain_and_fallback(dg):
+    """FGMRES(30) in FP64 with block-Jacobi stalls on this problem; the network trained on the solver's own
+    (residual, error) pairs, used on the first direction of every cycle (whose input is a true residual),
+    gives a residual more than 3 times smaller after the same 1500 iterations (measured: 0.12 against
+    0.94; after 3000 iterations 1e-5 against 0.94)."""
+    from paper_1711_10885_gb300 import learned
+    train = [inputs.small_case(n=(16, 16, 16), k=4, seed=s, sigma_D=1.5) for s in (10, 11)]
+    mlp, info = learned.train_preconditioner(train, 4, pairs=8000, epochs=40, batch=256, lr=1e-3, seed=0,
+                                             minus_block_jacobi=False)
+    assert info["last_epoch_loss"] < 0.5 * info["first_epoch_loss"], info
+    w = inputs.small_case(n=(16, 16, 16), k=4, seed=20, sigma_D=1.5)
+    op = dg.operator_for(w)
+    op.precond_setup()
+    res = {}
+    for name, pc in (("bj", dg.DG_PRECOND_BLOCK_JACOBI), ("learned", dg.DG_PRECOND_BJ_MLP)):
+        x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+        res[name] = op.solve(x, mode=dg.DG_SOLVE_FP64, preconditioner=pc, mlp=mlp, mlp_placement=1, rtol=1e-8,
+                             max_iterations=1500, raise_on_error=False)
+    assert res["learned"]["rel_residual"] <= 0.3 * res["bj"]["rel_residual"], res
+    # mixed precision with the learned first direction converges to the tolerance
+    x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    st = op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BJ_MLP, mlp=mlp, mlp_placement=1,
+                  rtol=1e-8, inner_rtol=1e-2)
+    assert st["rel_residual"] <= 1e-8
+    # the network alone in every application stagnates; the stagnation test switches to block-Jacobi
+    x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    st = op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_MLP, mlp=mlp, rtol=1e-8,
+                  inner_rtol=1e-2, fallback_ratio=0.5)
+    assert st["fallback"] == 1 and st["rel_residual"] <= 1e-8
+    mlp.close()
+    op.close()
