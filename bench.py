@@ -275,6 +275,51 @@ def batch_benchmark(reps=20):
     return out
 
 
+def learned_benchmark(rtol=1e-8, fp64_cap_s=60.0, pairs=20000, epochs=60):
+    """Learned preconditioner at 64^3 Q4 (32.8M DOF, sigma 1.5, seed 20), trained on four 32^3 Q4 meshes
+    (seeds 10..13): time to rtol for plain FP64 block-Jacobi FGMRES(30) (capped), the same with the learned
+    first direction per cycle, and the mixed-precision solve with and without it."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, inputs, learned
+    train = [inputs.Workload(f"train{s}", (32, 32, 32), 4, inputs.log_normal_D(32 ** 3, 1.5, s)) for s in
+             (10, 11, 12, 13)]
+    t0 = time.perf_counter()
+    mlp, info = learned.train_preconditioner(train, 4, pairs=pairs, epochs=epochs, batch=256, lr=1e-3, seed=0,
+                                             minus_block_jacobi=False)
+    torch.cuda.synchronize()
+    info["train_s"] = time.perf_counter() - t0
+    ev = inputs.Workload("eval", (64, 64, 64), 4, inputs.log_normal_D(64 ** 3, 1.5, 20))
+    op = dg.operator_for(ev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op.precond_setup()
+    torch.cuda.synchronize()
+    out = {"workload": "64^3 Q4, D log-normal sigma 1.5", "dofs": ev.ndof, "rtol": rtol, "mlp": info,
+           "precond_setup_s": time.perf_counter() - t0}
+    # FP64 iteration rate, to cap the plain FP64 solve at about fp64_cap_s seconds
+    x = torch.zeros(ev.ndof, dtype=torch.float64, device="cuda")
+    st = op.solve(x, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=rtol, max_iterations=30,
+                  raise_on_error=False)
+    cap = max(30, int(fp64_cap_s / (st["seconds"] / 30)))
+    runs = (("fp64_bj", dg.DG_SOLVE_FP64, dg.DG_PRECOND_BLOCK_JACOBI, cap),
+            ("fp64_bj_learned", dg.DG_SOLVE_FP64, dg.DG_PRECOND_BJ_MLP, cap),
+            ("mixed_bj", dg.DG_SOLVE_MIXED, dg.DG_PRECOND_BLOCK_JACOBI, 0),
+            ("mixed_bj_learned", dg.DG_SOLVE_MIXED, dg.DG_PRECOND_BJ_MLP, 0))
+    for name, mode, pc, maxit in runs:
+        x = torch.zeros(ev.ndof, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.solve(x, mode=mode, preconditioner=pc, mlp=mlp, mlp_placement=1, rtol=rtol, inner_rtol=1e-2,
+                      max_iterations=maxit, raise_on_error=False)
+        torch.cuda.synchronize()
+        st["wall_s"] = time.perf_counter() - t0
+        out[name] = st
+    mlp.close()
+    op.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -419,7 +464,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
-    ap.add_argument("--solve-only", action="store_true", help="print the mixed vs FP64 solve comparison only")
+    ap.add_argument("--solve-only", nargs="?", const="all", default=None, choices=["all", "mixed", "learned"],
+                    help="print the solver comparisons only (mixed precision at 48^3 Q5, learned at 64^3 Q4)")
     ap.add_argument("--profile", action="store_true",
                     help="only run warmup + steps residual applies (for ncu launch lists and captures)")
     args = ap.parse_args()
@@ -432,7 +478,10 @@ def main():
     elif args.solve_only:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps(solve_benchmark()), flush=True)
+        if args.solve_only in ("all", "mixed"):
+            print(json.dumps({"mixed_precision_q5_48": solve_benchmark()}), flush=True)
+        if args.solve_only in ("all", "learned"):
+            print(json.dumps({"learned_q4_64": learned_benchmark()}), flush=True)
     else:
         run_ours(args)
 

@@ -29,8 +29,10 @@ def solver_pairs(workloads, mlp, pairs_per_problem, snapshots=(0, 3, 8, 16, 32, 
         op = dg.operator_for(w)
         op.precond_setup()
         xstar = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
-        op.solve(xstar, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=1e-11,
-                 inner_rtol=1e-3)
+        # the reference solution only has to be accurate relative to the errors of the early iterates;
+        # 1e-9 stays above the attainable FP64 residual of high-contrast problems
+        op.solve(xstar, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=1e-9,
+                 inner_rtol=1e-3, max_iterations=2000, raise_on_error=False)
         x = torch.zeros_like(xstar)
         done = 0
         for target in snapshots:
