@@ -396,7 +396,8 @@ def run_ours(args):
 
     # other precisions / operations of the same path, reported alongside
     extra = {}
-    for name, fn, x in (("jacobian_f64", op.apply_jacobian, u), ("residual_f32", op.apply_residual, u.float())):
+    for name, fn, x in (("jacobian_f64", op.apply_jacobian, u), ("residual_f32", op.apply_residual, u.float()),
+                        ("residual_f64x", lambda a_, b_: op.apply_residual(a_, b_, precision=dg.DG_F64X), u)):
         y = torch.empty_like(x)
         for _ in range(3):
             fn(x, y)

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "dg_dfloat.cuh"
 #include "dg_internal.h"
 
 namespace dgi {
@@ -135,6 +136,7 @@ int dg_destroy(dg_handle* h) {
   if (!h) return DG_OK;
   free_buffers(h->p64);
   free_buffers(h->p32);
+  free_buffers(h->pX);
   cudaFree(h->work_V);
   cudaFree(h->work_tr);
   cudaFree(h->bj64);
@@ -250,6 +252,9 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
       }
   }
   std::vector<float> D32(D.begin(), D.end()), fc32(fc.begin(), fc.end());
+  std::vector<dgk::dfl> DX(D.size()), fcX(fc.size());
+  for (size_t i = 0; i < D.size(); ++i) DX[i] = dgk::dfl(D[i]);
+  for (size_t i = 0; i < fc.size(); ++i) fcX[i] = dgk::dfl(fc[i]);
 
   int rc = DG_OK;
   cudaError_t e = cudaSuccess;
@@ -267,6 +272,8 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
     DG_TRY(cudaMalloc(&h->p32.D, ncell * sizeof(float)), "cudaMalloc(D32)");
     DG_TRY(cudaMalloc(&h->p64.fc, ncell * 18 * sizeof(double)), "cudaMalloc(fc)");
     DG_TRY(cudaMalloc(&h->p32.fc, ncell * 18 * sizeof(float)), "cudaMalloc(fc32)");
+    DG_TRY(cudaMalloc(&h->pX.D, ncell * sizeof(dgk::dfl)), "cudaMalloc(D pairs)");
+    DG_TRY(cudaMalloc(&h->pX.fc, ncell * 18 * sizeof(dgk::dfl)), "cudaMalloc(fc pairs)");
     DG_TRY(cudaMalloc(&h->p64.F, ndof * sizeof(double)), "cudaMalloc(F)");
     DG_TRY(cudaMalloc(&h->p32.F, ndof * sizeof(float)), "cudaMalloc(F32)");
     DG_TRY(cudaMalloc(&h->work_V, ndof * sizeof(double)), "cudaMalloc(work V)");
@@ -276,6 +283,9 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
     DG_TRY(cudaMemcpyAsync(h->p64.fc, fc.data(), ncell * 18 * sizeof(double), cudaMemcpyHostToDevice, s), "copy fc");
     DG_TRY(cudaMemcpyAsync(h->p32.fc, fc32.data(), ncell * 18 * sizeof(float), cudaMemcpyHostToDevice, s),
            "copy fc32");
+    DG_TRY(cudaMemcpyAsync(h->pX.D, DX.data(), ncell * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s), "copy D pairs");
+    DG_TRY(cudaMemcpyAsync(h->pX.fc, fcX.data(), ncell * 18 * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s),
+           "copy fc pairs");
     // right hand side: f at the volume points goes through the work buffer
     if (f_qp) {
       DG_TRY(cudaMemcpyAsync(h->work_V, f_qp, ndof * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
@@ -362,8 +372,8 @@ static int check_apply(dg_handle* h, const void* in, void* out, int32_t precisio
     set_error(std::string(name) + ": input and output must not alias");
     return DG_ERR_INVALID_ARG;
   }
-  if (precision != DG_F64 && precision != DG_F32) {
-    set_error(std::string(name) + ": precision must be DG_F64 or DG_F32");
+  if (precision != DG_F64 && precision != DG_F32 && precision != DG_F64X) {
+    set_error(std::string(name) + ": precision must be DG_F64, DG_F32 or DG_F64X");
     return DG_ERR_INVALID_ARG;
   }
   int dev = -1;
@@ -380,6 +390,8 @@ int dg_apply_jacobian(dg_handle* h, const void* z, void* y, int32_t precision, v
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == DG_F64)
     return launch_apply_f64(h, static_cast<const double*>(z), static_cast<double*>(y), 0, 3, s);
+  if (precision == DG_F64X)
+    return launch_apply_f64x(h, static_cast<const double*>(z), static_cast<double*>(y), 0, 3, s);
   return launch_apply_f32(h, static_cast<const float*>(z), static_cast<float*>(y), 0, 3, s);
 }
 
@@ -388,6 +400,8 @@ int dg_apply_residual(dg_handle* h, const void* u, void* r, int32_t precision, v
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == DG_F64)
     return launch_apply_f64(h, static_cast<const double*>(u), static_cast<double*>(r), 1, 3, s);
+  if (precision == DG_F64X)
+    return launch_apply_f64x(h, static_cast<const double*>(u), static_cast<double*>(r), 1, 3, s);
   return launch_apply_f32(h, static_cast<const float*>(u), static_cast<float*>(r), 1, 3, s);
 }
 
@@ -405,6 +419,8 @@ int dg_apply_stage(dg_handle* h, int32_t stage, const void* in, void* out, int32
   const int mode = residual ? 1 : 0, stages = stage == 0 ? 1 : 2;
   if (precision == DG_F64)
     return launch_apply_f64(h, static_cast<const double*>(in), static_cast<double*>(out), mode, stages, s);
+  if (precision == DG_F64X)
+    return launch_apply_f64x(h, static_cast<const double*>(in), static_cast<double*>(out), mode, stages, s);
   return launch_apply_f32(h, static_cast<const float*>(in), static_cast<float*>(out), mode, stages, s);
 }
 

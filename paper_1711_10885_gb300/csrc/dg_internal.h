@@ -38,6 +38,7 @@ struct dg_handle {
   double c = 0, sigma = 0;
   dgi::Tables1D tab;
   dgi::Buffers p64, p32;   // FP64 and FP32 copies of the coefficient data
+  dgi::Buffers pX;         // double-float copies (D and face coefficients; F is read from p64)
   void* work_V = nullptr;  // point-space residual scratch [ncell][N^3] (sized for FP64)
   void* work_tr = nullptr; // face trace scratch [ncell][6][2][N^2] (sized for FP64)
   int device = 0;
@@ -60,6 +61,8 @@ int cuda_fail(cudaError_t e, const char* what);
 // mode 0: y = A z, mode 1: y = A z - F; stages: bit 0 cell kernel, bit 1 face kernel (3 = full apply)
 int launch_apply_f64(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s);
 int launch_apply_f32(const dg_handle* h, const float* z, float* y, int mode, int stages, cudaStream_t s);
+// FP64 vectors, operator evaluated in double-float arithmetic (pairs of FP32)
+int launch_apply_f64x(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s);
 int launch_diag_blocks_f64(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr,
                            cudaStream_t s);
 // block-Jacobi application z = M r (precision by type), M from dg_precond_setup

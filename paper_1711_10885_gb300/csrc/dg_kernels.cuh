@@ -34,6 +34,8 @@
 
 #include <cuda_runtime.h>
 
+#include "dg_dfloat.cuh"
+
 namespace dgk {
 
 // 1D tables for n = m = N (Sec. 3.1), in even-odd form.  H = floor(N/2) point pairs, C = ceil(N/2).
@@ -194,15 +196,16 @@ struct Launch {
 };
 
 // copy cpb cells (contiguous in global memory, N^3 each) into padded shared buffers
-template <int N, typename T>
-__device__ __forceinline__ void gload_cells(T* sbuf, const T* __restrict__ g, int cell0, int ncells_here) {
+// (TV: element type of the vector in global memory, converted to the compute type T on load)
+template <int N, typename T, typename TV>
+__device__ __forceinline__ void gload_cells(T* sbuf, const TV* __restrict__ g, int cell0, int ncells_here) {
   constexpr int N3 = N * N * N;
   const int total = ncells_here * N3;
-  const T* src = g + (size_t)cell0 * N3;
+  const TV* src = g + (size_t)cell0 * N3;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int c = e / N3, r = e - c * N3;
     const int i1 = r % N, i23 = r / N;
-    sbuf[c * Lay<N>::CS + i1 + Lay<N>::LS * i23] = src[e];
+    sbuf[c * Lay<N>::CS + i1 + Lay<N>::LS * i23] = T(src[e]);
   }
 }
 template <int N, typename T>
@@ -269,8 +272,8 @@ struct SelfArgs {
 
 // Cell-kernel work on one tile of `here` consecutive cells starting at cell0 (virtual cells in SELF mode),
 // run by all threads of the CTA (blockDim.x >= CPB * N^2; threads beyond that only help with copies).
-template <int N, typename T, bool SELF, int CPB>
-__device__ __forceinline__ void cell_tile(const Tab<N, T>& tb, const Geo<T>& g, const T* __restrict__ z,
+template <int N, typename T, bool SELF, int CPB, typename TV = T>
+__device__ __forceinline__ void cell_tile(const Tab<N, T>& tb, const Geo<T>& g, const TV* __restrict__ z,
                                           const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces,
                                           int cell0, int here, int cell_base, unsigned char* smem_raw) {
   constexpr int NN = N * N, N3 = N * N * N, CS = Lay<N>::CS;
@@ -340,14 +343,14 @@ __device__ __forceinline__ void cell_tile(const Tab<N, T>& tb, const Geo<T>& g, 
   gstore_cells<N>(Vout, sV, cell0, here);
 }
 
-template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB>
+template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T>
 __global__ void __launch_bounds__(CPB * N * N)
-dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g, const T* __restrict__ z,
+dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g, const TV* __restrict__ z,
                const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
-  cell_tile<N, T, SELF, CPB>(tb, g, z, Dcell, Vout, traces, cell0, here, sa_.cell_base, smem_raw);
+  cell_tile<N, T, SELF, CPB, TV>(tb, g, z, Dcell, Vout, traces, cell0, here, sa_.cell_base, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -356,22 +359,22 @@ dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo
 //                                   boundary: (D_own / h, 0, gamma_F)
 // mode 0: y = A z;  mode 1: y = A z - F;  mode 2 (right hand side): V from f, faces from g
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename TV = T>
 struct FaceArgs {
   const T* V;       // point-space residual from dg_cell_kernel (mode 0/1), or f at points (mode 2)
   const T* traces;  // traces from dg_cell_kernel (mode 0/1)
   const T* fc;      // face coefficients
-  const T* F;       // right hand side (mode 1)
+  const TV* F;      // right hand side (mode 1)
   const T* g[6];    // Dirichlet data per boundary side (mode 2), may be null
-  T* y;
+  TV* y;            // output vector (element type TV)
   int mode;
 };
 
 // face test weights of this thread's face point on face (dir, s): value weight Vf and normal-derivative
 // weight Wf (eq. blf: interior upwind, consistency, symmetry and penalty terms, or the Dirichlet terms;
 // mode 2: the Dirichlet terms of l_h)
-template <int N, typename T, bool SELF>
-__device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>& fa, int cell, int tcell,
+template <int N, typename T, bool SELF, typename TV>
+__device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, TV>& fa, int cell, int tcell,
                                              const int (&ic)[3], int dir, int s, int t, T wf, T& Vf, T& Wf) {
   constexpr int NN = N * N;
   const int face = 2 * dir + s;
@@ -427,8 +430,8 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T>&
 }
 
 // Face-kernel work on one tile of `here` consecutive cells starting at cell0 (see cell_tile).
-template <int N, typename T, bool SELF, int CPB>
-__device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, const FaceArgs<T>& fa, int cell0,
+template <int N, typename T, bool SELF, int CPB, typename TV = T>
+__device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, const FaceArgs<T, TV>& fa, int cell0,
                                           int here, int cell_base, unsigned char* smem_raw) {
   constexpr int NN = N * N, N3 = N * N * N, CS = Lay<N>::CS;
   T* sV = reinterpret_cast<T*>(smem_raw);
@@ -466,7 +469,7 @@ __device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, 
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         T Vf, Wf;
-        face_weights<N, T, SELF>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf, Wf);
+        face_weights<N, T, SELF, TV>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf, Wf);
 #pragma unroll
         for (int l = 0; l < N; ++l) v[l] = fma(tb.L[s][l], Vf, fma(tb.P[s][l], Wf, v[l]));
       }
@@ -496,25 +499,25 @@ __device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, 
   }
   // write out (minus F for the residual)
   const int total = here * N3;
-  T* dst = fa.y + (size_t)cell0 * N3;
-  const T* Fs = fa.F ? fa.F + (size_t)cell0 * N3 : nullptr;
+  TV* dst = fa.y + (size_t)cell0 * N3;
+  const TV* Fs = fa.F ? fa.F + (size_t)cell0 * N3 : nullptr;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int c = e / N3, r = e - c * N3;
     const int i1 = r % N, i23 = r / N;
     T val = sV[c * CS + i1 + Lay<N>::LS * i23];
-    if (fa.mode == 1) val -= Fs[e];
-    dst[e] = val;
+    if (fa.mode == 1) val = val - T(Fs[e]);
+    dst[e] = static_cast<TV>(val);
   }
 }
 
-template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB>
+template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T>
 __global__ void __launch_bounds__(CPB * N * N)
 dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g,
-               const __grid_constant__ FaceArgs<T> fa, SelfArgs sa_) {
+               const __grid_constant__ FaceArgs<T, TV> fa, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
-  face_tile<N, T, SELF, CPB>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
+  face_tile<N, T, SELF, CPB, TV>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
 }
 
 }  // namespace dgk

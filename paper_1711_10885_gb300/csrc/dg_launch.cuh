@@ -71,21 +71,30 @@ size_t face_smem() {
   return (size_t)dgk::Launch<N>::CPB * dgk::Lay<N>::CS * sizeof(T);
 }
 
-template <int N, typename T>
+template <int N, typename T, typename TV = T>
 int set_smem_attrs() {
-  static bool done = false;  // per (N, T) instantiation; attributes are per function
+  static bool done = false;  // per instantiation; attributes are per function
   if (done) return 0;
-  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)cell_smem<N, T>());
+  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T, false, dgk::Launch<N>::CPB, TV>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<N, T>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel)");
-  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)face_smem<N, T>());
+  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T, false, dgk::Launch<N>::CPB, TV>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<N, T>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
   done = true;
   return 0;
 }
 
-// stages: bit 0 = cell kernel (z -> work buffers), bit 1 = face kernel (work buffers -> y)
+// coefficient copies in the compute precision
+template <typename T>
+const Buffers& buffers_for(const dg_handle* h);
+template <>
+inline const Buffers& buffers_for<double>(const dg_handle* h) { return h->p64; }
+template <>
+inline const Buffers& buffers_for<float>(const dg_handle* h) { return h->p32; }
+template <>
+inline const Buffers& buffers_for<dgk::dfl>(const dg_handle* h) { return h->pX; }
+
 template <int N>
 int set_self_smem_attrs() {
   static bool done = false;
@@ -100,10 +109,12 @@ int set_self_smem_attrs() {
   return 0;
 }
 
-template <int N, typename T>
-int apply_n(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStream_t s) {
-  if (int rc = set_smem_attrs<N, T>()) return rc;
-  const Buffers& bf = sizeof(T) == 8 ? h->p64 : h->p32;
+template <int N, typename T, typename TV = T>
+int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s) {
+  if (int rc = set_smem_attrs<N, T, TV>()) return rc;
+  const Buffers& bf = buffers_for<T>(h);
+  // the right hand side is kept in the vector precision (FP64 for the double-float path)
+  const Buffers& bfv = sizeof(TV) == 8 ? h->p64 : h->p32;
   const auto tb = make_tab<N, T>(h->tab);
   const auto geo = make_geo<T>(h);
   const int cpb = dgk::Launch<N>::CPB;
@@ -111,19 +122,19 @@ int apply_n(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStre
   T* V = static_cast<T*>(h->work_V);
   T* tr = static_cast<T*>(h->work_tr);
   if (stages & 1)
-    dgk::dg_cell_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, cell_smem<N, T>(), s>>>(
+    dgk::dg_cell_kernel<N, T, false, dgk::Launch<N>::CPB, TV><<<grid, dgk::Launch<N>::THREADS, cell_smem<N, T>(), s>>>(
         tb, geo, z, static_cast<const T*>(bf.D), V, tr, dgk::SelfArgs{0, 0});
-  dgk::FaceArgs<T> fa;
+  dgk::FaceArgs<T, TV> fa;
   fa.V = V;
   fa.traces = tr;
   fa.fc = static_cast<const T*>(bf.fc);
-  fa.F = mode == 1 ? static_cast<const T*>(bf.F) : nullptr;
+  fa.F = mode == 1 ? static_cast<const TV*>(bfv.F) : nullptr;
   for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
   fa.y = y;
   fa.mode = mode;
   if (stages & 2)
-    dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa,
-                                                                                      dgk::SelfArgs{0, 0});
+    dgk::dg_face_kernel<N, T, false, dgk::Launch<N>::CPB, TV>
+        <<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");
   return 0;
@@ -166,7 +177,7 @@ int diag_blocks_n(const dg_handle* h, double* out, int cell_base, int ncells, do
   const unsigned grid = (unsigned)((nvirt + cpb - 1) / cpb);
   const dgk::SelfArgs sa{nvirt, cell_base};
   dgk::dg_cell_kernel<N, double, true><<<grid, dgk::Launch<N>::THREADS, cell_smem<N, double>(), s>>>(
-      tb, geo, nullptr, static_cast<const double*>(h->p64.D), V, tr, sa);
+      tb, geo, static_cast<const double*>(nullptr), static_cast<const double*>(h->p64.D), V, tr, sa);
   dgk::FaceArgs<double> fa;
   fa.V = V;
   fa.traces = tr;
@@ -199,19 +210,19 @@ inline int diag_blocks_dispatch(const dg_handle* h, double* out, int cell_base, 
   }
 }
 
-template <typename T>
-int apply_dispatch(const dg_handle* h, const T* z, T* y, int mode, int stages, cudaStream_t s) {
+template <typename T, typename TV = T>
+int apply_dispatch(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s) {
   switch (h->N) {
-    case 2: return apply_n<2, T>(h, z, y, mode, stages, s);
-    case 3: return apply_n<3, T>(h, z, y, mode, stages, s);
-    case 4: return apply_n<4, T>(h, z, y, mode, stages, s);
-    case 5: return apply_n<5, T>(h, z, y, mode, stages, s);
-    case 6: return apply_n<6, T>(h, z, y, mode, stages, s);
-    case 7: return apply_n<7, T>(h, z, y, mode, stages, s);
-    case 8: return apply_n<8, T>(h, z, y, mode, stages, s);
-    case 9: return apply_n<9, T>(h, z, y, mode, stages, s);
-    case 10: return apply_n<10, T>(h, z, y, mode, stages, s);
-    case 11: return apply_n<11, T>(h, z, y, mode, stages, s);
+    case 2: return apply_n<2, T, TV>(h, z, y, mode, stages, s);
+    case 3: return apply_n<3, T, TV>(h, z, y, mode, stages, s);
+    case 4: return apply_n<4, T, TV>(h, z, y, mode, stages, s);
+    case 5: return apply_n<5, T, TV>(h, z, y, mode, stages, s);
+    case 6: return apply_n<6, T, TV>(h, z, y, mode, stages, s);
+    case 7: return apply_n<7, T, TV>(h, z, y, mode, stages, s);
+    case 8: return apply_n<8, T, TV>(h, z, y, mode, stages, s);
+    case 9: return apply_n<9, T, TV>(h, z, y, mode, stages, s);
+    case 10: return apply_n<10, T, TV>(h, z, y, mode, stages, s);
+    case 11: return apply_n<11, T, TV>(h, z, y, mode, stages, s);
     default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
   }
 }

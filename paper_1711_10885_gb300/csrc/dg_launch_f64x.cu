@@ -1,0 +1,9 @@
+// Double-float instantiations of the operator kernels (degrees 1..10): FP64 vectors in and out, every
+// operation on pairs of FP32 numbers (about 48 significand bits) so that the work runs on the FP32 pipes.
+#include "dg_launch.cuh"
+
+namespace dgi {
+int launch_apply_f64x(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s) {
+  return apply_dispatch<dgk::dfl, double>(h, z, y, mode, stages, s);
+}
+}  // namespace dgi

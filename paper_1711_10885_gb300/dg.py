@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libdg.so")
 DG_OK = 0
 DG_F64 = 0
 DG_F32 = 1
+DG_F64X = 2  # FP64 vectors, double-float arithmetic on the FP32 pipes
 DG_MAX_DEGREE = 10
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -243,19 +244,27 @@ class Operator:
             if not t.is_cuda or not t.is_contiguous() or t.numel() != self.ndof:
                 raise ValueError("vectors must be contiguous CUDA tensors with ndof entries")
 
-    def apply_jacobian(self, z, y=None, stream=None):
-        """y = A z (dg_apply_jacobian)."""
+    def _precision(self, t, precision):
+        p = _prec(t)
+        if precision is None:
+            return p
+        if precision == DG_F64X and p != DG_F64:
+            raise TypeError("DG_F64X takes float64 vectors")
+        return int(precision)
+
+    def apply_jacobian(self, z, y=None, stream=None, precision=None):
+        """y = A z (dg_apply_jacobian); precision DG_F64X evaluates FP64 vectors in double-float."""
         import torch
         if y is None:
             y = torch.empty_like(z)
         self._vec_check(z, y)
         if z.dtype != y.dtype:
             raise TypeError("z and y must have the same dtype")
-        check(lib.dg_apply_jacobian(self.h, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(y.data_ptr()), _prec(z),
-                                    _stream_ptr(stream)))
+        check(lib.dg_apply_jacobian(self.h, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    self._precision(z, precision), _stream_ptr(stream)))
         return y
 
-    def apply_residual(self, u, r=None, stream=None):
+    def apply_residual(self, u, r=None, stream=None, precision=None):
         """r = A u - F (dg_apply_residual)."""
         import torch
         if r is None:
@@ -263,15 +272,15 @@ class Operator:
         self._vec_check(u, r)
         if u.dtype != r.dtype:
             raise TypeError("u and r must have the same dtype")
-        check(lib.dg_apply_residual(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(r.data_ptr()), _prec(u),
-                                    _stream_ptr(stream)))
+        check(lib.dg_apply_residual(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                    self._precision(u, precision), _stream_ptr(stream)))
         return r
 
-    def apply_stage(self, stage, x, y, residual=False, stream=None):
+    def apply_stage(self, stage, x, y, residual=False, stream=None, precision=None):
         """One kernel of an apply (dg_apply_stage): stage 0 cell kernel from x, stage 1 face kernel into y."""
         self._vec_check(x, y)
         check(lib.dg_apply_stage(self.h, int(stage), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
-                                 _prec(x), int(bool(residual)), _stream_ptr(stream)))
+                                 self._precision(x, precision), int(bool(residual)), _stream_ptr(stream)))
         return y
 
     def precond_setup(self, kind=DG_PRECOND_BLOCK_JACOBI, stream=None):

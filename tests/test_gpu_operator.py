@@ -75,6 +75,11 @@ def test_small_meshes_all_degrees(dg, case):
     r32 = op.apply_residual(u32).cpu().numpy()
     assert relerr(y32, y_ref) <= TOL32
     assert relerr(r32, r_ref) <= TOL32
+    # FP64 vectors evaluated in double-float arithmetic meet the FP64 bar
+    yx = op.apply_jacobian(u64, precision=dg.DG_F64X).cpu().numpy()
+    rx = op.apply_residual(u64, precision=dg.DG_F64X).cpu().numpy()
+    assert relerr(yx, y_ref) <= TOL64
+    assert relerr(rx, r_ref) <= TOL64
     op.close()
 
 
@@ -89,6 +94,7 @@ def test_unit_cube_q3_8_full_vector(dg):
     u = torch.tensor(w.u, device="cuda")
     assert relerr(op.apply_residual(u).cpu().numpy(), r_ref) <= TOL64
     assert relerr(op.apply_residual(u.float()).cpu().numpy(), r_ref) <= TOL32
+    assert relerr(op.apply_residual(u, precision=dg.DG_F64X).cpu().numpy(), r_ref) <= TOL64
     op.close()
 
 
@@ -117,6 +123,8 @@ def test_unit_cube_q7_32_sampled_cells(dg):
     assert relerr(r, y_ref - F_ref) <= TOL64
     y32 = op.apply_jacobian(u.float()).view(-1, w.nb)[cells].cpu().numpy()
     assert relerr(y32, y_ref) <= TOL32
+    rx = op.apply_residual(u, precision=dg.DG_F64X).view(-1, w.nb)[cells].cpu().numpy()
+    assert relerr(rx, y_ref - F_ref) <= TOL64
     op.close()
 
 
