@@ -43,6 +43,12 @@ NCU_TRAFFIC = {
 }
 
 
+# FP32 lane instructions (FADD + FFMA + FMUL) per cell of the double-float kernels at k = 7, from the ncu
+# counters smsp__sass_thread_inst_executed_op_{fadd,ffma,fmul}_pred_on.sum of one launch / 32768 cells
+F64X_FP32_INST_PER_CELL = {"cell": (9714008064 + 2585788416 + 878706688) / 32768,
+                           "face": (5093392384 + 1496776704 + 499712000) / 32768}
+
+
 def kernel_source_hash():
     p = os.path.join(ROOT, "paper_1711_10885_gb300", "csrc", "dg_kernels.cuh")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
@@ -174,10 +180,13 @@ def run_profile(args):
     w = inputs.unit_cube_q7_32()
     op = dg.operator_for(w)
     u = torch.tensor(w.u, device="cuda")
+    prec = {"f64": dg.DG_F64, "f64x": dg.DG_F64X, "f32": dg.DG_F32}[args.precision]
+    if prec == dg.DG_F32:
+        u = u.float()
     r = torch.empty_like(u)
     torch.cuda.synchronize()
     for _ in range(args.warmup + args.steps):
-        op.apply_residual(u, r)
+        op.apply_residual(u, r, precision=prec)
     torch.cuda.synchronize()
     print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
     op.close()
@@ -409,6 +418,18 @@ def run_ours(args):
         b.synchronize()
         extra[name + "_mdofs"] = w.ndof * 20 / (a.elapsed_time(b) * 1e-3) / 1e6
 
+    # double-float (DG_F64X) per-kernel times on the launching stream
+    evx = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    for i in range(args.steps):
+        evx[3 * i].record(stream)
+        op.apply_stage(0, u, r, residual=True, precision=dg.DG_F64X)
+        evx[3 * i + 1].record(stream)
+        op.apply_stage(1, u, r, residual=True, precision=dg.DG_F64X)
+        evx[3 * i + 2].record(stream)
+    barrier()
+    xcell_ms = sum(evx[3 * i].elapsed_time(evx[3 * i + 1]) for i in range(args.steps)) / args.steps
+    xface_ms = sum(evx[3 * i + 1].elapsed_time(evx[3 * i + 2]) for i in range(args.steps)) / args.steps
+
     if ws > 1:
         t = torch.tensor([ms, e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -446,6 +467,17 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "extra": extra,
+        "f64x": {
+            "what": "FP64 vectors, operator in double-float (FP32 pairs) arithmetic; parity <= 1e-12 vs the FP64 oracle",
+            "mdofs": extra["residual_f64x_mdofs"],
+            "kernels_ms": {"dg_cell_kernel<dfl>": xcell_ms, "dg_face_kernel<dfl>": xface_ms},
+            "fp64_equivalent_tflops": (cell_fl + face_fl) / ((xcell_ms + xface_ms) * 1e-3) / 1e12,
+            # FP32 lane instructions per cell (FADD + FFMA + FMUL, ncu counters of the current kernels)
+            "fp32_issue_frac_cell_kernel": F64X_FP32_INST_PER_CELL["cell"] * w.ncell / (xcell_ms * 1e-3)
+                                           / (FP32_PEAK_TFLOPS * 1e12 / 2),
+            "fp32_issue_frac_face_kernel": F64X_FP32_INST_PER_CELL["face"] * w.ncell / (xface_ms * 1e-3)
+                                           / (FP32_PEAK_TFLOPS * 1e12 / 2),
+        },
     }
     if ws == 1 and not args.no_batch:
         line["batch"] = batch_benchmark()
@@ -467,6 +499,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--solve-only", nargs="?", const="all", default=None, choices=["all", "mixed", "learned"],
                     help="print the solver comparisons only (mixed precision at 48^3 Q5, learned at 64^3 Q4)")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f64x", "f32"],
+                    help="precision of the --profile applies")
     ap.add_argument("--profile", action="store_true",
                     help="only run warmup + steps residual applies (for ncu launch lists and captures)")
     args = ap.parse_args()

@@ -97,15 +97,18 @@ void build_tables(int N, Tables1D* tb) {
   }
 }
 
-__global__ void cast_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__global__ void cast_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, dgk::dfl* __restrict__ x,
+                                int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     b[i] = (float)a[i];
+    x[i] = dgk::dfl_from_double(a[i]);
+  }
 }
 
-static int cast_launch(const double* a, float* b, int64_t n, cudaStream_t s) {
+static int cast_launch(const double* a, float* b, dgk::dfl* x, int64_t n, cudaStream_t s) {
   const int64_t blocks64 = (n + 255) / 256;
   const unsigned blocks = (unsigned)(blocks64 > 152 * 32 ? 152 * 32 : (blocks64 > 0 ? blocks64 : 1));
-  cast_f64_to_f32<<<blocks, 256, 0, s>>>(a, b, n);
+  cast_f64_to_f32<<<blocks, 256, 0, s>>>(a, b, x, n);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "cast kernel");
 }
@@ -276,6 +279,7 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
     DG_TRY(cudaMalloc(&h->pX.fc, ncell * 18 * sizeof(dgk::dfl)), "cudaMalloc(fc pairs)");
     DG_TRY(cudaMalloc(&h->p64.F, ndof * sizeof(double)), "cudaMalloc(F)");
     DG_TRY(cudaMalloc(&h->p32.F, ndof * sizeof(float)), "cudaMalloc(F32)");
+    DG_TRY(cudaMalloc(&h->pX.F, ndof * sizeof(dgk::dfl)), "cudaMalloc(F pairs)");
     DG_TRY(cudaMalloc(&h->work_V, ndof * sizeof(double)), "cudaMalloc(work V)");
     DG_TRY(cudaMalloc(&h->work_tr, ncell * 12 * N * N * sizeof(double)), "cudaMalloc(work traces)");
     DG_TRY(cudaMemcpyAsync(h->p64.D, D.data(), ncell * sizeof(double), cudaMemcpyHostToDevice, s), "copy D");
@@ -303,7 +307,9 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
       }
     }
     rc = launch_rhs_f64(h, static_cast<const double*>(h->work_V), gdev, static_cast<double*>(h->p64.F), s);
-    if (rc == DG_OK) rc = cast_launch(static_cast<const double*>(h->p64.F), static_cast<float*>(h->p32.F), ndof, s);
+    if (rc == DG_OK)
+      rc = cast_launch(static_cast<const double*>(h->p64.F), static_cast<float*>(h->p32.F),
+                       static_cast<dgk::dfl*>(h->pX.F), ndof, s);
     e = cudaStreamSynchronize(s);
     for (int sd = 0; sd < 6; ++sd) {
       cudaFree(gdev[sd]);

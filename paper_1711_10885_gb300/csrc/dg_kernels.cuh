@@ -86,6 +86,47 @@ struct Lay {
   __device__ static __forceinline__ int idx(int i1, int i2, int i3) { return i1 + LS * (i2 + N * i3); }
 };
 
+// Dot products sum_i a_i b_i: plain FMA chains for float / double; the pair type has its own lazily
+// normalised accumulator (dot_begin / dot_add / dot_end in dg_dfloat.cuh).
+template <typename T>
+struct DotAcc {
+  using type = T;
+};
+template <>
+struct DotAcc<dfl> {
+  using type = dacc;
+};
+template <typename T>
+__device__ __forceinline__ T dot_begin(T a, T b) {
+  return a * b;
+}
+template <typename T>
+__device__ __forceinline__ void dot_add(T& c, T a, T b) {
+  c = fma(a, b, c);
+}
+template <typename T>
+__device__ __forceinline__ T dot_end(const T& c) {
+  return c;
+}
+
+// conversions between the vector element type TV and the compute type T
+template <typename T, typename TV>
+__device__ __forceinline__ T to_compute(TV v) {
+  return T(v);
+}
+template <>
+__device__ __forceinline__ dfl to_compute<dfl, double>(double v) {
+  return dfl_from_double(v);
+}
+template <typename TV, typename T>
+__device__ __forceinline__ TV from_compute(T v) {
+  return static_cast<TV>(v);
+}
+template <>
+__device__ __forceinline__ double from_compute<double, dfl>(dfl v) {
+  return dfl_to_double(v);
+}
+
 template <int N, typename T>
 __device__ __forceinline__ void load_line(const T* s, int base, int st, T (&x)[N]) {
 #pragma unroll
@@ -117,17 +158,17 @@ __device__ __forceinline__ void eo_fwd(const Tab<N, T>& tb, const T (&x)[N], T (
   T e[C], o[H];
 #pragma unroll
   for (int i = 0; i < C; ++i) {
-    T acc = tb.AE[i][0] * x[0];
+    typename DotAcc<T>::type acc = dot_begin(tb.AE[i][0], x[0]);
 #pragma unroll
-    for (int k = 1; k < C; ++k) acc = fma(tb.AE[i][k], x[2 * k], acc);
-    e[i] = acc;
+    for (int k = 1; k < C; ++k) dot_add(acc, tb.AE[i][k], x[2 * k]);
+    e[i] = dot_end(acc);
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
-    T acc = tb.AO[i][0] * x[1];
+    typename DotAcc<T>::type acc = dot_begin(tb.AO[i][0], x[1]);
 #pragma unroll
-    for (int k = 1; k < H; ++k) acc = fma(tb.AO[i][k], x[2 * k + 1], acc);
-    o[i] = acc;
+    for (int k = 1; k < H; ++k) dot_add(acc, tb.AO[i][k], x[2 * k + 1]);
+    o[i] = dot_end(acc);
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
@@ -145,17 +186,17 @@ __device__ __forceinline__ void eo_bwd(const Tab<N, T>& tb, const T (&x)[N], T (
   split_sd<N, T>(x, s, d);
 #pragma unroll
   for (int k = 0; k < C; ++k) {
-    T acc = tb.AE[0][k] * s[0];
+    typename DotAcc<T>::type acc = dot_begin(tb.AE[0][k], s[0]);
 #pragma unroll
-    for (int i = 1; i < C; ++i) acc = fma(tb.AE[i][k], s[i], acc);
-    y[2 * k] = acc;
+    for (int i = 1; i < C; ++i) dot_add(acc, tb.AE[i][k], s[i]);
+    y[2 * k] = dot_end(acc);
   }
 #pragma unroll
   for (int k = 0; k < H; ++k) {
-    T acc = tb.AO[0][k] * d[0];
+    typename DotAcc<T>::type acc = dot_begin(tb.AO[0][k], d[0]);
 #pragma unroll
-    for (int i = 1; i < H; ++i) acc = fma(tb.AO[i][k], d[i], acc);
-    y[2 * k + 1] = acc;
+    for (int i = 1; i < H; ++i) dot_add(acc, tb.AO[i][k], d[i]);
+    y[2 * k + 1] = dot_end(acc);
   }
 }
 
@@ -168,17 +209,17 @@ __device__ __forceinline__ void eo_anti(const T (&Hm)[(N + 1) / 2][N / 2], const
   T gp[C], gm[H];
 #pragma unroll
   for (int i = 0; i < C; ++i) {
-    T acc = Hm[i][0] * d[0];
+    typename DotAcc<T>::type acc = dot_begin(Hm[i][0], d[0]);
 #pragma unroll
-    for (int l = 1; l < H; ++l) acc = fma(Hm[i][l], d[l], acc);
-    gp[i] = acc;
+    for (int l = 1; l < H; ++l) dot_add(acc, Hm[i][l], d[l]);
+    gp[i] = dot_end(acc);
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
-    T acc = Hp[i][0] * s[0];
+    typename DotAcc<T>::type acc = dot_begin(Hp[i][0], s[0]);
 #pragma unroll
-    for (int l = 1; l < C; ++l) acc = fma(Hp[i][l], s[l], acc);
-    gm[i] = acc;
+    for (int l = 1; l < C; ++l) dot_add(acc, Hp[i][l], s[l]);
+    gm[i] = dot_end(acc);
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
@@ -205,7 +246,7 @@ __device__ __forceinline__ void gload_cells(T* sbuf, const TV* __restrict__ g, i
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int c = e / N3, r = e - c * N3;
     const int i1 = r % N, i23 = r / N;
-    sbuf[c * Lay<N>::CS + i1 + Lay<N>::LS * i23] = T(src[e]);
+    sbuf[c * Lay<N>::CS + i1 + Lay<N>::LS * i23] = to_compute<T, TV>(src[e]);
   }
 }
 template <int N, typename T>
@@ -364,7 +405,7 @@ struct FaceArgs {
   const T* V;       // point-space residual from dg_cell_kernel (mode 0/1), or f at points (mode 2)
   const T* traces;  // traces from dg_cell_kernel (mode 0/1)
   const T* fc;      // face coefficients
-  const TV* F;      // right hand side (mode 1)
+  const T* F;       // right hand side (mode 1), in the compute type
   const T* g[6];    // Dirichlet data per boundary side (mode 2), may be null
   TV* y;            // output vector (element type TV)
   int mode;
@@ -500,13 +541,13 @@ __device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, 
   // write out (minus F for the residual)
   const int total = here * N3;
   TV* dst = fa.y + (size_t)cell0 * N3;
-  const TV* Fs = fa.F ? fa.F + (size_t)cell0 * N3 : nullptr;
+  const T* Fs = fa.F ? fa.F + (size_t)cell0 * N3 : nullptr;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int c = e / N3, r = e - c * N3;
     const int i1 = r % N, i23 = r / N;
     T val = sV[c * CS + i1 + Lay<N>::LS * i23];
-    if (fa.mode == 1) val = val - T(Fs[e]);
-    dst[e] = static_cast<TV>(val);
+    if (fa.mode == 1) val = val - Fs[e];
+    dst[e] = from_compute<TV, T>(val);
   }
 }
 

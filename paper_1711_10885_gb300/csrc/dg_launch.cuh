@@ -113,8 +113,6 @@ template <int N, typename T, typename TV = T>
 int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s) {
   if (int rc = set_smem_attrs<N, T, TV>()) return rc;
   const Buffers& bf = buffers_for<T>(h);
-  // the right hand side is kept in the vector precision (FP64 for the double-float path)
-  const Buffers& bfv = sizeof(TV) == 8 ? h->p64 : h->p32;
   const auto tb = make_tab<N, T>(h->tab);
   const auto geo = make_geo<T>(h);
   const int cpb = dgk::Launch<N>::CPB;
@@ -128,7 +126,7 @@ int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaSt
   fa.V = V;
   fa.traces = tr;
   fa.fc = static_cast<const T*>(bf.fc);
-  fa.F = mode == 1 ? static_cast<const TV*>(bfv.F) : nullptr;
+  fa.F = mode == 1 ? static_cast<const T*>(bf.F) : nullptr;
   for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
   fa.y = y;
   fa.mode = mode;
