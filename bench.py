@@ -38,8 +38,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
 # kernels as they were when profiled, keyed by the sha256 of the kernel source at that time.
 NCU_TRAFFIC = {
-    ("dg_cell_kernel", "80affeb6db9eb779"): 408182528,  # 134.55 MB read + 273.63 MB write
-    ("dg_face_kernel", "80affeb6db9eb779"): 588832768,  # 474.55 MB read + 114.28 MB write
+    ("dg_cell_kernel", "f46eab9c62c74d38"): 409366784,  # 135.64 MB read + 273.72 MB write
+    ("dg_face_kernel", "f46eab9c62c74d38"): 589047808,  # 474.55 MB read + 114.50 MB write
 }
 
 
