@@ -191,8 +191,8 @@ typedef struct {
 /* Build the block-Jacobi preconditioner (kind = DG_PRECOND_BLOCK_JACOBI): for every cell the
  * diagonal block A_TT ((k+1)^3 x (k+1)^3: the cell's volume term plus the self-coupling of its
  * faces) is assembled on the device by running the operator's own kernels on unit vectors, then
- * inverted in a batch (Gauss-Jordan, partial pivoting) and kept in FP64 and FP32.  Memory:
- * ncells * (k+1)^6 * 12 bytes, owned by the handle.  Requires (k+1)^3 <= 512.  Returns
+ * inverted in a batch (Gauss-Jordan, partial pivoting) and kept in FP64 and FP32 (FP32 rows padded
+ * to a multiple of 4).  Memory: about ncells * (k+1)^6 * 12 bytes, owned by the handle.  Requires (k+1)^3 <= 512.  Returns
  * DG_ERR_NAN if a block is singular.  Synchronises `stream`. */
 int dg_precond_setup(dg_handle* h, int32_t kind, void* stream);
 

@@ -124,9 +124,65 @@ __global__ void __launch_bounds__(256) bj_apply(const T* __restrict__ M, const T
   }
 }
 
-__global__ void cast_blocks(const double* __restrict__ a, float* __restrict__ b, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// FP32 copy of the inverse blocks with rows padded to np = n rounded up to 4 (16-byte rows)
+__global__ void cast_blocks(const double* __restrict__ a, float* __restrict__ b, int64_t nblocks, int n, int np) {
+  const size_t total = (size_t)nblocks * n * np;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t blk = i / ((size_t)n * np);
+    const int rem = (int)(i - blk * n * np), row = rem / np, col = rem - row * np;
+    b[i] = col < n ? (float)a[(blk * n + row) * n + col] : 0.f;
+  }
+}
+
+// FP32 block-Jacobi application: z_T = M_T^T r_T with M_T = (A_TT^{-1})^T stored row-padded to np.
+// A cell is handled by wpc warps, thread t owning output columns 4t .. 4t+3 (float4 loads of the padded
+// rows, several rows in flight); cpc cells share a CTA.
+__global__ void __launch_bounds__(128) bj_apply_f32v(const float* __restrict__ M, const float* __restrict__ r,
+                                                     float* __restrict__ z, int64_t ncell, int n, int np, int wpc,
+                                                     int cpc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* rs = reinterpret_cast<float*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lc = warp / wpc, wi = warp - lc * wpc;
+  const int64_t cell = (int64_t)blockIdx.x * cpc + lc;
+  const bool active = lc < cpc && cell < ncell;
+  float* rc = rs + lc * np;
+  if (active)
+    for (int j = wi * 32 + lane; j < n; j += wpc * 32) rc[j] = r[cell * n + j];
+  __syncthreads();
+  if (!active) return;
+  const int t = wi * 32 + lane;  // float4 column index
+  if (4 * t >= n) return;
+  const float4* Mc = reinterpret_cast<const float4*>(M + (size_t)cell * n * np) + t;
+  const int q = np / 4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  int j = 0;
+  for (; j + 8 <= n; j += 8) {
+    float4 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = __ldg(Mc + (size_t)(j + u) * q);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float rv = rc[j + u];
+      acc.x = fmaf(m[u].x, rv, acc.x);
+      acc.y = fmaf(m[u].y, rv, acc.y);
+      acc.z = fmaf(m[u].z, rv, acc.z);
+      acc.w = fmaf(m[u].w, rv, acc.w);
+    }
+  }
+  for (; j < n; ++j) {
+    const float4 m = __ldg(Mc + (size_t)j * q);
+    const float rv = rc[j];
+    acc.x = fmaf(m.x, rv, acc.x);
+    acc.y = fmaf(m.y, rv, acc.y);
+    acc.z = fmaf(m.z, rv, acc.z);
+    acc.w = fmaf(m.w, rv, acc.w);
+  }
+  float* zc = z + cell * n + 4 * t;
+  const float v[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    if (4 * t + c < n) zc[c] = v[c];
 }
 
 int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s) {
@@ -138,9 +194,13 @@ int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t 
 }
 
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
-  const int n = h->N * h->N * h->N;
-  const int threads = n >= 256 ? 256 : ((n + 31) / 32) * 32;
-  bj_apply<float><<<(unsigned)h->ncell, threads, n * sizeof(float), s>>>(static_cast<const float*>(h->bj32), r, z, n);
+  const int n = h->N * h->N * h->N, np = (n + 3) / 4 * 4;
+  const int wpc = (np / 4 + 31) / 32;            // warps per cell
+  const int cpc = wpc >= 4 ? 1 : 4 / wpc;        // cells per CTA
+  const int threads = 32 * wpc * cpc;
+  const unsigned grid = (unsigned)((h->ncell + cpc - 1) / cpc);
+  bj_apply_f32v<<<grid, threads, (size_t)cpc * np * sizeof(float), s>>>(static_cast<const float*>(h->bj32), r, z,
+                                                                        h->ncell, n, np, wpc, cpc);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply");
 }
@@ -163,13 +223,14 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
     return DG_ERR_INVALID_ARG;
   }
   const size_t nblk = (size_t)h->ncell * n * n;
+  const int np = (n + 3) / 4 * 4;
   cudaError_t e;
   if (!h->bj64) {
     e = cudaMalloc(&h->bj64, nblk * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(block-Jacobi FP64)");
   }
   if (!h->bj32) {
-    e = cudaMalloc(&h->bj32, nblk * sizeof(float));
+    e = cudaMalloc(&h->bj32, (size_t)h->ncell * n * np * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(block-Jacobi FP32)");
   }
   // assemble in chunks of cells: each chunk needs (cells * n) virtual cells of work buffers
@@ -200,7 +261,8 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      cast_blocks<<<152 * 8, 256, 0, s>>>(static_cast<const double*>(h->bj64), static_cast<float*>(h->bj32), nblk);
+      cast_blocks<<<152 * 8, 256, 0, s>>>(static_cast<const double*>(h->bj64), static_cast<float*>(h->bj32), h->ncell,
+                                         n, np);
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) rc = cuda_fail(e, "block inversion");
