@@ -49,22 +49,47 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(lib):
+    lib.oracle_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
+    lib.oracle_basis_1d.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+    lib.oracle_basis_1d.restype = None
+    lib.oracle_apply.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                 ctypes.c_double, _dp, _dp, _ip, ctypes.c_int]
+    lib.oracle_rhs.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                               ctypes.c_double, _dp, ctypes.POINTER(_dp), _dp]
+    lib.oracle_volume_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
+    lib.oracle_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            lib.oracle_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
-            lib.oracle_basis_1d.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
-            lib.oracle_basis_1d.restype = None
-            lib.oracle_apply.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                         ctypes.c_double, _dp, _dp, _ip, ctypes.c_int]
-            lib.oracle_rhs.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                       ctypes.c_double, _dp, ctypes.POINTER(_dp), _dp]
-            lib.oracle_volume_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
-            lib.oracle_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+class use_library:
+    """Context manager that routes this module's calls to another build of the oracle source (the
+    mutation tests compile copies of dg_oracle.c with one planted mistake)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        with _lock:
+            self.saved = _lib
+            _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+        return False
 
 
 def _d(a):

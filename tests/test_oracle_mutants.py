@@ -1,0 +1,71 @@
+"""Mutation check of the oracle's pins (CPU): each plausible mistake below is planted in a copy of
+oracle/dg_oracle.c (never in the file itself), compiled, and the pins of test_oracle_pins.py must fail
+for it.  This shows that the pins pin the oracle rather than restate it."""
+
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "dg_oracle.c")
+
+# (name, original text, mutated text)
+MUTANTS = [
+    ("weighted average sign", "wm * Dm * dnum + wp * Dp * dnup", "wm * Dm * dnum - wp * Dp * dnup"),
+    ("upwind branch swapped", "return bnu >= 0.0 ? um * bnu : up * bnu;", "return bnu >= 0.0 ? up * bnu : um * bnu;"),
+    ("penalty dropped", "+ gam * jump_u * jump_v", "+ 0.0 * gam * jump_u * jump_v"),
+    ("symmetry term sign", "- avg_dv * jump_u", "+ avg_dv * jump_u"),
+    ("convection sign", "DT * g[r] - pr->b[r] * uq", "DT * g[r] + pr->b[r] * uq"),
+    ("transposed basis index", "t->grad[o * 3 + 1] = v[0][j1] * d[1][j2] * v[2][j3];",
+     "t->grad[o * 3 + 1] = v[0][j1] * d[1][j3] * v[2][j2];"),
+    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double bnu = sgn * pr->b[dir];\n        double gam = DT",
+     "double sgn = 1.0;\n        double bnu = sgn * pr->b[dir];\n        double gam = DT"),
+    ("Gauss weight", "w[i] = 1.0 / ((1.0 - t * t) * dP[m] * dP[m]);", "w[i] = 2.0 / ((1.0 - t * t) * dP[m] * dP[m]);"),
+    ("Dirichlet data sign in the right hand side", "- DT * dnv * g + gam * g * v", "+ DT * dnv * g + gam * g * v"),
+    ("reaction dropped", "pr->c * uq * ph[i]", "0.0 * pr->c * uq * ph[i]"),
+    ("harmonic mean replaced by arithmetic mean", "return 2.0 * a * b / (a + b);", "return 0.5 * (a + b);"),
+    ("face weight swapped", "double wm = Dp / (Dm + Dp), wp = Dm / (Dm + Dp);",
+     "double wm = Dm / (Dm + Dp), wp = Dp / (Dm + Dp);"),
+]
+
+
+def _pin_checks():
+    """The fast pins, each returning normally when it holds."""
+    yield lambda: pins.test_gauss_legendre_matches_numpy(5)
+    yield lambda: pins.test_basis_matches_numpy_and_is_orthonormal(3)
+    for case in pins.KRON_CASES[1:3]:
+        yield lambda case=case: pins.test_oracle_matches_kronecker_closed_form(case)
+    yield lambda: pins.test_polynomial_solution_has_zero_residual(2, (3, 2, 2))
+    yield pins.test_diffusion_part_is_symmetric_and_coercive
+    yield lambda: pins.test_global_conservation((1.0, 0.5, 0.25))
+    yield pins.test_reaction_term_is_mass_matrix
+    yield pins.test_rhs_constant_source
+
+
+@pytest.mark.parametrize("name,orig,mutated", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, orig, mutated):
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site for '{name}' not found exactly once"
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "mutant.c")
+        lib = os.path.join(d, "libmutant.so")
+        open(src, "w").write(text.replace(orig, mutated))
+        subprocess.run(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-o", lib, src, "-lm"],
+                       check=True)
+        caught = []
+        with oracle.use_library(lib):
+            for check in _pin_checks():
+                try:
+                    check()
+                except AssertionError:
+                    caught.append(check)
+    assert caught, f"no pin fails for the planted mistake: {name}"
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    for check in _pin_checks():
+        check()
