@@ -185,3 +185,30 @@ def test_api_errors(dg):
         dg.check(dg.lib.dg_apply_jacobian(op.h, dg.ctypes.c_void_p(u.data_ptr()), dg.ctypes.c_void_p(1024), 7,
                                           None))
     op.close()
+
+
+@pytest.mark.parametrize("which", ["unit_cube_q5_48", "q4_64_sigma15"])
+def test_other_full_size_workloads_sampled_cells(dg, which):
+    """48^3 Q5 (sine source, log-normal D) and 64^3 Q4 (sigma 1.5): residual on sampled cells, all precisions."""
+    if which == "unit_cube_q5_48":
+        w = inputs.unit_cube_q5_48()
+    else:
+        w = inputs.Workload("q4_64", (64, 64, 64), 4, inputs.log_normal_D(64 ** 3, 1.5, 20), f_kind="one")
+        w.u = inputs.uniform_u(w.ndof, 21)
+    pr = oracle_problem(w)
+    cells = _sample_cells(w.n, 30, 7)
+    y_ref = oracle.apply(pr, w.u, cells=cells).reshape(len(cells), w.nb)
+    # right hand side on the sampled cells: (f, phi_i)_T from the oracle's own quadrature points
+    F_full = oracle_F(w, pr).reshape(w.ncell, w.nb)[cells] if w.ncell <= 48 ** 3 else None
+    op = dg.operator_for(w)
+    u = torch.tensor(w.u, device="cuda")
+    y = op.apply_jacobian(u).view(-1, w.nb)[cells].cpu().numpy()
+    assert relerr(y, y_ref) <= TOL64
+    yx = op.apply_jacobian(u, precision=dg.DG_F64X).view(-1, w.nb)[cells].cpu().numpy()
+    assert relerr(yx, y_ref) <= TOL64
+    y32 = op.apply_jacobian(u.float()).view(-1, w.nb)[cells].cpu().numpy()
+    assert relerr(y32, y_ref) <= TOL32
+    if F_full is not None:
+        r = op.apply_residual(u).view(-1, w.nb)[cells].cpu().numpy()
+        assert relerr(r, y_ref - F_full) <= TOL64
+    op.close()
