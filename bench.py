@@ -188,11 +188,46 @@ def cpu_baseline(w, seconds=15.0):
             "sample": f"A u on {count} random cells of the 32^3 Q7 workload ({dt:.1f} s, one thread)"}
 
 
+def run_profile_solver(args):
+    """Minimal launch sequence for profilers of the solver kernels at 48^3 Q5: FP32 block-Jacobi
+    applications and learned-preconditioner applications (untrained network)."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, inputs
+    torch.cuda.set_device(0)
+    w = inputs.unit_cube_q5_48(with_u=False)
+    op = dg.operator_for(w)
+    op.precond_setup()
+    mlp = dg.MLP(w.k, seed=0)
+    r = torch.randn(w.ndof, dtype=torch.float32, device="cuda")
+    z = torch.empty_like(r)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup + args.steps):
+        op.precond_apply(r, z)
+    for _ in range(args.warmup + args.steps):
+        mlp.apply(op, r, z)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(10):
+        mlp.apply(op, r, z)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / 10
+    flops = 2.0 * w.ncell * (256 * mlp.kinp + 256 * 256 + mlp.outp * 256)
+    print(json.dumps({"profile": "solver", "mlp_apply_ms": ms, "mlp_tflops": flops / (ms * 1e-3) / 1e12,
+                      "cells": w.ncell}))
+    mlp.close()
+    op.close()
+
+
 def run_profile(args):
     """Minimal launch sequence for profilers: W + K residual applies on the bench workload."""
     import torch
 
     from paper_1711_10885_gb300 import dg, inputs
+    if args.profile_solver:
+        return run_profile_solver(args)
     torch.cuda.set_device(0)
     w = inputs.unit_cube_q7_32()
     op = dg.operator_for(w)
@@ -513,6 +548,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--solve-only", nargs="?", const="all", default=None, choices=["all", "mixed", "learned"],
                     help="print the solver comparisons only (mixed precision at 48^3 Q5, learned at 64^3 Q4)")
+    ap.add_argument("--profile-solver", action="store_true",
+                    help="with --profile: block-Jacobi and network applications at 48^3 Q5 instead")
     ap.add_argument("--precision", default="f64", choices=["f64", "f64x", "f32"],
                     help="precision of the --profile applies")
     ap.add_argument("--profile", action="store_true",
