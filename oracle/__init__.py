@@ -57,6 +57,11 @@ def _configure(lib):
                                  ctypes.c_double, _dp, _dp, _ip, ctypes.c_int]
     lib.oracle_rhs.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                ctypes.c_double, _dp, ctypes.POINTER(_dp), _dp]
+    lib.oracle_apply_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                    ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _ip, ctypes.c_int]
+    lib.oracle_rhs_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                  ctypes.c_double, _ip, _dp, _dp, ctypes.POINTER(_dp), _dp]
+    lib.oracle_cell_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_volume_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
     return lib
@@ -128,7 +133,7 @@ class Problem:
     """
 
     def __init__(self, n, k, D, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-                 m=None):
+                 m=None, periodic=(0, 0, 0), b_vol=None, b_face=None):
         self.n = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(3))
         self.lo = _arr(lo, 3)
         self.hi = _arr(hi, 3)
@@ -141,6 +146,10 @@ class Problem:
         self.c = float(c)
         self.sigma = float(sigma) if sigma is not None else penalty_sigma(self.k, "baseline")
         self.nb = (self.k + 1) ** 3
+        # periodic axes and a velocity field at the quadrature points (Sec. 5.3); see oracle_apply_ex
+        self.periodic = np.ascontiguousarray(np.asarray(periodic, dtype=np.int32).reshape(3))
+        self.b_vol = None if b_vol is None else _arr(b_vol, self.ncell * self.m ** 3 * 3)
+        self.b_face = None if b_face is None else _arr(b_face, self.ncell * 6 * self.m ** 2)
 
     @property
     def ndof(self):
@@ -167,13 +176,15 @@ def penalty_sigma(k: int, mode: str = "baseline", alpha: float = 2.0, d: int = 3
 def apply(pr: Problem, u, cells=None) -> np.ndarray:
     """y = A u with (A u)_i = a_h(u, phi_i) (eq. blf); if ``cells`` is given only those cells' blocks."""
     u = _arr(u, pr.ndof)
+    ex = (pr.periodic.ctypes.data_as(_ip), _d(pr.b_vol) if pr.b_vol is not None else None,
+          _d(pr.b_face) if pr.b_face is not None else None)
     if cells is None:
         y = np.empty(pr.ndof)
-        rc = _load().oracle_apply(*pr._args(), _d(u), _d(y), None, 0)
+        rc = _load().oracle_apply_ex(*pr._args(), *ex, _d(u), _d(y), None, 0)
     else:
         cl = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1))
         y = np.empty(cl.size * pr.nb)
-        rc = _load().oracle_apply(*pr._args(), _d(u), _d(y), cl.ctypes.data_as(_ip), int(cl.size))
+        rc = _load().oracle_apply_ex(*pr._args(), *ex, _d(u), _d(y), cl.ctypes.data_as(_ip), int(cl.size))
     if rc != 0:
         raise RuntimeError(f"oracle_apply failed ({rc})")
     return y
@@ -194,7 +205,9 @@ def rhs(pr: Problem, f_qp=None, g_qp=None) -> np.ndarray:
                 a = _arr(g_qp[s])
                 keep.append(a)
                 garr[s] = _d(a)
-    rc = _load().oracle_rhs(*pr._args(), _d(fa) if fa is not None else None, garr, _d(F))
+    rc = _load().oracle_rhs_ex(*pr._args(), pr.periodic.ctypes.data_as(_ip),
+                               _d(pr.b_face) if pr.b_face is not None else None,
+                               _d(fa) if fa is not None else None, garr, _d(F))
     if rc != 0:
         raise RuntimeError(f"oracle_rhs failed ({rc})")
     return F
@@ -211,6 +224,14 @@ def volume_points(pr: Problem) -> np.ndarray:
     if _load().oracle_volume_points(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr.m, _d(xyz)) != 0:
         raise RuntimeError("oracle_volume_points failed")
     return xyz.reshape(pr.ncell, pr.m ** 3, 3)
+
+
+def cell_face_points(pr: Problem) -> np.ndarray:
+    """Physical coordinates [ncell, 6, m^2, 3] of the face points of every face of every cell."""
+    xyz = np.empty(pr.ncell * 6 * pr.m ** 2 * 3)
+    if _load().oracle_cell_face_points(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr.m, _d(xyz)) != 0:
+        raise RuntimeError("oracle_cell_face_points failed")
+    return xyz.reshape(pr.ncell, 6, pr.m ** 2, 3)
 
 
 def face_points(pr: Problem, s: int) -> np.ndarray:

@@ -22,7 +22,11 @@
  *  - orthonormal shifted Legendre basis on the reference interval [0,1]:
  *    theta_j(x) = sqrt(2j+1) P_j(2x-1)  ("L2-orthogonal Legendre", Sec. 2);
  *  - tensor Gauss-Legendre rule with m points per direction (Sec. 3.1);
- *  - scalar diffusion D_T * I constant per cell, constant b and c (Problem A);
+ *  - scalar diffusion D_T * I constant per cell, constant c, and either a
+ *    constant b (Problem A) or b given at the quadrature points (the
+ *    Taylor-Green transport problem of Sec. 5.3, evaluated by the caller);
+ *  - a periodic axis makes its two end faces interior faces between the last
+ *    and the first cell (Sec. 5.1, 5.3);
  *  - penalty gamma_F = <delta-,delta+> * sigma * |F| / min(|T-|,|T+|) where the
  *    caller passes sigma (the paper's alpha*p*(p+d-1), or 2k(k+1));
  *    on boundary faces <delta-,delta+> -> delta- and min|T| -> |T-|;
@@ -107,6 +111,9 @@ typedef struct {
   double b[3];         /* constant velocity                                  */
   double c;            /* reaction                                           */
   double sigma;        /* penalty factor, gamma = <d-,d+> sigma |F|/min|T|   */
+  int periodic[3];     /* 1: the axis wraps around (its end faces are interior faces) */
+  const double* b_vol;  /* NULL, or b at the volume points [ncells][m^3][3]          */
+  const double* b_face; /* NULL, or b . e_dir at each cell's face points [ncells][6][m^2] */
 } oracle_problem;
 
 /* Full 3D tables at one set of points: phi[p*nb + J], grad[(p*nb + J)*3 + r]
@@ -247,7 +254,10 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
     eval_fe(&cx->vol, p, zc, h, &uq, g);
     double dx = cx->vol.wgt[p] * cx->vol_T; /* Delta_T * w_i */
     double fl[3];
-    for (int r = 0; r < 3; ++r) fl[r] = DT * g[r] - pr->b[r] * uq;
+    for (int r = 0; r < 3; ++r) {
+      const double br = pr->b_vol ? pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + r] : pr->b[r];
+      fl[r] = DT * g[r] - br * uq;
+    }
     const double* ph = cx->vol.phi + (size_t)p * nb;
     const double* gr = cx->vol.grad + (size_t)p * nb * 3;
     for (int i = 0; i < nb; ++i) {
@@ -263,8 +273,11 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
       const table3d* ft = &cx->face[2 * dir + side]; /* this cell's trace at the face */
       int nic[3] = {ic[0], ic[1], ic[2]};
       nic[dir] += side ? 1 : -1;
+      if (pr->periodic[dir]) nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];
       int interior = nic[dir] >= 0 && nic[dir] < pr->n[dir];
       double dF = cx->area[dir];
+      /* normal velocity b . e_dir at face point p of this face */
+      const double* bfp = pr->b_face ? pr->b_face + ((size_t)cell * 6 + 2 * dir + side) * ft->np : 0;
       if (interior) {
         /* T- is the lower cell along dir, nu = +e_dir from T- to T+ */
         int nbr = cell_index(pr, nic);
@@ -275,8 +288,8 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
         double Dp = this_is_minus ? pr->D[nbr] : DT;
         double wm = Dp / (Dm + Dp), wp = Dm / (Dm + Dp); /* delta = nu^T D nu = D */
         double gam = harmonic(Dm, Dp) * pr->sigma * dF / cx->vol_T;
-        double bnu = pr->b[dir];
         for (int p = 0; p < ft->np; ++p) {
+          double bnu = bfp ? bfp[p] : pr->b[dir];
           double us, gs[3], un, gn[3];
           eval_fe(ft, p, zc, h, &us, gs);
           eval_fe(nt, p, zn, h, &un, gn);
@@ -300,9 +313,9 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
       } else {
         /* Dirichlet boundary face, nu = outward normal */
         double sgn = side ? 1.0 : -1.0;
-        double bnu = sgn * pr->b[dir];
         double gam = DT * pr->sigma * dF / cx->vol_T;
         for (int p = 0; p < ft->np; ++p) {
+          double bnu = sgn * (bfp ? bfp[p] : pr->b[dir]);
           double us, gs[3];
           eval_fe(ft, p, zc, h, &us, gs);
           double dnu = sgn * gs[dir];
@@ -333,16 +346,40 @@ static int fill_problem(oracle_problem* pr, const int* n, const double* lo, cons
   pr->D = D;
   pr->c = c;
   pr->sigma = sigma;
+  pr->periodic[0] = pr->periodic[1] = pr->periodic[2] = 0;
+  pr->b_vol = 0;
+  pr->b_face = 0;
   return 0;
 }
 
 /* y = A u restricted to the listed cells (cells == NULL: all cells, in order).
  * y holds ncell_out blocks of (k+1)^3 values, one per listed cell. */
+static int apply_impl(oracle_problem* pr_in, const double* u, double* y, const int* cells, int ncells_out);
+
 int oracle_apply(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
                  double c, double sigma, const double* u, double* y, const int* cells, int ncells_out) {
   oracle_problem pr;
-  oracle_ctx cx;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
+  return apply_impl(&pr, u, y, cells, ncells_out);
+}
+
+/* oracle_apply with periodic axes and a velocity field given at the quadrature points:
+ * b_vol [ncells][m^3][3] (NULL: constant b), b_face [ncells][6][m^2] = b . e_dir at each face point of
+ * each cell (NULL: constant b).  On a periodic axis the end faces couple the first and last cells. */
+int oracle_apply_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
+                    double c, double sigma, const int* periodic, const double* b_vol, const double* b_face,
+                    const double* u, double* y, const int* cells, int ncells_out) {
+  oracle_problem pr;
+  if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
+  for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
+  pr.b_vol = b_vol;
+  pr.b_face = b_face;
+  return apply_impl(&pr, u, y, cells, ncells_out);
+}
+
+static int apply_impl(oracle_problem* pr_in, const double* u, double* y, const int* cells, int ncells_out) {
+  oracle_problem pr = *pr_in;
+  oracle_ctx cx;
   if (ctx_build(&pr, &cx)) return -2;
   int nb = cx.vol.nb;
   int count = cells ? ncells_out : cx.ncell;
@@ -362,11 +399,29 @@ int oracle_apply(const int* n, const double* lo, const double* hi, int k, int m,
  * (f_qp: [ncells][m^3], NULL means f = 0) plus the Dirichlet terms
  * -(Phi(0,g,b_nu), v)_F - (nu . D grad v, g)_F + gamma_F (g, v)_F from g given
  * at the boundary face points (g_qp[s]: side s array, NULL means g = 0). */
+static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* const* g_qp, double* F);
+
 int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
                double c, double sigma, const double* f_qp, const double* const* g_qp, double* F) {
   oracle_problem pr;
-  oracle_ctx cx;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
+  return rhs_impl(&pr, f_qp, g_qp, F);
+}
+
+/* oracle_rhs with periodic axes (no Dirichlet faces there) and b . e_dir at the face points. */
+int oracle_rhs_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
+                  double c, double sigma, const int* periodic, const double* b_face, const double* f_qp,
+                  const double* const* g_qp, double* F) {
+  oracle_problem pr;
+  if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
+  for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
+  pr.b_face = b_face;
+  return rhs_impl(&pr, f_qp, g_qp, F);
+}
+
+static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* const* g_qp, double* F) {
+  oracle_problem pr = *pr_in;
+  oracle_ctx cx;
   if (ctx_build(&pr, &cx)) return -2;
   int nb = cx.vol.nb, npv = cx.vol.np;
   const double* h = cx.h;
@@ -386,18 +441,19 @@ int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, c
       for (int side = 0; side < 2; ++side) {
         int s = 2 * dir + side;
         int on_boundary = side ? ic[dir] == pr.n[dir] - 1 : ic[dir] == 0;
-        if (!on_boundary || !g_qp || !g_qp[s]) continue;
+        if (pr.periodic[dir] || !on_boundary || !g_qp || !g_qp[s]) continue;
         /* face index within the boundary layer: tangential cell indices, lower axis fastest */
         int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
         int fidx = ic[ta] + pr.n[ta] * ic[tb];
         const table3d* ft = &cx.face[s];
         double sgn = side ? 1.0 : -1.0;
-        double bnu = sgn * pr.b[dir];
+        const double* bfp = pr.b_face ? pr.b_face + ((size_t)cell * 6 + s) * ft->np : 0;
         double DT = pr.D[cell];
         double dF = cx.area[dir];
         double gam = DT * pr.sigma * dF / cx.vol_T;
         for (int p = 0; p < ft->np; ++p) {
           double g = g_qp[s][(size_t)fidx * ft->np + p];
+          double bnu = sgn * (bfp ? bfp[p] : pr.b[dir]);
           double dx = ft->wgt[p] * dF;
           const double* ph = ft->phi + (size_t)p * nb;
           const double* gr = ft->grad + (size_t)p * nb * 3;
@@ -459,6 +515,40 @@ int oracle_face_points(const int* n, const double* lo, const double* hi, int m, 
           xyz[o++] = p[1];
           xyz[o++] = p[2];
         }
+  free(x);
+  free(w);
+  return 0;
+}
+
+/* Physical coordinates of the face points of every face of every cell:
+ * xyz[((cell*6 + s)*m^2 + p)*3 + r], s = 2*dir + side, points ordered as in the face tables
+ * (lower tangential axis fastest). */
+int oracle_cell_face_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
+  double* x = (double*)malloc(sizeof(double) * m);
+  double* w = (double*)malloc(sizeof(double) * m);
+  if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
+  double h[3];
+  for (int r = 0; r < 3; ++r) h[r] = (hi[r] - lo[r]) / n[r];
+  size_t o = 0;
+  for (int iz = 0; iz < n[2]; ++iz)
+    for (int iy = 0; iy < n[1]; ++iy)
+      for (int ix = 0; ix < n[0]; ++ix) {
+        const int ic[3] = {ix, iy, iz};
+        for (int dir = 0; dir < 3; ++dir)
+          for (int side = 0; side < 2; ++side) {
+            int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+            for (int pb = 0; pb < m; ++pb)
+              for (int pa = 0; pa < m; ++pa) {
+                double p[3];
+                p[dir] = lo[dir] + h[dir] * (ic[dir] + side);
+                p[ta] = lo[ta] + h[ta] * (ic[ta] + x[pa]);
+                p[tb] = lo[tb] + h[tb] * (ic[tb] + x[pb]);
+                xyz[o++] = p[0];
+                xyz[o++] = p[1];
+                xyz[o++] = p[2];
+              }
+          }
+      }
   free(x);
   free(w);
   return 0;

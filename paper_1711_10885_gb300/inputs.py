@@ -39,6 +39,7 @@ class Workload:
     f_params: dict = field(default_factory=dict)
     lo: tuple = (0.0, 0.0, 0.0)
     hi: tuple = (1.0, 1.0, 1.0)
+    periodic: tuple = (0, 0, 0)     # 1 on an axis whose two end faces are identified
 
     @property
     def ncell(self):
@@ -129,3 +130,34 @@ def batch_problems(count: int = 64, seed: int = 5, nmin: int = 4, nmax: int = 24
         w.u = uniform_u(w.ndof, 2000 + i)
         out.append(w)
     return out
+
+
+def taylor_green_velocity(xyz: np.ndarray) -> np.ndarray:
+    """The fixed Taylor-Green type flow field of the transport example (Sec. 5.3) at points xyz[..., 3]:
+    b = (cos x1 sin(-x2) sin(-x3), 1/2 sin x1 cos(-x2) sin(-x3), 1/2 sin x1 sin(-x2) cos(-x3))."""
+    x1, x2, x3 = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    return np.stack([np.cos(x1) * np.sin(-x2) * np.sin(-x3),
+                     0.5 * np.sin(x1) * np.cos(-x2) * np.sin(-x3),
+                     0.5 * np.sin(x1) * np.sin(-x2) * np.cos(-x3)], axis=-1)
+
+
+def gaussian_bump(xyz: np.ndarray, x0=(0.5, 0.0, 0.0)) -> np.ndarray:
+    """Initial concentration of the transport example: exp(-2 |x - x0|^2)."""
+    d = xyz - np.asarray(x0)
+    return np.exp(-2.0 * np.sum(d * d, axis=-1))
+
+
+def face_normal_velocity(bfun, face_xyz: np.ndarray) -> np.ndarray:
+    """b . e_dir at the face points of every face of every cell, face_xyz[ncell, 6, m^2, 3] (face s = 2 dir + side)."""
+    b = bfun(face_xyz)
+    out = np.empty(face_xyz.shape[:3])
+    for s in range(6):
+        out[:, s] = b[:, s, :, s // 2]
+    return out
+
+
+def taylor_green(n=16, k=5) -> Workload:
+    """Transport on the periodic cube (-pi, pi)^3: D = 5e-6, c = 0, f = 0, Taylor-Green velocity (Sec. 5.3)."""
+    w = Workload(f"taylor_green_q{k}_{n}", (n, n, n), k, np.full(n ** 3, 5e-6), b=(0.0, 0.0, 0.0), c=0.0,
+                 f_kind="zero", lo=(-np.pi,) * 3, hi=(np.pi,) * 3, periodic=(1, 1, 1))
+    return w

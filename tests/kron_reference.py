@@ -50,8 +50,10 @@ def _embed(mat1d, q, n):
     return np.kron(mats[2], np.kron(mats[1], mats[0]))
 
 
-def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1)):
-    """Dense A with A[(T,I),(S,J)] = a_h(phi_{S,J}, phi_{T,I}) (row = test function)."""
+def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1), periodic=(0, 0, 0)):
+    """Dense A with A[(T,I),(S,J)] = a_h(phi_{S,J}, phi_{T,I}) (row = test function).
+
+    On a periodic axis the face after the last cell couples it to the first cell (an interior face)."""
     n = tuple(int(v) for v in n)
     nb1 = k + 1
     nb = nb1 ** 3
@@ -88,9 +90,9 @@ def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1)):
                     ic = [ix, iy, iz]
                     T = cid(*ic)
                     # interior face to the upper neighbour along q: T- = T, T+ = neighbour
-                    if ic[q] + 1 < n[q]:
+                    if ic[q] + 1 < n[q] or periodic[q]:
                         jc = list(ic)
-                        jc[q] += 1
+                        jc[q] = (jc[q] + 1) % n[q]
                         P = cid(*jc)
                         Dm, Dp = D[T], D[P]
                         wm, wp = Dp / (Dm + Dp), Dm / (Dm + Dp)
@@ -117,7 +119,7 @@ def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1)):
                         A[blk(P, P)] += area * _embed(pp, q, nb1)
                     # Dirichlet faces
                     for side in (0, 1):
-                        on_b = (ic[q] == 0) if side == 0 else (ic[q] == n[q] - 1)
+                        on_b = not periodic[q] and ((ic[q] == 0) if side == 0 else (ic[q] == n[q] - 1))
                         if not on_b:
                             continue
                         DT = D[T]

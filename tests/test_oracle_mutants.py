@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_transport_pins as tpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "dg_oracle.c")
 
@@ -19,17 +20,24 @@ MUTANTS = [
     ("upwind branch swapped", "return bnu >= 0.0 ? um * bnu : up * bnu;", "return bnu >= 0.0 ? up * bnu : um * bnu;"),
     ("penalty dropped", "+ gam * jump_u * jump_v", "+ 0.0 * gam * jump_u * jump_v"),
     ("symmetry term sign", "- avg_dv * jump_u", "+ avg_dv * jump_u"),
-    ("convection sign", "DT * g[r] - pr->b[r] * uq", "DT * g[r] + pr->b[r] * uq"),
+    ("convection sign", "fl[r] = DT * g[r] - br * uq;", "fl[r] = DT * g[r] + br * uq;"),
     ("transposed basis index", "t->grad[o * 3 + 1] = v[0][j1] * d[1][j2] * v[2][j3];",
      "t->grad[o * 3 + 1] = v[0][j1] * d[1][j3] * v[2][j2];"),
-    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double bnu = sgn * pr->b[dir];\n        double gam = DT",
-     "double sgn = 1.0;\n        double bnu = sgn * pr->b[dir];\n        double gam = DT"),
+    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double gam = DT",
+     "double sgn = 1.0;\n        double gam = DT"),
     ("Gauss weight", "w[i] = 1.0 / ((1.0 - t * t) * dP[m] * dP[m]);", "w[i] = 2.0 / ((1.0 - t * t) * dP[m] * dP[m]);"),
     ("Dirichlet data sign in the right hand side", "- DT * dnv * g + gam * g * v", "+ DT * dnv * g + gam * g * v"),
     ("reaction dropped", "pr->c * uq * ph[i]", "0.0 * pr->c * uq * ph[i]"),
     ("harmonic mean replaced by arithmetic mean", "return 2.0 * a * b / (a + b);", "return 0.5 * (a + b);"),
     ("face weight swapped", "double wm = Dp / (Dm + Dp), wp = Dm / (Dm + Dp);",
      "double wm = Dm / (Dm + Dp), wp = Dp / (Dm + Dp);"),
+    ("periodic wrap dropped", "if (pr->periodic[dir]) nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];",
+     "if (0) nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];"),
+    ("periodic wrap off by one", "nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];",
+     "nic[dir] = (nic[dir] + pr->n[dir] + 1) % pr->n[dir];"),
+    ("interior face velocity ignored", "double bnu = bfp ? bfp[p] : pr->b[dir];", "double bnu = pr->b[dir];"),
+    ("volume velocity component", "pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + r]",
+     "pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + 0]"),
 ]
 
 
@@ -44,6 +52,10 @@ def _pin_checks():
     yield lambda: pins.test_global_conservation((1.0, 0.5, 0.25))
     yield pins.test_reaction_term_is_mass_matrix
     yield pins.test_rhs_constant_source
+    yield lambda: tpins.test_periodic_matches_kronecker_closed_form((1, 0, 0))
+    yield tpins.test_constant_field_given_at_points_equals_constant_velocity
+    yield tpins.test_periodic_transport_conserves_mass_exactly
+    yield tpins.test_periodic_translation_invariance
 
 
 @pytest.mark.parametrize("name,orig,mutated", MUTANTS, ids=[m[0] for m in MUTANTS])
