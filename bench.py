@@ -381,6 +381,66 @@ def learned_benchmark(rtol=1e-8, fp64_cap_s=60.0, pairs=20000, epochs=60):
     return out
 
 
+def transport_benchmark(n=64, k=5, steps=10, warmup=3):
+    """The transport example of Sec. 5.3 at single-GPU scale: Taylor-Green flow on the periodic cube
+    (-pi, pi)^3, D = 5e-6, c = f = 0, q = 2p+4 (m = k+3 Gauss points), Heun's method from the projected
+    Gaussian bump.  One step = two Runge-Kutta stages = two operator applications with the stage update
+    fused into the face kernel (dg_ssprk2)."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10885_gb300 import dg, flops, inputs
+    w = inputs.taylor_green(n, k)
+    t0 = time.time()
+    op = dg.operator_for(w)
+    setup_s = time.time() - t0
+    xi = (np.polynomial.legendre.leggauss(w.m)[0] + 1.0) / 2.0
+    u0 = inputs.gaussian_bump_grid(w, xi, xp=torch, device="cuda")
+    z = op.project(u0.contiguous())
+    del u0
+    stream = torch.cuda.current_stream()
+    h = 2 * np.pi / n
+    dt = 0.3 * h / (2 * k + 1)  # CFL with max |b| = 1
+    mass0 = z.view(w.ncell, -1)[:, 0].sum().item()
+    op.ssprk2(z, dt, warmup)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    op.ssprk2(z, dt, steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    mass1 = z.view(w.ncell, -1)[:, 0].sum().item()
+    # per-kernel times of one operator application (cell kernel; face kernel with the residual epilogue)
+    r = torch.empty_like(z)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
+    for i in range(steps):
+        ev[3 * i].record(stream)
+        op.apply_stage(0, z, r, residual=True)
+        ev[3 * i + 1].record(stream)
+        op.apply_stage(1, z, r, residual=True)
+        ev[3 * i + 2].record(stream)
+    torch.cuda.synchronize()
+    cell_ms = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(steps)) / steps
+    face_ms = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(steps)) / steps
+    N, M = k + 1, w.m
+    cell_fl = flops.cell_kernel_flops(N, M, vb=True) * w.ncell
+    face_fl = flops.face_kernel_flops(N, M=M, stage=True) * w.ncell
+    finite = bool(torch.isfinite(z).all().item())
+    op.close()
+    return {"workload": w.name, "cells": [n, n, n], "k": k, "m": M, "dofs": w.ndof, "dt": dt,
+            "ms_per_heun_step": ms, "heun_steps_per_s": 1e3 / ms,
+            "mdofs_per_stage": 2 * w.ndof / (ms * 1e-3) / 1e6,
+            "mdof_steps_per_s": w.ndof / (ms * 1e-3) / 1e6,
+            "kernels_ms": {"dg_cell_kernel<vb>": cell_ms, "dg_face_kernel<vb>": face_ms},
+            "cell_kernel_fp64_frac": cell_fl / (cell_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "executed_flops_per_dof_stage": (cell_fl + face_fl) / w.ndof,
+            "fp64_tflops_executed": 2 * (cell_fl + face_fl) / (ms * 1e-3) / 1e12,
+            "mass_drift_rel": abs(mass1 - mass0) / abs(mass0), "finite": finite, "setup_s": setup_s,
+            "paper_context": "240^3 p=5 (3e9 DOF), 165000 steps in 143000 core-h on 6144 cores incl. I/O "
+                             "(Sec. 5.3): about 5.9e3 MDOF-steps/s for that machine"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -530,6 +590,8 @@ def run_ours(args):
     }
     if ws == 1 and not args.no_batch:
         line["batch"] = batch_benchmark()
+    if ws == 1 and not args.no_transport:
+        line["transport"] = transport_benchmark()
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -546,6 +608,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
+    ap.add_argument("--no-transport", action="store_true", help="skip the Taylor-Green transport section")
+    ap.add_argument("--transport", type=int, default=None, metavar="N",
+                    help="print only the Taylor-Green transport benchmark on N^3 cells (k = 5, m = 8)")
     ap.add_argument("--solve-only", nargs="?", const="all", default=None, choices=["all", "mixed", "learned"],
                     help="print the solver comparisons only (mixed precision at 48^3 Q5, learned at 64^3 Q4)")
     ap.add_argument("--profile-solver", action="store_true",
@@ -561,6 +626,11 @@ def main():
         run_reference(args)
     elif args.profile:
         run_profile(args)
+    elif args.transport:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"transport": transport_benchmark(n=args.transport, steps=args.steps,
+                                                           warmup=args.warmup)}), flush=True)
     elif args.solve_only:
         import torch
         torch.cuda.set_device(0)

@@ -328,6 +328,57 @@ int dg_batch_destroy(dg_batch* b);
 int dg_apply_jacobian_static(const dg_mesh* mesh, int32_t k, const double* D_dev, const double b[3], double c,
                              double sigma, const double* z_dev, double* y_dev, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Transport problems (Sec. 5.3): periodic axes, a flow field b(x), the q = 2p+4 quadrature rule,
+ * and explicit strong-stability-preserving Runge-Kutta time stepping (Sec. 2, "ODE": the basis is
+ * L2-orthogonal, so the mass matrix is |T| I and M^{-1} is a scaling).
+ * --------------------------------------------------------------------------------------------- */
+enum { DG_VELOCITY_CONSTANT = 0, DG_VELOCITY_POINTS = 1, DG_VELOCITY_TAYLOR_GREEN = 2 };
+
+typedef struct {
+  int32_t periodic[3];  /* 1: the axis wraps around; its two end faces are one interior face between the
+                           last and the first cell (no Dirichlet data there)                          */
+  int32_t m;            /* Gauss points per direction: 0 or k+1 (q = 2p), or k+3 (q = 2p+4, Sec. 5.3).
+                           f_qp, g_qp and dg_quadrature_points then use m points per direction.        */
+  int32_t velocity;     /* DG_VELOCITY_CONSTANT: coeffs->b.
+                           DG_VELOCITY_POINTS: b_qp and b_face below (coeffs->b is ignored).
+                           DG_VELOCITY_TAYLOR_GREEN: the fixed flow field of Sec. 5.3,
+                             b = (cos x1 sin(-x2) sin(-x3), sin x1 cos(-x2) sin(-x3) / 2,
+                                  sin x1 sin(-x2) cos(-x3) / 2),
+                           evaluated on the device at the quadrature points with CUDA's sin and cos.  */
+  const double* b_qp;   /* POINTS: host [ncells][m^3][3], b at the volume points (layout of f_qp)      */
+  const double* b_face; /* POINTS: host [ncells][6][m^2], b . e_dir at the points of face 2*dir+side
+                           of each cell (points p = p_a + m*p_b over the tangential axes a < b).  An
+                           interior face uses the value given for its lower cell's upper face for both
+                           cells, so the two sides see one flux.                                       */
+} dg_setup_ext;
+
+/* dg_setup with the options above (ext = NULL is dg_setup).  A field b(x) or m = k+3 selects the
+ * velocity field kernels, which support degrees 1..8 and DG_F64 applies only (DG_F32 / DG_F64X
+ * applies, the mixed-precision solver, block-Jacobi and batches reject such a handle).  On a periodic
+ * axis with a single cell the cell is its own neighbour.  Synchronises `stream`. */
+int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* coeffs, const dg_bc* bc, const double* f_qp,
+                const dg_setup_ext* ext, void* stream, dg_handle** out);
+
+/* L2 projection of a function given at the volume points onto the DG space (the initial value of a
+ * time-dependent run): z_i = (u0, phi_i)_T / |T|, computed with the handle's quadrature rule.
+ * u_qp_dev: device [ncells][m^3]; z_dev: device FP64 DOF vector. */
+int dg_project(dg_handle* h, const double* u_qp_dev, double* z_dev, void* stream);
+
+/* One explicit Runge-Kutta stage (Sec. 2, "ODE", with M = |T| I):
+ *     y = cz * z0 + cu * u - cdt * M^{-1} (A u - F)
+ * fused into the operator's face kernel.  F is the right hand side of the handle (f and g do not
+ * depend on time here).  u, z0, y are FP64 device vectors; y may alias u or z0 (every element is
+ * read before it is written, by the same thread). */
+int dg_rk_stage(dg_handle* h, const double* u_dev, const double* z0_dev, double* y_dev, double cz, double cu,
+                double cdt, void* stream);
+
+/* nsteps steps of Heun's method, the second-order strong-stability-preserving Runge-Kutta scheme of
+ * Sec. 5.3, on z_dev in place:  z1 = z - dt M^{-1}(A z - F);  z <- (z + z1 - dt M^{-1}(A z1 - F)) / 2.
+ * Four kernel launches per step; the stage vector is kept by the handle (allocated on the first
+ * call, which then synchronises `stream`). */
+int dg_ssprk2(dg_handle* h, double* z_dev, double dt, int32_t nsteps, void* stream);
+
 /* Message for the calling thread's last error ("" if none). */
 const char* dg_last_error(void);
 

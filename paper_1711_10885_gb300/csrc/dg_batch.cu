@@ -62,6 +62,9 @@ __device__ __forceinline__ dgk::FaceArgs<double> face_args(const Problem& p) {
   for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
   fa.y = p.y;
   fa.mode = p.mode;
+  fa.u = nullptr;
+  fa.z0 = nullptr;
+  fa.cz = fa.cu = fa.cr = 0.0;
   return fa;
 }
 
@@ -116,10 +119,12 @@ dg_batch_face_kernel(const __grid_constant__ Tabs tabs, const Problem* __restric
     switch (p.N * 2 + tl.variant) {
 #define X(NV, TB)                                                                                        \
   case 2 * NV:                                                                                           \
-    dgk::face_tile<NV, double, false, Cpb<NV>::FULL>(tabs.TB, p.geo, fa, tl.cell0, tl.here, 0, smem);   \
+    dgk::face_tile<NV, double, false, Cpb<NV>::FULL, double, NV, false, true>(tabs.TB, p.geo, fa, tl.cell0,  \
+                                                                              tl.here, 0, smem);         \
     break;                                                                                               \
   case 2 * NV + 1:                                                                                       \
-    dgk::face_tile<NV, double, false, Cpb<NV>::HALF>(tabs.TB, p.geo, fa, tl.cell0, tl.here, 0, smem);   \
+    dgk::face_tile<NV, double, false, Cpb<NV>::HALF, double, NV, false, true>(tabs.TB, p.geo, fa, tl.cell0,  \
+                                                                              tl.here, 0, smem);         \
     break;
       DG_BATCH_CASES(X)
 #undef X
@@ -240,8 +245,9 @@ int dg_batch_create(dg_handle* const* hs, int32_t count, void* stream, dg_batch*
   int dev = -1;
   cudaGetDevice(&dev);
   for (int i = 0; i < count; ++i)
-    if (!hs[i] || hs[i]->N < dgbt::NMIN || hs[i]->N > dgbt::NMAX || hs[i]->device != dev) {
-      set_error("dg_batch_create: every handle must exist, live on the current device and have 1 <= k <= 8");
+    if (!hs[i] || hs[i]->N < dgbt::NMIN || hs[i]->N > dgbt::NMAX || hs[i]->device != dev || hs[i]->vb) {
+      set_error("dg_batch_create: every handle must exist, live on the current device, have 1 <= k <= 8, a "
+                "constant velocity and m = k+1");
       return DG_ERR_INVALID_ARG;
     }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -251,7 +257,7 @@ int dg_batch_create(dg_handle* const* hs, int32_t count, void* stream, dg_batch*
   {
     dgi::Tables1D t;
 #define X(NV, TB)                              \
-  dgi::build_tables(NV, &t);                   \
+  dgi::build_tables(NV, NV, &t);                 \
   b->tabs.TB = dgi::make_tab<NV, double>(t);
     DG_BATCH_CASES(X)
 #undef X

@@ -35,59 +35,61 @@ static void shifted_legendre(int jmax, double x, double* p, double* dp) {
   }
 }
 
-// Gauss-Legendre nodes/weights on [0,1] (Sec. 3.1) and the 1D matrices of the kernels.
-void build_tables(int N, Tables1D* tb) {
+// Gauss-Legendre nodes/weights on [0,1] with M points (Sec. 3.1) and the 1D matrices of the kernels for
+// N = k+1 modes.
+void build_tables(int N, int M, Tables1D* tb) {
   tb->N = N;
-  double p[MAXN + 2], dp[MAXN + 2];
-  // Newton on P_N(2x-1) for the lower half of the nodes; the rule is symmetric about 1/2, and the
+  tb->M = M;
+  double p[MAXM + 2], dp[MAXM + 2];
+  // Newton on P_M(2x-1) for the lower half of the nodes; the rule is symmetric about 1/2, and the
   // kernels rely on that symmetry exactly (even-odd form), so the upper half is mirrored
-  for (int i = 0; i < (N + 1) / 2; ++i) {
-    double x = 0.5 * (1.0 - std::cos(M_PI * (i + 0.75) / (N + 0.5)));
-    if (2 * i + 1 == N) {
+  for (int i = 0; i < (M + 1) / 2; ++i) {
+    double x = 0.5 * (1.0 - std::cos(M_PI * (i + 0.75) / (M + 0.5)));
+    if (2 * i + 1 == M) {
       x = 0.5;
     } else {
       for (int it = 0; it < 60; ++it) {
-        shifted_legendre(N, x, p, dp);
-        const double dx = p[N] / dp[N];
+        shifted_legendre(M, x, p, dp);
+        const double dx = p[M] / dp[M];
         x -= dx;
         if (std::fabs(dx) < 1e-16) break;
       }
     }
-    shifted_legendre(N, x, p, dp);
+    shifted_legendre(M, x, p, dp);
     tb->xi[i] = x;
-    tb->w[i] = 1.0 / (x * (1.0 - x) * dp[N] * dp[N]);
-    tb->xi[N - 1 - i] = 1.0 - x;
-    tb->w[N - 1 - i] = tb->w[i];
+    tb->w[i] = 1.0 / (x * (1.0 - x) * dp[M] * dp[M]);
+    tb->xi[M - 1 - i] = 1.0 - x;
+    tb->w[M - 1 - i] = tb->w[i];
   }
-  // theta_j(x) = sqrt(2j+1) P_j(2x-1): values / derivatives at the nodes and at the end points
-  double th[MAXN][MAXN], dth[MAXN][MAXN], te[2][MAXN], dte[2][MAXN];
-  for (int i = 0; i < N; ++i) {
-    shifted_legendre(N - 1, tb->xi[i], p, dp);
-    for (int j = 0; j < N; ++j) {
+  // theta_j(x) = sqrt(2j+1) P_j(2x-1), j < M: values / derivatives at the nodes and at the end points
+  double th[MAXM][MAXM], dth[MAXM][MAXM], te[2][MAXM], dte[2][MAXM];
+  for (int i = 0; i < M; ++i) {
+    shifted_legendre(M - 1, tb->xi[i], p, dp);
+    for (int j = 0; j < M; ++j) {
       th[i][j] = std::sqrt(2.0 * j + 1.0) * p[j];
       dth[i][j] = std::sqrt(2.0 * j + 1.0) * dp[j];
     }
   }
   for (int s = 0; s < 2; ++s) {
-    shifted_legendre(N - 1, (double)s, p, dp);
-    for (int j = 0; j < N; ++j) {
+    shifted_legendre(M - 1, (double)s, p, dp);
+    for (int j = 0; j < M; ++j) {
       te[s][j] = std::sqrt(2.0 * j + 1.0) * p[j];
       dte[s][j] = std::sqrt(2.0 * j + 1.0) * dp[j];
     }
   }
-  for (int i = 0; i < N; ++i)
+  for (int i = 0; i < M; ++i)
     for (int j = 0; j < N; ++j) tb->A[i][j] = th[i][j];
-  // Lagrange basis on the Gauss points through the orthonormal expansion
-  //   l_l(x) = sum_j theta_j(x) theta_j(xi_l) w_l   (exact: the N-point rule integrates degree 2N-1)
-  for (int l = 0; l < N; ++l) {
-    for (int i = 0; i < N; ++i) {
+  // Lagrange basis on the M Gauss points through the orthonormal expansion
+  //   l_l(x) = sum_{j<M} theta_j(x) theta_j(xi_l) w_l   (exact: the M-point rule integrates degree 2M-1)
+  for (int l = 0; l < M; ++l) {
+    for (int i = 0; i < M; ++i) {
       double acc = 0.0;
-      for (int j = 0; j < N; ++j) acc += dth[i][j] * th[l][j];
+      for (int j = 0; j < M; ++j) acc += dth[i][j] * th[l][j];
       tb->Dt[i][l] = acc * tb->w[l];
     }
     for (int s = 0; s < 2; ++s) {
       double av = 0.0, ad = 0.0;
-      for (int j = 0; j < N; ++j) {
+      for (int j = 0; j < M; ++j) {
         av += te[s][j] * th[l][j];
         ad += dte[s][j] * th[l][j];
       }
@@ -144,6 +146,9 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->work_tr);
   cudaFree(h->bj64);
   cudaFree(h->bj32);
+  cudaFree(h->bsc);
+  cudaFree(h->bface);
+  cudaFree(h->rk_tmp);
   cudaFree(h->ws);
   if (h->ws_host) cudaFreeHost(h->ws_host);
   delete h;
@@ -163,6 +168,11 @@ int dg_sizes(const dg_handle* h, int64_t* ncells, int32_t* dofs_per_cell, int64_
 
 int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* bc, const double* f_qp,
              void* stream, dg_handle** out) {
+  return dg_setup_ex(mesh, k, co, bc, f_qp, nullptr, stream, out);
+}
+
+int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* bc, const double* f_qp,
+                const dg_setup_ext* ext, void* stream, dg_handle** out) {
   if (!out) {
     set_error("dg_setup: out is null");
     return DG_ERR_INVALID_ARG;
@@ -198,6 +208,33 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
     set_error("dg_setup: c must be finite and sigma finite and >= 0");
     return DG_ERR_INVALID_ARG;
   }
+  const int M = (ext && ext->m) ? ext->m : k + 1;
+  const int velocity = ext ? ext->velocity : DG_VELOCITY_CONSTANT;
+  if (M != k + 1 && M != k + 3) {
+    set_error("dg_setup: m must be k+1 or k+3 Gauss points per direction");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (velocity != DG_VELOCITY_CONSTANT && velocity != DG_VELOCITY_POINTS && velocity != DG_VELOCITY_TAYLOR_GREEN) {
+    set_error("dg_setup: unknown velocity kind");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (velocity == DG_VELOCITY_POINTS && (!ext->b_qp || !ext->b_face)) {
+    set_error("dg_setup: DG_VELOCITY_POINTS needs b_qp and b_face");
+    return DG_ERR_INVALID_ARG;
+  }
+  const bool vb = velocity != DG_VELOCITY_CONSTANT || M != k + 1;
+  if (vb && k > 8) {
+    set_error("dg_setup: a velocity field or m = k+3 needs degree k <= 8");
+    return DG_ERR_INVALID_ARG;
+  }
+  int periodic[3] = {0, 0, 0};
+  for (int r = 0; r < 3; ++r) {
+    if (ext && ext->periodic[r] != 0 && ext->periodic[r] != 1) {
+      set_error("dg_setup: periodic flags must be 0 or 1");
+      return DG_ERR_INVALID_ARG;
+    }
+    periodic[r] = ext ? ext->periodic[r] : 0;
+  }
   std::vector<double> D(ncell);
   for (int64_t i = 0; i < ncell; ++i) {
     D[i] = co->D_cell ? co->D_cell[i] : co->D_const;
@@ -225,11 +262,15 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
   }
   h->c = co->c;
   h->sigma = co->sigma;
-  build_tables(h->N, &h->tab);
+  h->M = M;
+  h->vb = vb;
+  for (int r = 0; r < 3; ++r) h->periodic[r] = periodic[r];
+  build_tables(h->N, M, &h->tab);
 
   const int N = h->N;
   const int64_t nb = (int64_t)N * N * N;
   const int64_t ndof = ncell * nb;
+  const int64_t npts = ncell * M * M * M;  // volume quadrature points
   // face coefficients per cell and face (Sec. 2: weights w+- = delta-+/(delta- + delta+), gamma_F)
   std::vector<double> fc(ncell * 18);
   for (int64_t cell = 0; cell < ncell; ++cell) {
@@ -240,13 +281,18 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
         double* c3 = &fc[(cell * 6 + 2 * dir + side) * 3];
         const double hq = h->h[dir];
         const double Do = D[cell];
-        const bool boundary = side ? ic[dir] == h->n[dir] - 1 : ic[dir] == 0;
+        const bool at_end = side ? ic[dir] == h->n[dir] - 1 : ic[dir] == 0;
+        const bool boundary = at_end && !h->periodic[dir];
         if (boundary) {
           c3[0] = Do / hq;
           c3[1] = 0.0;
           c3[2] = Do * h->sigma / hq;  // delta- sigma |F| / |T-|
         } else {
-          const double Dn = D[side ? cell + strides[dir] : cell - strides[dir]];
+          // the neighbour; across the end faces of a periodic axis it is the cell at the other end
+          const int64_t wrap = (int64_t)(h->n[dir] - 1) * strides[dir];
+          const int64_t nbr = side ? (at_end ? cell - wrap : cell + strides[dir])
+                                   : (at_end ? cell + wrap : cell - strides[dir]);
+          const double Dn = D[nbr];
           const double sum = Do + Dn;
           c3[0] = (Dn / sum) * Do / hq;  // w_own D_own / h
           c3[1] = (Do / sum) * Dn / hq;  // w_nbr D_nbr / h
@@ -280,8 +326,8 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
     DG_TRY(cudaMalloc(&h->p64.F, ndof * sizeof(double)), "cudaMalloc(F)");
     DG_TRY(cudaMalloc(&h->p32.F, ndof * sizeof(float)), "cudaMalloc(F32)");
     DG_TRY(cudaMalloc(&h->pX.F, ndof * sizeof(dgk::dfl)), "cudaMalloc(F pairs)");
-    DG_TRY(cudaMalloc(&h->work_V, ndof * sizeof(double)), "cudaMalloc(work V)");
-    DG_TRY(cudaMalloc(&h->work_tr, ncell * 12 * N * N * sizeof(double)), "cudaMalloc(work traces)");
+    DG_TRY(cudaMalloc(&h->work_V, npts * sizeof(double)), "cudaMalloc(work V)");
+    DG_TRY(cudaMalloc(&h->work_tr, ncell * 12 * M * M * sizeof(double)), "cudaMalloc(work traces)");
     DG_TRY(cudaMemcpyAsync(h->p64.D, D.data(), ncell * sizeof(double), cudaMemcpyHostToDevice, s), "copy D");
     DG_TRY(cudaMemcpyAsync(h->p32.D, D32.data(), ncell * sizeof(float), cudaMemcpyHostToDevice, s), "copy D32");
     DG_TRY(cudaMemcpyAsync(h->p64.fc, fc.data(), ncell * 18 * sizeof(double), cudaMemcpyHostToDevice, s), "copy fc");
@@ -290,17 +336,22 @@ int dg_setup(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc* b
     DG_TRY(cudaMemcpyAsync(h->pX.D, DX.data(), ncell * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s), "copy D pairs");
     DG_TRY(cudaMemcpyAsync(h->pX.fc, fcX.data(), ncell * 18 * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s),
            "copy fc pairs");
+    // velocity field tables (before the right hand side, whose inflow terms read b . nu)
+    if (vb) {
+      rc = setup_velocity(h, velocity, co->b, ext ? ext->b_qp : nullptr, ext ? ext->b_face : nullptr, s);
+      if (rc != DG_OK) goto fail;
+    }
     // right hand side: f at the volume points goes through the work buffer
     if (f_qp) {
-      DG_TRY(cudaMemcpyAsync(h->work_V, f_qp, ndof * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
+      DG_TRY(cudaMemcpyAsync(h->work_V, f_qp, npts * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
     } else {
-      DG_TRY(cudaMemsetAsync(h->work_V, 0, ndof * sizeof(double), s), "memset f");
+      DG_TRY(cudaMemsetAsync(h->work_V, 0, npts * sizeof(double), s), "memset f");
     }
     int64_t gsize[6];
     for (int sd = 0; sd < 6; ++sd) {
       const int dir = sd / 2, ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
-      gsize[sd] = (int64_t)h->n[ta] * h->n[tb] * N * N;
-      if (bc && bc->g_qp[sd]) {
+      gsize[sd] = (int64_t)h->n[ta] * h->n[tb] * M * M;
+      if (bc && bc->g_qp[sd] && !h->periodic[dir]) {
         DG_TRY(cudaMalloc(&gdev[sd], gsize[sd] * sizeof(double)), "cudaMalloc(g)");
         DG_TRY(cudaMemcpyAsync(gdev[sd], bc->g_qp[sd], gsize[sd] * sizeof(double), cudaMemcpyHostToDevice, s),
                "copy g");
@@ -336,7 +387,7 @@ int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
     set_error("dg_quadrature_points: bad arguments");
     return DG_ERR_INVALID_ARG;
   }
-  const int N = h->N;
+  const int N = h->M;  // points per direction
   const double* x = h->tab.xi;
   size_t o = 0;
   if (which == 0) {
@@ -380,6 +431,10 @@ static int check_apply(dg_handle* h, const void* in, void* out, int32_t precisio
   }
   if (precision != DG_F64 && precision != DG_F32 && precision != DG_F64X) {
     set_error(std::string(name) + ": precision must be DG_F64, DG_F32 or DG_F64X");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (h->vb && precision != DG_F64) {
+    set_error(std::string(name) + ": a handle with a velocity field or m = k+3 applies in DG_F64 only");
     return DG_ERR_INVALID_ARG;
   }
   int dev = -1;
@@ -431,7 +486,7 @@ int dg_apply_stage(dg_handle* h, int32_t stage, const void* in, void* out, int32
 }
 
 int dg_rhs(dg_handle* h, void* F, int32_t precision, void* stream) {
-  if (!h || !F || (precision != DG_F64 && precision != DG_F32)) {
+  if (!h || !F || (precision != DG_F64 && precision != DG_F32) || (h->vb && precision != DG_F64)) {
     set_error("dg_rhs: bad arguments");
     return DG_ERR_INVALID_ARG;
   }

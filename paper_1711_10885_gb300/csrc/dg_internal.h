@@ -11,14 +11,15 @@
 namespace dgi {
 
 constexpr int MAXN = DG_MAX_DEGREE + 1;
+constexpr int MAXM = MAXN + 2;  // Gauss points per direction: k+1 (q = 2p) or k+3 (q = 2p+4)
 
-// 1D tables in FP64 for n = m = N points/modes (Sec. 3.1), computed once per handle
+// 1D tables in FP64 for N modes and M Gauss points (Sec. 3.1), computed once per handle
 struct Tables1D {
-  int N;
-  double xi[MAXN], w[MAXN];      // Gauss-Legendre nodes / weights on [0,1]
-  double A[MAXN][MAXN];          // A[i][j] = theta_j(xi_i)
-  double Dt[MAXN][MAXN];         // Dt[i][l] = l_l'(xi_i)
-  double L[2][MAXN], P[2][MAXN]; // l_l(s), l_l'(s) for s = 0, 1
+  int N, M;
+  double xi[MAXM], w[MAXM];      // Gauss-Legendre nodes / weights on [0,1]
+  double A[MAXM][MAXN];          // A[i][j] = theta_j(xi_i)
+  double Dt[MAXM][MAXM];         // Dt[i][l] = l_l'(xi_i), Lagrange basis on the M points
+  double L[2][MAXM], P[2][MAXM]; // l_l(s), l_l'(s) for s = 0, 1
 };
 
 struct Buffers {
@@ -31,7 +32,15 @@ struct Buffers {
 
 struct dg_handle {
   int k = 0, N = 0;
+  int M = 0;                 // Gauss points per direction (N or N + 2)
   int n[3] = {0, 0, 0};
+  int periodic[3] = {0, 0, 0};
+  // velocity field kernels (a field b(x) or M != N; FP64 only): pre-scaled volume velocity
+  // [ncell][3][M][M^2] and normal velocity at the face points [ncell][6][M^2] (layouts of dgk::Geo)
+  bool vb = false;
+  void* bsc = nullptr;
+  void* bface = nullptr;
+  void* rk_tmp = nullptr;    // Runge-Kutta stage vector (FP64, allocated by the first dg_ssprk2 call)
   int64_t ncell = 0;
   double lo[3], hi[3], h[3];
   double b[3] = {0, 0, 0};
@@ -39,8 +48,8 @@ struct dg_handle {
   dgi::Tables1D tab;
   dgi::Buffers p64, p32;   // FP64 and FP32 copies of the coefficient data
   dgi::Buffers pX;         // double-float copies (D and face coefficients; F is read from p64)
-  void* work_V = nullptr;  // point-space residual scratch [ncell][N^3] (sized for FP64)
-  void* work_tr = nullptr; // face trace scratch [ncell][6][2][N^2] (sized for FP64)
+  void* work_V = nullptr;  // point-space residual scratch [ncell][M^3] (sized for FP64)
+  void* work_tr = nullptr; // face trace scratch [ncell][6][2][M^2] (sized for FP64)
   int device = 0;
   // block-Jacobi preconditioner: per cell (A_TT^{-1})^T, row-major [ncell][N^3][N^3], FP64 and FP32
   void* bj64 = nullptr;
@@ -54,8 +63,8 @@ struct dg_handle {
 namespace dgi {
 
 void set_error(const std::string& msg);
-// Gauss-Legendre nodes/weights and the 1D matrices for N = k+1 (host, FP64)
-void build_tables(int N, Tables1D* tb);
+// Gauss-Legendre nodes/weights (M points) and the 1D matrices for N = k+1 modes (host, FP64)
+void build_tables(int N, int M, Tables1D* tb);
 int cuda_fail(cudaError_t e, const char* what);
 
 // mode 0: y = A z, mode 1: y = A z - F; stages: bit 0 cell kernel, bit 1 face kernel (3 = full apply)
@@ -68,7 +77,24 @@ int launch_diag_blocks_f64(const dg_handle* h, double* out, int cell_base, int n
 // block-Jacobi application z = M r (precision by type), M from dg_precond_setup
 int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s);
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
-// F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null)
-int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s);
+// F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null);
+// with vol = 1 instead of |T| and no g this is the L2 projection z_i = (f, phi_i)_T / |T|
+int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,
+                   bool project = false);
+// explicit Runge-Kutta stage y = cz z0 + cu u - cr (A u - F) (mode 3 of the face kernel)
+struct StageArgs {
+  const double* z0;
+  double cz, cu, cr;
+};
+int launch_stage_f64(const dg_handle* h, const double* u, double* y, const StageArgs& st, cudaStream_t s);
+// velocity field tables of a vb handle (allocates h->bsc and h->bface): kind DG_VELOCITY_*, the constant b,
+// or host arrays b_qp [ncell][M^3][3] and b_face [ncell][6][M^2]
+int setup_velocity(dg_handle* h, int kind, const double b[3], const double* b_qp, const double* b_face,
+                   cudaStream_t s);
+// the velocity field kernels (h->vb): same launches for the FP64 operator
+int launch_apply_f64_vb(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+                        cudaStream_t s);
+int launch_rhs_f64_vb(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,
+                      bool project);
 
 }  // namespace dgi

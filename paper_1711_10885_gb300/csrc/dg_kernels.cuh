@@ -30,35 +30,49 @@
 // two half-size blocks acting on the symmetric and antisymmetric parts of the
 // line.  That is the same product with about 40 % fewer FP64 operations, which
 // is what bounds these kernels on GB300 (FP64 issue rate, not memory).
+//
+// N = k+1 basis functions and M Gauss points per direction.  M = N is the rule
+// of the benchmark problems (q = 2p); M = N+2 is the q = 2p+4 rule of the
+// transport example (Sec. 5.3).  With M > N the first passes map N modal
+// values to M points and the last ones map M points back to N test functions;
+// everything in between (collocation derivative, face extrapolation, lifting)
+// works on M-point lines, which is exact because a degree-k polynomial is its
+// own interpolant on M > k points.  VB = true reads the velocity at every
+// quadrature point (a flow field b(x), Sec. 5.3) instead of one constant b.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "dg_dfloat.cuh"
 
 namespace dgk {
 
-// 1D tables for n = m = N (Sec. 3.1), in even-odd form.  H = floor(N/2) point pairs, C = ceil(N/2).
-template <int N, typename T>
-struct Tab {
-  static constexpr int H = N / 2, C = (N + 1) / 2;
-  // basis at the points A[i][j] = theta_j(xi_i): AE[i][e] = A[i][2e] (i < C), AO[i][o] = A[i][2o+1] (i < H)
-  T AE[C][C];
-  T AO[C][H];
-  // collocation derivative M[i][l] = l_l'(xi_i) (Lagrange basis on the Gauss points) and the weighted
-  // transpose B[l][i] = w_i M[i][l]; both satisfy X[N-1-i][N-1-l] = -X[i][l].  Half blocks:
-  //   XHm[i][l] = (X[i][l] - X[i][N-1-l]) / 2  (i < C, l < H),  XHp[i][l] = (X[i][l] + X[i][N-1-l]) / 2  (i < H, l < C)
-  T DHm[C][H];
-  T DHp[H][C];
-  T BHm[C][H];
-  T BHp[H][C];
+// 1D tables for N = k+1 modes and M Gauss points (Sec. 3.1), in even-odd form.  HN = floor(N/2),
+// CN = ceil(N/2), and HM, CM likewise for the M points (point pairs i, M-1-i, and the middle point).
+template <int N, int M, typename T>
+struct TabNM {
+  static constexpr int HN = N / 2, CN = (N + 1) / 2, HM = M / 2, CM = (M + 1) / 2;
+  // basis at the points A[i][j] = theta_j(xi_i): AE[i][e] = A[i][2e] (i < CM), AO[i][o] = A[i][2o+1] (i < HM)
+  T AE[CM][CN];
+  T AO[HM][HN];
+  // collocation derivative X[i][l] = l_l'(xi_i) (Lagrange basis on the M Gauss points) and the weighted
+  // transpose B[l][i] = w_i X[i][l]; both satisfy X[M-1-i][M-1-l] = -X[i][l].  Half blocks:
+  //   XHm[i][l] = (X[i][l] - X[i][M-1-l]) / 2  (i < CM, l < HM),  XHp[i][l] = (X[i][l] + X[i][M-1-l]) / 2  (i < HM, l < CM)
+  T DHm[CM][HM];
+  T DHp[HM][CM];
+  T BHm[CM][HM];
+  T BHp[HM][CM];
   // face extrapolation from a point line: value/derivative at xi = 1 are LS.s + LD.d and PS.s + PD.d,
   // at xi = 0 they are LS.s - LD.d and -PS.s + PD.d (s, d: symmetric / antisymmetric parts)
-  T LS[C], LD[H], PS[C], PD[H];
-  T w[N];     // Gauss weights on [0,1]
-  T L[2][N];  // L[s][l] = l_l(s): lift of a face value onto the normal line
-  T P[2][N];  // P[s][l] = l_l'(s): lift of a face normal-derivative weight
+  T LS[CM], LD[HM], PS[CM], PD[HM];
+  T w[M];     // Gauss weights on [0,1]
+  T L[2][M];  // L[s][l] = l_l(s): lift of a face value onto the normal line
+  T P[2][M];  // P[s][l] = l_l'(s): lift of a face normal-derivative weight
 };
+template <int N, typename T>
+using Tab = TabNM<N, N, T>;
 
 template <typename T>
 struct Geo {
@@ -70,6 +84,14 @@ struct Geo {
   T beta[3];   // -b_r |T| / h_r    (convection weight of u)
   T b[3];      // velocity
   T creact;    // c |T|
+  int periodic[3];  // 1: the two end faces along this axis are one interior face (Sec. 5.3)
+  // velocity field (VB kernels only, else null):
+  //   bsc[((cell*3 + r)*M + l)*M^2 + t] = -b_r(x) |T| / h_r * w_a w_b at the point l of x-line/y-line/z-line t
+  //     (t = a + M b over the two other point indices in increasing axis order)
+  //   bface[(cell*6 + face)*M^2 + t] = b(x) . e_dir at the face points; an interior face takes the value that
+  //     its lower cell (T-) holds for its upper face, so both cells see one flux
+  const T* bsc;
+  const T* bface;
 };
 
 // shared-memory tensor of one cell: element (i1,i2,i3) at i1 + (N+1)*(i2 + N*i3)
@@ -84,6 +106,22 @@ struct Lay {
   }
   __device__ static __forceinline__ int stride(int dir) { return dir == 0 ? 1 : (dir == 1 ? LS : LS * N); }
   __device__ static __forceinline__ int idx(int i1, int i2, int i3) { return i1 + LS * (i2 + N * i3); }
+};
+
+// Lines of the modal (N-long) passes in the M-point cell buffer: the x pass runs over (j2, j3) < N, the y
+// pass over (i1 < M, j3 < N) and the z pass over (i1, i2) < M; with M = N these are the point lines.
+template <int N, int M>
+struct ModalLines {
+  __device__ static __forceinline__ int count(int dir) { return dir == 0 ? N * N : (dir == 1 ? M * N : M * M); }
+  __device__ static __forceinline__ int base(int dir, int t) {
+    if constexpr (M == N) {
+      return Lay<M>::base(dir, t);
+    } else {
+      if (dir == 0) return Lay<M>::idx(0, t % N, t / N);
+      if (dir == 1) return Lay<M>::idx(t % M, 0, t / M);
+      return Lay<M>::base(2, t);
+    }
+  }
 };
 
 // Dot products sum_i a_i b_i: plain FMA chains for float / double; the pair type has its own lazily
@@ -152,50 +190,50 @@ __device__ __forceinline__ void split_sd(const T (&x)[N], T (&s)[(N + 1) / 2], T
 }
 
 // modal -> points along one line: y[i] = sum_j theta_j(xi_i) x[j]   (eq. evalfe, one direction)
-template <int N, typename T>
-__device__ __forceinline__ void eo_fwd(const Tab<N, T>& tb, const T (&x)[N], T (&y)[N]) {
-  constexpr int H = N / 2, C = (N + 1) / 2;
-  T e[C], o[H];
+template <int N, int M, typename T>
+__device__ __forceinline__ void eo_fwd(const TabNM<N, M, T>& tb, const T (&x)[N], T (&y)[M]) {
+  constexpr int HN = N / 2, CN = (N + 1) / 2, HM = M / 2, CM = (M + 1) / 2;
+  T e[CM], o[HM];
 #pragma unroll
-  for (int i = 0; i < C; ++i) {
+  for (int i = 0; i < CM; ++i) {
     typename DotAcc<T>::type acc = dot_begin(tb.AE[i][0], x[0]);
 #pragma unroll
-    for (int k = 1; k < C; ++k) dot_add(acc, tb.AE[i][k], x[2 * k]);
+    for (int k = 1; k < CN; ++k) dot_add(acc, tb.AE[i][k], x[2 * k]);
     e[i] = dot_end(acc);
   }
 #pragma unroll
-  for (int i = 0; i < H; ++i) {
+  for (int i = 0; i < HM; ++i) {
     typename DotAcc<T>::type acc = dot_begin(tb.AO[i][0], x[1]);
 #pragma unroll
-    for (int k = 1; k < H; ++k) dot_add(acc, tb.AO[i][k], x[2 * k + 1]);
+    for (int k = 1; k < HN; ++k) dot_add(acc, tb.AO[i][k], x[2 * k + 1]);
     o[i] = dot_end(acc);
   }
 #pragma unroll
-  for (int i = 0; i < H; ++i) {
+  for (int i = 0; i < HM; ++i) {
     y[i] = e[i] + o[i];
-    y[N - 1 - i] = e[i] - o[i];
+    y[M - 1 - i] = e[i] - o[i];
   }
-  if (N & 1) y[H] = e[H];
+  if (M & 1) y[HM] = e[HM];
 }
 
 // points -> modal along one line: y[j] = sum_i theta_j(xi_i) x[i]   (test functions, eq. evalblf)
-template <int N, typename T>
-__device__ __forceinline__ void eo_bwd(const Tab<N, T>& tb, const T (&x)[N], T (&y)[N]) {
-  constexpr int H = N / 2, C = (N + 1) / 2;
-  T s[C], d[H > 0 ? H : 1];
-  split_sd<N, T>(x, s, d);
+template <int N, int M, typename T>
+__device__ __forceinline__ void eo_bwd(const TabNM<N, M, T>& tb, const T (&x)[M], T (&y)[N]) {
+  constexpr int HN = N / 2, CN = (N + 1) / 2, HM = M / 2, CM = (M + 1) / 2;
+  T s[CM], d[HM];
+  split_sd<M, T>(x, s, d);
 #pragma unroll
-  for (int k = 0; k < C; ++k) {
+  for (int k = 0; k < CN; ++k) {
     typename DotAcc<T>::type acc = dot_begin(tb.AE[0][k], s[0]);
 #pragma unroll
-    for (int i = 1; i < C; ++i) dot_add(acc, tb.AE[i][k], s[i]);
+    for (int i = 1; i < CM; ++i) dot_add(acc, tb.AE[i][k], s[i]);
     y[2 * k] = dot_end(acc);
   }
 #pragma unroll
-  for (int k = 0; k < H; ++k) {
+  for (int k = 0; k < HN; ++k) {
     typename DotAcc<T>::type acc = dot_begin(tb.AO[0][k], d[0]);
 #pragma unroll
-    for (int i = 1; i < H; ++i) dot_add(acc, tb.AO[i][k], d[i]);
+    for (int i = 1; i < HM; ++i) dot_add(acc, tb.AO[i][k], d[i]);
     y[2 * k + 1] = dot_end(acc);
   }
 }
@@ -236,9 +274,10 @@ struct Launch {
   static constexpr int THREADS = CPB * NN;
 };
 
-// copy cpb cells (contiguous in global memory, N^3 each) into padded shared buffers
+// copy cpb cells (contiguous in global memory, N^3 each) into padded shared buffers laid out for M points
+// per direction (the N^3 values take the corner j1, j2, j3 < N)
 // (TV: element type of the vector in global memory, converted to the compute type T on load)
-template <int N, typename T, typename TV>
+template <int N, typename T, typename TV, int M = N>
 __device__ __forceinline__ void gload_cells(T* sbuf, const TV* __restrict__ g, int cell0, int ncells_here) {
   constexpr int N3 = N * N * N;
   const int total = ncells_here * N3;
@@ -246,7 +285,11 @@ __device__ __forceinline__ void gload_cells(T* sbuf, const TV* __restrict__ g, i
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int c = e / N3, r = e - c * N3;
     const int i1 = r % N, i23 = r / N;
-    sbuf[c * Lay<N>::CS + i1 + Lay<N>::LS * i23] = to_compute<T, TV>(src[e]);
+    if constexpr (M == N) {
+      sbuf[c * Lay<M>::CS + i1 + Lay<M>::LS * i23] = to_compute<T, TV>(src[e]);
+    } else {
+      sbuf[c * Lay<M>::CS + Lay<M>::idx(i1, i23 % N, i23 / N)] = to_compute<T, TV>(src[e]);
+    }
   }
 }
 template <int N, typename T>
@@ -261,26 +304,37 @@ __device__ __forceinline__ void gstore_cells(T* __restrict__ g, const T* sbuf, i
   }
 }
 
-// One derivative pass along axis `dir` for the line u (values at the points) owned by this thread:
-// v (+)= B [ w_perp (sa d_r u + sb u) ] and the two face traces of this line.
-template <int N, typename T, bool FIRST>
-__device__ __forceinline__ void deriv_line(const Tab<N, T>& tb, const T (&u)[N], T (&v)[N], T sa, T sb, T sc,
-                                           T* __restrict__ tr, int NN, int t) {
-  constexpr int H = N / 2, C = (N + 1) / 2;
-  T s[C], d[H > 0 ? H : 1], gr[N], X[N];
-  split_sd<N, T>(u, s, d);
-  eo_anti<N, T>(tb.DHm, tb.DHp, s, d, gr);  // d u / d xi_r at the points (reference derivative)
+// One derivative pass along axis `dir` for the line u (values at the M points) owned by this thread:
+// v (+)= B [ w_perp (sa d_r u + sb u) ] and the two face traces of this line.  With VB the convection
+// weight is the point-wise bl[i * M^2] (pre-scaled velocity, see Geo::bsc) instead of the constant sb.
+template <int N, int M, typename T, bool FIRST, bool VB = false>
+__device__ __forceinline__ void deriv_line(const TabNM<N, M, T>& tb, const T (&u)[M], T (&v)[M], T sa, T sb, T sc,
+                                           const T* __restrict__ bl, T* __restrict__ tr, int NN, int t) {
+  constexpr int H = M / 2, C = (M + 1) / 2;
+  T bv[VB ? M : 1];
+  if constexpr (VB) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) X[i] = fma(sa, gr[i], sb * u[i]);  // eq. gauss_points, times w_perp
-  T xs[C], xd[H > 0 ? H : 1], c[N];
-  split_sd<N, T>(X, xs, xd);
-  eo_anti<N, T>(tb.BHm, tb.BHp, xs, xd, c);  // sum_i w_i l_l'(xi_i) X[i]
-  if (FIRST) {
+    for (int i = 0; i < M; ++i) bv[i] = bl[i * M * M];
+  }
+  T s[C], d[H > 0 ? H : 1], gr[M], X[M];
+  split_sd<M, T>(u, s, d);
+  eo_anti<M, T>(tb.DHm, tb.DHp, s, d, gr);  // d u / d xi_r at the points (reference derivative)
+  if constexpr (VB) {
 #pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = fma(sc * tb.w[l], u[l], c[l]);  // + c |T| w u (reaction)
+    for (int i = 0; i < M; ++i) X[i] = fma(sa, gr[i], bv[i] * u[i]);  // eq. gauss_points, b = b(x_i)
   } else {
 #pragma unroll
-    for (int l = 0; l < N; ++l) v[l] += c[l];
+    for (int i = 0; i < M; ++i) X[i] = fma(sa, gr[i], sb * u[i]);  // eq. gauss_points, times w_perp
+  }
+  T xs[C], xd[H > 0 ? H : 1], c[M];
+  split_sd<M, T>(X, xs, xd);
+  eo_anti<M, T>(tb.BHm, tb.BHp, xs, xd, c);  // sum_i w_i l_l'(xi_i) X[i]
+  if (FIRST) {
+#pragma unroll
+    for (int l = 0; l < M; ++l) v[l] = fma(sc * tb.w[l], u[l], c[l]);  // + c |T| w u (reaction)
+  } else {
+#pragma unroll
+    for (int l = 0; l < M; ++l) v[l] += c[l];
   }
   // traces at xi_r = 1 and 0 (value, reference normal derivative), Sec. 3.4
   T t1 = T(0), t2 = T(0), q1 = T(0), q2 = T(0);
@@ -312,12 +366,12 @@ struct SelfArgs {
 };
 
 // Cell-kernel work on one tile of `here` consecutive cells starting at cell0 (virtual cells in SELF mode),
-// run by all threads of the CTA (blockDim.x >= CPB * N^2; threads beyond that only help with copies).
-template <int N, typename T, bool SELF, int CPB, typename TV = T>
-__device__ __forceinline__ void cell_tile(const Tab<N, T>& tb, const Geo<T>& g, const TV* __restrict__ z,
+// run by all threads of the CTA (blockDim.x >= CPB * M^2; threads beyond that only help with copies).
+template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false>
+__device__ __forceinline__ void cell_tile(const TabNM<N, M, T>& tb, const Geo<T>& g, const TV* __restrict__ z,
                                           const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces,
                                           int cell0, int here, int cell_base, unsigned char* smem_raw) {
-  constexpr int NN = N * N, N3 = N * N * N, CS = Lay<N>::CS;
+  constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS;
   T* sU = reinterpret_cast<T*>(smem_raw);
   T* sV = sU + CPB * CS;
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
@@ -330,98 +384,123 @@ __device__ __forceinline__ void cell_tile(const Tab<N, T>& tb, const Geo<T>& g, 
   if (SELF) {
     for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
       const int c = e / N3, r = e - c * N3;
-      sU[c * CS + r % N + Lay<N>::LS * (r / N)] = (r == (cell0 + c) % N3) ? T(1) : T(0);
+      const int j1 = r % N, j23 = r / N;
+      const int pos = M == N ? j1 + Lay<M>::LS * j23 : Lay<M>::idx(j1, j23 % N, j23 / N);
+      sU[c * CS + pos] = (r == (cell0 + c) % N3) ? T(1) : T(0);
     }
   } else {
-    gload_cells<N>(sU, z, cell0, here);
+    gload_cells<N, T, TV, M>(sU, z, cell0, here);
   }
   __syncthreads();
 
   // Sec. 3.3, eq. evalfe: u at the Gauss points, axis x then y ...
 #pragma unroll
   for (int dir = 0; dir < 2; ++dir) {
-    if (active) {
-      T x[N], y[N];
-      const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
+    if (active && (M == N || t < ModalLines<N, M>::count(dir))) {
+      T x[N], y[M];
+      const int bs = ModalLines<N, M>::base(dir, t), st = Lay<M>::stride(dir);
       load_line<N>(U, bs, st, x);
-      eo_fwd<N, T>(tb, x, y);
-      store_line<N>(U, bs, st, y);
+      eo_fwd<N, M, T>(tb, x, y);
+      store_line<M>(U, bs, st, y);
     }
     __syncthreads();
   }
 
   const T DT = active ? Dcell[rcell] : T(0);
-  const int a = t % N, b = t / N;
+  const int a = t % M, b = t / M;
   const T wperp = tb.w[a] * tb.w[b];
   T* trc = traces + (size_t)cell * 12 * NN;
+  const T* bl = VB ? g.bsc + (size_t)rcell * 3 * M * NN + t : nullptr;
   // ... then z, kept in registers for the z derivative pass (Sec. 3.2, eqs. evalblf / gauss_points):
   // V = c|T| w u + B_z [w (alpha_z D d_z u + beta_z u)], traces on the two z faces
   if (active) {
-    T x[N], u[N], v[N];
-    const int bs = Lay<N>::base(2, t), st = Lay<N>::stride(2);
+    T x[N], u[M], v[M];
+    const int bs = Lay<M>::base(2, t), st = Lay<M>::stride(2);
     load_line<N>(U, bs, st, x);
-    eo_fwd<N, T>(tb, x, u);
-    store_line<N>(U, bs, st, u);
-    deriv_line<N, T, true>(tb, u, v, wperp * (DT * g.alpha[2]), wperp * g.beta[2], wperp * g.creact, trc + 8 * NN,
-                           NN, t);
-    store_line<N>(V, bs, st, v);
+    eo_fwd<N, M, T>(tb, x, u);
+    store_line<M>(U, bs, st, u);
+    deriv_line<N, M, T, true, VB>(tb, u, v, wperp * (DT * g.alpha[2]), wperp * g.beta[2], wperp * g.creact,
+                                  VB ? bl + 2 * M * NN : nullptr, trc + 8 * NN, NN, t);
+    store_line<M>(V, bs, st, v);
   }
   __syncthreads();
   // x and y derivative passes accumulate into V
 #pragma unroll
   for (int dir = 0; dir < 2; ++dir) {
     if (active) {
-      T u[N], v[N];
-      const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
-      load_line<N>(U, bs, st, u);
-      load_line<N>(V, bs, st, v);
-      deriv_line<N, T, false>(tb, u, v, wperp * (DT * g.alpha[dir]), wperp * g.beta[dir], T(0),
-                              trc + 4 * dir * NN, NN, t);
-      store_line<N>(V, bs, st, v);
+      T u[M], v[M];
+      const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
+      load_line<M>(U, bs, st, u);
+      load_line<M>(V, bs, st, v);
+      deriv_line<N, M, T, false, VB>(tb, u, v, wperp * (DT * g.alpha[dir]), wperp * g.beta[dir], T(0),
+                                     VB ? bl + dir * M * NN : nullptr, trc + 4 * dir * NN, NN, t);
+      store_line<M>(V, bs, st, v);
     }
     __syncthreads();
   }
-  gstore_cells<N>(Vout, sV, cell0, here);
+  gstore_cells<M>(Vout, sV, cell0, here);
 }
 
-template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T>
-__global__ void __launch_bounds__(CPB * N * N)
-dg_cell_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g, const TV* __restrict__ z,
+template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false>
+__global__ void __launch_bounds__(CPB * M * M)
+dg_cell_kernel(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g, const TV* __restrict__ z,
                const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
-  cell_tile<N, T, SELF, CPB, TV>(tb, g, z, Dcell, Vout, traces, cell0, here, sa_.cell_base, smem_raw);
+  cell_tile<N, T, SELF, CPB, TV, M, VB>(tb, g, z, Dcell, Vout, traces, cell0, here, sa_.cell_base, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Kernel 2: face fluxes + lift + backward contraction (+ residual)
 // fc[(cell*6 + face)*3 + {0,1,2}]: interior: (w_own D_own / h, w_nbr D_nbr / h, gamma_F);
 //                                   boundary: (D_own / h, 0, gamma_F)
-// mode 0: y = A z;  mode 1: y = A z - F;  mode 2 (right hand side): V from f, faces from g
+// mode 0: y = A z;  mode 1: y = A z - F;  mode 2 (right hand side): V from f, faces from g;
+// mode 3 (explicit Runge-Kutta stage, Sec. 2 "ODE"): y = c_z z0 + c_u u - c_r (A u - F), u the stage input
 // ---------------------------------------------------------------------------------------------
 template <typename T, typename TV = T>
 struct FaceArgs {
-  const T* V;       // point-space residual from dg_cell_kernel (mode 0/1), or f at points (mode 2)
-  const T* traces;  // traces from dg_cell_kernel (mode 0/1)
+  const T* V;       // point-space residual from dg_cell_kernel (mode 0/1/3), or f at points (mode 2)
+  const T* traces;  // traces from dg_cell_kernel (mode 0/1/3)
   const T* fc;      // face coefficients
-  const T* F;       // right hand side (mode 1), in the compute type
+  const T* F;       // right hand side (mode 1/3), in the compute type
   const T* g[6];    // Dirichlet data per boundary side (mode 2), may be null
   TV* y;            // output vector (element type TV)
   int mode;
+  const TV* u;      // mode 3: the stage input (the vector the cell kernel read)
+  const TV* z0;     // mode 3: the step's initial value (may be y: each element is read before it is written)
+  T cz, cu, cr;     // mode 3 coefficients
 };
 
 // face test weights of this thread's face point on face (dir, s): value weight Vf and normal-derivative
 // weight Wf (eq. blf: interior upwind, consistency, symmetry and penalty terms, or the Dirichlet terms;
-// mode 2: the Dirichlet terms of l_h)
-template <int N, typename T, bool SELF, typename TV>
+// mode 2: the Dirichlet terms of l_h).  With PER, an axis flagged periodic has interior end faces whose
+// neighbour is the cell at the other end (PER = false compiles the plain mesh only, which keeps the
+// register count of the FP32 and double-float kernels down).
+template <int N, typename T, bool SELF, typename TV, int M = N, bool VB = false, bool PER = false>
 __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, TV>& fa, int cell, int tcell,
                                              const int (&ic)[3], int dir, int s, int t, T wf, T& Vf, T& Wf) {
-  constexpr int NN = N * N;
+  constexpr int NN = M * M;
   const int face = 2 * dir + s;
-  const bool boundary = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
+  const bool at_end = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
+  const bool boundary = at_end && !(PER && g.periodic[dir]);
   const T* c3 = fa.fc + ((size_t)cell * 6 + face) * 3;
-  const T bq = g.b[dir];
+  // the neighbour across this face (on a periodic axis the end faces wrap around to the other end)
+  auto neighbour = [&]() {
+    const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
+    const int nwrap = (g.n[dir] - 1) * nstride;
+    if (!PER) return s ? cell + nstride : cell - nstride;
+    return s ? (at_end ? cell - nwrap : cell + nstride) : (at_end ? cell + nwrap : cell - nstride);
+  };
+  // normal velocity b . e_dir at this face point (interior faces: the lower cell's upper-face value)
+  T bq;
+  if constexpr (VB) {
+    const int owner = (boundary || s) ? cell : neighbour();
+    const int oface = boundary ? face : 2 * dir + 1;
+    bq = g.bface[((size_t)owner * 6 + oface) * NN + t];
+  } else {
+    bq = g.b[dir];
+  }
   Vf = T(0);
   Wf = T(0);
   if (fa.mode == 2) {
@@ -444,8 +523,7 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
   if (!boundary) {
     T un = T(0), dn = T(0);  // the neighbour contributes nothing to a diagonal block
     if (!SELF) {
-      const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
-      const int nb = s ? cell + nstride : cell - nstride;
+      const int nb = neighbour();
       const T* trn = fa.traces + ((size_t)nb * 6 + (2 * dir + 1 - s)) * 2 * NN;
       un = trn[t];
       dn = trn[NN + t];
@@ -471,10 +549,10 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
 }
 
 // Face-kernel work on one tile of `here` consecutive cells starting at cell0 (see cell_tile).
-template <int N, typename T, bool SELF, int CPB, typename TV = T>
-__device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, const FaceArgs<T, TV>& fa, int cell0,
-                                          int here, int cell_base, unsigned char* smem_raw) {
-  constexpr int NN = N * N, N3 = N * N * N, CS = Lay<N>::CS;
+template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false, bool PER = false>
+__device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>& g, const FaceArgs<T, TV>& fa,
+                                          int cell0, int here, int cell_base, unsigned char* smem_raw) {
+  constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS;
   T* sV = reinterpret_cast<T*>(smem_raw);
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
   const bool active = lc < here;
@@ -482,14 +560,14 @@ __device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, 
   const int cell = SELF ? cell_base + vcell / N3 : vcell;      // real cell
   T* V = sV + lc * CS;
 
-  gload_cells<N>(sV, fa.V, cell0, here);
+  gload_cells<M>(sV, fa.V, cell0, here);
   __syncthreads();
-  const int a = t % N, b = t / N;
+  const int a = t % M, b = t / M;
   if (fa.mode == 2 && active) {
     // (f, v)_T: scale f by the quadrature weight Delta_T w_i (Sec. 3.1)
     const T wz = g.vol * tb.w[a] * tb.w[b];
 #pragma unroll
-    for (int l = 0; l < N; ++l) V[Lay<N>::idx(l, a, b)] *= wz * tb.w[l];
+    for (int l = 0; l < M; ++l) V[Lay<M>::idx(l, a, b)] *= wz * tb.w[l];
   }
   __syncthreads();
 
@@ -503,62 +581,75 @@ __device__ __forceinline__ void face_tile(const Tab<N, T>& tb, const Geo<T>& g, 
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     if (active) {
-      const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
-      T v[N];
-      load_line<N>(V, bs, st, v);
+      const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
+      T v[M];
+      load_line<M>(V, bs, st, v);
       const T wf = g.area[dir] * wab;
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         T Vf, Wf;
-        face_weights<N, T, SELF, TV>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf, Wf);
+        face_weights<N, T, SELF, TV, M, VB, PER>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf, Wf);
 #pragma unroll
-        for (int l = 0; l < N; ++l) v[l] = fma(tb.L[s][l], Vf, fma(tb.P[s][l], Wf, v[l]));
+        for (int l = 0; l < M; ++l) v[l] = fma(tb.L[s][l], Vf, fma(tb.P[s][l], Wf, v[l]));
       }
       if (dir == 2) {
         T y[N];
-        eo_bwd<N, T>(tb, v, y);
+        eo_bwd<N, M, T>(tb, v, y);
         store_line<N>(V, bs, st, y);
       } else {
-        store_line<N>(V, bs, st, v);
+        store_line<M>(V, bs, st, v);
       }
     }
     __syncthreads();
   }
 
-  // Sec. 3.2: test functions, A^T along y and x
+  // Sec. 3.2: test functions, A^T along y and x (M -> N on the modal lines)
 #pragma unroll
   for (int dd = 0; dd < 2; ++dd) {
     const int dir = 1 - dd;
-    if (active) {
-      T x[N], y[N];
-      const int bs = Lay<N>::base(dir, t), st = Lay<N>::stride(dir);
-      load_line<N>(V, bs, st, x);
-      eo_bwd<N, T>(tb, x, y);
+    if (active && (M == N || t < ModalLines<N, M>::count(dir))) {
+      T x[M], y[N];
+      const int bs = ModalLines<N, M>::base(dir, t), st = Lay<M>::stride(dir);
+      load_line<M>(V, bs, st, x);
+      eo_bwd<N, M, T>(tb, x, y);
       store_line<N>(V, bs, st, y);
     }
     __syncthreads();
   }
-  // write out (minus F for the residual)
+  // write out (minus F for the residual, or the Runge-Kutta stage combination)
   const int total = here * N3;
   TV* dst = fa.y + (size_t)cell0 * N3;
   const T* Fs = fa.F ? fa.F + (size_t)cell0 * N3 : nullptr;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int c = e / N3, r = e - c * N3;
     const int i1 = r % N, i23 = r / N;
-    T val = sV[c * CS + i1 + Lay<N>::LS * i23];
+    T val;
+    if constexpr (M == N) {
+      val = sV[c * CS + i1 + Lay<M>::LS * i23];
+    } else {
+      val = sV[c * CS + Lay<M>::idx(i1, i23 % N, i23 / N)];
+    }
     if (fa.mode == 1) val = val - Fs[e];
+    if constexpr (std::is_same<T, double>::value) {  // Runge-Kutta stages are offered in FP64 only
+      if (fa.mode == 3) {
+        const size_t ge = (size_t)cell0 * N3 + e;
+        const T r_ = Fs ? val - Fs[e] : val;
+        val = fma(fa.cz, to_compute<T, TV>(fa.z0[ge]), fma(fa.cu, to_compute<T, TV>(fa.u[ge]), -fa.cr * r_));
+      }
+    }
     dst[e] = from_compute<TV, T>(val);
   }
 }
 
-template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T>
-__global__ void __launch_bounds__(CPB * N * N)
-dg_face_kernel(const __grid_constant__ Tab<N, T> tb, const __grid_constant__ Geo<T> g,
+template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false,
+          bool PER = false>
+__global__ void __launch_bounds__(CPB * M * M, (std::is_same<T, float>::value && CPB * M * M == 256) ? 8 : 1)
+dg_face_kernel(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g,
                const __grid_constant__ FaceArgs<T, TV> fa, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
-  face_tile<N, T, SELF, CPB, TV>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
+  face_tile<N, T, SELF, CPB, TV, M, VB, PER>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
 }
 
 }  // namespace dgk

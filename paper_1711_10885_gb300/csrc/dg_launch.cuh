@@ -6,36 +6,37 @@
 
 namespace dgi {
 
-template <int N, typename T>
-dgk::Tab<N, T> make_tab(const Tables1D& t) {
-  constexpr int H = N / 2, C = (N + 1) / 2;
-  dgk::Tab<N, T> r;
+template <int N, typename T, int M = N>
+dgk::TabNM<N, M, T> make_tab(const Tables1D& t) {
+  constexpr int HN = N / 2, CN = (N + 1) / 2, HM = M / 2, CM = (M + 1) / 2;
+  dgk::TabNM<N, M, T> r;
   // B[o][i] = w_i Dt[i][o]: the weighted transposed collocation derivative
-  double B[MAXN][MAXN];
-  for (int o = 0; o < N; ++o)
-    for (int i = 0; i < N; ++i) B[o][i] = t.w[i] * t.Dt[i][o];
-  for (int i = 0; i < C; ++i) {
-    for (int k = 0; k < C; ++k) r.AE[i][k] = (T)t.A[i][2 * k];
-    for (int k = 0; k < H; ++k) r.AO[i][k] = (T)t.A[i][2 * k + 1];
-    for (int l = 0; l < H; ++l) {
-      r.DHm[i][l] = (T)(0.5 * (t.Dt[i][l] - t.Dt[i][N - 1 - l]));
-      r.BHm[i][l] = (T)(0.5 * (B[i][l] - B[i][N - 1 - l]));
+  double B[MAXM][MAXM];
+  for (int o = 0; o < M; ++o)
+    for (int i = 0; i < M; ++i) B[o][i] = t.w[i] * t.Dt[i][o];
+  for (int i = 0; i < CM; ++i) {
+    for (int k = 0; k < CN; ++k) r.AE[i][k] = (T)t.A[i][2 * k];
+    for (int l = 0; l < HM; ++l) {
+      r.DHm[i][l] = (T)(0.5 * (t.Dt[i][l] - t.Dt[i][M - 1 - l]));
+      r.BHm[i][l] = (T)(0.5 * (B[i][l] - B[i][M - 1 - l]));
     }
   }
-  for (int i = 0; i < H; ++i)
-    for (int l = 0; l < C; ++l) {
-      r.DHp[i][l] = (T)(0.5 * (t.Dt[i][l] + t.Dt[i][N - 1 - l]));
-      r.BHp[i][l] = (T)(0.5 * (B[i][l] + B[i][N - 1 - l]));
+  for (int i = 0; i < HM; ++i) {
+    for (int k = 0; k < HN; ++k) r.AO[i][k] = (T)t.A[i][2 * k + 1];
+    for (int l = 0; l < CM; ++l) {
+      r.DHp[i][l] = (T)(0.5 * (t.Dt[i][l] + t.Dt[i][M - 1 - l]));
+      r.BHp[i][l] = (T)(0.5 * (B[i][l] + B[i][M - 1 - l]));
     }
-  for (int l = 0; l < C; ++l) {
-    r.LS[l] = (T)(0.5 * (t.L[1][l] + t.L[1][N - 1 - l]));
-    r.PS[l] = (T)(0.5 * (t.P[1][l] + t.P[1][N - 1 - l]));
   }
-  for (int l = 0; l < H; ++l) {
-    r.LD[l] = (T)(0.5 * (t.L[1][l] - t.L[1][N - 1 - l]));
-    r.PD[l] = (T)(0.5 * (t.P[1][l] - t.P[1][N - 1 - l]));
+  for (int l = 0; l < CM; ++l) {
+    r.LS[l] = (T)(0.5 * (t.L[1][l] + t.L[1][M - 1 - l]));
+    r.PS[l] = (T)(0.5 * (t.P[1][l] + t.P[1][M - 1 - l]));
   }
-  for (int i = 0; i < N; ++i) {
+  for (int l = 0; l < HM; ++l) {
+    r.LD[l] = (T)(0.5 * (t.L[1][l] - t.L[1][M - 1 - l]));
+    r.PD[l] = (T)(0.5 * (t.P[1][l] - t.P[1][M - 1 - l]));
+  }
+  for (int i = 0; i < M; ++i) {
     r.w[i] = (T)t.w[i];
     for (int s = 0; s < 2; ++s) {
       r.L[s][i] = (T)t.L[s][i];
@@ -59,30 +60,56 @@ dgk::Geo<T> make_geo(const dg_handle* h) {
   g.ncell = (int)h->ncell;
   g.vol = (T)vol;
   g.creact = (T)(h->c * vol);
+  for (int r = 0; r < 3; ++r) g.periodic[r] = h->periodic[r];
+  g.bsc = nullptr;
+  g.bface = nullptr;
   return g;
 }
 
-template <int N, typename T>
+// shared memory of the two kernels for M points per direction (CPB = Launch<M>::CPB cells per CTA)
+template <int M, typename T>
 size_t cell_smem() {
-  return 2 * (size_t)dgk::Launch<N>::CPB * dgk::Lay<N>::CS * sizeof(T);
+  return 2 * (size_t)dgk::Launch<M>::CPB * dgk::Lay<M>::CS * sizeof(T);
 }
-template <int N, typename T>
+template <int M, typename T>
 size_t face_smem() {
-  return (size_t)dgk::Launch<N>::CPB * dgk::Lay<N>::CS * sizeof(T);
+  return (size_t)dgk::Launch<M>::CPB * dgk::Lay<M>::CS * sizeof(T);
 }
 
-template <int N, typename T, typename TV = T>
+template <int N, typename T, typename TV = T, int M = N, bool VB = false>
 int set_smem_attrs() {
   static bool done = false;  // per instantiation; attributes are per function
   if (done) return 0;
-  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T, false, dgk::Launch<N>::CPB, TV>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<N, T>());
+  constexpr int CPB = dgk::Launch<M>::CPB;
+  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<M, T>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel)");
-  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T, false, dgk::Launch<N>::CPB, TV>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<N, T>());
+  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
+  if constexpr (!VB) {
+    e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T>());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
+  }
   done = true;
   return 0;
+}
+
+// face kernel launch: the periodic-aware variant when the mesh has a periodic axis (always for the
+// velocity field kernels, which are FP64 only and lose nothing by it)
+template <int N, typename T, typename TV, int M, bool VB>
+void launch_face(const dg_handle* h, const dgk::TabNM<N, M, T>& tb, const dgk::Geo<T>& geo,
+                 const dgk::FaceArgs<T, TV>& fa, unsigned grid, cudaStream_t s) {
+  constexpr int CPB = dgk::Launch<M>::CPB;
+  const bool per = h->periodic[0] || h->periodic[1] || h->periodic[2];
+  if (VB || per) {
+    dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, true>
+        <<<grid, dgk::Launch<M>::THREADS, face_smem<M, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
+  } else if constexpr (!VB) {
+    dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, false>
+        <<<grid, dgk::Launch<M>::THREADS, face_smem<M, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
+  }
 }
 
 // coefficient copies in the compute precision
@@ -102,60 +129,86 @@ int set_self_smem_attrs() {
   cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, double, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<N, double>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel self)");
-  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)face_smem<N, double>());
+  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, double, true, dgk::Launch<N>::CPB, double, N, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<N, double>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel self)");
   done = true;
   return 0;
 }
 
-template <int N, typename T, typename TV = T>
-int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s) {
-  if (int rc = set_smem_attrs<N, T, TV>()) return rc;
+// geometry of the handle with the velocity field tables of the VB kernels
+template <typename T, bool VB>
+dgk::Geo<T> geo_for(const dg_handle* h) {
+  dgk::Geo<T> geo = make_geo<T>(h);
+  if (VB) {
+    geo.bsc = static_cast<const T*>(h->bsc);
+    geo.bface = static_cast<const T*>(h->bface);
+  }
+  return geo;
+}
+
+template <int N, typename T, typename TV = T, int M = N, bool VB = false>
+int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s,
+            const StageArgs* st = nullptr) {
+  if (int rc = set_smem_attrs<N, T, TV, M, VB>()) return rc;
+  constexpr int CPB = dgk::Launch<M>::CPB;
   const Buffers& bf = buffers_for<T>(h);
-  const auto tb = make_tab<N, T>(h->tab);
-  const auto geo = make_geo<T>(h);
-  const int cpb = dgk::Launch<N>::CPB;
-  const unsigned grid = (unsigned)((h->ncell + cpb - 1) / cpb);
+  const auto tb = make_tab<N, T, M>(h->tab);
+  const auto geo = geo_for<T, VB>(h);
+  const unsigned grid = (unsigned)((h->ncell + CPB - 1) / CPB);
   T* V = static_cast<T*>(h->work_V);
   T* tr = static_cast<T*>(h->work_tr);
   if (stages & 1)
-    dgk::dg_cell_kernel<N, T, false, dgk::Launch<N>::CPB, TV><<<grid, dgk::Launch<N>::THREADS, cell_smem<N, T>(), s>>>(
+    dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB><<<grid, dgk::Launch<M>::THREADS, cell_smem<M, T>(), s>>>(
         tb, geo, z, static_cast<const T*>(bf.D), V, tr, dgk::SelfArgs{0, 0});
   dgk::FaceArgs<T, TV> fa;
   fa.V = V;
   fa.traces = tr;
   fa.fc = static_cast<const T*>(bf.fc);
-  fa.F = mode == 1 ? static_cast<const T*>(bf.F) : nullptr;
+  fa.F = (mode == 1 || mode == 3) ? static_cast<const T*>(bf.F) : nullptr;
   for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
   fa.y = y;
   fa.mode = mode;
-  if (stages & 2)
-    dgk::dg_face_kernel<N, T, false, dgk::Launch<N>::CPB, TV>
-        <<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
+  fa.u = z;
+  fa.z0 = nullptr;
+  fa.cz = fa.cu = fa.cr = T(0);
+  if (mode == 3) {
+    if (!st) {
+      set_error("Runge-Kutta stage without coefficients");
+      return DG_ERR_INVALID_ARG;
+    }
+    fa.z0 = reinterpret_cast<const TV*>(st->z0);
+    fa.cz = (T)st->cz;
+    fa.cu = (T)st->cu;
+    fa.cr = (T)st->cr;
+  }
+  if (stages & 2) launch_face<N, T, TV, M, VB>(h, tb, geo, fa, grid, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");
   return 0;
 }
 
-template <int N, typename T>
-int rhs_n(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_t s) {
-  if (int rc = set_smem_attrs<N, T>()) return rc;
+template <int N, typename T, int M = N, bool VB = false>
+int rhs_n(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_t s, bool project = false) {
+  if (int rc = set_smem_attrs<N, T, T, M, VB>()) return rc;
+  constexpr int CPB = dgk::Launch<M>::CPB;
   const Buffers& bf = sizeof(T) == 8 ? h->p64 : h->p32;
-  const auto tb = make_tab<N, T>(h->tab);
-  const auto geo = make_geo<T>(h);
-  const int cpb = dgk::Launch<N>::CPB;
-  const unsigned grid = (unsigned)((h->ncell + cpb - 1) / cpb);
+  const auto tb = make_tab<N, T, M>(h->tab);
+  auto geo = geo_for<T, VB>(h);
+  if (project) geo.vol = T(1);  // (f, phi_i)_T / |T|: the mass matrix is |T| I
+  const unsigned grid = (unsigned)((h->ncell + CPB - 1) / CPB);
   dgk::FaceArgs<T> fa;
   fa.V = f;
   fa.traces = nullptr;
   fa.fc = static_cast<const T*>(bf.fc);
   fa.F = nullptr;
-  for (int i = 0; i < 6; ++i) fa.g[i] = g[i];
+  for (int i = 0; i < 6; ++i) fa.g[i] = project ? nullptr : g[i];
   fa.y = F;
   fa.mode = 2;
-  dgk::dg_face_kernel<N, T><<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>(), s>>>(tb, geo, fa,
-                                                                                    dgk::SelfArgs{0, 0});
+  fa.u = nullptr;
+  fa.z0 = nullptr;
+  fa.cz = fa.cu = fa.cr = T(0);
+  launch_face<N, T, T, M, VB>(h, tb, geo, fa, grid, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rhs kernel launch");
   return 0;
@@ -165,7 +218,6 @@ int rhs_n(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_
 // out[(c * N^3 + j) * N^3 + i], i.e. each block is stored as A_TT^T in row-major order.
 template <int N>
 int diag_blocks_n(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr, cudaStream_t s) {
-  if (int rc = set_smem_attrs<N, double>()) return rc;
   if (int rc = set_self_smem_attrs<N>()) return rc;
   constexpr int N3 = N * N * N;
   const auto tb = make_tab<N, double>(h->tab);
@@ -184,62 +236,71 @@ int diag_blocks_n(const dg_handle* h, double* out, int cell_base, int ncells, do
   for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
   fa.y = out;
   fa.mode = 0;
-  dgk::dg_face_kernel<N, double, true><<<grid, dgk::Launch<N>::THREADS, face_smem<N, double>(), s>>>(tb, geo, fa,
-                                                                                                    sa);
+  fa.u = nullptr;
+  fa.z0 = nullptr;
+  fa.cz = fa.cu = fa.cr = 0.0;
+  dgk::dg_face_kernel<N, double, true, dgk::Launch<N>::CPB, double, N, false, true>
+      <<<grid, dgk::Launch<N>::THREADS, face_smem<N, double>(), s>>>(tb, geo, fa, sa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "diagonal block kernel launch");
   return 0;
 }
 
-inline int diag_blocks_dispatch(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr,
-                                cudaStream_t s) {
-  switch (h->N) {
-    case 2: return diag_blocks_n<2>(h, out, cell_base, ncells, V, tr, s);
-    case 3: return diag_blocks_n<3>(h, out, cell_base, ncells, V, tr, s);
-    case 4: return diag_blocks_n<4>(h, out, cell_base, ncells, V, tr, s);
-    case 5: return diag_blocks_n<5>(h, out, cell_base, ncells, V, tr, s);
-    case 6: return diag_blocks_n<6>(h, out, cell_base, ncells, V, tr, s);
-    case 7: return diag_blocks_n<7>(h, out, cell_base, ncells, V, tr, s);
-    case 8: return diag_blocks_n<8>(h, out, cell_base, ncells, V, tr, s);
-    case 9: return diag_blocks_n<9>(h, out, cell_base, ncells, V, tr, s);
-    case 10: return diag_blocks_n<10>(h, out, cell_base, ncells, V, tr, s);
-    case 11: return diag_blocks_n<11>(h, out, cell_base, ncells, V, tr, s);
-    default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
-  }
-}
-
 template <typename T, typename TV = T>
-int apply_dispatch(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s) {
+int apply_dispatch(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s,
+                   const StageArgs* st = nullptr) {
   switch (h->N) {
-    case 2: return apply_n<2, T, TV>(h, z, y, mode, stages, s);
-    case 3: return apply_n<3, T, TV>(h, z, y, mode, stages, s);
-    case 4: return apply_n<4, T, TV>(h, z, y, mode, stages, s);
-    case 5: return apply_n<5, T, TV>(h, z, y, mode, stages, s);
-    case 6: return apply_n<6, T, TV>(h, z, y, mode, stages, s);
-    case 7: return apply_n<7, T, TV>(h, z, y, mode, stages, s);
-    case 8: return apply_n<8, T, TV>(h, z, y, mode, stages, s);
-    case 9: return apply_n<9, T, TV>(h, z, y, mode, stages, s);
-    case 10: return apply_n<10, T, TV>(h, z, y, mode, stages, s);
-    case 11: return apply_n<11, T, TV>(h, z, y, mode, stages, s);
+    case 2: return apply_n<2, T, TV>(h, z, y, mode, stages, s, st);
+    case 3: return apply_n<3, T, TV>(h, z, y, mode, stages, s, st);
+    case 4: return apply_n<4, T, TV>(h, z, y, mode, stages, s, st);
+    case 5: return apply_n<5, T, TV>(h, z, y, mode, stages, s, st);
+    case 6: return apply_n<6, T, TV>(h, z, y, mode, stages, s, st);
+    case 7: return apply_n<7, T, TV>(h, z, y, mode, stages, s, st);
+    case 8: return apply_n<8, T, TV>(h, z, y, mode, stages, s, st);
+    case 9: return apply_n<9, T, TV>(h, z, y, mode, stages, s, st);
+    case 10: return apply_n<10, T, TV>(h, z, y, mode, stages, s, st);
+    case 11: return apply_n<11, T, TV>(h, z, y, mode, stages, s, st);
     default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
   }
 }
 
 template <typename T>
-int rhs_dispatch(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_t s) {
+int rhs_dispatch(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_t s, bool project = false) {
   switch (h->N) {
-    case 2: return rhs_n<2, T>(h, f, g, F, s);
-    case 3: return rhs_n<3, T>(h, f, g, F, s);
-    case 4: return rhs_n<4, T>(h, f, g, F, s);
-    case 5: return rhs_n<5, T>(h, f, g, F, s);
-    case 6: return rhs_n<6, T>(h, f, g, F, s);
-    case 7: return rhs_n<7, T>(h, f, g, F, s);
-    case 8: return rhs_n<8, T>(h, f, g, F, s);
-    case 9: return rhs_n<9, T>(h, f, g, F, s);
-    case 10: return rhs_n<10, T>(h, f, g, F, s);
-    case 11: return rhs_n<11, T>(h, f, g, F, s);
+    case 2: return rhs_n<2, T>(h, f, g, F, s, project);
+    case 3: return rhs_n<3, T>(h, f, g, F, s, project);
+    case 4: return rhs_n<4, T>(h, f, g, F, s, project);
+    case 5: return rhs_n<5, T>(h, f, g, F, s, project);
+    case 6: return rhs_n<6, T>(h, f, g, F, s, project);
+    case 7: return rhs_n<7, T>(h, f, g, F, s, project);
+    case 8: return rhs_n<8, T>(h, f, g, F, s, project);
+    case 9: return rhs_n<9, T>(h, f, g, F, s, project);
+    case 10: return rhs_n<10, T>(h, f, g, F, s, project);
+    case 11: return rhs_n<11, T>(h, f, g, F, s, project);
     default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
   }
+}
+
+}  // namespace dgi
+
+namespace dgi {
+
+// The velocity field kernels: M = N (q = 2p) or M = N + 2 (q = 2p+4), degrees 1..8, FP64.
+template <int N>
+int apply_vb_n(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+               cudaStream_t s) {
+  if (h->M == N) return apply_n<N, double, double, N, true>(h, z, y, mode, stages, s, st);
+  if (h->M == N + 2) return apply_n<N, double, double, N + 2, true>(h, z, y, mode, stages, s, st);
+  set_error("unsupported number of quadrature points");
+  return DG_ERR_INVALID_ARG;
+}
+template <int N>
+int rhs_vb_n(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,
+             bool project) {
+  if (h->M == N) return rhs_n<N, double, N, true>(h, f, g, F, s, project);
+  if (h->M == N + 2) return rhs_n<N, double, N + 2, true>(h, f, g, F, s, project);
+  set_error("unsupported number of quadrature points");
+  return DG_ERR_INVALID_ARG;
 }
 
 }  // namespace dgi

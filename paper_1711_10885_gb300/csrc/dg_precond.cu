@@ -216,6 +216,16 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
     set_error("dg_precond_setup: kind must be 1 (block-Jacobi)");
     return DG_ERR_INVALID_ARG;
   }
+  if (h->vb) {
+    set_error("dg_precond_setup: block-Jacobi needs a constant velocity and m = k+1");
+    return DG_ERR_INVALID_ARG;
+  }
+  for (int r = 0; r < 3; ++r)
+    if (h->periodic[r] && h->n[r] == 1) {
+      // the diagonal block would have to include the cell's coupling with itself across the wrap
+      set_error("dg_precond_setup: a periodic axis needs at least 2 cells for block-Jacobi");
+      return DG_ERR_INVALID_ARG;
+    }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int N = h->N, n = N * N * N;
   if (n > 512) {

@@ -116,6 +116,7 @@ int dg_apply_jacobian_static(const dg_mesh* mesh, int32_t k, const double* D_dev
   dg_handle h;
   h.k = k;
   h.N = N;
+  h.M = N;
   h.ncell = ncell;
   for (int r = 0; r < 3; ++r) {
     h.n[r] = mesh->n[r];
@@ -126,7 +127,7 @@ int dg_apply_jacobian_static(const dg_mesh* mesh, int32_t k, const double* D_dev
   }
   h.c = c;
   h.sigma = sigma;
-  build_tables(N, &h.tab);
+  build_tables(N, N, &h.tab);
   h.work_V = p;
   h.work_tr = p + bytes_V;
   h.p64.fc = p + bytes_V + bytes_tr;

@@ -44,6 +44,17 @@ class dg_bc(ctypes.Structure):
     _fields_ = [("g_qp", _dp * 6)]
 
 
+DG_VELOCITY_CONSTANT = 0
+DG_VELOCITY_POINTS = 1
+DG_VELOCITY_TAYLOR_GREEN = 2
+_VELOCITY = {"constant": DG_VELOCITY_CONSTANT, "points": DG_VELOCITY_POINTS, "taylor_green": DG_VELOCITY_TAYLOR_GREEN}
+
+
+class dg_setup_ext(ctypes.Structure):
+    _fields_ = [("periodic", ctypes.c_int32 * 3), ("m", ctypes.c_int32), ("velocity", ctypes.c_int32),
+                ("b_qp", _dp), ("b_face", _dp)]
+
+
 DG_SOLVE_FP64 = 0
 DG_SOLVE_MIXED = 1
 DG_PRECOND_NONE = 0
@@ -87,6 +98,11 @@ def _load():
     lib.dg_penalty_sigma.argtypes = [ctypes.c_int32, ctypes.c_int32]
     lib.dg_setup.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int32, ctypes.POINTER(dg_coeffs),
                              ctypes.POINTER(dg_bc), _dp, vp, ctypes.POINTER(vp)]
+    lib.dg_setup_ex.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int32, ctypes.POINTER(dg_coeffs),
+                                ctypes.POINTER(dg_bc), _dp, ctypes.POINTER(dg_setup_ext), vp, ctypes.POINTER(vp)]
+    lib.dg_project.argtypes = [vp, vp, vp, vp]
+    lib.dg_rk_stage.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
+    lib.dg_ssprk2.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int32, vp]
     lib.dg_destroy.argtypes = [vp]
     lib.dg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_int64)]
@@ -128,7 +144,8 @@ EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadra
             "dg_precond_apply", "dg_solve", "dg_batch_create", "dg_batch_apply", "dg_batch_tuning",
             "dg_batch_destroy", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_dims", "dg_mlp_params",
             "dg_mlp_param_offsets", "dg_mlp_set_target_scale", "dg_mlp_features", "dg_mlp_forward", "dg_mlp_loss_grad",
-            "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load"]
+            "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load",
+            "dg_apply_jacobian_static", "dg_setup_ex", "dg_project", "dg_rk_stage", "dg_ssprk2"]
 
 
 def check(rc):
@@ -164,10 +181,15 @@ def _f64(a):
 
 
 class Operator:
-    """A dg_handle: mesh, degree, coefficients and right hand side (dg_setup), freed by close()."""
+    """A dg_handle: mesh, degree, coefficients and right hand side (dg_setup / dg_setup_ex), freed by close().
+
+    Transport options (dg_setup_ext): ``periodic`` flags per axis, ``m`` Gauss points per direction (k+1 or
+    k+3), ``velocity`` "constant" (b), "points" (b_qp [ncell, m^3, 3] and b_face [ncell, 6, m^2]) or
+    "taylor_green" (the flow field of Sec. 5.3, evaluated by the library)."""
 
     def __init__(self, n, k, D=1.0, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0),
-                 hi=(1.0, 1.0, 1.0), f_qp=None, g_qp=None, stream=None):
+                 hi=(1.0, 1.0, 1.0), f_qp=None, g_qp=None, stream=None, periodic=(0, 0, 0), m=None,
+                 velocity="constant", b_qp=None, b_face=None):
         mesh = dg_mesh()
         for r in range(3):
             mesh.lo[r], mesh.hi[r], mesh.n[r] = float(lo[r]), float(hi[r]), int(n[r])
@@ -205,11 +227,24 @@ class Operator:
             fa = _f64(f_qp).reshape(-1)
             keep.append(fa)
             fptr = fa.ctypes.data_as(_dp)
+        ext = dg_setup_ext()
+        for r in range(3):
+            ext.periodic[r] = int(periodic[r])
+        ext.m = int(m) if m is not None else 0
+        ext.velocity = _VELOCITY[velocity]
+        if velocity == "points":
+            bq = _f64(b_qp).reshape(-1)
+            bf = _f64(b_face).reshape(-1)
+            keep += [bq, bf]
+            ext.b_qp = bq.ctypes.data_as(_dp)
+            ext.b_face = bf.ctypes.data_as(_dp)
         h = ctypes.c_void_p()
-        check(lib.dg_setup(ctypes.byref(mesh), int(k), ctypes.byref(co), bcp, fptr, _stream_ptr(stream),
-                           ctypes.byref(h)))
+        check(lib.dg_setup_ex(ctypes.byref(mesh), int(k), ctypes.byref(co), bcp, fptr, ctypes.byref(ext),
+                              _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
         self.k = int(k)
+        self.m = int(m) if m else int(k) + 1
+        self.periodic = tuple(int(v) for v in periodic)
         self.n = tuple(int(v) for v in n)
         nc, dpc, nd = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
         check(lib.dg_sizes(h, ctypes.byref(nc), ctypes.byref(dpc), ctypes.byref(nd)))
@@ -228,7 +263,7 @@ class Operator:
             pass
 
     def quadrature_points(self, which: int = 0) -> np.ndarray:
-        m = self.k + 1
+        m = self.m
         if which == 0:
             shape = (self.ncell, m ** 3, 3)
         else:
@@ -317,6 +352,32 @@ class Operator:
         d = st.as_dict()
         d["rc"] = rc
         return d
+
+    def project(self, u_qp, z=None, stream=None):
+        """z = L2 projection of u given at the volume points [ncell, m^3] (dg_project, FP64 CUDA tensors)."""
+        import torch
+        if z is None:
+            z = torch.empty(self.ndof, dtype=torch.float64, device=u_qp.device)
+        self._vec_check(z)
+        if not u_qp.is_cuda or u_qp.dtype != torch.float64 or not u_qp.is_contiguous() or \
+                u_qp.numel() != self.ncell * self.m ** 3:
+            raise ValueError("u_qp must be a contiguous float64 CUDA tensor with ncell * m^3 entries")
+        check(lib.dg_project(self.h, ctypes.c_void_p(u_qp.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                             _stream_ptr(stream)))
+        return z
+
+    def rk_stage(self, u, z0, y, cz, cu, cdt, stream=None):
+        """y = cz z0 + cu u - cdt M^{-1}(A u - F) (dg_rk_stage, FP64 CUDA tensors; y may alias u or z0)."""
+        self._vec_check(u, z0, y)
+        check(lib.dg_rk_stage(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(z0.data_ptr()),
+                              ctypes.c_void_p(y.data_ptr()), float(cz), float(cu), float(cdt), _stream_ptr(stream)))
+        return y
+
+    def ssprk2(self, z, dt, nsteps=1, stream=None):
+        """nsteps Heun steps on the FP64 CUDA tensor z in place (dg_ssprk2)."""
+        self._vec_check(z)
+        check(lib.dg_ssprk2(self.h, ctypes.c_void_p(z.data_ptr()), float(dt), int(nsteps), _stream_ptr(stream)))
+        return z
 
     def rhs(self, dtype=None, stream=None):
         """F = l_h(phi_i) (dg_rhs)."""
@@ -466,13 +527,14 @@ def operator_for(w, stream=None, sigma=None):
     """Build an Operator for an inputs.Workload, with f sampled at the library's own quadrature points."""
     import numpy as np
     from . import inputs
-    m3 = (w.k + 1) ** 3
+    m = getattr(w, "m", None) or w.k + 1
+    ext = dict(periodic=getattr(w, "periodic", (0, 0, 0)), m=m, velocity=getattr(w, "velocity", "constant"))
     if w.f_kind == "zero":
         f = None
     elif w.f_kind == "one":
-        f = np.ones(w.ncell * m3)
+        f = np.ones(w.ncell * m ** 3)
     else:
-        probe = Operator(w.n, w.k, w.D, b=w.b, c=w.c, sigma=sigma, lo=w.lo, hi=w.hi, stream=stream)
+        probe = Operator(w.n, w.k, w.D, b=w.b, c=w.c, sigma=sigma, lo=w.lo, hi=w.hi, stream=stream, **ext)
         f = inputs.f_at(w, probe.quadrature_points(0))
         probe.close()
-    return Operator(w.n, w.k, w.D, b=w.b, c=w.c, sigma=sigma, lo=w.lo, hi=w.hi, f_qp=f, stream=stream)
+    return Operator(w.n, w.k, w.D, b=w.b, c=w.c, sigma=sigma, lo=w.lo, hi=w.hi, f_qp=f, stream=stream, **ext)

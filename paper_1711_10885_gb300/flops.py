@@ -21,15 +21,20 @@ def _halves(N):
     return N // 2, (N + 1) // 2
 
 
-def eo_fwd_flops(N):
-    """Modal -> points on one line in even-odd form (mul + fma chains, then the +/- recombination)."""
-    H, C = _halves(N)
-    return C * (2 * C - 1) + H * (2 * H - 1) + 2 * H
+def eo_fwd_flops(N, M=None):
+    """Modal (N) -> points (M) on one line in even-odd form (mul + fma chains, then the +/- recombination)."""
+    M = M or N
+    HN, CN = _halves(N)
+    HM, CM = _halves(M)
+    return CM * (2 * CN - 1) + HM * (2 * HN - 1) + 2 * HM
 
 
-def eo_bwd_flops(N):
-    H, C = _halves(N)
-    return 2 * H + C * (2 * C - 1) + H * (2 * H - 1)
+def eo_bwd_flops(N, M=None):
+    """Points (M) -> modal (N): split of the line, then the two half-size products."""
+    M = M or N
+    HN, CN = _halves(N)
+    HM, CM = _halves(M)
+    return 2 * HM + CN * (2 * CM - 1) + HN * (2 * HM - 1)
 
 
 def eo_anti_flops(N):
@@ -39,30 +44,36 @@ def eo_anti_flops(N):
 
 
 def deriv_line_flops(N, first):
+    """One derivative pass on a line of N points (the point count, M in the kernels)."""
     H, C = _halves(N)
     split = 2 * H
-    flux = 3 * N  # sa * grad + sb * u
+    flux = 3 * N  # sa * grad + sb * u (or the point-wise b * u)
     acc = 3 * N if first else N  # reaction (mul + fma) on the first pass, else add
     traces = 4 * N + 4
     return split + eo_anti_flops(N) + flux + split + eo_anti_flops(N) + acc + traces
 
 
-def cell_kernel_flops(N: int) -> float:
-    """Executed FP operations of dg_cell_kernel for one cell (n = m = N)."""
-    NN = N * N
-    fwd = 3 * NN * eo_fwd_flops(N)
-    deriv = NN * (deriv_line_flops(N, True) + 2 * deriv_line_flops(N, False))
-    scalars = NN * (1 + 3 * 3 + 1)  # wperp; sa (2) and sb (1) per pass; sc once
+def cell_kernel_flops(N: int, M: int | None = None, vb: bool = False) -> float:
+    """Executed FP operations of dg_cell_kernel for one cell: N = k+1 modes, M Gauss points per direction
+    (default N); vb: the velocity field kernels (the constant convection weight is not formed)."""
+    M = M or N
+    MM = M * M
+    fwd = (N * N + M * N + M * M) * eo_fwd_flops(N, M)  # x, y and z modal passes
+    deriv = MM * (deriv_line_flops(M, True) + 2 * deriv_line_flops(M, False))
+    scalars = MM * (1 + 3 * (2 if vb else 3) + 1)  # wperp; sa (2) [and sb (1)] per pass; sc once
     return fwd + deriv + scalars
 
 
-def face_kernel_flops(N: int, n=(1, 1, 1), residual: bool = True) -> float:
-    """Executed FP operations of dg_face_kernel, averaged per cell for an n[0] x n[1] x n[2] mesh."""
-    NN = N * N
+def face_kernel_flops(N: int, n=(1, 1, 1), residual: bool = True, M: int | None = None,
+                      stage: bool = False) -> float:
+    """Executed FP operations of dg_face_kernel per cell; stage: the Runge-Kutta epilogue (mode 3)."""
+    M = M or N
+    MM = M * M
     per_point = 11  # face weights: jump, average (mul+fma), upwind, H (sub+fma), V, W (2 mul), sign
-    lift = 3 * NN * (1 + 2 * (per_point + 4 * N))  # wf, then per side the weights and 2 fma per point
-    back = 3 * NN * eo_bwd_flops(N)
-    return NN + lift + back + (N ** 3 if residual else 0)
+    lift = 3 * MM * (1 + 2 * (per_point + 4 * M))  # wf, then per side the weights and 2 fma per point
+    back = (M * M + M * N + N * N) * eo_bwd_flops(N, M)
+    epilogue = 6 * N ** 3 if stage else (N ** 3 if residual else 0)
+    return MM + lift + back + epilogue
 
 
 def apply_flops_per_dof(k: int, n=(1, 1, 1), residual: bool = True) -> float:
@@ -70,9 +81,14 @@ def apply_flops_per_dof(k: int, n=(1, 1, 1), residual: bool = True) -> float:
     return (cell_kernel_flops(N) + face_kernel_flops(N, n, residual)) / N ** 3
 
 
-def bytes_per_cell(N: int, elt: int = 8, residual: bool = True) -> dict:
-    """Algorithmic DRAM bytes per cell of each kernel: its compulsory reads and writes."""
-    n3, nn = N ** 3, N * N
-    cell = elt * (n3 + 1 + n3 + 12 * nn)  # read z, D; write V and 6x2 traces
-    face = elt * (n3 + 2 * 12 * nn + 18 + n3 + (n3 if residual else 0))  # V, own+nbr traces, fc, y, F
+def bytes_per_cell(N: int, elt: int = 8, residual: bool = True, M: int | None = None, vb: bool = False,
+                   stage: bool = False) -> dict:
+    """Algorithmic DRAM bytes per cell of each kernel: its compulsory reads and writes.  vb adds the
+    velocity tables (3 M^3 volume values; 3 M^2 face values, one per interior face point); stage the
+    Runge-Kutta epilogue's reads of u and z0 next to F."""
+    M = M or N
+    n3, m3, mm = N ** 3, M ** 3, M * M
+    cell = elt * (n3 + 1 + m3 + 12 * mm + (3 * m3 if vb else 0))  # read z, D (, b); write V and 6x2 traces
+    face = elt * (m3 + 2 * 12 * mm + 18 + n3 + (n3 if residual or stage else 0) + (2 * n3 if stage else 0)
+                  + (3 * mm if vb else 0))  # V, own+nbr traces, fc, y, F (, u, z0, b . nu)
     return {"cell": cell, "face": face}

@@ -40,6 +40,8 @@ class Workload:
     lo: tuple = (0.0, 0.0, 0.0)
     hi: tuple = (1.0, 1.0, 1.0)
     periodic: tuple = (0, 0, 0)     # 1 on an axis whose two end faces are identified
+    velocity: str = "constant"      # "constant" (b) or "taylor_green" (the flow field of Sec. 5.3)
+    m: int | None = None            # Gauss points per direction (None: k+1)
 
     @property
     def ncell(self):
@@ -147,6 +149,24 @@ def gaussian_bump(xyz: np.ndarray, x0=(0.5, 0.0, 0.0)) -> np.ndarray:
     return np.exp(-2.0 * np.sum(d * d, axis=-1))
 
 
+def gaussian_bump_grid(w: Workload, xi, x0=(0.5, 0.0, 0.0), xp=np, **kw):
+    """exp(-2 |x - x0|^2) at the volume points [ncell, m^3] of the workload's mesh, built from its three
+    one-dimensional factors (the bump is separable), so no [ncell, m^3, 3] coordinate array is formed.
+    xi: the m Gauss points on [0,1]; xp: numpy or torch (kw, e.g. device=, go to xp.asarray)."""
+    m = len(xi)
+    xi = xp.asarray(np.asarray(xi, dtype=np.float64), **kw)
+    g = []
+    for r in range(3):
+        h = (w.hi[r] - w.lo[r]) / w.n[r]
+        ic = xp.asarray(np.arange(w.n[r], dtype=np.float64), **kw)
+        x = w.lo[r] + h * (ic[:, None] + xi[None, :])          # [n_r, m]
+        g.append(xp.exp(-2.0 * (x - x0[r]) ** 2))
+    gx, gy, gz = g
+    # axes (iz, iy, ix, i3, i2, i1): cell = ix + nx (iy + ny iz), point q = i1 + m (i2 + m i3)
+    v = gz[:, None, None, :, None, None] * gy[None, :, None, None, :, None] * gx[None, None, :, None, None, :]
+    return v.reshape(w.ncell, m ** 3)
+
+
 def face_normal_velocity(bfun, face_xyz: np.ndarray) -> np.ndarray:
     """b . e_dir at the face points of every face of every cell, face_xyz[ncell, 6, m^2, 3] (face s = 2 dir + side)."""
     b = bfun(face_xyz)
@@ -156,8 +176,11 @@ def face_normal_velocity(bfun, face_xyz: np.ndarray) -> np.ndarray:
     return out
 
 
-def taylor_green(n=16, k=5) -> Workload:
-    """Transport on the periodic cube (-pi, pi)^3: D = 5e-6, c = 0, f = 0, Taylor-Green velocity (Sec. 5.3)."""
+def taylor_green(n=16, k=5, m=None) -> Workload:
+    """Transport on the periodic cube (-pi, pi)^3: D = 5e-6, c = 0, f = 0, Taylor-Green velocity and
+    q = 2p+4, i.e. m = k+3 Gauss points per direction (Sec. 5.3).  The initial value is the Gaussian bump
+    exp(-2 |x - (1/2, 0, 0)|^2), projected onto the DG space by the caller."""
     w = Workload(f"taylor_green_q{k}_{n}", (n, n, n), k, np.full(n ** 3, 5e-6), b=(0.0, 0.0, 0.0), c=0.0,
-                 f_kind="zero", lo=(-np.pi,) * 3, hi=(np.pi,) * 3, periodic=(1, 1, 1))
+                 f_kind="zero", lo=(-np.pi,) * 3, hi=(np.pi,) * 3, periodic=(1, 1, 1), velocity="taylor_green",
+                 m=m if m is not None else k + 3)
     return w

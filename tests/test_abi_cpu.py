@@ -80,3 +80,37 @@ def test_setup_rejects_invalid_arguments_on_host():
     assert setup(2, mesh=m2) == -1
     assert dg.lib.dg_setup(ctypes.byref(mesh), 2, ctypes.byref(co), None, None, None, None) == -1
     assert h.value is None
+
+
+def test_setup_ex_rejects_invalid_transport_options_on_host():
+    from paper_1711_10885_gb300 import dg
+    mesh = dg.dg_mesh()
+    for r in range(3):
+        mesh.lo[r], mesh.hi[r], mesh.n[r] = 0.0, 1.0, 2
+    co = dg.dg_coeffs()
+    co.D_const, co.c, co.sigma = 1.0, 0.0, 4.0
+    h = ctypes.c_void_p()
+
+    def setup(k, ext):
+        return dg.lib.dg_setup_ex(ctypes.byref(mesh), k, ctypes.byref(co), None, None, ctypes.byref(ext), None,
+                                  ctypes.byref(h))
+
+    ext = dg.dg_setup_ext()
+    ext.m = 5  # k+2: only k+1 and k+3 are offered
+    assert setup(3, ext) == -1 and b"m must be" in dg.lib.dg_last_error()
+    ext.m, ext.velocity = 0, 7
+    assert setup(3, ext) == -1 and b"velocity" in dg.lib.dg_last_error()
+    ext.velocity = dg.DG_VELOCITY_POINTS  # needs both point arrays
+    assert setup(3, ext) == -1 and b"b_qp" in dg.lib.dg_last_error()
+    ext.velocity = dg.DG_VELOCITY_TAYLOR_GREEN
+    assert setup(9, ext) == -1 and b"k <= 8" in dg.lib.dg_last_error()
+    ext.velocity, ext.periodic[1] = dg.DG_VELOCITY_CONSTANT, 2
+    assert setup(3, ext) == -1 and b"periodic" in dg.lib.dg_last_error()
+    assert h.value is None
+
+
+def test_time_stepping_entry_points_reject_null_arguments_on_host():
+    from paper_1711_10885_gb300 import dg
+    assert dg.lib.dg_project(None, None, None, None) == -1
+    assert dg.lib.dg_rk_stage(None, None, None, None, 0.0, 1.0, 0.1, None) == -1
+    assert dg.lib.dg_ssprk2(None, None, 0.1, 1, None) == -1

@@ -91,3 +91,15 @@ def test_periodic_translation_invariance():
     for axis in (0, 1, 2):
         ys = oracle.apply(pr, np.roll(u, 1, axis=axis).ravel()).reshape(y.shape)
         assert rel(ys, np.roll(y, 1, axis=axis)) < 1e-13
+
+
+def test_rhs_volume_term_reproduces_a_dg_field():
+    """(u_h, phi_i)_T / |T| = z_i for u_h = sum_j z_j phi_j: the m >= k+1 point rule integrates the
+    degree-2k product exactly and the basis is orthonormal (mass matrix |T| I, Sec. 2)."""
+    from tests.test_gpu_transport import oracle_field_values
+    for k, m in ((2, 3), (3, 6)):
+        pr = oracle.Problem((2, 3, 2), k, 1.0, b=(0, 0, 0), c=0.0, m=m, lo=(0, 0, 0), hi=(1, 2, 0.5))
+        z = np.random.default_rng(k).uniform(-1, 1, pr.ndof)
+        vol = 1.0 / 2 * 2.0 / 3 * 0.5 / 2
+        F = oracle.rhs(pr, oracle_field_values(pr, z), None)
+        assert rel(F / vol, z) < 1e-13
