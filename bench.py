@@ -385,7 +385,8 @@ def transport_benchmark(n=64, k=5, steps=10, warmup=3):
     """The transport example of Sec. 5.3 at single-GPU scale: Taylor-Green flow on the periodic cube
     (-pi, pi)^3, D = 5e-6, c = f = 0, q = 2p+4 (m = k+3 Gauss points), Heun's method from the projected
     Gaussian bump.  One step = two Runge-Kutta stages = two operator applications with the stage update
-    fused into the face kernel (dg_ssprk2)."""
+    fused into the face kernel (dg_ssprk2).  Timed with the FP64 operator and with the double-float one
+    (FP64 vectors and FP64 stage updates, operator on the FP32 pipes)."""
     import numpy as np
     import torch
 
@@ -396,49 +397,61 @@ def transport_benchmark(n=64, k=5, steps=10, warmup=3):
     setup_s = time.time() - t0
     xi = (np.polynomial.legendre.leggauss(w.m)[0] + 1.0) / 2.0
     u0 = inputs.gaussian_bump_grid(w, xi, xp=torch, device="cuda")
-    z = op.project(u0.contiguous())
+    z0 = op.project(u0.contiguous())
     del u0
     stream = torch.cuda.current_stream()
     h = 2 * np.pi / n
     dt = 0.3 * h / (2 * k + 1)  # CFL with max |b| = 1
-    mass0 = z.view(w.ncell, -1)[:, 0].sum().item()
-    op.ssprk2(z, dt, warmup)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    op.ssprk2(z, dt, steps)
-    b.record(stream)
-    b.synchronize()
-    ms = a.elapsed_time(b) / steps
-    mass1 = z.view(w.ncell, -1)[:, 0].sum().item()
-    # per-kernel times of one operator application (cell kernel; face kernel with the residual epilogue)
-    r = torch.empty_like(z)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
-    for i in range(steps):
-        ev[3 * i].record(stream)
-        op.apply_stage(0, z, r, residual=True)
-        ev[3 * i + 1].record(stream)
-        op.apply_stage(1, z, r, residual=True)
-        ev[3 * i + 2].record(stream)
-    torch.cuda.synchronize()
-    cell_ms = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(steps)) / steps
-    face_ms = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(steps)) / steps
+    mass0 = z0.view(w.ncell, -1)[:, 0].sum().item()
     N, M = k + 1, w.m
     cell_fl = flops.cell_kernel_flops(N, M, vb=True) * w.ncell
     face_fl = flops.face_kernel_flops(N, M=M, stage=True) * w.ncell
-    finite = bool(torch.isfinite(z).all().item())
+    out = {"workload": w.name, "cells": [n, n, n], "k": k, "m": M, "dofs": w.ndof, "dt": dt,
+           "executed_flops_per_dof_stage": (cell_fl + face_fl) / w.ndof}
+    finals = {}
+    for name, prec in (("f64", dg.DG_F64), ("f64x", dg.DG_F64X)):
+        z = z0.clone()
+        op.ssprk2(z, dt, warmup, precision=prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        op.ssprk2(z, dt, steps, precision=prec)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        mass1 = z.view(w.ncell, -1)[:, 0].sum().item()
+        # per-kernel times of one operator application (cell kernel; face kernel with the residual epilogue)
+        r = torch.empty_like(z)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
+        for i in range(steps):
+            ev[3 * i].record(stream)
+            op.apply_stage(0, z, r, residual=True, precision=prec)
+            ev[3 * i + 1].record(stream)
+            op.apply_stage(1, z, r, residual=True, precision=prec)
+            ev[3 * i + 2].record(stream)
+        torch.cuda.synchronize()
+        cell_ms = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(steps)) / steps
+        face_ms = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(steps)) / steps
+        finals[name] = z
+        out[name] = {"ms_per_heun_step": ms, "heun_steps_per_s": 1e3 / ms,
+                     "mdofs_per_stage": 2 * w.ndof / (ms * 1e-3) / 1e6,
+                     "mdof_steps_per_s": w.ndof / (ms * 1e-3) / 1e6,
+                     "kernels_ms": {"dg_cell_kernel<vb>": cell_ms, "dg_face_kernel<vb>": face_ms},
+                     "fp64_equivalent_tflops": 2 * (cell_fl + face_fl) / (ms * 1e-3) / 1e12,
+                     "mass_drift_rel": abs(mass1 - mass0) / abs(mass0),
+                     "finite": bool(torch.isfinite(z).all().item())}
+    cms = out["f64"]["kernels_ms"]["dg_cell_kernel<vb>"]
+    achieved = cell_fl / (cms * 1e-3) / 1e12
+    out["roofline_f64"] = {"bound": "alu", "kernel": "dg_cell_kernel<double, M=8, VB>", "achieved": achieved,
+                           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                           "flops_per_launch": cell_fl}
+    out["f64x_vs_f64_after_steps"] = float(((finals["f64x"] - finals["f64"]).abs().max()
+                                            / finals["f64"].abs().max()).item())
+    out["setup_s"] = setup_s
+    out["paper_context"] = ("240^3 p=5 (3e9 DOF), 165000 steps in 143000 core-h on 6144 cores incl. I/O "
+                            "(Sec. 5.3): about 5.9e3 MDOF-steps/s for that machine")
     op.close()
-    return {"workload": w.name, "cells": [n, n, n], "k": k, "m": M, "dofs": w.ndof, "dt": dt,
-            "ms_per_heun_step": ms, "heun_steps_per_s": 1e3 / ms,
-            "mdofs_per_stage": 2 * w.ndof / (ms * 1e-3) / 1e6,
-            "mdof_steps_per_s": w.ndof / (ms * 1e-3) / 1e6,
-            "kernels_ms": {"dg_cell_kernel<vb>": cell_ms, "dg_face_kernel<vb>": face_ms},
-            "cell_kernel_fp64_frac": cell_fl / (cell_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-            "executed_flops_per_dof_stage": (cell_fl + face_fl) / w.ndof,
-            "fp64_tflops_executed": 2 * (cell_fl + face_fl) / (ms * 1e-3) / 1e12,
-            "mass_drift_rel": abs(mass1 - mass0) / abs(mass0), "finite": finite, "setup_s": setup_s,
-            "paper_context": "240^3 p=5 (3e9 DOF), 165000 steps in 143000 core-h on 6144 cores incl. I/O "
-                             "(Sec. 5.3): about 5.9e3 MDOF-steps/s for that machine"}
+    return out
 
 
 def run_ours(args):

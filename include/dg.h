@@ -354,8 +354,8 @@ typedef struct {
 } dg_setup_ext;
 
 /* dg_setup with the options above (ext = NULL is dg_setup).  A field b(x) or m = k+3 selects the
- * velocity field kernels, which support degrees 1..8 and DG_F64 applies only (DG_F32 / DG_F64X
- * applies, the mixed-precision solver, block-Jacobi and batches reject such a handle).  On a periodic
+ * velocity field kernels, which support degrees 1..8 and DG_F64 and DG_F64X applies (DG_F32 applies,
+ * the mixed-precision solver, block-Jacobi and batches reject such a handle).  On a periodic
  * axis with a single cell the cell is its own neighbour.  Synchronises `stream`. */
 int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* coeffs, const dg_bc* bc, const double* f_qp,
                 const dg_setup_ext* ext, void* stream, dg_handle** out);
@@ -369,15 +369,16 @@ int dg_project(dg_handle* h, const double* u_qp_dev, double* z_dev, void* stream
  *     y = cz * z0 + cu * u - cdt * M^{-1} (A u - F)
  * fused into the operator's face kernel.  F is the right hand side of the handle (f and g do not
  * depend on time here).  u, z0, y are FP64 device vectors; y may alias u or z0 (every element is
- * read before it is written, by the same thread). */
+ * read before it is written, by the same thread).  precision: DG_F64, or DG_F64X (A u - F in
+ * double-float; the update itself is FP64 in both). */
 int dg_rk_stage(dg_handle* h, const double* u_dev, const double* z0_dev, double* y_dev, double cz, double cu,
-                double cdt, void* stream);
+                double cdt, int32_t precision, void* stream);
 
 /* nsteps steps of Heun's method, the second-order strong-stability-preserving Runge-Kutta scheme of
  * Sec. 5.3, on z_dev in place:  z1 = z - dt M^{-1}(A z - F);  z <- (z + z1 - dt M^{-1}(A z1 - F)) / 2.
  * Four kernel launches per step; the stage vector is kept by the handle (allocated on the first
- * call, which then synchronises `stream`). */
-int dg_ssprk2(dg_handle* h, double* z_dev, double dt, int32_t nsteps, void* stream);
+ * call, which then synchronises `stream`).  precision as in dg_rk_stage. */
+int dg_ssprk2(dg_handle* h, double* z_dev, double dt, int32_t nsteps, int32_t precision, void* stream);
 
 /* Message for the calling thread's last error ("" if none). */
 const char* dg_last_error(void);

@@ -148,6 +148,8 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->bj32);
   cudaFree(h->bsc);
   cudaFree(h->bface);
+  cudaFree(h->bscX);
+  cudaFree(h->bfaceX);
   cudaFree(h->rk_tmp);
   cudaFree(h->ws);
   if (h->ws_host) cudaFreeHost(h->ws_host);
@@ -433,8 +435,8 @@ static int check_apply(dg_handle* h, const void* in, void* out, int32_t precisio
     set_error(std::string(name) + ": precision must be DG_F64, DG_F32 or DG_F64X");
     return DG_ERR_INVALID_ARG;
   }
-  if (h->vb && precision != DG_F64) {
-    set_error(std::string(name) + ": a handle with a velocity field or m = k+3 applies in DG_F64 only");
+  if (h->vb && precision == DG_F32) {
+    set_error(std::string(name) + ": a handle with a velocity field or m = k+3 applies in DG_F64 or DG_F64X only");
     return DG_ERR_INVALID_ARG;
   }
   int dev = -1;

@@ -40,6 +40,8 @@ struct dg_handle {
   bool vb = false;
   void* bsc = nullptr;
   void* bface = nullptr;
+  void* bscX = nullptr;      // double-float copies of the two tables (DG_F64X applies)
+  void* bfaceX = nullptr;
   void* rk_tmp = nullptr;    // Runge-Kutta stage vector (FP64, allocated by the first dg_ssprk2 call)
   int64_t ncell = 0;
   double lo[3], hi[3], h[3];
@@ -87,6 +89,7 @@ struct StageArgs {
   double cz, cu, cr;
 };
 int launch_stage_f64(const dg_handle* h, const double* u, double* y, const StageArgs& st, cudaStream_t s);
+int launch_stage_f64x(const dg_handle* h, const double* u, double* y, const StageArgs& st, cudaStream_t s);
 // velocity field tables of a vb handle (allocates h->bsc and h->bface): kind DG_VELOCITY_*, the constant b,
 // or host arrays b_qp [ncell][M^3][3] and b_face [ncell][6][M^2]
 int setup_velocity(dg_handle* h, int kind, const double b[3], const double* b_qp, const double* b_face,
@@ -96,5 +99,7 @@ int launch_apply_f64_vb(const dg_handle* h, const double* z, double* y, int mode
                         cudaStream_t s);
 int launch_rhs_f64_vb(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,
                       bool project);
+int launch_apply_f64x_vb(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+                         cudaStream_t s);
 
 }  // namespace dgi

@@ -469,7 +469,7 @@ struct FaceArgs {
   int mode;
   const TV* u;      // mode 3: the stage input (the vector the cell kernel read)
   const TV* z0;     // mode 3: the step's initial value (may be y: each element is read before it is written)
-  T cz, cu, cr;     // mode 3 coefficients
+  double cz, cu, cr;  // mode 3 coefficients (the stage update runs in FP64)
 };
 
 // face test weights of this thread's face point on face (dir, s): value weight Vf and normal-derivative
@@ -630,26 +630,51 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
       val = sV[c * CS + Lay<M>::idx(i1, i23 % N, i23 / N)];
     }
     if (fa.mode == 1) val = val - Fs[e];
-    if constexpr (std::is_same<T, double>::value) {  // Runge-Kutta stages are offered in FP64 only
+    TV out = from_compute<TV, T>(val);
+    if constexpr (!std::is_same<T, float>::value) {
+      // Runge-Kutta stage (FP64 vectors): the update itself is done in FP64 also when the operator ran in
+      // double-float, so the state keeps full FP64 precision from step to step
       if (fa.mode == 3) {
         const size_t ge = (size_t)cell0 * N3 + e;
-        const T r_ = Fs ? val - Fs[e] : val;
-        val = fma(fa.cz, to_compute<T, TV>(fa.z0[ge]), fma(fa.cu, to_compute<T, TV>(fa.u[ge]), -fa.cr * r_));
+        const double rd = Fs ? out - from_compute<double, T>(Fs[e]) : out;
+        out = fma(fa.cz, (double)fa.z0[ge], fma(fa.cu, (double)fa.u[ge], -fa.cr * rd));
       }
     }
-    dst[e] = from_compute<TV, T>(val);
+    dst[e] = out;
   }
 }
 
 template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false,
           bool PER = false>
-__global__ void __launch_bounds__(CPB * M * M, (std::is_same<T, float>::value && CPB * M * M == 256) ? 8 : 1)
+__global__ void __launch_bounds__(CPB * M * M)
 dg_face_kernel(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g,
                const __grid_constant__ FaceArgs<T, TV> fa, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
   face_tile<N, T, SELF, CPB, TV, M, VB, PER>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
+}
+
+// The same kernel with 8 resident CTAs of 256 threads requested: used for FP32 when a CTA has 256 threads
+// (k = 1, 3, 7), where the compiler otherwise settles on more than the 32 registers per thread that allow it.
+template <int N, typename T, int CPB, typename TV, int M, bool PER>
+__global__ void __launch_bounds__(CPB * M * M, 8)
+dg_face_kernel_occ8(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g,
+                    const __grid_constant__ FaceArgs<T, TV> fa, SelfArgs sa_) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * CPB;
+  const int here = min(CPB, g.ncell - cell0);
+  face_tile<N, T, false, CPB, TV, M, false, PER>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
+}
+
+// the face kernel of a launch configuration (the FP32 256-thread variant above, or the general one)
+template <int N, typename T, int CPB, typename TV, int M, bool VB, bool PER>
+constexpr auto face_kernel_for() {
+  if constexpr (std::is_same<T, float>::value && !VB && CPB * M * M == 256) {
+    return &dg_face_kernel_occ8<N, T, CPB, TV, M, PER>;
+  } else {
+    return &dg_face_kernel<N, T, false, CPB, TV, M, VB, PER>;
+  }
 }
 
 }  // namespace dgk

@@ -84,11 +84,11 @@ int set_smem_attrs() {
   cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<M, T>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel)");
-  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, true>,
+  e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, true>(),
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
   if constexpr (!VB) {
-    e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, false>,
+    e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, false>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T>());
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
   }
@@ -97,17 +97,17 @@ int set_smem_attrs() {
 }
 
 // face kernel launch: the periodic-aware variant when the mesh has a periodic axis (always for the
-// velocity field kernels, which are FP64 only and lose nothing by it)
+// velocity field kernels)
 template <int N, typename T, typename TV, int M, bool VB>
 void launch_face(const dg_handle* h, const dgk::TabNM<N, M, T>& tb, const dgk::Geo<T>& geo,
                  const dgk::FaceArgs<T, TV>& fa, unsigned grid, cudaStream_t s) {
   constexpr int CPB = dgk::Launch<M>::CPB;
   const bool per = h->periodic[0] || h->periodic[1] || h->periodic[2];
   if (VB || per) {
-    dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, true>
+    dgk::face_kernel_for<N, T, CPB, TV, M, VB, true>()
         <<<grid, dgk::Launch<M>::THREADS, face_smem<M, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
   } else if constexpr (!VB) {
-    dgk::dg_face_kernel<N, T, false, CPB, TV, M, VB, false>
+    dgk::face_kernel_for<N, T, CPB, TV, M, VB, false>()
         <<<grid, dgk::Launch<M>::THREADS, face_smem<M, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
   }
 }
@@ -136,13 +136,14 @@ int set_self_smem_attrs() {
   return 0;
 }
 
-// geometry of the handle with the velocity field tables of the VB kernels
+// geometry of the handle with the velocity field tables of the VB kernels (FP64, or the double-float copies)
 template <typename T, bool VB>
 dgk::Geo<T> geo_for(const dg_handle* h) {
   dgk::Geo<T> geo = make_geo<T>(h);
   if (VB) {
-    geo.bsc = static_cast<const T*>(h->bsc);
-    geo.bface = static_cast<const T*>(h->bface);
+    const bool pair = std::is_same<T, dgk::dfl>::value;
+    geo.bsc = static_cast<const T*>(pair ? h->bscX : h->bsc);
+    geo.bface = static_cast<const T*>(pair ? h->bfaceX : h->bface);
   }
   return geo;
 }
@@ -171,16 +172,16 @@ int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaSt
   fa.mode = mode;
   fa.u = z;
   fa.z0 = nullptr;
-  fa.cz = fa.cu = fa.cr = T(0);
+  fa.cz = fa.cu = fa.cr = 0.0;
   if (mode == 3) {
-    if (!st) {
-      set_error("Runge-Kutta stage without coefficients");
+    if (!st || !std::is_same<TV, double>::value || std::is_same<T, float>::value) {
+      set_error("Runge-Kutta stages need FP64 vectors and the FP64 or double-float operator");
       return DG_ERR_INVALID_ARG;
     }
     fa.z0 = reinterpret_cast<const TV*>(st->z0);
-    fa.cz = (T)st->cz;
-    fa.cu = (T)st->cu;
-    fa.cr = (T)st->cr;
+    fa.cz = st->cz;
+    fa.cu = st->cu;
+    fa.cr = st->cr;
   }
   if (stages & 2) launch_face<N, T, TV, M, VB>(h, tb, geo, fa, grid, s);
   cudaError_t e = cudaGetLastError();
@@ -207,7 +208,7 @@ int rhs_n(const dg_handle* h, const T* f, const T* const g[6], T* F, cudaStream_
   fa.mode = 2;
   fa.u = nullptr;
   fa.z0 = nullptr;
-  fa.cz = fa.cu = fa.cr = T(0);
+  fa.cz = fa.cu = fa.cr = 0.0;
   launch_face<N, T, T, M, VB>(h, tb, geo, fa, grid, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rhs kernel launch");
@@ -285,12 +286,13 @@ int rhs_dispatch(const dg_handle* h, const T* f, const T* const g[6], T* F, cuda
 
 namespace dgi {
 
-// The velocity field kernels: M = N (q = 2p) or M = N + 2 (q = 2p+4), degrees 1..8, FP64.
-template <int N>
+// The velocity field kernels: M = N (q = 2p) or M = N + 2 (q = 2p+4), degrees 1..8, FP64 vectors, operator
+// in FP64 (T = double) or double-float (T = dfl).
+template <int N, typename T = double>
 int apply_vb_n(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
                cudaStream_t s) {
-  if (h->M == N) return apply_n<N, double, double, N, true>(h, z, y, mode, stages, s, st);
-  if (h->M == N + 2) return apply_n<N, double, double, N + 2, true>(h, z, y, mode, stages, s, st);
+  if (h->M == N) return apply_n<N, T, double, N, true>(h, z, y, mode, stages, s, st);
+  if (h->M == N + 2) return apply_n<N, T, double, N + 2, true>(h, z, y, mode, stages, s, st);
   set_error("unsupported number of quadrature points");
   return DG_ERR_INVALID_ARG;
 }

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <string>
 
+#include "dg_dfloat.cuh"
 #include "dg_internal.h"
 
 namespace {
@@ -93,6 +94,12 @@ __global__ void scale_velocity(PointGeo pg, const double* __restrict__ raw, doub
   }
 }
 
+// double-float copy of a table (DG_F64X applies of the velocity field kernels)
+__global__ void to_pairs(const double* __restrict__ a, dgk::dfl* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = dgk::dfl_from_double(a[i]);
+}
+
 unsigned grid_for(int64_t n) {
   const int64_t blocks = (n + 255) / 256;
   return (unsigned)(blocks > 152 * 16 ? 152 * 16 : (blocks > 0 ? blocks : 1));
@@ -120,6 +127,8 @@ int setup_velocity(dg_handle* h, int kind, const double b[3], const double* b_qp
   double* raw = nullptr;
   cudaError_t e = cudaMalloc(&h->bsc, npts * 3 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->bface, nface * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->bscX, npts * 3 * sizeof(dgk::dfl));
+  if (e == cudaSuccess) e = cudaMalloc(&h->bfaceX, nface * sizeof(dgk::dfl));
   if (e == cudaSuccess) e = cudaMalloc(&raw, npts * 3 * sizeof(double));
   if (e != cudaSuccess) {
     cudaFree(raw);
@@ -137,6 +146,10 @@ int setup_velocity(dg_handle* h, int kind, const double b[3], const double* b_qp
   }
   if (e == cudaSuccess) {
     scale_velocity<<<grid_for(npts * 3), 256, 0, s>>>(pg, raw, static_cast<double*>(h->bsc), npts * 3);
+    to_pairs<<<grid_for(npts * 3), 256, 0, s>>>(static_cast<const double*>(h->bsc), static_cast<dgk::dfl*>(h->bscX),
+                                                npts * 3);
+    to_pairs<<<grid_for(nface), 256, 0, s>>>(static_cast<const double*>(h->bface),
+                                             static_cast<dgk::dfl*>(h->bfaceX), nface);
     e = cudaGetLastError();
   }
   // the temporary field is released once the kernels that read it are done
@@ -162,10 +175,19 @@ int dg_project(dg_handle* h, const double* u_qp, double* z, void* stream) {
   return launch_rhs_f64(h, u_qp, none, z, static_cast<cudaStream_t>(stream), true);
 }
 
+static int stage(const dg_handle* h, const double* u, double* y, const StageArgs& st, int32_t precision,
+                 cudaStream_t s) {
+  return precision == DG_F64X ? launch_stage_f64x(h, u, y, st, s) : launch_stage_f64(h, u, y, st, s);
+}
+
 int dg_rk_stage(dg_handle* h, const double* u, const double* z0, double* y, double cz, double cu, double cdt,
-                void* stream) {
+                int32_t precision, void* stream) {
   if (!h || !u || !z0 || !y) {
     set_error("dg_rk_stage: null argument");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (precision != DG_F64 && precision != DG_F64X) {
+    set_error("dg_rk_stage: precision must be DG_F64 or DG_F64X");
     return DG_ERR_INVALID_ARG;
   }
   if (!std::isfinite(cz) || !std::isfinite(cu) || !std::isfinite(cdt)) {
@@ -174,12 +196,12 @@ int dg_rk_stage(dg_handle* h, const double* u, const double* z0, double* y, doub
   }
   const double vol = h->h[0] * h->h[1] * h->h[2];
   const StageArgs st{z0, cz, cu, cdt / vol};  // M^{-1} = I / |T|
-  return launch_stage_f64(h, u, y, st, static_cast<cudaStream_t>(stream));
+  return stage(h, u, y, st, precision, static_cast<cudaStream_t>(stream));
 }
 
-int dg_ssprk2(dg_handle* h, double* z, double dt, int32_t nsteps, void* stream) {
-  if (!h || !z || nsteps < 0 || !std::isfinite(dt)) {
-    set_error("dg_ssprk2: bad arguments");
+int dg_ssprk2(dg_handle* h, double* z, double dt, int32_t nsteps, int32_t precision, void* stream) {
+  if (!h || !z || nsteps < 0 || !std::isfinite(dt) || (precision != DG_F64 && precision != DG_F64X)) {
+    set_error("dg_ssprk2: bad arguments (precision DG_F64 or DG_F64X, nsteps >= 0, finite dt)");
     return DG_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -194,8 +216,8 @@ int dg_ssprk2(dg_handle* h, double* z, double dt, int32_t nsteps, void* stream) 
   const StageArgs st1{z, 0.0, 1.0, dt / vol};
   const StageArgs st2{z, 0.5, 0.5, 0.5 * dt / vol};
   for (int32_t i = 0; i < nsteps; ++i) {
-    if (int rc = launch_stage_f64(h, z, z1, st1, s)) return rc;   // z1 = z - dt M^{-1}(A z - F)
-    if (int rc = launch_stage_f64(h, z1, z, st2, s)) return rc;   // z = (z + z1 - dt M^{-1}(A z1 - F)) / 2
+    if (int rc = stage(h, z, z1, st1, precision, s)) return rc;   // z1 = z - dt M^{-1}(A z - F)
+    if (int rc = stage(h, z1, z, st2, precision, s)) return rc;   // z = (z + z1 - dt M^{-1}(A z1 - F)) / 2
   }
   return DG_OK;
 }

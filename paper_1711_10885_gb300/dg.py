@@ -101,8 +101,8 @@ def _load():
     lib.dg_setup_ex.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int32, ctypes.POINTER(dg_coeffs),
                                 ctypes.POINTER(dg_bc), _dp, ctypes.POINTER(dg_setup_ext), vp, ctypes.POINTER(vp)]
     lib.dg_project.argtypes = [vp, vp, vp, vp]
-    lib.dg_rk_stage.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp]
-    lib.dg_ssprk2.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int32, vp]
+    lib.dg_rk_stage.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp]
+    lib.dg_ssprk2.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, vp]
     lib.dg_destroy.argtypes = [vp]
     lib.dg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_int64)]
@@ -366,17 +366,19 @@ class Operator:
                              _stream_ptr(stream)))
         return z
 
-    def rk_stage(self, u, z0, y, cz, cu, cdt, stream=None):
+    def rk_stage(self, u, z0, y, cz, cu, cdt, stream=None, precision=DG_F64):
         """y = cz z0 + cu u - cdt M^{-1}(A u - F) (dg_rk_stage, FP64 CUDA tensors; y may alias u or z0)."""
         self._vec_check(u, z0, y)
         check(lib.dg_rk_stage(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(z0.data_ptr()),
-                              ctypes.c_void_p(y.data_ptr()), float(cz), float(cu), float(cdt), _stream_ptr(stream)))
+                              ctypes.c_void_p(y.data_ptr()), float(cz), float(cu), float(cdt), int(precision),
+                              _stream_ptr(stream)))
         return y
 
-    def ssprk2(self, z, dt, nsteps=1, stream=None):
-        """nsteps Heun steps on the FP64 CUDA tensor z in place (dg_ssprk2)."""
+    def ssprk2(self, z, dt, nsteps=1, stream=None, precision=DG_F64):
+        """nsteps Heun steps on the FP64 CUDA tensor z in place (dg_ssprk2); precision DG_F64 or DG_F64X."""
         self._vec_check(z)
-        check(lib.dg_ssprk2(self.h, ctypes.c_void_p(z.data_ptr()), float(dt), int(nsteps), _stream_ptr(stream)))
+        check(lib.dg_ssprk2(self.h, ctypes.c_void_p(z.data_ptr()), float(dt), int(nsteps), int(precision),
+                            _stream_ptr(stream)))
         return z
 
     def rhs(self, dtype=None, stream=None):

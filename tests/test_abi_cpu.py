@@ -112,5 +112,5 @@ def test_setup_ex_rejects_invalid_transport_options_on_host():
 def test_time_stepping_entry_points_reject_null_arguments_on_host():
     from paper_1711_10885_gb300 import dg
     assert dg.lib.dg_project(None, None, None, None) == -1
-    assert dg.lib.dg_rk_stage(None, None, None, None, 0.0, 1.0, 0.1, None) == -1
-    assert dg.lib.dg_ssprk2(None, None, 0.1, 1, None) == -1
+    assert dg.lib.dg_rk_stage(None, None, None, None, 0.0, 1.0, 0.1, 0, None) == -1
+    assert dg.lib.dg_ssprk2(None, None, 0.1, 1, 0, None) == -1
