@@ -229,6 +229,19 @@ def run_profile(args):
     if args.profile_solver:
         return run_profile_solver(args)
     torch.cuda.set_device(0)
+    if args.transport:
+        # Taylor-Green transport (k = 5, m = 8): W + K Heun steps, 4 launches each
+        import numpy as np
+        w = inputs.taylor_green(args.transport, 5)
+        op = dg.operator_for(w)
+        xi = (np.polynomial.legendre.leggauss(w.m)[0] + 1.0) / 2.0
+        z = op.project(inputs.gaussian_bump_grid(w, xi, xp=torch, device="cuda").contiguous())
+        prec = dg.DG_F64X if args.precision == "f64x" else dg.DG_F64
+        op.ssprk2(z, 0.3 * 2 * np.pi / args.transport / 11, args.warmup + args.steps, precision=prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "heun_steps": args.warmup + args.steps, "z_max": float(z.abs().max())}))
+        op.close()
+        return
     w = inputs.unit_cube_q7_32()
     op = dg.operator_for(w)
     u = torch.tensor(w.u, device="cuda")
@@ -623,7 +636,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--no-transport", action="store_true", help="skip the Taylor-Green transport section")
     ap.add_argument("--transport", type=int, default=None, metavar="N",
-                    help="print only the Taylor-Green transport benchmark on N^3 cells (k = 5, m = 8)")
+                    help="print only the Taylor-Green transport benchmark on N^3 cells (k = 5, m = 8); with "
+                         "--profile: only W + K Heun steps of it")
     ap.add_argument("--solve-only", nargs="?", const="all", default=None, choices=["all", "mixed", "learned"],
                     help="print the solver comparisons only (mixed precision at 48^3 Q5, learned at 64^3 Q4)")
     ap.add_argument("--profile-solver", action="store_true",

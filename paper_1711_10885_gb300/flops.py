@@ -83,12 +83,13 @@ def apply_flops_per_dof(k: int, n=(1, 1, 1), residual: bool = True) -> float:
 
 def bytes_per_cell(N: int, elt: int = 8, residual: bool = True, M: int | None = None, vb: bool = False,
                    stage: bool = False) -> dict:
-    """Algorithmic DRAM bytes per cell of each kernel: its compulsory reads and writes.  vb adds the
-    velocity tables (3 M^3 volume values; 3 M^2 face values, one per interior face point); stage the
-    Runge-Kutta epilogue's reads of u and z0 next to F."""
+    """Algorithmic DRAM bytes per cell of each kernel: its compulsory reads and writes.  The face kernel
+    reads every cell's traces twice (as its own and as a neighbour's); the second read is an L2 hit, so
+    the traces count once.  vb adds the velocity tables (3 M^3 volume values; 3 M^2 face values, one per
+    interior face point); stage the Runge-Kutta epilogue's reads of u and z0 next to F."""
     M = M or N
     n3, m3, mm = N ** 3, M ** 3, M * M
     cell = elt * (n3 + 1 + m3 + 12 * mm + (3 * m3 if vb else 0))  # read z, D (, b); write V and 6x2 traces
-    face = elt * (m3 + 2 * 12 * mm + 18 + n3 + (n3 if residual or stage else 0) + (2 * n3 if stage else 0)
-                  + (3 * mm if vb else 0))  # V, own+nbr traces, fc, y, F (, u, z0, b . nu)
+    face = elt * (m3 + 12 * mm + 18 + n3 + (n3 if residual or stage else 0) + (2 * n3 if stage else 0)
+                  + (3 * mm if vb else 0))  # V, traces, fc, y, F (, u, z0, b . nu)
     return {"cell": cell, "face": face}
