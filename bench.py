@@ -38,14 +38,14 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
 # kernels as they were when profiled, keyed by the sha256 of the kernel source at that time.
 NCU_TRAFFIC = {
-    ("dg_cell_kernel", "f46eab9c62c74d38"): 409366784,  # 135.64 MB read + 273.72 MB write
-    ("dg_face_kernel", "f46eab9c62c74d38"): 589047808,  # 474.55 MB read + 114.50 MB write
+    ("dg_cell_kernel", "8c1608fcf3d82c42"): 134540032 + 273837568,  # 134.54 MB read + 273.84 MB write
+    ("dg_face_kernel", "8c1608fcf3d82c42"): 474537472 + 113914880,  # 474.54 MB read + 113.91 MB write
 }
 
 
 # FP32 lane instructions (FADD + FFMA + FMUL) per cell of the double-float kernels at k = 7, from the ncu
 # counters smsp__sass_thread_inst_executed_op_{fadd,ffma,fmul}_pred_on.sum of one launch / 32768 cells
-F64X_FP32_INST_PER_CELL = {"cell": (9714008064 + 2585788416 + 878706688) / 32768,
+F64X_FP32_INST_PER_CELL = {"cell": (9747562496 + 2602565632 + 878706688) / 32768,
                            "face": (5093392384 + 1496776704 + 499712000) / 32768}
 
 
