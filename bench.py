@@ -229,6 +229,20 @@ def run_profile(args):
     if args.profile_solver:
         return run_profile_solver(args)
     torch.cuda.set_device(0)
+    if args.matrix:
+        # matrix-based comparison: assemble on matrix_n^3 cells of degree matrix_k, then W + K products
+        w = inputs.small_case(n=(args.matrix_n,) * 3, k=args.matrix_k, seed=200 + args.matrix_k)
+        op = dg.operator_for(w)
+        A = dg.Matrix(op)
+        x = torch.tensor(w.u, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(args.warmup + args.steps):
+            A.spmv(x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "spmv": args.warmup + args.steps, "nnzb": A.nnzb, "y_max": float(y.abs().max())}))
+        A.close()
+        op.close()
+        return
     if args.transport:
         # Taylor-Green transport (k = 5, m = 8): W + K Heun steps, 4 launches each
         import numpy as np
@@ -304,6 +318,76 @@ def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10):
         b.synchronize()
         out[f"block_jacobi_{prec}_ms"] = a.elapsed_time(b) / 20
     op.close()
+    return out
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def matrix_benchmark(reps=20, degrees=(1, 3, 5, 7)):
+    """Matrix-free vs matrix-based application (Sec. 5.2 table): per degree, the operator's block-sparse
+    matrix is assembled on a mesh whose matrix takes 3-40 GB of HBM, and its product is timed next
+    to the matrix-free FP64 (and double-float) application on a ~17-24 M DOF mesh of the same workload
+    family (per-cell log-normal D, b = (1, .5, .25), c = 1).  The matrix-based meshes are smaller, as in
+    the paper, because the matrix has 7 (k+1)^6 entries per cell."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, inputs
+    peak, peak_src = hbm_peak_gbs()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    n_mat = {1: 96, 2: 64, 3: 48, 4: 32, 5: 24, 6: 18, 7: 14}  # matrices of 3-40 GB, >= 2744 block rows
+    n_free = {1: 128, 2: 96, 3: 64, 4: 56, 5: 48, 6: 40, 7: 32}
+    out = {"hbm_peak_gbs": peak, "hbm_peak_source": peak_src, "degrees": {}}
+    for k in degrees:
+        nb = (k + 1) ** 3
+        wm = inputs.small_case(n=(n_mat[k],) * 3, k=k, seed=200 + k)
+        op = dg.operator_for(wm)
+        A = dg.Matrix(op)
+        x = torch.tensor(wm.u, device="cuda")
+        y = torch.empty_like(x)
+        ms_spmv = timed(lambda: A.spmv(x, y))
+        bytes_spmv = A.nnzb * nb * nb * 8 + A.nnzb * nb * 8 + wm.ndof * 8 + (A.nrows + 1 + A.nnzb) * 4
+        check = float((y - op.apply_jacobian(x)).abs().max() / op.apply_jacobian(x).abs().max())
+        rec = {"matrix_mesh": [n_mat[k]] * 3, "matrix_dofs": wm.ndof, "matrix_gb": A.nnzb * nb * nb * 8 / 1e9,
+               "assembly_s": A.assemble_seconds, "assembly_mdofs": wm.ndof / A.assemble_seconds / 1e6,
+               "spmv_ms": ms_spmv, "spmv_mdofs": wm.ndof / (ms_spmv * 1e-3) / 1e6,
+               "spmv_gbs": bytes_spmv / (ms_spmv * 1e-3) / 1e9, "spmv_hbm_frac": bytes_spmv / (ms_spmv * 1e-3) / 1e9 / peak,
+               "spmv_vs_apply_rel": check}
+        A.close()
+        op.close()
+        del x, y
+        wf = inputs.small_case(n=(n_free[k],) * 3, k=k, seed=300 + k)
+        op = dg.operator_for(wf)
+        x = torch.tensor(wf.u, device="cuda")
+        y = torch.empty_like(x)
+        ms64 = timed(lambda: op.apply_jacobian(x, y))
+        msx = timed(lambda: op.apply_jacobian(x, y, precision=dg.DG_F64X))
+        rec.update({"free_mesh": [n_free[k]] * 3, "free_dofs": wf.ndof,
+                    "free_f64_mdofs": wf.ndof / (ms64 * 1e-3) / 1e6, "free_f64x_mdofs": wf.ndof / (msx * 1e-3) / 1e6})
+        rec["speedup_f64_over_matrix"] = rec["free_f64_mdofs"] / rec["spmv_mdofs"]
+        rec["speedup_f64x_over_matrix"] = rec["free_f64x_mdofs"] / rec["spmv_mdofs"]
+        out["degrees"][k] = rec
+        op.close()
+    out["paper_context"] = ("2x Xeon E5-2698v3, 32 cores (Sec. 5.2 table): p=7 matrix-free A 570 MDOF/s, "
+                            "matrix-based 1.46 MDOF/s (x390), assembly 0.66 MDOF/s; p=1: 170 vs 206 MDOF/s")
     return out
 
 
@@ -618,6 +702,8 @@ def run_ours(args):
         line["batch"] = batch_benchmark()
     if ws == 1 and not args.no_transport:
         line["transport"] = transport_benchmark()
+    if ws == 1 and not args.no_matrix:
+        line["matrix_based"] = matrix_benchmark(degrees=(3, 7))
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -635,6 +721,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--no-transport", action="store_true", help="skip the Taylor-Green transport section")
+    ap.add_argument("--no-matrix", action="store_true", help="skip the matrix-based comparison section")
+    ap.add_argument("--matrix", action="store_true",
+                    help="print only the matrix-free vs matrix-based comparison for k = 1, 3, 5, 7; with --profile: "
+                         "assemble on --matrix-n^3 cells of degree --matrix-k and run W + K products")
+    ap.add_argument("--matrix-k", type=int, default=7)
+    ap.add_argument("--matrix-n", type=int, default=8)
     ap.add_argument("--transport", type=int, default=None, metavar="N",
                     help="print only the Taylor-Green transport benchmark on N^3 cells (k = 5, m = 8); with "
                          "--profile: only W + K Heun steps of it")
@@ -653,6 +745,10 @@ def main():
         run_reference(args)
     elif args.profile:
         run_profile(args)
+    elif args.matrix:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"matrix_based": matrix_benchmark()}), flush=True)
     elif args.transport:
         import torch
         torch.cuda.set_device(0)

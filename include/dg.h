@@ -380,6 +380,35 @@ int dg_rk_stage(dg_handle* h, const double* u_dev, const double* z0_dev, double*
  * call, which then synchronises `stream`).  precision as in dg_rk_stage. */
 int dg_ssprk2(dg_handle* h, double* z_dev, double dt, int32_t nsteps, int32_t precision, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Matrix-based comparison (Sec. 5.2, table of matrix-free vs matrix-based application and matrix
+ * assembly).  The operator's matrix in block compressed row storage: block row T holds one
+ * (k+1)^3 x (k+1)^3 block A_{T,S} for S = T and each face neighbour of T (sorted by S; on a periodic
+ * axis with one or two cells, coinciding neighbours share one block), nb = (k+1)^3.  On the device the
+ * blocks are column-major with each column padded to an even length; dg_matrix_export returns them
+ * column-major without padding: entry (i, j) of block b at vals[(b*nb + j)*nb + i].
+ * --------------------------------------------------------------------------------------------- */
+typedef struct dg_matrix dg_matrix;
+
+/* Assemble the FP64 matrix of the handle's operator (A of dg_apply_jacobian) on the device, by applying
+ * the matrix-free operator to colour-class probe vectors: cells are coloured so that no two cells of a
+ * colour share a face neighbour (27 colours on a non-periodic mesh), and each (colour, basis index)
+ * pair costs one operator application.  Needs (k+1)^3 <= 512.  Memory: about nnzb * (k+1)^6 * 8 bytes,
+ * owned by the matrix.  Synchronises `stream`. */
+int dg_assemble(dg_handle* h, void* stream, dg_matrix** out);
+
+/* Block rows, stored blocks, block size, and the assembly time in seconds (device events). */
+int dg_matrix_info(const dg_matrix* m, int64_t* nrows, int64_t* nnzb, int32_t* block, double* assemble_seconds);
+
+/* Copy the structure (host arrays of nrows+1 and nnzb entries) and the values (host, nnzb*nb*nb) out;
+ * any pointer may be NULL.  Synchronous. */
+int dg_matrix_export(const dg_matrix* m, int32_t* rowptr_host, int32_t* colidx_host, double* vals_host);
+
+/* y = A x, block sparse matrix-vector product (FP64 device vectors, x != y), asynchronous on `stream`. */
+int dg_spmv(const dg_matrix* m, const double* x_dev, double* y_dev, void* stream);
+
+int dg_matrix_destroy(dg_matrix* m);
+
 /* Message for the calling thread's last error ("" if none). */
 const char* dg_last_error(void);
 

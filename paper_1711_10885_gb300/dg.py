@@ -103,6 +103,12 @@ def _load():
     lib.dg_project.argtypes = [vp, vp, vp, vp]
     lib.dg_rk_stage.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp]
     lib.dg_ssprk2.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, vp]
+    lib.dg_assemble.argtypes = [vp, vp, ctypes.POINTER(vp)]
+    lib.dg_matrix_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+    lib.dg_matrix_export.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _dp]
+    lib.dg_spmv.argtypes = [vp, vp, vp, vp]
+    lib.dg_matrix_destroy.argtypes = [vp]
     lib.dg_destroy.argtypes = [vp]
     lib.dg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_int64)]
@@ -145,7 +151,8 @@ EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadra
             "dg_batch_destroy", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_dims", "dg_mlp_params",
             "dg_mlp_param_offsets", "dg_mlp_set_target_scale", "dg_mlp_features", "dg_mlp_forward", "dg_mlp_loss_grad",
             "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load",
-            "dg_apply_jacobian_static", "dg_setup_ex", "dg_project", "dg_rk_stage", "dg_ssprk2"]
+            "dg_apply_jacobian_static", "dg_setup_ex", "dg_project", "dg_rk_stage", "dg_ssprk2", "dg_assemble",
+            "dg_matrix_info", "dg_matrix_export", "dg_spmv", "dg_matrix_destroy"]
 
 
 def check(rc):
@@ -388,6 +395,57 @@ class Operator:
         F = torch.empty(self.ndof, dtype=dtype, device="cuda")
         check(lib.dg_rhs(self.h, ctypes.c_void_p(F.data_ptr()), _prec(F), _stream_ptr(stream)))
         return F
+
+
+class Matrix:
+    """The operator's assembled block-sparse matrix (dg_assemble), its product (dg_spmv) and export."""
+
+    def __init__(self, op, stream=None):
+        m = ctypes.c_void_p()
+        check(lib.dg_assemble(op.h, _stream_ptr(stream), ctypes.byref(m)))
+        self.m = m
+        nr, nz, nb, secs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+        check(lib.dg_matrix_info(m, ctypes.byref(nr), ctypes.byref(nz), ctypes.byref(nb), ctypes.byref(secs)))
+        self.nrows, self.nnzb, self.block, self.assemble_seconds = nr.value, nz.value, nb.value, secs.value
+
+    def spmv(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        if x.dtype != torch.float64 or y.dtype != torch.float64 or not x.is_cuda:
+            raise TypeError("dg_spmv takes FP64 CUDA vectors")
+        check(lib.dg_spmv(self.m, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), _stream_ptr(stream)))
+        return y
+
+    def export(self):
+        """(rowptr, colidx, vals[nnzb, nb, nb] with vals[b, i, j] = entry (i, j) of block b)."""
+        rp = np.empty(self.nrows + 1, dtype=np.int32)
+        ci = np.empty(self.nnzb, dtype=np.int32)
+        v = np.empty((self.nnzb, self.block, self.block))
+        check(lib.dg_matrix_export(self.m, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), v.ctypes.data_as(_dp)))
+        return rp, ci, np.ascontiguousarray(v.transpose(0, 2, 1))  # stored column-major
+
+    def dense(self):
+        rp, ci, v = self.export()
+        nb = self.block
+        A = np.zeros((self.nrows * nb, self.nrows * nb))
+        for t in range(self.nrows):
+            for b in range(rp[t], rp[t + 1]):
+                s = ci[b]
+                A[t * nb:(t + 1) * nb, s * nb:(s + 1) * nb] = v[b]
+        return A
+
+    def close(self):
+        if getattr(self, "m", None):
+            lib.dg_matrix_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MLP:
