@@ -13,7 +13,7 @@ Every function here cites the passage of the paper it follows:
 * :func:`gauss_legendre` -- the tensor Gauss rule of Sec. 3.1, one axis on [0,1].
 * :func:`basis_1d` -- the 1D shape functions theta_j of Sec. 3.1, read as the
   orthonormal shifted Legendre polynomials ("L2-orthogonal Legendre", Sec. 2).
-* :func:`apply` -- (A u)_i = a_h(u, phi_i), eq. blf.
+* :func:`apply` -- (A u)_i = a_h(u, phi_i), eq. blf (scalar or tensor D, axis-parallel or affine cells).
 * :func:`rhs` -- F_i = l_h(phi_i), the right hand side functional of Sec. 2.
 * :func:`residual` -- r = A u - F (the residual evaluation of Sec. 1).
 """
@@ -58,10 +58,13 @@ def _configure(lib):
     lib.oracle_rhs.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                ctypes.c_double, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_apply_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                    ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _ip, ctypes.c_int]
+                                    ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _ip, ctypes.c_int]
     lib.oracle_rhs_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                  ctypes.c_double, _ip, _dp, _dp, ctypes.POINTER(_dp), _dp]
+                                  ctypes.c_double, _ip, _dp, _dp, _dp, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_cell_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
+    lib.oracle_volume_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, _dp]
+    lib.oracle_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    lib.oracle_cell_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_volume_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
     return lib
@@ -130,10 +133,13 @@ class Problem:
 
     ``sigma`` is the penalty factor of gamma_F = <delta-,delta+> sigma |F| / min(|T-|,|T+|) (Sec. 2);
     ``penalty_sigma`` gives the two readings.  ``m`` defaults to k+1 Gauss points (q = 2p, Sec. 5.1).
+    Options: ``periodic`` axes and a velocity field ``b_vol``/``b_face`` (Sec. 5.3); a per-cell diffusion
+    tensor ``D_tensor`` [ncell, 6] = (xx, yy, zz, xy, xz, yz) (Sec. 5.1); an affine geometry ``J`` (3x3 cell
+    Jacobian, cells lo + J (ic + [0,1]^3); ``hi`` is then unused).
     """
 
     def __init__(self, n, k, D, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-                 m=None, periodic=(0, 0, 0), b_vol=None, b_face=None):
+                 m=None, periodic=(0, 0, 0), b_vol=None, b_face=None, D_tensor=None, J=None):
         self.n = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(3))
         self.lo = _arr(lo, 3)
         self.hi = _arr(hi, 3)
@@ -150,6 +156,11 @@ class Problem:
         self.periodic = np.ascontiguousarray(np.asarray(periodic, dtype=np.int32).reshape(3))
         self.b_vol = None if b_vol is None else _arr(b_vol, self.ncell * self.m ** 3 * 3)
         self.b_face = None if b_face is None else _arr(b_face, self.ncell * 6 * self.m ** 2)
+        self.D_tensor = None if D_tensor is None else _arr(D_tensor, self.ncell * 6)
+        self.J = None if J is None else _arr(J, 9)
+
+    def _general(self):
+        return (_d(self.D_tensor) if self.D_tensor is not None else None, _d(self.J) if self.J is not None else None)
 
     @property
     def ndof(self):
@@ -177,7 +188,7 @@ def apply(pr: Problem, u, cells=None) -> np.ndarray:
     """y = A u with (A u)_i = a_h(u, phi_i) (eq. blf); if ``cells`` is given only those cells' blocks."""
     u = _arr(u, pr.ndof)
     ex = (pr.periodic.ctypes.data_as(_ip), _d(pr.b_vol) if pr.b_vol is not None else None,
-          _d(pr.b_face) if pr.b_face is not None else None)
+          _d(pr.b_face) if pr.b_face is not None else None, *pr._general())
     if cells is None:
         y = np.empty(pr.ndof)
         rc = _load().oracle_apply_ex(*pr._args(), *ex, _d(u), _d(y), None, 0)
@@ -206,7 +217,7 @@ def rhs(pr: Problem, f_qp=None, g_qp=None) -> np.ndarray:
                 keep.append(a)
                 garr[s] = _d(a)
     rc = _load().oracle_rhs_ex(*pr._args(), pr.periodic.ctypes.data_as(_ip),
-                               _d(pr.b_face) if pr.b_face is not None else None,
+                               _d(pr.b_face) if pr.b_face is not None else None, *pr._general(),
                                _d(fa) if fa is not None else None, garr, _d(F))
     if rc != 0:
         raise RuntimeError(f"oracle_rhs failed ({rc})")
@@ -221,7 +232,8 @@ def residual(pr: Problem, u, F) -> np.ndarray:
 def volume_points(pr: Problem) -> np.ndarray:
     """Physical coordinates [ncell, m^3, 3] of the volume quadrature points (oracle's own nodes)."""
     xyz = np.empty(pr.ncell * pr.m ** 3 * 3)
-    if _load().oracle_volume_points(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr.m, _d(xyz)) != 0:
+    if _load().oracle_volume_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr._general()[1], pr.m,
+                                       _d(xyz)) != 0:
         raise RuntimeError("oracle_volume_points failed")
     return xyz.reshape(pr.ncell, pr.m ** 3, 3)
 
@@ -229,7 +241,8 @@ def volume_points(pr: Problem) -> np.ndarray:
 def cell_face_points(pr: Problem) -> np.ndarray:
     """Physical coordinates [ncell, 6, m^2, 3] of the face points of every face of every cell."""
     xyz = np.empty(pr.ncell * 6 * pr.m ** 2 * 3)
-    if _load().oracle_cell_face_points(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr.m, _d(xyz)) != 0:
+    if _load().oracle_cell_face_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr._general()[1], pr.m,
+                                          _d(xyz)) != 0:
         raise RuntimeError("oracle_cell_face_points failed")
     return xyz.reshape(pr.ncell, 6, pr.m ** 2, 3)
 
@@ -240,6 +253,7 @@ def face_points(pr: Problem, s: int) -> np.ndarray:
     ta, tb = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
     nf = int(pr.n[ta] * pr.n[tb])
     xyz = np.empty(nf * pr.m ** 2 * 3)
-    if _load().oracle_face_points(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr.m, s, _d(xyz)) != 0:
+    if _load().oracle_face_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr._general()[1], pr.m, s,
+                                     _d(xyz)) != 0:
         raise RuntimeError("oracle_face_points failed")
     return xyz.reshape(nf, pr.m ** 2, 3)

@@ -22,9 +22,16 @@
  *  - orthonormal shifted Legendre basis on the reference interval [0,1]:
  *    theta_j(x) = sqrt(2j+1) P_j(2x-1)  ("L2-orthogonal Legendre", Sec. 2);
  *  - tensor Gauss-Legendre rule with m points per direction (Sec. 3.1);
- *  - scalar diffusion D_T * I constant per cell, constant c, and either a
- *    constant b (Problem A) or b given at the quadrature points (the
+ *  - diffusion constant per cell, either scalar D_T * I or a full symmetric
+ *    tensor D_T (the "tensor-valued diffusion coefficients" of Sec. 5.1), with
+ *    delta = nu^T D nu in the face weights and the penalty; constant c; and
+ *    either a constant b (Problem A) or b given at the quadrature points (the
  *    Taylor-Green transport problem of Sec. 5.3, evaluated by the caller);
+ *  - geometry: axis-parallel cells, or an affine image of the structured grid
+ *    (every cell T = lo + J (ic + [0,1]^3) with one constant Jacobian J, as in
+ *    Problem B of Sec. 5.1); gradients map as J^{-T}, |T| = |det J|, a face
+ *    normal to reference axis r has nu = J^{-T} e_r / |J^{-T} e_r| and area
+ *    |det J| |J^{-T} e_r|;
  *  - a periodic axis makes its two end faces interior faces between the last
  *    and the first cell (Sec. 5.1, 5.3);
  *  - penalty gamma_F = <delta-,delta+> * sigma * |F| / min(|T-|,|T+|) where the
@@ -113,7 +120,10 @@ typedef struct {
   double sigma;        /* penalty factor, gamma = <d-,d+> sigma |F|/min|T|   */
   int periodic[3];     /* 1: the axis wraps around (its end faces are interior faces) */
   const double* b_vol;  /* NULL, or b at the volume points [ncells][m^3][3]          */
-  const double* b_face; /* NULL, or b . e_dir at each cell's face points [ncells][6][m^2] */
+  const double* b_face; /* NULL, or b . nu_dir at each cell's face points [ncells][6][m^2] */
+  const double* Dten;   /* NULL, or [ncells][6] diffusion tensor (xx, yy, zz, xy, xz, yz); replaces D */
+  int affine;           /* 1: cells are lo + J (ic + [0,1]^3) with the Jacobian J below; 0: J = diag(h) */
+  double J[3][3];
 } oracle_problem;
 
 /* Full 3D tables at one set of points: phi[p*nb + J], grad[(p*nb + J)*3 + r]
@@ -167,8 +177,10 @@ static int table_build(int k, const double* ax[3], const double* aw[3], const in
 typedef struct {
   table3d vol;
   table3d face[6]; /* face s = 2*dir + side, side 0 at xi_dir = 0, side 1 at 1 */
-  double h[3], vol_T;
-  double area[3]; /* |F| of a face normal to dir */
+  double J[3][3], Jinv[3][3];
+  double vol_T;    /* |T| = |det J| */
+  double nrm[3][3]; /* nrm[r]: unit normal of the faces across reference axis r, J^{-T} e_r / |J^{-T} e_r| */
+  double area[3];  /* |F| of a face across reference axis r: |det J| |J^{-T} e_r| */
   int ncell;
 } oracle_ctx;
 
@@ -195,9 +207,31 @@ static int ctx_build(const oracle_problem* pr, oracle_ctx* cx) {
     }
   free(x);
   free(w);
-  for (int r = 0; r < 3; ++r) cx->h[r] = (pr->hi[r] - pr->lo[r]) / pr->n[r];
-  cx->vol_T = cx->h[0] * cx->h[1] * cx->h[2];
-  for (int r = 0; r < 3; ++r) cx->area[r] = cx->vol_T / cx->h[r];
+  /* the cell Jacobian: diag(h) for the axis-parallel mesh, else the given affine map */
+  for (int a = 0; a < 3; ++a)
+    for (int r = 0; r < 3; ++r)
+      cx->J[a][r] = pr->affine ? pr->J[a][r] : (a == r ? (pr->hi[r] - pr->lo[r]) / pr->n[r] : 0.0);
+  const double (*J)[3] = cx->J;
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  if (det == 0.0) return -1;
+  /* inverse by cofactors */
+  cx->Jinv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  cx->Jinv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  cx->Jinv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  cx->Jinv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  cx->Jinv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  cx->Jinv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  cx->Jinv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  cx->Jinv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  cx->Jinv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  cx->vol_T = fabs(det);
+  for (int r = 0; r < 3; ++r) {
+    /* J^{-T} e_r is row r of J^{-1} */
+    double len = sqrt(cx->Jinv[r][0] * cx->Jinv[r][0] + cx->Jinv[r][1] * cx->Jinv[r][1] + cx->Jinv[r][2] * cx->Jinv[r][2]);
+    for (int a = 0; a < 3; ++a) cx->nrm[r][a] = cx->Jinv[r][a] / len;
+    cx->area[r] = cx->vol_T * len;
+  }
   cx->ncell = pr->n[0] * pr->n[1] * pr->n[2];
   return 0;
 }
@@ -207,22 +241,56 @@ static void ctx_free(oracle_ctx* cx) {
   for (int s = 0; s < 6; ++s) table_free(&cx->face[s]);
 }
 
+/* physical gradient from a reference gradient: g = J^{-T} gref */
+static void phys_grad(const oracle_ctx* cx, const double gref[3], double g[3]) {
+  for (int a = 0; a < 3; ++a) {
+    g[a] = 0.0;
+    for (int r = 0; r < 3; ++r) g[a] += cx->Jinv[r][a] * gref[r];
+  }
+}
+
 /* u and physical gradient of the FE function with coefficients zc at point p of table t */
-static void eval_fe(const table3d* t, int p, const double* zc, const double h[3], double* u, double g[3]) {
-  double uu = 0, g0 = 0, g1 = 0, g2 = 0;
+static void eval_fe(const table3d* t, int p, const double* zc, const oracle_ctx* cx, double* u, double g[3]) {
+  double uu = 0, gr3[3] = {0, 0, 0};
   const double* ph = t->phi + (size_t)p * t->nb;
   const double* gr = t->grad + (size_t)p * t->nb * 3;
   for (int J = 0; J < t->nb; ++J) {
     uu += zc[J] * ph[J];
-    g0 += zc[J] * gr[3 * J + 0];
-    g1 += zc[J] * gr[3 * J + 1];
-    g2 += zc[J] * gr[3 * J + 2];
+    gr3[0] += zc[J] * gr[3 * J + 0];
+    gr3[1] += zc[J] * gr[3 * J + 1];
+    gr3[2] += zc[J] * gr[3 * J + 2];
   }
   *u = uu;
-  /* S_T = diag(1/h) maps reference to physical gradients (Sec. 3.2) */
-  g[0] = g0 / h[0];
-  g[1] = g1 / h[1];
-  g[2] = g2 / h[2];
+  phys_grad(cx, gr3, g);
+}
+
+/* diffusion tensor of a cell: the given symmetric tensor, or D_T * I */
+static void diff_tensor(const oracle_problem* pr, int cell, double Dm[3][3]) {
+  if (pr->Dten) {
+    const double* t = pr->Dten + (size_t)cell * 6;
+    Dm[0][0] = t[0];
+    Dm[1][1] = t[1];
+    Dm[2][2] = t[2];
+    Dm[0][1] = Dm[1][0] = t[3];
+    Dm[0][2] = Dm[2][0] = t[4];
+    Dm[1][2] = Dm[2][1] = t[5];
+  } else {
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) Dm[a][c] = a == c ? pr->D[cell] : 0.0;
+  }
+}
+
+/* nu . (D w) */
+static double flux_along(const double nu[3], const double Dm[3][3], const double w[3]) {
+  double s = 0.0;
+  for (int a = 0; a < 3; ++a) s += nu[a] * (Dm[a][0] * w[0] + Dm[a][1] * w[1] + Dm[a][2] * w[2]);
+  return s;
+}
+
+/* physical gradient of test function i at point p of table t */
+static void test_grad(const table3d* t, int p, int i, const oracle_ctx* cx, double g[3]) {
+  const double* gr = t->grad + ((size_t)p * t->nb + i) * 3;
+  phys_grad(cx, gr, g);
 }
 
 static double upwind(double um, double up, double bnu) { return bnu >= 0.0 ? um * bnu : up * bnu; }
@@ -244,25 +312,26 @@ static int cell_index(const oracle_problem* pr, const int ic[3]) {
 static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const double* u, int cell, double* y) {
   const int nb = cx->vol.nb;
   const double* zc = u + (size_t)cell * nb;
-  const double* h = cx->h;
-  const double DT = pr->D[cell];
+  double DT[3][3];
+  diff_tensor(pr, cell, DT);
   for (int i = 0; i < nb; ++i) y[i] = 0.0;
 
   /* volume: (D grad u - b u, grad v)_T + (c u, v)_T */
   for (int p = 0; p < cx->vol.np; ++p) {
     double uq, g[3];
-    eval_fe(&cx->vol, p, zc, h, &uq, g);
+    eval_fe(&cx->vol, p, zc, cx, &uq, g);
     double dx = cx->vol.wgt[p] * cx->vol_T; /* Delta_T * w_i */
-    double fl[3];
+    double Dg[3], fl[3];
+    for (int a = 0; a < 3; ++a) Dg[a] = DT[a][0] * g[0] + DT[a][1] * g[1] + DT[a][2] * g[2];
     for (int r = 0; r < 3; ++r) {
       const double br = pr->b_vol ? pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + r] : pr->b[r];
-      fl[r] = DT * g[r] - br * uq;
+      fl[r] = Dg[r] - br * uq;
     }
     const double* ph = cx->vol.phi + (size_t)p * nb;
-    const double* gr = cx->vol.grad + (size_t)p * nb * 3;
     for (int i = 0; i < nb; ++i) {
-      double gv0 = gr[3 * i] / h[0], gv1 = gr[3 * i + 1] / h[1], gv2 = gr[3 * i + 2] / h[2];
-      y[i] += dx * (fl[0] * gv0 + fl[1] * gv1 + fl[2] * gv2 + pr->c * uq * ph[i]);
+      double gv[3];
+      test_grad(&cx->vol, p, i, cx, gv);
+      y[i] += dx * (fl[0] * gv[0] + fl[1] * gv[1] + fl[2] * gv[2] + pr->c * uq * ph[i]);
     }
   }
 
@@ -276,55 +345,63 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
       if (pr->periodic[dir]) nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];
       int interior = nic[dir] >= 0 && nic[dir] < pr->n[dir];
       double dF = cx->area[dir];
-      /* normal velocity b . e_dir at face point p of this face */
+      const double* nu = cx->nrm[dir]; /* unit normal pointing along +reference axis dir */
+      const double bdotn = pr->b[0] * nu[0] + pr->b[1] * nu[1] + pr->b[2] * nu[2];
+      /* normal velocity b . nu at face point p of this face */
       const double* bfp = pr->b_face ? pr->b_face + ((size_t)cell * 6 + 2 * dir + side) * ft->np : 0;
       if (interior) {
-        /* T- is the lower cell along dir, nu = +e_dir from T- to T+ */
+        /* T- is the lower cell along dir, nu from T- to T+ */
         int nbr = cell_index(pr, nic);
         const double* zn = u + (size_t)nbr * nb;
         const table3d* nt = &cx->face[2 * dir + (1 - side)]; /* neighbour's trace */
         int this_is_minus = side == 1;
-        double Dm = this_is_minus ? DT : pr->D[nbr];
-        double Dp = this_is_minus ? pr->D[nbr] : DT;
-        double wm = Dp / (Dm + Dp), wp = Dm / (Dm + Dp); /* delta = nu^T D nu = D */
-        double gam = harmonic(Dm, Dp) * pr->sigma * dF / cx->vol_T;
+        double DN[3][3];
+        diff_tensor(pr, nbr, DN);
+        const double(*Dm)[3] = this_is_minus ? DT : DN;
+        const double(*Dp)[3] = this_is_minus ? DN : DT;
+        double dm = flux_along(nu, Dm, nu), dp = flux_along(nu, Dp, nu); /* delta = nu^T D nu */
+        double wm = dp / (dm + dp), wp = dm / (dm + dp);
+        double gam = harmonic(dm, dp) * pr->sigma * dF / cx->vol_T;
         for (int p = 0; p < ft->np; ++p) {
-          double bnu = bfp ? bfp[p] : pr->b[dir];
+          double bnu = bfp ? bfp[p] : bdotn;
           double us, gs[3], un, gn[3];
-          eval_fe(ft, p, zc, h, &us, gs);
-          eval_fe(nt, p, zn, h, &un, gn);
+          eval_fe(ft, p, zc, cx, &us, gs);
+          eval_fe(nt, p, zn, cx, &un, gn);
           double um = this_is_minus ? us : un, up = this_is_minus ? un : us;
-          double dnum = this_is_minus ? gs[dir] : gn[dir]; /* nu . grad u- */
-          double dnup = this_is_minus ? gn[dir] : gs[dir];
+          double dnum = flux_along(nu, Dm, this_is_minus ? gs : gn); /* nu . D- grad u- */
+          double dnup = flux_along(nu, Dp, this_is_minus ? gn : gs);
           double jump_u = um - up;
-          double avg_flux = wm * Dm * dnum + wp * Dp * dnup; /* nu . {D grad u}_w */
+          double avg_flux = wm * dnum + wp * dnup; /* nu . {D grad u}_w */
           double phi_flux = upwind(um, up, bnu);
           double dx = ft->wgt[p] * dF;
           const double* ph = ft->phi + (size_t)p * nb;
-          const double* gr = ft->grad + (size_t)p * nb * 3;
           for (int i = 0; i < nb; ++i) {
-            double v = ph[i], dv = gr[3 * i + dir] / h[dir];
+            double gv[3];
+            test_grad(ft, p, i, cx, gv);
+            double v = ph[i], dv = flux_along(nu, DT, gv); /* nu . D grad v on this cell */
             /* jump and weighted average of the test function supported on this cell */
             double jump_v = this_is_minus ? v : -v;
-            double avg_dv = this_is_minus ? wm * Dm * dv : wp * Dp * dv;
+            double avg_dv = this_is_minus ? wm * dv : wp * dv;
             y[i] += dx * (phi_flux * jump_v - avg_flux * jump_v - avg_dv * jump_u + gam * jump_u * jump_v);
           }
         }
       } else {
-        /* Dirichlet boundary face, nu = outward normal */
+        /* Dirichlet boundary face, outward normal sgn * nu */
         double sgn = side ? 1.0 : -1.0;
-        double gam = DT * pr->sigma * dF / cx->vol_T;
+        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};
+        double gam = flux_along(nout, DT, nout) * pr->sigma * dF / cx->vol_T;
         for (int p = 0; p < ft->np; ++p) {
-          double bnu = sgn * (bfp ? bfp[p] : pr->b[dir]);
+          double bnu = sgn * (bfp ? bfp[p] : bdotn);
           double us, gs[3];
-          eval_fe(ft, p, zc, h, &us, gs);
-          double dnu = sgn * gs[dir];
+          eval_fe(ft, p, zc, cx, &us, gs);
+          double dnu = flux_along(nout, DT, gs);
           double dx = ft->wgt[p] * dF;
           const double* ph = ft->phi + (size_t)p * nb;
-          const double* gr = ft->grad + (size_t)p * nb * 3;
           for (int i = 0; i < nb; ++i) {
-            double v = ph[i], dnv = sgn * gr[3 * i + dir] / h[dir];
-            y[i] += dx * (upwind(us, 0.0, bnu) * v - DT * dnu * v - DT * dnv * us + gam * us * v);
+            double gv[3];
+            test_grad(ft, p, i, cx, gv);
+            double v = ph[i], dnv = flux_along(nout, DT, gv);
+            y[i] += dx * (upwind(us, 0.0, bnu) * v - dnu * v - dnv * us + gam * us * v);
           }
         }
       }
@@ -349,7 +426,20 @@ static int fill_problem(oracle_problem* pr, const int* n, const double* lo, cons
   pr->periodic[0] = pr->periodic[1] = pr->periodic[2] = 0;
   pr->b_vol = 0;
   pr->b_face = 0;
+  pr->Dten = 0;
+  pr->affine = 0;
+  memset(pr->J, 0, sizeof(pr->J));
   return 0;
+}
+
+/* tensor diffusion and affine geometry options shared by the _ex entry points */
+static void set_general(oracle_problem* pr, const double* Dten, const double* Jmap) {
+  pr->Dten = Dten;
+  if (Jmap) {
+    pr->affine = 1;
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < 3; ++r) pr->J[a][r] = Jmap[3 * a + r];
+  }
 }
 
 /* y = A u restricted to the listed cells (cells == NULL: all cells, in order).
@@ -363,17 +453,23 @@ int oracle_apply(const int* n, const double* lo, const double* hi, int k, int m,
   return apply_impl(&pr, u, y, cells, ncells_out);
 }
 
-/* oracle_apply with periodic axes and a velocity field given at the quadrature points:
- * b_vol [ncells][m^3][3] (NULL: constant b), b_face [ncells][6][m^2] = b . e_dir at each face point of
- * each cell (NULL: constant b).  On a periodic axis the end faces couple the first and last cells. */
+/* oracle_apply with periodic axes, a velocity field given at the quadrature points, a tensor diffusion
+ * coefficient and an affine geometry:
+ *   b_vol [ncells][m^3][3] (NULL: constant b), b_face [ncells][6][m^2] = b . nu at each face point of each
+ *   cell, nu the unit normal along +reference axis (NULL: constant b);
+ *   Dten [ncells][6] = (xx, yy, zz, xy, xz, yz) (NULL: D_T * I from D);
+ *   Jmap [9] row-major cell Jacobian, cells lo + J (ic + [0,1]^3) (NULL: the axis-parallel [lo, hi] grid).
+ * On a periodic axis the end faces couple the first and last cells. */
 int oracle_apply_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
                     double c, double sigma, const int* periodic, const double* b_vol, const double* b_face,
-                    const double* u, double* y, const int* cells, int ncells_out) {
+                    const double* Dten, const double* Jmap, const double* u, double* y, const int* cells,
+                    int ncells_out) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
   pr.b_vol = b_vol;
   pr.b_face = b_face;
+  set_general(&pr, Dten, Jmap);
   return apply_impl(&pr, u, y, cells, ncells_out);
 }
 
@@ -408,14 +504,16 @@ int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, c
   return rhs_impl(&pr, f_qp, g_qp, F);
 }
 
-/* oracle_rhs with periodic axes (no Dirichlet faces there) and b . e_dir at the face points. */
+/* oracle_rhs with periodic axes (no Dirichlet faces there), b . nu at the face points, a tensor diffusion
+ * coefficient and an affine geometry (arguments as in oracle_apply_ex). */
 int oracle_rhs_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
-                  double c, double sigma, const int* periodic, const double* b_face, const double* f_qp,
-                  const double* const* g_qp, double* F) {
+                  double c, double sigma, const int* periodic, const double* b_face, const double* Dten,
+                  const double* Jmap, const double* f_qp, const double* const* g_qp, double* F) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
   pr.b_face = b_face;
+  set_general(&pr, Dten, Jmap);
   return rhs_impl(&pr, f_qp, g_qp, F);
 }
 
@@ -424,7 +522,6 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
   oracle_ctx cx;
   if (ctx_build(&pr, &cx)) return -2;
   int nb = cx.vol.nb, npv = cx.vol.np;
-  const double* h = cx.h;
   for (int cell = 0; cell < cx.ncell; ++cell) {
     double* y = F + (size_t)cell * nb;
     for (int i = 0; i < nb; ++i) y[i] = 0.0;
@@ -447,19 +544,24 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
         int fidx = ic[ta] + pr.n[ta] * ic[tb];
         const table3d* ft = &cx.face[s];
         double sgn = side ? 1.0 : -1.0;
+        const double* nu = cx.nrm[dir];
+        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};
+        const double bdotn = pr.b[0] * nu[0] + pr.b[1] * nu[1] + pr.b[2] * nu[2];
         const double* bfp = pr.b_face ? pr.b_face + ((size_t)cell * 6 + s) * ft->np : 0;
-        double DT = pr.D[cell];
+        double DT[3][3];
+        diff_tensor(&pr, cell, DT);
         double dF = cx.area[dir];
-        double gam = DT * pr.sigma * dF / cx.vol_T;
+        double gam = flux_along(nout, DT, nout) * pr.sigma * dF / cx.vol_T;
         for (int p = 0; p < ft->np; ++p) {
           double g = g_qp[s][(size_t)fidx * ft->np + p];
-          double bnu = sgn * (bfp ? bfp[p] : pr.b[dir]);
+          double bnu = sgn * (bfp ? bfp[p] : bdotn);
           double dx = ft->wgt[p] * dF;
           const double* ph = ft->phi + (size_t)p * nb;
-          const double* gr = ft->grad + (size_t)p * nb * 3;
           for (int i = 0; i < nb; ++i) {
-            double v = ph[i], dnv = sgn * gr[3 * i + dir] / h[dir];
-            y[i] += dx * (-upwind(0.0, g, bnu) * v - DT * dnv * g + gam * g * v);
+            double gv[3];
+            test_grad(ft, p, i, &cx, gv);
+            double v = ph[i], dnv = flux_along(nout, DT, gv);
+            y[i] += dx * (-upwind(0.0, g, bnu) * v - dnv * g + gam * g * v);
           }
         }
       }
@@ -468,13 +570,25 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
   return 0;
 }
 
+/* x = lo + J xi for a point xi of the structured reference grid (xi_r = cell index + local coordinate);
+ * J = diag((hi - lo) / n) without an affine map */
+static void map_point(const int* n, const double* lo, const double* hi, const double* Jmap, const double xi[3],
+                      double* out) {
+  for (int a = 0; a < 3; ++a) {
+    if (Jmap) {
+      out[a] = lo[a] + Jmap[3 * a] * xi[0] + Jmap[3 * a + 1] * xi[1] + Jmap[3 * a + 2] * xi[2];
+    } else {
+      out[a] = lo[a] + (hi[a] - lo[a]) / n[a] * xi[a];
+    }
+  }
+}
+
 /* Physical coordinates of the volume quadrature points: xyz[(cell*m^3 + q)*3 + r]. */
-int oracle_volume_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
+int oracle_volume_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap, int m,
+                            double* xyz) {
   double* x = (double*)malloc(sizeof(double) * m);
   double* w = (double*)malloc(sizeof(double) * m);
   if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
-  double h[3];
-  for (int r = 0; r < 3; ++r) h[r] = (hi[r] - lo[r]) / n[r];
   size_t o = 0;
   for (int iz = 0; iz < n[2]; ++iz)
     for (int iy = 0; iy < n[1]; ++iy)
@@ -482,53 +596,58 @@ int oracle_volume_points(const int* n, const double* lo, const double* hi, int m
         for (int i3 = 0; i3 < m; ++i3)
           for (int i2 = 0; i2 < m; ++i2)
             for (int i1 = 0; i1 < m; ++i1) {
-              xyz[o++] = lo[0] + h[0] * (ix + x[i1]);
-              xyz[o++] = lo[1] + h[1] * (iy + x[i2]);
-              xyz[o++] = lo[2] + h[2] * (iz + x[i3]);
+              const double xi[3] = {ix + x[i1], iy + x[i2], iz + x[i3]};
+              map_point(n, lo, hi, Jmap, xi, xyz + o);
+              o += 3;
             }
   free(x);
   free(w);
   return 0;
 }
 
+int oracle_volume_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
+  return oracle_volume_points_ex(n, lo, hi, 0, m, xyz);
+}
+
 /* Physical coordinates of the boundary face points of side s = 2*dir + side:
  * xyz[(face*m^2 + p)*3 + r], faces and points ordered as documented above. */
-int oracle_face_points(const int* n, const double* lo, const double* hi, int m, int s, double* xyz) {
+int oracle_face_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap, int m, int s,
+                          double* xyz) {
   if (s < 0 || s > 5) return -1;
   double* x = (double*)malloc(sizeof(double) * m);
   double* w = (double*)malloc(sizeof(double) * m);
   if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
   int dir = s / 2, side = s % 2;
   int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
-  double h[3];
-  for (int r = 0; r < 3; ++r) h[r] = (hi[r] - lo[r]) / n[r];
   size_t o = 0;
   for (int cb = 0; cb < n[tb]; ++cb)
     for (int ca = 0; ca < n[ta]; ++ca)
       for (int pb = 0; pb < m; ++pb)
         for (int pa = 0; pa < m; ++pa) {
-          double p[3];
-          p[dir] = side ? hi[dir] : lo[dir];
-          p[ta] = lo[ta] + h[ta] * (ca + x[pa]);
-          p[tb] = lo[tb] + h[tb] * (cb + x[pb]);
-          xyz[o++] = p[0];
-          xyz[o++] = p[1];
-          xyz[o++] = p[2];
+          double xi[3];
+          xi[dir] = side ? n[dir] : 0;
+          xi[ta] = ca + x[pa];
+          xi[tb] = cb + x[pb];
+          map_point(n, lo, hi, Jmap, xi, xyz + o);
+          o += 3;
         }
   free(x);
   free(w);
   return 0;
 }
 
+int oracle_face_points(const int* n, const double* lo, const double* hi, int m, int s, double* xyz) {
+  return oracle_face_points_ex(n, lo, hi, 0, m, s, xyz);
+}
+
 /* Physical coordinates of the face points of every face of every cell:
  * xyz[((cell*6 + s)*m^2 + p)*3 + r], s = 2*dir + side, points ordered as in the face tables
  * (lower tangential axis fastest). */
-int oracle_cell_face_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
+int oracle_cell_face_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap, int m,
+                               double* xyz) {
   double* x = (double*)malloc(sizeof(double) * m);
   double* w = (double*)malloc(sizeof(double) * m);
   if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
-  double h[3];
-  for (int r = 0; r < 3; ++r) h[r] = (hi[r] - lo[r]) / n[r];
   size_t o = 0;
   for (int iz = 0; iz < n[2]; ++iz)
     for (int iy = 0; iy < n[1]; ++iy)
@@ -539,17 +658,20 @@ int oracle_cell_face_points(const int* n, const double* lo, const double* hi, in
             int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
             for (int pb = 0; pb < m; ++pb)
               for (int pa = 0; pa < m; ++pa) {
-                double p[3];
-                p[dir] = lo[dir] + h[dir] * (ic[dir] + side);
-                p[ta] = lo[ta] + h[ta] * (ic[ta] + x[pa]);
-                p[tb] = lo[tb] + h[tb] * (ic[tb] + x[pb]);
-                xyz[o++] = p[0];
-                xyz[o++] = p[1];
-                xyz[o++] = p[2];
+                double xi[3];
+                xi[dir] = ic[dir] + side;
+                xi[ta] = ic[ta] + x[pa];
+                xi[tb] = ic[tb] + x[pb];
+                map_point(n, lo, hi, Jmap, xi, xyz + o);
+                o += 3;
               }
           }
       }
   free(x);
   free(w);
   return 0;
+}
+
+int oracle_cell_face_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
+  return oracle_cell_face_points_ex(n, lo, hi, 0, m, xyz);
 }

@@ -10,34 +10,39 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_tensor_pins as xpins
 from tests import test_oracle_transport_pins as tpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "dg_oracle.c")
 
 # (name, original text, mutated text)
 MUTANTS = [
-    ("weighted average sign", "wm * Dm * dnum + wp * Dp * dnup", "wm * Dm * dnum - wp * Dp * dnup"),
+    ("weighted average sign", "wm * dnum + wp * dnup", "wm * dnum - wp * dnup"),
     ("upwind branch swapped", "return bnu >= 0.0 ? um * bnu : up * bnu;", "return bnu >= 0.0 ? up * bnu : um * bnu;"),
     ("penalty dropped", "+ gam * jump_u * jump_v", "+ 0.0 * gam * jump_u * jump_v"),
     ("symmetry term sign", "- avg_dv * jump_u", "+ avg_dv * jump_u"),
-    ("convection sign", "fl[r] = DT * g[r] - br * uq;", "fl[r] = DT * g[r] + br * uq;"),
+    ("convection sign", "fl[r] = Dg[r] - br * uq;", "fl[r] = Dg[r] + br * uq;"),
     ("transposed basis index", "t->grad[o * 3 + 1] = v[0][j1] * d[1][j2] * v[2][j3];",
      "t->grad[o * 3 + 1] = v[0][j1] * d[1][j3] * v[2][j2];"),
-    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double gam = DT",
-     "double sgn = 1.0;\n        double gam = DT"),
+    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        double gam",
+     "double sgn = 1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        double gam"),
     ("Gauss weight", "w[i] = 1.0 / ((1.0 - t * t) * dP[m] * dP[m]);", "w[i] = 2.0 / ((1.0 - t * t) * dP[m] * dP[m]);"),
-    ("Dirichlet data sign in the right hand side", "- DT * dnv * g + gam * g * v", "+ DT * dnv * g + gam * g * v"),
+    ("Dirichlet data sign in the right hand side", "- dnv * g + gam * g * v", "+ dnv * g + gam * g * v"),
     ("reaction dropped", "pr->c * uq * ph[i]", "0.0 * pr->c * uq * ph[i]"),
     ("harmonic mean replaced by arithmetic mean", "return 2.0 * a * b / (a + b);", "return 0.5 * (a + b);"),
-    ("face weight swapped", "double wm = Dp / (Dm + Dp), wp = Dm / (Dm + Dp);",
-     "double wm = Dm / (Dm + Dp), wp = Dp / (Dm + Dp);"),
+    ("face weight swapped", "double wm = dp / (dm + dp), wp = dm / (dm + dp);",
+     "double wm = dm / (dm + dp), wp = dp / (dm + dp);"),
     ("periodic wrap dropped", "if (pr->periodic[dir]) nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];",
      "if (0) nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];"),
     ("periodic wrap off by one", "nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];",
      "nic[dir] = (nic[dir] + pr->n[dir] + 1) % pr->n[dir];"),
-    ("interior face velocity ignored", "double bnu = bfp ? bfp[p] : pr->b[dir];", "double bnu = pr->b[dir];"),
+    ("interior face velocity ignored", "double bnu = bfp ? bfp[p] : bdotn;", "double bnu = bdotn;"),
     ("volume velocity component", "pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + r]",
      "pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + 0]"),
+    ("tensor off-diagonal entry", "Dm[0][1] = Dm[1][0] = t[3];", "Dm[0][1] = Dm[1][0] = t[4];"),
+    ("gradient mapped by J^-1 instead of J^-T", "g[a] += cx->Jinv[r][a] * gref[r];", "g[a] += cx->Jinv[a][r] * gref[r];"),
+    ("face normal from J instead of J^-T", "cx->nrm[r][a] = cx->Jinv[r][a] / len;", "cx->nrm[r][a] = cx->J[a][r] / len;"),
+    ("face area without the normal scale", "cx->area[r] = cx->vol_T * len;", "cx->area[r] = cx->vol_T;"),
 ]
 
 
@@ -56,6 +61,9 @@ def _pin_checks():
     yield tpins.test_constant_field_given_at_points_equals_constant_velocity
     yield tpins.test_periodic_transport_conserves_mass_exactly
     yield tpins.test_periodic_translation_invariance
+    yield lambda: xpins.test_tensor_diffusion_matches_kronecker_closed_form((2, 3, 2), 2, (0, 0, 0))
+    yield lambda: xpins.test_linear_map_scales_the_operator_by_its_determinant(2)
+    yield lambda: xpins.test_polynomial_solution_on_affine_mesh_has_zero_residual(2)
 
 
 @pytest.mark.parametrize("name,orig,mutated", MUTANTS, ids=[m[0] for m in MUTANTS])
