@@ -351,6 +351,15 @@ typedef struct {
                            of each cell (points p = p_a + m*p_b over the tangential axes a < b).  An
                            interior face uses the value given for its lower cell's upper face for both
                            cells, so the two sides see one flux.                                       */
+  const double* D_tensor; /* host [ncells][6] = (xx, yy, zz, xy, xz, yz): a symmetric positive definite
+                           diffusion tensor per cell (Sec. 5.1: "tensor-valued diffusion coefficients"),
+                           replacing coeffs->D_cell / D_const; NULL: D_T * I.  delta = nu^T D nu enters
+                           the face weights and the penalty.                                          */
+  const double* jacobian; /* host [9], row-major J: the cells are lo + J (ic + [0,1]^3), an affine image
+                           of the structured grid (Problem B of Sec. 5.1); mesh->hi is then unused and
+                           the quadrature points follow the map.  NULL: the axis-parallel [lo, hi] grid.
+                           With D_tensor or jacobian the tensor-diffusion kernels run (m = k+1, constant
+                           velocity, degrees 1..8, DG_F64 and DG_F64X applies).                       */
 } dg_setup_ext;
 
 /* dg_setup with the options above (ext = NULL is dg_setup).  A field b(x) or m = k+3 selects the

@@ -245,9 +245,9 @@ int dg_batch_create(dg_handle* const* hs, int32_t count, void* stream, dg_batch*
   int dev = -1;
   cudaGetDevice(&dev);
   for (int i = 0; i < count; ++i)
-    if (!hs[i] || hs[i]->N < dgbt::NMIN || hs[i]->N > dgbt::NMAX || hs[i]->device != dev || hs[i]->vb) {
+    if (!hs[i] || hs[i]->N < dgbt::NMIN || hs[i]->N > dgbt::NMAX || hs[i]->device != dev || hs[i]->vb || hs[i]->td) {
       set_error("dg_batch_create: every handle must exist, live on the current device, have 1 <= k <= 8, a "
-                "constant velocity and m = k+1");
+                "constant velocity, m = k+1 and scalar diffusion on the axis-parallel grid");
       return DG_ERR_INVALID_ARG;
     }
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -229,6 +229,22 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     set_error("dg_setup: a velocity field or m = k+3 needs degree k <= 8");
     return DG_ERR_INVALID_ARG;
   }
+  const bool td = ext && (ext->D_tensor || ext->jacobian);
+  if (td && (vb || k > 8)) {
+    set_error("dg_setup: a diffusion tensor or an affine geometry needs a constant velocity, m = k+1 and k <= 8");
+    return DG_ERR_INVALID_ARG;
+  }
+  double Jm[3][3];
+  if (td && ext->jacobian) {
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < 3; ++r) {
+        Jm[a][r] = ext->jacobian[3 * a + r];
+        if (!std::isfinite(Jm[a][r])) {
+          set_error("dg_setup: the Jacobian must be finite");
+          return DG_ERR_INVALID_ARG;
+        }
+      }
+  }
   int periodic[3] = {0, 0, 0};
   for (int r = 0; r < 3; ++r) {
     if (ext && ext->periodic[r] != 0 && ext->periodic[r] != 1) {
@@ -238,7 +254,23 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     periodic[r] = ext ? ext->periodic[r] : 0;
   }
   std::vector<double> D(ncell);
+  const bool tensor_given = td && ext->D_tensor;
   for (int64_t i = 0; i < ncell; ++i) {
+    if (tensor_given) {
+      // symmetric positive definite: positive leading principal minors (Sylvester's criterion)
+      const double* t = ext->D_tensor + 6 * i;
+      bool ok = true;
+      for (int q = 0; q < 6; ++q) ok = ok && std::isfinite(t[q]);
+      const double m2 = t[0] * t[1] - t[3] * t[3];
+      const double m3 = t[0] * (t[1] * t[2] - t[5] * t[5]) - t[3] * (t[3] * t[2] - t[5] * t[4]) +
+                        t[4] * (t[3] * t[5] - t[1] * t[4]);
+      if (!ok || !(t[0] > 0) || !(m2 > 0) || !(m3 > 0)) {
+        set_error("dg_setup: every D_T must be symmetric positive definite (cell " + std::to_string(i) + ")");
+        return DG_ERR_INVALID_ARG;
+      }
+      D[i] = t[0];
+      continue;
+    }
     D[i] = co->D_cell ? co->D_cell[i] : co->D_const;
     if (!finite_pos(D[i])) {
       set_error("dg_setup: every D_T must be finite and > 0 (cell " + std::to_string(i) + ")");
@@ -266,7 +298,36 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
   h->sigma = co->sigma;
   h->M = M;
   h->vb = vb;
+  h->td = td;
+  h->affine = td && ext->jacobian;
   for (int r = 0; r < 3; ++r) h->periodic[r] = periodic[r];
+  // cell Jacobian: the affine map, or diag(h) for the axis-parallel grid
+  for (int a = 0; a < 3; ++a)
+    for (int r = 0; r < 3; ++r) h->J[a][r] = h->affine ? Jm[a][r] : (a == r ? h->h[r] : 0.0);
+  {
+    const double(*J)[3] = h->J;
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(std::fabs(det) > 0) || !std::isfinite(det)) {
+      delete h;
+      set_error("dg_setup: the Jacobian must be invertible");
+      return DG_ERR_INVALID_ARG;
+    }
+    h->Jinv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    h->Jinv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    h->Jinv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    h->Jinv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    h->Jinv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    h->Jinv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    h->Jinv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    h->Jinv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    h->Jinv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    h->detJ = std::fabs(det);
+    for (int r = 0; r < 3; ++r)
+      h->fscale[r] = std::sqrt(h->Jinv[r][0] * h->Jinv[r][0] + h->Jinv[r][1] * h->Jinv[r][1] +
+                               h->Jinv[r][2] * h->Jinv[r][2]);
+  }
   build_tables(h->N, M, &h->tab);
 
   const int N = h->N;
@@ -302,6 +363,77 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
         }
       }
   }
+  if (td) {
+    // K = |det J| J^{-1} D_T J^{-T} per cell (D_T the tensor, or D_T I), and per face (w_own, w_nbr, gamma,
+    // kn, kt1, kt2): delta = nu^T D nu is proportional to K_rr on every cell (one Jacobian), so the weights
+    // are w_own = K_nbr,rr / (K_own,rr + K_nbr,rr); gamma = <delta-, delta+> sigma |F| / |T| with
+    // delta = K_rr / (|det J| |J^{-T} e_r|^2) and |F| / |T| = |J^{-T} e_r|; kn, kt = w_own K_r. / |F_r|
+    std::vector<double> K(ncell * 6);
+    for (int64_t cell = 0; cell < ncell; ++cell) {
+      double Dt[3][3];
+      if (tensor_given) {
+        const double* t = ext->D_tensor + 6 * cell;
+        Dt[0][0] = t[0], Dt[1][1] = t[1], Dt[2][2] = t[2];
+        Dt[0][1] = Dt[1][0] = t[3];
+        Dt[0][2] = Dt[2][0] = t[4];
+        Dt[1][2] = Dt[2][1] = t[5];
+      } else {
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) Dt[a][b] = a == b ? D[cell] : 0.0;
+      }
+      double Km[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double acc = 0.0;
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) acc += h->Jinv[a][p] * Dt[p][q] * h->Jinv[b][q];
+          Km[a][b] = h->detJ * acc;
+        }
+      double* k6 = &K[cell * 6];
+      k6[0] = Km[0][0], k6[1] = Km[1][1], k6[2] = Km[2][2], k6[3] = Km[0][1], k6[4] = Km[0][2], k6[5] = Km[1][2];
+    }
+    auto Kat = [&](int64_t cell, int a, int b) {
+      const double* k6 = &K[cell * 6];
+      if (a == b) return k6[a];
+      const int lo_ = a < b ? a : b, hi_ = a < b ? b : a;
+      return lo_ == 0 ? (hi_ == 1 ? k6[3] : k6[4]) : k6[5];
+    };
+    fc.assign(ncell * 36, 0.0);
+    for (int64_t cell = 0; cell < ncell; ++cell) {
+      int ic[3] = {(int)(cell % h->n[0]), (int)((cell / h->n[0]) % h->n[1]),
+                   (int)(cell / ((int64_t)h->n[0] * h->n[1]))};
+      const int64_t strides[3] = {1, h->n[0], (int64_t)h->n[0] * h->n[1]};
+      for (int dir = 0; dir < 3; ++dir)
+        for (int side = 0; side < 2; ++side) {
+          double* c6 = &fc[(cell * 6 + 2 * dir + side) * 6];
+          const int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+          const double area = h->detJ * h->fscale[dir];
+          const double dscale = 1.0 / (h->detJ * h->fscale[dir] * h->fscale[dir]);  // delta = K_rr * dscale
+          const double ko = Kat(cell, dir, dir);
+          const bool at_end = side ? ic[dir] == h->n[dir] - 1 : ic[dir] == 0;
+          const bool boundary = at_end && !h->periodic[dir];
+          double wo = 1.0, wn = 0.0, gam;
+          if (boundary) {
+            gam = ko * dscale * h->sigma * h->fscale[dir];
+          } else {
+            const int64_t wrap = (int64_t)(h->n[dir] - 1) * strides[dir];
+            const int64_t nbr = side ? (at_end ? cell - wrap : cell + strides[dir])
+                                     : (at_end ? cell + wrap : cell - strides[dir]);
+            const double kn_ = Kat(nbr, dir, dir);
+            wo = kn_ / (ko + kn_);
+            wn = ko / (ko + kn_);
+            gam = (2.0 * ko * kn_ / (ko + kn_)) * dscale * h->sigma * h->fscale[dir];
+          }
+          c6[0] = wo;
+          c6[1] = wn;
+          c6[2] = gam;
+          c6[3] = wo * ko / area;
+          c6[4] = wo * Kat(cell, dir, ta) / area;
+          c6[5] = wo * Kat(cell, dir, tb) / area;
+        }
+    }
+    D.swap(K);
+  }
   std::vector<float> D32(D.begin(), D.end()), fc32(fc.begin(), fc.end());
   std::vector<dgk::dfl> DX(D.size()), fcX(fc.size());
   for (size_t i = 0; i < D.size(); ++i) DX[i] = dgk::dfl(D[i]);
@@ -319,24 +451,24 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     }                                 \
   } while (0)
   {
-    DG_TRY(cudaMalloc(&h->p64.D, ncell * sizeof(double)), "cudaMalloc(D)");
-    DG_TRY(cudaMalloc(&h->p32.D, ncell * sizeof(float)), "cudaMalloc(D32)");
-    DG_TRY(cudaMalloc(&h->p64.fc, ncell * 18 * sizeof(double)), "cudaMalloc(fc)");
-    DG_TRY(cudaMalloc(&h->p32.fc, ncell * 18 * sizeof(float)), "cudaMalloc(fc32)");
-    DG_TRY(cudaMalloc(&h->pX.D, ncell * sizeof(dgk::dfl)), "cudaMalloc(D pairs)");
-    DG_TRY(cudaMalloc(&h->pX.fc, ncell * 18 * sizeof(dgk::dfl)), "cudaMalloc(fc pairs)");
+    const size_t nD = D.size(), nfc = fc.size();  // per cell 1 and 18 values, or 6 and 36 (td)
+    DG_TRY(cudaMalloc(&h->p64.D, nD * sizeof(double)), "cudaMalloc(D)");
+    DG_TRY(cudaMalloc(&h->p32.D, nD * sizeof(float)), "cudaMalloc(D32)");
+    DG_TRY(cudaMalloc(&h->p64.fc, nfc * sizeof(double)), "cudaMalloc(fc)");
+    DG_TRY(cudaMalloc(&h->p32.fc, nfc * sizeof(float)), "cudaMalloc(fc32)");
+    DG_TRY(cudaMalloc(&h->pX.D, nD * sizeof(dgk::dfl)), "cudaMalloc(D pairs)");
+    DG_TRY(cudaMalloc(&h->pX.fc, nfc * sizeof(dgk::dfl)), "cudaMalloc(fc pairs)");
     DG_TRY(cudaMalloc(&h->p64.F, ndof * sizeof(double)), "cudaMalloc(F)");
     DG_TRY(cudaMalloc(&h->p32.F, ndof * sizeof(float)), "cudaMalloc(F32)");
     DG_TRY(cudaMalloc(&h->pX.F, ndof * sizeof(dgk::dfl)), "cudaMalloc(F pairs)");
     DG_TRY(cudaMalloc(&h->work_V, npts * sizeof(double)), "cudaMalloc(work V)");
     DG_TRY(cudaMalloc(&h->work_tr, ncell * 12 * M * M * sizeof(double)), "cudaMalloc(work traces)");
-    DG_TRY(cudaMemcpyAsync(h->p64.D, D.data(), ncell * sizeof(double), cudaMemcpyHostToDevice, s), "copy D");
-    DG_TRY(cudaMemcpyAsync(h->p32.D, D32.data(), ncell * sizeof(float), cudaMemcpyHostToDevice, s), "copy D32");
-    DG_TRY(cudaMemcpyAsync(h->p64.fc, fc.data(), ncell * 18 * sizeof(double), cudaMemcpyHostToDevice, s), "copy fc");
-    DG_TRY(cudaMemcpyAsync(h->p32.fc, fc32.data(), ncell * 18 * sizeof(float), cudaMemcpyHostToDevice, s),
-           "copy fc32");
-    DG_TRY(cudaMemcpyAsync(h->pX.D, DX.data(), ncell * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s), "copy D pairs");
-    DG_TRY(cudaMemcpyAsync(h->pX.fc, fcX.data(), ncell * 18 * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s),
+    DG_TRY(cudaMemcpyAsync(h->p64.D, D.data(), nD * sizeof(double), cudaMemcpyHostToDevice, s), "copy D");
+    DG_TRY(cudaMemcpyAsync(h->p32.D, D32.data(), nD * sizeof(float), cudaMemcpyHostToDevice, s), "copy D32");
+    DG_TRY(cudaMemcpyAsync(h->p64.fc, fc.data(), nfc * sizeof(double), cudaMemcpyHostToDevice, s), "copy fc");
+    DG_TRY(cudaMemcpyAsync(h->p32.fc, fc32.data(), nfc * sizeof(float), cudaMemcpyHostToDevice, s), "copy fc32");
+    DG_TRY(cudaMemcpyAsync(h->pX.D, DX.data(), nD * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s), "copy D pairs");
+    DG_TRY(cudaMemcpyAsync(h->pX.fc, fcX.data(), nfc * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s),
            "copy fc pairs");
     // velocity field tables (before the right hand side, whose inflow terms read b . nu)
     if (vb) {
@@ -391,6 +523,12 @@ int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
   }
   const int N = h->M;  // points per direction
   const double* x = h->tab.xi;
+  // x = lo + J xi for a point xi of the structured reference grid (J = diag(h) without an affine map)
+  auto map = [&](const double xi[3], double* out) {
+    for (int a = 0; a < 3; ++a)
+      out[a] = h->affine ? h->lo[a] + h->J[a][0] * xi[0] + h->J[a][1] * xi[1] + h->J[a][2] * xi[2]
+                         : h->lo[a] + h->h[a] * xi[a];
+  };
   size_t o = 0;
   if (which == 0) {
     for (int iz = 0; iz < h->n[2]; ++iz)
@@ -399,9 +537,9 @@ int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
           for (int i3 = 0; i3 < N; ++i3)
             for (int i2 = 0; i2 < N; ++i2)
               for (int i1 = 0; i1 < N; ++i1) {
-                xyz[o++] = h->lo[0] + h->h[0] * (ix + x[i1]);
-                xyz[o++] = h->lo[1] + h->h[1] * (iy + x[i2]);
-                xyz[o++] = h->lo[2] + h->h[2] * (iz + x[i3]);
+                const double xi[3] = {ix + x[i1], iy + x[i2], iz + x[i3]};
+                map(xi, xyz + o);
+                o += 3;
               }
     return DG_OK;
   }
@@ -411,13 +549,22 @@ int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
     for (int ca = 0; ca < h->n[ta]; ++ca)
       for (int pb = 0; pb < N; ++pb)
         for (int pa = 0; pa < N; ++pa) {
-          double pt[3];
-          pt[dir] = side ? h->hi[dir] : h->lo[dir];
-          pt[ta] = h->lo[ta] + h->h[ta] * (ca + x[pa]);
-          pt[tb] = h->lo[tb] + h->h[tb] * (cb + x[pb]);
-          xyz[o++] = pt[0];
-          xyz[o++] = pt[1];
-          xyz[o++] = pt[2];
+          double xi[3];
+          xi[dir] = side ? h->n[dir] : 0;
+          xi[ta] = ca + x[pa];
+          xi[tb] = cb + x[pb];
+          if (!h->affine && side) {
+            // the upper boundary exactly at hi
+            double pt[3];
+            map(xi, pt);
+            pt[dir] = h->hi[dir];
+            xyz[o++] = pt[0];
+            xyz[o++] = pt[1];
+            xyz[o++] = pt[2];
+            continue;
+          }
+          map(xi, xyz + o);
+          o += 3;
         }
   return DG_OK;
 }
@@ -435,8 +582,9 @@ static int check_apply(dg_handle* h, const void* in, void* out, int32_t precisio
     set_error(std::string(name) + ": precision must be DG_F64, DG_F32 or DG_F64X");
     return DG_ERR_INVALID_ARG;
   }
-  if (h->vb && precision == DG_F32) {
-    set_error(std::string(name) + ": a handle with a velocity field or m = k+3 applies in DG_F64 or DG_F64X only");
+  if ((h->vb || h->td) && precision == DG_F32) {
+    set_error(std::string(name) + ": a handle with a velocity field, m = k+3, a diffusion tensor or an affine "
+                                  "geometry applies in DG_F64 or DG_F64X only");
     return DG_ERR_INVALID_ARG;
   }
   int dev = -1;
@@ -488,7 +636,7 @@ int dg_apply_stage(dg_handle* h, int32_t stage, const void* in, void* out, int32
 }
 
 int dg_rhs(dg_handle* h, void* F, int32_t precision, void* stream) {
-  if (!h || !F || (precision != DG_F64 && precision != DG_F32) || (h->vb && precision != DG_F64)) {
+  if (!h || !F || (precision != DG_F64 && precision != DG_F32) || ((h->vb || h->td) && precision != DG_F64)) {
     set_error("dg_rhs: bad arguments");
     return DG_ERR_INVALID_ARG;
   }

@@ -43,6 +43,14 @@ struct dg_handle {
   void* bscX = nullptr;      // double-float copies of the two tables (DG_F64X applies)
   void* bfaceX = nullptr;
   void* rk_tmp = nullptr;    // Runge-Kutta stage vector (FP64, allocated by the first dg_ssprk2 call)
+  // tensor diffusion / affine geometry kernels (td): Buffers::D then holds K = |det J| J^{-1} D_T J^{-T}
+  // ([ncell][6]) and Buffers::fc six coefficients per face; J is the cell Jacobian (diag(h) unless affine)
+  bool td = false;
+  bool affine = false;
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double Jinv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double detJ = 0;           // |det J| = |T|
+  double fscale[3] = {0, 0, 0};  // |J^{-T} e_r| = |F_r| / |T|
   int64_t ncell = 0;
   double lo[3], hi[3], h[3];
   double b[3] = {0, 0, 0};
@@ -101,5 +109,10 @@ int launch_rhs_f64_vb(const dg_handle* h, const double* f, const double* const g
                       bool project);
 int launch_apply_f64x_vb(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
                          cudaStream_t s);
+// tensor diffusion / affine kernels (h->td): FP64 and double-float operators, FP64 vectors
+int launch_apply_td(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+                    bool pairs, cudaStream_t s);
+int launch_rhs_td(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,
+                  bool project);
 
 }  // namespace dgi

@@ -70,6 +70,7 @@ struct TabNM {
   T w[M];     // Gauss weights on [0,1]
   T L[2][M];  // L[s][l] = l_l(s): lift of a face value onto the normal line
   T P[2][M];  // P[s][l] = l_l'(s): lift of a face normal-derivative weight
+  T Dc[M][M]; // the collocation derivative itself, Dc[i][l] = l_l'(xi_i) (tangential derivatives on faces)
 };
 template <int N, typename T>
 using Tab = TabNM<N, N, T>;
@@ -80,6 +81,7 @@ struct Geo {
   int ncell;
   T vol;       // |T| = h_x h_y h_z
   T area[3];   // |F| of a face normal to axis r
+  T inv_area[3];  // 1 / |F| (conormal traces of the tensor-diffusion kernels)
   T alpha[3];  // |T| / h_r^2       (times D_T: diffusion weight of d_r u)
   T beta[3];   // -b_r |T| / h_r    (convection weight of u)
   T b[3];      // velocity
@@ -441,6 +443,134 @@ __device__ __forceinline__ void cell_tile(const TabNM<N, M, T>& tb, const Geo<T>
   gstore_cells<M>(Vout, sV, cell0, here);
 }
 
+// Cell-kernel work with a full diffusion metric (TD: a per-cell tensor D_T and/or an affine geometry).
+// Reference coordinates: with the cell Jacobian J, K = |det J| J^{-1} D_T J^{-T} (Kc[cell][6] = K00, K11,
+// K22, K01, K02, K12) and the convection vector g.beta = -|det J| J^{-1} b, the volume term of eq. blf is
+//   sum_points w (K grad u + beta u) . grad v + c |det J| w u v        (gradients in reference coordinates).
+// Every flux component needs all three reference derivatives, so the derivative and the transposed
+// derivative passes are split: (1) three derivative passes store grad u; (2) a pointwise pass forms
+// X_r = (K grad u)_r + beta_r u and the reaction; (3) three transposed passes sum B_r (w_perp X_r) into V.
+// The second trace slot of each face holds the physical conormal flux nu . D grad u = (K grad u)_r / |F_r|
+// (nu along +reference axis r), extrapolated from X_r.
+template <int N, typename T, int CPB, typename TV = T, int M = N>
+__device__ __forceinline__ void cell_tile_td(const TabNM<N, M, T>& tb, const Geo<T>& g, const TV* __restrict__ z,
+                                             const T* __restrict__ Kc, T* __restrict__ Vout,
+                                             T* __restrict__ traces, int cell0, int here, unsigned char* smem_raw) {
+  constexpr int NN = M * M, CS = Lay<M>::CS, H = M / 2, C = (M + 1) / 2;
+  T* sU = reinterpret_cast<T*>(smem_raw);  // u, then V
+  T* sG = sU + CPB * CS;                    // [3][CPB][CS]: grad u, then X
+  const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
+  const bool active = lc < here;
+  const int cell = cell0 + lc;
+  T* U = sU + lc * CS;
+  T* G[3] = {sG + lc * CS, sG + (CPB + lc) * CS, sG + (2 * CPB + lc) * CS};
+
+  gload_cells<N, T, TV, M>(sU, z, cell0, here);
+  __syncthreads();
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    if (active && (M == N || t < ModalLines<N, M>::count(dir))) {
+      T x[N], y[M];
+      const int bs = ModalLines<N, M>::base(dir, t), st = Lay<M>::stride(dir);
+      load_line<N>(U, bs, st, x);
+      eo_fwd<N, M, T>(tb, x, y);
+      store_line<M>(U, bs, st, y);
+    }
+    __syncthreads();
+  }
+  T* trc = traces + (size_t)cell * 12 * NN;
+  T ut[3][2];  // value traces of this thread's lines, kept for the conormal traces
+  // (1) z values (last modal pass), then the three derivative passes
+  if (active) {
+    T x[N], u[M];
+    const int bs = Lay<M>::base(2, t), st = Lay<M>::stride(2);
+    load_line<N>(U, bs, st, x);
+    eo_fwd<N, M, T>(tb, x, u);
+    store_line<M>(U, bs, st, u);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    if (active) {
+      T u[M], s[C], d[H > 0 ? H : 1], gr[M];
+      const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
+      load_line<M>(U, bs, st, u);
+      split_sd<M, T>(u, s, d);
+      eo_anti<M, T>(tb.DHm, tb.DHp, s, d, gr);
+      store_line<M>(G[dir], bs, st, gr);
+      T t1 = T(0), t2 = T(0);
+#pragma unroll
+      for (int l = 0; l < C; ++l) t1 = fma(tb.LS[l], s[l], t1);
+#pragma unroll
+      for (int l = 0; l < H; ++l) t2 = fma(tb.LD[l], d[l], t2);
+      ut[dir][0] = t1 - t2;
+      ut[dir][1] = t1 + t2;
+      trc[(4 * dir + 0) * NN + t] = ut[dir][0];
+      trc[(4 * dir + 2) * NN + t] = ut[dir][1];
+    }
+  }
+  __syncthreads();
+  // (2) pointwise: X_r = (K grad u)_r + beta_r u in place of grad u; V = c |det J| w u in place of u.
+  // Thread t handles the points of its z-line (a, b).
+  if (active) {
+    T k6[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) k6[q] = Kc[(size_t)cell * 6 + q];
+    const int a = t % M, b = t / M;
+    const T wab = tb.w[a] * tb.w[b];
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const int p = Lay<M>::idx(a, b, l);
+      const T u = U[p], g0 = G[0][p], g1 = G[1][p], g2 = G[2][p];
+      G[0][p] = fma(k6[0], g0, fma(k6[3], g1, fma(k6[4], g2, g.beta[0] * u)));
+      G[1][p] = fma(k6[3], g0, fma(k6[1], g1, fma(k6[5], g2, g.beta[1] * u)));
+      G[2][p] = fma(k6[4], g0, fma(k6[5], g1, fma(k6[2], g2, g.beta[2] * u)));
+      U[p] = g.creact * wab * tb.w[l] * u;
+    }
+  }
+  __syncthreads();
+  // (3) transposed passes V += B_r (w_perp X_r); conormal traces (X_face - beta_r u_face) / |F_r|
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    if (active) {
+      T X[M], v[M], xs[C], xd[H > 0 ? H : 1], c[M];
+      const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
+      const int a = t % M, b = t / M;
+      const T wperp = tb.w[a] * tb.w[b];
+      load_line<M>(G[dir], bs, st, X);
+      load_line<M>(U, bs, st, v);
+      split_sd<M, T>(X, xs, xd);
+      T t1 = T(0), t2 = T(0);
+#pragma unroll
+      for (int l = 0; l < C; ++l) t1 = fma(tb.LS[l], xs[l], t1);
+#pragma unroll
+      for (int l = 0; l < H; ++l) t2 = fma(tb.LD[l], xd[l], t2);
+      trc[(4 * dir + 1) * NN + t] = (t1 - t2 - g.beta[dir] * ut[dir][0]) * g.inv_area[dir];
+      trc[(4 * dir + 3) * NN + t] = (t1 + t2 - g.beta[dir] * ut[dir][1]) * g.inv_area[dir];
+#pragma unroll
+      for (int i = 0; i < C; ++i) xs[i] = wperp * xs[i];
+#pragma unroll
+      for (int i = 0; i < (H > 0 ? H : 1); ++i) xd[i] = wperp * xd[i];
+      eo_anti<M, T>(tb.BHm, tb.BHp, xs, xd, c);
+#pragma unroll
+      for (int l = 0; l < M; ++l) v[l] += c[l];
+      store_line<M>(U, bs, st, v);
+    }
+    __syncthreads();
+  }
+  gstore_cells<M>(Vout, sU, cell0, here);
+}
+
+template <int N, typename T, int CPB, typename TV = T, int M = N>
+__global__ void __launch_bounds__(CPB * M * M)
+dg_cell_kernel_td(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g,
+                  const TV* __restrict__ z, const T* __restrict__ Kc, T* __restrict__ Vout, T* __restrict__ traces) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cell0 = blockIdx.x * CPB;
+  const int here = min(CPB, g.ncell - cell0);
+  cell_tile_td<N, T, CPB, TV, M>(tb, g, z, Kc, Vout, traces, cell0, here, smem_raw);
+}
+
 template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false>
 __global__ void __launch_bounds__(CPB * M * M)
 dg_cell_kernel(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g, const TV* __restrict__ z,
@@ -477,14 +607,21 @@ struct FaceArgs {
 // mode 2: the Dirichlet terms of l_h).  With PER, an axis flagged periodic has interior end faces whose
 // neighbour is the cell at the other end (PER = false compiles the plain mesh only, which keeps the
 // register count of the FP32 and double-float kernels down).
-template <int N, typename T, bool SELF, typename TV, int M = N, bool VB = false, bool PER = false>
+//
+// TD (tensor diffusion / affine geometry): the face coefficients are (w_own, w_nbr, gamma, kn, kt1, kt2) with
+// kn, kt = w_own (K_rr, K_r,ta, K_r,tb) / |F_r| (boundary: w_own = 1, w_nbr = 0), the second trace is the
+// conormal flux nu . D grad u, and the test-function side -nu.{D grad v}_w also has tangential parts: Wt1,
+// Wt2 weight the reference derivatives of v along the lower and upper tangential axes at the face point.
+template <int N, typename T, bool SELF, typename TV, int M = N, bool VB = false, bool PER = false, bool TD = false>
 __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, TV>& fa, int cell, int tcell,
-                                             const int (&ic)[3], int dir, int s, int t, T wf, T& Vf, T& Wf) {
+                                             const int (&ic)[3], int dir, int s, int t, T wf, T& Vf, T& Wf,
+                                             T& Wt1, T& Wt2) {
   constexpr int NN = M * M;
   const int face = 2 * dir + s;
   const bool at_end = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
   const bool boundary = at_end && !(PER && g.periodic[dir]);
-  const T* c3 = fa.fc + ((size_t)cell * 6 + face) * 3;
+  const T* c3 = fa.fc + ((size_t)cell * 6 + face) * (TD ? 6 : 3);
+  const T kn = TD ? c3[3] : c3[0];  // coefficient of the normal reference derivative of v
   // the neighbour across this face (on a periodic axis the end faces wrap around to the other end)
   auto neighbour = [&]() {
     const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
@@ -503,6 +640,8 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
   }
   Vf = T(0);
   Wf = T(0);
+  Wt1 = T(0);
+  Wt2 = T(0);
   if (fa.mode == 2) {
     // -(Phi(0,g,b_nu), v) - (nu.D grad v, g) + gamma (g, v)
     const T* gs = fa.g[face];
@@ -514,7 +653,11 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
       const T bnu = sgn * bq;
       const T phi = bnu >= T(0) ? T(0) : bnu * gv;
       Vf = wf * (c3[2] * gv - phi);
-      Wf = -wf * sgn * c3[0] * gv;
+      Wf = -wf * sgn * kn * gv;
+      if (TD) {
+        Wt1 = -wf * sgn * c3[4] * gv;
+        Wt2 = -wf * sgn * c3[5] * gv;
+      }
     }
     return;
   }
@@ -536,7 +679,11 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
     const T phi = bq * (bq >= T(0) ? um : up);   // upwind flux Phi(u-, u+, b_nu)
     const T H = fma(gam, jump, phi - avg);        // Phi - nu.{D grad u}_w + gamma [[u]]
     Vf = s ? wf * H : -wf * H;                    // times [[v]] = +v (T-) or -v (T+)
-    Wf = -wf * ao * jump;                         // -nu.{D grad v}_w [[u]]
+    Wf = -wf * kn * jump;                         // -nu.{D grad v}_w [[u]]
+    if (TD) {
+      Wt1 = -wf * c3[4] * jump;
+      Wt2 = -wf * c3[5] * jump;
+    }
   } else {
     // Phi(u,0,b_nu) v - (nu.D grad u) v - (nu.D grad v) u + gamma u v, nu = outward normal
     const T sgn = s ? T(1) : T(-1);
@@ -544,16 +691,22 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
     const T phi = bnu >= T(0) ? bnu * uo : T(0);
     const T aD = c3[0];
     Vf = wf * (phi - sgn * aD * dO + c3[2] * uo);
-    Wf = -wf * sgn * aD * uo;
+    Wf = -wf * sgn * kn * uo;
+    if (TD) {
+      Wt1 = -wf * sgn * c3[4] * uo;
+      Wt2 = -wf * sgn * c3[5] * uo;
+    }
   }
 }
 
 // Face-kernel work on one tile of `here` consecutive cells starting at cell0 (see cell_tile).
-template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false, bool PER = false>
+template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false, bool PER = false,
+          bool TD = false>
 __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>& g, const FaceArgs<T, TV>& fa,
                                           int cell0, int here, int cell_base, unsigned char* smem_raw) {
   constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS;
   T* sV = reinterpret_cast<T*>(smem_raw);
+  T* sW = sV + CPB * CS;  // TD: tangential weights [CPB][side][2][M^2]
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
   const bool active = lc < here;
   const int vcell = cell0 + lc;                                // output / trace index
@@ -580,17 +733,44 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
   // v_l += l_l(s) Vf + l_l'(s) Wf; the z pass continues with the first transposed contraction
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
+    T Vf[2], Wf[2];
+    if (active) {
+      const T wf = g.area[dir] * wab;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        T Wt1, Wt2;
+        face_weights<N, T, SELF, TV, M, VB, PER, TD>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf[s], Wf[s], Wt1,
+                                                     Wt2);
+        if (TD) {
+          sW[((lc * 2 + s) * 2 + 0) * NN + t] = Wt1;
+          sW[((lc * 2 + s) * 2 + 1) * NN + t] = Wt2;
+        }
+      }
+    }
+    if (TD) {
+      // tangential derivatives of v at the face points, transposed: the weight Wt at (a2, b) reaches the
+      // value of v at (a, b) through Dc[a2][a] (and likewise along b)
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const T* W1 = sW + ((lc * 2 + s) * 2 + 0) * NN;
+          const T* W2 = sW + ((lc * 2 + s) * 2 + 1) * NN;
+          T e = Vf[s];
+#pragma unroll
+          for (int q = 0; q < M; ++q) e = fma(tb.Dc[q][a], W1[q + M * b], fma(tb.Dc[q][b], W2[a + M * q], e));
+          Vf[s] = e;
+        }
+      }
+    }
     if (active) {
       const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
       T v[M];
       load_line<M>(V, bs, st, v);
-      const T wf = g.area[dir] * wab;
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        T Vf, Wf;
-        face_weights<N, T, SELF, TV, M, VB, PER>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf, Wf);
 #pragma unroll
-        for (int l = 0; l < M; ++l) v[l] = fma(tb.L[s][l], Vf, fma(tb.P[s][l], Wf, v[l]));
+        for (int l = 0; l < M; ++l) v[l] = fma(tb.L[s][l], Vf[s], fma(tb.P[s][l], Wf[s], v[l]));
       }
       if (dir == 2) {
         T y[N];
@@ -645,14 +825,14 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
 }
 
 template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false,
-          bool PER = false>
+          bool PER = false, bool TD = false>
 __global__ void __launch_bounds__(CPB * M * M)
 dg_face_kernel(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g,
                const __grid_constant__ FaceArgs<T, TV> fa, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
-  face_tile<N, T, SELF, CPB, TV, M, VB, PER>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
+  face_tile<N, T, SELF, CPB, TV, M, VB, PER, TD>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
 }
 
 // The same kernel with 8 resident CTAs of 256 threads requested: used for FP32 when a CTA has 256 threads
@@ -668,12 +848,12 @@ dg_face_kernel_occ8(const __grid_constant__ TabNM<N, M, T> tb, const __grid_cons
 }
 
 // the face kernel of a launch configuration (the FP32 256-thread variant above, or the general one)
-template <int N, typename T, int CPB, typename TV, int M, bool VB, bool PER>
+template <int N, typename T, int CPB, typename TV, int M, bool VB, bool PER, bool TD = false>
 constexpr auto face_kernel_for() {
-  if constexpr (std::is_same<T, float>::value && !VB && CPB * M * M == 256) {
+  if constexpr (std::is_same<T, float>::value && !VB && !TD && CPB * M * M == 256) {
     return &dg_face_kernel_occ8<N, T, CPB, TV, M, PER>;
   } else {
-    return &dg_face_kernel<N, T, false, CPB, TV, M, VB, PER>;
+    return &dg_face_kernel<N, T, false, CPB, TV, M, VB, PER, TD>;
   }
 }
 

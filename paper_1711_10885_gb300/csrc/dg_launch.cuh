@@ -42,6 +42,7 @@ dgk::TabNM<N, M, T> make_tab(const Tables1D& t) {
       r.L[s][i] = (T)t.L[s][i];
       r.P[s][i] = (T)t.P[s][i];
     }
+    for (int l = 0; l < M; ++l) r.Dc[i][l] = (T)t.Dt[i][l];
   }
   return r;
 }
@@ -49,17 +50,34 @@ dgk::TabNM<N, M, T> make_tab(const Tables1D& t) {
 template <typename T>
 dgk::Geo<T> make_geo(const dg_handle* h) {
   dgk::Geo<T> g;
-  const double vol = h->h[0] * h->h[1] * h->h[2];
-  for (int r = 0; r < 3; ++r) {
-    g.n[r] = h->n[r];
-    g.area[r] = (T)(vol / h->h[r]);
-    g.alpha[r] = (T)(vol / (h->h[r] * h->h[r]));
-    g.beta[r] = (T)(-h->b[r] * vol / h->h[r]);
-    g.b[r] = (T)h->b[r];
+  if (!h->affine) {
+    const double vol = h->h[0] * h->h[1] * h->h[2];
+    for (int r = 0; r < 3; ++r) {
+      g.n[r] = h->n[r];
+      g.area[r] = (T)(vol / h->h[r]);
+      g.inv_area[r] = (T)(h->h[r] / vol);
+      g.alpha[r] = (T)(vol / (h->h[r] * h->h[r]));
+      g.beta[r] = (T)(-h->b[r] * vol / h->h[r]);
+      g.b[r] = (T)h->b[r];
+    }
+    g.vol = (T)vol;
+    g.creact = (T)(h->c * vol);
+  } else {
+    // affine cells: |F_r| = |det J| |J^{-T} e_r|, b . nu_r = (J^{-1} b)_r / |J^{-T} e_r|,
+    // convection weight -|det J| (J^{-1} b)_r
+    for (int r = 0; r < 3; ++r) {
+      const double jb = h->Jinv[r][0] * h->b[0] + h->Jinv[r][1] * h->b[1] + h->Jinv[r][2] * h->b[2];
+      g.n[r] = h->n[r];
+      g.area[r] = (T)(h->detJ * h->fscale[r]);
+      g.inv_area[r] = (T)(1.0 / (h->detJ * h->fscale[r]));
+      g.alpha[r] = T(0);
+      g.beta[r] = (T)(-h->detJ * jb);
+      g.b[r] = (T)(jb / h->fscale[r]);
+    }
+    g.vol = (T)h->detJ;
+    g.creact = (T)(h->c * h->detJ);
   }
   g.ncell = (int)h->ncell;
-  g.vol = (T)vol;
-  g.creact = (T)(h->c * vol);
   for (int r = 0; r < 3; ++r) g.periodic[r] = h->periodic[r];
   g.bsc = nullptr;
   g.bface = nullptr;
@@ -303,6 +321,72 @@ int rhs_vb_n(const dg_handle* h, const double* f, const double* const g[6], doub
   if (h->M == N + 2) return rhs_n<N, double, N + 2, true>(h, f, g, F, s, project);
   set_error("unsupported number of quadrature points");
   return DG_ERR_INVALID_ARG;
+}
+
+}  // namespace dgi
+
+namespace dgi {
+
+// Tensor diffusion / affine geometry kernels (M = N), FP64 (T = double) or double-float (T = dfl) operator.
+template <int N, typename T>
+int set_td_smem_attrs() {
+  static bool done = false;
+  if (done) return 0;
+  constexpr int CPB = dgk::Launch<N>::CPB;
+  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel_td<N, T, CPB, double, N>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * cell_smem<N, T>()));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel_td)");
+  e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, double, N, false, true, true>(),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(face_smem<N, T>() + (size_t)CPB * 4 * N * N * sizeof(T)));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel td)");
+  done = true;
+  return 0;
+}
+
+template <int N, typename T>
+int apply_td_n(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+               const double* const g6[6], cudaStream_t s, bool project) {
+  if (int rc = set_td_smem_attrs<N, T>()) return rc;
+  constexpr int CPB = dgk::Launch<N>::CPB;
+  const Buffers& bf = buffers_for<T>(h);
+  const auto tb = make_tab<N, T>(h->tab);
+  auto geo = make_geo<T>(h);
+  const unsigned grid = (unsigned)((h->ncell + CPB - 1) / CPB);
+  T* V = static_cast<T*>(h->work_V);
+  T* tr = static_cast<T*>(h->work_tr);
+  if (mode != 2 && (stages & 1))
+    dgk::dg_cell_kernel_td<N, T, CPB, double, N><<<grid, dgk::Launch<N>::THREADS, 2 * cell_smem<N, T>(), s>>>(
+        tb, geo, z, static_cast<const T*>(bf.D), V, tr);
+  dgk::FaceArgs<T, double> fa;
+  fa.V = mode == 2 ? reinterpret_cast<const T*>(z) : V;
+  fa.traces = mode == 2 ? nullptr : tr;
+  fa.fc = static_cast<const T*>(bf.fc);
+  fa.F = (mode == 1 || mode == 3) ? static_cast<const T*>(bf.F) : nullptr;
+  for (int i = 0; i < 6; ++i) fa.g[i] = (mode == 2 && !project && g6) ? reinterpret_cast<const T*>(g6[i]) : nullptr;
+  fa.y = y;
+  fa.mode = mode;
+  fa.u = z;
+  fa.z0 = nullptr;
+  fa.cz = fa.cu = fa.cr = 0.0;
+  if (mode == 2 && project) geo.vol = T(1);
+  if (mode == 3) {
+    if (!st) {
+      set_error("Runge-Kutta stage without coefficients");
+      return DG_ERR_INVALID_ARG;
+    }
+    fa.z0 = st->z0;
+    fa.cz = st->cz;
+    fa.cu = st->cu;
+    fa.cr = st->cr;
+  }
+  if (stages & 2)
+    dgk::face_kernel_for<N, T, CPB, double, N, false, true, true>()
+        <<<grid, dgk::Launch<N>::THREADS, face_smem<N, T>() + (size_t)CPB * 4 * N * N * sizeof(T), s>>>(
+            tb, geo, fa, dgk::SelfArgs{0, 0});
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-diffusion kernel launch");
+  return 0;
 }
 
 }  // namespace dgi

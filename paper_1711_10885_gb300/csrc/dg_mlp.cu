@@ -618,8 +618,9 @@ int dg_mlp_param_offsets(const dg_mlp* m, int64_t* offsets6) {
 int dg_mlp_features(const dg_mlp* m, const dg_handle* h, const void* r, int32_t precision, const int32_t* cells,
                     int64_t rows, void* X, float* scale, void* stream) {
   if (!m || !h || !r || !X || !scale || (precision != DG_F64 && precision != DG_F32) ||
-      h->N * h->N * h->N != m->d.nb) {
-    set_error("dg_mlp_features: bad arguments or degree mismatch");
+      h->N * h->N * h->N != m->d.nb || h->td) {
+    set_error("dg_mlp_features: bad arguments, degree mismatch, or a tensor-diffusion handle (the features use "
+              "the scalar log D of each cell)");
     return DG_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -730,8 +731,8 @@ int dgi::mlp_apply_impl(dg_mlp* m, const dg_handle* h, const void* r, void* z, i
                         cudaStream_t s) {
   void* stream = s;
   if (!m || !h || !r || !z || r == z || (precision != DG_F64 && precision != DG_F32) ||
-      h->N * h->N * h->N != m->d.nb) {
-    set_error("dg_mlp_apply: bad arguments or degree mismatch");
+      h->N * h->N * h->N != m->d.nb || h->td) {
+    set_error("dg_mlp_apply: bad arguments, degree mismatch, or a tensor-diffusion handle");
     return DG_ERR_INVALID_ARG;
   }
   const int64_t rows = h->ncell;

@@ -216,8 +216,9 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
     set_error("dg_precond_setup: kind must be 1 (block-Jacobi)");
     return DG_ERR_INVALID_ARG;
   }
-  if (h->vb) {
-    set_error("dg_precond_setup: block-Jacobi needs a constant velocity and m = k+1");
+  if (h->vb || h->td) {
+    set_error("dg_precond_setup: block-Jacobi needs a constant velocity, m = k+1 and scalar diffusion on the "
+              "axis-parallel grid");
     return DG_ERR_INVALID_ARG;
   }
   for (int r = 0; r < 3; ++r)

@@ -239,8 +239,9 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     set_error("dg_solve: bad options (restart <= 60, mode, preconditioner, rtol > 0, 0 < inner_rtol < 1)");
     return DG_ERR_INVALID_ARG;
   }
-  if (h->vb && o->mode != DG_SOLVE_FP64) {
-    set_error("dg_solve: a handle with a velocity field or m = k+3 solves in DG_SOLVE_FP64 only");
+  if ((h->vb || h->td) && o->mode != DG_SOLVE_FP64) {
+    set_error("dg_solve: a handle with a velocity field, m = k+3, a diffusion tensor or an affine geometry solves "
+              "in DG_SOLVE_FP64 only");
     return DG_ERR_INVALID_ARG;
   }
   if ((o->preconditioner == DG_PRECOND_BLOCK_JACOBI || o->preconditioner == DG_PRECOND_BJ_MLP) && !h->bj64) {

@@ -194,7 +194,7 @@ int dg_rk_stage(dg_handle* h, const double* u, const double* z0, double* y, doub
     set_error("dg_rk_stage: coefficients must be finite");
     return DG_ERR_INVALID_ARG;
   }
-  const double vol = h->h[0] * h->h[1] * h->h[2];
+  const double vol = h->detJ;  // |T|: the mass matrix is |T| I
   const StageArgs st{z0, cz, cu, cdt / vol};  // M^{-1} = I / |T|
   return stage(h, u, y, st, precision, static_cast<cudaStream_t>(stream));
 }
@@ -212,7 +212,7 @@ int dg_ssprk2(dg_handle* h, double* z, double dt, int32_t nsteps, int32_t precis
     if (e != cudaSuccess) return cuda_fail(e, "dg_ssprk2: stage vector");
   }
   double* z1 = static_cast<double*>(h->rk_tmp);
-  const double vol = h->h[0] * h->h[1] * h->h[2];
+  const double vol = h->detJ;  // |T|: the mass matrix is |T| I
   const StageArgs st1{z, 0.0, 1.0, dt / vol};
   const StageArgs st2{z, 0.5, 0.5, 0.5 * dt / vol};
   for (int32_t i = 0; i < nsteps; ++i) {

@@ -52,7 +52,7 @@ _VELOCITY = {"constant": DG_VELOCITY_CONSTANT, "points": DG_VELOCITY_POINTS, "ta
 
 class dg_setup_ext(ctypes.Structure):
     _fields_ = [("periodic", ctypes.c_int32 * 3), ("m", ctypes.c_int32), ("velocity", ctypes.c_int32),
-                ("b_qp", _dp), ("b_face", _dp)]
+                ("b_qp", _dp), ("b_face", _dp), ("D_tensor", _dp), ("jacobian", _dp)]
 
 
 DG_SOLVE_FP64 = 0
@@ -192,11 +192,12 @@ class Operator:
 
     Transport options (dg_setup_ext): ``periodic`` flags per axis, ``m`` Gauss points per direction (k+1 or
     k+3), ``velocity`` "constant" (b), "points" (b_qp [ncell, m^3, 3] and b_face [ncell, 6, m^2]) or
-    "taylor_green" (the flow field of Sec. 5.3, evaluated by the library)."""
+    "taylor_green" (the flow field of Sec. 5.3, evaluated by the library); ``D_tensor`` [ncell, 6] per-cell
+    diffusion tensors and ``jacobian`` (3x3) affine cells lo + J (ic + [0,1]^3) (Sec. 5.1)."""
 
     def __init__(self, n, k, D=1.0, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), f_qp=None, g_qp=None, stream=None, periodic=(0, 0, 0), m=None,
-                 velocity="constant", b_qp=None, b_face=None):
+                 velocity="constant", b_qp=None, b_face=None, D_tensor=None, jacobian=None):
         mesh = dg_mesh()
         for r in range(3):
             mesh.lo[r], mesh.hi[r], mesh.n[r] = float(lo[r]), float(hi[r]), int(n[r])
@@ -245,6 +246,18 @@ class Operator:
             keep += [bq, bf]
             ext.b_qp = bq.ctypes.data_as(_dp)
             ext.b_face = bf.ctypes.data_as(_dp)
+        if D_tensor is not None:
+            dt = _f64(D_tensor).reshape(-1)
+            if dt.size != 6 * self.ncell:
+                raise ValueError("D_tensor must have 6 values per cell")
+            keep.append(dt)
+            ext.D_tensor = dt.ctypes.data_as(_dp)
+        if jacobian is not None:
+            jm = _f64(jacobian).reshape(-1)
+            if jm.size != 9:
+                raise ValueError("jacobian must be 3x3")
+            keep.append(jm)
+            ext.jacobian = jm.ctypes.data_as(_dp)
         h = ctypes.c_void_p()
         check(lib.dg_setup_ex(ctypes.byref(mesh), int(k), ctypes.byref(co), bcp, fptr, ctypes.byref(ext),
                               _stream_ptr(stream), ctypes.byref(h)))

@@ -184,3 +184,16 @@ def taylor_green(n=16, k=5, m=None) -> Workload:
                  f_kind="zero", lo=(-np.pi,) * 3, hi=(np.pi,) * 3, periodic=(1, 1, 1), velocity="taylor_green",
                  m=m if m is not None else k + 3)
     return w
+
+
+def log_normal_tensors(ncell: int, sigma: float, seed: int, anisotropy: float = 0.5) -> np.ndarray:
+    """Per-cell symmetric positive definite diffusion tensors (xx, yy, zz, xy, xz, yz): R diag(l) R^T with
+    log-normal eigenvalues l = exp(sigma N(0,1)) and a random rotation R per cell, the eigenvalues spread by
+    a further factor exp(anisotropy N(0,1)) each."""
+    rng = np.random.default_rng(seed)
+    base = np.exp(sigma * rng.standard_normal(ncell))
+    lam = base[:, None] * np.exp(anisotropy * rng.standard_normal((ncell, 3)))
+    Q, R = np.linalg.qr(rng.standard_normal((ncell, 3, 3)))
+    Q = Q * np.sign(np.diagonal(R, axis1=1, axis2=2))[:, None, :]
+    M = np.einsum("cij,cj,ckj->cik", Q, lam, Q)
+    return np.stack([M[:, 0, 0], M[:, 1, 1], M[:, 2, 2], M[:, 0, 1], M[:, 0, 2], M[:, 1, 2]], axis=1)

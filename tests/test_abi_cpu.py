@@ -114,3 +114,27 @@ def test_time_stepping_entry_points_reject_null_arguments_on_host():
     assert dg.lib.dg_project(None, None, None, None) == -1
     assert dg.lib.dg_rk_stage(None, None, None, None, 0.0, 1.0, 0.1, 0, None) == -1
     assert dg.lib.dg_ssprk2(None, None, 0.1, 1, 0, None) == -1
+
+
+def test_setup_ex_rejects_bad_tensors_and_jacobians_on_host():
+    from paper_1711_10885_gb300 import dg
+    mesh = dg.dg_mesh()
+    for r in range(3):
+        mesh.lo[r], mesh.hi[r], mesh.n[r] = 0.0, 1.0, 1
+    co = dg.dg_coeffs()
+    co.D_const, co.c, co.sigma = 1.0, 0.0, 4.0
+    h = ctypes.c_void_p()
+    ext = dg.dg_setup_ext()
+    bad = (ctypes.c_double * 6)(1.0, 1.0, 1.0, 2.0, 0.0, 0.0)  # indefinite: xy entry too large
+    ext.D_tensor = ctypes.cast(bad, dg._dp)
+    rc = dg.lib.dg_setup_ex(ctypes.byref(mesh), 2, ctypes.byref(co), None, None, ctypes.byref(ext), None,
+                            ctypes.byref(h))
+    assert rc == -1 and b"positive definite" in dg.lib.dg_last_error()
+    ext.D_tensor = dg._dp()
+    ext.velocity = dg.DG_VELOCITY_TAYLOR_GREEN
+    J = (ctypes.c_double * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    ext.jacobian = ctypes.cast(J, dg._dp)
+    rc = dg.lib.dg_setup_ex(ctypes.byref(mesh), 2, ctypes.byref(co), None, None, ctypes.byref(ext), None,
+                            ctypes.byref(h))
+    assert rc == -1 and b"constant velocity" in dg.lib.dg_last_error()
+    assert h.value is None
