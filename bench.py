@@ -229,6 +229,21 @@ def run_profile(args):
     if args.profile_solver:
         return run_profile_solver(args)
     torch.cuda.set_device(0)
+    if args.tensor:
+        # tensor diffusion on the 32^3 Q7 workload: W + K residual applies
+        import numpy as np
+        w = inputs.unit_cube_q7_32()
+        op = dg.Operator(w.n, w.k, 1.0, b=w.b, c=w.c, D_tensor=inputs.log_normal_tensors(w.ncell, 1.0, 60),
+                         f_qp=np.ones(w.ncell * (w.k + 1) ** 3))
+        u = torch.tensor(w.u, device="cuda")
+        r = torch.empty_like(u)
+        prec = dg.DG_F64X if args.precision == "f64x" else dg.DG_F64
+        for _ in range(args.warmup + args.steps):
+            op.apply_residual(u, r, precision=prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
+        op.close()
+        return
     if args.matrix:
         # matrix-based comparison: assemble on matrix_n^3 cells of degree matrix_k, then W + K products
         w = inputs.small_case(n=(args.matrix_n,) * 3, k=args.matrix_k, seed=200 + args.matrix_k)
@@ -318,6 +333,57 @@ def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10):
         b.synchronize()
         out[f"block_jacobi_{prec}_ms"] = a.elapsed_time(b) / 20
     op.close()
+    return out
+
+
+def tensor_benchmark(reps=20):
+    """The paper's Problem A coefficients (Sec. 5.1: tensor-valued diffusion, constant per cell) on the
+    32^3 Q7 workload: per-cell SPD tensors R diag(l) R^T with log-normal eigenvalues (seed 60), b, c, f
+    as in the scalar workload; the same mesh with affine (sheared and rotated) cells.  FP64 and
+    double-float residual applications."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10885_gb300 import dg, flops, inputs
+    w = inputs.unit_cube_q7_32()
+    Dt = inputs.log_normal_tensors(w.ncell, 1.0, 60)
+    th = 0.35
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    S = np.array([[1.0, 0.25, -0.15], [0.0, 1.1, 0.3], [0.05, 0.0, 0.9]])
+    J = R @ S @ np.diag([1.0 / 32] * 3)
+    N = w.k + 1
+    cell_fl = flops.cell_kernel_flops_td(N) * w.ncell
+    face_fl = flops.face_kernel_flops_td(N) * w.ncell
+    stream = torch.cuda.current_stream()
+    out = {"workload": "unit_cube_q7_32 with per-cell tensors", "dofs": w.ndof,
+           "executed_flops_per_dof": (cell_fl + face_fl) / w.ndof, "paper_flopdof": flops.paper_flopdof(w.k)}
+    for name, jac in (("axis_parallel", None), ("affine", J)):
+        op = dg.Operator(w.n, w.k, 1.0, b=w.b, c=w.c, D_tensor=Dt, jacobian=jac,
+                         f_qp=np.ones(w.ncell * N ** 3))
+        u = torch.tensor(w.u, device="cuda")
+        r = torch.empty_like(u)
+        rec = {}
+        for pname, prec in (("f64", dg.DG_F64), ("f64x", dg.DG_F64X)):
+            for _ in range(3):
+                op.apply_residual(u, r, precision=prec)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+            for i in range(reps):
+                ev[3 * i].record(stream)
+                op.apply_stage(0, u, r, residual=True, precision=prec)
+                ev[3 * i + 1].record(stream)
+                op.apply_stage(1, u, r, residual=True, precision=prec)
+                ev[3 * i + 2].record(stream)
+            torch.cuda.synchronize()
+            cms = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(reps)) / reps
+            fms = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(reps)) / reps
+            rec[pname] = {"mdofs": w.ndof / ((cms + fms) * 1e-3) / 1e6,
+                          "kernels_ms": {"dg_cell_kernel_td": cms, "dg_face_kernel<td>": fms},
+                          "fp64_equivalent_tflops": (cell_fl + face_fl) / ((cms + fms) * 1e-3) / 1e12}
+        ach = cell_fl / (rec["f64"]["kernels_ms"]["dg_cell_kernel_td"] * 1e-3) / 1e12
+        rec["roofline_f64"] = {"bound": "alu", "kernel": "dg_cell_kernel_td<8, double>", "achieved": ach,
+                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}
+        out[name] = rec
+        op.close()
     return out
 
 
@@ -704,6 +770,8 @@ def run_ours(args):
         line["transport"] = transport_benchmark()
     if ws == 1 and not args.no_matrix:
         line["matrix_based"] = matrix_benchmark(degrees=(3, 7))
+    if ws == 1 and not args.no_tensor:
+        line["tensor_diffusion"] = tensor_benchmark()
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -722,6 +790,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--no-transport", action="store_true", help="skip the Taylor-Green transport section")
     ap.add_argument("--no-matrix", action="store_true", help="skip the matrix-based comparison section")
+    ap.add_argument("--no-tensor", action="store_true", help="skip the tensor-diffusion / affine section")
+    ap.add_argument("--tensor", action="store_true", help="print only the tensor-diffusion / affine section")
     ap.add_argument("--matrix", action="store_true",
                     help="print only the matrix-free vs matrix-based comparison for k = 1, 3, 5, 7; with --profile: "
                          "assemble on --matrix-n^3 cells of degree --matrix-k and run W + K products")
@@ -749,6 +819,10 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"matrix_based": matrix_benchmark()}), flush=True)
+    elif args.tensor:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"tensor_diffusion": tensor_benchmark()}), flush=True)
     elif args.transport:
         import torch
         torch.cuda.set_device(0)

@@ -76,6 +76,30 @@ def face_kernel_flops(N: int, n=(1, 1, 1), residual: bool = True, M: int | None 
     return MM + lift + back + epilogue
 
 
+def cell_kernel_flops_td(N: int) -> float:
+    """Executed FP operations of dg_cell_kernel_td (tensor diffusion / affine cells, M = N) per cell."""
+    H, C = _halves(N)
+    NN = N * N
+    fwd = 3 * NN * eo_fwd_flops(N)
+    traces_u = 2 * C + 2 * H + 2
+    deriv = 3 * NN * (2 * H + eo_anti_flops(N) + traces_u)
+    pointwise = NN * (1 + N * (3 * 7 + 3))  # wab; per point 3 rows (3 fma + beta mul) and the reaction
+    traces_x = 2 * C + 2 * H + 2 + 8
+    transposed = 3 * NN * (2 * H + traces_x + 1 + N + eo_anti_flops(N) + N)
+    return fwd + deriv + pointwise + transposed
+
+
+def face_kernel_flops_td(N: int, residual: bool = True) -> float:
+    """Executed FP operations of the tensor-diffusion face kernel per cell: the face weights with the two
+    tangential weights, their transposed tangential derivatives (2 N fma per point and side), the lift and
+    the backward contractions."""
+    NN = N * N
+    per_point = 11 + 4 + 4 * N  # weights, tangential weights, tangential derivative sums
+    lift = 3 * NN * (1 + 2 * (per_point + 4 * N))
+    back = 3 * NN * eo_bwd_flops(N)
+    return NN + lift + back + (N ** 3 if residual else 0)
+
+
 def apply_flops_per_dof(k: int, n=(1, 1, 1), residual: bool = True) -> float:
     N = k + 1
     return (cell_kernel_flops(N) + face_kernel_flops(N, n, residual)) / N ** 3
