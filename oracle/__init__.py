@@ -58,9 +58,10 @@ def _configure(lib):
     lib.oracle_rhs.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                ctypes.c_double, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_apply_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                    ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _ip, ctypes.c_int]
+                                    ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip,
+                                    ctypes.c_int]
     lib.oracle_rhs_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                  ctypes.c_double, _ip, _dp, _dp, _dp, _dp, ctypes.POINTER(_dp), _dp]
+                                  ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_cell_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_volume_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
@@ -139,7 +140,8 @@ class Problem:
     """
 
     def __init__(self, n, k, D, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
-                 m=None, periodic=(0, 0, 0), b_vol=None, b_face=None, D_tensor=None, J=None):
+                 m=None, periodic=(0, 0, 0), b_vol=None, b_face=None, D_tensor=None, J=None, D_vol=None,
+                 D_face=None, c_vol=None):
         self.n = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(3))
         self.lo = _arr(lo, 3)
         self.hi = _arr(hi, 3)
@@ -158,9 +160,17 @@ class Problem:
         self.b_face = None if b_face is None else _arr(b_face, self.ncell * 6 * self.m ** 2)
         self.D_tensor = None if D_tensor is None else _arr(D_tensor, self.ncell * 6)
         self.J = None if J is None else _arr(J, 9)
+        # coefficients at the quadrature points (Problem B): D_vol [ncell, m^3, 6], D_face [ncell, 6, m^2, 6],
+        # c_vol [ncell, m^3]
+        self.D_vol = None if D_vol is None else _arr(D_vol, self.ncell * self.m ** 3 * 6)
+        self.D_face = None if D_face is None else _arr(D_face, self.ncell * 6 * self.m ** 2 * 6)
+        self.c_vol = None if c_vol is None else _arr(c_vol, self.ncell * self.m ** 3)
 
     def _general(self):
         return (_d(self.D_tensor) if self.D_tensor is not None else None, _d(self.J) if self.J is not None else None)
+
+    def _pointwise(self):
+        return tuple(_d(a) if a is not None else None for a in (self.D_vol, self.D_face, self.c_vol))
 
     @property
     def ndof(self):
@@ -188,7 +198,7 @@ def apply(pr: Problem, u, cells=None) -> np.ndarray:
     """y = A u with (A u)_i = a_h(u, phi_i) (eq. blf); if ``cells`` is given only those cells' blocks."""
     u = _arr(u, pr.ndof)
     ex = (pr.periodic.ctypes.data_as(_ip), _d(pr.b_vol) if pr.b_vol is not None else None,
-          _d(pr.b_face) if pr.b_face is not None else None, *pr._general())
+          _d(pr.b_face) if pr.b_face is not None else None, *pr._general(), *pr._pointwise())
     if cells is None:
         y = np.empty(pr.ndof)
         rc = _load().oracle_apply_ex(*pr._args(), *ex, _d(u), _d(y), None, 0)
@@ -218,7 +228,7 @@ def rhs(pr: Problem, f_qp=None, g_qp=None) -> np.ndarray:
                 garr[s] = _d(a)
     rc = _load().oracle_rhs_ex(*pr._args(), pr.periodic.ctypes.data_as(_ip),
                                _d(pr.b_face) if pr.b_face is not None else None, *pr._general(),
-                               _d(fa) if fa is not None else None, garr, _d(F))
+                               pr._pointwise()[1], _d(fa) if fa is not None else None, garr, _d(F))
     if rc != 0:
         raise RuntimeError(f"oracle_rhs failed ({rc})")
     return F

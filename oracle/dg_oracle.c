@@ -27,6 +27,11 @@
  *    delta = nu^T D nu in the face weights and the penalty; constant c; and
  *    either a constant b (Problem A) or b given at the quadrature points (the
  *    Taylor-Green transport problem of Sec. 5.3, evaluated by the caller);
+ *  - coefficients given at the quadrature points instead (Problem B of Sec. 5.1:
+ *    "coefficients that are polynomials in the coordinates", evaluated by the
+ *    caller): D at the volume points and at each cell's face points, c at the
+ *    volume points; on a face, delta, the weights and the penalty are then
+ *    taken point by point from the two cells' tensors at that point;
  *  - geometry: axis-parallel cells, or an affine image of the structured grid
  *    (every cell T = lo + J (ic + [0,1]^3) with one constant Jacobian J, as in
  *    Problem B of Sec. 5.1); gradients map as J^{-T}, |T| = |det J|, a face
@@ -124,6 +129,9 @@ typedef struct {
   const double* Dten;   /* NULL, or [ncells][6] diffusion tensor (xx, yy, zz, xy, xz, yz); replaces D */
   int affine;           /* 1: cells are lo + J (ic + [0,1]^3) with the Jacobian J below; 0: J = diag(h) */
   double J[3][3];
+  const double* D_vol;  /* NULL, or the tensor at the volume points [ncells][m^3][6]            */
+  const double* D_face; /* NULL, or the tensor at each cell's face points [ncells][6][m^2][6]   */
+  const double* c_vol;  /* NULL, or c at the volume points [ncells][m^3]                      */
 } oracle_problem;
 
 /* Full 3D tables at one set of points: phi[p*nb + J], grad[(p*nb + J)*3 + r]
@@ -264,16 +272,20 @@ static void eval_fe(const table3d* t, int p, const double* zc, const oracle_ctx*
   phys_grad(cx, gr3, g);
 }
 
+/* a packed symmetric tensor (xx, yy, zz, xy, xz, yz) as a 3x3 matrix */
+static void unpack6(const double* t, double Dm[3][3]) {
+  Dm[0][0] = t[0];
+  Dm[1][1] = t[1];
+  Dm[2][2] = t[2];
+  Dm[0][1] = Dm[1][0] = t[3];
+  Dm[0][2] = Dm[2][0] = t[4];
+  Dm[1][2] = Dm[2][1] = t[5];
+}
+
 /* diffusion tensor of a cell: the given symmetric tensor, or D_T * I */
 static void diff_tensor(const oracle_problem* pr, int cell, double Dm[3][3]) {
   if (pr->Dten) {
-    const double* t = pr->Dten + (size_t)cell * 6;
-    Dm[0][0] = t[0];
-    Dm[1][1] = t[1];
-    Dm[2][2] = t[2];
-    Dm[0][1] = Dm[1][0] = t[3];
-    Dm[0][2] = Dm[2][0] = t[4];
-    Dm[1][2] = Dm[2][1] = t[5];
+    unpack6(pr->Dten + (size_t)cell * 6, Dm);
   } else {
     for (int a = 0; a < 3; ++a)
       for (int c = 0; c < 3; ++c) Dm[a][c] = a == c ? pr->D[cell] : 0.0;
@@ -321,8 +333,12 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
     double uq, g[3];
     eval_fe(&cx->vol, p, zc, cx, &uq, g);
     double dx = cx->vol.wgt[p] * cx->vol_T; /* Delta_T * w_i */
+    double Dp_[3][3];
+    if (pr->D_vol) unpack6(pr->D_vol + ((size_t)cell * cx->vol.np + p) * 6, Dp_);
+    const double(*Dq)[3] = pr->D_vol ? Dp_ : DT;   /* D at this point */
+    const double cq = pr->c_vol ? pr->c_vol[(size_t)cell * cx->vol.np + p] : pr->c;
     double Dg[3], fl[3];
-    for (int a = 0; a < 3; ++a) Dg[a] = DT[a][0] * g[0] + DT[a][1] * g[1] + DT[a][2] * g[2];
+    for (int a = 0; a < 3; ++a) Dg[a] = Dq[a][0] * g[0] + Dq[a][1] * g[1] + Dq[a][2] * g[2];
     for (int r = 0; r < 3; ++r) {
       const double br = pr->b_vol ? pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + r] : pr->b[r];
       fl[r] = Dg[r] - br * uq;
@@ -331,7 +347,7 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
     for (int i = 0; i < nb; ++i) {
       double gv[3];
       test_grad(&cx->vol, p, i, cx, gv);
-      y[i] += dx * (fl[0] * gv[0] + fl[1] * gv[1] + fl[2] * gv[2] + pr->c * uq * ph[i]);
+      y[i] += dx * (fl[0] * gv[0] + fl[1] * gv[1] + fl[2] * gv[2] + cq * uq * ph[i]);
     }
   }
 
@@ -357,12 +373,21 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
         int this_is_minus = side == 1;
         double DN[3][3];
         diff_tensor(pr, nbr, DN);
-        const double(*Dm)[3] = this_is_minus ? DT : DN;
-        const double(*Dp)[3] = this_is_minus ? DN : DT;
-        double dm = flux_along(nu, Dm, nu), dp = flux_along(nu, Dp, nu); /* delta = nu^T D nu */
-        double wm = dp / (dm + dp), wp = dm / (dm + dp);
-        double gam = harmonic(dm, dp) * pr->sigma * dF / cx->vol_T;
+        const int oface = 2 * dir + (1 - side); /* the same face seen from the neighbour */
         for (int p = 0; p < ft->np; ++p) {
+          /* the two cells' tensors at this face point (constant per cell unless given point-wise) */
+          double Do_[3][3], Dn_[3][3];
+          if (pr->D_face) {
+            unpack6(pr->D_face + (((size_t)cell * 6 + 2 * dir + side) * ft->np + p) * 6, Do_);
+            unpack6(pr->D_face + (((size_t)nbr * 6 + oface) * ft->np + p) * 6, Dn_);
+          }
+          const double(*Dow)[3] = pr->D_face ? Do_ : DT;
+          const double(*Dnb)[3] = pr->D_face ? Dn_ : DN;
+          const double(*Dm)[3] = this_is_minus ? Dow : Dnb;
+          const double(*Dp)[3] = this_is_minus ? Dnb : Dow;
+          double dm = flux_along(nu, Dm, nu), dp = flux_along(nu, Dp, nu); /* delta = nu^T D nu */
+          double wm = dp / (dm + dp), wp = dm / (dm + dp);
+          double gam = harmonic(dm, dp) * pr->sigma * dF / cx->vol_T;
           double bnu = bfp ? bfp[p] : bdotn;
           double us, gs[3], un, gn[3];
           eval_fe(ft, p, zc, cx, &us, gs);
@@ -378,7 +403,7 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
           for (int i = 0; i < nb; ++i) {
             double gv[3];
             test_grad(ft, p, i, cx, gv);
-            double v = ph[i], dv = flux_along(nu, DT, gv); /* nu . D grad v on this cell */
+            double v = ph[i], dv = flux_along(nu, Dow, gv); /* nu . D grad v on this cell */
             /* jump and weighted average of the test function supported on this cell */
             double jump_v = this_is_minus ? v : -v;
             double avg_dv = this_is_minus ? wm * dv : wp * dv;
@@ -389,18 +414,21 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
         /* Dirichlet boundary face, outward normal sgn * nu */
         double sgn = side ? 1.0 : -1.0;
         double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};
-        double gam = flux_along(nout, DT, nout) * pr->sigma * dF / cx->vol_T;
         for (int p = 0; p < ft->np; ++p) {
+          double Db_[3][3];
+          if (pr->D_face) unpack6(pr->D_face + (((size_t)cell * 6 + 2 * dir + side) * ft->np + p) * 6, Db_);
+          const double(*DB)[3] = pr->D_face ? Db_ : DT;
+          double gam = flux_along(nout, DB, nout) * pr->sigma * dF / cx->vol_T;
           double bnu = sgn * (bfp ? bfp[p] : bdotn);
           double us, gs[3];
           eval_fe(ft, p, zc, cx, &us, gs);
-          double dnu = flux_along(nout, DT, gs);
+          double dnu = flux_along(nout, DB, gs);
           double dx = ft->wgt[p] * dF;
           const double* ph = ft->phi + (size_t)p * nb;
           for (int i = 0; i < nb; ++i) {
             double gv[3];
             test_grad(ft, p, i, cx, gv);
-            double v = ph[i], dnv = flux_along(nout, DT, gv);
+            double v = ph[i], dnv = flux_along(nout, DB, gv);
             y[i] += dx * (upwind(us, 0.0, bnu) * v - dnu * v - dnv * us + gam * us * v);
           }
         }
@@ -427,14 +455,21 @@ static int fill_problem(oracle_problem* pr, const int* n, const double* lo, cons
   pr->b_vol = 0;
   pr->b_face = 0;
   pr->Dten = 0;
+  pr->D_vol = 0;
+  pr->D_face = 0;
+  pr->c_vol = 0;
   pr->affine = 0;
   memset(pr->J, 0, sizeof(pr->J));
   return 0;
 }
 
 /* tensor diffusion and affine geometry options shared by the _ex entry points */
-static void set_general(oracle_problem* pr, const double* Dten, const double* Jmap) {
+static void set_general(oracle_problem* pr, const double* Dten, const double* Jmap, const double* D_vol,
+                        const double* D_face, const double* c_vol) {
   pr->Dten = Dten;
+  pr->D_vol = D_vol;
+  pr->D_face = D_face;
+  pr->c_vol = c_vol;
   if (Jmap) {
     pr->affine = 1;
     for (int a = 0; a < 3; ++a)
@@ -458,18 +493,20 @@ int oracle_apply(const int* n, const double* lo, const double* hi, int k, int m,
  *   b_vol [ncells][m^3][3] (NULL: constant b), b_face [ncells][6][m^2] = b . nu at each face point of each
  *   cell, nu the unit normal along +reference axis (NULL: constant b);
  *   Dten [ncells][6] = (xx, yy, zz, xy, xz, yz) (NULL: D_T * I from D);
- *   Jmap [9] row-major cell Jacobian, cells lo + J (ic + [0,1]^3) (NULL: the axis-parallel [lo, hi] grid).
+ *   Jmap [9] row-major cell Jacobian, cells lo + J (ic + [0,1]^3) (NULL: the axis-parallel [lo, hi] grid);
+ *   D_vol [ncells][m^3][6], D_face [ncells][6][m^2][6], c_vol [ncells][m^3]: coefficients at the quadrature
+ *   points (NULL: per cell / constant).
  * On a periodic axis the end faces couple the first and last cells. */
 int oracle_apply_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
                     double c, double sigma, const int* periodic, const double* b_vol, const double* b_face,
-                    const double* Dten, const double* Jmap, const double* u, double* y, const int* cells,
-                    int ncells_out) {
+                    const double* Dten, const double* Jmap, const double* D_vol, const double* D_face,
+                    const double* c_vol, const double* u, double* y, const int* cells, int ncells_out) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
   pr.b_vol = b_vol;
   pr.b_face = b_face;
-  set_general(&pr, Dten, Jmap);
+  set_general(&pr, Dten, Jmap, D_vol, D_face, c_vol);
   return apply_impl(&pr, u, y, cells, ncells_out);
 }
 
@@ -508,12 +545,13 @@ int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, c
  * coefficient and an affine geometry (arguments as in oracle_apply_ex). */
 int oracle_rhs_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
                   double c, double sigma, const int* periodic, const double* b_face, const double* Dten,
-                  const double* Jmap, const double* f_qp, const double* const* g_qp, double* F) {
+                  const double* Jmap, const double* D_face, const double* f_qp, const double* const* g_qp,
+                  double* F) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
   pr.b_face = b_face;
-  set_general(&pr, Dten, Jmap);
+  set_general(&pr, Dten, Jmap, 0, D_face, 0);
   return rhs_impl(&pr, f_qp, g_qp, F);
 }
 
@@ -551,8 +589,11 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
         double DT[3][3];
         diff_tensor(&pr, cell, DT);
         double dF = cx.area[dir];
-        double gam = flux_along(nout, DT, nout) * pr.sigma * dF / cx.vol_T;
         for (int p = 0; p < ft->np; ++p) {
+          double Db_[3][3];
+          if (pr.D_face) unpack6(pr.D_face + (((size_t)cell * 6 + s) * ft->np + p) * 6, Db_);
+          const double(*DB)[3] = pr.D_face ? Db_ : DT;
+          double gam = flux_along(nout, DB, nout) * pr.sigma * dF / cx.vol_T;
           double g = g_qp[s][(size_t)fidx * ft->np + p];
           double bnu = sgn * (bfp ? bfp[p] : bdotn);
           double dx = ft->wgt[p] * dF;
@@ -560,7 +601,7 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
           for (int i = 0; i < nb; ++i) {
             double gv[3];
             test_grad(ft, p, i, &cx, gv);
-            double v = ph[i], dnv = flux_along(nout, DT, gv);
+            double v = ph[i], dnv = flux_along(nout, DB, gv);
             y[i] += dx * (-upwind(0.0, g, bnu) * v - dnv * g + gam * g * v);
           }
         }

@@ -24,11 +24,11 @@ MUTANTS = [
     ("convection sign", "fl[r] = Dg[r] - br * uq;", "fl[r] = Dg[r] + br * uq;"),
     ("transposed basis index", "t->grad[o * 3 + 1] = v[0][j1] * d[1][j2] * v[2][j3];",
      "t->grad[o * 3 + 1] = v[0][j1] * d[1][j3] * v[2][j2];"),
-    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        double gam",
-     "double sgn = 1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        double gam"),
+    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        for",
+     "double sgn = 1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        for"),
     ("Gauss weight", "w[i] = 1.0 / ((1.0 - t * t) * dP[m] * dP[m]);", "w[i] = 2.0 / ((1.0 - t * t) * dP[m] * dP[m]);"),
     ("Dirichlet data sign in the right hand side", "- dnv * g + gam * g * v", "+ dnv * g + gam * g * v"),
-    ("reaction dropped", "pr->c * uq * ph[i]", "0.0 * pr->c * uq * ph[i]"),
+    ("reaction dropped", "cq * uq * ph[i]", "0.0 * cq * uq * ph[i]"),
     ("harmonic mean replaced by arithmetic mean", "return 2.0 * a * b / (a + b);", "return 0.5 * (a + b);"),
     ("face weight swapped", "double wm = dp / (dm + dp), wp = dm / (dm + dp);",
      "double wm = dm / (dm + dp), wp = dp / (dm + dp);"),
@@ -43,6 +43,10 @@ MUTANTS = [
     ("gradient mapped by J^-1 instead of J^-T", "g[a] += cx->Jinv[r][a] * gref[r];", "g[a] += cx->Jinv[a][r] * gref[r];"),
     ("face normal from J instead of J^-T", "cx->nrm[r][a] = cx->Jinv[r][a] / len;", "cx->nrm[r][a] = cx->J[a][r] / len;"),
     ("face area without the normal scale", "cx->area[r] = cx->vol_T * len;", "cx->area[r] = cx->vol_T;"),
+    ("neighbour's tensor from its far face", "unpack6(pr->D_face + (((size_t)nbr * 6 + oface) * ft->np + p) * 6, Dn_);",
+     "unpack6(pr->D_face + (((size_t)nbr * 6 + 2 * dir + side) * ft->np + p) * 6, Dn_);"),
+    ("point-wise reaction ignored", "const double cq = pr->c_vol ? pr->c_vol[(size_t)cell * cx->vol.np + p] : pr->c;",
+     "const double cq = pr->c;"),
 ]
 
 
@@ -64,6 +68,7 @@ def _pin_checks():
     yield lambda: xpins.test_tensor_diffusion_matches_kronecker_closed_form((2, 3, 2), 2, (0, 0, 0))
     yield lambda: xpins.test_linear_map_scales_the_operator_by_its_determinant(2)
     yield lambda: xpins.test_polynomial_solution_on_affine_mesh_has_zero_residual(2)
+    yield lambda: xpins.test_polynomial_solution_with_polynomial_coefficients_has_zero_residual(2)
 
 
 @pytest.mark.parametrize("name,orig,mutated", MUTANTS, ids=[m[0] for m in MUTANTS])
