@@ -117,9 +117,10 @@ int dg_destroy(dg_handle* h);
 /* Sizes of the handle's problem: number of cells, DOFs per cell, total DOFs. */
 int dg_sizes(const dg_handle* h, int64_t* ncells, int32_t* dofs_per_cell, int64_t* ndofs);
 
-/* Physical coordinates of the quadrature points, written to a host array:
- * which = 0: volume points [ncells][(k+1)^3][3]; which = 1+s: boundary side s
- * [faces][(k+1)^2][3].  Use them to sample f and g for dg_setup. */
+/* Physical coordinates of the quadrature points, written to a host array (m = k+1, or the handle's m):
+ * which = 0: volume points [ncells][m^3][3]; which = 1+s: boundary side s [faces][m^2][3]; which = 7:
+ * the points of all 6 faces of every cell [ncells][6][m^2][3] (face 2*dir+side, points as for
+ * dg_setup_ext.D_face).  Use them to sample f, g and point-wise coefficients for dg_setup_ex. */
 int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz_host);
 
 /* y = A z: matrix-free application of eq. blf by sum factorisation (Algorithm 1 of Sec. 3.6:
@@ -360,6 +361,20 @@ typedef struct {
                            the quadrature points follow the map.  NULL: the axis-parallel [lo, hi] grid.
                            With D_tensor or jacobian the tensor-diffusion kernels run (m = k+1, constant
                            velocity, degrees 1..8, DG_F64 and DG_F64X applies).                       */
+  /* Coefficients given at the quadrature points (Problem B of Sec. 5.1: affine cells and coefficients that
+     are polynomials in the coordinates, integrated with q = 2p+4, i.e. m = k+3).  The caller evaluates them
+     at the points of dg_quadrature_points (which = 0 for the volume, 7 for every cell's faces).  Given D_qp
+     and D_face, the point-wise kernels run: they replace coeffs->D_cell / D_const and D_tensor, work with
+     m = k+1 or k+3, a constant velocity or DG_VELOCITY_POINTS (b_face is then the normal velocity b . nu
+     along +reference axis dir, nu the unit normal), periodic axes and the jacobian, for degrees 1..8 and
+     DG_F64 / DG_F64X applies.  On an interior face the weights w+-, delta = nu^T D nu and the penalty are
+     formed point by point from both cells' D_face values at that point (Sec. 2, with readings 1-3 above). */
+  const double* D_qp;   /* host [ncells][m^3][6] (xx, yy, zz, xy, xz, yz): D at the volume points, every
+                           point symmetric positive definite; with D_face, or NULL                    */
+  const double* D_face; /* host [ncells][6][m^2][6]: D at the points of face 2*dir+side of each cell
+                           (points p = p_a + m*p_b over the tangential axes a < b)                    */
+  const double* c_qp;   /* host [ncells][m^3]: c at the volume points (point-wise kernels only), or NULL
+                           for coeffs->c                                                               */
 } dg_setup_ext;
 
 /* dg_setup with the options above (ext = NULL is dg_setup).  A field b(x) or m = k+3 selects the

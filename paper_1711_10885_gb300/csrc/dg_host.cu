@@ -150,6 +150,10 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->bface);
   cudaFree(h->bscX);
   cudaFree(h->bfaceX);
+  cudaFree(h->kq64);
+  cudaFree(h->kqX);
+  cudaFree(h->kf64);
+  cudaFree(h->kfX);
   cudaFree(h->rk_tmp);
   cudaFree(h->ws);
   if (h->ws_host) cudaFreeHost(h->ws_host);
@@ -229,8 +233,21 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     set_error("dg_setup: a velocity field or m = k+3 needs degree k <= 8");
     return DG_ERR_INVALID_ARG;
   }
-  const bool td = ext && (ext->D_tensor || ext->jacobian);
-  if (td && (vb || k > 8)) {
+  const bool pw = ext && (ext->D_qp || ext->D_face);
+  if (pw && (!ext->D_qp || !ext->D_face)) {
+    set_error("dg_setup: point-wise coefficients need both D_qp and D_face");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (pw && (k > 8 || velocity == DG_VELOCITY_TAYLOR_GREEN)) {
+    set_error("dg_setup: point-wise coefficients need degree k <= 8 and a constant or point-wise velocity");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (!pw && ext && ext->c_qp) {
+    set_error("dg_setup: c_qp needs the point-wise coefficients D_qp and D_face");
+    return DG_ERR_INVALID_ARG;
+  }
+  const bool td = ext && (ext->D_tensor || ext->jacobian || pw);
+  if (td && !pw && (vb || k > 8)) {
     set_error("dg_setup: a diffusion tensor or an affine geometry needs a constant velocity, m = k+1 and k <= 8");
     return DG_ERR_INVALID_ARG;
   }
@@ -254,8 +271,12 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     periodic[r] = ext ? ext->periodic[r] : 0;
   }
   std::vector<double> D(ncell);
-  const bool tensor_given = td && ext->D_tensor;
+  const bool tensor_given = td && ext->D_tensor && !pw;
   for (int64_t i = 0; i < ncell; ++i) {
+    if (pw) {
+      D[i] = 1.0;  // unused: the point tables carry the coefficients
+      continue;
+    }
     if (tensor_given) {
       // symmetric positive definite: positive leading principal minors (Sylvester's criterion)
       const double* t = ext->D_tensor + 6 * i;
@@ -299,6 +320,7 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
   h->M = M;
   h->vb = vb;
   h->td = td;
+  h->pw = pw;
   h->affine = td && ext->jacobian;
   for (int r = 0; r < 3; ++r) h->periodic[r] = periodic[r];
   // cell Jacobian: the affine map, or diag(h) for the axis-parallel grid
@@ -434,6 +456,17 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     }
     D.swap(K);
   }
+  std::vector<double> kq, kf, bface_pw;
+  if (pw) {
+    const int prc = build_pointwise_tables(h, ext->D_qp, ext->D_face, ext->c_qp, co->c, co->b,
+                                           velocity == DG_VELOCITY_POINTS ? ext->b_qp : nullptr,
+                                           velocity == DG_VELOCITY_POINTS ? ext->b_face : nullptr, kq, kf, fc,
+                                           bface_pw);
+    if (prc != DG_OK) {
+      delete h;
+      return prc;
+    }
+  }
   std::vector<float> D32(D.begin(), D.end()), fc32(fc.begin(), fc.end());
   std::vector<dgk::dfl> DX(D.size()), fcX(fc.size());
   for (size_t i = 0; i < D.size(); ++i) DX[i] = dgk::dfl(D[i]);
@@ -470,8 +503,27 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     DG_TRY(cudaMemcpyAsync(h->pX.D, DX.data(), nD * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s), "copy D pairs");
     DG_TRY(cudaMemcpyAsync(h->pX.fc, fcX.data(), nfc * sizeof(dgk::dfl), cudaMemcpyHostToDevice, s),
            "copy fc pairs");
+    if (pw) {
+      // point tables, FP64 and double-float (the face coefficients went with fc above)
+      const int64_t nkq = (int64_t)kq.size(), nkf = (int64_t)kf.size(), nbf = (int64_t)bface_pw.size();
+      DG_TRY(cudaMalloc(&h->kq64, nkq * sizeof(double)), "cudaMalloc(point table)");
+      DG_TRY(cudaMalloc(&h->kqX, nkq * sizeof(dgk::dfl)), "cudaMalloc(point table pairs)");
+      DG_TRY(cudaMalloc(&h->kf64, nkf * sizeof(double)), "cudaMalloc(face metric)");
+      DG_TRY(cudaMalloc(&h->kfX, nkf * sizeof(dgk::dfl)), "cudaMalloc(face metric pairs)");
+      DG_TRY(cudaMalloc(&h->bface, nbf * sizeof(double)), "cudaMalloc(normal velocity)");
+      DG_TRY(cudaMalloc(&h->bfaceX, nbf * sizeof(dgk::dfl)), "cudaMalloc(normal velocity pairs)");
+      DG_TRY(cudaMemcpyAsync(h->kq64, kq.data(), nkq * sizeof(double), cudaMemcpyHostToDevice, s), "copy kq");
+      DG_TRY(cudaMemcpyAsync(h->kf64, kf.data(), nkf * sizeof(double), cudaMemcpyHostToDevice, s), "copy kf");
+      DG_TRY(cudaMemcpyAsync(h->bface, bface_pw.data(), nbf * sizeof(double), cudaMemcpyHostToDevice, s),
+             "copy bface");
+      if ((rc = copy_to_pairs(static_cast<const double*>(h->kq64), h->kqX, nkq, s)) != DG_OK) goto fail;
+      if ((rc = copy_to_pairs(static_cast<const double*>(h->kf64), h->kfX, nkf, s)) != DG_OK) goto fail;
+      if ((rc = copy_to_pairs(static_cast<const double*>(h->bface), h->bfaceX, nbf, s)) != DG_OK) goto fail;
+      // the host tables must outlive the asynchronous copies
+      DG_TRY(cudaStreamSynchronize(s), "dg_setup synchronize");
+    }
     // velocity field tables (before the right hand side, whose inflow terms read b . nu)
-    if (vb) {
+    if (vb && !pw) {
       rc = setup_velocity(h, velocity, co->b, ext ? ext->b_qp : nullptr, ext ? ext->b_face : nullptr, s);
       if (rc != DG_OK) goto fail;
     }
@@ -517,7 +569,7 @@ fail:
 }
 
 int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
-  if (!h || !xyz || which < 0 || which > 6) {
+  if (!h || !xyz || which < 0 || which > 7) {
     set_error("dg_quadrature_points: bad arguments");
     return DG_ERR_INVALID_ARG;
   }
@@ -541,6 +593,26 @@ int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
                 map(xi, xyz + o);
                 o += 3;
               }
+    return DG_OK;
+  }
+  if (which == 7) {
+    // every face of every cell: face 2*dir+side at xi_dir = ic_dir + side, points (pa, pb) tangential
+    for (int64_t cell = 0; cell < h->ncell; ++cell) {
+      const int ic[3] = {(int)(cell % h->n[0]), (int)((cell / h->n[0]) % h->n[1]),
+                         (int)(cell / ((int64_t)h->n[0] * h->n[1]))};
+      for (int face = 0; face < 6; ++face) {
+        const int dir = face / 2, side = face % 2, ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+        for (int pb = 0; pb < N; ++pb)
+          for (int pa = 0; pa < N; ++pa) {
+            double xi[3];
+            xi[dir] = ic[dir] + side;
+            xi[ta] = ic[ta] + x[pa];
+            xi[tb] = ic[tb] + x[pb];
+            map(xi, xyz + o);
+            o += 3;
+          }
+      }
+    }
     return DG_OK;
   }
   const int sd = which - 1, dir = sd / 2, side = sd % 2;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/dg.h"
 
@@ -47,6 +48,15 @@ struct dg_handle {
   // ([ncell][6]) and Buffers::fc six coefficients per face; J is the cell Jacobian (diag(h) unless affine)
   bool td = false;
   bool affine = false;
+  // point-wise coefficients (pw, a td handle with Problem B's coefficients at the quadrature points):
+  // kq [ncell][10][M^3] = (K00, K11, K22, K01, K02, K12, beta_0..2, c |det J| w) at every volume point,
+  // kf [ncell][6][3][M^2] = row dir of K / |F_dir| at every face point, Buffers::fc [ncell][6][6][M^2] the
+  // face coefficients of every face point, bface the normal velocity; FP64 and double-float copies
+  bool pw = false;
+  void* kq64 = nullptr;
+  void* kqX = nullptr;
+  void* kf64 = nullptr;
+  void* kfX = nullptr;
   double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   double Jinv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   double detJ = 0;           // |det J| = |T|
@@ -114,5 +124,20 @@ int launch_apply_td(const dg_handle* h, const double* z, double* y, int mode, in
                     bool pairs, cudaStream_t s);
 int launch_rhs_td(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,
                   bool project);
+// point-wise coefficient kernels (h->pw): FP64 (dg_launch_pw.cu) and double-float (dg_launch_pwx.cu) operators
+int launch_apply_pw(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+                    cudaStream_t s);
+int launch_apply_pwx(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+                     cudaStream_t s);
+int launch_rhs_pw(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,
+                  bool project);
+// host tables of a pw handle (h->J, h->M, mesh, sigma set): kq, kf, fc and bface in the layouts above; the
+// velocity is b (constant) or b_qp [ncell][M^3][3] and b_face [ncell][6][M^2] (normal velocity) when given
+int build_pointwise_tables(const dg_handle* h, const double* D_qp, const double* D_face, const double* c_qp,
+                           double c_const, const double b[3], const double* b_qp, const double* b_face,
+                           std::vector<double>& kq, std::vector<double>& kf, std::vector<double>& fc,
+                           std::vector<double>& bface);
+// x[i] = pair of FP32 numbers closest to a[i] (double-float copies of the coefficient tables)
+int copy_to_pairs(const double* a, void* x_pairs, int64_t n, cudaStream_t s);
 
 }  // namespace dgi

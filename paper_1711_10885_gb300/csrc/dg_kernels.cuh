@@ -452,10 +452,18 @@ __device__ __forceinline__ void cell_tile(const TabNM<N, M, T>& tb, const Geo<T>
 // X_r = (K grad u)_r + beta_r u and the reaction; (3) three transposed passes sum B_r (w_perp X_r) into V.
 // The second trace slot of each face holds the physical conormal flux nu . D grad u = (K grad u)_r / |F_r|
 // (nu along +reference axis r), extrapolated from X_r.
-template <int N, typename T, int CPB, typename TV = T, int M = N>
+//
+// PW (coefficients given at the quadrature points, Problem B of Sec. 5.1): K, beta and c vary from point to
+// point.  Kc is then the point table [cell][10][M^3] of (K00, K11, K22, K01, K02, K12, beta_0, beta_1, beta_2,
+// c |det J| w) with the point index q = i1 + M (i2 + M i3) fastest, and Kf [cell][face][3][M^2] holds row r of
+// K at each face point divided by |F_r| (K from the tensor at the face point itself).  The conormal traces are
+// then sum_c Kf_c (grad u)_c with grad u extrapolated to the face along the normal lines; extrapolating X_r
+// instead would only be exact when K grad u is a polynomial of degree < M along the line.
+template <int N, typename T, int CPB, typename TV = T, int M = N, bool PW = false>
 __device__ __forceinline__ void cell_tile_td(const TabNM<N, M, T>& tb, const Geo<T>& g, const TV* __restrict__ z,
-                                             const T* __restrict__ Kc, T* __restrict__ Vout,
-                                             T* __restrict__ traces, int cell0, int here, unsigned char* smem_raw) {
+                                             const T* __restrict__ Kc, const T* __restrict__ Kf,
+                                             T* __restrict__ Vout, T* __restrict__ traces, int cell0, int here,
+                                             unsigned char* smem_raw) {
   constexpr int NN = M * M, CS = Lay<M>::CS, H = M / 2, C = (M + 1) / 2;
   T* sU = reinterpret_cast<T*>(smem_raw);  // u, then V
   T* sG = sU + CPB * CS;                    // [3][CPB][CS]: grad u, then X
@@ -510,9 +518,52 @@ __device__ __forceinline__ void cell_tile_td(const TabNM<N, M, T>& tb, const Geo
     }
   }
   __syncthreads();
-  // (2) pointwise: X_r = (K grad u)_r + beta_r u in place of grad u; V = c |det J| w u in place of u.
-  // Thread t handles the points of its z-line (a, b).
-  if (active) {
+  if constexpr (PW) {
+    // (1b) conormal traces nu . D grad u = sum_c Kf_c (grad u)_c at both faces of each normal line
+    if (active) {
+      const T* kf = Kf + (size_t)cell * 18 * NN + t;
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir) {
+        const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
+        T f0 = T(0), f1 = T(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T x[M], s[C], d[H > 0 ? H : 1];
+          load_line<M>(G[c], bs, st, x);
+          split_sd<M, T>(x, s, d);
+          T t1 = T(0), t2 = T(0);
+#pragma unroll
+          for (int l = 0; l < C; ++l) t1 = fma(tb.LS[l], s[l], t1);
+#pragma unroll
+          for (int l = 0; l < H; ++l) t2 = fma(tb.LD[l], d[l], t2);
+          f0 = fma(kf[((2 * dir) * 3 + c) * NN], t1 - t2, f0);
+          f1 = fma(kf[((2 * dir + 1) * 3 + c) * NN], t1 + t2, f1);
+        }
+        trc[(4 * dir + 1) * NN + t] = f0;
+        trc[(4 * dir + 3) * NN + t] = f1;
+      }
+    }
+    __syncthreads();
+    // (2) pointwise with the coefficients of each point (coalesced: consecutive t, consecutive points)
+    if (active) {
+      const int a = t % M, b = t / M;
+      const T* kq = Kc + (size_t)cell * 10 * M * NN + t;
+      constexpr int FS = M * NN;  // stride between the ten fields
+#pragma unroll 2
+      for (int l = 0; l < M; ++l) {
+        const int p = Lay<M>::idx(a, b, l);
+        const T* q = kq + l * NN;
+        const T u = U[p], g0 = G[0][p], g1 = G[1][p], g2 = G[2][p];
+        const T k0 = q[0], k1 = q[FS], k2 = q[2 * FS], k3 = q[3 * FS], k4 = q[4 * FS], k5 = q[5 * FS];
+        G[0][p] = fma(k0, g0, fma(k3, g1, fma(k4, g2, q[6 * FS] * u)));
+        G[1][p] = fma(k3, g0, fma(k1, g1, fma(k5, g2, q[7 * FS] * u)));
+        G[2][p] = fma(k4, g0, fma(k5, g1, fma(k2, g2, q[8 * FS] * u)));
+        U[p] = q[9 * FS] * u;
+      }
+    }
+  } else if (active) {
+    // (2) pointwise: X_r = (K grad u)_r + beta_r u in place of grad u; V = c |det J| w u in place of u.
+    // Thread t handles the points of its z-line (a, b).
     T k6[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) k6[q] = Kc[(size_t)cell * 6 + q];
@@ -540,13 +591,15 @@ __device__ __forceinline__ void cell_tile_td(const TabNM<N, M, T>& tb, const Geo
       load_line<M>(G[dir], bs, st, X);
       load_line<M>(U, bs, st, v);
       split_sd<M, T>(X, xs, xd);
-      T t1 = T(0), t2 = T(0);
+      if constexpr (!PW) {
+        T t1 = T(0), t2 = T(0);
 #pragma unroll
-      for (int l = 0; l < C; ++l) t1 = fma(tb.LS[l], xs[l], t1);
+        for (int l = 0; l < C; ++l) t1 = fma(tb.LS[l], xs[l], t1);
 #pragma unroll
-      for (int l = 0; l < H; ++l) t2 = fma(tb.LD[l], xd[l], t2);
-      trc[(4 * dir + 1) * NN + t] = (t1 - t2 - g.beta[dir] * ut[dir][0]) * g.inv_area[dir];
-      trc[(4 * dir + 3) * NN + t] = (t1 + t2 - g.beta[dir] * ut[dir][1]) * g.inv_area[dir];
+        for (int l = 0; l < H; ++l) t2 = fma(tb.LD[l], xd[l], t2);
+        trc[(4 * dir + 1) * NN + t] = (t1 - t2 - g.beta[dir] * ut[dir][0]) * g.inv_area[dir];
+        trc[(4 * dir + 3) * NN + t] = (t1 + t2 - g.beta[dir] * ut[dir][1]) * g.inv_area[dir];
+      }
 #pragma unroll
       for (int i = 0; i < C; ++i) xs[i] = wperp * xs[i];
 #pragma unroll
@@ -561,14 +614,15 @@ __device__ __forceinline__ void cell_tile_td(const TabNM<N, M, T>& tb, const Geo
   gstore_cells<M>(Vout, sU, cell0, here);
 }
 
-template <int N, typename T, int CPB, typename TV = T, int M = N>
+template <int N, typename T, int CPB, typename TV = T, int M = N, bool PW = false>
 __global__ void __launch_bounds__(CPB * M * M)
 dg_cell_kernel_td(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g,
-                  const TV* __restrict__ z, const T* __restrict__ Kc, T* __restrict__ Vout, T* __restrict__ traces) {
+                  const TV* __restrict__ z, const T* __restrict__ Kc, const T* __restrict__ Kf,
+                  T* __restrict__ Vout, T* __restrict__ traces) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, g.ncell - cell0);
-  cell_tile_td<N, T, CPB, TV, M>(tb, g, z, Kc, Vout, traces, cell0, here, smem_raw);
+  cell_tile_td<N, T, CPB, TV, M, PW>(tb, g, z, Kc, Kf, Vout, traces, cell0, here, smem_raw);
 }
 
 template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false>
@@ -612,7 +666,10 @@ struct FaceArgs {
 // kn, kt = w_own (K_rr, K_r,ta, K_r,tb) / |F_r| (boundary: w_own = 1, w_nbr = 0), the second trace is the
 // conormal flux nu . D grad u, and the test-function side -nu.{D grad v}_w also has tangential parts: Wt1,
 // Wt2 weight the reference derivatives of v along the lower and upper tangential axes at the face point.
-template <int N, typename T, bool SELF, typename TV, int M = N, bool VB = false, bool PER = false, bool TD = false>
+// PW (coefficients at the quadrature points): the six coefficients vary over the face points, stored as
+// fc[((cell*6 + face)*6 + q)*M^2 + t] (the weights and the penalty from both cells' tensors at the point).
+template <int N, typename T, bool SELF, typename TV, int M = N, bool VB = false, bool PER = false, bool TD = false,
+          bool PW = false>
 __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, TV>& fa, int cell, int tcell,
                                              const int (&ic)[3], int dir, int s, int t, T wf, T& Vf, T& Wf,
                                              T& Wt1, T& Wt2) {
@@ -620,8 +677,9 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
   const int face = 2 * dir + s;
   const bool at_end = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
   const bool boundary = at_end && !(PER && g.periodic[dir]);
-  const T* c3 = fa.fc + ((size_t)cell * 6 + face) * (TD ? 6 : 3);
-  const T kn = TD ? c3[3] : c3[0];  // coefficient of the normal reference derivative of v
+  const T* c3 = PW ? fa.fc + ((size_t)cell * 6 + face) * 6 * NN + t : fa.fc + ((size_t)cell * 6 + face) * (TD ? 6 : 3);
+  constexpr int CST = PW ? NN : 1;  // stride between the coefficients of one face point
+  const T kn = TD ? c3[3 * CST] : c3[0];  // coefficient of the normal reference derivative of v
   // the neighbour across this face (on a periodic axis the end faces wrap around to the other end)
   auto neighbour = [&]() {
     const int nstride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
@@ -652,11 +710,11 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
       const T sgn = s ? T(1) : T(-1);
       const T bnu = sgn * bq;
       const T phi = bnu >= T(0) ? T(0) : bnu * gv;
-      Vf = wf * (c3[2] * gv - phi);
+      Vf = wf * (c3[2 * CST] * gv - phi);
       Wf = -wf * sgn * kn * gv;
       if (TD) {
-        Wt1 = -wf * sgn * c3[4] * gv;
-        Wt2 = -wf * sgn * c3[5] * gv;
+        Wt1 = -wf * sgn * c3[4 * CST] * gv;
+        Wt2 = -wf * sgn * c3[5 * CST] * gv;
       }
     }
     return;
@@ -671,7 +729,7 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
       un = trn[t];
       dn = trn[NN + t];
     }
-    const T ao = c3[0], an = c3[1], gam = c3[2];
+    const T ao = c3[0], an = c3[1 * CST], gam = c3[2 * CST];
     // the own cell is T- for s = 1 and T+ for s = 0; nu = +e_dir
     const T um = s ? uo : un, up = s ? un : uo;
     const T jump = um - up;
@@ -681,8 +739,8 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
     Vf = s ? wf * H : -wf * H;                    // times [[v]] = +v (T-) or -v (T+)
     Wf = -wf * kn * jump;                         // -nu.{D grad v}_w [[u]]
     if (TD) {
-      Wt1 = -wf * c3[4] * jump;
-      Wt2 = -wf * c3[5] * jump;
+      Wt1 = -wf * c3[4 * CST] * jump;
+      Wt2 = -wf * c3[5 * CST] * jump;
     }
   } else {
     // Phi(u,0,b_nu) v - (nu.D grad u) v - (nu.D grad v) u + gamma u v, nu = outward normal
@@ -690,18 +748,18 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
     const T bnu = sgn * bq;
     const T phi = bnu >= T(0) ? bnu * uo : T(0);
     const T aD = c3[0];
-    Vf = wf * (phi - sgn * aD * dO + c3[2] * uo);
+    Vf = wf * (phi - sgn * aD * dO + c3[2 * CST] * uo);
     Wf = -wf * sgn * kn * uo;
     if (TD) {
-      Wt1 = -wf * sgn * c3[4] * uo;
-      Wt2 = -wf * sgn * c3[5] * uo;
+      Wt1 = -wf * sgn * c3[4 * CST] * uo;
+      Wt2 = -wf * sgn * c3[5 * CST] * uo;
     }
   }
 }
 
 // Face-kernel work on one tile of `here` consecutive cells starting at cell0 (see cell_tile).
 template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false, bool PER = false,
-          bool TD = false>
+          bool TD = false, bool PW = false>
 __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>& g, const FaceArgs<T, TV>& fa,
                                           int cell0, int here, int cell_base, unsigned char* smem_raw) {
   constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS;
@@ -739,8 +797,8 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         T Wt1, Wt2;
-        face_weights<N, T, SELF, TV, M, VB, PER, TD>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf[s], Wf[s], Wt1,
-                                                     Wt2);
+        face_weights<N, T, SELF, TV, M, VB, PER, TD, PW>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf[s], Wf[s], Wt1,
+                                                         Wt2);
         if (TD) {
           sW[((lc * 2 + s) * 2 + 0) * NN + t] = Wt1;
           sW[((lc * 2 + s) * 2 + 1) * NN + t] = Wt2;
@@ -825,14 +883,14 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
 }
 
 template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false,
-          bool PER = false, bool TD = false>
+          bool PER = false, bool TD = false, bool PW = false>
 __global__ void __launch_bounds__(CPB * M * M)
 dg_face_kernel(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g,
                const __grid_constant__ FaceArgs<T, TV> fa, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cell0 = blockIdx.x * CPB;
   const int here = min(CPB, (SELF ? sa_.nvirt : g.ncell) - cell0);
-  face_tile<N, T, SELF, CPB, TV, M, VB, PER, TD>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
+  face_tile<N, T, SELF, CPB, TV, M, VB, PER, TD, PW>(tb, g, fa, cell0, here, sa_.cell_base, smem_raw);
 }
 
 // The same kernel with 8 resident CTAs of 256 threads requested: used for FP32 when a CTA has 256 threads
@@ -848,12 +906,12 @@ dg_face_kernel_occ8(const __grid_constant__ TabNM<N, M, T> tb, const __grid_cons
 }
 
 // the face kernel of a launch configuration (the FP32 256-thread variant above, or the general one)
-template <int N, typename T, int CPB, typename TV, int M, bool VB, bool PER, bool TD = false>
+template <int N, typename T, int CPB, typename TV, int M, bool VB, bool PER, bool TD = false, bool PW = false>
 constexpr auto face_kernel_for() {
   if constexpr (std::is_same<T, float>::value && !VB && !TD && CPB * M * M == 256) {
     return &dg_face_kernel_occ8<N, T, CPB, TV, M, PER>;
   } else {
-    return &dg_face_kernel<N, T, false, CPB, TV, M, VB, PER, TD>;
+    return &dg_face_kernel<N, T, false, CPB, TV, M, VB, PER, TD, PW>;
   }
 }
 

@@ -357,7 +357,7 @@ int apply_td_n(const dg_handle* h, const double* z, double* y, int mode, int sta
   T* tr = static_cast<T*>(h->work_tr);
   if (mode != 2 && (stages & 1))
     dgk::dg_cell_kernel_td<N, T, CPB, double, N><<<grid, dgk::Launch<N>::THREADS, 2 * cell_smem<N, T>(), s>>>(
-        tb, geo, z, static_cast<const T*>(bf.D), V, tr);
+        tb, geo, z, static_cast<const T*>(bf.D), nullptr, V, tr);
   dgk::FaceArgs<T, double> fa;
   fa.V = mode == 2 ? reinterpret_cast<const T*>(z) : V;
   fa.traces = mode == 2 ? nullptr : tr;
@@ -387,6 +387,101 @@ int apply_td_n(const dg_handle* h, const double* z, double* y, int mode, int sta
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tensor-diffusion kernel launch");
   return 0;
+}
+
+}  // namespace dgi
+
+namespace dgi {
+
+// Point-wise coefficient kernels (Problem B of Sec. 5.1): the tensor-diffusion kernels with K, beta and c read
+// at every volume point and the face coefficients at every face point; M = N (q = 2p) or M = N + 2
+// (q = 2p+4); FP64 (T = double) or double-float (T = dfl) operator, FP64 vectors.
+template <int N, typename T, int M>
+int set_pw_smem_attrs() {
+  static bool done = false;
+  if (done) return 0;
+  constexpr int CPB = dgk::Launch<M>::CPB;
+  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel_td<N, T, CPB, double, M, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * cell_smem<M, T>()));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel_td pw)");
+  e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, double, M, true, true, true, true>(),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(face_smem<M, T>() + (size_t)CPB * 4 * M * M * sizeof(T)));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel pw)");
+  done = true;
+  return 0;
+}
+
+template <int N, typename T, int M>
+int apply_pw_nm(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+                const double* const g6[6], cudaStream_t s, bool project) {
+  if (int rc = set_pw_smem_attrs<N, T, M>()) return rc;
+  constexpr int CPB = dgk::Launch<M>::CPB;
+  const bool pair = std::is_same<T, dgk::dfl>::value;
+  const Buffers& bf = buffers_for<T>(h);
+  const auto tb = make_tab<N, T, M>(h->tab);
+  auto geo = geo_for<T, true>(h);  // normal velocity at the face points
+  const unsigned grid = (unsigned)((h->ncell + CPB - 1) / CPB);
+  T* V = static_cast<T*>(h->work_V);
+  T* tr = static_cast<T*>(h->work_tr);
+  if (mode != 2 && (stages & 1))
+    dgk::dg_cell_kernel_td<N, T, CPB, double, M, true><<<grid, dgk::Launch<M>::THREADS, 2 * cell_smem<M, T>(), s>>>(
+        tb, geo, z, static_cast<const T*>(pair ? h->kqX : h->kq64), static_cast<const T*>(pair ? h->kfX : h->kf64),
+        V, tr);
+  dgk::FaceArgs<T, double> fa;
+  fa.V = mode == 2 ? reinterpret_cast<const T*>(z) : V;
+  fa.traces = mode == 2 ? nullptr : tr;
+  fa.fc = static_cast<const T*>(bf.fc);
+  fa.F = (mode == 1 || mode == 3) ? static_cast<const T*>(bf.F) : nullptr;
+  for (int i = 0; i < 6; ++i) fa.g[i] = (mode == 2 && !project && g6) ? reinterpret_cast<const T*>(g6[i]) : nullptr;
+  fa.y = y;
+  fa.mode = mode;
+  fa.u = z;
+  fa.z0 = nullptr;
+  fa.cz = fa.cu = fa.cr = 0.0;
+  if (mode == 2 && project) geo.vol = T(1);
+  if (mode == 3) {
+    if (!st) {
+      set_error("Runge-Kutta stage without coefficients");
+      return DG_ERR_INVALID_ARG;
+    }
+    fa.z0 = st->z0;
+    fa.cz = st->cz;
+    fa.cu = st->cu;
+    fa.cr = st->cr;
+  }
+  if (stages & 2)
+    dgk::face_kernel_for<N, T, CPB, double, M, true, true, true, true>()
+        <<<grid, dgk::Launch<M>::THREADS, face_smem<M, T>() + (size_t)CPB * 4 * M * M * sizeof(T), s>>>(
+            tb, geo, fa, dgk::SelfArgs{0, 0});
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "point-wise coefficient kernel launch");
+  return 0;
+}
+
+template <int N, typename T>
+int apply_pw_n(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+               const double* const g6[6], cudaStream_t s, bool project) {
+  if (h->M == N) return apply_pw_nm<N, T, N>(h, z, y, mode, stages, st, g6, s, project);
+  if (h->M == N + 2) return apply_pw_nm<N, T, N + 2>(h, z, y, mode, stages, st, g6, s, project);
+  set_error("unsupported number of quadrature points");
+  return DG_ERR_INVALID_ARG;
+}
+
+template <typename T>
+int pw_dispatch(const dg_handle* h, const double* z, double* y, int mode, int stages, const StageArgs* st,
+                const double* const g6[6], cudaStream_t s, bool project) {
+  switch (h->N) {
+    case 2: return apply_pw_n<2, T>(h, z, y, mode, stages, st, g6, s, project);
+    case 3: return apply_pw_n<3, T>(h, z, y, mode, stages, st, g6, s, project);
+    case 4: return apply_pw_n<4, T>(h, z, y, mode, stages, st, g6, s, project);
+    case 5: return apply_pw_n<5, T>(h, z, y, mode, stages, st, g6, s, project);
+    case 6: return apply_pw_n<6, T>(h, z, y, mode, stages, st, g6, s, project);
+    case 7: return apply_pw_n<7, T>(h, z, y, mode, stages, st, g6, s, project);
+    case 8: return apply_pw_n<8, T>(h, z, y, mode, stages, st, g6, s, project);
+    case 9: return apply_pw_n<9, T>(h, z, y, mode, stages, st, g6, s, project);
+    default: set_error("point-wise coefficient kernels support degrees 1..8"); return DG_ERR_INVALID_ARG;
+  }
 }
 
 }  // namespace dgi

@@ -109,6 +109,12 @@ unsigned grid_for(int64_t n) {
 
 namespace dgi {
 
+int copy_to_pairs(const double* a, void* x_pairs, int64_t n, cudaStream_t s) {
+  to_pairs<<<grid_for(n), 256, 0, s>>>(a, static_cast<dgk::dfl*>(x_pairs), n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "to_pairs launch");
+}
+
 int setup_velocity(dg_handle* h, int kind, const double b[3], const double* b_qp, const double* b_face,
                    cudaStream_t s) {
   const int M = h->M;

@@ -52,7 +52,8 @@ _VELOCITY = {"constant": DG_VELOCITY_CONSTANT, "points": DG_VELOCITY_POINTS, "ta
 
 class dg_setup_ext(ctypes.Structure):
     _fields_ = [("periodic", ctypes.c_int32 * 3), ("m", ctypes.c_int32), ("velocity", ctypes.c_int32),
-                ("b_qp", _dp), ("b_face", _dp), ("D_tensor", _dp), ("jacobian", _dp)]
+                ("b_qp", _dp), ("b_face", _dp), ("D_tensor", _dp), ("jacobian", _dp), ("D_qp", _dp),
+                ("D_face", _dp), ("c_qp", _dp)]
 
 
 DG_SOLVE_FP64 = 0
@@ -193,11 +194,14 @@ class Operator:
     Transport options (dg_setup_ext): ``periodic`` flags per axis, ``m`` Gauss points per direction (k+1 or
     k+3), ``velocity`` "constant" (b), "points" (b_qp [ncell, m^3, 3] and b_face [ncell, 6, m^2]) or
     "taylor_green" (the flow field of Sec. 5.3, evaluated by the library); ``D_tensor`` [ncell, 6] per-cell
-    diffusion tensors and ``jacobian`` (3x3) affine cells lo + J (ic + [0,1]^3) (Sec. 5.1)."""
+    diffusion tensors and ``jacobian`` (3x3) affine cells lo + J (ic + [0,1]^3) (Sec. 5.1).  Problem B's
+    coefficients at the quadrature points: ``D_qp`` [ncell, m^3, 6] and ``D_face`` [ncell, 6, m^2, 6] (both, at
+    quadrature_points(0) and quadrature_points(7)), ``c_qp`` [ncell, m^3] optional."""
 
     def __init__(self, n, k, D=1.0, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), f_qp=None, g_qp=None, stream=None, periodic=(0, 0, 0), m=None,
-                 velocity="constant", b_qp=None, b_face=None, D_tensor=None, jacobian=None):
+                 velocity="constant", b_qp=None, b_face=None, D_tensor=None, jacobian=None, D_qp=None,
+                 D_face=None, c_qp=None):
         mesh = dg_mesh()
         for r in range(3):
             mesh.lo[r], mesh.hi[r], mesh.n[r] = float(lo[r]), float(hi[r]), int(n[r])
@@ -258,6 +262,11 @@ class Operator:
                 raise ValueError("jacobian must be 3x3")
             keep.append(jm)
             ext.jacobian = jm.ctypes.data_as(_dp)
+        for name, arr in (("D_qp", D_qp), ("D_face", D_face), ("c_qp", c_qp)):
+            if arr is not None:
+                a = _f64(arr).reshape(-1)
+                keep.append(a)
+                setattr(ext, name, a.ctypes.data_as(_dp))
         h = ctypes.c_void_p()
         check(lib.dg_setup_ex(ctypes.byref(mesh), int(k), ctypes.byref(co), bcp, fptr, ctypes.byref(ext),
                               _stream_ptr(stream), ctypes.byref(h)))
@@ -286,6 +295,8 @@ class Operator:
         m = self.m
         if which == 0:
             shape = (self.ncell, m ** 3, 3)
+        elif which == 7:
+            shape = (self.ncell, 6, m ** 2, 3)
         else:
             d = (which - 1) // 2
             ta, tb = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))

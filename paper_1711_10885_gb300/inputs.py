@@ -197,3 +197,68 @@ def log_normal_tensors(ncell: int, sigma: float, seed: int, anisotropy: float = 
     Q = Q * np.sign(np.diagonal(R, axis1=1, axis2=2))[:, None, :]
     M = np.einsum("cij,cj,ckj->cik", Q, lam, Q)
     return np.stack([M[:, 0, 0], M[:, 1, 1], M[:, 2, 2], M[:, 0, 1], M[:, 0, 2], M[:, 1, 2]], axis=1)
+
+
+def pack_sym(Mx: np.ndarray) -> np.ndarray:
+    """Symmetric 3x3 matrices [..., 3, 3] as (xx, yy, zz, xy, xz, yz) [..., 6], the layout of the tensor inputs."""
+    return np.stack([Mx[..., 0, 0], Mx[..., 1, 1], Mx[..., 2, 2], Mx[..., 0, 1], Mx[..., 0, 2], Mx[..., 1, 2]],
+                    axis=-1)
+
+
+class PolynomialFields:
+    """Seeded coefficients that are polynomials in the coordinates (Problem B of Sec. 5.1).
+
+    With s = (x - lo) / (hi - lo) the position normalised to the domain's bounding box:
+      D(x) = A(s) A(s)^T + d0 I,  A(s) = A0 + s_0 A1 + s_1 A2 + s_2 A3   (quadratic, symmetric positive definite),
+      b(x) = b0 + B1 s,   c(x) = c0 + c1 . s  (c0 > |c1|_1, so c > 0 on the box).
+    ``spread`` scales the random parts of A relative to the identity part.
+    """
+
+    def __init__(self, seed: int, lo, hi, spread: float = 0.4, d0: float = 0.2):
+        rng = np.random.default_rng(seed)
+        self.lo = np.asarray(lo, dtype=np.float64)
+        self.scale = 1.0 / (np.asarray(hi, dtype=np.float64) - self.lo)
+        self.A = np.concatenate([np.eye(3)[None] + spread * rng.uniform(-1, 1, (1, 3, 3)),
+                                 spread * rng.uniform(-1, 1, (3, 3, 3))])
+        self.d0 = d0
+        self.b0 = rng.uniform(-1, 1, 3)
+        self.B1 = rng.uniform(-0.5, 0.5, (3, 3))
+        self.c1 = rng.uniform(-0.3, 0.3, 3)
+        self.c0 = 1.0 + np.abs(self.c1).sum()
+
+    def _s(self, xyz):
+        return (np.asarray(xyz, dtype=np.float64) - self.lo) * self.scale
+
+    def D(self, xyz) -> np.ndarray:
+        """D at the points xyz [..., 3] as [..., 6] (pack_sym layout)."""
+        s = self._s(xyz)
+        A = self.A[0] + np.einsum("...k,kij->...ij", s, self.A[1:])
+        return pack_sym(np.einsum("...ik,...jk->...ij", A, A) + self.d0 * np.eye(3))
+
+    def b(self, xyz) -> np.ndarray:
+        return self.b0 + self._s(xyz) @ self.B1.T
+
+    def c(self, xyz) -> np.ndarray:
+        return self.c0 + self._s(xyz) @ self.c1
+
+
+def face_unit_normals(J) -> np.ndarray:
+    """Unit normals along +reference axis r of the cells lo + J (ic + [0,1]^3): the rows of J^{-1}, normalised
+    (the axis-parallel grid has J = diag(h) and e_r)."""
+    Ji = np.linalg.inv(np.asarray(J, dtype=np.float64).reshape(3, 3))
+    return Ji / np.linalg.norm(Ji, axis=1)[:, None]
+
+
+def face_normal_velocity_affine(bfun, face_xyz: np.ndarray, J) -> np.ndarray:
+    """b . nu at the points of every face of every cell, face_xyz [ncell, 6, m^2, 3] (face s = 2 dir + side, nu
+    the unit normal along +reference axis dir)."""
+    nrm = face_unit_normals(J)
+    return np.einsum("cspi,si->csp", bfun(face_xyz), np.repeat(nrm, 2, axis=0))
+
+
+def sheared_jacobian(h, seed: int = 0, shear: float = 0.25) -> np.ndarray:
+    """A seeded affine cell map J = (I + shear * U) diag(h), U with entries in [-1, 1] above the diagonal (an
+    invertible sheared version of the axis-parallel cell of size h)."""
+    rng = np.random.default_rng(seed)
+    U = np.triu(rng.uniform(-1, 1, (3, 3)), 1)
+    return (np.eye(3) + shear * U) @ np.diag(np.asarray(h, dtype=np.float64))
