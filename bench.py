@@ -244,6 +244,26 @@ def run_profile(args):
         print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
         op.close()
         return
+    if args.problem_b:
+        # Problem B (point-wise coefficients, k = 7, m = 10) on problem_b^3 sheared cells: W + K residual applies
+        import numpy as np
+        n, k = args.problem_b, 7
+        m = k + 3
+        J = inputs.sheared_jacobian(np.full(3, 1.0 / n), 70)
+        fields = inputs.PolynomialFields(70, np.zeros(3), J @ np.full(3, float(n)))
+        xv, xf = affine_grid_points((n, n, n), m, np.zeros(3), J)
+        op = dg.Operator((n, n, n), k, 1.0, b=(0.0, 0.0, 0.0), c=0.0, m=m, jacobian=J, D_qp=fields.D(xv),
+                         D_face=fields.D(xf), c_qp=fields.c(xv), velocity="points", b_qp=fields.b(xv),
+                         b_face=inputs.face_normal_velocity_affine(fields.b, xf, J), f_qp=np.ones(n ** 3 * m ** 3))
+        u = torch.tensor(inputs.uniform_u(op.ndof, 71), device="cuda")
+        r = torch.empty_like(u)
+        prec = dg.DG_F64X if args.precision == "f64x" else dg.DG_F64
+        for _ in range(args.warmup + args.steps):
+            op.apply_residual(u, r, precision=prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
+        op.close()
+        return
     if args.matrix:
         # matrix-based comparison: assemble on matrix_n^3 cells of degree matrix_k, then W + K products
         w = inputs.small_case(n=(args.matrix_n,) * 3, k=args.matrix_k, seed=200 + args.matrix_k)
@@ -384,6 +404,90 @@ def tensor_benchmark(reps=20):
                                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}
         out[name] = rec
         op.close()
+    return out
+
+
+def affine_grid_points(n, m, lo, J):
+    """Gauss points of the cells lo + J (ic + [0,1]^3): volume [ncell, m^3, 3] (point q = i1 + m (i2 + m i3)) and
+    every cell's faces [ncell, 6, m^2, 3] (face 2 dir + side, point pa + m pb over the tangential axes)."""
+    import numpy as np
+    xi = (np.polynomial.legendre.leggauss(m)[0] + 1.0) / 2.0
+    nx, ny, nz = n
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ic = np.stack([ix, iy, iz], axis=-1).reshape(-1, 3).astype(np.float64)
+    p3, p2, p1 = np.meshgrid(xi, xi, xi, indexing="ij")
+    pts = np.stack([p1, p2, p3], axis=-1).reshape(-1, 3)
+    J = np.asarray(J, dtype=np.float64)
+    vol = np.asarray(lo) + (ic[:, None, :] + pts[None, :, :]) @ J.T
+    pb, pa = np.meshgrid(xi, xi, indexing="ij")
+    face_ref = np.empty((6, m * m, 3))
+    for face in range(6):
+        d, side = face // 2, face % 2
+        ta, tb = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+        face_ref[face, :, d] = side
+        face_ref[face, :, ta] = pa.ravel()
+        face_ref[face, :, tb] = pb.ravel()
+    faces = np.asarray(lo) + (ic[:, None, None, :] + face_ref[None]) @ J.T
+    return vol, faces
+
+
+def problem_b_benchmark(reps=20, n=32, k=7, seed=70):
+    """Problem B of Sec. 5.1 on one GPU: n^3 sheared affine cells of the unit cube's image, Q_k, q = 2p+4
+    (m = k+3 Gauss points per direction), D(x) quadratic SPD, b(x) affine, c(x) affine (inputs.PolynomialFields,
+    seeded), f = 1, g = 0.  FP64 and double-float residual applications, per-kernel event times."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10885_gb300 import dg, flops, inputs
+    m, N = k + 3, k + 1
+    h = np.full(3, 1.0 / n)
+    J = inputs.sheared_jacobian(h, seed)
+    lo = np.zeros(3)
+    fields = inputs.PolynomialFields(seed, lo, J @ np.full(3, float(n)))
+    t0 = time.time()
+    xv, xf = affine_grid_points((n, n, n), m, lo, J)
+    kw = dict(D_qp=fields.D(xv), D_face=fields.D(xf), c_qp=fields.c(xv), velocity="points", b_qp=fields.b(xv),
+              b_face=inputs.face_normal_velocity_affine(fields.b, xf, J))
+    del xf
+    ncell = n ** 3
+    op = dg.Operator((n, n, n), k, 1.0, b=(0.0, 0.0, 0.0), c=0.0, m=m, jacobian=J, f_qp=np.ones(ncell * m ** 3),
+                     **kw)
+    setup_s = time.time() - t0
+    del kw, xv
+    u = torch.tensor(inputs.uniform_u(op.ndof, seed + 1), device="cuda")
+    r = torch.empty_like(u)
+    stream = torch.cuda.current_stream()
+    cell_fl = flops.cell_kernel_flops_pw(N, m) * ncell
+    face_fl = flops.face_kernel_flops_pw(N, m) * ncell
+    by = flops.bytes_per_cell_pw(N, m)
+    out = {"workload": f"problem_b_q{k}_{n}: {n}^3 sheared cells, k = {k}, m = {m}, polynomial D(x), b(x), c(x)",
+           "dofs": op.ndof, "setup_s": setup_s, "executed_flops_per_dof": (cell_fl + face_fl) / op.ndof,
+           "algorithmic_bytes_per_dof": (by["cell"] + by["face"]) / N ** 3,
+           "paper_problem_b_p7_mdofs_32_cores": 398.0}
+    hbm, hbm_src = hbm_peak_gbs()
+    for pname, prec in (("f64", dg.DG_F64), ("f64x", dg.DG_F64X)):
+        for _ in range(3):
+            op.apply_residual(u, r, precision=prec)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+        for i in range(reps):
+            ev[3 * i].record(stream)
+            op.apply_stage(0, u, r, residual=True, precision=prec)
+            ev[3 * i + 1].record(stream)
+            op.apply_stage(1, u, r, residual=True, precision=prec)
+            ev[3 * i + 2].record(stream)
+        torch.cuda.synchronize()
+        cms = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(reps)) / reps
+        fms = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(reps)) / reps
+        out[pname] = {"mdofs": op.ndof / ((cms + fms) * 1e-3) / 1e6,
+                      "kernels_ms": {"dg_cell_kernel_td<pw>": cms, "dg_face_kernel<td, pw>": fms},
+                      "fp64_equivalent_tflops": (cell_fl + face_fl) / ((cms + fms) * 1e-3) / 1e12,
+                      "algorithmic_gbs": {"cell": by["cell"] * ncell / (cms * 1e-3) / 1e9,
+                                          "face": by["face"] * ncell / (fms * 1e-3) / 1e9,
+                                          "peak": hbm, "peak_source": hbm_src}}
+    ach = cell_fl / (out["f64"]["kernels_ms"]["dg_cell_kernel_td<pw>"] * 1e-3) / 1e12
+    out["roofline_f64"] = {"bound": "alu", "kernel": f"dg_cell_kernel_td<{N}, double, M={m}, pw>", "achieved": ach,
+                           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}
+    op.close()
     return out
 
 
@@ -772,6 +876,8 @@ def run_ours(args):
         line["matrix_based"] = matrix_benchmark(degrees=(3, 7))
     if ws == 1 and not args.no_tensor:
         line["tensor_diffusion"] = tensor_benchmark()
+    if ws == 1 and not args.no_problem_b:
+        line["problem_b"] = problem_b_benchmark()
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -792,6 +898,10 @@ def main():
     ap.add_argument("--no-matrix", action="store_true", help="skip the matrix-based comparison section")
     ap.add_argument("--no-tensor", action="store_true", help="skip the tensor-diffusion / affine section")
     ap.add_argument("--tensor", action="store_true", help="print only the tensor-diffusion / affine section")
+    ap.add_argument("--no-problem-b", action="store_true", help="skip the Problem B (point-wise coefficients) section")
+    ap.add_argument("--problem-b", type=int, default=None, metavar="N",
+                    help="print only the Problem B section on N^3 cells (k = 7, m = 10); with --profile: only "
+                         "W + K residual applies of it")
     ap.add_argument("--matrix", action="store_true",
                     help="print only the matrix-free vs matrix-based comparison for k = 1, 3, 5, 7; with --profile: "
                          "assemble on --matrix-n^3 cells of degree --matrix-k and run W + K products")
@@ -823,6 +933,10 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"tensor_diffusion": tensor_benchmark()}), flush=True)
+    elif args.problem_b:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"problem_b": problem_b_benchmark(n=args.problem_b)}), flush=True)
     elif args.transport:
         import torch
         torch.cuda.set_device(0)

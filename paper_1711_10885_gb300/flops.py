@@ -100,6 +100,44 @@ def face_kernel_flops_td(N: int, residual: bool = True) -> float:
     return NN + lift + back + (N ** 3 if residual else 0)
 
 
+def cell_kernel_flops_pw(N: int, M: int | None = None) -> float:
+    """Executed FP operations per cell of dg_cell_kernel_td with coefficients at the quadrature points (Problem B):
+    modal passes N -> M, three derivative passes with value traces, the conormal traces from the three
+    gradient components extrapolated to both faces of each line, the point-wise flux (3 rows of 3 fma and a
+    beta mul, plus the reaction mul) and the three weighted transposed passes."""
+    M = M or N
+    H, C = _halves(M)
+    MM = M * M
+    fwd = (N * N + M * N + MM) * eo_fwd_flops(N, M)
+    deriv = 3 * MM * (2 * H + eo_anti_flops(M) + 2 * C + 2 * H + 2)
+    conormal = 3 * MM * 3 * (2 * H + 2 * C + 2 * H + 2 + 4)
+    pointwise = MM * M * 22
+    transposed = 3 * MM * (2 * H + 1 + M + eo_anti_flops(M) + M)
+    return fwd + deriv + conormal + pointwise + transposed
+
+
+def face_kernel_flops_pw(N: int, M: int | None = None, residual: bool = True) -> float:
+    """Executed FP operations per cell of the point-wise tensor face kernel (the tensor-diffusion face kernel on
+    M-point faces, contracted back to N modes)."""
+    M = M or N
+    MM = M * M
+    per_point = 11 + 4 + 4 * M
+    lift = 3 * MM * (1 + 2 * (per_point + 4 * M))
+    back = (MM + M * N + N * N) * eo_bwd_flops(N, M)
+    return MM + lift + back + (N ** 3 if residual else 0)
+
+
+def bytes_per_cell_pw(N: int, M: int, elt: int = 8, residual: bool = True) -> dict:
+    """Algorithmic DRAM bytes per cell of the point-wise coefficient kernels.  Cell kernel: read z, the ten
+    point fields (K, beta, c w) at M^3 points and the 3 conormal rows at 6 M^2 face points; write V and the
+    6 x 2 traces.  Face kernel: read V, the traces (once, as for the other kernels), the 6 face coefficients
+    at 6 M^2 points, the normal velocity (one value per interior face point, 3 M^2), write y (and read F)."""
+    n3, m3, mm = N ** 3, M ** 3, M * M
+    cell = elt * (n3 + 10 * m3 + 18 * mm + m3 + 12 * mm)
+    face = elt * (m3 + 12 * mm + 36 * mm + 3 * mm + n3 + (n3 if residual else 0))
+    return {"cell": cell, "face": face}
+
+
 def apply_flops_per_dof(k: int, n=(1, 1, 1), residual: bool = True) -> float:
     N = k + 1
     return (cell_kernel_flops(N) + face_kernel_flops(N, n, residual)) / N ** 3
