@@ -58,10 +58,10 @@ def _configure(lib):
     lib.oracle_rhs.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                ctypes.c_double, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_apply_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                    ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip,
+                                    ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip,
                                     ctypes.c_int]
     lib.oracle_rhs_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                  ctypes.c_double, _ip, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_dp), _dp]
+                                  ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_cell_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_volume_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
@@ -136,12 +136,15 @@ class Problem:
     ``penalty_sigma`` gives the two readings.  ``m`` defaults to k+1 Gauss points (q = 2p, Sec. 5.1).
     Options: ``periodic`` axes and a velocity field ``b_vol``/``b_face`` (Sec. 5.3); a per-cell diffusion
     tensor ``D_tensor`` [ncell, 6] = (xx, yy, zz, xy, xz, yz) (Sec. 5.1); an affine geometry ``J`` (3x3 cell
-    Jacobian, cells lo + J (ic + [0,1]^3); ``hi`` is then unused).
+    Jacobian, cells lo + J (ic + [0,1]^3); ``hi`` is then unused).  ``bc``: the boundary type of each side
+    2*dir + (0 lower | 1 upper), "dirichlet", "neumann" or "outflow" (eq. modelproblem: Gamma_D, Gamma_N,
+    Gamma_O); rhs() then reads g on Dirichlet sides and the total flux j = (b u - D grad u) . nu on Neumann
+    sides from its per-side arrays.
     """
 
     def __init__(self, n, k, D, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
                  m=None, periodic=(0, 0, 0), b_vol=None, b_face=None, D_tensor=None, J=None, D_vol=None,
-                 D_face=None, c_vol=None):
+                 D_face=None, c_vol=None, bc=None):
         self.n = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(3))
         self.lo = _arr(lo, 3)
         self.hi = _arr(hi, 3)
@@ -165,6 +168,10 @@ class Problem:
         self.D_vol = None if D_vol is None else _arr(D_vol, self.ncell * self.m ** 3 * 6)
         self.D_face = None if D_face is None else _arr(D_face, self.ncell * 6 * self.m ** 2 * 6)
         self.c_vol = None if c_vol is None else _arr(c_vol, self.ncell * self.m ** 3)
+        kinds = {"dirichlet": 0, "neumann": 1, "outflow": 2}
+        self.bc = np.ascontiguousarray(np.asarray([kinds[t] if isinstance(t, str) else int(t)
+                                                   for t in (bc if bc is not None else ["dirichlet"] * 6)],
+                                                  dtype=np.int32).reshape(6))
 
     def _general(self):
         return (_d(self.D_tensor) if self.D_tensor is not None else None, _d(self.J) if self.J is not None else None)
@@ -197,7 +204,7 @@ def penalty_sigma(k: int, mode: str = "baseline", alpha: float = 2.0, d: int = 3
 def apply(pr: Problem, u, cells=None) -> np.ndarray:
     """y = A u with (A u)_i = a_h(u, phi_i) (eq. blf); if ``cells`` is given only those cells' blocks."""
     u = _arr(u, pr.ndof)
-    ex = (pr.periodic.ctypes.data_as(_ip), _d(pr.b_vol) if pr.b_vol is not None else None,
+    ex = (pr.periodic.ctypes.data_as(_ip), pr.bc.ctypes.data_as(_ip), _d(pr.b_vol) if pr.b_vol is not None else None,
           _d(pr.b_face) if pr.b_face is not None else None, *pr._general(), *pr._pointwise())
     if cells is None:
         y = np.empty(pr.ndof)
@@ -212,7 +219,8 @@ def apply(pr: Problem, u, cells=None) -> np.ndarray:
 
 
 def rhs(pr: Problem, f_qp=None, g_qp=None) -> np.ndarray:
-    """F_i = l_h(phi_i) (Sec. 2): f at volume points [ncell, m^3]; g_qp: list of 6 side arrays or None."""
+    """F_i = l_h(phi_i) (Sec. 2): f at volume points [ncell, m^3]; g_qp: list of 6 side arrays (g on Dirichlet
+    sides, j on Neumann sides) or None."""
     F = np.empty(pr.ndof)
     fa = None if f_qp is None else _arr(f_qp, pr.ncell * pr.m ** 3)
     keep = []
@@ -226,7 +234,7 @@ def rhs(pr: Problem, f_qp=None, g_qp=None) -> np.ndarray:
                 a = _arr(g_qp[s])
                 keep.append(a)
                 garr[s] = _d(a)
-    rc = _load().oracle_rhs_ex(*pr._args(), pr.periodic.ctypes.data_as(_ip),
+    rc = _load().oracle_rhs_ex(*pr._args(), pr.periodic.ctypes.data_as(_ip), pr.bc.ctypes.data_as(_ip),
                                _d(pr.b_face) if pr.b_face is not None else None, *pr._general(),
                                pr._pointwise()[1], _d(fa) if fa is not None else None, garr, _d(F))
     if rc != 0:

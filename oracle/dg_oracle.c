@@ -42,8 +42,12 @@
  *  - penalty gamma_F = <delta-,delta+> * sigma * |F| / min(|T-|,|T+|) where the
  *    caller passes sigma (the paper's alpha*p*(p+d-1), or 2k(k+1));
  *    on boundary faces <delta-,delta+> -> delta- and min|T| -> |T-|;
- *  - every boundary face is Dirichlet; interior faces are oriented from the
- *    cell with the lower index along the face normal (T-) to the upper (T+);
+ *  - boundary faces are Dirichlet unless a side is declared Neumann (no term
+ *    in a_h, -(j, v) in l_h with the total flux j = (b u - D grad u) . nu) or
+ *    outflow (only the upwind flux Phi(u, 0, b_nu) in a_h, nothing in l_h), as
+ *    the face sets F^D, F^N, F^O of eq. blf and l_h split them; interior faces
+ *    are oriented from the cell with the lower index along the face normal (T-)
+ *    to the upper (T+);
  *  - upwind tie b_nu = 0 takes the u- branch (value 0 either way).
  *
  * Layouts (shared with the library only as a documented interface):
@@ -132,7 +136,11 @@ typedef struct {
   const double* D_vol;  /* NULL, or the tensor at the volume points [ncells][m^3][6]            */
   const double* D_face; /* NULL, or the tensor at each cell's face points [ncells][6][m^2][6]   */
   const double* c_vol;  /* NULL, or c at the volume points [ncells][m^3]                      */
+  int bc[6];            /* boundary type of side 2*dir + (0 lower | 1 upper): BC_DIRICHLET, BC_NEUMANN or
+                           BC_OUTFLOW (eq. modelproblem: Gamma_D, Gamma_N, Gamma_O)                     */
 } oracle_problem;
+
+enum { BC_DIRICHLET = 0, BC_NEUMANN = 1, BC_OUTFLOW = 2 };
 
 /* Full 3D tables at one set of points: phi[p*nb + J], grad[(p*nb + J)*3 + r]
  * are the reference-cube basis values and reference gradients. */
@@ -410,6 +418,19 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
             y[i] += dx * (phi_flux * jump_v - avg_flux * jump_v - avg_dv * jump_u + gam * jump_u * jump_v);
           }
         }
+      } else if (pr->bc[2 * dir + side] == BC_NEUMANN) {
+        /* Neumann face: eq. blf has no term on F^N; the prescribed total flux j enters l_h */
+      } else if (pr->bc[2 * dir + side] == BC_OUTFLOW) {
+        /* outflow face (F^O, (D grad u) . nu = 0): only the upwind convective flux Phi(u, 0, b_nu) */
+        double sgn = side ? 1.0 : -1.0;
+        for (int p = 0; p < ft->np; ++p) {
+          double bnu = sgn * (bfp ? bfp[p] : bdotn);
+          double us, gs[3];
+          eval_fe(ft, p, zc, cx, &us, gs);
+          double dx = ft->wgt[p] * dF;
+          const double* ph = ft->phi + (size_t)p * nb;
+          for (int i = 0; i < nb; ++i) y[i] += dx * upwind(us, 0.0, bnu) * ph[i];
+        }
       } else {
         /* Dirichlet boundary face, outward normal sgn * nu */
         double sgn = side ? 1.0 : -1.0;
@@ -458,8 +479,18 @@ static int fill_problem(oracle_problem* pr, const int* n, const double* lo, cons
   pr->D_vol = 0;
   pr->D_face = 0;
   pr->c_vol = 0;
+  for (int s = 0; s < 6; ++s) pr->bc[s] = BC_DIRICHLET;
   pr->affine = 0;
   memset(pr->J, 0, sizeof(pr->J));
+  return 0;
+}
+
+/* boundary types per side (bc == NULL: all Dirichlet); a periodic axis has no boundary sides */
+static int set_bc(oracle_problem* pr, const int* bc) {
+  for (int s = 0; s < 6; ++s) {
+    pr->bc[s] = bc ? bc[s] : BC_DIRICHLET;
+    if (pr->bc[s] < BC_DIRICHLET || pr->bc[s] > BC_OUTFLOW) return -1;
+  }
   return 0;
 }
 
@@ -498,12 +529,14 @@ int oracle_apply(const int* n, const double* lo, const double* hi, int k, int m,
  *   points (NULL: per cell / constant).
  * On a periodic axis the end faces couple the first and last cells. */
 int oracle_apply_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
-                    double c, double sigma, const int* periodic, const double* b_vol, const double* b_face,
-                    const double* Dten, const double* Jmap, const double* D_vol, const double* D_face,
-                    const double* c_vol, const double* u, double* y, const int* cells, int ncells_out) {
+                    double c, double sigma, const int* periodic, const int* bc, const double* b_vol,
+                    const double* b_face, const double* Dten, const double* Jmap, const double* D_vol,
+                    const double* D_face, const double* c_vol, const double* u, double* y, const int* cells,
+                    int ncells_out) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
+  if (set_bc(&pr, bc)) return -1;
   pr.b_vol = b_vol;
   pr.b_face = b_face;
   set_general(&pr, Dten, Jmap, D_vol, D_face, c_vol);
@@ -529,9 +562,10 @@ static int apply_impl(oracle_problem* pr_in, const double* u, double* y, const i
 }
 
 /* F_i = l_h(phi_i): (f, v)_T from f given at the volume quadrature points
- * (f_qp: [ncells][m^3], NULL means f = 0) plus the Dirichlet terms
+ * (f_qp: [ncells][m^3], NULL means f = 0) plus, on Dirichlet sides, the terms
  * -(Phi(0,g,b_nu), v)_F - (nu . D grad v, g)_F + gamma_F (g, v)_F from g given
- * at the boundary face points (g_qp[s]: side s array, NULL means g = 0). */
+ * at the boundary face points (g_qp[s]: side s array, NULL means g = 0), and on
+ * Neumann sides -(j, v)_F with j given in the same per-side array. */
 static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* const* g_qp, double* F);
 
 int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
@@ -544,12 +578,13 @@ int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, c
 /* oracle_rhs with periodic axes (no Dirichlet faces there), b . nu at the face points, a tensor diffusion
  * coefficient and an affine geometry (arguments as in oracle_apply_ex). */
 int oracle_rhs_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
-                  double c, double sigma, const int* periodic, const double* b_face, const double* Dten,
-                  const double* Jmap, const double* D_face, const double* f_qp, const double* const* g_qp,
-                  double* F) {
+                  double c, double sigma, const int* periodic, const int* bc, const double* b_face,
+                  const double* Dten, const double* Jmap, const double* D_face, const double* f_qp,
+                  const double* const* g_qp, double* F) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
+  if (set_bc(&pr, bc)) return -1;
   pr.b_face = b_face;
   set_general(&pr, Dten, Jmap, 0, D_face, 0);
   return rhs_impl(&pr, f_qp, g_qp, F);
@@ -589,6 +624,17 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
         double DT[3][3];
         diff_tensor(&pr, cell, DT);
         double dF = cx.area[dir];
+        if (pr.bc[s] == BC_OUTFLOW) continue; /* no outflow term in l_h */
+        if (pr.bc[s] == BC_NEUMANN) {
+          /* -(j, v)_F with the prescribed total flux j = (b u - D grad u) . nu_out at the face points */
+          for (int p = 0; p < ft->np; ++p) {
+            double jf = g_qp[s][(size_t)fidx * ft->np + p];
+            double dx = ft->wgt[p] * dF;
+            const double* ph = ft->phi + (size_t)p * nb;
+            for (int i = 0; i < nb; ++i) y[i] -= dx * jf * ph[i];
+          }
+          continue;
+        }
         for (int p = 0; p < ft->np; ++p) {
           double Db_[3][3];
           if (pr.D_face) unpack6(pr.D_face + (((size_t)cell * 6 + s) * ft->np + p) * 6, Db_);

@@ -50,10 +50,13 @@ def _embed(mat1d, q, n):
     return np.kron(mats[2], np.kron(mats[1], mats[0]))
 
 
-def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1), periodic=(0, 0, 0)):
+def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1), periodic=(0, 0, 0), bc=None):
     """Dense A with A[(T,I),(S,J)] = a_h(phi_{S,J}, phi_{T,I}) (row = test function).
 
-    On a periodic axis the face after the last cell couples it to the first cell (an interior face)."""
+    On a periodic axis the face after the last cell couples it to the first cell (an interior face).  bc: the
+    type of each boundary side 2*dir + (0 lower | 1 upper), 0 Dirichlet (default), 1 Neumann (no term in
+    a_h), 2 outflow (only the upwind flux Phi(u, 0, b_nu))."""
+    bc = [0] * 6 if bc is None else [{"dirichlet": 0, "neumann": 1, "outflow": 2}.get(t, t) for t in bc]
     n = tuple(int(v) for v in n)
     nb1 = k + 1
     nb = nb1 ** 3
@@ -128,8 +131,12 @@ def assemble(n, k, D, b, c, sigma, lo=(0, 0, 0), hi=(1, 1, 1), periodic=(0, 0, 0
                         ev = e1 if side else e0
                         dv = sgn * (d1 if side else d0) / hq  # nu . grad of the 1D factor
                         bnu = sgn * b[q]
-                        mat = (bnu * np.outer(ev, ev) if bnu >= 0 else 0.0) - DT * np.outer(ev, dv) \
-                            - DT * np.outer(dv, ev) + gam * np.outer(ev, ev)
+                        kind = bc[2 * q + side]
+                        if kind == 1:
+                            continue
+                        mat = bnu * np.outer(ev, ev) if bnu >= 0 else np.zeros((nb1, nb1))
+                        if kind == 0:
+                            mat = mat - DT * np.outer(ev, dv) - DT * np.outer(dv, ev) + gam * np.outer(ev, ev)
                         A[blk(T, T)] += area * _embed(mat, q, nb1)
     return A
 

@@ -11,6 +11,7 @@ import pytest
 import oracle
 from tests import test_oracle_pins as pins
 from tests import test_oracle_tensor_pins as xpins
+from tests import test_oracle_bc_pins as bpins
 from tests import test_oracle_transport_pins as tpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "dg_oracle.c")
@@ -47,6 +48,11 @@ MUTANTS = [
      "unpack6(pr->D_face + (((size_t)nbr * 6 + 2 * dir + side) * ft->np + p) * 6, Dn_);"),
     ("point-wise reaction ignored", "const double cq = pr->c_vol ? pr->c_vol[(size_t)cell * cx->vol.np + p] : pr->c;",
      "const double cq = pr->c;"),
+    ("Neumann flux sign in the right hand side", "y[i] -= dx * jf * ph[i];", "y[i] += dx * jf * ph[i];"),
+    ("outflow face without its upwind flux", "y[i] += dx * upwind(us, 0.0, bnu) * ph[i];",
+     "y[i] += 0.0 * dx * upwind(us, 0.0, bnu) * ph[i];"),
+    ("Neumann face given the Dirichlet terms", "} else if (pr->bc[2 * dir + side] == BC_NEUMANN) {",
+     "} else if (0) {"),
 ]
 
 
@@ -69,6 +75,9 @@ def _pin_checks():
     yield lambda: xpins.test_linear_map_scales_the_operator_by_its_determinant(2)
     yield lambda: xpins.test_polynomial_solution_on_affine_mesh_has_zero_residual(2)
     yield lambda: xpins.test_polynomial_solution_with_polynomial_coefficients_has_zero_residual(2)
+    yield lambda: bpins.test_mixed_boundary_types_match_kronecker_closed_form(bpins.BC_CASES[0])
+    yield lambda: bpins.test_polynomial_solution_with_mixed_boundary_types_has_zero_residual(2)
+    yield bpins.test_neumann_rhs_closed_form
 
 
 @pytest.mark.parametrize("name,orig,mutated", MUTANTS, ids=[m[0] for m in MUTANTS])
