@@ -29,8 +29,9 @@
  * weighted average {v}_w = w- v- + w+ v+; penalty
  *   gamma_F = <D-,D+> * sigma * |F| / min(|T-|,|T+|),  <a,b> = 2ab/(a+b),
  * with the caller's sigma (dg_penalty_sigma gives the two conventions);
- * boundary faces use D- and |T-|; all boundary faces are Dirichlet; interior
- * faces are oriented from the lower-index cell T- to T+ along the axis.
+ * boundary faces use D- and |T-|; boundary faces are Dirichlet unless
+ * dg_setup_ext.bc_type makes a side Neumann or outflow; interior faces are
+ * oriented from the lower-index cell T- to T+ along the axis.
  *
  * Ownership: the caller owns every vector it passes (device pointers for the
  * *_dev arguments, in layout above, 8-byte (FP64) or 4-byte (FP32) elements,
@@ -95,8 +96,10 @@ typedef struct {
   double sigma;
 } dg_coeffs;
 
-/* Dirichlet data g at the boundary face points: g_qp[s] is a host array of
- * (faces of side s) * (k+1)^2 values, or NULL for g = 0 on that side. */
+/* Boundary data at the boundary face points: g_qp[s] is a host array of
+ * (faces of side s) * m^2 values, or NULL for zero data on that side: the
+ * Dirichlet value g, or on a Neumann side (dg_setup_ext.bc_type) the total
+ * flux j = (b u - D grad u) . nu (nu the outer unit normal). */
 typedef struct {
   const double* g_qp[6];
 } dg_bc;
@@ -375,7 +378,14 @@ typedef struct {
                            (points p = p_a + m*p_b over the tangential axes a < b)                    */
   const double* c_qp;   /* host [ncells][m^3]: c at the volume points (point-wise kernels only), or NULL
                            for coeffs->c                                                               */
+  int32_t bc_type[6];   /* boundary type of side 2*dir+side (Sec. 2, eq. modelproblem; ignored on periodic
+                           axes): DG_BC_DIRICHLET (0, u = g), DG_BC_NEUMANN (total flux (b u - D grad u) . nu
+                           = j: no term in a_h, -(j, v) in l_h, j given in dg_bc.g_qp of that side), or
+                           DG_BC_OUTFLOW ((D grad u) . nu = 0: only the upwind flux Phi(u, 0, b . nu) in a_h,
+                           meant for sides with b . nu >= 0; nothing in l_h)                         */
 } dg_setup_ext;
+
+enum { DG_BC_DIRICHLET = 0, DG_BC_NEUMANN = 1, DG_BC_OUTFLOW = 2 };
 
 /* dg_setup with the options above (ext = NULL is dg_setup).  A field b(x) or m = k+3 selects the
  * velocity field kernels, which support degrees 1..8 and DG_F64 and DG_F64X applies (DG_F32 applies,

@@ -262,6 +262,14 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
         }
       }
   }
+  int bc_type[6] = {0, 0, 0, 0, 0, 0};
+  for (int f = 0; f < 6; ++f) {
+    bc_type[f] = ext ? ext->bc_type[f] : DG_BC_DIRICHLET;
+    if (bc_type[f] != DG_BC_DIRICHLET && bc_type[f] != DG_BC_NEUMANN && bc_type[f] != DG_BC_OUTFLOW) {
+      set_error("dg_setup: bc_type must be DG_BC_DIRICHLET, DG_BC_NEUMANN or DG_BC_OUTFLOW");
+      return DG_ERR_INVALID_ARG;
+    }
+  }
   int periodic[3] = {0, 0, 0};
   for (int r = 0; r < 3; ++r) {
     if (ext && ext->periodic[r] != 0 && ext->periodic[r] != 1) {
@@ -323,6 +331,7 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
   h->pw = pw;
   h->affine = td && ext->jacobian;
   for (int r = 0; r < 3; ++r) h->periodic[r] = periodic[r];
+  for (int f = 0; f < 6; ++f) h->bc_type[f] = periodic[f / 2] ? DG_BC_DIRICHLET : bc_type[f];
   // cell Jacobian: the affine map, or diag(h) for the axis-parallel grid
   for (int a = 0; a < 3; ++a)
     for (int r = 0; r < 3; ++r) h->J[a][r] = h->affine ? Jm[a][r] : (a == r ? h->h[r] : 0.0);
@@ -369,9 +378,12 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
         const bool at_end = side ? ic[dir] == h->n[dir] - 1 : ic[dir] == 0;
         const bool boundary = at_end && !h->periodic[dir];
         if (boundary) {
-          c3[0] = Do / hq;
-          c3[1] = 0.0;
-          c3[2] = Do * h->sigma / hq;  // delta- sigma |F| / |T-|
+          // Dirichlet: (D_own / h, upwind factor 1, delta- sigma |F| / |T-|); outflow: upwind flux only;
+          // Neumann: no term in a_h
+          const int bt = h->bc_type[2 * dir + side];
+          c3[0] = bt == DG_BC_DIRICHLET ? Do / hq : 0.0;
+          c3[1] = bt == DG_BC_NEUMANN ? 0.0 : 1.0;
+          c3[2] = bt == DG_BC_DIRICHLET ? Do * h->sigma / hq : 0.0;
         } else {
           // the neighbour; across the end faces of a periodic axis it is the cell at the other end
           const int64_t wrap = (int64_t)(h->n[dir] - 1) * strides[dir];
@@ -452,6 +464,13 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
           c6[3] = wo * ko / area;
           c6[4] = wo * Kat(cell, dir, ta) / area;
           c6[5] = wo * Kat(cell, dir, tb) / area;
+          if (boundary) {
+            // the second coefficient multiplies the upwind flux on a boundary face; outflow and Neumann faces
+            // have no diffusion or penalty term
+            const int bt = h->bc_type[2 * dir + side];
+            c6[1] = bt == DG_BC_NEUMANN ? 0.0 : 1.0;
+            if (bt != DG_BC_DIRICHLET) c6[0] = c6[2] = c6[3] = c6[4] = c6[5] = 0.0;
+          }
         }
     }
     D.swap(K);

@@ -36,6 +36,7 @@ struct dg_handle {
   int M = 0;                 // Gauss points per direction (N or N + 2)
   int n[3] = {0, 0, 0};
   int periodic[3] = {0, 0, 0};
+  int bc_type[6] = {0, 0, 0, 0, 0, 0};  // DG_BC_* per boundary side (0 = Dirichlet)
   // velocity field kernels (a field b(x) or M != N; FP64 only): pre-scaled volume velocity
   // [ncell][3][M][M^2] and normal velocity at the face points [ncell][6][M^2] (layouts of dgk::Geo)
   bool vb = false;

@@ -87,6 +87,7 @@ struct Geo {
   T b[3];      // velocity
   T creact;    // c |T|
   int periodic[3];  // 1: the two end faces along this axis are one interior face (Sec. 5.3)
+  int bc[6];        // boundary side 2*dir+side: 0 Dirichlet, 1 Neumann, 2 outflow (eq. modelproblem)
   // velocity field (VB kernels only, else null):
   //   bsc[((cell*3 + r)*M + l)*M^2 + t] = -b_r(x) |T| / h_r * w_a w_b at the point l of x-line/y-line/z-line t
   //     (t = a + M b over the two other point indices in increasing axis order)
@@ -677,6 +678,7 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
   const int face = 2 * dir + s;
   const bool at_end = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
   const bool boundary = at_end && !(PER && g.periodic[dir]);
+  const int btype = boundary ? g.bc[face] : 0;  // F^D, F^N or F^O of eq. blf
   const T* c3 = PW ? fa.fc + ((size_t)cell * 6 + face) * 6 * NN + t : fa.fc + ((size_t)cell * 6 + face) * (TD ? 6 : 3);
   constexpr int CST = PW ? NN : 1;  // stride between the coefficients of one face point
   const T kn = TD ? c3[3 * CST] : c3[0];  // coefficient of the normal reference derivative of v
@@ -701,12 +703,16 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
   Wt1 = T(0);
   Wt2 = T(0);
   if (fa.mode == 2) {
-    // -(Phi(0,g,b_nu), v) - (nu.D grad v, g) + gamma (g, v)
+    // Dirichlet: -(Phi(0,g,b_nu), v) - (nu.D grad v, g) + gamma (g, v); Neumann: -(j, v); outflow: nothing
     const T* gs = fa.g[face];
-    if (boundary && gs != nullptr) {
+    if (boundary && gs != nullptr && btype != 2) {
       const int ta = dir == 0 ? 1 : 0, tbx = dir == 2 ? 1 : 2;
       const int fidx = ic[ta] + g.n[ta] * ic[tbx];
       const T gv = gs[(size_t)fidx * NN + t];
+      if (btype == 1) {
+        Vf = -wf * gv;
+        return;
+      }
       const T sgn = s ? T(1) : T(-1);
       const T bnu = sgn * bq;
       const T phi = bnu >= T(0) ? T(0) : bnu * gv;
@@ -743,12 +749,14 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
       Wt2 = -wf * c3[5 * CST] * jump;
     }
   } else {
-    // Phi(u,0,b_nu) v - (nu.D grad u) v - (nu.D grad v) u + gamma u v, nu = outward normal
+    // Phi(u,0,b_nu) v - (nu.D grad u) v - (nu.D grad v) u + gamma u v, nu = outward normal.  The set-up encodes
+    // the side's type in the coefficients: the second one multiplies the upwind flux (1 on Dirichlet and
+    // outflow faces, 0 on Neumann faces); an outflow or Neumann face has zero diffusion and penalty ones.
     const T sgn = s ? T(1) : T(-1);
     const T bnu = sgn * bq;
     const T phi = bnu >= T(0) ? bnu * uo : T(0);
     const T aD = c3[0];
-    Vf = wf * (phi - sgn * aD * dO + c3[2 * CST] * uo);
+    Vf = wf * (c3[1 * CST] * phi - sgn * aD * dO + c3[2 * CST] * uo);
     Wf = -wf * sgn * kn * uo;
     if (TD) {
       Wt1 = -wf * sgn * c3[4 * CST] * uo;

@@ -79,6 +79,7 @@ dgk::Geo<T> make_geo(const dg_handle* h) {
   }
   g.ncell = (int)h->ncell;
   for (int r = 0; r < 3; ++r) g.periodic[r] = h->periodic[r];
+  for (int f = 0; f < 6; ++f) g.bc[f] = h->bc_type[f];
   g.bsc = nullptr;
   g.bface = nullptr;
   return g;

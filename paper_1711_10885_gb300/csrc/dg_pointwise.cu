@@ -135,6 +135,13 @@ int build_pointwise_tables(const dg_handle* h, const double* D_qp, const double*
           c6[3 * MM] = wo * Ko[dir][dir] / area;
           c6[4 * MM] = wo * Ko[dir][ta] / area;
           c6[5 * MM] = wo * Ko[dir][tb] / area;
+          if (boundary) {
+            // the second coefficient multiplies the upwind flux on a boundary face; outflow and Neumann faces
+            // have no diffusion or penalty term
+            const int bt = h->bc_type[face];
+            c6[1 * MM] = bt == DG_BC_NEUMANN ? 0.0 : 1.0;
+            if (bt != DG_BC_DIRICHLET) c6[0] = c6[2 * MM] = c6[3 * MM] = c6[4 * MM] = c6[5 * MM] = 0.0;
+          }
           for (int c = 0; c < 3; ++c) kf[(((size_t)cell * 6 + face) * 3 + c) * MM + p] = Ko[dir][c] / area;
           const size_t fi = ((size_t)cell * 6 + face) * MM + p;
           bface[fi] = b_face ? b_face[fi] : bnu;

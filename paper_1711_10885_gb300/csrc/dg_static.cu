@@ -37,7 +37,7 @@ int static_scratch(void** out) {
 }
 
 // Face coefficients of every cell, the same quantities dg_setup computes on the host:
-// interior (w_own D_own / h, w_nbr D_nbr / h, gamma_F), boundary (D_own / h, 0, gamma_F).
+// interior (w_own D_own / h, w_nbr D_nbr / h, gamma_F), Dirichlet boundary (D_own / h, 1, gamma_F).
 __global__ void static_face_coeffs(const double* __restrict__ D, int nx, int ny, int nz, double hx, double hy,
                                    double hz, double sigma, double* __restrict__ fc) {
   const int64_t ncell = (int64_t)nx * ny * nz;
@@ -55,7 +55,7 @@ __global__ void static_face_coeffs(const double* __restrict__ D, int nx, int ny,
         const bool boundary = side ? ic[dir] == n[dir] - 1 : ic[dir] == 0;
         if (boundary) {
           c3[0] = Do / hq;
-          c3[1] = 0.0;
+          c3[1] = 1.0;  // the upwind flux of a Dirichlet face
           c3[2] = Do * sigma / hq;
         } else {
           const double Dn = D[side ? cell + strides[dir] : cell - strides[dir]];

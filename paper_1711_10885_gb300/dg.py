@@ -44,6 +44,9 @@ class dg_bc(ctypes.Structure):
     _fields_ = [("g_qp", _dp * 6)]
 
 
+DG_BC_DIRICHLET = 0
+DG_BC_NEUMANN = 1
+DG_BC_OUTFLOW = 2
 DG_VELOCITY_CONSTANT = 0
 DG_VELOCITY_POINTS = 1
 DG_VELOCITY_TAYLOR_GREEN = 2
@@ -53,7 +56,7 @@ _VELOCITY = {"constant": DG_VELOCITY_CONSTANT, "points": DG_VELOCITY_POINTS, "ta
 class dg_setup_ext(ctypes.Structure):
     _fields_ = [("periodic", ctypes.c_int32 * 3), ("m", ctypes.c_int32), ("velocity", ctypes.c_int32),
                 ("b_qp", _dp), ("b_face", _dp), ("D_tensor", _dp), ("jacobian", _dp), ("D_qp", _dp),
-                ("D_face", _dp), ("c_qp", _dp)]
+                ("D_face", _dp), ("c_qp", _dp), ("bc_type", ctypes.c_int32 * 6)]
 
 
 DG_SOLVE_FP64 = 0
@@ -196,12 +199,14 @@ class Operator:
     "taylor_green" (the flow field of Sec. 5.3, evaluated by the library); ``D_tensor`` [ncell, 6] per-cell
     diffusion tensors and ``jacobian`` (3x3) affine cells lo + J (ic + [0,1]^3) (Sec. 5.1).  Problem B's
     coefficients at the quadrature points: ``D_qp`` [ncell, m^3, 6] and ``D_face`` [ncell, 6, m^2, 6] (both, at
-    quadrature_points(0) and quadrature_points(7)), ``c_qp`` [ncell, m^3] optional."""
+    quadrature_points(0) and quadrature_points(7)), ``c_qp`` [ncell, m^3] optional.  ``bc``: the type of each
+    boundary side 2*dir + side, "dirichlet" (default), "neumann" (g_qp then holds the total flux j) or
+    "outflow" (Sec. 2, eq. modelproblem)."""
 
     def __init__(self, n, k, D=1.0, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), f_qp=None, g_qp=None, stream=None, periodic=(0, 0, 0), m=None,
                  velocity="constant", b_qp=None, b_face=None, D_tensor=None, jacobian=None, D_qp=None,
-                 D_face=None, c_qp=None):
+                 D_face=None, c_qp=None, bc=None):
         mesh = dg_mesh()
         for r in range(3):
             mesh.lo[r], mesh.hi[r], mesh.n[r] = float(lo[r]), float(hi[r]), int(n[r])
@@ -225,15 +230,15 @@ class Operator:
         keep = []
         bcp = None
         if g_qp is not None:
-            bc = dg_bc()
+            bdata = dg_bc()
             for s in range(6):
                 if g_qp[s] is None:
-                    bc.g_qp[s] = _dp()
+                    bdata.g_qp[s] = _dp()
                 else:
                     a = _f64(g_qp[s]).reshape(-1)
                     keep.append(a)
-                    bc.g_qp[s] = a.ctypes.data_as(_dp)
-            bcp = ctypes.byref(bc)
+                    bdata.g_qp[s] = a.ctypes.data_as(_dp)
+            bcp = ctypes.byref(bdata)
         fptr = None
         if f_qp is not None:
             fa = _f64(f_qp).reshape(-1)
@@ -262,6 +267,10 @@ class Operator:
                 raise ValueError("jacobian must be 3x3")
             keep.append(jm)
             ext.jacobian = jm.ctypes.data_as(_dp)
+        if bc is not None:
+            kinds = {"dirichlet": DG_BC_DIRICHLET, "neumann": DG_BC_NEUMANN, "outflow": DG_BC_OUTFLOW}
+            for f in range(6):
+                ext.bc_type[f] = kinds[bc[f]] if isinstance(bc[f], str) else int(bc[f])
         for name, arr in (("D_qp", D_qp), ("D_face", D_face), ("c_qp", c_qp)):
             if arr is not None:
                 a = _f64(arr).reshape(-1)

@@ -138,3 +138,45 @@ def test_setup_ex_rejects_bad_tensors_and_jacobians_on_host():
                             ctypes.byref(h))
     assert rc == -1 and b"constant velocity" in dg.lib.dg_last_error()
     assert h.value is None
+
+
+def test_setup_ex_rejects_bad_boundary_types_on_host():
+    from paper_1711_10885_gb300 import dg
+    mesh = dg.dg_mesh()
+    for r in range(3):
+        mesh.lo[r], mesh.hi[r], mesh.n[r] = 0.0, 1.0, 2
+    co = dg.dg_coeffs()
+    co.D_const, co.c, co.sigma = 1.0, 0.0, 4.0
+    h = ctypes.c_void_p()
+    ext = dg.dg_setup_ext()
+    ext.bc_type[3] = 5
+    rc = dg.lib.dg_setup_ex(ctypes.byref(mesh), 2, ctypes.byref(co), None, None, ctypes.byref(ext), None,
+                            ctypes.byref(h))
+    assert rc == -1 and b"bc_type" in dg.lib.dg_last_error()
+    ext.bc_type[3] = dg.DG_BC_OUTFLOW
+    D = (ctypes.c_double * 6)(1.0, 1.0, 1.0, 0.0, 0.0, 0.0)
+    ext.D_qp = ctypes.cast(D, dg._dp)  # D_face missing
+    rc = dg.lib.dg_setup_ex(ctypes.byref(mesh), 2, ctypes.byref(co), None, None, ctypes.byref(ext), None,
+                            ctypes.byref(h))
+    assert rc == -1 and b"D_face" in dg.lib.dg_last_error()
+    assert h.value is None
+
+
+def test_operator_marshals_every_option():
+    """The binding turns every option into the C structs (on a machine without a GPU the call then fails in
+    CUDA, which the binding reports as DGError; a marshalling mistake would raise something else)."""
+    import numpy as np
+    from paper_1711_10885_gb300 import dg
+    n, k, m = (2, 1, 1), 1, 4
+    nc = 2
+    eye6 = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+    kw = dict(b=(0.5, 0.0, 0.0), c=0.3, m=m, periodic=(0, 1, 0), velocity="points",
+              b_qp=np.zeros((nc, m ** 3, 3)), b_face=np.zeros((nc, 6, m ** 2)), jacobian=np.eye(3) * 0.5,
+              D_qp=np.tile(eye6, (nc, m ** 3, 1)), D_face=np.tile(eye6, (nc, 6, m ** 2, 1)),
+              c_qp=np.ones((nc, m ** 3)), bc=("dirichlet", "outflow", "neumann", "neumann", 0, 2),
+              f_qp=np.ones(nc * m ** 3), g_qp=[np.zeros(m * m)] * 6, stream=0)
+    try:
+        op = dg.Operator(n, k, 1.0, **kw)
+    except dg.DGError:
+        return
+    op.close()  # a GPU was present: the handle was built
