@@ -38,8 +38,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
 # kernels as they were when profiled, keyed by the sha256 of the kernel source at that time.
 NCU_TRAFFIC = {
-    ("dg_cell_kernel", "8c1608fcf3d82c42"): 134540032 + 273837568,  # 134.54 MB read + 273.84 MB write
-    ("dg_face_kernel", "8c1608fcf3d82c42"): 474537472 + 113914880,  # 474.54 MB read + 113.91 MB write
+    ("dg_cell_kernel", "d895148003a8cd9d"): 134606336 + 271982592,  # 134.61 MB read + 271.98 MB write
+    ("dg_face_kernel", "d895148003a8cd9d"): 474576128 + 113232128,  # 474.58 MB read + 113.23 MB write
 }
 
 
