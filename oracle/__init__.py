@@ -58,14 +58,14 @@ def _configure(lib):
     lib.oracle_rhs.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                ctypes.c_double, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_apply_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                    ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip,
-                                    ctypes.c_int]
+                                    ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                    _ip, ctypes.c_int]
     lib.oracle_rhs_ex.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
-                                  ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_dp), _dp]
+                                  ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(_dp), _dp]
     lib.oracle_cell_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
-    lib.oracle_volume_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, _dp]
-    lib.oracle_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
-    lib.oracle_cell_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_int, _dp]
+    lib.oracle_volume_points_ex.argtypes = [_ip, _dp, _dp, _dp, _dp, ctypes.c_int, _dp]
+    lib.oracle_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    lib.oracle_cell_face_points_ex.argtypes = [_ip, _dp, _dp, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_volume_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp]
     lib.oracle_face_points.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
     return lib
@@ -139,12 +139,14 @@ class Problem:
     Jacobian, cells lo + J (ic + [0,1]^3); ``hi`` is then unused).  ``bc``: the boundary type of each side
     2*dir + (0 lower | 1 upper), "dirichlet", "neumann" or "outflow" (eq. modelproblem: Gamma_D, Gamma_N,
     Gamma_O); rhs() then reads g on Dirichlet sides and the total flux j = (b u - D grad u) . nu on Neumann
-    sides from its per-side arrays.
+    sides from its per-side arrays.  ``vertices`` [(n0+1)(n1+1)(n2+1), 3] (x fastest): multilinear cells,
+    each the trilinear image of [0,1]^3 through its 8 corner vertices (Problem C of Sec. 5.1); ``lo``, ``hi``
+    and ``J`` are then unused.
     """
 
     def __init__(self, n, k, D, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
                  m=None, periodic=(0, 0, 0), b_vol=None, b_face=None, D_tensor=None, J=None, D_vol=None,
-                 D_face=None, c_vol=None, bc=None):
+                 D_face=None, c_vol=None, bc=None, vertices=None):
         self.n = np.ascontiguousarray(np.asarray(n, dtype=np.int32).reshape(3))
         self.lo = _arr(lo, 3)
         self.hi = _arr(hi, 3)
@@ -168,13 +170,17 @@ class Problem:
         self.D_vol = None if D_vol is None else _arr(D_vol, self.ncell * self.m ** 3 * 6)
         self.D_face = None if D_face is None else _arr(D_face, self.ncell * 6 * self.m ** 2 * 6)
         self.c_vol = None if c_vol is None else _arr(c_vol, self.ncell * self.m ** 3)
+        # multilinear cells (Problem C): vertex coordinates [(n0+1)(n1+1)(n2+1), 3], x fastest
+        nv = int(np.prod(self.n + 1))
+        self.vertices = None if vertices is None else _arr(vertices, nv * 3)
         kinds = {"dirichlet": 0, "neumann": 1, "outflow": 2}
         self.bc = np.ascontiguousarray(np.asarray([kinds[t] if isinstance(t, str) else int(t)
                                                    for t in (bc if bc is not None else ["dirichlet"] * 6)],
                                                   dtype=np.int32).reshape(6))
 
     def _general(self):
-        return (_d(self.D_tensor) if self.D_tensor is not None else None, _d(self.J) if self.J is not None else None)
+        return (_d(self.D_tensor) if self.D_tensor is not None else None, _d(self.J) if self.J is not None else None,
+                _d(self.vertices) if self.vertices is not None else None)
 
     def _pointwise(self):
         return tuple(_d(a) if a is not None else None for a in (self.D_vol, self.D_face, self.c_vol))
@@ -250,8 +256,8 @@ def residual(pr: Problem, u, F) -> np.ndarray:
 def volume_points(pr: Problem) -> np.ndarray:
     """Physical coordinates [ncell, m^3, 3] of the volume quadrature points (oracle's own nodes)."""
     xyz = np.empty(pr.ncell * pr.m ** 3 * 3)
-    if _load().oracle_volume_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr._general()[1], pr.m,
-                                       _d(xyz)) != 0:
+    if _load().oracle_volume_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), *pr._general()[1:],
+                                       pr.m, _d(xyz)) != 0:
         raise RuntimeError("oracle_volume_points failed")
     return xyz.reshape(pr.ncell, pr.m ** 3, 3)
 
@@ -259,8 +265,8 @@ def volume_points(pr: Problem) -> np.ndarray:
 def cell_face_points(pr: Problem) -> np.ndarray:
     """Physical coordinates [ncell, 6, m^2, 3] of the face points of every face of every cell."""
     xyz = np.empty(pr.ncell * 6 * pr.m ** 2 * 3)
-    if _load().oracle_cell_face_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr._general()[1], pr.m,
-                                          _d(xyz)) != 0:
+    if _load().oracle_cell_face_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), *pr._general()[1:],
+                                          pr.m, _d(xyz)) != 0:
         raise RuntimeError("oracle_cell_face_points failed")
     return xyz.reshape(pr.ncell, 6, pr.m ** 2, 3)
 
@@ -271,7 +277,7 @@ def face_points(pr: Problem, s: int) -> np.ndarray:
     ta, tb = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
     nf = int(pr.n[ta] * pr.n[tb])
     xyz = np.empty(nf * pr.m ** 2 * 3)
-    if _load().oracle_face_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), pr._general()[1], pr.m, s,
-                                     _d(xyz)) != 0:
+    if _load().oracle_face_points_ex(pr.n.ctypes.data_as(_ip), _d(pr.lo), _d(pr.hi), *pr._general()[1:],
+                                     pr.m, s, _d(xyz)) != 0:
         raise RuntimeError("oracle_face_points failed")
     return xyz.reshape(nf, pr.m ** 2, 3)

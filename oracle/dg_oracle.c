@@ -32,11 +32,15 @@
  *    caller): D at the volume points and at each cell's face points, c at the
  *    volume points; on a face, delta, the weights and the penalty are then
  *    taken point by point from the two cells' tensors at that point;
- *  - geometry: axis-parallel cells, or an affine image of the structured grid
+ *  - geometry: axis-parallel cells, an affine image of the structured grid
  *    (every cell T = lo + J (ic + [0,1]^3) with one constant Jacobian J, as in
- *    Problem B of Sec. 5.1); gradients map as J^{-T}, |T| = |det J|, a face
- *    normal to reference axis r has nu = J^{-T} e_r / |J^{-T} e_r| and area
- *    |det J| |J^{-T} e_r|;
+ *    Problem B of Sec. 5.1), or multilinear cells (Problem C): each cell the
+ *    trilinear image of [0,1]^3 through its 8 corner vertices, J = J(x) taken
+ *    at every quadrature point; gradients map as J^{-T}, the volume element is
+ *    |det J|, a face across reference axis r has the unit normal
+ *    nu = J^{-T} e_r / |J^{-T} e_r| and the area element |det J| |J^{-T} e_r|;
+ *    the penalty's |F| and |T| are the face area and cell volume (integrals of
+ *    those elements by the same rule);
  *  - a periodic axis makes its two end faces interior faces between the last
  *    and the first cell (Sec. 5.1, 5.3);
  *  - penalty gamma_F = <delta-,delta+> * sigma * |F| / min(|T-|,|T+|) where the
@@ -138,6 +142,9 @@ typedef struct {
   const double* c_vol;  /* NULL, or c at the volume points [ncells][m^3]                      */
   int bc[6];            /* boundary type of side 2*dir + (0 lower | 1 upper): BC_DIRICHLET, BC_NEUMANN or
                            BC_OUTFLOW (eq. modelproblem: Gamma_D, Gamma_N, Gamma_O)                     */
+  const double* vertices; /* NULL, or multilinear cells (Problem C of Sec. 5.1): the grid's vertex coordinates
+                             [(n0+1)(n1+1)(n2+1)][3], vertex (i, j, l) at i + (n0+1)(j + (n1+1) l); cell (ix, iy,
+                             iz) is the trilinear image of [0,1]^3 through its 8 corner vertices            */
 } oracle_problem;
 
 enum { BC_DIRICHLET = 0, BC_NEUMANN = 1, BC_OUTFLOW = 2 };
@@ -149,12 +156,14 @@ typedef struct {
   double* phi;
   double* grad;
   double* wgt; /* quadrature weight per point (reference measure) */
+  double* xi;  /* local reference coordinates of each point in [0,1]^3, xi[p*3 + r] */
 } table3d;
 
 static void table_free(table3d* t) {
   free(t->phi);
   free(t->grad);
   free(t->wgt);
+  free(t->xi);
 }
 
 /* Points given by three per-axis coordinate lists; point p = a + na*(b + nb_*c)
@@ -166,7 +175,8 @@ static int table_build(int k, const double* ax[3], const double* aw[3], const in
   t->phi = (double*)malloc(sizeof(double) * t->np * t->nb);
   t->grad = (double*)malloc(sizeof(double) * t->np * t->nb * 3);
   t->wgt = (double*)malloc(sizeof(double) * t->np);
-  if (!t->phi || !t->grad || !t->wgt) return -1;
+  t->xi = (double*)malloc(sizeof(double) * t->np * 3);
+  if (!t->phi || !t->grad || !t->wgt || !t->xi) return -1;
   double v[3][66], d[3][66];
   for (int p2 = 0; p2 < na[2]; ++p2)
     for (int p1 = 0; p1 < na[1]; ++p1)
@@ -176,6 +186,9 @@ static int table_build(int k, const double* ax[3], const double* aw[3], const in
         oracle_basis_1d(k, ax[1][p1], v[1], d[1]);
         oracle_basis_1d(k, ax[2][p2], v[2], d[2]);
         t->wgt[p] = aw[0][p0] * aw[1][p1] * aw[2][p2];
+        t->xi[3 * p + 0] = ax[0][p0];
+        t->xi[3 * p + 1] = ax[1][p1];
+        t->xi[3 * p + 2] = ax[2][p2];
         for (int j3 = 0; j3 < n; ++j3)
           for (int j2 = 0; j2 < n; ++j2)
             for (int j1 = 0; j1 < n; ++j1) {
@@ -257,16 +270,22 @@ static void ctx_free(oracle_ctx* cx) {
   for (int s = 0; s < 6; ++s) table_free(&cx->face[s]);
 }
 
+/* Geometry of the cell map at one point (Sec. 3.2: gradients map with S = J^{-T}, volumes with Delta = |det J|) */
+typedef struct {
+  double Jinv[3][3];
+  double det; /* |det J| */
+} pgeo;
+
 /* physical gradient from a reference gradient: g = J^{-T} gref */
-static void phys_grad(const oracle_ctx* cx, const double gref[3], double g[3]) {
+static void phys_grad(const double Jinv[3][3], const double gref[3], double g[3]) {
   for (int a = 0; a < 3; ++a) {
     g[a] = 0.0;
-    for (int r = 0; r < 3; ++r) g[a] += cx->Jinv[r][a] * gref[r];
+    for (int r = 0; r < 3; ++r) g[a] += Jinv[r][a] * gref[r];
   }
 }
 
-/* u and physical gradient of the FE function with coefficients zc at point p of table t */
-static void eval_fe(const table3d* t, int p, const double* zc, const oracle_ctx* cx, double* u, double g[3]) {
+/* u and physical gradient of the FE function with coefficients zc at point p of table t (J^{-1} at the point) */
+static void eval_fe(const table3d* t, int p, const double* zc, const double Jinv[3][3], double* u, double g[3]) {
   double uu = 0, gr3[3] = {0, 0, 0};
   const double* ph = t->phi + (size_t)p * t->nb;
   const double* gr = t->grad + (size_t)p * t->nb * 3;
@@ -277,7 +296,7 @@ static void eval_fe(const table3d* t, int p, const double* zc, const oracle_ctx*
     gr3[2] += zc[J] * gr[3 * J + 2];
   }
   *u = uu;
-  phys_grad(cx, gr3, g);
+  phys_grad(Jinv, gr3, g);
 }
 
 /* a packed symmetric tensor (xx, yy, zz, xy, xz, yz) as a 3x3 matrix */
@@ -308,9 +327,9 @@ static double flux_along(const double nu[3], const double Dm[3][3], const double
 }
 
 /* physical gradient of test function i at point p of table t */
-static void test_grad(const table3d* t, int p, int i, const oracle_ctx* cx, double g[3]) {
+static void test_grad(const table3d* t, int p, int i, const double Jinv[3][3], double g[3]) {
   const double* gr = t->grad + ((size_t)p * t->nb + i) * 3;
-  phys_grad(cx, gr, g);
+  phys_grad(Jinv, gr, g);
 }
 
 static double upwind(double um, double up, double bnu) { return bnu >= 0.0 ? um * bnu : up * bnu; }
@@ -327,8 +346,91 @@ static int cell_index(const oracle_problem* pr, const int ic[3]) {
   return ic[0] + pr->n[0] * (ic[1] + pr->n[1] * ic[2]);
 }
 
+/* inverse and |determinant| of a 3x3 matrix, by cofactors */
+static void invert3(const double J[3][3], double Jinv[3][3], double* absdet) {
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  Jinv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  Jinv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  Jinv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  Jinv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  Jinv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  Jinv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  Jinv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  Jinv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  Jinv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  *absdet = fabs(det);
+}
+
+/* The cell map's geometry at the local reference point xi of a cell: the constant J of the axis-parallel or
+ * affine grid, or, for multilinear cells, the derivative of the trilinear map
+ *   x(xi) = sum over the corners (a, b, c) in {0,1}^3 of N_a(xi_0) N_b(xi_1) N_c(xi_2) X_abc,
+ *   N_0(t) = 1 - t, N_1(t) = t,  J[row][r] = d x_row / d xi_r. */
+static void point_geo(const oracle_problem* pr, const oracle_ctx* cx, int cell, const double xi[3], pgeo* g) {
+  if (!pr->vertices) {
+    memcpy(g->Jinv, cx->Jinv, sizeof(g->Jinv));
+    g->det = cx->vol_T;
+    return;
+  }
+  int ic[3];
+  cell_coords(pr, cell, ic);
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int corner[3] = {a, b, c};
+        double N[3], dN[3];
+        for (int r = 0; r < 3; ++r) {
+          N[r] = corner[r] ? xi[r] : 1.0 - xi[r];
+          dN[r] = corner[r] ? 1.0 : -1.0;
+        }
+        const double d[3] = {dN[0] * N[1] * N[2], N[0] * dN[1] * N[2], N[0] * N[1] * dN[2]};
+        const size_t v = (size_t)(ic[0] + a) + (size_t)(pr->n[0] + 1) * ((ic[1] + b) + (size_t)(pr->n[1] + 1) * (ic[2] + c));
+        const double* X = pr->vertices + 3 * v;
+        for (int row = 0; row < 3; ++row)
+          for (int r = 0; r < 3; ++r) J[row][r] += X[row] * d[r];
+      }
+  invert3(J, g->Jinv, &g->det);
+}
+
+/* unit normal nu along +reference axis r at a point of a face across r, and the face's area element
+ * |det J| |J^{-T} e_r| there (J^{-T} e_r is row r of J^{-1}) */
+static double face_normal(const pgeo* g, int r, double nu[3]) {
+  const double len = sqrt(g->Jinv[r][0] * g->Jinv[r][0] + g->Jinv[r][1] * g->Jinv[r][1] + g->Jinv[r][2] * g->Jinv[r][2]);
+  for (int a = 0; a < 3; ++a) nu[a] = g->Jinv[r][a] / len;
+  return g->det * len;
+}
+
+/* |T|: the cell's volume by the volume rule (exact for multilinear cells: |det J| has degree 2 per direction) */
+static double cell_volume(const oracle_problem* pr, const oracle_ctx* cx, int cell) {
+  if (!pr->vertices) return cx->vol_T;
+  double v = 0.0;
+  for (int p = 0; p < cx->vol.np; ++p) {
+    pgeo g;
+    point_geo(pr, cx, cell, cx->vol.xi + 3 * p, &g);
+    v += cx->vol.wgt[p] * g.det;
+  }
+  return v;
+}
+
+/* |F|: the area of face s = 2*dir + side of a cell, by the face rule */
+static double face_area(const oracle_problem* pr, const oracle_ctx* cx, int cell, int s) {
+  if (!pr->vertices) return cx->area[s / 2];
+  const table3d* ft = &cx->face[s];
+  double a = 0.0;
+  for (int p = 0; p < ft->np; ++p) {
+    pgeo g;
+    double nu[3];
+    point_geo(pr, cx, cell, ft->xi + 3 * p, &g);
+    a += ft->wgt[p] * face_normal(&g, s / 2, nu);
+  }
+  return a;
+}
+
 /* a_h(u, phi_i) for all test functions phi_i supported on one cell: the
- * cell's volume term plus every face of the cell (eq. blf). */
+ * cell's volume term plus every face of the cell (eq. blf).  Gradients, normals,
+ * area and volume elements are taken at each quadrature point from the cell
+ * map (constant for the axis-parallel and affine grids). */
 static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const double* u, int cell, double* y) {
   const int nb = cx->vol.nb;
   const double* zc = u + (size_t)cell * nb;
@@ -338,9 +440,11 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
 
   /* volume: (D grad u - b u, grad v)_T + (c u, v)_T */
   for (int p = 0; p < cx->vol.np; ++p) {
+    pgeo G;
+    point_geo(pr, cx, cell, cx->vol.xi + 3 * p, &G);
     double uq, g[3];
-    eval_fe(&cx->vol, p, zc, cx, &uq, g);
-    double dx = cx->vol.wgt[p] * cx->vol_T; /* Delta_T * w_i */
+    eval_fe(&cx->vol, p, zc, G.Jinv, &uq, g);
+    double dx = cx->vol.wgt[p] * G.det; /* Delta_T * w_i */
     double Dp_[3][3];
     if (pr->D_vol) unpack6(pr->D_vol + ((size_t)cell * cx->vol.np + p) * 6, Dp_);
     const double(*Dq)[3] = pr->D_vol ? Dp_ : DT;   /* D at this point */
@@ -354,13 +458,14 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
     const double* ph = cx->vol.phi + (size_t)p * nb;
     for (int i = 0; i < nb; ++i) {
       double gv[3];
-      test_grad(&cx->vol, p, i, cx, gv);
+      test_grad(&cx->vol, p, i, G.Jinv, gv);
       y[i] += dx * (fl[0] * gv[0] + fl[1] * gv[1] + fl[2] * gv[2] + cq * uq * ph[i]);
     }
   }
 
   int ic[3];
   cell_coords(pr, cell, ic);
+  const double volT = cell_volume(pr, cx, cell);
   for (int dir = 0; dir < 3; ++dir)
     for (int side = 0; side < 2; ++side) {
       const table3d* ft = &cx->face[2 * dir + side]; /* this cell's trace at the face */
@@ -368,9 +473,7 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
       nic[dir] += side ? 1 : -1;
       if (pr->periodic[dir]) nic[dir] = (nic[dir] + pr->n[dir]) % pr->n[dir];
       int interior = nic[dir] >= 0 && nic[dir] < pr->n[dir];
-      double dF = cx->area[dir];
-      const double* nu = cx->nrm[dir]; /* unit normal pointing along +reference axis dir */
-      const double bdotn = pr->b[0] * nu[0] + pr->b[1] * nu[1] + pr->b[2] * nu[2];
+      const double areaF = face_area(pr, cx, cell, 2 * dir + side); /* |F| of the penalty */
       /* normal velocity b . nu at face point p of this face */
       const double* bfp = pr->b_face ? pr->b_face + ((size_t)cell * 6 + 2 * dir + side) * ft->np : 0;
       if (interior) {
@@ -381,8 +484,16 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
         int this_is_minus = side == 1;
         double DN[3][3];
         diff_tensor(pr, nbr, DN);
+        const double volN = cell_volume(pr, cx, nbr);
+        const double vmin = volT < volN ? volT : volN; /* min(|T-|, |T+|) */
         const int oface = 2 * dir + (1 - side); /* the same face seen from the neighbour */
         for (int p = 0; p < ft->np; ++p) {
+          pgeo Go, Gn;
+          point_geo(pr, cx, cell, ft->xi + 3 * p, &Go);
+          point_geo(pr, cx, nbr, nt->xi + 3 * p, &Gn);
+          double nu[3]; /* unit normal pointing along +reference axis dir */
+          const double dA = face_normal(&Go, dir, nu);
+          const double bdotn = pr->b[0] * nu[0] + pr->b[1] * nu[1] + pr->b[2] * nu[2];
           /* the two cells' tensors at this face point (constant per cell unless given point-wise) */
           double Do_[3][3], Dn_[3][3];
           if (pr->D_face) {
@@ -395,22 +506,22 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
           const double(*Dp)[3] = this_is_minus ? Dnb : Dow;
           double dm = flux_along(nu, Dm, nu), dp = flux_along(nu, Dp, nu); /* delta = nu^T D nu */
           double wm = dp / (dm + dp), wp = dm / (dm + dp);
-          double gam = harmonic(dm, dp) * pr->sigma * dF / cx->vol_T;
+          double gam = harmonic(dm, dp) * pr->sigma * areaF / vmin;
           double bnu = bfp ? bfp[p] : bdotn;
           double us, gs[3], un, gn[3];
-          eval_fe(ft, p, zc, cx, &us, gs);
-          eval_fe(nt, p, zn, cx, &un, gn);
+          eval_fe(ft, p, zc, Go.Jinv, &us, gs);
+          eval_fe(nt, p, zn, Gn.Jinv, &un, gn);
           double um = this_is_minus ? us : un, up = this_is_minus ? un : us;
           double dnum = flux_along(nu, Dm, this_is_minus ? gs : gn); /* nu . D- grad u- */
           double dnup = flux_along(nu, Dp, this_is_minus ? gn : gs);
           double jump_u = um - up;
           double avg_flux = wm * dnum + wp * dnup; /* nu . {D grad u}_w */
           double phi_flux = upwind(um, up, bnu);
-          double dx = ft->wgt[p] * dF;
+          double dx = ft->wgt[p] * dA;
           const double* ph = ft->phi + (size_t)p * nb;
           for (int i = 0; i < nb; ++i) {
             double gv[3];
-            test_grad(ft, p, i, cx, gv);
+            test_grad(ft, p, i, Go.Jinv, gv);
             double v = ph[i], dv = flux_along(nu, Dow, gv); /* nu . D grad v on this cell */
             /* jump and weighted average of the test function supported on this cell */
             double jump_v = this_is_minus ? v : -v;
@@ -424,31 +535,41 @@ static void apply_cell(const oracle_problem* pr, const oracle_ctx* cx, const dou
         /* outflow face (F^O, (D grad u) . nu = 0): only the upwind convective flux Phi(u, 0, b_nu) */
         double sgn = side ? 1.0 : -1.0;
         for (int p = 0; p < ft->np; ++p) {
+          pgeo Go;
+          point_geo(pr, cx, cell, ft->xi + 3 * p, &Go);
+          double nu[3];
+          const double dA = face_normal(&Go, dir, nu);
+          const double bdotn = pr->b[0] * nu[0] + pr->b[1] * nu[1] + pr->b[2] * nu[2];
           double bnu = sgn * (bfp ? bfp[p] : bdotn);
           double us, gs[3];
-          eval_fe(ft, p, zc, cx, &us, gs);
-          double dx = ft->wgt[p] * dF;
+          eval_fe(ft, p, zc, Go.Jinv, &us, gs);
+          double dx = ft->wgt[p] * dA;
           const double* ph = ft->phi + (size_t)p * nb;
           for (int i = 0; i < nb; ++i) y[i] += dx * upwind(us, 0.0, bnu) * ph[i];
         }
       } else {
         /* Dirichlet boundary face, outward normal sgn * nu */
         double sgn = side ? 1.0 : -1.0;
-        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};
         for (int p = 0; p < ft->np; ++p) {
+          pgeo Go;
+          point_geo(pr, cx, cell, ft->xi + 3 * p, &Go);
+          double nu[3];
+          const double dA = face_normal(&Go, dir, nu);
+          const double bdotn = pr->b[0] * nu[0] + pr->b[1] * nu[1] + pr->b[2] * nu[2];
+          double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};
           double Db_[3][3];
           if (pr->D_face) unpack6(pr->D_face + (((size_t)cell * 6 + 2 * dir + side) * ft->np + p) * 6, Db_);
           const double(*DB)[3] = pr->D_face ? Db_ : DT;
-          double gam = flux_along(nout, DB, nout) * pr->sigma * dF / cx->vol_T;
+          double gam = flux_along(nout, DB, nout) * pr->sigma * areaF / volT;
           double bnu = sgn * (bfp ? bfp[p] : bdotn);
           double us, gs[3];
-          eval_fe(ft, p, zc, cx, &us, gs);
+          eval_fe(ft, p, zc, Go.Jinv, &us, gs);
           double dnu = flux_along(nout, DB, gs);
-          double dx = ft->wgt[p] * dF;
+          double dx = ft->wgt[p] * dA;
           const double* ph = ft->phi + (size_t)p * nb;
           for (int i = 0; i < nb; ++i) {
             double gv[3];
-            test_grad(ft, p, i, cx, gv);
+            test_grad(ft, p, i, Go.Jinv, gv);
             double v = ph[i], dnv = flux_along(nout, DB, gv);
             y[i] += dx * (upwind(us, 0.0, bnu) * v - dnu * v - dnv * us + gam * us * v);
           }
@@ -480,6 +601,7 @@ static int fill_problem(oracle_problem* pr, const int* n, const double* lo, cons
   pr->D_face = 0;
   pr->c_vol = 0;
   for (int s = 0; s < 6; ++s) pr->bc[s] = BC_DIRICHLET;
+  pr->vertices = 0;
   pr->affine = 0;
   memset(pr->J, 0, sizeof(pr->J));
   return 0;
@@ -530,9 +652,9 @@ int oracle_apply(const int* n, const double* lo, const double* hi, int k, int m,
  * On a periodic axis the end faces couple the first and last cells. */
 int oracle_apply_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
                     double c, double sigma, const int* periodic, const int* bc, const double* b_vol,
-                    const double* b_face, const double* Dten, const double* Jmap, const double* D_vol,
-                    const double* D_face, const double* c_vol, const double* u, double* y, const int* cells,
-                    int ncells_out) {
+                    const double* b_face, const double* Dten, const double* Jmap, const double* verts,
+                    const double* D_vol, const double* D_face, const double* c_vol, const double* u, double* y,
+                    const int* cells, int ncells_out) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
@@ -540,6 +662,7 @@ int oracle_apply_ex(const int* n, const double* lo, const double* hi, int k, int
   pr.b_vol = b_vol;
   pr.b_face = b_face;
   set_general(&pr, Dten, Jmap, D_vol, D_face, c_vol);
+  pr.vertices = verts;
   return apply_impl(&pr, u, y, cells, ncells_out);
 }
 
@@ -579,14 +702,15 @@ int oracle_rhs(const int* n, const double* lo, const double* hi, int k, int m, c
  * coefficient and an affine geometry (arguments as in oracle_apply_ex). */
 int oracle_rhs_ex(const int* n, const double* lo, const double* hi, int k, int m, const double* D, const double* b,
                   double c, double sigma, const int* periodic, const int* bc, const double* b_face,
-                  const double* Dten, const double* Jmap, const double* D_face, const double* f_qp,
-                  const double* const* g_qp, double* F) {
+                  const double* Dten, const double* Jmap, const double* verts, const double* D_face,
+                  const double* f_qp, const double* const* g_qp, double* F) {
   oracle_problem pr;
   if (fill_problem(&pr, n, lo, hi, k, m, D, b, c, sigma)) return -1;
   for (int r = 0; r < 3; ++r) pr.periodic[r] = periodic ? periodic[r] != 0 : 0;
   if (set_bc(&pr, bc)) return -1;
   pr.b_face = b_face;
   set_general(&pr, Dten, Jmap, 0, D_face, 0);
+  pr.vertices = verts;
   return rhs_impl(&pr, f_qp, g_qp, F);
 }
 
@@ -600,7 +724,9 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
     for (int i = 0; i < nb; ++i) y[i] = 0.0;
     if (f_qp) {
       for (int p = 0; p < npv; ++p) {
-        double fx = f_qp[(size_t)cell * npv + p] * cx.vol.wgt[p] * cx.vol_T;
+        pgeo G;
+        point_geo(&pr, &cx, cell, cx.vol.xi + 3 * p, &G);
+        double fx = f_qp[(size_t)cell * npv + p] * cx.vol.wgt[p] * G.det;
         const double* ph = cx.vol.phi + (size_t)p * nb;
         for (int i = 0; i < nb; ++i) y[i] += fx * ph[i];
       }
@@ -612,41 +738,40 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
         int s = 2 * dir + side;
         int on_boundary = side ? ic[dir] == pr.n[dir] - 1 : ic[dir] == 0;
         if (pr.periodic[dir] || !on_boundary || !g_qp || !g_qp[s]) continue;
+        if (pr.bc[s] == BC_OUTFLOW) continue; /* no outflow term in l_h */
         /* face index within the boundary layer: tangential cell indices, lower axis fastest */
         int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
         int fidx = ic[ta] + pr.n[ta] * ic[tb];
         const table3d* ft = &cx.face[s];
         double sgn = side ? 1.0 : -1.0;
-        const double* nu = cx.nrm[dir];
-        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};
-        const double bdotn = pr.b[0] * nu[0] + pr.b[1] * nu[1] + pr.b[2] * nu[2];
         const double* bfp = pr.b_face ? pr.b_face + ((size_t)cell * 6 + s) * ft->np : 0;
         double DT[3][3];
         diff_tensor(&pr, cell, DT);
-        double dF = cx.area[dir];
-        if (pr.bc[s] == BC_OUTFLOW) continue; /* no outflow term in l_h */
-        if (pr.bc[s] == BC_NEUMANN) {
-          /* -(j, v)_F with the prescribed total flux j = (b u - D grad u) . nu_out at the face points */
-          for (int p = 0; p < ft->np; ++p) {
-            double jf = g_qp[s][(size_t)fidx * ft->np + p];
-            double dx = ft->wgt[p] * dF;
-            const double* ph = ft->phi + (size_t)p * nb;
-            for (int i = 0; i < nb; ++i) y[i] -= dx * jf * ph[i];
-          }
-          continue;
-        }
+        const double areaF = face_area(&pr, &cx, cell, s), volT = cell_volume(&pr, &cx, cell);
         for (int p = 0; p < ft->np; ++p) {
+          pgeo Go;
+          point_geo(&pr, &cx, cell, ft->xi + 3 * p, &Go);
+          double nu[3];
+          const double dA = face_normal(&Go, dir, nu);
+          double dx = ft->wgt[p] * dA;
+          const double* ph = ft->phi + (size_t)p * nb;
+          if (pr.bc[s] == BC_NEUMANN) {
+            /* -(j, v)_F with the prescribed total flux j = (b u - D grad u) . nu_out at the face points */
+            double jf = g_qp[s][(size_t)fidx * ft->np + p];
+            for (int i = 0; i < nb; ++i) y[i] -= dx * jf * ph[i];
+            continue;
+          }
+          double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};
+          const double bdotn = pr.b[0] * nu[0] + pr.b[1] * nu[1] + pr.b[2] * nu[2];
           double Db_[3][3];
           if (pr.D_face) unpack6(pr.D_face + (((size_t)cell * 6 + s) * ft->np + p) * 6, Db_);
           const double(*DB)[3] = pr.D_face ? Db_ : DT;
-          double gam = flux_along(nout, DB, nout) * pr.sigma * dF / cx.vol_T;
+          double gam = flux_along(nout, DB, nout) * pr.sigma * areaF / volT;
           double g = g_qp[s][(size_t)fidx * ft->np + p];
           double bnu = sgn * (bfp ? bfp[p] : bdotn);
-          double dx = ft->wgt[p] * dF;
-          const double* ph = ft->phi + (size_t)p * nb;
           for (int i = 0; i < nb; ++i) {
             double gv[3];
-            test_grad(ft, p, i, &cx, gv);
+            test_grad(ft, p, i, Go.Jinv, gv);
             double v = ph[i], dnv = flux_along(nout, DB, gv);
             y[i] += dx * (-upwind(0.0, g, bnu) * v - dnv * g + gam * g * v);
           }
@@ -658,9 +783,29 @@ static int rhs_impl(oracle_problem* pr_in, const double* f_qp, const double* con
 }
 
 /* x = lo + J xi for a point xi of the structured reference grid (xi_r = cell index + local coordinate);
- * J = diag((hi - lo) / n) without an affine map */
-static void map_point(const int* n, const double* lo, const double* hi, const double* Jmap, const double xi[3],
-                      double* out) {
+ * J = diag((hi - lo) / n) without an affine map; with vertices, the trilinear map of the cell that holds xi
+ * (a point on a face between two cells is mapped by the lower one; both give the same point) */
+static void map_point_v(const int* n, const double* lo, const double* hi, const double* Jmap, const double* verts,
+                        const double xi[3], double* out) {
+  if (verts) {
+    int ic[3];
+    double t[3];
+    for (int r = 0; r < 3; ++r) {
+      ic[r] = (int)floor(xi[r]);
+      if (ic[r] > n[r] - 1) ic[r] = n[r] - 1;
+      if (ic[r] < 0) ic[r] = 0;
+      t[r] = xi[r] - ic[r];
+    }
+    for (int a = 0; a < 3; ++a) out[a] = 0.0;
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          const double N = (a ? t[0] : 1.0 - t[0]) * (b ? t[1] : 1.0 - t[1]) * (c ? t[2] : 1.0 - t[2]);
+          const size_t v = (size_t)(ic[0] + a) + (size_t)(n[0] + 1) * ((ic[1] + b) + (size_t)(n[1] + 1) * (ic[2] + c));
+          for (int r = 0; r < 3; ++r) out[r] += N * verts[3 * v + r];
+        }
+    return;
+  }
   for (int a = 0; a < 3; ++a) {
     if (Jmap) {
       out[a] = lo[a] + Jmap[3 * a] * xi[0] + Jmap[3 * a + 1] * xi[1] + Jmap[3 * a + 2] * xi[2];
@@ -671,8 +816,8 @@ static void map_point(const int* n, const double* lo, const double* hi, const do
 }
 
 /* Physical coordinates of the volume quadrature points: xyz[(cell*m^3 + q)*3 + r]. */
-int oracle_volume_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap, int m,
-                            double* xyz) {
+int oracle_volume_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap,
+                            const double* verts, int m, double* xyz) {
   double* x = (double*)malloc(sizeof(double) * m);
   double* w = (double*)malloc(sizeof(double) * m);
   if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
@@ -684,7 +829,7 @@ int oracle_volume_points_ex(const int* n, const double* lo, const double* hi, co
           for (int i2 = 0; i2 < m; ++i2)
             for (int i1 = 0; i1 < m; ++i1) {
               const double xi[3] = {ix + x[i1], iy + x[i2], iz + x[i3]};
-              map_point(n, lo, hi, Jmap, xi, xyz + o);
+              map_point_v(n, lo, hi, Jmap, verts, xi, xyz + o);
               o += 3;
             }
   free(x);
@@ -693,13 +838,13 @@ int oracle_volume_points_ex(const int* n, const double* lo, const double* hi, co
 }
 
 int oracle_volume_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
-  return oracle_volume_points_ex(n, lo, hi, 0, m, xyz);
+  return oracle_volume_points_ex(n, lo, hi, 0, 0, m, xyz);
 }
 
 /* Physical coordinates of the boundary face points of side s = 2*dir + side:
  * xyz[(face*m^2 + p)*3 + r], faces and points ordered as documented above. */
-int oracle_face_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap, int m, int s,
-                          double* xyz) {
+int oracle_face_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap,
+                          const double* verts, int m, int s, double* xyz) {
   if (s < 0 || s > 5) return -1;
   double* x = (double*)malloc(sizeof(double) * m);
   double* w = (double*)malloc(sizeof(double) * m);
@@ -715,7 +860,7 @@ int oracle_face_points_ex(const int* n, const double* lo, const double* hi, cons
           xi[dir] = side ? n[dir] : 0;
           xi[ta] = ca + x[pa];
           xi[tb] = cb + x[pb];
-          map_point(n, lo, hi, Jmap, xi, xyz + o);
+          map_point_v(n, lo, hi, Jmap, verts, xi, xyz + o);
           o += 3;
         }
   free(x);
@@ -724,14 +869,14 @@ int oracle_face_points_ex(const int* n, const double* lo, const double* hi, cons
 }
 
 int oracle_face_points(const int* n, const double* lo, const double* hi, int m, int s, double* xyz) {
-  return oracle_face_points_ex(n, lo, hi, 0, m, s, xyz);
+  return oracle_face_points_ex(n, lo, hi, 0, 0, m, s, xyz);
 }
 
 /* Physical coordinates of the face points of every face of every cell:
  * xyz[((cell*6 + s)*m^2 + p)*3 + r], s = 2*dir + side, points ordered as in the face tables
  * (lower tangential axis fastest). */
-int oracle_cell_face_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap, int m,
-                               double* xyz) {
+int oracle_cell_face_points_ex(const int* n, const double* lo, const double* hi, const double* Jmap,
+                               const double* verts, int m, double* xyz) {
   double* x = (double*)malloc(sizeof(double) * m);
   double* w = (double*)malloc(sizeof(double) * m);
   if (!x || !w || oracle_gauss_legendre(m, x, w)) return -1;
@@ -749,7 +894,7 @@ int oracle_cell_face_points_ex(const int* n, const double* lo, const double* hi,
                 xi[dir] = ic[dir] + side;
                 xi[ta] = ic[ta] + x[pa];
                 xi[tb] = ic[tb] + x[pb];
-                map_point(n, lo, hi, Jmap, xi, xyz + o);
+                map_point_v(n, lo, hi, Jmap, verts, xi, xyz + o);
                 o += 3;
               }
           }
@@ -760,5 +905,5 @@ int oracle_cell_face_points_ex(const int* n, const double* lo, const double* hi,
 }
 
 int oracle_cell_face_points(const int* n, const double* lo, const double* hi, int m, double* xyz) {
-  return oracle_cell_face_points_ex(n, lo, hi, 0, m, xyz);
+  return oracle_cell_face_points_ex(n, lo, hi, 0, 0, m, xyz);
 }

@@ -262,3 +262,22 @@ def sheared_jacobian(h, seed: int = 0, shear: float = 0.25) -> np.ndarray:
     rng = np.random.default_rng(seed)
     U = np.triu(rng.uniform(-1, 1, (3, 3)), 1)
     return (np.eye(3) + shear * U) @ np.diag(np.asarray(h, dtype=np.float64))
+
+
+def multilinear_vertices(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), seed: int = 0, amplitude: float = 0.2):
+    """Vertices [(n0+1)(n1+1)(n2+1), 3] (x fastest) of a structured grid of [lo, hi] whose vertices are moved by
+    seeded offsets of up to amplitude * h per component, so that the cells are general trilinear hexahedra
+    (Problem C of Sec. 5.1).  A vertex on the boundary moves only within its boundary face, so the domain stays
+    the box [lo, hi]; amplitude < 0.25 keeps every cell's map invertible."""
+    n = [int(v) for v in n]
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    h = (hi - lo) / np.asarray(n)
+    k, j, i = np.meshgrid(np.arange(n[2] + 1), np.arange(n[1] + 1), np.arange(n[0] + 1), indexing="ij")
+    idx = np.stack([i, j, k], axis=-1).reshape(-1, 3)
+    X = lo + idx * h
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-amplitude, amplitude, X.shape) * h
+    on_bnd = (idx == 0) | (idx == np.asarray(n))
+    d[on_bnd] = 0.0
+    return X + d

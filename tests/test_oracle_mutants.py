@@ -12,6 +12,7 @@ import oracle
 from tests import test_oracle_pins as pins
 from tests import test_oracle_tensor_pins as xpins
 from tests import test_oracle_bc_pins as bpins
+from tests import test_oracle_multilinear_pins as mpins
 from tests import test_oracle_transport_pins as tpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "dg_oracle.c")
@@ -25,8 +26,8 @@ MUTANTS = [
     ("convection sign", "fl[r] = Dg[r] - br * uq;", "fl[r] = Dg[r] + br * uq;"),
     ("transposed basis index", "t->grad[o * 3 + 1] = v[0][j1] * d[1][j2] * v[2][j3];",
      "t->grad[o * 3 + 1] = v[0][j1] * d[1][j3] * v[2][j2];"),
-    ("boundary normal sign", "double sgn = side ? 1.0 : -1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        for",
-     "double sgn = 1.0;\n        double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n        for"),
+    ("boundary normal sign", "double nout[3] = {sgn * nu[0], sgn * nu[1], sgn * nu[2]};\n          double Db_[3][3];",
+     "double nout[3] = {nu[0], nu[1], nu[2]};\n          double Db_[3][3];"),
     ("Gauss weight", "w[i] = 1.0 / ((1.0 - t * t) * dP[m] * dP[m]);", "w[i] = 2.0 / ((1.0 - t * t) * dP[m] * dP[m]);"),
     ("Dirichlet data sign in the right hand side", "- dnv * g + gam * g * v", "+ dnv * g + gam * g * v"),
     ("reaction dropped", "cq * uq * ph[i]", "0.0 * cq * uq * ph[i]"),
@@ -41,13 +42,20 @@ MUTANTS = [
     ("volume velocity component", "pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + r]",
      "pr->b_vol[((size_t)cell * cx->vol.np + p) * 3 + 0]"),
     ("tensor off-diagonal entry", "Dm[0][1] = Dm[1][0] = t[3];", "Dm[0][1] = Dm[1][0] = t[4];"),
-    ("gradient mapped by J^-1 instead of J^-T", "g[a] += cx->Jinv[r][a] * gref[r];", "g[a] += cx->Jinv[a][r] * gref[r];"),
-    ("face normal from J instead of J^-T", "cx->nrm[r][a] = cx->Jinv[r][a] / len;", "cx->nrm[r][a] = cx->J[a][r] / len;"),
-    ("face area without the normal scale", "cx->area[r] = cx->vol_T * len;", "cx->area[r] = cx->vol_T;"),
+    ("gradient mapped by J^-1 instead of J^-T", "g[a] += Jinv[r][a] * gref[r];", "g[a] += Jinv[a][r] * gref[r];"),
+    ("face normal from a column of J^-1 instead of a row", "for (int a = 0; a < 3; ++a) nu[a] = g->Jinv[r][a] / len;",
+     "for (int a = 0; a < 3; ++a) nu[a] = g->Jinv[a][r] / len;"),
+    ("face area element without the normal scale", "return g->det * len;", "return g->det;"),
     ("neighbour's tensor from its far face", "unpack6(pr->D_face + (((size_t)nbr * 6 + oface) * ft->np + p) * 6, Dn_);",
      "unpack6(pr->D_face + (((size_t)nbr * 6 + 2 * dir + side) * ft->np + p) * 6, Dn_);"),
     ("point-wise reaction ignored", "const double cq = pr->c_vol ? pr->c_vol[(size_t)cell * cx->vol.np + p] : pr->c;",
      "const double cq = pr->c;"),
+    ("trilinear shape derivative sign", "dN[r] = corner[r] ? 1.0 : -1.0;", "dN[r] = corner[r] ? 1.0 : 1.0;"),
+    ("neighbour's gradient with the own cell's geometry", "eval_fe(nt, p, zn, Gn.Jinv, &un, gn);",
+     "eval_fe(nt, p, zn, Go.Jinv, &un, gn);"),
+    ("penalty with the larger cell volume", "const double vmin = volT < volN ? volT : volN;",
+     "const double vmin = volT > volN ? volT : volN;"),
+    ("volume element dropped on multilinear cells", "v += cx->vol.wgt[p] * g.det;", "v += cx->vol.wgt[p];"),
     ("Neumann flux sign in the right hand side", "y[i] -= dx * jf * ph[i];", "y[i] += dx * jf * ph[i];"),
     ("outflow face without its upwind flux", "y[i] += dx * upwind(us, 0.0, bnu) * ph[i];",
      "y[i] += 0.0 * dx * upwind(us, 0.0, bnu) * ph[i];"),
@@ -78,6 +86,10 @@ def _pin_checks():
     yield lambda: bpins.test_mixed_boundary_types_match_kronecker_closed_form(bpins.BC_CASES[0])
     yield lambda: bpins.test_polynomial_solution_with_mixed_boundary_types_has_zero_residual(2)
     yield bpins.test_neumann_rhs_closed_form
+    yield lambda: mpins.test_quadratic_solution_on_multilinear_mesh_has_zero_residual(2)
+    yield mpins.test_volume_element_integrates_the_domain
+    yield mpins.test_interior_penalty_on_multilinear_cells
+    yield lambda: mpins.test_affine_vertices_reproduce_the_affine_map(2, 3)
 
 
 @pytest.mark.parametrize("name,orig,mutated", MUTANTS, ids=[m[0] for m in MUTANTS])
