@@ -383,6 +383,13 @@ typedef struct {
                            = j: no term in a_h, -(j, v) in l_h, j given in dg_bc.g_qp of that side), or
                            DG_BC_OUTFLOW ((D grad u) . nu = 0: only the upwind flux Phi(u, 0, b . nu) in a_h,
                            meant for sides with b . nu >= 0; nothing in l_h)                         */
+  const double* vertices; /* host [(n0+1)(n1+1)(n2+1)][3], vertex (i, j, l) at i + (n0+1)(j + (n1+1) l), or
+                           NULL.  Multilinear cells (Problem C of Sec. 5.1): cell (ix, iy, iz) is the trilinear
+                           image of [0,1]^3 through its 8 corner vertices; mesh->lo/hi and jacobian are unused.
+                           The point-wise kernels run (coefficients from D_qp/D_face/c_qp when given, else from
+                           coeffs / D_tensor), with J taken at every quadrature point; the penalty's |F| and |T|
+                           are the face area and cell volume.  No periodic axes; degrees 1..8; dg_project and the
+                           Runge-Kutta calls reject such a handle (its mass matrix is not |T| I). */
 } dg_setup_ext;
 
 enum { DG_BC_DIRICHLET = 0, DG_BC_NEUMANN = 1, DG_BC_OUTFLOW = 2 };

@@ -154,6 +154,7 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->kqX);
   cudaFree(h->kf64);
   cudaFree(h->kfX);
+  delete[] h->verts;
   cudaFree(h->rk_tmp);
   cudaFree(h->ws);
   if (h->ws_host) cudaFreeHost(h->ws_host);
@@ -233,14 +234,29 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     set_error("dg_setup: a velocity field or m = k+3 needs degree k <= 8");
     return DG_ERR_INVALID_ARG;
   }
-  const bool pw = ext && (ext->D_qp || ext->D_face);
-  if (pw && (!ext->D_qp || !ext->D_face)) {
+  const bool ml = ext && ext->vertices;
+  const bool pw_given = ext && (ext->D_qp || ext->D_face);
+  if (pw_given && (!ext->D_qp || !ext->D_face)) {
     set_error("dg_setup: point-wise coefficients need both D_qp and D_face");
     return DG_ERR_INVALID_ARG;
   }
+  const bool pw = pw_given || ml;
   if (pw && (k > 8 || velocity == DG_VELOCITY_TAYLOR_GREEN)) {
-    set_error("dg_setup: point-wise coefficients need degree k <= 8 and a constant or point-wise velocity");
+    set_error("dg_setup: point-wise coefficients and multilinear cells need degree k <= 8 and a constant or "
+              "point-wise velocity");
     return DG_ERR_INVALID_ARG;
+  }
+  if (ml && (ext->jacobian || ext->periodic[0] || ext->periodic[1] || ext->periodic[2])) {
+    set_error("dg_setup: multilinear cells (vertices) exclude an affine jacobian and periodic axes");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (ml) {
+    const int64_t nv = (int64_t)(mesh->n[0] + 1) * (mesh->n[1] + 1) * (mesh->n[2] + 1);
+    for (int64_t i = 0; i < 3 * nv; ++i)
+      if (!std::isfinite(ext->vertices[i])) {
+        set_error("dg_setup: vertices must be finite");
+        return DG_ERR_INVALID_ARG;
+      }
   }
   if (!pw && ext && ext->c_qp) {
     set_error("dg_setup: c_qp needs the point-wise coefficients D_qp and D_face");
@@ -279,9 +295,9 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     periodic[r] = ext ? ext->periodic[r] : 0;
   }
   std::vector<double> D(ncell);
-  const bool tensor_given = td && ext->D_tensor && !pw;
+  const bool tensor_given = td && ext->D_tensor && !pw_given;
   for (int64_t i = 0; i < ncell; ++i) {
-    if (pw) {
+    if (pw_given) {
       D[i] = 1.0;  // unused: the point tables carry the coefficients
       continue;
     }
@@ -329,7 +345,18 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
   h->vb = vb;
   h->td = td;
   h->pw = pw;
+  h->ml = ml;
   h->affine = td && ext->jacobian;
+  if (ml) {
+    const size_t nv = (size_t)(h->n[0] + 1) * (h->n[1] + 1) * (h->n[2] + 1) * 3;
+    h->verts = new (std::nothrow) double[nv];
+    if (!h->verts) {
+      delete h;
+      set_error("dg_setup: host allocation failed");
+      return DG_ERR_OOM;
+    }
+    std::memcpy(h->verts, ext->vertices, nv * sizeof(double));
+  }
   for (int r = 0; r < 3; ++r) h->periodic[r] = periodic[r];
   for (int f = 0; f < 6; ++f) h->bc_type[f] = periodic[f / 2] ? DG_BC_DIRICHLET : bc_type[f];
   // cell Jacobian: the affine map, or diag(h) for the axis-parallel grid
@@ -477,12 +504,35 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
   }
   std::vector<double> kq, kf, bface_pw;
   if (pw) {
-    const int prc = build_pointwise_tables(h, ext->D_qp, ext->D_face, ext->c_qp, co->c, co->b,
+    // multilinear cells with per-cell coefficients: repeat each cell's tensor at its points
+    std::vector<double> Dq, Df;
+    const double* Dqp = pw_given ? ext->D_qp : nullptr;
+    const double* Dfp = pw_given ? ext->D_face : nullptr;
+    if (!pw_given) {
+      const int64_t M3 = (int64_t)M * M * M, MM = (int64_t)M * M;
+      Dq.resize((size_t)ncell * M3 * 6);
+      Df.resize((size_t)ncell * 6 * MM * 6);
+      for (int64_t cell = 0; cell < ncell; ++cell) {
+        double t6[6];
+        if (tensor_given) {
+          for (int q = 0; q < 6; ++q) t6[q] = ext->D_tensor[6 * cell + q];
+        } else {
+          // (D itself holds the per-cell metric by now)
+          t6[0] = t6[1] = t6[2] = co->D_cell ? co->D_cell[cell] : co->D_const;
+          t6[3] = t6[4] = t6[5] = 0.0;
+        }
+        for (int64_t q = 0; q < M3; ++q) std::memcpy(&Dq[(cell * M3 + q) * 6], t6, sizeof(t6));
+        for (int64_t q = 0; q < 6 * MM; ++q) std::memcpy(&Df[(cell * 6 * MM + q) * 6], t6, sizeof(t6));
+      }
+      Dqp = Dq.data();
+      Dfp = Df.data();
+    }
+    const int prc = build_pointwise_tables(h, Dqp, Dfp, ext->c_qp, co->c, co->b,
                                            velocity == DG_VELOCITY_POINTS ? ext->b_qp : nullptr,
                                            velocity == DG_VELOCITY_POINTS ? ext->b_face : nullptr, kq, kf, fc,
                                            bface_pw);
     if (prc != DG_OK) {
-      delete h;
+      dg_destroy(h);
       return prc;
     }
   }
@@ -546,8 +596,21 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
       rc = setup_velocity(h, velocity, co->b, ext ? ext->b_qp : nullptr, ext ? ext->b_face : nullptr, s);
       if (rc != DG_OK) goto fail;
     }
-    // right hand side: f at the volume points goes through the work buffer
-    if (f_qp) {
+    // right hand side: f at the volume points goes through the work buffer (on multilinear cells times the
+    // volume element |det J| of each point: the kernels then see |T| = 1)
+    if (f_qp && ml) {
+      std::vector<double> fs(f_qp, f_qp + npts);
+      const int64_t M3 = (int64_t)M * M * M;
+      for (int64_t e = 0; e < npts; ++e) {
+        const int q = (int)(e % M3);
+        const double xi[3] = {h->tab.xi[q % M], h->tab.xi[(q / M) % M], h->tab.xi[q / (M * M)]};
+        MapGeo g;
+        if ((rc = point_geometry(h, e / M3, xi, &g)) != DG_OK) goto fail;
+        fs[e] *= g.det;
+      }
+      DG_TRY(cudaMemcpyAsync(h->work_V, fs.data(), npts * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
+      DG_TRY(cudaStreamSynchronize(s), "dg_setup synchronize");
+    } else if (f_qp) {
       DG_TRY(cudaMemcpyAsync(h->work_V, f_qp, npts * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
     } else {
       DG_TRY(cudaMemsetAsync(h->work_V, 0, npts * sizeof(double), s), "memset f");
@@ -558,8 +621,31 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
       gsize[sd] = (int64_t)h->n[ta] * h->n[tb] * M * M;
       if (bc && bc->g_qp[sd] && !h->periodic[dir]) {
         DG_TRY(cudaMalloc(&gdev[sd], gsize[sd] * sizeof(double)), "cudaMalloc(g)");
-        DG_TRY(cudaMemcpyAsync(gdev[sd], bc->g_qp[sd], gsize[sd] * sizeof(double), cudaMemcpyHostToDevice, s),
-               "copy g");
+        if (ml && h->bc_type[sd] == DG_BC_NEUMANN) {
+          // Neumann flux times the face's area element (the kernels see a unit face measure)
+          std::vector<double> js(bc->g_qp[sd], bc->g_qp[sd] + gsize[sd]);
+          const int MM = M * M;
+          for (int64_t e = 0; e < gsize[sd]; ++e) {
+            const int64_t fidx = e / MM;
+            const int p = (int)(e % MM);
+            int ic3[3];
+            ic3[dir] = (sd % 2) ? h->n[dir] - 1 : 0;
+            ic3[ta] = (int)(fidx % h->n[ta]);
+            ic3[tb] = (int)(fidx / h->n[ta]);
+            const int64_t cell = ic3[0] + (int64_t)h->n[0] * (ic3[1] + (int64_t)h->n[1] * ic3[2]);
+            double xi[3], nu[3];
+            face_xi(h, sd, p, xi);
+            MapGeo g;
+            if ((rc = point_geometry(h, cell, xi, &g)) != DG_OK) goto fail;
+            js[e] *= face_frame(g, dir, nu);
+          }
+          DG_TRY(cudaMemcpyAsync(gdev[sd], js.data(), gsize[sd] * sizeof(double), cudaMemcpyHostToDevice, s),
+                 "copy j");
+          DG_TRY(cudaStreamSynchronize(s), "dg_setup synchronize");
+        } else {
+          DG_TRY(cudaMemcpyAsync(gdev[sd], bc->g_qp[sd], gsize[sd] * sizeof(double), cudaMemcpyHostToDevice, s),
+                 "copy g");
+        }
       }
     }
     rc = launch_rhs_f64(h, static_cast<const double*>(h->work_V), gdev, static_cast<double*>(h->p64.F), s);
@@ -594,8 +680,30 @@ int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
   }
   const int N = h->M;  // points per direction
   const double* x = h->tab.xi;
-  // x = lo + J xi for a point xi of the structured reference grid (J = diag(h) without an affine map)
+  // x = lo + J xi for a point xi of the structured reference grid (J = diag(h) without an affine map); on
+  // multilinear cells the trilinear map of the cell that holds xi (a point on a face between two cells is
+  // mapped by the upper one; both maps give the same point)
   auto map = [&](const double xi[3], double* out) {
+    if (h->ml) {
+      int ic[3];
+      double t[3];
+      for (int r = 0; r < 3; ++r) {
+        ic[r] = (int)std::floor(xi[r]);
+        if (ic[r] > h->n[r] - 1) ic[r] = h->n[r] - 1;
+        if (ic[r] < 0) ic[r] = 0;
+        t[r] = xi[r] - ic[r];
+      }
+      for (int a = 0; a < 3; ++a) out[a] = 0.0;
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a) {
+            const double Nw = (a ? t[0] : 1.0 - t[0]) * (b ? t[1] : 1.0 - t[1]) * (c ? t[2] : 1.0 - t[2]);
+            const int64_t v =
+                (ic[0] + a) + (int64_t)(h->n[0] + 1) * ((ic[1] + b) + (int64_t)(h->n[1] + 1) * (ic[2] + c));
+            for (int r = 0; r < 3; ++r) out[r] += Nw * h->verts[3 * v + r];
+          }
+      return;
+    }
     for (int a = 0; a < 3; ++a)
       out[a] = h->affine ? h->lo[a] + h->J[a][0] * xi[0] + h->J[a][1] * xi[1] + h->J[a][2] * xi[2]
                          : h->lo[a] + h->h[a] * xi[a];
@@ -644,7 +752,7 @@ int dg_quadrature_points(const dg_handle* h, int32_t which, double* xyz) {
           xi[dir] = side ? h->n[dir] : 0;
           xi[ta] = ca + x[pa];
           xi[tb] = cb + x[pb];
-          if (!h->affine && side) {
+          if (!h->affine && !h->ml && side) {
             // the upper boundary exactly at hi
             double pt[3];
             map(xi, pt);

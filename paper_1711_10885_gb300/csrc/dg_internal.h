@@ -54,6 +54,10 @@ struct dg_handle {
   // kf [ncell][6][3][M^2] = row dir of K / |F_dir| at every face point, Buffers::fc [ncell][6][6][M^2] the
   // face coefficients of every face point, bface the normal velocity; FP64 and double-float copies
   bool pw = false;
+  // multilinear cells (ml, a pw handle, Problem C): host copy of the vertex coordinates
+  // [(n0+1)(n1+1)(n2+1)][3]; the kernels then see a unit face measure and |T| = 1 (both folded into the tables)
+  bool ml = false;
+  double* verts = nullptr;
   void* kq64 = nullptr;
   void* kqX = nullptr;
   void* kf64 = nullptr;
@@ -138,6 +142,17 @@ int build_pointwise_tables(const dg_handle* h, const double* D_qp, const double*
                            double c_const, const double b[3], const double* b_qp, const double* b_face,
                            std::vector<double>& kq, std::vector<double>& kf, std::vector<double>& fc,
                            std::vector<double>& bface);
+// geometry of a cell's map at a local reference point xi in [0,1]^3: J^{-1} and |det J| (constant unless the
+// cells are multilinear); face_frame: unit normal along +reference axis r and the area element
+// |det J| |J^{-T} e_r|; face_xi: the local coordinates of point p of face 2*dir+side
+struct MapGeo {
+  double Jinv[3][3];
+  double det;   // |det J|
+  double sdet;  // det J (its sign is the cell map's orientation)
+};
+int point_geometry(const dg_handle* h, int64_t cell, const double xi[3], MapGeo* g);
+double face_frame(const MapGeo& g, int r, double nu[3]);
+void face_xi(const dg_handle* h, int face, int p, double xi[3]);
 // x[i] = pair of FP32 numbers closest to a[i] (double-float copies of the coefficient tables)
 int copy_to_pairs(const double* a, void* x_pairs, int64_t n, cudaStream_t s);
 

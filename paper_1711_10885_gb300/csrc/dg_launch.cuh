@@ -77,6 +77,12 @@ dgk::Geo<T> make_geo(const dg_handle* h) {
     g.vol = (T)h->detJ;
     g.creact = (T)(h->c * h->detJ);
   }
+  if (h->ml) {
+    // multilinear cells: the volume and area elements vary over a cell and are folded into the point tables,
+    // the face coefficients and the right hand side data, so the kernels see |T| = 1 and |F| = 1
+    for (int r = 0; r < 3; ++r) g.area[r] = T(1);
+    g.vol = T(1);
+  }
   g.ncell = (int)h->ncell;
   for (int r = 0; r < 3; ++r) g.periodic[r] = h->periodic[r];
   for (int f = 0; f < 6; ++f) g.bc[f] = h->bc_type[f];

@@ -177,12 +177,20 @@ int dg_project(dg_handle* h, const double* u_qp, double* z, void* stream) {
     set_error("dg_project: null argument");
     return DG_ERR_INVALID_ARG;
   }
+  if (h->ml) {
+    set_error("dg_project: the mass matrix of multilinear cells is not |T| I");
+    return DG_ERR_INVALID_ARG;
+  }
   const double* none[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   return launch_rhs_f64(h, u_qp, none, z, static_cast<cudaStream_t>(stream), true);
 }
 
 static int stage(const dg_handle* h, const double* u, double* y, const StageArgs& st, int32_t precision,
                  cudaStream_t s) {
+  if (h->ml) {
+    set_error("Runge-Kutta stages: the mass matrix of multilinear cells is not |T| I");
+    return DG_ERR_INVALID_ARG;
+  }
   return precision == DG_F64X ? launch_stage_f64x(h, u, y, st, s) : launch_stage_f64(h, u, y, st, s);
 }
 

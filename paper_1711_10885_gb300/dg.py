@@ -56,7 +56,7 @@ _VELOCITY = {"constant": DG_VELOCITY_CONSTANT, "points": DG_VELOCITY_POINTS, "ta
 class dg_setup_ext(ctypes.Structure):
     _fields_ = [("periodic", ctypes.c_int32 * 3), ("m", ctypes.c_int32), ("velocity", ctypes.c_int32),
                 ("b_qp", _dp), ("b_face", _dp), ("D_tensor", _dp), ("jacobian", _dp), ("D_qp", _dp),
-                ("D_face", _dp), ("c_qp", _dp), ("bc_type", ctypes.c_int32 * 6)]
+                ("D_face", _dp), ("c_qp", _dp), ("bc_type", ctypes.c_int32 * 6), ("vertices", _dp)]
 
 
 DG_SOLVE_FP64 = 0
@@ -201,12 +201,13 @@ class Operator:
     coefficients at the quadrature points: ``D_qp`` [ncell, m^3, 6] and ``D_face`` [ncell, 6, m^2, 6] (both, at
     quadrature_points(0) and quadrature_points(7)), ``c_qp`` [ncell, m^3] optional.  ``bc``: the type of each
     boundary side 2*dir + side, "dirichlet" (default), "neumann" (g_qp then holds the total flux j) or
-    "outflow" (Sec. 2, eq. modelproblem)."""
+    "outflow" (Sec. 2, eq. modelproblem).  ``vertices`` [(n0+1)(n1+1)(n2+1), 3] (x fastest): multilinear cells
+    (Problem C of Sec. 5.1)."""
 
     def __init__(self, n, k, D=1.0, b=(1.0, 0.5, 0.25), c=1.0, sigma=None, lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), f_qp=None, g_qp=None, stream=None, periodic=(0, 0, 0), m=None,
                  velocity="constant", b_qp=None, b_face=None, D_tensor=None, jacobian=None, D_qp=None,
-                 D_face=None, c_qp=None, bc=None):
+                 D_face=None, c_qp=None, bc=None, vertices=None):
         mesh = dg_mesh()
         for r in range(3):
             mesh.lo[r], mesh.hi[r], mesh.n[r] = float(lo[r]), float(hi[r]), int(n[r])
@@ -271,7 +272,7 @@ class Operator:
             kinds = {"dirichlet": DG_BC_DIRICHLET, "neumann": DG_BC_NEUMANN, "outflow": DG_BC_OUTFLOW}
             for f in range(6):
                 ext.bc_type[f] = kinds[bc[f]] if isinstance(bc[f], str) else int(bc[f])
-        for name, arr in (("D_qp", D_qp), ("D_face", D_face), ("c_qp", c_qp)):
+        for name, arr in (("D_qp", D_qp), ("D_face", D_face), ("c_qp", c_qp), ("vertices", vertices)):
             if arr is not None:
                 a = _f64(arr).reshape(-1)
                 keep.append(a)

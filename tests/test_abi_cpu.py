@@ -180,3 +180,30 @@ def test_operator_marshals_every_option():
     except dg.DGError:
         return
     op.close()  # a GPU was present: the handle was built
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets of include/dg.h (compiled here with gcc)."""
+    import os
+    import subprocess
+    from paper_1711_10885_gb300 import dg
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = {"dg_mesh": dg.dg_mesh, "dg_coeffs": dg.dg_coeffs, "dg_bc": dg.dg_bc, "dg_setup_ext": dg.dg_setup_ext,
+               "dg_solve_opts": dg.dg_solve_opts, "dg_solve_stats": dg.dg_solve_stats,
+               "dg_mlp_train_opts": dg.dg_mlp_train_opts, "dg_mlp_train_stats": dg.dg_mlp_train_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dg.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
