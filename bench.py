@@ -491,6 +491,85 @@ def problem_b_benchmark(reps=20, n=32, k=7, seed=70):
     return out
 
 
+def multilinear_grid_points(n, m, verts):
+    """Gauss points of the trilinear cells of a vertex grid: volume [ncell, m^3, 3] and every cell's faces
+    [ncell, 6, m^2, 3] (the layouts of dg_quadrature_points 0 and 7)."""
+    import numpy as np
+    xi = (np.polynomial.legendre.leggauss(m)[0] + 1.0) / 2.0
+    nx, ny, nz = n
+    V = np.asarray(verts, dtype=np.float64).reshape(nz + 1, ny + 1, nx + 1, 3)
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    C = np.stack([V[iz + c, iy + b, ix + a] for c in range(2) for b in range(2) for a in range(2)], axis=1)
+
+    def shape(loc):  # [p, 3] local coordinates -> trilinear weights [p, 8] (corner a + 2 b + 4 c)
+        return np.stack([(loc[:, 0] if a else 1 - loc[:, 0]) * (loc[:, 1] if b else 1 - loc[:, 1]) *
+                         (loc[:, 2] if c else 1 - loc[:, 2]) for c in range(2) for b in range(2) for a in range(2)],
+                        axis=1)
+
+    p3, p2, p1 = np.meshgrid(xi, xi, xi, indexing="ij")
+    vol = np.einsum("qv,cvd->cqd", shape(np.stack([p1.ravel(), p2.ravel(), p3.ravel()], axis=1)), C)
+    pb, pa = np.meshgrid(xi, xi, indexing="ij")
+    faces = np.empty((C.shape[0], 6, m * m, 3))
+    for face in range(6):
+        d, side = face // 2, face % 2
+        ta, tb = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+        loc = np.empty((m * m, 3))
+        loc[:, d], loc[:, ta], loc[:, tb] = side, pa.ravel(), pb.ravel()
+        faces[:, face] = np.einsum("pv,cvd->cpd", shape(loc), C)
+    return vol, faces
+
+
+def problem_c_benchmark(reps=20, n=32, k=7, seed=80):
+    """Problem C of Sec. 5.1 on one GPU: n^3 multilinear cells of the unit cube (vertices moved by up to 0.2 h,
+    inputs.multilinear_vertices), Q_k, m = k+3 Gauss points per direction, D(x) quadratic SPD and c(x) affine
+    (inputs.PolynomialFields), constant b, f = 1, g = 0.  FP64 and double-float residual applications."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10885_gb300 import dg, flops, inputs
+    m, N = k + 3, k + 1
+    verts = inputs.multilinear_vertices((n, n, n), seed=seed, amplitude=0.2)
+    fields = inputs.PolynomialFields(seed, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    t0 = time.time()
+    xv, xf = multilinear_grid_points((n, n, n), m, verts)
+    kw = dict(D_qp=fields.D(xv), D_face=fields.D(xf), c_qp=fields.c(xv))
+    del xv, xf
+    ncell = n ** 3
+    op = dg.Operator((n, n, n), k, 1.0, b=tuple(fields.b0), c=0.0, m=m, vertices=verts,
+                     f_qp=np.ones(ncell * m ** 3), **kw)
+    setup_s = time.time() - t0
+    del kw
+    u = torch.tensor(inputs.uniform_u(op.ndof, seed + 1), device="cuda")
+    r = torch.empty_like(u)
+    stream = torch.cuda.current_stream()
+    cell_fl = flops.cell_kernel_flops_pw(N, m) * ncell
+    face_fl = flops.face_kernel_flops_pw(N, m) * ncell
+    out = {"workload": f"problem_c_q{k}_{n}: {n}^3 multilinear cells, k = {k}, m = {m}, polynomial D(x), c(x)",
+           "dofs": op.ndof, "setup_s": setup_s, "executed_flops_per_dof": (cell_fl + face_fl) / op.ndof}
+    for pname, prec in (("f64", dg.DG_F64), ("f64x", dg.DG_F64X)):
+        for _ in range(3):
+            op.apply_residual(u, r, precision=prec)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+        for i in range(reps):
+            ev[3 * i].record(stream)
+            op.apply_stage(0, u, r, residual=True, precision=prec)
+            ev[3 * i + 1].record(stream)
+            op.apply_stage(1, u, r, residual=True, precision=prec)
+            ev[3 * i + 2].record(stream)
+        torch.cuda.synchronize()
+        cms = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(reps)) / reps
+        fms = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(reps)) / reps
+        out[pname] = {"mdofs": op.ndof / ((cms + fms) * 1e-3) / 1e6,
+                      "kernels_ms": {"dg_cell_kernel_td<pw>": cms, "dg_face_kernel<td, pw>": fms},
+                      "fp64_equivalent_tflops": (cell_fl + face_fl) / ((cms + fms) * 1e-3) / 1e12}
+    ach = cell_fl / (out["f64"]["kernels_ms"]["dg_cell_kernel_td<pw>"] * 1e-3) / 1e12
+    out["roofline_f64"] = {"bound": "alu", "kernel": f"dg_cell_kernel_td<{N}, double, M={m}, pw>", "achieved": ach,
+                           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}
+    op.close()
+    return out
+
+
 def hbm_peak_gbs():
     """Measured HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else the recipe's fallback."""
     try:
@@ -878,6 +957,7 @@ def run_ours(args):
         line["tensor_diffusion"] = tensor_benchmark()
     if ws == 1 and not args.no_problem_b:
         line["problem_b"] = problem_b_benchmark()
+        line["problem_c"] = problem_c_benchmark()
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -898,7 +978,10 @@ def main():
     ap.add_argument("--no-matrix", action="store_true", help="skip the matrix-based comparison section")
     ap.add_argument("--no-tensor", action="store_true", help="skip the tensor-diffusion / affine section")
     ap.add_argument("--tensor", action="store_true", help="print only the tensor-diffusion / affine section")
-    ap.add_argument("--no-problem-b", action="store_true", help="skip the Problem B (point-wise coefficients) section")
+    ap.add_argument("--no-problem-b", action="store_true",
+                    help="skip the Problem B (point-wise coefficients) and Problem C (multilinear cells) sections")
+    ap.add_argument("--problem-c", type=int, default=None, metavar="N",
+                    help="print only the Problem C section on N^3 multilinear cells (k = 7, m = 10)")
     ap.add_argument("--problem-b", type=int, default=None, metavar="N",
                     help="print only the Problem B section on N^3 cells (k = 7, m = 10); with --profile: only "
                          "W + K residual applies of it")
@@ -937,6 +1020,10 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"problem_b": problem_b_benchmark(n=args.problem_b)}), flush=True)
+    elif args.problem_c:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"problem_c": problem_c_benchmark(n=args.problem_c)}), flush=True)
     elif args.transport:
         import torch
         torch.cuda.set_device(0)

@@ -145,3 +145,30 @@ def test_multilinear_handles_reject_unsupported_options(dg):
     with pytest.raises(dg.DGError):
         op.ssprk2(z, 0.01, 1)
     op.close()
+
+
+def test_multilinear_sampled_cells_at_bench_size(dg):
+    """The benchmark's Problem C launch configuration: 32^3 multilinear cells, k = 7, m = 10, polynomial D(x) and
+    c(x), constant b; sampled cells (corners included) against the oracle in FP64 and double-float."""
+    n, k, m = (32, 32, 32), 7, 10
+    seed = 80
+    verts = inputs.multilinear_vertices(n, seed=seed, amplitude=0.2)
+    fields = inputs.PolynomialFields(seed, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    nc = 32 ** 3
+    geo = oracle.Problem(n, k, np.ones(nc), m=m, vertices=verts)
+    xv, xf = oracle.volume_points(geo), oracle.cell_face_points(geo)
+    Dv, Df, cv = fields.D(xv), fields.D(xf), fields.c(xv)
+    del xv, xf
+    b = tuple(fields.b0)
+    pr = oracle.Problem(n, k, np.ones(nc), b=b, c=0.0, m=m, vertices=verts, D_vol=Dv, D_face=Df, c_vol=cv)
+    op = dg.Operator(n, k, 1.0, b=b, c=0.0, m=m, vertices=verts, D_qp=Dv, D_face=Df, c_qp=cv)
+    u = inputs.uniform_u(pr.ndof, seed + 1)
+    ut = torch.tensor(u, device="cuda")
+    y = op.apply_jacobian(ut).cpu().numpy().reshape(nc, -1)
+    yx = op.apply_jacobian(ut, precision=dg.DG_F64X).cpu().numpy().reshape(nc, -1)
+    op.close()
+    cells = np.concatenate([np.random.default_rng(seed + 2).choice(nc, 8, replace=False),
+                            [0, 31, 32 * 31, 32 * 32 - 1, nc - 32 * 32, nc - 1]])
+    yref = oracle.apply(pr, u, cells=cells).reshape(len(cells), -1)
+    assert relerr(y[cells], yref) <= TOL
+    assert relerr(yx[cells], yref) <= TOL
