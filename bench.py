@@ -609,6 +609,47 @@ def small_case_latency(replays=1000):
     return out
 
 
+def mlp_forward_benchmark(rows=262144, k=4, reps=20):
+    """Inference of the learned preconditioner's network (132 -> 256 -> 256 -> 125 at k = 4, BF16 operands,
+    FP32 accumulation) on `rows` feature rows (64^3 cells): the tcgen05 kernel (tensor memory accumulators)
+    against the mma.sync kernel, with the dense flops 2 (kinp 256 + 256^2 + 256 outp) per row."""
+    import numpy as np
+    import torch
+
+    from paper_1711_10885_gb300 import dg
+    mlp = dg.MLP(k, seed=7)
+    X = torch.randn(rows, mlp.kinp, device="cuda").to(torch.bfloat16)
+    Y = torch.empty(rows, mlp.outp, device="cuda")
+    flop = 2.0 * rows * (mlp.kinp * 256 + 256 * 256 + 256 * mlp.outp)
+    stream = torch.cuda.current_stream()
+    peak = 1937.5
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        pass
+    out = {"rows": rows, "k": k, "gflop_per_forward": flop / 1e9}
+    for name, env in (("tcgen05", None), ("mma_sync", "1")):
+        if env:
+            os.environ["DG_MLP_NO_TCGEN05"] = env
+        try:
+            for _ in range(3):
+                mlp.forward(X)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                mlp.forward(X)
+            b.record(stream)
+            b.synchronize()
+        finally:
+            os.environ.pop("DG_MLP_NO_TCGEN05", None)
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12, "frac_of_bf16_peak": flop / (ms * 1e-3) / 1e12 / peak}
+    out["peak_bf16_tflops"] = peak
+    mlp.close()
+    return out
+
+
 def hbm_peak_gbs():
     """Measured HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else the recipe's fallback."""
     try:
@@ -1032,6 +1073,8 @@ def run_ours(args):
     }
     if ws == 1:
         line["small_case_latency"] = small_case_latency()
+    if ws == 1:
+        line["mlp_forward"] = mlp_forward_benchmark()
     if ws == 1 and not args.no_batch:
         line["batch"] = batch_benchmark()
     if ws == 1 and not args.no_transport:
@@ -1065,6 +1108,7 @@ def main():
     ap.add_argument("--tensor", action="store_true", help="print only the tensor-diffusion / affine section")
     ap.add_argument("--no-problem-b", action="store_true",
                     help="skip the Problem B (point-wise coefficients) and Problem C (multilinear cells) sections")
+    ap.add_argument("--mlp-forward", action="store_true", help="print only the network inference timing")
     ap.add_argument("--problem-c", type=int, default=None, metavar="N",
                     help="print only the Problem C section on N^3 multilinear cells (k = 7, m = 10)")
     ap.add_argument("--problem-b", type=int, default=None, metavar="N",
@@ -1105,6 +1149,10 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"problem_b": problem_b_benchmark(n=args.problem_b)}), flush=True)
+    elif args.mlp_forward:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"mlp_forward": mlp_forward_benchmark()}), flush=True)
     elif args.problem_c:
         import torch
         torch.cuda.set_device(0)

@@ -6,6 +6,7 @@
 // units each); the correction is z_T = s * t_scale * y.  Weights are kept in FP32 (master copy, Adam
 // moments) and rounded to BF16 for the forward GEMMs; accumulation is FP32.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <random>
@@ -200,6 +201,217 @@ __global__ void __launch_bounds__(FWD_THREADS) mlp_forward(const FwdArgs a) {
       default:
         break;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same fused forward pass on the 5th-generation tensor cores (tcgen05): one CTA per 128 rows.  For
+// each layer the A operand (the X tile, then H1, then H2, BF16) and the layer's weights are staged in
+// shared memory in the no-swizzle K-major canonical layout (8-row x 16-byte core matrices, consecutive
+// along K at LBO = 128 B, 8-row groups at SBO = K/8 x 128 B); one thread issues the K/16 MMAs
+// (M = 128, N = layer width, FP32 accumulator in tensor memory) and commits them to an mbarrier; the four
+// warps then read their 32 accumulator rows back with tcgen05.ld for the bias / ReLU / BF16 epilogue,
+// which writes the next layer's A operand in place.  Inference only (kinp <= 256, outp <= 256).
+// ---------------------------------------------------------------------------------------------
+constexpr int TC_ROWS = 128;
+constexpr int TC_THREADS = 128;
+constexpr int TC_KMAX = 256;
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr size_t TC_ABYTES = (size_t)TC_ROWS * TC_KMAX * 2;  // 64 KB
+constexpr size_t TC_WBYTES = (size_t)HID * TC_KMAX * 2;      // 128 KB
+constexpr size_t TC_SMEM = TC_ABYTES + TC_WBYTES + 64;       // + mbarrier and the tensor-memory address
+constexpr uint32_t TC_WAIT_ITERS = 1u << 21;                 // bounded mbarrier wait (about a second)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte offset of the 16-byte chunk (row r, elements 8c..8c+7) in the canonical layout of a K-wide operand
+__device__ __forceinline__ uint32_t core_chunk(int r, int c, int K) {
+  return (uint32_t)((r >> 3) * (K >> 3) * 128 + c * 128 + (r & 7) * 16);
+}
+// shared memory matrix descriptor: start address, LBO, SBO (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
+__device__ __forceinline__ uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the mbarrier phase with the given parity; false after TC_WAIT_ITERS unsuccessful tries
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < TC_WAIT_ITERS; ++it) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    __nanosleep(128);
+  }
+  return false;
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// rows n = threadIdx.x, threadIdx.x + 128, ... < nrows of a row-major [nrows][K] BF16 matrix into the canonical
+// layout at dst (rows >= valid are zero)
+__device__ __forceinline__ void tc_stage(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int nrows,
+                                         int valid, int K) {
+  const int nc = K >> 3;
+  for (int n = threadIdx.x; n < nrows; n += TC_THREADS) {
+    const uint4* row = reinterpret_cast<const uint4*>(src + (size_t)n * K);
+    for (int c = 0; c < nc; ++c) {
+      const uint4 v = n < valid ? __ldg(row + c) : make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(dst + core_chunk(n, c, K)) = v;
+    }
+  }
+}
+
+// one layer: D (tensor memory) = A (128 x K) W^T (W: N x K), issued by thread 0 and committed to the mbarrier
+__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_s, uint32_t w_s, int K, int N, uint32_t mbar) {
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = tc_idesc(TC_ROWS, N), sbo = (uint32_t)(K >> 3) * 128;
+    for (int kk = 0; kk < (K >> 4); ++kk)
+      tc_mma(tmem, tc_sdesc(a_s + kk * 256, 128, sbo), tc_sdesc(w_s + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
+    tc_commit(mbar);
+  }
+}
+
+// bias + ReLU of this thread's accumulator row, as BF16, into the next layer's A operand (K = HID)
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, const float* __restrict__ bias, unsigned char* As,
+                                                   bool ok) {
+  const int r = threadIdx.x;
+  for (int cb = 0; cb < HID; cb += 16) {
+    float v[16];
+    tmem_ld16(trow + cb, v);
+    uint32_t p[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float x0 = ok ? fmaxf(v[2 * i] + __ldg(bias + cb + 2 * i), 0.f) : __int_as_float(0x7fc00000);
+      const float x1 = ok ? fmaxf(v[2 * i + 1] + __ldg(bias + cb + 2 * i + 1), 0.f) : __int_as_float(0x7fc00000);
+      p[i] = pack_bf16(x0, x1);
+    }
+    *reinterpret_cast<uint4*>(As + core_chunk(r, cb >> 3, HID)) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4*>(As + core_chunk(r, (cb >> 3) + 1, HID)) = make_uint4(p[4], p[5], p[6], p[7]);
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* As = tc_smem;
+  unsigned char* Ws = tc_smem + TC_ABYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_ABYTES + TC_WBYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + TC_ABYTES + TC_WBYTES + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
+  const int here = (int)min((int64_t)TC_ROWS, a.rows - row0);
+  const uint32_t a_s = smem_u32(As), w_s = smem_u32(Ws), mb = smem_u32(mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(mb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // layer 1 operands: the X tile and W1
+  tc_stage(As, a.X + row0 * a.kinp, TC_ROWS, here, a.kinp);
+  tc_stage(Ws, a.W1, HID, HID, a.kinp);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes = its 32 rows
+  bool ok = true;
+  uint32_t parity = 0;
+#pragma unroll 1
+  for (int layer = 0; layer < 2; ++layer) {
+    tc_layer(tmem, a_s, w_s, layer == 0 ? a.kinp : HID, HID, mb);
+    ok = mbar_wait(mb, parity) && ok;
+    parity ^= 1u;
+    tc_fence_after();
+    // the MMAs have read A and W: the epilogue overwrites A with the hidden layer, then W with the next weights
+    tc_hidden_epilogue(trow, layer == 0 ? a.b1 : a.b2, As, ok);
+    if (layer == 0)
+      tc_stage(Ws, a.W2, HID, HID, HID);
+    else
+      tc_stage(Ws, a.W3, a.outp, a.outp, HID);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  tc_layer(tmem, a_s, w_s, HID, a.outp, mb);
+  ok = mbar_wait(mb, parity) && ok;
+  tc_fence_after();
+  // output layer: bias, then the raw output Y or the scaled preconditioner output z (every lane takes part in
+  // the warp-collective tensor-memory loads; only rows of the mesh are stored)
+  const int r = tid;
+  const bool store = r < here;
+  const int64_t row = row0 + r;
+  for (int cb = 0; cb < a.outp; cb += 16) {
+    float v[16];
+    tmem_ld16(trow + cb, v);
+    if (!store) continue;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int col = cb + i;
+      const float y = ok ? v[i] + __ldg(a.b3 + col) : __int_as_float(0x7fc00000);
+      if (a.Y) a.Y[row * a.outp + col] = y;
+      if (a.z && col < a.nb) {
+        const float zv = a.scale[row] * y;
+        const size_t zi = (size_t)row * a.nb + col;
+        if (a.z_is_f64) {
+          double* zp = static_cast<double*>(a.z) + zi;
+          *zp = a.z_accumulate ? *zp + (double)zv : (double)zv;
+        } else {
+          float* zp = static_cast<float*>(a.z) + zi;
+          *zp = a.z_accumulate ? *zp + zv : zv;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
 }
 
@@ -409,7 +621,27 @@ dgm::FwdArgs fwd_args(const dg_mlp* m, const __nv_bfloat16* X, int64_t rows) {
   return a;
 }
 
+// the tensor-memory (tcgen05) forward pass serves inference of networks with kinp, outp <= 256 (degrees 1..5);
+// training, which also stores the hidden layers, and larger networks use the mma.sync kernel
+bool use_tc_forward(const dg_mlp* m, const dgm::FwdArgs& a) {
+  return !a.H1 && !a.H2 && m->d.kinp <= dgm::TC_KMAX && m->d.outp <= dgm::HID && !std::getenv("DG_MLP_NO_TCGEN05");
+}
+
 int launch_forward(const dg_mlp* m, const dgm::FwdArgs& a, cudaStream_t s) {
+  if (use_tc_forward(m, a)) {
+    static bool tc_attr = false;
+    if (!tc_attr) {
+      if (int rc = cfail(cudaFuncSetAttribute(dgm::mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)dgm::TC_SMEM),
+                         "MLP tcgen05 forward smem"))
+        return rc;
+      tc_attr = true;
+    }
+    const unsigned grid = (unsigned)((a.rows + dgm::TC_ROWS - 1) / dgm::TC_ROWS);
+    if (grid == 0) return 0;
+    dgm::mlp_forward_tc<<<grid, dgm::TC_THREADS, dgm::TC_SMEM, s>>>(a);
+    return cfail(cudaGetLastError(), "MLP tcgen05 forward");
+  }
   static bool attr = false;
   const size_t smem = fwd_smem(m->d);
   if (!attr || smem > 48 * 1024) {

@@ -176,3 +176,24 @@ def test_learned_preconditioner_gain_and_fallback(dg):
     assert st["fallback"] == 1 and st["rel_residual"] <= 1e-8
     mlp.close()
     op.close()
+
+
+@pytest.mark.parametrize("k,rows", [(4, 1000), (5, 129), (1, 128)])
+def test_tensor_memory_forward_equals_mma_sync_forward(dg, k, rows):
+    """The tcgen05 forward kernel (inference, degrees 1..5) and the mma.sync kernel compute the same network in
+    the same precisions (BF16 operands and hidden layers, FP32 accumulation); they differ only in summation
+    order, and in a rare hidden value rounded to the neighbouring BF16 number."""
+    rng = np.random.default_rng(40 + k)
+    mlp = dg.MLP(k, seed=4)
+    mlp.set_params(_random_params(mlp, rng))
+    X = torch.tensor(_rows(mlp, rng, rows), dtype=torch.bfloat16, device="cuda")
+    y_tc = mlp.forward(X)
+    os.environ["DG_MLP_NO_TCGEN05"] = "1"
+    try:
+        y_mma = mlp.forward(X)
+    finally:
+        del os.environ["DG_MLP_NO_TCGEN05"]
+    assert torch.isfinite(y_tc).all()
+    err = (torch.linalg.norm(y_tc - y_mma) / torch.linalg.norm(y_mma)).item()
+    assert err <= 1e-3, err
+    mlp.close()
