@@ -244,6 +244,16 @@ def run_profile(args):
         print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
         op.close()
         return
+    if args.mlp_forward:
+        # network inference on 262144 feature rows (k = 4): W + K forward passes
+        mlp = dg.MLP(4, seed=7)
+        X = torch.randn(262144, mlp.kinp, device="cuda").to(torch.bfloat16)
+        for _ in range(args.warmup + args.steps):
+            Y = mlp.forward(X)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "forwards": args.warmup + args.steps, "y_max": float(Y.abs().max())}))
+        mlp.close()
+        return
     if args.problem_b:
         # Problem B (point-wise coefficients, k = 7, m = 10) on problem_b^3 sheared cells: W + K residual applies
         import numpy as np

@@ -94,6 +94,10 @@ struct FwdArgs {
   int z_accumulate;  // z += ... instead of z = ...
   int64_t rows;
   int kinp, outp, nb;
+  // tcgen05 kernel: W1, W2, W3 pre-packed in the canonical shared-memory layout (see pack_canonical)
+  const __nv_bfloat16* W1p;
+  const __nv_bfloat16* W2p;
+  const __nv_bfloat16* W3p;
 };
 
 // Output layer on 8 NT columns starting at c0 for this warp's 16 rows, with the bias and either the
@@ -214,12 +218,13 @@ __global__ void __launch_bounds__(FWD_THREADS) mlp_forward(const FwdArgs a) {
 // which writes the next layer's A operand in place.  Inference only (kinp <= 256, outp <= 256).
 // ---------------------------------------------------------------------------------------------
 constexpr int TC_ROWS = 128;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;  // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. (its rows), columns half w / 4
 constexpr int TC_KMAX = 256;
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr size_t TC_ABYTES = (size_t)TC_ROWS * TC_KMAX * 2;  // 64 KB
 constexpr size_t TC_WBYTES = (size_t)HID * TC_KMAX * 2;      // 128 KB
-constexpr size_t TC_SMEM = TC_ABYTES + TC_WBYTES + 64;       // + mbarrier and the tensor-memory address
+constexpr size_t TC_BBYTES = 3 * HID * 4;                    // the three bias vectors (FP32)
+constexpr size_t TC_SMEM = TC_ABYTES + TC_WBYTES + TC_BBYTES + 64;  // + mbarriers and the tensor-memory address
 constexpr uint32_t TC_WAIT_ITERS = 1u << 21;                 // bounded mbarrier wait (about a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -273,36 +278,71 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   }
   return false;
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// 32 (or 8) consecutive accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// rows n = threadIdx.x, threadIdx.x + 128, ... < nrows of a row-major [nrows][K] BF16 matrix into the canonical
-// layout at dst (rows >= valid are zero)
-__device__ __forceinline__ void tc_stage(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int nrows,
-                                         int valid, int K) {
-  const int nc = K >> 3;
-  for (int n = threadIdx.x; n < nrows; n += TC_THREADS) {
-    const uint4* row = reinterpret_cast<const uint4*>(src + (size_t)n * K);
-    for (int c = 0; c < nc; ++c) {
-      const uint4 v = n < valid ? __ldg(row + c) : make_uint4(0u, 0u, 0u, 0u);
-      *reinterpret_cast<uint4*>(dst + core_chunk(n, c, K)) = v;
-    }
+// a row-major [128][K] BF16 tile into the canonical layout at dst (zero rows from `valid` on): thread t takes row
+// t % 128 and half t / 128 of its 16-byte chunks, eight loads in flight
+__device__ __forceinline__ void tc_stage_rows(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int valid,
+                                              int K) {
+  const int n = threadIdx.x & (TC_ROWS - 1), nc = K >> 3, hc = (nc + 1) >> 1;
+  const int cbeg = (threadIdx.x >> 7) * hc, cend = min(nc, cbeg + hc);
+  const uint4* row = reinterpret_cast<const uint4*>(src + (size_t)n * K);
+  for (int c0 = cbeg; c0 < cend; c0 += 8) {
+    uint4 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = (n < valid && c0 + j < cend) ? __ldg(row + c0 + j) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (c0 + j < cend) *reinterpret_cast<uint4*>(dst + core_chunk(n, c0 + j, K)) = v[j];
   }
 }
 
-// one layer: D (tensor memory) = A (128 x K) W^T (W: N x K), issued by thread 0 and committed to the mbarrier
-__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_s, uint32_t w_s, int K, int N, uint32_t mbar) {
+// bulk asynchronous copy of `bytes` (a multiple of 16) from global memory into shared memory, completing as
+// transaction bytes on the mbarrier; issued in pieces of at most 32 KB by one thread, after it announced the
+// total with expect_tx
+__device__ __forceinline__ void tc_bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  const char* g = static_cast<const char*>(src);
+  for (uint32_t o = 0; o < bytes; o += 32768u) {
+    const uint32_t n = bytes - o < 32768u ? bytes - o : 32768u;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst + o),
+                 "l"(g + o), "r"(n), "r"(mbar)
+                 : "memory");
+  }
+}
+
+// one layer: D (tensor memory) = A (128 x K) W^T (W: N x K), issued by thread 0 once the weights have arrived
+// (mbarrier wbar, phase parity wpar) and committed to the mbarrier mbar
+__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_s, uint32_t w_s, int K, int N, uint32_t wbar,
+                                         uint32_t wpar, uint32_t mbar) {
   if (threadIdx.x == 0) {
+    mbar_wait(wbar, wpar);  // on a timeout the MMAs read stale weights; the caller's wait reports it
     const uint32_t idesc = tc_idesc(TC_ROWS, N), sbo = (uint32_t)(K >> 3) * 128;
     for (int kk = 0; kk < (K >> 4); ++kk)
       tc_mma(tmem, tc_sdesc(a_s + kk * 256, 128, sbo), tc_sdesc(w_s + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
@@ -310,22 +350,25 @@ __device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_s, uint32_t w
   }
 }
 
-// bias + ReLU of this thread's accumulator row, as BF16, into the next layer's A operand (K = HID)
-__device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, const float* __restrict__ bias, unsigned char* As,
-                                                   bool ok) {
-  const int r = threadIdx.x;
-  for (int cb = 0; cb < HID; cb += 16) {
-    float v[16];
-    tmem_ld16(trow + cb, v);
-    uint32_t p[8];
+// bias + ReLU of this thread's accumulator row (columns of its half), as BF16, into the next layer's A operand
+// (K = HID); bias in shared memory
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, int row, int c_lo, const float* bias,
+                                                   unsigned char* As, bool ok) {
+  for (int cb = c_lo; cb < c_lo + HID / 2; cb += 32) {
+    float v[32];
+    tmem_ld32(trow + cb, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float x0 = ok ? fmaxf(v[2 * i] + __ldg(bias + cb + 2 * i), 0.f) : __int_as_float(0x7fc00000);
-      const float x1 = ok ? fmaxf(v[2 * i + 1] + __ldg(bias + cb + 2 * i + 1), 0.f) : __int_as_float(0x7fc00000);
-      p[i] = pack_bf16(x0, x1);
+    for (int q = 0; q < 4; ++q) {
+      uint32_t p[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = 8 * q + 2 * i;
+        const float x0 = ok ? fmaxf(v[j] + bias[cb + j], 0.f) : __int_as_float(0x7fc00000);
+        const float x1 = ok ? fmaxf(v[j + 1] + bias[cb + j + 1], 0.f) : __int_as_float(0x7fc00000);
+        p[i] = pack_bf16(x0, x1);
+      }
+      *reinterpret_cast<uint4*>(As + core_chunk(row, (cb >> 3) + q, HID)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
-    *reinterpret_cast<uint4*>(As + core_chunk(r, cb >> 3, HID)) = make_uint4(p[0], p[1], p[2], p[3]);
-    *reinterpret_cast<uint4*>(As + core_chunk(r, (cb >> 3) + 1, HID)) = make_uint4(p[4], p[5], p[6], p[7]);
   }
 }
 
@@ -333,12 +376,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* As = tc_smem;
   unsigned char* Ws = tc_smem + TC_ABYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_ABYTES + TC_WBYTES);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_ABYTES + TC_WBYTES);  // MMA completion
+  uint64_t* wbar = mbar + 1;                                                      // weight arrival
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + TC_ABYTES + TC_WBYTES + 16);
+  float* bs = reinterpret_cast<float*>(tc_smem + TC_ABYTES + TC_WBYTES + 64);  // b1, b2, b3
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = 32 * (warp & 3) + (tid & 31), half = warp >> 2;  // TMEM lane = row; column half
   const int64_t row0 = (int64_t)blockIdx.x * TC_ROWS;
   const int here = (int)min((int64_t)TC_ROWS, a.rows - row0);
-  const uint32_t a_s = smem_u32(As), w_s = smem_u32(Ws), mb = smem_u32(mbar);
+  const uint32_t a_s = smem_u32(As), w_s = smem_u32(Ws), mb = smem_u32(mbar), wb = smem_u32(wbar);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(TC_TMEM_COLS)
@@ -347,56 +393,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
   }
   if (tid == 0) {
     mbar_init(mb, 1);
+    mbar_init(wb, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    tc_bulk_load(w_s, a.W1p, (uint32_t)(HID * a.kinp * 2), wb);  // W1 streams in while the X tile is staged
   }
-  // layer 1 operands: the X tile and W1
-  tc_stage(As, a.X + row0 * a.kinp, TC_ROWS, here, a.kinp);
-  tc_stage(Ws, a.W1, HID, HID, a.kinp);
+  tc_stage_rows(As, a.X + row0 * a.kinp, here, a.kinp);
+  for (int i = tid; i < 3 * HID; i += TC_THREADS) {
+    const int l = i / HID, j = i - l * HID;
+    bs[i] = l == 0 ? __ldg(a.b1 + j) : (l == 1 ? __ldg(a.b2 + j) : (j < a.outp ? __ldg(a.b3 + j) : 0.f));
+  }
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes = its 32 rows
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's 32 lanes = its 32 rows
   bool ok = true;
   uint32_t parity = 0;
 #pragma unroll 1
   for (int layer = 0; layer < 2; ++layer) {
-    tc_layer(tmem, a_s, w_s, layer == 0 ? a.kinp : HID, HID, mb);
+    tc_layer(tmem, a_s, w_s, layer == 0 ? a.kinp : HID, HID, wb, parity, mb);
     ok = mbar_wait(mb, parity) && ok;
-    parity ^= 1u;
     tc_fence_after();
-    // the MMAs have read A and W: the epilogue overwrites A with the hidden layer, then W with the next weights
-    tc_hidden_epilogue(trow, layer == 0 ? a.b1 : a.b2, As, ok);
-    if (layer == 0)
-      tc_stage(Ws, a.W2, HID, HID, HID);
-    else
-      tc_stage(Ws, a.W3, a.outp, a.outp, HID);
+    // the MMAs have read A and W: the next weights stream in during the epilogue, which overwrites A with the
+    // hidden layer
+    if (tid == 0)
+      tc_bulk_load(w_s, layer == 0 ? a.W2p : a.W3p, (uint32_t)((layer == 0 ? HID : a.outp) * HID * 2), wb);
+    parity ^= 1u;
+    tc_hidden_epilogue(trow, row, half * (HID / 2), bs + layer * HID, As, ok);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
   }
-  tc_layer(tmem, a_s, w_s, HID, a.outp, mb);
+  tc_layer(tmem, a_s, w_s, HID, a.outp, wb, parity, mb);
   ok = mbar_wait(mb, parity) && ok;
   tc_fence_after();
   // output layer: bias, then the raw output Y or the scaled preconditioner output z (every lane takes part in
   // the warp-collective tensor-memory loads; only rows of the mesh are stored)
-  const int r = tid;
-  const bool store = r < here;
-  const int64_t row = row0 + r;
-  for (int cb = 0; cb < a.outp; cb += 16) {
-    float v[16];
-    tmem_ld16(trow + cb, v);
+  const bool store = row < here;
+  const int64_t grow = row0 + row;
+  const int ohalf = a.outp >> 1;  // a multiple of 8
+  for (int cb = half * ohalf; cb < (half + 1) * ohalf; cb += 8) {
+    float v[8];
+    tmem_ld8(trow + cb, v);
     if (!store) continue;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 8; ++i) {
       const int col = cb + i;
-      const float y = ok ? v[i] + __ldg(a.b3 + col) : __int_as_float(0x7fc00000);
-      if (a.Y) a.Y[row * a.outp + col] = y;
+      const float y = ok ? v[i] + bs[2 * HID + col] : __int_as_float(0x7fc00000);
+      if (a.Y) a.Y[grow * a.outp + col] = y;
       if (a.z && col < a.nb) {
-        const float zv = a.scale[row] * y;
-        const size_t zi = (size_t)row * a.nb + col;
+        const float zv = a.scale[grow] * y;
+        const size_t zi = (size_t)grow * a.nb + col;
         if (a.z_is_f64) {
           double* zp = static_cast<double*>(a.z) + zi;
           *zp = a.z_accumulate ? *zp + (double)zv : (double)zv;
@@ -540,6 +590,17 @@ __global__ void col_sum(const float* __restrict__ dZ, int64_t rows, int cols, fl
   db[c] = acc;
 }
 
+// W (row-major [N][K] BF16) into the canonical no-swizzle K-major layout of the tcgen05 forward pass: the
+// 16-byte chunk (n, c) at byte (n / 8) (K / 8) 128 + 128 c + 16 (n % 8)
+__global__ void pack_canonical(const __nv_bfloat16* __restrict__ W, int N, int K, __nv_bfloat16* __restrict__ P) {
+  const int nc = K >> 3;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * nc; e += gridDim.x * blockDim.x) {
+    const int n = e / nc, c = e - n * nc;
+    const size_t dst = ((size_t)(n >> 3) * nc * 128 + (size_t)c * 128 + (n & 7) * 16) / 2;
+    *reinterpret_cast<uint4*>(P + dst) = *reinterpret_cast<const uint4*>(W + (size_t)n * K + 8 * c);
+  }
+}
+
 __global__ void adam_step(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                           float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
                           float c2, __nv_bfloat16* __restrict__ wh) {
@@ -575,6 +636,10 @@ struct dg_mlp {
   float* m = nullptr;
   float* v = nullptr;
   __nv_bfloat16* wh = nullptr;  // BF16 copy of the whole block (only W1, W2, W3 are read)
+  // W1, W2, W3 of wh packed for the tcgen05 forward pass (refreshed when wh_version moves on)
+  mutable __nv_bfloat16* whp = nullptr;
+  mutable int64_t packed_version = -1;
+  int64_t wh_version = 0;
   int64_t adam_t = 0;
   // training / inference scratch (grown on demand)
   void* ws = nullptr;
@@ -627,8 +692,32 @@ bool use_tc_forward(const dg_mlp* m, const dgm::FwdArgs& a) {
   return !a.H1 && !a.H2 && m->d.kinp <= dgm::TC_KMAX && m->d.outp <= dgm::HID && !std::getenv("DG_MLP_NO_TCGEN05");
 }
 
-int launch_forward(const dg_mlp* m, const dgm::FwdArgs& a, cudaStream_t s) {
+// the weights of the tcgen05 kernel in its shared-memory layout, repacked on the stream after every change of
+// the BF16 copy
+int packed_weights(const dg_mlp* m, cudaStream_t s, dgm::FwdArgs& a) {
+  const int H = dgm::HID;
+  const int64_t n1 = (int64_t)H * m->d.kinp, n2 = (int64_t)H * H, n3 = (int64_t)m->d.outp * H;
+  if (!m->whp) {
+    if (int rc = cfail(cudaMalloc(&m->whp, (n1 + n2 + n3) * sizeof(__nv_bfloat16)), "cudaMalloc(MLP packed)"))
+      return rc;
+  }
+  if (m->packed_version != m->wh_version) {
+    dgm::pack_canonical<<<64, 256, 0, s>>>(m->wh + m->off[0], H, m->d.kinp, m->whp);
+    dgm::pack_canonical<<<64, 256, 0, s>>>(m->wh + m->off[2], H, H, m->whp + n1);
+    dgm::pack_canonical<<<64, 256, 0, s>>>(m->wh + m->off[4], m->d.outp, H, m->whp + n1 + n2);
+    if (int rc = cfail(cudaGetLastError(), "MLP weight packing")) return rc;
+    m->packed_version = m->wh_version;
+  }
+  a.W1p = m->whp;
+  a.W2p = m->whp + n1;
+  a.W3p = m->whp + n1 + n2;
+  return 0;
+}
+
+int launch_forward(const dg_mlp* m, const dgm::FwdArgs& a_in, cudaStream_t s) {
+  dgm::FwdArgs a = a_in;
   if (use_tc_forward(m, a)) {
+    if (int rc = packed_weights(m, s, a)) return rc;
     static bool tc_attr = false;
     if (!tc_attr) {
       if (int rc = cfail(cudaFuncSetAttribute(dgm::mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -736,6 +825,7 @@ void free_mlp(dg_mlp* m) {
   cudaFree(m->m);
   cudaFree(m->v);
   cudaFree(m->wh);
+  cudaFree(m->whp);
   cudaFree(m->ws);
   delete m;
 }
@@ -785,6 +875,7 @@ int dg_mlp_create(int32_t k, uint64_t seed, dg_mlp** out) {
   if (!rc) rc = cfail(cudaMemset(m->g, 0, o * sizeof(float)), "MLP memset");
   if (!rc) {
     dgm::to_bf16<<<256, 256>>>(m->w, m->wh, o);
+    ++m->wh_version;
     rc = cfail(cudaDeviceSynchronize(), "MLP init");
   }
   if (rc) {
@@ -829,6 +920,7 @@ int dg_mlp_params(dg_mlp* m, float* host, int32_t direction, float* t_scale) {
     rc = cfail(cudaMemcpy(m->w, host, bytes, cudaMemcpyHostToDevice), "MLP upload");
     if (!rc) {
       dgm::to_bf16<<<256, 256>>>(m->w, m->wh, m->nparam);
+      ++m->wh_version;
       rc = cfail(cudaDeviceSynchronize(), "MLP bf16 refresh");
     }
     if (!rc && t_scale) m->t_scale = *t_scale;
@@ -917,6 +1009,7 @@ int dg_mlp_train(dg_mlp* m, const void* X, const float* T, int64_t rows, const d
       ++m->adam_t;
       const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
       dgm::adam_step<<<512, 256, 0, s>>>(m->w, m->g, m->m, m->v, m->nparam, (float)o->lr, b1, b2, eps, c1, c2, m->wh);
+      ++m->wh_version;
       if ((rc = cfail(cudaGetLastError(), "Adam step"))) return rc;
     }
     const double mean = sum / nbatch;
@@ -1043,6 +1136,7 @@ int dg_mlp_load(const char* path, dg_mlp** out) {
            cudaMemcpy(m->v, vv.data(), m->nparam * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
       if (ok) {
         dgm::to_bf16<<<256, 256>>>(m->w, m->wh, m->nparam);
+        ++m->wh_version;
         ok = cudaDeviceSynchronize() == cudaSuccess;
       }
       m->t_scale = ts;
