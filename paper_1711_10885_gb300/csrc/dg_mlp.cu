@@ -430,30 +430,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
   tc_layer(tmem, a_s, w_s, HID, a.outp, wb, parity, mb);
   ok = mbar_wait(mb, parity) && ok;
   tc_fence_after();
-  // output layer: bias, then the raw output Y or the scaled preconditioner output z (every lane takes part in
-  // the warp-collective tensor-memory loads; only rows of the mesh are stored)
-  const bool store = row < here;
-  const int64_t grow = row0 + row;
+  // output layer: the accumulator rows plus bias go through shared memory (A and W are free now; rows padded by
+  // four floats), then the tile's block of Y (rows x outp) or z (cells x nb, scaled) is written contiguously
+  float* Ys = reinterpret_cast<float*>(tc_smem);
+  const int ys = a.outp + 4;
   const int ohalf = a.outp >> 1;  // a multiple of 8
   for (int cb = half * ohalf; cb < (half + 1) * ohalf; cb += 8) {
     float v[8];
     tmem_ld8(trow + cb, v);
-    if (!store) continue;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int col = cb + i;
-      const float y = ok ? v[i] + bs[2 * HID + col] : __int_as_float(0x7fc00000);
-      if (a.Y) a.Y[grow * a.outp + col] = y;
-      if (a.z && col < a.nb) {
-        const float zv = a.scale[grow] * y;
-        const size_t zi = (size_t)grow * a.nb + col;
-        if (a.z_is_f64) {
-          double* zp = static_cast<double*>(a.z) + zi;
-          *zp = a.z_accumulate ? *zp + (double)zv : (double)zv;
-        } else {
-          float* zp = static_cast<float*>(a.z) + zi;
-          *zp = a.z_accumulate ? *zp + zv : zv;
-        }
+    for (int i = 0; i < 8; ++i) v[i] = ok ? v[i] + bs[2 * HID + cb + i] : __int_as_float(0x7fc00000);
+    *reinterpret_cast<float4*>(Ys + row * ys + cb) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(Ys + row * ys + cb + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  }
+  __syncthreads();
+  if (a.Y) {
+    float* dst = a.Y + row0 * a.outp;
+    for (int e = tid; e < here * a.outp; e += TC_THREADS) {
+      const int r = e / a.outp, c = e - r * a.outp;
+      dst[e] = Ys[r * ys + c];
+    }
+  }
+  if (a.z) {
+    for (int e = tid; e < here * a.nb; e += TC_THREADS) {
+      const int r = e / a.nb, c = e - r * a.nb;
+      const float zv = a.scale[row0 + r] * Ys[r * ys + c];
+      const size_t zi = (size_t)row0 * a.nb + e;
+      if (a.z_is_f64) {
+        double* zp = static_cast<double*>(a.z) + zi;
+        *zp = a.z_accumulate ? *zp + (double)zv : (double)zv;
+      } else {
+        float* zp = static_cast<float*>(a.z) + zi;
+        *zp = a.z_accumulate ? *zp + zv : zv;
       }
     }
   }
