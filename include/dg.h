@@ -179,6 +179,10 @@ typedef struct {
   double fallback_ratio;  /* DG_PRECOND_MLP: if one inner cycle (MIXED) or restart cycle (FP64) reduces
                              its residual by less than this factor (e.g. 0.5), the rest of the solve
                              uses block-Jacobi when dg_precond_setup was called; 0 = never          */
+  int32_t inner_block_precision; /* MIXED with block-Jacobi: 0 = the inner FP32 solve applies FP16 copies of
+                             the inverse blocks, each divided by its largest |entry| (half the bytes of
+                             this bandwidth-bound product; a flexible method tolerates the ~5e-4 relative
+                             rounding of the preconditioner); 1 = the FP32 blocks                       */
 } dg_solve_opts;
 
 typedef struct {

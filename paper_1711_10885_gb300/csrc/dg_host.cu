@@ -146,6 +146,8 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->work_tr);
   cudaFree(h->bj64);
   cudaFree(h->bj32);
+  cudaFree(h->bj16);
+  cudaFree(h->bj16s);
   cudaFree(h->bsc);
   cudaFree(h->bface);
   cudaFree(h->bscX);

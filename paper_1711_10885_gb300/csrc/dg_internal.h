@@ -79,6 +79,10 @@ struct dg_handle {
   // block-Jacobi preconditioner: per cell (A_TT^{-1})^T, row-major [ncell][N^3][N^3], FP64 and FP32
   void* bj64 = nullptr;
   void* bj32 = nullptr;
+  // FP16 copy divided by each block's largest |entry| (bj16s: the FP32 factors), rows padded to a multiple of 8;
+  // used by the FP32 inner solves of DG_SOLVE_MIXED
+  void* bj16 = nullptr;
+  void* bj16s = nullptr;
   // Krylov workspace (grown on demand, freed by dg_destroy)
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -102,6 +106,7 @@ int launch_diag_blocks_f64(const dg_handle* h, double* out, int cell_base, int n
 // block-Jacobi application z = M r (precision by type), M from dg_precond_setup
 int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s);
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
+int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 // F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null);
 // with vol = 1 instead of |T| and no g this is the L2 projection z_i = (f, phi_i)_T / |T|
 int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <string>
 
+#include <cuda_fp16.h>
+
 #include "dg_internal.h"
 
 namespace dgi {
@@ -185,6 +187,113 @@ __global__ void __launch_bounds__(128) bj_apply_f32v(const float* __restrict__ M
     if (4 * t + c < n) zc[c] = v[c];
 }
 
+// FP16 copy of the inverse blocks for the FP32 inner solves of DG_SOLVE_MIXED: each block is divided by its
+// largest |entry| (kept as an FP32 factor per cell), so FP16's range holds any diffusion contrast; rows padded
+// to np8 = n rounded up to 8 (16-byte rows).  One CTA per block.
+__global__ void __launch_bounds__(256) cast_blocks_f16(const double* __restrict__ a, __half* __restrict__ b,
+                                                       float* __restrict__ scale, int n, int np8) {
+  __shared__ double red[8];
+  const size_t blk = blockIdx.x;
+  const double* A = a + blk * n * n;
+  double mx = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) mx = fmax(mx, fabs(A[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    red[0] = m > 0.0 ? m : 1.0;
+  }
+  __syncthreads();
+  const double sc = red[0], inv = 1.0 / sc;
+  if (threadIdx.x == 0) scale[blk] = (float)sc;
+  __half* B = b + blk * n * np8;
+  for (int e = threadIdx.x; e < n * np8; e += blockDim.x) {
+    const int row = e / np8, col = e - row * np8;
+    B[e] = __double2half(col < n ? A[(size_t)row * n + col] * inv : 0.0);
+  }
+}
+
+// FP32 block-Jacobi application from the FP16 blocks: z_T = s_T M16_T^T r_T.  Thread column group t owns output
+// columns 8t .. 8t+7 (one 16-byte load per row); with at most 16 column groups a warp splits the rows between
+// its two halves and adds the halves' sums at the end.  cpc cells share a CTA of 128 threads.
+__global__ void __launch_bounds__(128) bj_apply_f16(const __half* __restrict__ M, const float* __restrict__ scale,
+                                                    const float* __restrict__ r, float* __restrict__ z,
+                                                    int64_t ncell, int n, int np8, int wpc, int cpc, int rsplit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* rs = reinterpret_cast<float*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lc = warp / wpc, wi = warp - lc * wpc;
+  const int64_t cell = (int64_t)blockIdx.x * cpc + lc;
+  const bool active = lc < cpc && cell < ncell;
+  float* rc = rs + lc * np8;
+  if (active)
+    for (int j = wi * 32 + lane; j < n; j += wpc * 32) rc[j] = r[cell * n + j];
+  __syncthreads();
+  if (!active) return;
+  const int ct = np8 / 8;
+  const int t = rsplit == 2 ? (lane & 15) : wi * 32 + lane;  // column group
+  const int part = rsplit == 2 ? (lane >> 4) : 0;           // rows part, part + rsplit, ...
+  const bool cols = t < ct;
+  const uint4* Mc = reinterpret_cast<const uint4*>(M + (size_t)cell * n * np8) + t;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (cols) {
+    int j = part;
+    for (; j + 3 * rsplit < n; j += 4 * rsplit) {
+      uint4 m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m[u] = __ldg(Mc + (size_t)(j + u * rsplit) * ct);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float rv = rc[j + u * rsplit];
+        const __half2* h2 = reinterpret_cast<const __half2*>(&m[u]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 f = __half22float2(h2[q]);
+          acc[2 * q] = fmaf(f.x, rv, acc[2 * q]);
+          acc[2 * q + 1] = fmaf(f.y, rv, acc[2 * q + 1]);
+        }
+      }
+    }
+    for (; j < n; j += rsplit) {
+      const uint4 m = __ldg(Mc + (size_t)j * ct);
+      const float rv = rc[j];
+      const __half2* h2 = reinterpret_cast<const __half2*>(&m);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 f = __half22float2(h2[q]);
+        acc[2 * q] = fmaf(f.x, rv, acc[2 * q]);
+        acc[2 * q + 1] = fmaf(f.y, rv, acc[2 * q + 1]);
+      }
+    }
+  }
+  if (rsplit == 2) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+  }
+  if (!cols || part != 0) return;
+  const float sc = scale[cell];
+  float* zc = z + cell * n + 8 * t;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (8 * t + c < n) zc[c] = sc * acc[c];
+}
+
+int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
+  const int n = h->N * h->N * h->N, np8 = (n + 7) / 8 * 8, ct = np8 / 8;
+  const int rsplit = ct <= 16 ? 2 : 1;
+  const int wpc = rsplit == 2 ? 1 : (ct + 31) / 32;
+  const int cpc = wpc >= 4 ? 1 : 4 / wpc;
+  const unsigned grid = (unsigned)((h->ncell + cpc - 1) / cpc);
+  bj_apply_f16<<<grid, 32 * wpc * cpc, (size_t)cpc * np8 * sizeof(float), s>>>(
+      static_cast<const __half*>(h->bj16), static_cast<const float*>(h->bj16s), r, z, h->ncell, n, np8, wpc, cpc,
+      rsplit);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (FP16 blocks)");
+}
+
 int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s) {
   const int n = h->N * h->N * h->N;
   const int threads = n >= 256 ? 256 : ((n + 31) / 32) * 32;
@@ -244,6 +353,12 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
     e = cudaMalloc(&h->bj32, (size_t)h->ncell * n * np * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(block-Jacobi FP32)");
   }
+  const int np8 = (n + 7) / 8 * 8;
+  if (!h->bj16) {
+    e = cudaMalloc(&h->bj16, (size_t)h->ncell * n * np8 * sizeof(__half));
+    if (e == cudaSuccess) e = cudaMalloc(&h->bj16s, (size_t)h->ncell * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(block-Jacobi FP16)");
+  }
   // assemble in chunks of cells: each chunk needs (cells * n) virtual cells of work buffers
   int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(h->ncell, h->ncell / n));
   double *V = nullptr, *tr = nullptr;
@@ -274,6 +389,12 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
     if (e == cudaSuccess) {
       cast_blocks<<<152 * 8, 256, 0, s>>>(static_cast<const double*>(h->bj64), static_cast<float*>(h->bj32), h->ncell,
                                          n, np);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      cast_blocks_f16<<<(unsigned)h->ncell, 256, 0, s>>>(static_cast<const double*>(h->bj64),
+                                                          static_cast<__half*>(h->bj16), static_cast<float*>(h->bj16s),
+                                                          n, np8);
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) rc = cuda_fail(e, "block inversion");

@@ -233,6 +233,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   const int m = o->restart > 0 ? o->restart : 30;
   const int mo = o->outer_restart > 0 ? o->outer_restart : 10;
   if (m > 60 || mo > 60 || (o->mode != DG_SOLVE_FP64 && o->mode != DG_SOLVE_MIXED) ||
+      (o->inner_block_precision != 0 && o->inner_block_precision != 1) ||
       (o->preconditioner != DG_PRECOND_NONE && o->preconditioner != DG_PRECOND_BLOCK_JACOBI &&
        o->preconditioner != DG_PRECOND_MLP && o->preconditioner != DG_PRECOND_BJ_MLP) ||
       !(o->rtol > 0) || (o->mode == DG_SOLVE_MIXED && !(o->inner_rtol > 0 && o->inner_rtol < 1))) {
@@ -336,14 +337,19 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     float* rhs32 = Z32 + (pc ? (size_t)m * n : 0);
     float* e32 = rhs32 + n;
     std::function<int(const float*, float*)> M32;
+    // block-Jacobi inside the FP32 inner solve: the FP16 blocks (half the bytes of this HBM-bound product) unless
+    // the caller asked for the FP32 ones
+    auto bj_inner = [&](const float* r, float* z) {
+      return o->inner_block_precision == 1 ? precond_bj_f32(h, r, z, s) : precond_bj_f16(h, r, z, s);
+    };
     if (pc)
       M32 = [&](const float* r, float* z) {
-        if (!use_mlp || first_only) return with_bj || !use_mlp ? precond_bj_f32(h, r, z, s)
+        if (!use_mlp || first_only) return with_bj || !use_mlp ? bj_inner(r, z)
                                                              : cuda_check(cudaMemcpyAsync(z, r, n * sizeof(float),
                                                                                           cudaMemcpyDeviceToDevice, s),
                                                                           "copy");
         if (!with_bj) return mlp_apply_impl(mlp, h, r, z, DG_F32, 0, s);
-        int e2 = precond_bj_f32(h, r, z, s);
+        int e2 = bj_inner(r, z);
         return e2 ? e2 : mlp_apply_impl(mlp, h, r, z, DG_F32, 1, s);
       };
     std::function<int(const double*, double*)> P = [&](const double* v, double* z) -> int {

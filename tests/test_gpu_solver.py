@@ -58,7 +58,7 @@ def test_block_jacobi_matches_oracle_blocks(dg, n, k):
     op.close()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp64_bj", "mixed_bj", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_bj", "mixed_bj", "mixed_bj32", "mixed"])
 def test_fgmres_solution_matches_dense_solve(dg, mode):
     w = inputs.small_case(n=(3, 2, 2), k=2, seed=8, b=(1.0, 0.5, 0.25), f_kind="sines")
     w.f_params = inputs.sine_modes(9)
@@ -67,12 +67,14 @@ def test_fgmres_solution_matches_dense_solve(dg, mode):
     F = oracle.rhs(pr, inputs.f_at(w, oracle.volume_points(pr)), None)
     x_ref = np.linalg.solve(A, F)
     op = dg.operator_for(w)
-    pc = dg.DG_PRECOND_BLOCK_JACOBI if mode.endswith("bj") else dg.DG_PRECOND_NONE
+    # mixed_bj: the inner FP32 solve applies the FP16 copies of the inverse blocks (the default); mixed_bj32: FP32
+    pc = dg.DG_PRECOND_BLOCK_JACOBI if mode.endswith("bj") or mode.endswith("bj32") else dg.DG_PRECOND_NONE
     if pc:
         op.precond_setup()
     x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
     m = dg.DG_SOLVE_MIXED if mode.startswith("mixed") else dg.DG_SOLVE_FP64
-    st = op.solve(x, mode=m, preconditioner=pc, rtol=1e-12, restart=20, outer_restart=8, inner_rtol=1e-2)
+    st = op.solve(x, mode=m, preconditioner=pc, rtol=1e-12, restart=20, outer_restart=8, inner_rtol=1e-2,
+                  inner_block_precision=1 if mode.endswith("bj32") else 0)
     assert st["rc"] == 0 and st["rel_residual"] <= 1e-12
     xs = x.cpu().numpy()
     # field error bound: ||x - x*|| <= cond(A) * rtol * ||x*||; checked directly against the LU solution
