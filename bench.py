@@ -244,6 +244,18 @@ def run_profile(args):
         print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
         op.close()
         return
+    if args.small:
+        # the 8^3-cell Q3 unit-cube workload: W + K residual applies
+        w = inputs.unit_cube_q3_8()
+        op = dg.operator_for(w)
+        u = torch.tensor(w.u, device="cuda")
+        r = torch.empty_like(u)
+        for _ in range(args.warmup + args.steps):
+            op.apply_residual(u, r)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_max": float(r.abs().max())}))
+        op.close()
+        return
     if args.mlp_forward:
         # network inference on 262144 feature rows (k = 4): W + K forward passes
         mlp = dg.MLP(4, seed=7)
@@ -1128,6 +1140,7 @@ def main():
     ap.add_argument("--no-problem-b", action="store_true",
                     help="skip the Problem B (point-wise coefficients) and Problem C (multilinear cells) sections")
     ap.add_argument("--mlp-forward", action="store_true", help="print only the network inference timing")
+    ap.add_argument("--small", action="store_true", help="with --profile: W + K applies of the 8^3 Q3 workload")
     ap.add_argument("--problem-c", type=int, default=None, metavar="N",
                     help="print only the Problem C section on N^3 multilinear cells (k = 7, m = 10)")
     ap.add_argument("--problem-b", type=int, default=None, metavar="N",
