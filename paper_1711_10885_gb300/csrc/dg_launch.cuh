@@ -91,30 +91,36 @@ dgk::Geo<T> make_geo(const dg_handle* h) {
   return g;
 }
 
-// shared memory of the two kernels for M points per direction (CPB = Launch<M>::CPB cells per CTA)
-template <int M, typename T>
+// shared memory of the two kernels for M points per direction and CPB cells per CTA
+template <int M, typename T, int CPB = dgk::Launch<M>::CPB>
 size_t cell_smem() {
-  return 2 * (size_t)dgk::Launch<M>::CPB * dgk::Lay<M>::CS * sizeof(T);
+  return 2 * (size_t)CPB * dgk::Lay<M>::CS * sizeof(T);
 }
-template <int M, typename T>
+template <int M, typename T, int CPB = dgk::Launch<M>::CPB>
 size_t face_smem() {
-  return (size_t)dgk::Launch<M>::CPB * dgk::Lay<M>::CS * sizeof(T);
+  return (size_t)CPB * dgk::Lay<M>::CS * sizeof(T);
 }
 
-template <int N, typename T, typename TV = T, int M = N, bool VB = false>
+// cells per CTA of the small-mesh variant of the FP64 kernels: a quarter of the full tile, so that meshes of
+// fewer than 152 full tiles still spread over the 152 SMs (each SM issues only two FP64 FMAs per clock)
+template <int M>
+constexpr int small_cpb() {
+  return dgk::Launch<M>::CPB / 4 > 0 ? dgk::Launch<M>::CPB / 4 : 1;
+}
+
+template <int N, typename T, typename TV = T, int M = N, bool VB = false, int CPB = dgk::Launch<M>::CPB>
 int set_smem_attrs() {
   static bool done = false;  // per instantiation; attributes are per function
   if (done) return 0;
-  constexpr int CPB = dgk::Launch<M>::CPB;
   cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<M, T>());
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<M, T, CPB>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel)");
   e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, true>(),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T>());
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T, CPB>());
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
   if constexpr (!VB) {
     e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, false>(),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T>());
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T, CPB>());
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
   }
   done = true;
@@ -123,17 +129,16 @@ int set_smem_attrs() {
 
 // face kernel launch: the periodic-aware variant when the mesh has a periodic axis (always for the
 // velocity field kernels)
-template <int N, typename T, typename TV, int M, bool VB>
+template <int N, typename T, typename TV, int M, bool VB, int CPB = dgk::Launch<M>::CPB>
 void launch_face(const dg_handle* h, const dgk::TabNM<N, M, T>& tb, const dgk::Geo<T>& geo,
                  const dgk::FaceArgs<T, TV>& fa, unsigned grid, cudaStream_t s) {
-  constexpr int CPB = dgk::Launch<M>::CPB;
   const bool per = h->periodic[0] || h->periodic[1] || h->periodic[2];
   if (VB || per) {
     dgk::face_kernel_for<N, T, CPB, TV, M, VB, true>()
-        <<<grid, dgk::Launch<M>::THREADS, face_smem<M, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
+        <<<grid, CPB * M * M, face_smem<M, T, CPB>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
   } else if constexpr (!VB) {
     dgk::face_kernel_for<N, T, CPB, TV, M, VB, false>()
-        <<<grid, dgk::Launch<M>::THREADS, face_smem<M, T>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
+        <<<grid, CPB * M * M, face_smem<M, T, CPB>(), s>>>(tb, geo, fa, dgk::SelfArgs{0, 0});
   }
 }
 
@@ -173,11 +178,10 @@ dgk::Geo<T> geo_for(const dg_handle* h) {
   return geo;
 }
 
-template <int N, typename T, typename TV = T, int M = N, bool VB = false>
+template <int N, typename T, typename TV = T, int M = N, bool VB = false, int CPB = dgk::Launch<M>::CPB>
 int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s,
             const StageArgs* st = nullptr) {
-  if (int rc = set_smem_attrs<N, T, TV, M, VB>()) return rc;
-  constexpr int CPB = dgk::Launch<M>::CPB;
+  if (int rc = set_smem_attrs<N, T, TV, M, VB, CPB>()) return rc;
   const Buffers& bf = buffers_for<T>(h);
   const auto tb = make_tab<N, T, M>(h->tab);
   const auto geo = geo_for<T, VB>(h);
@@ -185,7 +189,7 @@ int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaSt
   T* V = static_cast<T*>(h->work_V);
   T* tr = static_cast<T*>(h->work_tr);
   if (stages & 1)
-    dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB><<<grid, dgk::Launch<M>::THREADS, cell_smem<M, T>(), s>>>(
+    dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB><<<grid, CPB * M * M, cell_smem<M, T, CPB>(), s>>>(
         tb, geo, z, static_cast<const T*>(bf.D), V, tr, dgk::SelfArgs{0, 0});
   dgk::FaceArgs<T, TV> fa;
   fa.V = V;
@@ -208,10 +212,21 @@ int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaSt
     fa.cu = st->cu;
     fa.cr = st->cr;
   }
-  if (stages & 2) launch_face<N, T, TV, M, VB>(h, tb, geo, fa, grid, s);
+  if (stages & 2) launch_face<N, T, TV, M, VB, CPB>(h, tb, geo, fa, grid, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");
   return 0;
+}
+
+// FP64 applies: meshes with fewer full tiles than SMs take the small-tile variant
+template <int N, typename T, typename TV>
+int apply_sized(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s, const StageArgs* st) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<TV, double>::value &&
+                small_cpb<N>() < dgk::Launch<N>::CPB) {
+    if (h->ncell < (int64_t)152 * dgk::Launch<N>::CPB)
+      return apply_n<N, T, TV, N, false, small_cpb<N>()>(h, z, y, mode, stages, s, st);
+  }
+  return apply_n<N, T, TV>(h, z, y, mode, stages, s, st);
 }
 
 template <int N, typename T, int M = N, bool VB = false>
@@ -276,16 +291,16 @@ template <typename T, typename TV = T>
 int apply_dispatch(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s,
                    const StageArgs* st = nullptr) {
   switch (h->N) {
-    case 2: return apply_n<2, T, TV>(h, z, y, mode, stages, s, st);
-    case 3: return apply_n<3, T, TV>(h, z, y, mode, stages, s, st);
-    case 4: return apply_n<4, T, TV>(h, z, y, mode, stages, s, st);
-    case 5: return apply_n<5, T, TV>(h, z, y, mode, stages, s, st);
-    case 6: return apply_n<6, T, TV>(h, z, y, mode, stages, s, st);
-    case 7: return apply_n<7, T, TV>(h, z, y, mode, stages, s, st);
-    case 8: return apply_n<8, T, TV>(h, z, y, mode, stages, s, st);
-    case 9: return apply_n<9, T, TV>(h, z, y, mode, stages, s, st);
-    case 10: return apply_n<10, T, TV>(h, z, y, mode, stages, s, st);
-    case 11: return apply_n<11, T, TV>(h, z, y, mode, stages, s, st);
+    case 2: return apply_sized<2, T, TV>(h, z, y, mode, stages, s, st);
+    case 3: return apply_sized<3, T, TV>(h, z, y, mode, stages, s, st);
+    case 4: return apply_sized<4, T, TV>(h, z, y, mode, stages, s, st);
+    case 5: return apply_sized<5, T, TV>(h, z, y, mode, stages, s, st);
+    case 6: return apply_sized<6, T, TV>(h, z, y, mode, stages, s, st);
+    case 7: return apply_sized<7, T, TV>(h, z, y, mode, stages, s, st);
+    case 8: return apply_sized<8, T, TV>(h, z, y, mode, stages, s, st);
+    case 9: return apply_sized<9, T, TV>(h, z, y, mode, stages, s, st);
+    case 10: return apply_sized<10, T, TV>(h, z, y, mode, stages, s, st);
+    case 11: return apply_sized<11, T, TV>(h, z, y, mode, stages, s, st);
     default: set_error("unsupported degree"); return DG_ERR_INVALID_ARG;
   }
 }
