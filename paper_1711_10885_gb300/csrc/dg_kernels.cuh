@@ -627,7 +627,7 @@ dg_cell_kernel_td(const __grid_constant__ TabNM<N, M, T> tb, const __grid_consta
 }
 
 template <int N, typename T, bool SELF = false, int CPB = Launch<N>::CPB, typename TV = T, int M = N, bool VB = false>
-__global__ void __launch_bounds__(CPB * M * M)
+__global__ void __launch_bounds__(CPB * M * M, (N == 8 && M == 8 && sizeof(T) == 8 && !VB) ? 4 : 1)
 dg_cell_kernel(const __grid_constant__ TabNM<N, M, T> tb, const __grid_constant__ Geo<T> g, const TV* __restrict__ z,
                const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces, SelfArgs sa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
