@@ -330,8 +330,8 @@ def run_profile(args):
 
 def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10, with_fp64=True):
     """Mixed-precision vs plain FP64 block-Jacobi FGMRES on the 48^3 Q5 workload (sine source, log-normal D).
-    The mixed solve runs with the FP16 inverse blocks in its inner FP32 solve (the default) and with the FP32
-    ones; with_fp64=False skips the two-minute plain FP64 solve."""
+    The mixed solve runs with its default inner block inverse (fast diagonalisation) and with the FP32 dense
+    blocks; with_fp64=False skips the two-minute plain FP64 solve."""
     import torch
 
     from paper_1711_10885_gb300 import dg, inputs
@@ -361,8 +361,8 @@ def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10, w
     if with_fp64:
         out["field_diff_mixed_vs_fp64"] = float((xs["mixed"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
         out["speedup_mixed_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
-    out["field_diff_fp16_vs_fp32_blocks"] = float((xs["mixed"] - xs["mixed_fp32_blocks"]).abs().max()
-                                                  / xs["mixed_fp32_blocks"].abs().max())
+    out["field_diff_default_vs_fp32_blocks"] = float((xs["mixed"] - xs["mixed_fp32_blocks"]).abs().max()
+                                                     / xs["mixed_fp32_blocks"].abs().max())
     # operator throughput at this size
     for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
         u = torch.rand(w.ndof, dtype=dt, device="cuda")

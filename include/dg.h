@@ -179,10 +179,13 @@ typedef struct {
   double fallback_ratio;  /* DG_PRECOND_MLP: if one inner cycle (MIXED) or restart cycle (FP64) reduces
                              its residual by less than this factor (e.g. 0.5), the rest of the solve
                              uses block-Jacobi when dg_precond_setup was called; 0 = never          */
-  int32_t inner_block_precision; /* MIXED with block-Jacobi: 0 = the inner FP32 solve applies FP16 copies of
-                             the inverse blocks, each divided by its largest |entry| (half the bytes of
-                             this bandwidth-bound product; a flexible method tolerates the ~5e-4 relative
-                             rounding of the preconditioner); 1 = the FP32 blocks                       */
+  int32_t inner_block_precision; /* MIXED with block-Jacobi, the block inverse applied in the inner FP32
+                             solve: 0 = by fast diagonalisation (each diagonal block is a Kronecker sum of
+                             three 1D cell operators; six complex FP32 1D contractions per cell), or the
+                             FP16 blocks if it could not be built; 1 = the FP32 dense blocks; 2 = FP16
+                             copies of the dense blocks, each divided by its largest |entry| (half the
+                             bytes of that bandwidth-bound product).  A flexible method tolerates the
+                             rounding of the preconditioner.                                           */
 } dg_solve_opts;
 
 typedef struct {
@@ -204,7 +207,11 @@ typedef struct {
  * DG_ERR_NAN if a block is singular.  Synchronises `stream`. */
 int dg_precond_setup(dg_handle* h, int32_t kind, void* stream);
 
-/* z = M^{-1} r with the block-Jacobi preconditioner (r, z device vectors of the given precision). */
+/* z = M^{-1} r with the block-Jacobi preconditioner (r, z device vectors of the given precision).  DG_F64
+ * applies the dense FP64 inverse blocks; DG_F32 the exact block inverse by fast diagonalisation (every
+ * diagonal block is a Kronecker sum of three 1D cell operators, inverted through their eigen-decompositions
+ * with complex FP32 contractions), or the FP32 dense blocks where the 1D operators could not be
+ * diagonalised. */
 int dg_precond_apply(dg_handle* h, const void* r_dev, void* z_dev, int32_t precision, void* stream);
 
 /* Solve A x = b (b_dev NULL: b = F, the right hand side of dg_setup) with FGMRES; x_dev holds the

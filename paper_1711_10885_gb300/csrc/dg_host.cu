@@ -148,6 +148,7 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->bj32);
   cudaFree(h->bj16);
   cudaFree(h->bj16s);
+  cudaFree(h->fdm);
   cudaFree(h->bsc);
   cudaFree(h->bface);
   cudaFree(h->bscX);

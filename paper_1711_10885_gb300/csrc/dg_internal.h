@@ -83,6 +83,8 @@ struct dg_handle {
   // used by the FP32 inner solves of DG_SOLVE_MIXED
   void* bj16 = nullptr;
   void* bj16s = nullptr;
+  // exact block inverse by fast diagonalisation (complex FP32 tables, see dg_precond.cu); null if not built
+  void* fdm = nullptr;
   // Krylov workspace (grown on demand, freed by dg_destroy)
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -107,6 +109,7 @@ int launch_diag_blocks_f64(const dg_handle* h, double* out, int cell_base, int n
 int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s);
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s);
+int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 // F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null);
 // with vol = 1 instead of |T| and no g this is the L2 projection z_i = (f, phi_i)_T / |T|
 int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,

@@ -3,9 +3,12 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include <cuda_fp16.h>
 
+#include "dg_eig.h"
 #include "dg_internal.h"
 
 namespace dgi {
@@ -281,6 +284,207 @@ __global__ void __launch_bounds__(128) bj_apply_f16(const __half* __restrict__ M
     if (8 * t + c < n) zc[c] = sc * acc[c];
 }
 
+// ---------------------------------------------------------------------------------------------
+// Exact block inverse by fast diagonalisation.  On an axis-parallel cell with a per-cell scalar D and a constant
+// velocity, every term of the diagonal block A_TT (the volume term and the self-coupling of the cell's faces,
+// eq. blf) is a tensor product of a 1D matrix along one axis with identities (the basis is orthonormal), so
+//   A_TT = I (x) I (x) A_x + I (x) A_y (x) I + A_z (x) I (x) I + c |T| I
+// with per-cell 1D operators A_r = V_r diag(lambda_r) V_r^{-1}, and
+//   A_TT^{-1} = (V_z (x) V_y (x) V_x) diag(1 / (lambda_x + lambda_y + lambda_z + c |T|)) (W_z (x) W_y (x) W_x),
+// W_r = V_r^{-1}: six 1D complex contractions per cell instead of a dense n^3 x n^3 product, from 3 (2 n^2 + n)
+// complex numbers per cell instead of n^6.
+// Table per cell (float2 = complex FP32): for r = 0..2: W_r [n][n], V_r [n][n], lambda_r [n]; then c |T|.
+// ---------------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) fdm_apply(const float2* __restrict__ tab, const float* __restrict__ r,
+                                                 float* __restrict__ z, int64_t ncell, int cpb) {
+  constexpr int NN = N * N, N3 = NN * N, TS = 3 * (2 * NN + N) + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* U = reinterpret_cast<float2*>(smem_raw);  // [cpb][N3]
+  float2* T = U + (size_t)cpb * N3;                  // [cpb][TS]
+  const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
+  const int64_t cell0 = (int64_t)blockIdx.x * cpb;
+  const int here = (int)min((int64_t)cpb, ncell - cell0);
+  for (int e = threadIdx.x; e < here * TS; e += blockDim.x) T[e] = tab[cell0 * TS + e];
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) U[e] = make_float2(r[cell0 * N3 + e], 0.f);
+  __syncthreads();
+  const bool active = lc < here;
+  float2* u = U + lc * N3;
+  const float2* tb = T + lc * TS;
+  // line of this thread along axis d: the N points with the other two indices (a, b) = (t % N, t / N)
+  auto base = [&](int d) { return d == 0 ? N * t : (d == 1 ? (t % N) + NN * (t / N) : t); };
+  auto stride = [](int d) { return d == 0 ? 1 : (d == 1 ? N : NN); };
+  auto pass = [&](int d, const float2* Mx) {  // u_line <- Mx u_line (complex N x N)
+    if (active) {
+      const int bs = base(d), st = stride(d);
+      float2 x[N], y[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) x[l] = u[bs + l * st];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const float2 m = Mx[i * N + l];
+          re = fmaf(m.x, x[l].x, fmaf(-m.y, x[l].y, re));
+          im = fmaf(m.x, x[l].y, fmaf(m.y, x[l].x, im));
+        }
+        y[i] = make_float2(re, im);
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) u[bs + i * st] = y[i];
+    }
+    __syncthreads();
+  };
+  for (int d = 0; d < 3; ++d) pass(d, tb + d * (2 * NN + N));  // W_d
+  if (active) {
+    // divide by lambda_x(a) + lambda_y(b) + lambda_z(c) + c |T| along this thread's z-line (a, b)
+    const float2* lx = tb + 0 * (2 * NN + N) + 2 * NN;
+    const float2* ly = tb + 1 * (2 * NN + N) + 2 * NN;
+    const float2* lz = tb + 2 * (2 * NN + N) + 2 * NN;
+    const float cs = tb[TS - 1].x;
+    const int a = t % N, b = t / N;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      const float dr = lx[a].x + ly[b].x + lz[c].x + cs, di = lx[a].y + ly[b].y + lz[c].y;
+      const float inv = 1.f / (dr * dr + di * di);
+      const float2 v = u[a + N * b + NN * c];
+      u[a + N * b + NN * c] = make_float2((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
+    }
+  }
+  __syncthreads();
+  for (int d = 0; d < 3; ++d) pass(d, tb + d * (2 * NN + N) + NN);  // V_d
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) z[cell0 * N3 + e] = U[e].x;
+}
+
+namespace {
+
+// 1D cell operator of axis r for cell `cell` (row = test function, column = trial function), from the 1D
+// tables: volume D |T| / h^2 S - b_r |T| / h C, plus the self-coupling of the two faces across r (interior
+// faces with the neighbours' D, or the side's boundary type), each times |F| = |T| / h
+void cell_operator_1d(const dg_handle* h, const std::vector<double>& D, int64_t cell, int r,
+                      const std::vector<double>& S, const std::vector<double>& C, const double* e0, const double* e1,
+                      const double* d0, const double* d1, double* A) {
+  const int n = h->N;
+  const int ic[3] = {(int)(cell % h->n[0]), (int)((cell / h->n[0]) % h->n[1]),
+                     (int)(cell / ((int64_t)h->n[0] * h->n[1]))};
+  const int64_t strides[3] = {1, h->n[0], (int64_t)h->n[0] * h->n[1]};
+  const double hr = h->h[r], vol = h->h[0] * h->h[1] * h->h[2], area = vol / hr, b = h->b[r], Dt = D[cell];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[i * n + j] = vol * (Dt / (hr * hr) * S[i * n + j] - b / hr * C[i * n + j]);
+  for (int side = 0; side < 2; ++side) {
+    const bool at_end = side ? ic[r] == h->n[r] - 1 : ic[r] == 0;
+    const bool boundary = at_end && !h->periodic[r];
+    const double* ev = side ? e1 : e0;
+    const double* dv = side ? d1 : d0;
+    const double sgn = side ? 1.0 : -1.0;  // outward normal along axis r
+    double up, cons, pen;  // coefficients of ev ev^T (upwind), (ev dv^T + dv ev^T) / h (consistency), ev ev^T
+    if (boundary) {
+      const int bt = h->bc_type[2 * r + side];
+      const double bnu = sgn * b;
+      up = (bt != DG_BC_NEUMANN && bnu >= 0.0) ? bnu : 0.0;
+      cons = bt == DG_BC_DIRICHLET ? -sgn * Dt : 0.0;
+      pen = bt == DG_BC_DIRICHLET ? Dt * h->sigma / hr : 0.0;
+    } else {
+      const int64_t wrap = (int64_t)(h->n[r] - 1) * strides[r];
+      const int64_t nbr = side ? (at_end ? cell - wrap : cell + strides[r]) : (at_end ? cell + wrap : cell - strides[r]);
+      const double Dn = D[nbr], w = Dn / (Dt + Dn);  // weight of the own side's flux
+      up = side ? (b >= 0.0 ? b : 0.0) : (b < 0.0 ? -b : 0.0);
+      cons = -sgn * w * Dt;
+      pen = 2.0 * Dt * Dn / (Dt + Dn) * h->sigma / hr;
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        A[i * n + j] += area * ((up + pen) * ev[i] * ev[j] + cons / hr * (ev[i] * dv[j] + dv[i] * ev[j]));
+  }
+}
+
+}  // namespace
+
+// the fast-diagonalisation tables of every cell (host, threads over cells); false if a 1D operator could not be
+// diagonalised (the preconditioner then keeps the dense blocks)
+bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<float2>& tab) {
+  const int n = h->N, M = h->M, NN = n * n, TS = 3 * (2 * NN + n) + 1;
+  const Tables1D& t = h->tab;
+  // theta_j and theta_j' at the points and at the ends, from the Lagrange tables (exact: degree <= k < M)
+  std::vector<double> th(M * n), dth(M * n), S(n * n, 0.0), C(n * n, 0.0);
+  double e0[MAXN], e1[MAXN], d0[MAXN], d1[MAXN];
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < M; ++i) {
+      th[i * n + j] = t.A[i][j];
+      double acc = 0.0;
+      for (int l = 0; l < M; ++l) acc += t.Dt[i][l] * t.A[l][j];
+      dth[i * n + j] = acc;
+    }
+    double v0 = 0, v1 = 0, g0 = 0, g1 = 0;
+    for (int l = 0; l < M; ++l) {
+      v0 += t.L[0][l] * t.A[l][j];
+      v1 += t.L[1][l] * t.A[l][j];
+      g0 += t.P[0][l] * t.A[l][j];
+      g1 += t.P[1][l] * t.A[l][j];
+    }
+    e0[j] = v0, e1[j] = v1, d0[j] = g0, d1[j] = g1;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int q = 0; q < M; ++q) {
+        S[i * n + j] += t.w[q] * dth[q * n + i] * dth[q * n + j];
+        C[i * n + j] += t.w[q] * dth[q * n + i] * th[q * n + j];
+      }
+  tab.assign((size_t)h->ncell * TS, make_float2(0.f, 0.f));
+  const double cvol = h->c * h->h[0] * h->h[1] * h->h[2];
+  const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<int> ok(nth, 1);
+  auto work = [&](int w) {
+    std::vector<double> A(NN);
+    std::vector<dge::cd> V(NN), W(NN), lam(n);
+    for (int64_t cell = w; cell < h->ncell && ok[w]; cell += nth) {
+      float2* o = &tab[(size_t)cell * TS];
+      for (int r = 0; r < 3; ++r) {
+        cell_operator_1d(h, D, cell, r, S, C, e0, e1, d0, d1, A.data());
+        if (!dge::eig_general(n, A.data(), V.data(), W.data(), lam.data())) {
+          ok[w] = 0;
+          break;
+        }
+        float2* b = o + r * (2 * NN + n);
+        for (int e = 0; e < NN; ++e) {
+          b[e] = make_float2((float)W[e].real(), (float)W[e].imag());
+          b[NN + e] = make_float2((float)V[e].real(), (float)V[e].imag());
+        }
+        for (int e = 0; e < n; ++e) b[2 * NN + e] = make_float2((float)lam[e].real(), (float)lam[e].imag());
+      }
+      o[TS - 1] = make_float2((float)cvol, 0.f);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < nth; ++w) pool.emplace_back(work, w);
+  work(0);
+  for (auto& th_ : pool) th_.join();
+  for (int w = 0; w < nth; ++w)
+    if (!ok[w]) return false;
+  return true;
+}
+
+int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
+  const int N = h->N, NN = N * N, cpb = std::max(1, 256 / NN), TS = 3 * (2 * NN + N) + 1;
+  const size_t smem = (size_t)cpb * (N * NN + TS) * sizeof(float2);
+  const unsigned grid = (unsigned)((h->ncell + cpb - 1) / cpb);
+  const float2* tab = static_cast<const float2*>(h->fdm);
+  switch (N) {
+#define FDM(NV) \
+  case NV:      \
+    fdm_apply<NV><<<grid, cpb * NN, smem, s>>>(tab, r, z, h->ncell, cpb); \
+    break;
+    FDM(2) FDM(3) FDM(4) FDM(5) FDM(6) FDM(7) FDM(8) FDM(9) FDM(10) FDM(11)
+#undef FDM
+    default:
+      set_error("fast diagonalisation: unsupported degree");
+      return DG_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation)");
+}
+
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
   const int n = h->N * h->N * h->N, np8 = (n + 7) / 8 * 8, ct = np8 / 8;
   const int rsplit = ct <= 16 ? 2 : 1;
@@ -410,6 +614,22 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
   cudaFree(V);
   cudaFree(tr);
   cudaFree(status);
+  if (rc == DG_OK && !bad && !h->fdm) {
+    // the exact block inverse by fast diagonalisation for the FP32 inner solves (kept only if every cell's
+    // 1D operators could be diagonalised)
+    std::vector<double> Dh(h->ncell);
+    e = cudaMemcpy(Dh.data(), h->p64.D, h->ncell * sizeof(double), cudaMemcpyDeviceToHost);
+    std::vector<float2> tab;
+    if (e == cudaSuccess && build_fdm(h, Dh, tab)) {
+      e = cudaMalloc(&h->fdm, tab.size() * sizeof(float2));
+      if (e == cudaSuccess) e = cudaMemcpy(h->fdm, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(h->fdm);
+        h->fdm = nullptr;
+        rc = cuda_fail(e, "fast diagonalisation tables");
+      }
+    }
+  }
   if (rc == DG_OK && bad) {
     set_error("dg_precond_setup: " + std::to_string(bad) + " singular diagonal block(s)");
     rc = DG_ERR_NAN;
@@ -428,6 +648,8 @@ int dg_precond_apply(dg_handle* h, const void* r, void* z, int32_t precision, vo
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == DG_F64) return precond_bj_f64(h, static_cast<const double*>(r), static_cast<double*>(z), s);
+  // FP32: the exact block inverse by fast diagonalisation when it was built, else the FP32 dense blocks
+  if (h->fdm) return precond_fdm_f32(h, static_cast<const float*>(r), static_cast<float*>(z), s);
   return precond_bj_f32(h, static_cast<const float*>(r), static_cast<float*>(z), s);
 }
 

@@ -233,7 +233,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   const int m = o->restart > 0 ? o->restart : 30;
   const int mo = o->outer_restart > 0 ? o->outer_restart : 10;
   if (m > 60 || mo > 60 || (o->mode != DG_SOLVE_FP64 && o->mode != DG_SOLVE_MIXED) ||
-      (o->inner_block_precision != 0 && o->inner_block_precision != 1) ||
+      (o->inner_block_precision < 0 || o->inner_block_precision > 2) ||
       (o->preconditioner != DG_PRECOND_NONE && o->preconditioner != DG_PRECOND_BLOCK_JACOBI &&
        o->preconditioner != DG_PRECOND_MLP && o->preconditioner != DG_PRECOND_BJ_MLP) ||
       !(o->rtol > 0) || (o->mode == DG_SOLVE_MIXED && !(o->inner_rtol > 0 && o->inner_rtol < 1))) {
@@ -340,7 +340,9 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     // block-Jacobi inside the FP32 inner solve: the FP16 blocks (half the bytes of this HBM-bound product) unless
     // the caller asked for the FP32 ones
     auto bj_inner = [&](const float* r, float* z) {
-      return o->inner_block_precision == 1 ? precond_bj_f32(h, r, z, s) : precond_bj_f16(h, r, z, s);
+      if (o->inner_block_precision == 1) return precond_bj_f32(h, r, z, s);
+      if (o->inner_block_precision == 0 && h->fdm) return precond_fdm_f32(h, r, z, s);
+      return precond_bj_f16(h, r, z, s);
     };
     if (pc)
       M32 = [&](const float* r, float* z) {
