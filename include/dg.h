@@ -199,7 +199,14 @@ typedef struct {
   int32_t fallback;         /* 1 if an MLP-preconditioned solve switched to block-Jacobi            */
 } dg_solve_stats;
 
-/* Build the block-Jacobi preconditioner (kind = DG_PRECOND_BLOCK_JACOBI): for every cell the
+/* Kinds of dg_precond_setup.  DG_BJ_DENSE: the dense inverse blocks below (FP64, FP32, FP16) and the
+ * fast-diagonalisation tables.  DG_BJ_FAST_DIAG: only the fast-diagonalisation tables (complex FP32 and FP64,
+ * 3 (2 (k+1)^2 + k+1) + 1 numbers per cell; any degree): every diagonal block is a Kronecker sum of three
+ * 1D cell operators A_TT = I (x) I (x) A_x + I (x) A_y (x) I + A_z (x) I (x) I + c |T| I, inverted exactly
+ * through their eigen-decompositions (computed on the host).  Both need the scalar axis-parallel kernels. */
+enum { DG_BJ_DENSE = 1, DG_BJ_FAST_DIAG = 2 };
+
+/* Build the block-Jacobi preconditioner (kind = DG_BJ_DENSE): for every cell the
  * diagonal block A_TT ((k+1)^3 x (k+1)^3: the cell's volume term plus the self-coupling of its
  * faces) is assembled on the device by running the operator's own kernels on unit vectors, then
  * inverted in a batch (Gauss-Jordan, partial pivoting) and kept in FP64 and FP32 (FP32 rows padded
@@ -208,10 +215,9 @@ typedef struct {
 int dg_precond_setup(dg_handle* h, int32_t kind, void* stream);
 
 /* z = M^{-1} r with the block-Jacobi preconditioner (r, z device vectors of the given precision).  DG_F64
- * applies the dense FP64 inverse blocks; DG_F32 the exact block inverse by fast diagonalisation (every
- * diagonal block is a Kronecker sum of three 1D cell operators, inverted through their eigen-decompositions
- * with complex FP32 contractions), or the FP32 dense blocks where the 1D operators could not be
- * diagonalised. */
+ * applies the dense FP64 inverse blocks (or, after DG_BJ_FAST_DIAG, the fast diagonalisation in complex FP64);
+ * DG_F32 the exact block inverse by fast diagonalisation with complex FP32 contractions, or the FP32 dense
+ * blocks where the 1D operators could not be diagonalised. */
 int dg_precond_apply(dg_handle* h, const void* r_dev, void* z_dev, int32_t precision, void* stream);
 
 /* Solve A x = b (b_dev NULL: b = F, the right hand side of dg_setup) with FGMRES; x_dev holds the

@@ -149,6 +149,7 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->bj16);
   cudaFree(h->bj16s);
   cudaFree(h->fdm);
+  cudaFree(h->fdm64);
   cudaFree(h->bsc);
   cudaFree(h->bface);
   cudaFree(h->bscX);

@@ -85,6 +85,7 @@ struct dg_handle {
   void* bj16s = nullptr;
   // exact block inverse by fast diagonalisation (complex FP32 tables, see dg_precond.cu); null if not built
   void* fdm = nullptr;
+  void* fdm64 = nullptr;  // the same tables in complex FP64
   // Krylov workspace (grown on demand, freed by dg_destroy)
   void* ws = nullptr;
   size_t ws_bytes = 0;

@@ -295,41 +295,59 @@ __global__ void __launch_bounds__(128) bj_apply_f16(const __half* __restrict__ M
 // complex numbers per cell instead of n^6.
 // Table per cell (float2 = complex FP32): for r = 0..2: W_r [n][n], V_r [n][n], lambda_r [n]; then c |T|.
 // ---------------------------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(256) fdm_apply(const float2* __restrict__ tab, const float* __restrict__ r,
-                                                 float* __restrict__ z, int64_t ncell, int cpb) {
+template <typename R>
+struct Cx;
+template <>
+struct Cx<float> {
+  using type = float2;
+};
+template <>
+struct Cx<double> {
+  using type = double2;
+};
+
+template <int N, typename R>
+__global__ void __launch_bounds__(256) fdm_apply(const typename Cx<R>::type* __restrict__ tab, const R* __restrict__ r,
+                                                 R* __restrict__ z, int64_t ncell, int cpb) {
+  using C = typename Cx<R>::type;
   constexpr int NN = N * N, N3 = NN * N, TS = 3 * (2 * NN + N) + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* U = reinterpret_cast<float2*>(smem_raw);  // [cpb][N3]
-  float2* T = U + (size_t)cpb * N3;                  // [cpb][TS]
+  C* U = reinterpret_cast<C*>(smem_raw);  // [cpb][N3]
+  C* T = U + (size_t)cpb * N3;             // [cpb][TS]
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
   const int64_t cell0 = (int64_t)blockIdx.x * cpb;
   const int here = (int)min((int64_t)cpb, ncell - cell0);
   for (int e = threadIdx.x; e < here * TS; e += blockDim.x) T[e] = tab[cell0 * TS + e];
-  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) U[e] = make_float2(r[cell0 * N3 + e], 0.f);
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    C v;
+    v.x = r[cell0 * N3 + e];
+    v.y = R(0);
+    U[e] = v;
+  }
   __syncthreads();
   const bool active = lc < here;
-  float2* u = U + lc * N3;
-  const float2* tb = T + lc * TS;
+  C* u = U + lc * N3;
+  const C* tb = T + lc * TS;
   // line of this thread along axis d: the N points with the other two indices (a, b) = (t % N, t / N)
   auto base = [&](int d) { return d == 0 ? N * t : (d == 1 ? (t % N) + NN * (t / N) : t); };
   auto stride = [](int d) { return d == 0 ? 1 : (d == 1 ? N : NN); };
-  auto pass = [&](int d, const float2* Mx) {  // u_line <- Mx u_line (complex N x N)
+  auto pass = [&](int d, const C* Mx) {  // u_line <- Mx u_line (complex N x N)
     if (active) {
       const int bs = base(d), st = stride(d);
-      float2 x[N], y[N];
+      C x[N], y[N];
 #pragma unroll
       for (int l = 0; l < N; ++l) x[l] = u[bs + l * st];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float re = 0.f, im = 0.f;
+        R re = R(0), im = R(0);
 #pragma unroll
         for (int l = 0; l < N; ++l) {
-          const float2 m = Mx[i * N + l];
-          re = fmaf(m.x, x[l].x, fmaf(-m.y, x[l].y, re));
-          im = fmaf(m.x, x[l].y, fmaf(m.y, x[l].x, im));
+          const C m = Mx[i * N + l];
+          re = fma(m.x, x[l].x, fma(-m.y, x[l].y, re));
+          im = fma(m.x, x[l].y, fma(m.y, x[l].x, im));
         }
-        y[i] = make_float2(re, im);
+        y[i].x = re;
+        y[i].y = im;
       }
 #pragma unroll
       for (int i = 0; i < N; ++i) u[bs + i * st] = y[i];
@@ -339,17 +357,20 @@ __global__ void __launch_bounds__(256) fdm_apply(const float2* __restrict__ tab,
   for (int d = 0; d < 3; ++d) pass(d, tb + d * (2 * NN + N));  // W_d
   if (active) {
     // divide by lambda_x(a) + lambda_y(b) + lambda_z(c) + c |T| along this thread's z-line (a, b)
-    const float2* lx = tb + 0 * (2 * NN + N) + 2 * NN;
-    const float2* ly = tb + 1 * (2 * NN + N) + 2 * NN;
-    const float2* lz = tb + 2 * (2 * NN + N) + 2 * NN;
-    const float cs = tb[TS - 1].x;
+    const C* lx = tb + 0 * (2 * NN + N) + 2 * NN;
+    const C* ly = tb + 1 * (2 * NN + N) + 2 * NN;
+    const C* lz = tb + 2 * (2 * NN + N) + 2 * NN;
+    const R cs = tb[TS - 1].x;
     const int a = t % N, b = t / N;
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-      const float dr = lx[a].x + ly[b].x + lz[c].x + cs, di = lx[a].y + ly[b].y + lz[c].y;
-      const float inv = 1.f / (dr * dr + di * di);
-      const float2 v = u[a + N * b + NN * c];
-      u[a + N * b + NN * c] = make_float2((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
+      const R dr = lx[a].x + ly[b].x + lz[c].x + cs, di = lx[a].y + ly[b].y + lz[c].y;
+      const R inv = R(1) / (dr * dr + di * di);
+      C v = u[a + N * b + NN * c];
+      const R vr = (v.x * dr + v.y * di) * inv, vi = (v.y * dr - v.x * di) * inv;
+      v.x = vr;
+      v.y = vi;
+      u[a + N * b + NN * c] = v;
     }
   }
   __syncthreads();
@@ -403,7 +424,7 @@ void cell_operator_1d(const dg_handle* h, const std::vector<double>& D, int64_t 
 
 // the fast-diagonalisation tables of every cell (host, threads over cells); false if a 1D operator could not be
 // diagonalised (the preconditioner then keeps the dense blocks)
-bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<float2>& tab) {
+bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<double2>& tab) {
   const int n = h->N, M = h->M, NN = n * n, TS = 3 * (2 * NN + n) + 1;
   const Tables1D& t = h->tab;
   // theta_j and theta_j' at the points and at the ends, from the Lagrange tables (exact: degree <= k < M)
@@ -431,7 +452,7 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<flo
         S[i * n + j] += t.w[q] * dth[q * n + i] * dth[q * n + j];
         C[i * n + j] += t.w[q] * dth[q * n + i] * th[q * n + j];
       }
-  tab.assign((size_t)h->ncell * TS, make_float2(0.f, 0.f));
+  tab.assign((size_t)h->ncell * TS, make_double2(0.0, 0.0));
   const double cvol = h->c * h->h[0] * h->h[1] * h->h[2];
   const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::vector<int> ok(nth, 1);
@@ -439,21 +460,21 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<flo
     std::vector<double> A(NN);
     std::vector<dge::cd> V(NN), W(NN), lam(n);
     for (int64_t cell = w; cell < h->ncell && ok[w]; cell += nth) {
-      float2* o = &tab[(size_t)cell * TS];
+      double2* o = &tab[(size_t)cell * TS];
       for (int r = 0; r < 3; ++r) {
         cell_operator_1d(h, D, cell, r, S, C, e0, e1, d0, d1, A.data());
         if (!dge::eig_general(n, A.data(), V.data(), W.data(), lam.data())) {
           ok[w] = 0;
           break;
         }
-        float2* b = o + r * (2 * NN + n);
+        double2* b = o + r * (2 * NN + n);
         for (int e = 0; e < NN; ++e) {
-          b[e] = make_float2((float)W[e].real(), (float)W[e].imag());
-          b[NN + e] = make_float2((float)V[e].real(), (float)V[e].imag());
+          b[e] = make_double2(W[e].real(), W[e].imag());
+          b[NN + e] = make_double2(V[e].real(), V[e].imag());
         }
-        for (int e = 0; e < n; ++e) b[2 * NN + e] = make_float2((float)lam[e].real(), (float)lam[e].imag());
+        for (int e = 0; e < n; ++e) b[2 * NN + e] = make_double2(lam[e].real(), lam[e].imag());
       }
-      o[TS - 1] = make_float2((float)cvol, 0.f);
+      o[TS - 1] = make_double2(cvol, 0.0);
     }
   };
   std::vector<std::thread> pool;
@@ -465,15 +486,23 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<flo
   return true;
 }
 
-int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
+template <typename R>
+int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
+  using C = typename Cx<R>::type;
   const int N = h->N, NN = N * N, cpb = std::max(1, 256 / NN), TS = 3 * (2 * NN + N) + 1;
-  const size_t smem = (size_t)cpb * (N * NN + TS) * sizeof(float2);
+  const size_t smem = (size_t)cpb * (N * NN + TS) * sizeof(C);
   const unsigned grid = (unsigned)((h->ncell + cpb - 1) / cpb);
-  const float2* tab = static_cast<const float2*>(h->fdm);
+  const C* tab = static_cast<const C*>(sizeof(R) == 4 ? h->fdm : h->fdm64);
+  if (!tab) {
+    set_error("block-Jacobi: the fast diagonalisation was not set up");
+    return DG_ERR_INVALID_ARG;
+  }
   switch (N) {
-#define FDM(NV) \
-  case NV:      \
-    fdm_apply<NV><<<grid, cpb * NN, smem, s>>>(tab, r, z, h->ncell, cpb); \
+#define FDM(NV)                                                                                           \
+  case NV:                                                                                                \
+    if (smem > 48 * 1024)                                                                                 \
+      cudaFuncSetAttribute(fdm_apply<NV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    fdm_apply<NV, R><<<grid, cpb * NN, smem, s>>>(tab, r, z, h->ncell, cpb);                              \
     break;
     FDM(2) FDM(3) FDM(4) FDM(5) FDM(6) FDM(7) FDM(8) FDM(9) FDM(10) FDM(11)
 #undef FDM
@@ -485,7 +514,10 @@ int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s
   return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation)");
 }
 
+int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) { return precond_fdm(h, r, z, s); }
+
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
+  if (!h->bj16) return precond_fdm(h, r, z, s);
   const int n = h->N * h->N * h->N, np8 = (n + 7) / 8 * 8, ct = np8 / 8;
   const int rsplit = ct <= 16 ? 2 : 1;
   const int wpc = rsplit == 2 ? 1 : (ct + 31) / 32;
@@ -499,6 +531,7 @@ int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s)
 }
 
 int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t s) {
+  if (!h->bj64) return precond_fdm(h, r, z, s);  // set up with the fast diagonalisation only
   const int n = h->N * h->N * h->N;
   const int threads = n >= 256 ? 256 : ((n + 31) / 32) * 32;
   bj_apply<double><<<(unsigned)h->ncell, threads, n * sizeof(double), s>>>(static_cast<const double*>(h->bj64), r, z, n);
@@ -507,6 +540,7 @@ int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t 
 }
 
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
+  if (!h->bj32) return precond_fdm(h, r, z, s);
   const int n = h->N * h->N * h->N, np = (n + 3) / 4 * 4;
   const int wpc = (np / 4 + 31) / 32;            // warps per cell
   const int cpc = wpc >= 4 ? 1 : 4 / wpc;        // cells per CTA
@@ -524,9 +558,38 @@ using namespace dgi;
 
 extern "C" {
 
+namespace {
+// the fast-diagonalisation tables (complex FP32 and FP64) of every cell; DG_ERR_NAN if a 1D cell operator
+// could not be diagonalised
+int setup_fdm(dg_handle* h) {
+  if (h->fdm && h->fdm64) return DG_OK;
+  std::vector<double> Dh(h->ncell);
+  cudaError_t e = cudaMemcpy(Dh.data(), h->p64.D, h->ncell * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "fast diagonalisation: D");
+  std::vector<double2> tab;
+  if (!build_fdm(h, Dh, tab)) {
+    set_error("dg_precond_setup: a 1D cell operator could not be diagonalised");
+    return DG_ERR_NAN;
+  }
+  std::vector<float2> tab32(tab.size());
+  for (size_t i = 0; i < tab.size(); ++i) tab32[i] = make_float2((float)tab[i].x, (float)tab[i].y);
+  e = cudaMalloc(&h->fdm64, tab.size() * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&h->fdm, tab.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpy(h->fdm64, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->fdm, tab32.data(), tab32.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(h->fdm);
+    cudaFree(h->fdm64);
+    h->fdm = h->fdm64 = nullptr;
+    return cuda_fail(e, "fast diagonalisation tables");
+  }
+  return DG_OK;
+}
+}  // namespace
+
 int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
-  if (!h || kind != 1) {
-    set_error("dg_precond_setup: kind must be 1 (block-Jacobi)");
+  if (!h || (kind != DG_BJ_DENSE && kind != DG_BJ_FAST_DIAG)) {
+    set_error("dg_precond_setup: kind must be DG_BJ_DENSE (1) or DG_BJ_FAST_DIAG (2)");
     return DG_ERR_INVALID_ARG;
   }
   if (h->vb || h->td) {
@@ -542,8 +605,13 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
     }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int N = h->N, n = N * N * N;
+  if (kind == DG_BJ_FAST_DIAG) {
+    const cudaError_t e0 = cudaStreamSynchronize(s);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "dg_precond_setup synchronize");
+    return setup_fdm(h);
+  }
   if (n > 512) {
-    set_error("dg_precond_setup: block-Jacobi supports (k+1)^3 <= 512");
+    set_error("dg_precond_setup: dense block-Jacobi supports (k+1)^3 <= 512");
     return DG_ERR_INVALID_ARG;
   }
   const size_t nblk = (size_t)h->ncell * n * n;
@@ -614,21 +682,11 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
   cudaFree(V);
   cudaFree(tr);
   cudaFree(status);
-  if (rc == DG_OK && !bad && !h->fdm) {
-    // the exact block inverse by fast diagonalisation for the FP32 inner solves (kept only if every cell's
-    // 1D operators could be diagonalised)
-    std::vector<double> Dh(h->ncell);
-    e = cudaMemcpy(Dh.data(), h->p64.D, h->ncell * sizeof(double), cudaMemcpyDeviceToHost);
-    std::vector<float2> tab;
-    if (e == cudaSuccess && build_fdm(h, Dh, tab)) {
-      e = cudaMalloc(&h->fdm, tab.size() * sizeof(float2));
-      if (e == cudaSuccess) e = cudaMemcpy(h->fdm, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) {
-        cudaFree(h->fdm);
-        h->fdm = nullptr;
-        rc = cuda_fail(e, "fast diagonalisation tables");
-      }
-    }
+  if (rc == DG_OK && !bad) {
+    // also the exact block inverse by fast diagonalisation for FP32 applies (kept only if every cell's 1D
+    // operators could be diagonalised; otherwise the FP32 applies use the dense blocks)
+    const int frc = setup_fdm(h);
+    if (frc == DG_ERR_CUDA || frc == DG_ERR_OOM) rc = frc;
   }
   if (rc == DG_OK && bad) {
     set_error("dg_precond_setup: " + std::to_string(bad) + " singular diagonal block(s)");
@@ -642,7 +700,7 @@ int dg_precond_apply(dg_handle* h, const void* r, void* z, int32_t precision, vo
     set_error("dg_precond_apply: bad arguments");
     return DG_ERR_INVALID_ARG;
   }
-  if (!h->bj64) {
+  if (!h->bj64 && !h->fdm64) {
     set_error("dg_precond_apply: call dg_precond_setup first");
     return DG_ERR_INVALID_ARG;
   }

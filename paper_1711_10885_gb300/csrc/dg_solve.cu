@@ -245,7 +245,8 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
               "in DG_SOLVE_FP64 only");
     return DG_ERR_INVALID_ARG;
   }
-  if ((o->preconditioner == DG_PRECOND_BLOCK_JACOBI || o->preconditioner == DG_PRECOND_BJ_MLP) && !h->bj64) {
+  if ((o->preconditioner == DG_PRECOND_BLOCK_JACOBI || o->preconditioner == DG_PRECOND_BJ_MLP) && !h->bj64 &&
+      !h->fdm64) {
     set_error("dg_solve: block-Jacobi requested but dg_precond_setup was not called");
     return DG_ERR_INVALID_ARG;
   }
@@ -266,7 +267,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   int fallback = 0;
   dg_mlp* mlp = const_cast<dg_mlp*>(o->mlp);
   auto maybe_fallback = [&](double start, double end) {
-    if (use_mlp && o->fallback_ratio > 0 && h->bj64 && start > 0 && end > o->fallback_ratio * start) {
+    if (use_mlp && o->fallback_ratio > 0 && (h->bj64 || h->fdm64) && start > 0 && end > o->fallback_ratio * start) {
       use_mlp = false;
       fallback = 1;
     }

@@ -65,6 +65,8 @@ DG_PRECOND_NONE = 0
 DG_PRECOND_BLOCK_JACOBI = 1
 DG_PRECOND_MLP = 2
 DG_PRECOND_BJ_MLP = 3
+DG_BJ_DENSE = 1
+DG_BJ_FAST_DIAG = 2
 
 
 class dg_solve_opts(ctypes.Structure):
@@ -360,7 +362,8 @@ class Operator:
         return y
 
     def precond_setup(self, kind=DG_PRECOND_BLOCK_JACOBI, stream=None):
-        """Assemble and invert the per-cell diagonal blocks (dg_precond_setup)."""
+        """Block-Jacobi set-up (dg_precond_setup): DG_BJ_DENSE (default) assembles and inverts the dense per-cell
+        blocks and builds the fast-diagonalisation tables; DG_BJ_FAST_DIAG builds only the latter."""
         check(lib.dg_precond_setup(self.h, int(kind), _stream_ptr(stream)))
 
     def precond_apply(self, r, z=None, stream=None):

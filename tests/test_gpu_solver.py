@@ -137,4 +137,41 @@ def test_fast_diagonalisation_equals_dense_block_inverse(dg, case):
     z64 = op.precond_apply(r).cpu().numpy()
     z32 = op.precond_apply(r.float()).cpu().numpy()
     assert np.max(np.abs(z32 - z64)) <= 1e-4 * np.max(np.abs(z64))
+    # the same inverse in complex FP64 when only the fast diagonalisation is set up
+    op2 = dg.Operator(w.n, w.k, w.D, b=w.b, c=w.c, periodic=per, bc=bc)
+    op2.precond_setup(dg.DG_BJ_FAST_DIAG)
+    z64f = op2.precond_apply(r).cpu().numpy()
+    assert np.max(np.abs(z64f - z64)) <= 1e-10 * np.max(np.abs(z64))
+    op.close()
+    op2.close()
+
+
+@pytest.mark.parametrize("k", [8, 10])
+def test_fast_diagonalisation_inverts_the_one_cell_operator(dg, k):
+    """Degrees whose dense blocks are not built ((k+1)^3 > 512): on a one-cell mesh the operator is its own
+    diagonal block, so A M^{-1} r = r (FP64 fast diagonalisation; FP32 to its rounding)."""
+    w = inputs.small_case(n=(1, 1, 1), k=k, seed=70 + k, b=(0.9, -0.4, 0.2), c=0.3)
+    op = dg.Operator(w.n, w.k, w.D, b=w.b, c=w.c)
+    op.precond_setup(dg.DG_BJ_FAST_DIAG)
+    r = torch.tensor(np.random.default_rng(71 + k).uniform(-1, 1, w.ndof), device="cuda")
+    z = op.precond_apply(r)
+    assert torch.max(torch.abs(op.apply_jacobian(z) - r)).item() <= 1e-8
+    z32 = op.precond_apply(r.float())
+    assert torch.max(torch.abs(op.apply_jacobian(z32.double()) - r)).item() <= 1e-2
+    op.close()
+
+
+def test_solves_with_the_fast_diagonalisation_only(dg):
+    w = inputs.small_case(n=(3, 2, 2), k=3, seed=8, b=(1.0, 0.5, 0.25), f_kind="sines")
+    w.f_params = inputs.sine_modes(9)
+    pr = oracle_problem(w)
+    x_ref = np.linalg.solve(oracle_matrix(pr), oracle.rhs(pr, inputs.f_at(w, oracle.volume_points(pr)), None))
+    op = dg.operator_for(w)
+    op.precond_setup(dg.DG_BJ_FAST_DIAG)
+    for mode in (dg.DG_SOLVE_FP64, dg.DG_SOLVE_MIXED):
+        x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+        st = op.solve(x, mode=mode, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=1e-12, restart=20,
+                      outer_restart=8, inner_rtol=1e-2)
+        assert st["rc"] == 0
+        assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-9 * np.max(np.abs(x_ref))
     op.close()
