@@ -1,4 +1,5 @@
-// dg_blas.cuh -- vector kernels of the Krylov solvers (deterministic fixed-order reductions).
+// dg_blas.cuh -- vector kernels of the Krylov solvers (deterministic fixed-order reductions).  The basis
+// passes are bound by HBM bandwidth: they move 16 bytes per load and keep several rows in flight.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -6,9 +7,11 @@
 
 namespace dgb {
 
-constexpr int RED_BLOCKS = 152 * 4;  // one wave of 4 CTAs per SM
+constexpr int RED_BLOCKS = 152 * 4;   // rows of the partial-sum buffer hold up to this many block sums
 constexpr int RED_THREADS = 256;
-constexpr int MDOT_GROUP = 8;         // vectors reduced per pass over w
+constexpr int PASS_BLOCKS = 152 * 2;  // grid of the basis passes: two CTAs per SM, one wave
+constexpr int LOADS = 8;              // basis rows whose packs are loaded together (in flight per thread)
+constexpr int MAX_ROWS = 64;          // basis rows per pass (restart lengths up to 60, plus w . w)
 
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
@@ -16,35 +19,83 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// part[v * gridDim.x + block] = sum over this block's share of i of V[v*ld + i] * w[i]  (v < nv)
-// Per-thread sums run in T; the block and final reductions in FP64.
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS)
-mdot_partial(const T* __restrict__ V, size_t ld, int nv, const T* __restrict__ w, size_t n, double* __restrict__ part) {
-  __shared__ double red[MDOT_GROUP][RED_THREADS / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int v0 = 0; v0 < nv; v0 += MDOT_GROUP) {
-    T acc[MDOT_GROUP];
+// W consecutive elements moved by one load or store (16 bytes when W = 16 / sizeof(T))
+template <typename T, int W>
+struct alignas(sizeof(T) * W) Pack {
+  T v[W];
+};
+
+template <typename T, int W>
+__device__ __forceinline__ Pack<T, W> ld_pack(const T* row, size_t p) {
+  return reinterpret_cast<const Pack<T, W>*>(row)[p];
+}
+
+// The basis passes below read the rows V_q = V + q * ld (q < nv <= 60) in packs of W elements: thread t of
+// block b takes packs p = b * RED_THREADS + t, p + gridDim.x * RED_THREADS, ...  Each thread keeps its partial
+// dot products in its own column of shared memory (acc[q * RED_THREADS + t]), so w is loaded once per pack
+// however many rows there are, and the block sums are taken in FP64 in a fixed order (deterministic).
+
+// UPDATE = false: part[q * gridDim.x + b] = this block's share of V_q . w              (q < nv)
+// UPDATE = true:  w <- w - sum_q h[q] V_q first (h on the device); then the same dots with the new w, and
+//                 part[nv * gridDim.x + b] = its share of w . w
+// Dynamic shared memory: (nv + UPDATE) * RED_THREADS * sizeof(T).  w is not a row of V[0 .. nv).
+template <typename T, int W, bool UPDATE>
+__global__ void __launch_bounds__(RED_THREADS, 2)
+basis_dots(const T* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, T* w, size_t npack,
+           double* __restrict__ part) {
+  extern __shared__ unsigned char basis_smem[];
+  T* acc = reinterpret_cast<T*>(basis_smem);
+  __shared__ T hs[MAX_ROWS];
+  const int t = threadIdx.x;
+  const int nrow = nv + (UPDATE ? 1 : 0);
+  for (int q = 0; q < nrow; ++q) acc[q * RED_THREADS + t] = T(0);
+  if (UPDATE && t < nv) hs[t] = (T)h[t];
+  __syncthreads();
+  for (size_t p = (size_t)blockIdx.x * RED_THREADS + t; p < npack; p += (size_t)gridDim.x * RED_THREADS) {
+    Pack<T, W> wp = ld_pack<T, W>(w, p);
+    if (UPDATE) {
+      for (int v0 = 0; v0 < nv; v0 += LOADS) {
+        Pack<T, W> a[LOADS];
 #pragma unroll
-    for (int q = 0; q < MDOT_GROUP; ++q) acc[q] = T(0);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-      const T wi = w[i];
+        for (int q = 0; q < LOADS; ++q)
+          if (v0 + q < nv) a[q] = ld_pack<T, W>(V + (size_t)(v0 + q) * ld, p);
 #pragma unroll
-      for (int q = 0; q < MDOT_GROUP; ++q)
-        if (v0 + q < nv) acc[q] = fma(V[(size_t)(v0 + q) * ld + i], wi, acc[q]);
-    }
+        for (int q = 0; q < LOADS; ++q)
+          if (v0 + q < nv) {
 #pragma unroll
-    for (int q = 0; q < MDOT_GROUP; ++q) {
-      const double s = warp_sum((double)acc[q]);
-      if (lane == 0) red[q][wid] = s;
+            for (int e = 0; e < W; ++e) wp.v[e] = fma(-hs[v0 + q], a[q].v[e], wp.v[e]);
+          }
+      }
+      reinterpret_cast<Pack<T, W>*>(w)[p] = wp;
+      T s = T(0);
+#pragma unroll
+      for (int e = 0; e < W; ++e) s = fma(wp.v[e], wp.v[e], s);
+      acc[nv * RED_THREADS + t] += s;
     }
-    __syncthreads();
-    if (threadIdx.x < MDOT_GROUP && v0 + (int)threadIdx.x < nv) {
-      double s = 0.0;
-      for (int k = 0; k < RED_THREADS / 32; ++k) s += red[threadIdx.x][k];
-      part[(size_t)(v0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    // (with UPDATE the rows were just read: these loads are served by the caches)
+    for (int v0 = 0; v0 < nv; v0 += LOADS) {
+      Pack<T, W> a[LOADS];
+#pragma unroll
+      for (int q = 0; q < LOADS; ++q)
+        if (v0 + q < nv) a[q] = ld_pack<T, W>(V + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < LOADS; ++q)
+        if (v0 + q < nv) {
+          T s = T(0);
+#pragma unroll
+          for (int e = 0; e < W; ++e) s = fma(a[q].v[e], wp.v[e], s);
+          acc[(v0 + q) * RED_THREADS + t] += s;
+        }
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  // warp k reduces rows k, k + 8, ... over the block's threads in FP64
+  const int lane = t & 31, wid = t >> 5;
+  for (int q = wid; q < nrow; q += RED_THREADS / 32) {
+    double s = 0.0;
+    for (int k = lane; k < RED_THREADS; k += 32) s += (double)acc[q * RED_THREADS + k];
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)q * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -63,31 +114,79 @@ __global__ void mdot_final(const double* __restrict__ part, int nblk, double* __
   }
 }
 
-// w[i] -= sum_v V[v*ld + i] * h[v]   (nv <= 64)
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS)
-maxpy(const T* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, T* __restrict__ w, size_t n) {
-  __shared__ T hs[64];
-  if (threadIdx.x < nv) hs[threadIdx.x] = (T)h[threadIdx.x];
+// w <- alpha (w - sum_{q < nv} h[q] V_q), h on the device.  alpha = 1, or with normalise
+// alpha = 1 / sqrt(h[nv] - sum_q h[q]^2): when h[q] = V_q . w and h[nv] = w . w for orthonormal rows V_q, that
+// is the inverse norm of the result (Pythagoras); alpha = 1 when the difference is not positive.
+template <typename T, int W>
+__global__ void __launch_bounds__(RED_THREADS, 2)
+basis_update(const T* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, int normalise, T* w,
+             size_t npack) {
+  __shared__ T hs[MAX_ROWS];
+  __shared__ T alpha_s;
+  const int t = threadIdx.x;
+  if (t < nv) hs[t] = (T)h[t];
+  if (t == 0) {
+    double a = 1.0;
+    if (normalise) {
+      double s2 = h[nv];
+      for (int q = 0; q < nv; ++q) s2 -= h[q] * h[q];
+      if (s2 > 0.0) a = 1.0 / sqrt(s2);
+    }
+    alpha_s = (T)a;
+  }
   __syncthreads();
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    T acc = w[i];
-    for (int v = 0; v < nv; ++v) acc = fma(-hs[v], V[(size_t)v * ld + i], acc);
-    w[i] = acc;
+  const T alpha = alpha_s;
+  for (size_t p = (size_t)blockIdx.x * RED_THREADS + t; p < npack; p += (size_t)gridDim.x * RED_THREADS) {
+    Pack<T, W> wp = ld_pack<T, W>(w, p);
+    for (int v0 = 0; v0 < nv; v0 += LOADS) {
+      Pack<T, W> a[LOADS];
+#pragma unroll
+      for (int q = 0; q < LOADS; ++q)
+        if (v0 + q < nv) a[q] = ld_pack<T, W>(V + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < LOADS; ++q)
+        if (v0 + q < nv) {
+#pragma unroll
+          for (int e = 0; e < W; ++e) wp.v[e] = fma(-hs[v0 + q], a[q].v[e], wp.v[e]);
+        }
+    }
+    if (normalise) {
+#pragma unroll
+      for (int e = 0; e < W; ++e) wp.v[e] *= alpha;
+    }
+    reinterpret_cast<Pack<T, W>*>(w)[p] = wp;
   }
 }
 
-// x[i] += sum_v Z[v*ld + i] * y[v]  with x in FP64 (solution update of FGMRES), Z in T, y on the device
-template <typename T, typename TX>
-__global__ void __launch_bounds__(RED_THREADS)
-lincomb_add(const T* __restrict__ Z, size_t ld, int nv, const double* __restrict__ y, TX* __restrict__ x, size_t n) {
-  __shared__ double ys[64];
-  if (threadIdx.x < nv) ys[threadIdx.x] = y[threadIdx.x];
+// x <- x + sum_{q < nv} y[q] Z_q  (the solution update of FGMRES; y on the device)
+template <typename T, int W>
+__global__ void __launch_bounds__(RED_THREADS, 2)
+lincomb_add(const T* __restrict__ Z, size_t ld, int nv, const double* __restrict__ y, T* __restrict__ x,
+            size_t npack) {
+  __shared__ T ys[MAX_ROWS];
+  if (threadIdx.x < nv) ys[threadIdx.x] = (T)y[threadIdx.x];
   __syncthreads();
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    T acc = T(0);
-    for (int v = 0; v < nv; ++v) acc = fma((T)ys[v], Z[(size_t)v * ld + i], acc);
-    x[i] = (TX)((TX)acc + x[i]);
+  for (size_t p = (size_t)blockIdx.x * RED_THREADS + threadIdx.x; p < npack;
+       p += (size_t)gridDim.x * RED_THREADS) {
+    Pack<T, W> s;
+#pragma unroll
+    for (int e = 0; e < W; ++e) s.v[e] = T(0);
+    for (int v0 = 0; v0 < nv; v0 += LOADS) {
+      Pack<T, W> a[LOADS];
+#pragma unroll
+      for (int q = 0; q < LOADS; ++q)
+        if (v0 + q < nv) a[q] = ld_pack<T, W>(Z + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < LOADS; ++q)
+        if (v0 + q < nv) {
+#pragma unroll
+          for (int e = 0; e < W; ++e) s.v[e] = fma(ys[v0 + q], a[q].v[e], s.v[e]);
+        }
+    }
+    Pack<T, W> xp = ld_pack<T, W>(x, p);
+#pragma unroll
+    for (int e = 0; e < W; ++e) xp.v[e] = s.v[e] + xp.v[e];
+    reinterpret_cast<Pack<T, W>*>(x)[p] = xp;
   }
 }
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -24,38 +25,93 @@ struct Ctx {
   dg_handle* h;
   cudaStream_t s;
   size_t n;
-  double* part;  // RED_BLOCKS * 64 partial sums
-  double* hdev;  // 64 reduction results
-  double* ydev;  // 64 coefficients
-  double* hhost; // pinned, 64
+  double* part;   // MAX_ROWS rows of RED_BLOCKS block sums
+  double* hdev;   // 64 results of the first projection (and of plain dot products)
+  double* ydev;   // 64 coefficients of the solution update
+  double* h2dev;  // 64 results of the second projection, then w . w
+  double* hhost;  // pinned, 256
   int applies64 = 0, applies32 = 0;
 };
 
 int cuda_check(cudaError_t e, const char* what) { return e == cudaSuccess ? 0 : cuda_fail(e, what); }
 
+// 16-byte packs when the length and every row start allow them, else one element per load
+template <typename T>
+bool packable(size_t n, std::initializer_list<const void*> ptrs) {
+  constexpr size_t W = 16 / sizeof(T);
+  if (n % W) return false;
+  for (const void* q : ptrs)
+    if (reinterpret_cast<uintptr_t>(q) % 16) return false;
+  return true;
+}
+
+// the per-thread partial sums of a basis pass take up to MAX_ROWS columns of shared memory (128 KB in FP64),
+// beyond the 48 KB (static plus dynamic) a launch gets without opting in: opt in once per kernel
+template <typename T, int W, bool UPDATE>
+int basis_smem_attr() {
+  static bool done = false;
+  if (done) return 0;
+  if (int rc = cuda_check(cudaFuncSetAttribute(dgb::basis_dots<T, W, UPDATE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               dgb::MAX_ROWS * dgb::RED_THREADS * (int)sizeof(T)),
+                          "basis pass shared memory"))
+    return rc;
+  done = true;
+  return 0;
+}
+
+// dst[q] = V_q . w (q < nv) on the device; with UPDATE, w <- w - sum_q h[q] V_q first and dst[nv] = w . w
+template <typename T, bool UPDATE>
+int basis_dots(Ctx& c, const T* V, int nv, const double* h, T* w, double* dst) {
+  const int rows = nv + (UPDATE ? 1 : 0);
+  const size_t smem = (size_t)rows * dgb::RED_THREADS * sizeof(T);
+  if (packable<T>(c.n, {V, w})) {
+    constexpr int W = 16 / sizeof(T);
+    if (int rc = basis_smem_attr<T, W, UPDATE>()) return rc;
+    dgb::basis_dots<T, W, UPDATE><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n / W,
+                                                                                    c.part);
+  } else {
+    if (int rc = basis_smem_attr<T, 1, UPDATE>()) return rc;
+    dgb::basis_dots<T, 1, UPDATE><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n, c.part);
+  }
+  dgb::mdot_final<<<rows, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::PASS_BLOCKS, dst);
+  return cuda_check(cudaGetLastError(), "basis dot kernels");
+}
+
+// w <- alpha (w - sum_q h[q] V_q), alpha the inverse norm of the result from h when normalise
+template <typename T>
+int basis_update(Ctx& c, const T* V, int nv, const double* h, bool normalise, T* w) {
+  if (packable<T>(c.n, {V, w})) {
+    constexpr int W = 16 / sizeof(T);
+    dgb::basis_update<T, W><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n / W);
+  } else {
+    dgb::basis_update<T, 1><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n);
+  }
+  return cuda_check(cudaGetLastError(), "basis update");
+}
+
+// x <- x + sum_q y[q] Z_q, y on the device
+template <typename T>
+int lincomb_add(Ctx& c, const T* Z, int nv, const double* y, T* x) {
+  if (packable<T>(c.n, {Z, x})) {
+    constexpr int W = 16 / sizeof(T);
+    dgb::lincomb_add<T, W><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n / W);
+  } else {
+    dgb::lincomb_add<T, 1><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n);
+  }
+  return cuda_check(cudaGetLastError(), "solution update");
+}
+
+// out_host[q] = V_q . w for q < nv (synchronises)
 template <typename T>
 int dots(Ctx& c, const T* V, int nv, const T* w, double* out_host) {
-  dgb::mdot_partial<T><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, w, c.n, c.part);
-  dgb::mdot_final<<<nv, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::RED_BLOCKS, c.hdev);
-  if (int rc = cuda_check(cudaGetLastError(), "dot kernels")) return rc;
+  if (int rc = basis_dots<T, false>(c, V, nv, nullptr, const_cast<T*>(w), c.hdev)) return rc;
   if (int rc = cuda_check(cudaMemcpyAsync(c.hhost, c.hdev, nv * sizeof(double), cudaMemcpyDeviceToHost, c.s),
                           "dot copy"))
     return rc;
   if (int rc = cuda_check(cudaStreamSynchronize(c.s), "dot sync")) return rc;
   std::memcpy(out_host, c.hhost, nv * sizeof(double));
   return 0;
-}
-
-template <typename T>
-int axpy_many(Ctx& c, const T* V, int nv, const double* coef_host, T* w) {
-  std::memcpy(c.hhost, coef_host, nv * sizeof(double));
-  if (int rc = cuda_check(cudaMemcpyAsync(c.ydev, c.hhost, nv * sizeof(double), cudaMemcpyHostToDevice, c.s),
-                          "coef copy"))
-    return rc;
-  dgb::maxpy<T><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, c.ydev, w, c.n);
-  // the pinned staging buffer is reused by the next call: wait for this copy to be consumed
-  if (int rc = cuda_check(cudaStreamSynchronize(c.s), "axpy sync")) return rc;
-  return cuda_check(cudaGetLastError(), "maxpy");
 }
 
 template <typename T>
@@ -137,12 +193,22 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
           return rc;
       }
       if (int rc = apply_A<T>(c, zj, w)) return rc;
-      // classical Gram-Schmidt, twice
-      if (int rc = dots<T>(c, V, j + 1, w, hv.data())) return rc;
-      if (int rc = axpy_many<T>(c, V, j + 1, hv.data(), w)) return rc;
-      if (int rc = dots<T>(c, V, j + 2, w, h2.data())) return rc;  // last entry: ||w||^2
-      if (int rc = axpy_many<T>(c, V, j + 1, h2.data(), w)) return rc;
-      double s2 = h2[j + 1];
+      // classical Gram-Schmidt, twice, in three passes over the basis with the coefficients kept on the device:
+      // h = V^T w; then w -= V h together with h2 = V^T w and ||w||^2; then w = (w - V h2) / ||w - V h2||, the
+      // norm by Pythagoras.  One synchronisation fetches h and h2 for the Hessenberg column.
+      if (int rc = basis_dots<T, false>(c, V, j + 1, nullptr, w, c.hdev)) return rc;
+      if (int rc = basis_dots<T, true>(c, V, j + 1, c.hdev, w, c.h2dev)) return rc;
+      if (int rc = basis_update<T>(c, V, j + 1, c.h2dev, true, w)) return rc;
+      if (int rc = cuda_check(cudaMemcpyAsync(c.hhost, c.hdev, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                                              c.s), "h copy"))
+        return rc;
+      if (int rc = cuda_check(cudaMemcpyAsync(c.hhost + 128, c.h2dev, (j + 2) * sizeof(double),
+                                              cudaMemcpyDeviceToHost, c.s), "h2 copy"))
+        return rc;
+      if (int rc = cuda_check(cudaStreamSynchronize(c.s), "Arnoldi sync")) return rc;
+      std::memcpy(hv.data(), c.hhost, (j + 1) * sizeof(double));
+      std::memcpy(h2.data(), c.hhost + 128, (j + 2) * sizeof(double));
+      double s2 = h2[j + 1];  // ||w||^2 after the first projection
       for (int i = 0; i <= j; ++i) {
         H[i * m + j] = hv[i] + h2[i];
         s2 -= h2[i] * h2[i];
@@ -152,9 +218,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
         set_error("FGMRES: non-finite Arnoldi vector");
         return DG_ERR_NAN;
       }
-      H[(j + 1) * m + j] = hn;
-      if (hn > 0)
-        if (int rc = scale<T>(c, w, 1.0 / hn)) return rc;
+      H[(j + 1) * m + j] = hn;  // (w was scaled by 1 / hn on the device when hn > 0)
       // Givens rotations
       for (int i = 0; i < j; ++i) {
         const double a = H[i * m + j], bb = H[(i + 1) * m + j];
@@ -189,7 +253,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
                             "y copy"))
       return rc;
     const T* basis = (M || M0) ? Z : V;
-    dgb::lincomb_add<T, T><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(basis, n, jend, c.ydev, x, n);
+    if (int rc = lincomb_add<T>(c, basis, jend, c.ydev, x)) return rc;
     if (int rc = cuda_check(cudaStreamSynchronize(c.s), "solution update")) return rc;
     if (cycle_hook) cycle_hook(beta, r.res);
     if (est_conv && !true_residual_check) {
@@ -210,7 +274,7 @@ int ensure_ws(dg_handle* h, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(solver workspace)");
   h->ws_bytes = bytes;
   if (!h->ws_host) {
-    e = cudaMallocHost(&h->ws_host, 64 * sizeof(double));
+    e = cudaMallocHost(&h->ws_host, 256 * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost(solver staging)");
   }
   return 0;
@@ -273,7 +337,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     }
   };
   // workspace: reductions, r/b copy, FP64 basis (V, Z), FP32 basis for the inner solve
-  const size_t small = (size_t)dgb::RED_BLOCKS * 64 + 128;
+  const size_t small = (size_t)dgb::RED_BLOCKS * dgb::MAX_ROWS + 192;
   size_t v64 = 0, v32 = 0;
   if (o->mode == DG_SOLVE_FP64) {
     v64 = (size_t)(m + 1 + (pc ? m : 0)) * n;
@@ -291,6 +355,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   c.part = base;
   c.hdev = base + (size_t)dgb::RED_BLOCKS * 64;
   c.ydev = c.hdev + 64;
+  c.h2dev = c.ydev + 64;
   double* bcopy = base + small;
   double* V64 = bcopy + n;
   float* f32 = reinterpret_cast<float*>(V64 + v64);

@@ -175,3 +175,32 @@ def test_solves_with_the_fast_diagonalisation_only(dg):
         assert st["rc"] == 0
         assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-9 * np.max(np.abs(x_ref))
     op.close()
+
+
+@pytest.mark.parametrize("case", ["odd_length", "unaligned_x", "restart_60"])
+def test_fgmres_basis_passes_off_the_packed_path(dg, case):
+    """The basis passes of FGMRES move 16-byte packs only when the vector length and every row start allow it.
+    An odd number of DOFs (81) runs them one element per load in FP32 and FP64; a solution vector one element past
+    a 16-byte boundary runs the update of x that way; a restart of 60 without a preconditioner takes up to 61 rows
+    of per-thread partial sums (more than 48 KB of shared memory in FP64)."""
+    n, k = ((3, 1, 1), 2) if case == "odd_length" else ((3, 2, 2), 2)
+    w = inputs.small_case(n=n, k=k, seed=8, b=(1.0, 0.5, 0.25), f_kind="sines")
+    w.f_params = inputs.sine_modes(9)
+    pr = oracle_problem(w)
+    A = oracle_matrix(pr)
+    F = oracle.rhs(pr, inputs.f_at(w, oracle.volume_points(pr)), None)
+    x_ref = np.linalg.solve(A, F)
+    op = dg.operator_for(w)
+    op.precond_setup()
+    long = case == "restart_60"
+    pc = dg.DG_PRECOND_NONE if long else dg.DG_PRECOND_BLOCK_JACOBI
+    for mode in (dg.DG_SOLVE_FP64, dg.DG_SOLVE_MIXED):
+        buf = torch.zeros(w.ndof + 1, dtype=torch.float64, device="cuda")
+        x = buf[1:] if case == "unaligned_x" else buf[:w.ndof]
+        st = op.solve(x, mode=mode, preconditioner=pc, rtol=1e-12, restart=60 if long else 20,
+                      outer_restart=8, inner_rtol=1e-2)
+        assert st["rc"] == 0
+        if long and mode == dg.DG_SOLVE_FP64:
+            assert st["iterations"] > 30  # the restart cycle grew past 30 rows
+        assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-9 * np.max(np.abs(x_ref)), st
+    op.close()
