@@ -189,21 +189,26 @@ def cpu_baseline(w, seconds=15.0):
 
 
 def run_profile_solver(args):
-    """Minimal launch sequence for profilers of the solver kernels at 48^3 Q5: FP32 block-Jacobi
-    applications and learned-preconditioner applications (untrained network)."""
+    """Minimal launch sequence for profilers of the solver kernels: at 48^3 Q5 (fast diagonalisation only, under
+    1 GB on the device) W + K FP32 and FP64 block-Jacobi applications and learned-preconditioner applications
+    (untrained network); then one outer iteration of the mixed solve (one inner FGMRES(30) cycle) at 32^3 Q5 for
+    the basis passes (about 3 GB)."""
     import torch
 
     from paper_1711_10885_gb300 import dg, inputs
     torch.cuda.set_device(0)
     w = inputs.unit_cube_q5_48(with_u=False)
     op = dg.operator_for(w)
-    op.precond_setup()
+    op.precond_setup(dg.DG_BJ_FAST_DIAG)
     mlp = dg.MLP(w.k, seed=0)
     r = torch.randn(w.ndof, dtype=torch.float32, device="cuda")
     z = torch.empty_like(r)
+    r64, z64 = r.double(), torch.empty(w.ndof, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     for _ in range(args.warmup + args.steps):
         op.precond_apply(r, z)
+    for _ in range(args.warmup + args.steps):
+        op.precond_apply(r64, z64)
     for _ in range(args.warmup + args.steps):
         mlp.apply(op, r, z)
     torch.cuda.synchronize()
@@ -215,10 +220,19 @@ def run_profile_solver(args):
     b.synchronize()
     ms = a.elapsed_time(b) / 10
     flops = 2.0 * w.ncell * (256 * mlp.kinp + 256 * 256 + mlp.outp * 256)
-    print(json.dumps({"profile": "solver", "mlp_apply_ms": ms, "mlp_tflops": flops / (ms * 1e-3) / 1e12,
-                      "cells": w.ncell}))
     mlp.close()
     op.close()
+    del r, z, r64, z64
+    ws = inputs.Workload("unit_cube_q5_32", (32, 32, 32), 5, inputs.log_normal_D(32 ** 3, 1.0, 3), f_kind="sines",
+                         f_params=inputs.sine_modes(4))
+    ops = dg.operator_for(ws)
+    ops.precond_setup(dg.DG_BJ_FAST_DIAG)
+    x = torch.zeros(ws.ndof, dtype=torch.float64, device="cuda")
+    st = ops.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=1e-10, restart=30,
+                   outer_restart=10, inner_rtol=1e-3, max_iterations=1, raise_on_error=False)
+    ops.close()
+    print(json.dumps({"profile": "solver", "mlp_apply_ms": ms, "mlp_tflops": flops / (ms * 1e-3) / 1e12,
+                      "cells": w.ncell, "solve_32": {k: st[k] for k in ("iterations", "inner_iterations")}}))
 
 
 def run_profile(args):

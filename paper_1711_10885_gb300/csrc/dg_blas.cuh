@@ -9,8 +9,10 @@ namespace dgb {
 
 constexpr int RED_BLOCKS = 152 * 4;   // rows of the partial-sum buffer hold up to this many block sums
 constexpr int RED_THREADS = 256;
-constexpr int PASS_BLOCKS = 152 * 2;  // grid of the basis passes: two CTAs per SM, one wave
-constexpr int LOADS = 8;              // basis rows whose packs are loaded together (in flight per thread)
+constexpr int PASS_MINB = 3;           // resident CTAs per SM of the basis passes (their launch bounds)
+constexpr int PASS_BLOCKS = 152 * PASS_MINB;  // their grid: one wave
+constexpr int PASS_LOADS = 8;          // rows loaded together by the dot and update passes (80 registers or fewer)
+constexpr int FUSED_LOADS = 6;         // the same for the fused update-and-dots pass (no spills at 3 CTAs per SM)
 constexpr int MAX_ROWS = 64;          // basis rows per pass (restart lengths up to 60, plus w . w)
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -39,8 +41,8 @@ __device__ __forceinline__ Pack<T, W> ld_pack(const T* row, size_t p) {
 // UPDATE = true:  w <- w - sum_q h[q] V_q first (h on the device); then the same dots with the new w, and
 //                 part[nv * gridDim.x + b] = its share of w . w
 // Dynamic shared memory: (nv + UPDATE) * RED_THREADS * sizeof(T).  w is not a row of V[0 .. nv).
-template <typename T, int W, bool UPDATE>
-__global__ void __launch_bounds__(RED_THREADS, 2)
+template <typename T, int W, bool UPDATE, int MINB = 2, int LOADS = 8>
+__global__ void __launch_bounds__(RED_THREADS, MINB)
 basis_dots(const T* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, T* w, size_t npack,
            double* __restrict__ part) {
   extern __shared__ unsigned char basis_smem[];
@@ -117,8 +119,8 @@ __global__ void mdot_final(const double* __restrict__ part, int nblk, double* __
 // w <- alpha (w - sum_{q < nv} h[q] V_q), h on the device.  alpha = 1, or with normalise
 // alpha = 1 / sqrt(h[nv] - sum_q h[q]^2): when h[q] = V_q . w and h[nv] = w . w for orthonormal rows V_q, that
 // is the inverse norm of the result (Pythagoras); alpha = 1 when the difference is not positive.
-template <typename T, int W>
-__global__ void __launch_bounds__(RED_THREADS, 2)
+template <typename T, int W, int MINB = 2, int LOADS = 8>
+__global__ void __launch_bounds__(RED_THREADS, MINB)
 basis_update(const T* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, int normalise, T* w,
              size_t npack) {
   __shared__ T hs[MAX_ROWS];
@@ -159,8 +161,8 @@ basis_update(const T* __restrict__ V, size_t ld, int nv, const double* __restric
 }
 
 // x <- x + sum_{q < nv} y[q] Z_q  (the solution update of FGMRES; y on the device)
-template <typename T, int W>
-__global__ void __launch_bounds__(RED_THREADS, 2)
+template <typename T, int W, int MINB = 2, int LOADS = 8>
+__global__ void __launch_bounds__(RED_THREADS, MINB)
 lincomb_add(const T* __restrict__ Z, size_t ld, int nv, const double* __restrict__ y, T* __restrict__ x,
             size_t npack) {
   __shared__ T ys[MAX_ROWS];

@@ -378,6 +378,152 @@ __global__ void __launch_bounds__(256) fdm_apply(const typename Cx<R>::type* __r
   for (int e = threadIdx.x; e < here * N3; e += blockDim.x) z[cell0 * N3 + e] = U[e].x;
 }
 
+// FP32 variant for n <= 6 with fewer shared-memory transactions: n threads per cell.  Thread p owns the plane
+// c = p for the x and y passes and the lines (a, b = p) for the z passes, so only two barriers separate the
+// passes.  Each pass holds its n x n complex matrix in registers (one load per thread instead of one per line)
+// and streams the thread's n lines through it; the first pass reads real data and the last keeps only the real
+// part.  Plane and table pitches are odd (in 8-byte words), so lanes of neighbouring planes and cells fall on
+// distinct shared-memory banks.
+template <int N>
+struct FdmPlanes {
+  static constexpr int NN = N * N, N3 = NN * N;
+  static constexpr int PP = NN | 1;                   // pitch of a plane c (complex words)
+  static constexpr int CP = N * PP;                   // pitch of a cell's data
+  static constexpr int TS = 3 * (2 * NN + N) + 1;     // table entries per cell
+  static constexpr int TSP = TS | 1;                  // their pitch in shared memory
+  static constexpr int CELL_BYTES = (CP + TSP) * 8;
+  static constexpr int CB_SMEM = 56 * 1024 / CELL_BYTES;
+  static constexpr int CB = CB_SMEM < 128 / N ? CB_SMEM : 128 / N;  // cells per CTA (4 CTAs per SM)
+  static constexpr int SMEM = CB * CELL_BYTES;
+};
+
+// u[base + i * stride] <- sum_l m[i][l] u[base + l * stride] (complex); RIN: the input is real; ROUT: only the
+// real part of the output is formed
+template <int N, bool RIN, bool ROUT>
+__device__ __forceinline__ void fdm_line(const float2 (&m)[N][N], float2* u, int base, int stride) {
+  float2 x[N], y[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) x[l] = u[base + l * stride];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      if (RIN) {
+        re = fmaf(m[i][l].x, x[l].x, re);
+        im = fmaf(m[i][l].y, x[l].x, im);
+      } else {
+        re = fmaf(m[i][l].x, x[l].x, fmaf(-m[i][l].y, x[l].y, re));
+        if (!ROUT) im = fmaf(m[i][l].x, x[l].y, fmaf(m[i][l].y, x[l].x, im));
+      }
+    }
+    y[i] = make_float2(re, im);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) u[base + i * stride] = y[i];
+}
+
+template <int N>
+__device__ __forceinline__ void fdm_matrix(float2 (&m)[N][N], const float2* M) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int l = 0; l < N; ++l) m[i][l] = M[i * N + l];
+}
+
+// asynchronous global -> shared copies (no registers held, so a thread keeps all its copies in flight)
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes_is_8) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (bytes_is_8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int N>
+__global__ void __launch_bounds__(128, 4) fdm_apply_planes(const float2* __restrict__ tab, const float* __restrict__ r,
+                                                          float* __restrict__ z, int64_t ncell) {
+  using P = FdmPlanes<N>;
+  constexpr int NN = P::NN, N3 = P::N3, PP = P::PP, CP = P::CP, TS = P::TS, TSP = P::TSP, AX = 2 * NN + N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* U = reinterpret_cast<float2*>(smem_raw);  // [CB][CP]: U[cell][c * PP + a + N b]
+  float2* T = U + P::CB * CP;                        // [CB][TSP]
+  const int64_t cell0 = (int64_t)blockIdx.x * P::CB;
+  const int here = (int)min((int64_t)P::CB, ncell - cell0);
+  // the real input of plane c sits in the upper half of its complex slot: floats PP .. PP + NN - 1 of the plane
+  for (int e = threadIdx.x; e < here * TS; e += blockDim.x) {
+    const int l = e / TS;
+    cp_async(T + l * TSP + (e - l * TS), tab + cell0 * TS + e, 1);
+  }
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3, rem = e - l * N3, c = rem / NN;
+    cp_async(reinterpret_cast<float*>(U + l * CP + c * PP) + PP + (rem - c * NN), r + cell0 * N3 + e, 0);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int lc = threadIdx.x / N, p = threadIdx.x - lc * N;
+  const bool active = lc < here;
+  float2* u = U + lc * CP;
+  const float2* tb = T + lc * TSP;
+  float2 m[N][N];
+  if (active) {  // W_x on the x-lines (b, c = p) from the real input, W_y on the y-lines (a, c = p)
+    fdm_matrix<N>(m, tb);
+    const float* ur = reinterpret_cast<const float*>(u + p * PP) + PP;
+    for (int b = 0; b < N; ++b) {
+      // line b's complex output (floats 2 N b .. 2 N (b + 1) - 1 of the plane) stays below the real input of the
+      // later lines (floats PP + N (b + 1) ...), since N (b + 1) <= N^2 < PP + 1
+      float x[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) x[l] = ur[N * b + l];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          re = fmaf(m[i][l].x, x[l], re);
+          im = fmaf(m[i][l].y, x[l], im);
+        }
+        u[p * PP + N * b + i] = make_float2(re, im);
+      }
+    }
+    fdm_matrix<N>(m, tb + AX);
+    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, p * PP + a, N);
+  }
+  __syncthreads();
+  if (active) {  // W_z on the z-lines (a, b = p); divide by lambda_x(a) + lambda_y(p) + lambda_z(c) + c |T|; V_z
+    fdm_matrix<N>(m, tb + 2 * AX);
+    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, a + N * p, PP);
+    const float2* lx = tb + 2 * NN;
+    const float2 ly = tb[AX + 2 * NN + p];
+    const float2* lz = tb + 2 * AX + 2 * NN;
+    const float cs = tb[TS - 1].x;
+    for (int a = 0; a < N; ++a) {
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        const float dr = lx[a].x + ly.x + lz[c].x + cs, di = lx[a].y + ly.y + lz[c].y;
+        const float inv = 1.f / (dr * dr + di * di);
+        float2 v = u[a + N * p + PP * c];
+        u[a + N * p + PP * c] = make_float2((v.x * dr + v.y * di) * inv, (v.y * dr - v.x * di) * inv);
+      }
+    }
+    fdm_matrix<N>(m, tb + 2 * AX + NN);
+    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, a + N * p, PP);
+  }
+  __syncthreads();
+  if (active) {  // V_y on the y-lines, V_x on the x-lines (real part only)
+    fdm_matrix<N>(m, tb + AX + NN);
+    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, p * PP + a, N);
+    fdm_matrix<N>(m, tb + NN);
+    for (int b = 0; b < N; ++b) fdm_line<N, false, true>(m, u, p * PP + N * b, 1);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3, rem = e - l * N3, c = rem / NN;
+    z[cell0 * N3 + e] = U[l * CP + c * PP + (rem - c * NN)].x;
+  }
+}
+
 namespace {
 
 // 1D cell operator of axis r for cell `cell` (row = test function, column = trial function), from the 1D
@@ -496,6 +642,30 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
   if (!tab) {
     set_error("block-Jacobi: the fast diagonalisation was not set up");
     return DG_ERR_INVALID_ARG;
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (N <= 6) {
+      switch (N) {
+#define FDMP(NV)                                                                                          \
+  case NV: {                                                                                              \
+    using P = FdmPlanes<NV>;                                                                              \
+    static bool attr = false;                                                                             \
+    if (!attr && P::SMEM > 48 * 1024) {                                                                   \
+      cudaError_t ea = cudaFuncSetAttribute(fdm_apply_planes<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                            P::SMEM);                                                     \
+      if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply_planes)");             \
+    }                                                                                                     \
+    attr = true;                                                                                          \
+    fdm_apply_planes<NV><<<(unsigned)((h->ncell + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>(          \
+        tab, r, z, h->ncell);                                                                             \
+    break;                                                                                                \
+  }
+        FDMP(2) FDMP(3) FDMP(4) FDMP(5) FDMP(6)
+#undef FDMP
+      }
+      cudaError_t e = cudaGetLastError();
+      return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation)");
+    }
   }
   switch (N) {
 #define FDM(NV)                                                                                           \

@@ -47,11 +47,14 @@ bool packable(size_t n, std::initializer_list<const void*> ptrs) {
 
 // the per-thread partial sums of a basis pass take up to MAX_ROWS columns of shared memory (128 KB in FP64),
 // beyond the 48 KB (static plus dynamic) a launch gets without opting in: opt in once per kernel
+template <typename T, bool UPDATE>
+constexpr int dots_loads() { return UPDATE ? dgb::FUSED_LOADS : dgb::PASS_LOADS; }
+
 template <typename T, int W, bool UPDATE>
 int basis_smem_attr() {
   static bool done = false;
   if (done) return 0;
-  if (int rc = cuda_check(cudaFuncSetAttribute(dgb::basis_dots<T, W, UPDATE>,
+  if (int rc = cuda_check(cudaFuncSetAttribute(dgb::basis_dots<T, W, UPDATE, dgb::PASS_MINB, dots_loads<T, UPDATE>()>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                dgb::MAX_ROWS * dgb::RED_THREADS * (int)sizeof(T)),
                           "basis pass shared memory"))
@@ -68,11 +71,12 @@ int basis_dots(Ctx& c, const T* V, int nv, const double* h, T* w, double* dst) {
   if (packable<T>(c.n, {V, w})) {
     constexpr int W = 16 / sizeof(T);
     if (int rc = basis_smem_attr<T, W, UPDATE>()) return rc;
-    dgb::basis_dots<T, W, UPDATE><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n / W,
-                                                                                    c.part);
+    dgb::basis_dots<T, W, UPDATE, dgb::PASS_MINB, dots_loads<T, UPDATE>()>
+        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n / W, c.part);
   } else {
     if (int rc = basis_smem_attr<T, 1, UPDATE>()) return rc;
-    dgb::basis_dots<T, 1, UPDATE><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n, c.part);
+    dgb::basis_dots<T, 1, UPDATE, dgb::PASS_MINB, dots_loads<T, UPDATE>()>
+        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n, c.part);
   }
   dgb::mdot_final<<<rows, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::PASS_BLOCKS, dst);
   return cuda_check(cudaGetLastError(), "basis dot kernels");
@@ -83,9 +87,9 @@ template <typename T>
 int basis_update(Ctx& c, const T* V, int nv, const double* h, bool normalise, T* w) {
   if (packable<T>(c.n, {V, w})) {
     constexpr int W = 16 / sizeof(T);
-    dgb::basis_update<T, W><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n / W);
+    dgb::basis_update<T, W, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n / W);
   } else {
-    dgb::basis_update<T, 1><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n);
+    dgb::basis_update<T, 1, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n);
   }
   return cuda_check(cudaGetLastError(), "basis update");
 }
@@ -95,9 +99,9 @@ template <typename T>
 int lincomb_add(Ctx& c, const T* Z, int nv, const double* y, T* x) {
   if (packable<T>(c.n, {Z, x})) {
     constexpr int W = 16 / sizeof(T);
-    dgb::lincomb_add<T, W><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n / W);
+    dgb::lincomb_add<T, W, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n / W);
   } else {
-    dgb::lincomb_add<T, 1><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n);
+    dgb::lincomb_add<T, 1, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n);
   }
   return cuda_check(cudaGetLastError(), "solution update");
 }

@@ -121,6 +121,8 @@ FDM_CASES = [
     ((4, 2, 2), 4, (0, 1, 1), ("dirichlet", "outflow", "neumann", "dirichlet", "neumann", "outflow")),
     ((2, 2, 3), 7, (0, 0, 0), ("neumann",) * 6),
     ((2, 2, 2), 6, (0, 0, 1), None),
+    ((3, 2, 3), 5, (1, 0, 1), ("outflow", "dirichlet", "dirichlet", "neumann", "dirichlet", "dirichlet")),
+    ((5, 3, 2), 1, (0, 1, 0), None),
 ]
 
 
