@@ -12,7 +12,6 @@ constexpr int RED_THREADS = 256;
 constexpr int PASS_MINB = 3;           // resident CTAs per SM of the basis passes (their launch bounds)
 constexpr int PASS_BLOCKS = 152 * PASS_MINB;  // their grid: one wave
 constexpr int PASS_LOADS = 8;          // rows loaded together by the dot and update passes (80 registers or fewer)
-constexpr int FUSED_LOADS = 6;         // the same for the fused update-and-dots pass (no spills at 3 CTAs per SM)
 constexpr int MAX_ROWS = 64;          // basis rows per pass (restart lengths up to 60, plus w . w)
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -37,44 +36,19 @@ __device__ __forceinline__ Pack<T, W> ld_pack(const T* row, size_t p) {
 // dot products in its own column of shared memory (acc[q * RED_THREADS + t]), so w is loaded once per pack
 // however many rows there are, and the block sums are taken in FP64 in a fixed order (deterministic).
 
-// UPDATE = false: part[q * gridDim.x + b] = this block's share of V_q . w              (q < nv)
-// UPDATE = true:  w <- w - sum_q h[q] V_q first (h on the device); then the same dots with the new w, and
-//                 part[nv * gridDim.x + b] = its share of w . w
-// Dynamic shared memory: (nv + UPDATE) * RED_THREADS * sizeof(T).  w is not a row of V[0 .. nv).
-template <typename T, int W, bool UPDATE, int MINB = 2, int LOADS = 8>
+// part[q * gridDim.x + b] = this block's share of V_q . w  (q < nv).  Dynamic shared memory:
+// nv * RED_THREADS * sizeof(T).
+template <typename T, int W, int MINB, int LOADS>
 __global__ void __launch_bounds__(RED_THREADS, MINB)
-basis_dots(const T* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, T* w, size_t npack,
+basis_dots(const T* __restrict__ V, size_t ld, int nv, const T* __restrict__ w, size_t npack,
            double* __restrict__ part) {
   extern __shared__ unsigned char basis_smem[];
   T* acc = reinterpret_cast<T*>(basis_smem);
-  __shared__ T hs[MAX_ROWS];
   const int t = threadIdx.x;
-  const int nrow = nv + (UPDATE ? 1 : 0);
-  for (int q = 0; q < nrow; ++q) acc[q * RED_THREADS + t] = T(0);
-  if (UPDATE && t < nv) hs[t] = (T)h[t];
+  for (int q = 0; q < nv; ++q) acc[q * RED_THREADS + t] = T(0);
   __syncthreads();
   for (size_t p = (size_t)blockIdx.x * RED_THREADS + t; p < npack; p += (size_t)gridDim.x * RED_THREADS) {
-    Pack<T, W> wp = ld_pack<T, W>(w, p);
-    if (UPDATE) {
-      for (int v0 = 0; v0 < nv; v0 += LOADS) {
-        Pack<T, W> a[LOADS];
-#pragma unroll
-        for (int q = 0; q < LOADS; ++q)
-          if (v0 + q < nv) a[q] = ld_pack<T, W>(V + (size_t)(v0 + q) * ld, p);
-#pragma unroll
-        for (int q = 0; q < LOADS; ++q)
-          if (v0 + q < nv) {
-#pragma unroll
-            for (int e = 0; e < W; ++e) wp.v[e] = fma(-hs[v0 + q], a[q].v[e], wp.v[e]);
-          }
-      }
-      reinterpret_cast<Pack<T, W>*>(w)[p] = wp;
-      T s = T(0);
-#pragma unroll
-      for (int e = 0; e < W; ++e) s = fma(wp.v[e], wp.v[e], s);
-      acc[nv * RED_THREADS + t] += s;
-    }
-    // (with UPDATE the rows were just read: these loads are served by the caches)
+    const Pack<T, W> wp = ld_pack<T, W>(w, p);
     for (int v0 = 0; v0 < nv; v0 += LOADS) {
       Pack<T, W> a[LOADS];
 #pragma unroll
@@ -93,11 +67,126 @@ basis_dots(const T* __restrict__ V, size_t ld, int nv, const double* __restrict_
   __syncthreads();
   // warp k reduces rows k, k + 8, ... over the block's threads in FP64
   const int lane = t & 31, wid = t >> 5;
-  for (int q = wid; q < nrow; q += RED_THREADS / 32) {
+  for (int q = wid; q < nv; q += RED_THREADS / 32) {
     double s = 0.0;
     for (int k = lane; k < RED_THREADS; k += 32) s += (double)acc[q * RED_THREADS + k];
     s = warp_sum(s);
     if (lane == 0) part[(size_t)q * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// Arnoldi with the reorthogonalisation delayed by one step takes two passes per step over the basis.  Rows
+// V_0 .. V_{nr-2} are final (orthonormal), the last row u = V_{nr-1} is provisional and w is the new vector.
+constexpr int DOTS2_THREADS = 128;
+constexpr int DOTS2_MINB = 6;
+constexpr int DOTS2_BLOCKS = 152 * DOTS2_MINB;
+constexpr int PART_ROWS = 2 * MAX_ROWS + 1;  // rows of block sums a pass can produce
+constexpr int DOTS2_LOADS = 6;
+
+// pass 1, dots against u and w in one pass:
+//   part row q       (q < nr): V_q . u   (q = nr - 1: u . u)
+//   part row nr + q  (q < nr): V_q . w
+//   part row 2 nr:             w . w
+// Dynamic shared memory: (2 nr + 1) * DOTS2_THREADS * sizeof(T).
+template <typename T, int W>
+__global__ void __launch_bounds__(DOTS2_THREADS, DOTS2_MINB)
+basis_dots2(const T* __restrict__ V, size_t ld, int nr, const T* __restrict__ w, size_t npack,
+            double* __restrict__ part) {
+  extern __shared__ unsigned char basis_smem[];
+  T* acc = reinterpret_cast<T*>(basis_smem);
+  const int t = threadIdx.x;
+  const int nrow = 2 * nr + 1, nf = nr - 1;
+  for (int q = 0; q < nrow; ++q) acc[q * DOTS2_THREADS + t] = T(0);
+  __syncthreads();
+  const T* u = V + (size_t)nf * ld;
+  for (size_t p = (size_t)blockIdx.x * DOTS2_THREADS + t; p < npack; p += (size_t)gridDim.x * DOTS2_THREADS) {
+    const Pack<T, W> wp = ld_pack<T, W>(w, p), up = ld_pack<T, W>(u, p);
+    for (int v0 = 0; v0 < nf; v0 += DOTS2_LOADS) {
+      Pack<T, W> a[DOTS2_LOADS];
+#pragma unroll
+      for (int q = 0; q < DOTS2_LOADS; ++q)
+        if (v0 + q < nf) a[q] = ld_pack<T, W>(V + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < DOTS2_LOADS; ++q)
+        if (v0 + q < nf) {
+          T su = T(0), sw = T(0);
+#pragma unroll
+          for (int e = 0; e < W; ++e) {
+            su = fma(a[q].v[e], up.v[e], su);
+            sw = fma(a[q].v[e], wp.v[e], sw);
+          }
+          acc[(v0 + q) * DOTS2_THREADS + t] += su;
+          acc[(nr + v0 + q) * DOTS2_THREADS + t] += sw;
+        }
+    }
+    T uu = T(0), uw = T(0), ww = T(0);
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      uu = fma(up.v[e], up.v[e], uu);
+      uw = fma(up.v[e], wp.v[e], uw);
+      ww = fma(wp.v[e], wp.v[e], ww);
+    }
+    acc[nf * DOTS2_THREADS + t] += uu;
+    acc[(nr + nf) * DOTS2_THREADS + t] += uw;
+    acc[2 * nr * DOTS2_THREADS + t] += ww;
+  }
+  __syncthreads();
+  const int lane = t & 31, wid = t >> 5;
+  for (int q = wid; q < nrow; q += DOTS2_THREADS / 32) {
+    double s = 0.0;
+    for (int k = lane; k < DOTS2_THREADS; k += 32) s += (double)acc[q * DOTS2_THREADS + k];
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)q * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// pass 2 (coef on the device: a[q] at coef[q], d[q] at coef[MAX_ROWS + q] for q < nr - 1, then 1/alpha, e, 1/beta
+// at coef[2 MAX_ROWS + 0, 1, 2]):
+//   u = V_{nr-1} <- (u - sum_q a[q] V_q) / alpha         (the reorthogonalised final row; only when write_u)
+//   w            <- (w - sum_q d[q] V_q - e u_old) / beta  (the next provisional row)
+template <typename T, int W>
+__global__ void __launch_bounds__(RED_THREADS, PASS_MINB)
+basis_update2(T* V, size_t ld, int nr, const double* __restrict__ coef, int write_u, T* w, size_t npack) {
+  __shared__ T as[MAX_ROWS], ds[MAX_ROWS];
+  __shared__ T sc[3];
+  const int t = threadIdx.x, nf = nr - 1;
+  if (t < nf) {
+    as[t] = (T)coef[t];
+    ds[t] = (T)coef[MAX_ROWS + t];
+  }
+  if (t < 3) sc[t] = (T)coef[2 * MAX_ROWS + t];
+  __syncthreads();
+  const T ia = sc[0], e = sc[1], ib = sc[2];
+  T* u = V + (size_t)nf * ld;
+  for (size_t p = (size_t)blockIdx.x * RED_THREADS + t; p < npack; p += (size_t)gridDim.x * RED_THREADS) {
+    Pack<T, W> up = ld_pack<T, W>(u, p), wp = ld_pack<T, W>(w, p), tu, tw;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      tu.v[k] = up.v[k];
+      tw.v[k] = fma(-e, up.v[k], wp.v[k]);
+    }
+    for (int v0 = 0; v0 < nf; v0 += PASS_LOADS) {
+      Pack<T, W> a[PASS_LOADS];
+#pragma unroll
+      for (int q = 0; q < PASS_LOADS; ++q)
+        if (v0 + q < nf) a[q] = ld_pack<T, W>(V + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < PASS_LOADS; ++q)
+        if (v0 + q < nf) {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            tu.v[k] = fma(-as[v0 + q], a[q].v[k], tu.v[k]);
+            tw.v[k] = fma(-ds[v0 + q], a[q].v[k], tw.v[k]);
+          }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      tu.v[k] *= ia;
+      tw.v[k] *= ib;
+    }
+    if (write_u) reinterpret_cast<Pack<T, W>*>(u)[p] = tu;
+    reinterpret_cast<Pack<T, W>*>(w)[p] = tw;
   }
 }
 
@@ -113,50 +202,6 @@ __global__ void mdot_final(const double* __restrict__ part, int nblk, double* __
     double t = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
     h[blockIdx.x] = t;
-  }
-}
-
-// w <- alpha (w - sum_{q < nv} h[q] V_q), h on the device.  alpha = 1, or with normalise
-// alpha = 1 / sqrt(h[nv] - sum_q h[q]^2): when h[q] = V_q . w and h[nv] = w . w for orthonormal rows V_q, that
-// is the inverse norm of the result (Pythagoras); alpha = 1 when the difference is not positive.
-template <typename T, int W, int MINB = 2, int LOADS = 8>
-__global__ void __launch_bounds__(RED_THREADS, MINB)
-basis_update(const T* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, int normalise, T* w,
-             size_t npack) {
-  __shared__ T hs[MAX_ROWS];
-  __shared__ T alpha_s;
-  const int t = threadIdx.x;
-  if (t < nv) hs[t] = (T)h[t];
-  if (t == 0) {
-    double a = 1.0;
-    if (normalise) {
-      double s2 = h[nv];
-      for (int q = 0; q < nv; ++q) s2 -= h[q] * h[q];
-      if (s2 > 0.0) a = 1.0 / sqrt(s2);
-    }
-    alpha_s = (T)a;
-  }
-  __syncthreads();
-  const T alpha = alpha_s;
-  for (size_t p = (size_t)blockIdx.x * RED_THREADS + t; p < npack; p += (size_t)gridDim.x * RED_THREADS) {
-    Pack<T, W> wp = ld_pack<T, W>(w, p);
-    for (int v0 = 0; v0 < nv; v0 += LOADS) {
-      Pack<T, W> a[LOADS];
-#pragma unroll
-      for (int q = 0; q < LOADS; ++q)
-        if (v0 + q < nv) a[q] = ld_pack<T, W>(V + (size_t)(v0 + q) * ld, p);
-#pragma unroll
-      for (int q = 0; q < LOADS; ++q)
-        if (v0 + q < nv) {
-#pragma unroll
-          for (int e = 0; e < W; ++e) wp.v[e] = fma(-hs[v0 + q], a[q].v[e], wp.v[e]);
-        }
-    }
-    if (normalise) {
-#pragma unroll
-      for (int e = 0; e < W; ++e) wp.v[e] *= alpha;
-    }
-    reinterpret_cast<Pack<T, W>*>(w)[p] = wp;
   }
 }
 

@@ -26,10 +26,10 @@ struct Ctx {
   cudaStream_t s;
   size_t n;
   double* part;   // MAX_ROWS rows of RED_BLOCKS block sums
-  double* hdev;   // 64 results of the first projection (and of plain dot products)
+  double* hdev;   // 128 results of a dot pass
   double* ydev;   // 64 coefficients of the solution update
-  double* h2dev;  // 64 results of the second projection, then w . w
-  double* hhost;  // pinned, 256
+  double* cdev;   // 2 MAX_ROWS + 3 coefficients of the second basis pass
+  double* hhost;  // pinned, 512: reduction results at 0, solution coefficients at 0, pass coefficients at 256
   int applies64 = 0, applies32 = 0;
 };
 
@@ -45,16 +45,13 @@ bool packable(size_t n, std::initializer_list<const void*> ptrs) {
   return true;
 }
 
-// the per-thread partial sums of a basis pass take up to MAX_ROWS columns of shared memory (128 KB in FP64),
-// beyond the 48 KB (static plus dynamic) a launch gets without opting in: opt in once per kernel
-template <typename T, bool UPDATE>
-constexpr int dots_loads() { return UPDATE ? dgb::FUSED_LOADS : dgb::PASS_LOADS; }
-
-template <typename T, int W, bool UPDATE>
+// the per-thread partial sums of a dot pass take up to MAX_ROWS columns of shared memory (128 KB in FP64), beyond
+// the 48 KB a launch gets without opting in: opt in once per kernel
+template <typename T, int W>
 int basis_smem_attr() {
   static bool done = false;
   if (done) return 0;
-  if (int rc = cuda_check(cudaFuncSetAttribute(dgb::basis_dots<T, W, UPDATE, dgb::PASS_MINB, dots_loads<T, UPDATE>()>,
+  if (int rc = cuda_check(cudaFuncSetAttribute(dgb::basis_dots<T, W, dgb::PASS_MINB, dgb::PASS_LOADS>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                dgb::MAX_ROWS * dgb::RED_THREADS * (int)sizeof(T)),
                           "basis pass shared memory"))
@@ -63,35 +60,22 @@ int basis_smem_attr() {
   return 0;
 }
 
-// dst[q] = V_q . w (q < nv) on the device; with UPDATE, w <- w - sum_q h[q] V_q first and dst[nv] = w . w
-template <typename T, bool UPDATE>
-int basis_dots(Ctx& c, const T* V, int nv, const double* h, T* w, double* dst) {
-  const int rows = nv + (UPDATE ? 1 : 0);
-  const size_t smem = (size_t)rows * dgb::RED_THREADS * sizeof(T);
-  if (packable<T>(c.n, {V, w})) {
-    constexpr int W = 16 / sizeof(T);
-    if (int rc = basis_smem_attr<T, W, UPDATE>()) return rc;
-    dgb::basis_dots<T, W, UPDATE, dgb::PASS_MINB, dots_loads<T, UPDATE>()>
-        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n / W, c.part);
-  } else {
-    if (int rc = basis_smem_attr<T, 1, UPDATE>()) return rc;
-    dgb::basis_dots<T, 1, UPDATE, dgb::PASS_MINB, dots_loads<T, UPDATE>()>
-        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, h, w, c.n, c.part);
-  }
-  dgb::mdot_final<<<rows, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::PASS_BLOCKS, dst);
-  return cuda_check(cudaGetLastError(), "basis dot kernels");
-}
-
-// w <- alpha (w - sum_q h[q] V_q), alpha the inverse norm of the result from h when normalise
+// dst[q] = V_q . w (q < nv) on the device
 template <typename T>
-int basis_update(Ctx& c, const T* V, int nv, const double* h, bool normalise, T* w) {
+int basis_dots(Ctx& c, const T* V, int nv, const T* w, double* dst) {
+  const size_t smem = (size_t)nv * dgb::RED_THREADS * sizeof(T);
   if (packable<T>(c.n, {V, w})) {
     constexpr int W = 16 / sizeof(T);
-    dgb::basis_update<T, W, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n / W);
+    if (int rc = basis_smem_attr<T, W>()) return rc;
+    dgb::basis_dots<T, W, dgb::PASS_MINB, dgb::PASS_LOADS>
+        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, w, c.n / W, c.part);
   } else {
-    dgb::basis_update<T, 1, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nv, h, normalise, w, c.n);
+    if (int rc = basis_smem_attr<T, 1>()) return rc;
+    dgb::basis_dots<T, 1, dgb::PASS_MINB, dgb::PASS_LOADS>
+        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, w, c.n, c.part);
   }
-  return cuda_check(cudaGetLastError(), "basis update");
+  dgb::mdot_final<<<nv, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::PASS_BLOCKS, dst);
+  return cuda_check(cudaGetLastError(), "basis dot kernels");
 }
 
 // x <- x + sum_q y[q] Z_q, y on the device
@@ -109,7 +93,7 @@ int lincomb_add(Ctx& c, const T* Z, int nv, const double* y, T* x) {
 // out_host[q] = V_q . w for q < nv (synchronises)
 template <typename T>
 int dots(Ctx& c, const T* V, int nv, const T* w, double* out_host) {
-  if (int rc = basis_dots<T, false>(c, V, nv, nullptr, const_cast<T*>(w), c.hdev)) return rc;
+  if (int rc = basis_dots<T>(c, V, nv, w, c.hdev)) return rc;
   if (int rc = cuda_check(cudaMemcpyAsync(c.hhost, c.hdev, nv * sizeof(double), cudaMemcpyDeviceToHost, c.s),
                           "dot copy"))
     return rc;
@@ -145,15 +129,71 @@ struct Result {
   bool converged = false;
 };
 
-// Flexible GMRES(m) on A x = b in precision T with right preconditioner M (nullptr: none).
-// V: (m+1) n, Z: m n (ignored without M).  x holds the initial guess unless x0_zero.
+// Pass 1 of the lagged Arnoldi step: dst[0 .. 2 nr] = (V_q . u, q < nr; V_q . w, q < nr; w . w), u = V_{nr-1}
+template <typename T>
+int basis_dots2(Ctx& c, const T* V, int nr, const T* w, double* dst) {
+  const int rows = 2 * nr + 1;
+  const size_t smem = (size_t)rows * dgb::DOTS2_THREADS * sizeof(T);
+  static bool attr_packed = false, attr_scalar = false;
+  const bool pk = packable<T>(c.n, {V, w});
+  constexpr int W = 16 / sizeof(T);
+  bool& attr = pk ? attr_packed : attr_scalar;
+  if (!attr) {
+    const int most = dgb::PART_ROWS * dgb::DOTS2_THREADS * (int)sizeof(T);
+    cudaError_t e = pk ? cudaFuncSetAttribute(dgb::basis_dots2<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)
+                       : cudaFuncSetAttribute(dgb::basis_dots2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (int rc = cuda_check(e, "basis pass shared memory")) return rc;
+    attr = true;
+  }
+  if (pk)
+    dgb::basis_dots2<T, W><<<dgb::DOTS2_BLOCKS, dgb::DOTS2_THREADS, smem, c.s>>>(V, c.n, nr, w, c.n / W, c.part);
+  else
+    dgb::basis_dots2<T, 1><<<dgb::DOTS2_BLOCKS, dgb::DOTS2_THREADS, smem, c.s>>>(V, c.n, nr, w, c.n, c.part);
+  dgb::mdot_final<<<rows, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::DOTS2_BLOCKS, dst);
+  return cuda_check(cudaGetLastError(), "basis dot kernels");
+}
+
+// Pass 2: coefficients from the host (staged in the pinned buffer, copied ahead of the kernel on the stream)
+template <typename T>
+int basis_update2(Ctx& c, T* V, int nr, const double* coef_host, bool write_u, T* w) {
+  double* stage = c.hhost + 256;
+  std::memcpy(stage, coef_host, (2 * dgb::MAX_ROWS + 3) * sizeof(double));
+  if (int rc = cuda_check(cudaMemcpyAsync(c.cdev, stage, (2 * dgb::MAX_ROWS + 3) * sizeof(double),
+                                          cudaMemcpyHostToDevice, c.s), "coefficient copy"))
+    return rc;
+  if (packable<T>(c.n, {V, w})) {
+    constexpr int W = 16 / sizeof(T);
+    dgb::basis_update2<T, W><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w,
+                                                                              c.n / W);
+  } else {
+    dgb::basis_update2<T, 1><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w, c.n);
+  }
+  return cuda_check(cudaGetLastError(), "basis update");
+}
+
+// Flexible GMRES(m) on A x = b in precision T with right preconditioner M (nullptr: none, z_j = v_j).
+// V: (m+1) n, Z: m n.  x holds the initial guess unless x0_zero.
+//
+// Arnoldi by classical Gram-Schmidt with the reorthogonalisation delayed by one step (two passes over the basis
+// per step instead of three).  At step j the rows V_0 .. V_{j-1} are final and V_j holds a provisional u_j (u_0 =
+// r0 / ||r0|| is final).  The step preconditions the provisional vector, z_j = M(u_j), forms w = A z_j and in
+// pass 1 takes a = V_{<j}^T u_j, ||u_j||^2, V_{<=j}^T w and ||w||^2.  The final v_j = (u_j - V_{<j} a) / alpha,
+// alpha^2 = ||u_j||^2 - ||a||^2, so the coefficients of w on the final basis are c_i = V_i . w (i < j) and
+// c_j = (u_j . w - a . c_{<j}) / alpha, and the projection of w leaves beta^2 = ||w||^2 - ||c||^2.  Pass 2
+// writes v_j and the next provisional row u_{j+1} = (w - V_{<=j} c) / beta (with v_j expressed through u_j).
+// Column j of H follows one step later, from w = V_{<=j} c + beta u_{j+1} and u_{j+1}'s own reorthogonalisation
+// (a', alpha'): H[0..j][j] = c + beta a', H[j+1][j] = beta alpha'.  FGMRES needs only A Z = V H with V
+// orthonormal, and z_j = M(u_j) is such a direction whatever the later correction of u_j.  Convergence is
+// decided on a provisional estimate (H[j+1][j] ~ beta); when it or the restart length stops the cycle, one more
+// dot pass finalises column j.
 template <typename T>
 int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, bool x0_zero, T* V, T* Z, int m,
            double tol_abs, int maxit, int max_cycles, bool true_residual_check, Result* out,
            const std::function<void(double, double)>& cycle_hook = {},
            const std::function<int(const T*, T*)>& M0 = {}) {
   const size_t n = c.n;
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), hv(m + 2), h2(m + 2), y(m);
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), res(2 * dgb::MAX_ROWS + 2),
+      a(m + 1), cc(m + 1), cprev(m + 1), coef(2 * dgb::MAX_ROWS + 3);
   Result r;
   for (int cycle = 0; cycle < max_cycles; ++cycle) {
     T* v0 = V;
@@ -182,69 +222,140 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     if (int rc = scale<T>(c, v0, 1.0 / beta)) return rc;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
-    int jend = 0;
+    int jend = 0, fin = 0;  // columns 0 .. fin-1 of H are final and rotated into g
     bool est_conv = false;
+    double btil = 0.0;      // provisional norm of the last projection
+    // rotate column col (previous rotations, then a new one annihilating H[col+1][col]) and update g
+    auto rotate = [&](int col) {
+      for (int i = 0; i < col; ++i) {
+        const double p = H[i * m + col], q = H[(i + 1) * m + col];
+        H[i * m + col] = cs[i] * p + sn[i] * q;
+        H[(i + 1) * m + col] = -sn[i] * p + cs[i] * q;
+      }
+      const double p = H[col * m + col], q = H[(col + 1) * m + col];
+      const double rr = std::hypot(p, q);
+      cs[col] = rr > 0 ? p / rr : 1.0;
+      sn[col] = rr > 0 ? q / rr : 0.0;
+      H[col * m + col] = rr;
+      H[(col + 1) * m + col] = 0.0;
+      g[col + 1] = -sn[col] * g[col];
+      g[col] = cs[col] * g[col];
+      fin = col + 1;
+      r.res = std::fabs(g[col + 1]);
+    };
+    // column col from the provisional coefficients cprev, btil and u_{col+1}'s reorthogonalisation (ap, alpha)
+    auto finalize = [&](int col, const double* ap, double alpha) {
+      for (int i = 0; i <= col; ++i) H[i * m + col] = cprev[i] + btil * ap[i];
+      H[(col + 1) * m + col] = btil * alpha;
+      rotate(col);
+    };
     for (int j = 0; j < m; ++j) {
-      T* vj = V + (size_t)j * n;
-      T* zj = (M || M0) ? Z + (size_t)j * n : vj;
+      T* uj = V + (size_t)j * n;
+      T* zj = Z + (size_t)j * n;
       T* w = V + (size_t)(j + 1) * n;
       if (j == 0 && M0) {
-        if (int rc = M0(vj, zj)) return rc;
+        if (int rc = M0(uj, zj)) return rc;
       } else if (M) {
-        if (int rc = M(vj, zj)) return rc;
-      } else if (M0) {
-        if (int rc = cuda_check(cudaMemcpyAsync(zj, vj, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s), "copy v"))
+        if (int rc = M(uj, zj)) return rc;
+      } else {
+        if (int rc = cuda_check(cudaMemcpyAsync(zj, uj, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s), "copy v"))
           return rc;
       }
       if (int rc = apply_A<T>(c, zj, w)) return rc;
-      // classical Gram-Schmidt, twice, in three passes over the basis with the coefficients kept on the device:
-      // h = V^T w; then w -= V h together with h2 = V^T w and ||w||^2; then w = (w - V h2) / ||w - V h2||, the
-      // norm by Pythagoras.  One synchronisation fetches h and h2 for the Hessenberg column.
-      if (int rc = basis_dots<T, false>(c, V, j + 1, nullptr, w, c.hdev)) return rc;
-      if (int rc = basis_dots<T, true>(c, V, j + 1, c.hdev, w, c.h2dev)) return rc;
-      if (int rc = basis_update<T>(c, V, j + 1, c.h2dev, true, w)) return rc;
-      if (int rc = cuda_check(cudaMemcpyAsync(c.hhost, c.hdev, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost,
-                                              c.s), "h copy"))
-        return rc;
-      if (int rc = cuda_check(cudaMemcpyAsync(c.hhost + 128, c.h2dev, (j + 2) * sizeof(double),
-                                              cudaMemcpyDeviceToHost, c.s), "h2 copy"))
+      // pass 1
+      if (int rc = basis_dots2<T>(c, V, j + 1, w, c.hdev)) return rc;
+      if (int rc = cuda_check(cudaMemcpyAsync(c.hhost, c.hdev, (2 * j + 3) * sizeof(double),
+                                              cudaMemcpyDeviceToHost, c.s), "dot copy"))
         return rc;
       if (int rc = cuda_check(cudaStreamSynchronize(c.s), "Arnoldi sync")) return rc;
-      std::memcpy(hv.data(), c.hhost, (j + 1) * sizeof(double));
-      std::memcpy(h2.data(), c.hhost + 128, (j + 2) * sizeof(double));
-      double s2 = h2[j + 1];  // ||w||^2 after the first projection
-      for (int i = 0; i <= j; ++i) {
-        H[i * m + j] = hv[i] + h2[i];
-        s2 -= h2[i] * h2[i];
+      std::memcpy(res.data(), c.hhost, (2 * j + 3) * sizeof(double));
+      const double* pu = res.data();          // V_q . u_j
+      const double* qw = res.data() + j + 1;  // V_q . w
+      const double ww = res[2 * j + 2];
+      double alpha = 1.0;                     // u_0 is final
+      if (j > 0) {
+        double s2 = pu[j];
+        for (int i = 0; i < j; ++i) {
+          a[i] = pu[i];
+          s2 -= a[i] * a[i];
+        }
+        if (!std::isfinite(s2)) {
+          set_error("FGMRES: non-finite Arnoldi vector");
+          return DG_ERR_NAN;
+        }
+        alpha = std::sqrt(std::max(s2, 0.0));
+        if (fin < j) finalize(j - 1, a.data(), alpha);
+        if (r.res <= tol_abs || alpha == 0.0) {  // converged, or u_j in the span of the final rows (breakdown)
+          est_conv = true;
+          jend = j;
+          break;
+        }
       }
-      const double hn = std::sqrt(std::max(s2, 0.0));
-      if (!std::isfinite(hn)) {
+      // coefficients of w on the final rows 0 .. j
+      double bt2 = ww, ca = 0.0;
+      for (int i = 0; i < j; ++i) {
+        cc[i] = qw[i];
+        ca += a[i] * qw[i];
+      }
+      cc[j] = (qw[j] - ca) / alpha;
+      for (int i = 0; i <= j; ++i) bt2 -= cc[i] * cc[i];
+      if (!std::isfinite(bt2)) {
         set_error("FGMRES: non-finite Arnoldi vector");
         return DG_ERR_NAN;
       }
-      H[(j + 1) * m + j] = hn;  // (w was scaled by 1 / hn on the device when hn > 0)
-      // Givens rotations
-      for (int i = 0; i < j; ++i) {
-        const double a = H[i * m + j], bb = H[(i + 1) * m + j];
-        H[i * m + j] = cs[i] * a + sn[i] * bb;
-        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
-      }
-      const double a = H[j * m + j], bb = H[(j + 1) * m + j];
-      const double rr = std::hypot(a, bb);
-      cs[j] = rr > 0 ? a / rr : 1.0;
-      sn[j] = rr > 0 ? bb / rr : 0.0;
-      H[j * m + j] = rr;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
       ++r.iterations;
       jend = j + 1;
-      r.res = std::fabs(g[j + 1]);
-      if (r.res <= tol_abs) {
+      for (int i = 0; i <= j; ++i) cprev[i] = cc[i];
+      if (bt2 <= 0.0) {  // w in the span of the basis: column j is final with a zero subdiagonal entry
+        btil = 0.0;
+        finalize(j, a.data(), 0.0);
         est_conv = true;
         break;
       }
-      if (r.iterations >= maxit || hn == 0.0) break;
+      btil = std::sqrt(bt2);
+      // pass 2: v_j = (u_j - V_{<j} a) / alpha, u_{j+1} = (w - V_{<j} d - e u_j) / btil
+      const double e = cc[j] / alpha;
+      for (int i = 0; i < j; ++i) {
+        coef[i] = a[i];
+        coef[dgb::MAX_ROWS + i] = cc[i] - e * a[i];
+      }
+      coef[2 * dgb::MAX_ROWS + 0] = 1.0 / alpha;
+      coef[2 * dgb::MAX_ROWS + 1] = e;
+      coef[2 * dgb::MAX_ROWS + 2] = 1.0 / btil;
+      if (int rc = basis_update2<T>(c, V, j + 1, coef.data(), j > 0, w)) return rc;
+      // provisional estimate of the residual after column j (H[j+1][j] ~ btil)
+      double hj = cc[j];
+      {
+        std::vector<double> col(cc.begin(), cc.begin() + j + 1);
+        for (int i = 0; i < j; ++i) {
+          const double p = col[i], q = col[i + 1];
+          col[i] = cs[i] * p + sn[i] * q;
+          col[i + 1] = -sn[i] * p + cs[i] * q;
+        }
+        hj = col[j];
+      }
+      const double prov = std::fabs(g[j]) * btil / std::max(std::hypot(hj, btil), 1e-300);
+      const bool last = j == m - 1 || r.iterations >= maxit;
+      if (prov <= tol_abs || last) {
+        // finalise column j: the reorthogonalisation of u_{j+1} against rows 0 .. j
+        if (int rc = dots<T>(c, V, j + 2, w, res.data())) return rc;
+        double s2 = res[j + 1];
+        for (int i = 0; i <= j; ++i) s2 -= res[i] * res[i];
+        if (!std::isfinite(s2)) {
+          set_error("FGMRES: non-finite Arnoldi vector");
+          return DG_ERR_NAN;
+        }
+        finalize(j, res.data(), std::sqrt(std::max(s2, 0.0)));
+        if (r.res <= tol_abs) {
+          est_conv = true;
+          break;
+        }
+        if (last) break;
+      }
+    }
+    if (fin != jend) {
+      set_error("FGMRES: internal error (Hessenberg column not finalised)");
+      return DG_ERR_INVALID_ARG;
     }
     // y = H^{-1} g (upper triangular), x += Z y
     for (int i = jend - 1; i >= 0; --i) {
@@ -256,8 +367,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     if (int rc = cuda_check(cudaMemcpyAsync(c.ydev, c.hhost, jend * sizeof(double), cudaMemcpyHostToDevice, c.s),
                             "y copy"))
       return rc;
-    const T* basis = (M || M0) ? Z : V;
-    if (int rc = lincomb_add<T>(c, basis, jend, c.ydev, x)) return rc;
+    if (int rc = lincomb_add<T>(c, Z, jend, c.ydev, x)) return rc;
     if (int rc = cuda_check(cudaStreamSynchronize(c.s), "solution update")) return rc;
     if (cycle_hook) cycle_hook(beta, r.res);
     if (est_conv && !true_residual_check) {
@@ -278,7 +388,7 @@ int ensure_ws(dg_handle* h, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(solver workspace)");
   h->ws_bytes = bytes;
   if (!h->ws_host) {
-    e = cudaMallocHost(&h->ws_host, 256 * sizeof(double));
+    e = cudaMallocHost(&h->ws_host, 512 * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost(solver staging)");
   }
   return 0;
@@ -341,13 +451,16 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     }
   };
   // workspace: reductions, r/b copy, FP64 basis (V, Z), FP32 basis for the inner solve
-  const size_t small = (size_t)dgb::RED_BLOCKS * dgb::MAX_ROWS + 192;
+  // partial sums (rows x blocks of the widest pass), then the dot results (128), y (128) and the pass
+  // coefficients (2 MAX_ROWS + 3 = 131); 400 keeps what follows 16-byte aligned
+  const size_t part_size = (size_t)dgb::PART_ROWS * std::max(dgb::DOTS2_BLOCKS, dgb::RED_BLOCKS);
+  const size_t small = part_size + 400;
   size_t v64 = 0, v32 = 0;
   if (o->mode == DG_SOLVE_FP64) {
-    v64 = (size_t)(m + 1 + (pc ? m : 0)) * n;
+    v64 = (size_t)(2 * m + 1) * n;  // V and Z (Z = V's provisional rows without a preconditioner)
   } else {
     v64 = (size_t)(2 * mo + 1) * n;
-    v32 = (size_t)(m + 1 + (pc ? m : 0) + 2) * n;
+    v32 = (size_t)(2 * m + 1 + 2) * n;
   }
   const size_t bytes = (small + n + v64) * sizeof(double) + v32 * sizeof(float) + 256;
   if (int rc = ensure_ws(h, bytes)) return rc;
@@ -357,9 +470,9 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   c.n = n;
   double* base = static_cast<double*>(h->ws);
   c.part = base;
-  c.hdev = base + (size_t)dgb::RED_BLOCKS * 64;
-  c.ydev = c.hdev + 64;
-  c.h2dev = c.ydev + 64;
+  c.hdev = base + part_size;  // up to 2 * 61 + 1 results of a pass
+  c.ydev = c.hdev + 128;
+  c.cdev = c.ydev + 128;
   double* bcopy = base + small;
   double* V64 = bcopy + n;
   float* f32 = reinterpret_cast<float*>(V64 + v64);
@@ -404,7 +517,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     // inner FP32 FGMRES(m) on the FP32 operator, x0 = 0, one cycle or until inner_rtol: z = P(v)
     float* V32 = f32;
     float* Z32 = V32 + (size_t)(m + 1) * n;
-    float* rhs32 = Z32 + (pc ? (size_t)m * n : 0);
+    float* rhs32 = Z32 + (size_t)m * n;
     float* e32 = rhs32 + n;
     std::function<int(const float*, float*)> M32;
     // block-Jacobi inside the FP32 inner solve: the FP16 blocks (half the bytes of this HBM-bound product) unless
