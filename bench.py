@@ -38,8 +38,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
 # kernels as they were when profiled, keyed by the sha256 of the kernel source at that time.
 NCU_TRAFFIC = {
-    ("dg_cell_kernel", "d895148003a8cd9d"): 134606336 + 271982592,  # 134.61 MB read + 271.98 MB write
-    ("dg_face_kernel", "d895148003a8cd9d"): 474576128 + 113232128,  # 474.58 MB read + 113.23 MB write
+    ("dg_cell_kernel", "5eaf0d8c36ebbee1"): 134589696 + 273854720,  # 134.59 MB read + 273.85 MB write
+    ("dg_face_kernel", "5eaf0d8c36ebbee1"): 474638080 + 112805888,  # 474.64 MB read + 112.81 MB write
 }
 
 
