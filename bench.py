@@ -348,7 +348,7 @@ def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10, w
     blocks; with_fp64=False skips the two-minute plain FP64 solve."""
     import torch
 
-    from paper_1711_10885_gb300 import dg, inputs
+    from paper_1711_10885_gb300 import dg, flops, inputs
     w = inputs.unit_cube_q5_48(with_u=False)
     op = dg.operator_for(w)
     # the fast diagonalisation alone (what the default mixed solve needs), then the dense blocks too
@@ -408,6 +408,10 @@ def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10, w
         b.record()
         b.synchronize()
         out[f"apply_{prec}_mdofs"] = w.ndof * 20 / (a.elapsed_time(b) * 1e-3) / 1e6
+        # executed flops of the cell and face kernels (flops.py model) against the unit-count peak
+        tflops = out[f"apply_{prec}_mdofs"] * 1e6 * flops.apply_flops_per_dof(w.k, w.n, residual=False) / 1e12
+        out[f"apply_{prec}_tflops"] = tflops
+        out[f"apply_{prec}_frac_of_peak"] = tflops / (FP32_PEAK_TFLOPS if prec == "f32" else FP64_PEAK_TFLOPS)
         r = torch.empty_like(u)
         a.record()
         for _ in range(20):
