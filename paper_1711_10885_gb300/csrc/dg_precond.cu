@@ -397,9 +397,9 @@ struct FdmPlanes {
   static constexpr int SMEM = CB * CELL_BYTES;
 };
 
-// u[base + i * stride] <- sum_l m[i][l] u[base + l * stride] (complex); RIN: the input is real; ROUT: only the
-// real part of the output is formed
-template <int N, bool RIN, bool ROUT>
+// u[base + i * stride] <- sum_l m[i][l] u[base + l * stride] (complex); ROUT: only the real part of the output
+// is formed
+template <int N, bool ROUT>
 __device__ __forceinline__ void fdm_line(const float2 (&m)[N][N], float2* u, int base, int stride) {
   float2 x[N], y[N];
 #pragma unroll
@@ -409,13 +409,8 @@ __device__ __forceinline__ void fdm_line(const float2 (&m)[N][N], float2* u, int
     float re = 0.f, im = 0.f;
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      if (RIN) {
-        re = fmaf(m[i][l].x, x[l].x, re);
-        im = fmaf(m[i][l].y, x[l].x, im);
-      } else {
-        re = fmaf(m[i][l].x, x[l].x, fmaf(-m[i][l].y, x[l].y, re));
-        if (!ROUT) im = fmaf(m[i][l].x, x[l].y, fmaf(m[i][l].y, x[l].x, im));
-      }
+      re = fmaf(m[i][l].x, x[l].x, fmaf(-m[i][l].y, x[l].y, re));
+      if (!ROUT) im = fmaf(m[i][l].x, x[l].y, fmaf(m[i][l].y, x[l].x, im));
     }
     y[i] = make_float2(re, im);
   }
@@ -488,12 +483,12 @@ __global__ void __launch_bounds__(128, 4) fdm_apply_planes(const float2* __restr
       }
     }
     fdm_matrix<N>(m, tb + AX);
-    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, p * PP + a, N);
+    for (int a = 0; a < N; ++a) fdm_line<N, false>(m, u, p * PP + a, N);
   }
   __syncthreads();
   if (active) {  // W_z on the z-lines (a, b = p); divide by lambda_x(a) + lambda_y(p) + lambda_z(c) + c |T|; V_z
     fdm_matrix<N>(m, tb + 2 * AX);
-    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, a + N * p, PP);
+    for (int a = 0; a < N; ++a) fdm_line<N, false>(m, u, a + N * p, PP);
     const float2* lx = tb + 2 * NN;
     const float2 ly = tb[AX + 2 * NN + p];
     const float2* lz = tb + 2 * AX + 2 * NN;
@@ -508,14 +503,14 @@ __global__ void __launch_bounds__(128, 4) fdm_apply_planes(const float2* __restr
       }
     }
     fdm_matrix<N>(m, tb + 2 * AX + NN);
-    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, a + N * p, PP);
+    for (int a = 0; a < N; ++a) fdm_line<N, false>(m, u, a + N * p, PP);
   }
   __syncthreads();
   if (active) {  // V_y on the y-lines, V_x on the x-lines (real part only)
     fdm_matrix<N>(m, tb + AX + NN);
-    for (int a = 0; a < N; ++a) fdm_line<N, false, false>(m, u, p * PP + a, N);
+    for (int a = 0; a < N; ++a) fdm_line<N, false>(m, u, p * PP + a, N);
     fdm_matrix<N>(m, tb + NN);
-    for (int b = 0; b < N; ++b) fdm_line<N, false, true>(m, u, p * PP + N * b, 1);
+    for (int b = 0; b < N; ++b) fdm_line<N, true>(m, u, p * PP + N * b, 1);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
