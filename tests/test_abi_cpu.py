@@ -207,3 +207,30 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert int(out[name]) == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+
+
+def header_constants():
+    """Integer constants of include/dg.h: enumerators with explicit values and plain integer #defines."""
+    text = open(os.path.join(ROOT, "include", "dg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body in re.findall(r"\benum\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"\b(DG_\w+)\s*=\s*(-?\d+)", body):
+            out[name] = int(val)
+    for name, val in re.findall(r"^\s*#define\s+(DG_\w+)\s+(-?\d+)\s*$", text, flags=re.M):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    from paper_1711_10885_gb300 import dg
+    consts = header_constants()
+    # every option family of the header is visible in the binding, with the header's values
+    for prefix in ("DG_F", "DG_SOLVE_", "DG_PRECOND_", "DG_BJ_", "DG_BC_", "DG_VELOCITY_"):
+        names = [n for n in consts if n.startswith(prefix) and not n.startswith("DG_ERR_")]
+        assert names, prefix
+        for n in names:
+            assert getattr(dg, n) == consts[n], n
+    for n, v in consts.items():
+        if hasattr(dg, n):
+            assert getattr(dg, n) == v, n
