@@ -186,13 +186,18 @@ typedef struct {
                              copies of the dense blocks, each divided by its largest |entry| (half the
                              bytes of that bandwidth-bound product).  A flexible method tolerates the
                              rounding of the preconditioner.                                           */
+  int32_t outer_precision; /* MIXED: arithmetic of the operator in the outer FGMRES (its vectors,
+                             orthogonalisation and defect updates are FP64 either way): 0 = double-float
+                             (DG_F64X: FP64-level results on the FP32 pipes, about 4x faster on GB300),
+                             with the stopping test confirmed by a true FP64 residual and the solve
+                             finished in FP64 if that residual is still above rtol; 1 = FP64      */
 } dg_solve_opts;
 
 typedef struct {
   int32_t status;           /* DG_OK or the returned error code                                    */
   int32_t iterations;       /* FGMRES iterations (outer iterations in MIXED mode)                    */
   int32_t inner_iterations; /* FP32 inner iterations (MIXED), else equal to iterations              */
-  int32_t applies_f64;      /* FP64 operator applications                                           */
+  int32_t applies_f64;      /* operator applications on FP64 vectors (FP64 or double-float)         */
   int32_t applies_f32;      /* FP32 operator applications                                           */
   double rel_residual;      /* final ||b - A x||_2 / ||b||_2 (true FP64 residual at exit)           */
   double seconds;           /* wall time of the call                                                */

@@ -31,6 +31,7 @@ struct Ctx {
   double* cdev;   // 2 MAX_ROWS + 3 coefficients of the second basis pass
   double* hhost;  // pinned, 512: reduction results at 0, solution coefficients at 0, pass coefficients at 256
   int applies64 = 0, applies32 = 0;
+  bool f64x = false;  // FP64 vectors with the double-float operator
 };
 
 int cuda_check(cudaError_t e, const char* what) { return e == cudaSuccess ? 0 : cuda_fail(e, what); }
@@ -114,7 +115,7 @@ int apply_A(Ctx& c, const T* x, T* y);
 template <>
 int apply_A<double>(Ctx& c, const double* x, double* y) {
   ++c.applies64;
-  return launch_apply_f64(c.h, x, y, 0, 3, c.s);
+  return c.f64x ? launch_apply_f64x(c.h, x, y, 0, 3, c.s) : launch_apply_f64(c.h, x, y, 0, 3, c.s);
 }
 template <>
 int apply_A<float>(Ctx& c, const float* x, float* y) {
@@ -412,6 +413,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   const int mo = o->outer_restart > 0 ? o->outer_restart : 10;
   if (m > 60 || mo > 60 || (o->mode != DG_SOLVE_FP64 && o->mode != DG_SOLVE_MIXED) ||
       (o->inner_block_precision < 0 || o->inner_block_precision > 2) ||
+      (o->outer_precision < 0 || o->outer_precision > 1) ||
       (o->preconditioner != DG_PRECOND_NONE && o->preconditioner != DG_PRECOND_BLOCK_JACOBI &&
        o->preconditioner != DG_PRECOND_MLP && o->preconditioner != DG_PRECOND_BJ_MLP) ||
       !(o->rtol > 0) || (o->mode == DG_SOLVE_MIXED && !(o->inner_rtol > 0 && o->inner_rtol < 1))) {
@@ -558,8 +560,28 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
         if (int rc2 = P(v, z)) return rc2;
         return use_mlp ? mlp_apply_impl(mlp, h, v, z, DG_F64, 1, s) : 0;
       };
-    rc = fgmres<double>(c, P, bcopy, x_dev, false, V64, V64 + (size_t)(mo + 1) * n, mo, tol, maxit, 1 << 20, true,
-                        &res, {}, P0);
+    // the outer operator in double-float; once its FGMRES stops, the true residual with the FP64 operator
+    // decides, and the solve continues in FP64 from the current x if that residual is still above tol
+    c.f64x = o->outer_precision == 0;
+    for (bool first = true;; first = false) {
+      Result part;
+      rc = fgmres<double>(c, P, bcopy, x_dev, false, V64, V64 + (size_t)(mo + 1) * n, mo, tol,
+                          maxit - res.iterations, 1 << 20, true, &part, {}, P0);
+      res.iterations += part.iterations;
+      res.res = part.res;
+      res.converged = part.converged;
+      if (first) res.beta0 = part.beta0;
+      if (rc || !part.converged || !c.f64x) break;
+      c.f64x = false;
+      double* r64 = V64;  // the basis is free between calls
+      if ((rc = apply_A<double>(c, x_dev, r64))) break;
+      dgb::sub<double><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, s>>>(bcopy, r64, r64, n);
+      double rn2;
+      if ((rc = dots<double>(c, r64, 1, r64, &rn2))) break;
+      res.res = std::sqrt(rn2);
+      res.converged = res.res <= tol;
+      if (res.converged || res.iterations >= maxit) break;
+    }
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) {

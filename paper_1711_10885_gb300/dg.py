@@ -73,7 +73,8 @@ class dg_solve_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("preconditioner", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("outer_restart", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("inner_rtol", ctypes.c_double), ("mlp", ctypes.c_void_p), ("mlp_placement", ctypes.c_int32),
-                ("fallback_ratio", ctypes.c_double), ("inner_block_precision", ctypes.c_int32)]
+                ("fallback_ratio", ctypes.c_double), ("inner_block_precision", ctypes.c_int32),
+                ("outer_precision", ctypes.c_int32)]
 
 
 class dg_mlp_train_opts(ctypes.Structure):
@@ -378,7 +379,7 @@ class Operator:
 
     def solve(self, x, b=None, mode=DG_SOLVE_FP64, preconditioner=DG_PRECOND_BLOCK_JACOBI, restart=30,
               outer_restart=10, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True,
-              mlp=None, fallback_ratio=0.0, mlp_placement=0, inner_block_precision=0):
+              mlp=None, fallback_ratio=0.0, mlp_placement=0, inner_block_precision=0, outer_precision=0):
         """Solve A x = b (b = F when None) in place on the FP64 tensor x (dg_solve); returns the stats dict."""
         import torch
         if x.dtype != torch.float64:
@@ -388,7 +389,7 @@ class Operator:
             self._vec_check(b)
         o = dg_solve_opts(mode, preconditioner, restart, outer_restart, max_iterations, rtol, inner_rtol,
                           mlp.m.value if mlp is not None else None, int(mlp_placement), fallback_ratio,
-                          int(inner_block_precision))
+                          int(inner_block_precision), int(outer_precision))
         st = dg_solve_stats()
         rc = lib.dg_solve(self.h, ctypes.c_void_p(b.data_ptr()) if b is not None else None,
                           ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))
