@@ -59,7 +59,8 @@ def test_block_jacobi_matches_oracle_blocks(dg, n, k):
     op.close()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp64_bj", "mixed_bj", "mixed_bj32", "mixed_bj16", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_bj", "mixed_bj", "mixed_bj32", "mixed_bj16", "mixed",
+                                  "mixed_bj_fp64outer"])
 def test_fgmres_solution_matches_dense_solve(dg, mode):
     w = inputs.small_case(n=(3, 2, 2), k=2, seed=8, b=(1.0, 0.5, 0.25), f_kind="sines")
     w.f_params = inputs.sine_modes(9)
@@ -75,8 +76,10 @@ def test_fgmres_solution_matches_dense_solve(dg, mode):
         op.precond_setup()
     x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
     m = dg.DG_SOLVE_MIXED if mode.startswith("mixed") else dg.DG_SOLVE_FP64
+    # mixed modes: the outer operator in double-float with an FP64-confirmed stop (default), or FP64 throughout
     st = op.solve(x, mode=m, preconditioner=pc, rtol=1e-12, restart=20, outer_restart=8, inner_rtol=1e-2,
-                  inner_block_precision={"mixed_bj32": 1, "mixed_bj16": 2}.get(mode, 0))
+                  inner_block_precision={"mixed_bj32": 1, "mixed_bj16": 2}.get(mode, 0),
+                  outer_precision=1 if mode.endswith("fp64outer") else 0)
     assert st["rc"] == 0 and st["rel_residual"] <= 1e-12
     xs = x.cpu().numpy()
     # field error bound: ||x - x*|| <= cond(A) * rtol * ||x*||; checked directly against the LU solution
@@ -110,6 +113,8 @@ def test_solver_errors(dg):
         op.solve(x, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI)
     with pytest.raises(dg.DGError):  # restart too long
         op.solve(x, preconditioner=dg.DG_PRECOND_NONE, restart=100)
+    with pytest.raises(dg.DGError):  # outer operator precision is 0 (double-float) or 1 (FP64)
+        op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_NONE, outer_precision=2)
     st = op.solve(x, preconditioner=dg.DG_PRECOND_NONE, max_iterations=2, rtol=1e-14, raise_on_error=False)
     assert st["rc"] == -4 and st["status"] == -4  # DG_ERR_NOT_CONVERGED
     op.close()
