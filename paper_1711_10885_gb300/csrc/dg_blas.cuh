@@ -254,13 +254,4 @@ sub(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_
     out[i] = a[i] - b[i];
 }
 
-// counts non-finite entries (NaN/Inf) into *bad (one atomic per block that saw one)
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) count_nonfinite(const T* __restrict__ a, size_t n, int* bad) {
-  int local = 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    local |= !isfinite((double)a[i]);
-  if (__syncthreads_or(local) && threadIdx.x == 0) atomicAdd(bad, 1);
-}
-
 }  // namespace dgb
