@@ -237,19 +237,19 @@ lincomb_add(const T* __restrict__ Z, size_t ld, int nv, const double* __restrict
   }
 }
 
-// out[i] = alpha * in[i] (with a precision change)
+// out[i] = alpha * in[i] (with a precision change; out may be in)
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(RED_THREADS)
-scale_copy(const TI* __restrict__ in, TO* __restrict__ out, double alpha, size_t n) {
+scale_copy(const TI* in, TO* out, double alpha, size_t n) {
   const TI a = (TI)alpha;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (TO)(a * in[i]);
 }
 
-// out[i] = a[i] - b[i]
+// out[i] = a[i] - b[i]  (out may be b: each element is read before it is written by the same thread)
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
-sub(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_t n) {
+sub(const T* __restrict__ a, const T* b, T* out, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = a[i] - b[i];
 }
