@@ -194,7 +194,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
            const std::function<int(const T*, T*)>& M0 = {}) {
   const size_t n = c.n;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), res(2 * dgb::MAX_ROWS + 2),
-      a(m + 1), cc(m + 1), cprev(m + 1), coef(2 * dgb::MAX_ROWS + 3);
+      a(m + 1), cc(m + 1), cprev(m + 1), col(m + 1), coef(2 * dgb::MAX_ROWS + 3);
   Result r;
   for (int cycle = 0; cycle < max_cycles; ++cycle) {
     T* v0 = V;
@@ -325,17 +325,13 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
       coef[2 * dgb::MAX_ROWS + 2] = 1.0 / btil;
       if (int rc = basis_update2<T>(c, V, j + 1, coef.data(), j > 0, w)) return rc;
       // provisional estimate of the residual after column j (H[j+1][j] ~ btil)
-      double hj = cc[j];
-      {
-        std::vector<double> col(cc.begin(), cc.begin() + j + 1);
-        for (int i = 0; i < j; ++i) {
-          const double p = col[i], q = col[i + 1];
-          col[i] = cs[i] * p + sn[i] * q;
-          col[i + 1] = -sn[i] * p + cs[i] * q;
-        }
-        hj = col[j];
+      for (int i = 0; i <= j; ++i) col[i] = cc[i];
+      for (int i = 0; i < j; ++i) {
+        const double p = col[i], q = col[i + 1];
+        col[i] = cs[i] * p + sn[i] * q;
+        col[i + 1] = -sn[i] * p + cs[i] * q;
       }
-      const double prov = std::fabs(g[j]) * btil / std::max(std::hypot(hj, btil), 1e-300);
+      const double prov = std::fabs(g[j]) * btil / std::max(std::hypot(col[j], btil), 1e-300);
       const bool last = j == m - 1 || r.iterations >= maxit;
       if (prov <= tol_abs || last) {
         // finalise column j: the reorthogonalisation of u_{j+1} against rows 0 .. j
