@@ -157,7 +157,7 @@ class Problem:
         self.D = _arr(np.full(self.ncell, float(D)) if D.ndim == 0 else D, self.ncell)
         self.b = _arr(b, 3)
         self.c = float(c)
-        self.sigma = float(sigma) if sigma is not None else penalty_sigma(self.k, "baseline")
+        self.sigma = float(sigma) if sigma is not None else penalty_sigma(self.k, "workload")
         self.nb = (self.k + 1) ** 3
         # periodic axes and a velocity field at the quadrature points (Sec. 5.3); see oracle_apply_ex
         self.periodic = np.ascontiguousarray(np.asarray(periodic, dtype=np.int32).reshape(3))
@@ -194,15 +194,15 @@ class Problem:
                 self.c, self.sigma)
 
 
-def penalty_sigma(k: int, mode: str = "baseline", alpha: float = 2.0, d: int = 3) -> float:
+def penalty_sigma(k: int, mode: str = "workload", alpha: float = 2.0, d: int = 3) -> float:
     """sigma in gamma_F = <delta-,delta+> sigma |F|/min|T| (Sec. 2).
 
-    'paper': alpha * p (p + d - 1) as printed with alpha = 2; 'baseline': 2 k (k+1), the value that the
+    'paper': alpha * p (p + d - 1) as printed with alpha = 2; 'workload': 2 k (k+1), the value that the
     benchmark workloads prescribe as "2k(k+1)/h" for D = I.
     """
     if mode == "paper":
         return alpha * k * (k + d - 1)
-    if mode == "baseline":
+    if mode == "workload":
         return 2.0 * k * (k + 1)
     raise ValueError(mode)
 

@@ -53,10 +53,10 @@ def test_basis_matches_numpy_and_is_orthonormal(k):
 
 KRON_CASES = [
     # n, k, b, c, penalty mode, lo, hi
-    ((1, 1, 1), 1, (1.0, 0.5, 0.25), 1.0, "baseline", (0, 0, 0), (1, 1, 1)),
-    ((2, 2, 2), 2, (1.0, 0.5, 0.25), 1.0, "baseline", (0, 0, 0), (1, 1, 1)),
+    ((1, 1, 1), 1, (1.0, 0.5, 0.25), 1.0, "workload", (0, 0, 0), (1, 1, 1)),
+    ((2, 2, 2), 2, (1.0, 0.5, 0.25), 1.0, "workload", (0, 0, 0), (1, 1, 1)),
     ((2, 3, 2), 3, (-0.7, 0.4, -1.3), 0.3, "paper", (0, -1, 0.5), (1, 2, 1.25)),
-    ((3, 1, 2), 2, (0.0, -2.0, 0.5), 0.0, "baseline", (-1, -1, -1), (2, 0, 1)),
+    ((3, 1, 2), 2, (0.0, -2.0, 0.5), 0.0, "workload", (-1, -1, -1), (2, 0, 1)),
 ]
 
 
@@ -128,7 +128,7 @@ def test_polynomial_solution_has_zero_residual(k, n):
     """Consistency: for u* in Q_k globally, f = -D lap u* + b.grad u* + c u*, g = u*: A Pi u* = F exactly."""
     rng = np.random.default_rng(3 + k)
     D0, b, c = 1.7, (0.8, -0.6, 0.35), 0.9
-    pr = oracle.Problem(n, k, D0, b=b, c=c, sigma=oracle.penalty_sigma(k, "baseline"), lo=(0.1, -0.2, 0.0),
+    pr = oracle.Problem(n, k, D0, b=b, c=c, sigma=oracle.penalty_sigma(k, "workload"), lo=(0.1, -0.2, 0.0),
                         hi=(1.3, 0.7, 0.8))
     terms = _poly_terms(k, rng)
     z = _proj_poly(pr, terms)
