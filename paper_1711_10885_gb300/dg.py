@@ -380,7 +380,11 @@ class Operator:
     def solve(self, x, b=None, mode=DG_SOLVE_FP64, preconditioner=DG_PRECOND_BLOCK_JACOBI, restart=30,
               outer_restart=10, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True,
               mlp=None, fallback_ratio=0.0, mlp_placement=0, inner_block_precision=0, outer_precision=0):
-        """Solve A x = b (b = F when None) in place on the FP64 tensor x (dg_solve); returns the stats dict."""
+        """Solve A x = b (b = F when None) in place on the FP64 tensor x (dg_solve); returns the stats dict.
+
+        DG_SOLVE_MIXED: inner_block_precision picks the inner FP32 solve's block inverse (0 fast
+        diagonalisation, 1 FP32 dense blocks, 2 scaled FP16 blocks); outer_precision picks the outer operator
+        (0 double-float with an FP64-confirmed stop, 1 FP64)."""
         import torch
         if x.dtype != torch.float64:
             raise TypeError("x must be float64")
