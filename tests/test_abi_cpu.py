@@ -234,3 +234,55 @@ def test_binding_constants_match_the_header():
     for n, v in consts.items():
         if hasattr(dg, n):
             assert getattr(dg, n) == v, n
+
+
+def declared_prototypes():
+    """(name, return type, [parameter types]) of every function include/dg.h declares."""
+    text = open(os.path.join(ROOT, "include", "dg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"^\s*#.*$", "", text, flags=re.M)
+    out = []
+    for ret, name, params in re.findall(r"([A-Za-z_][\w\s\*]*?)\b(dg_\w+)\s*\(([^)]*)\)\s*;", text):
+        ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        out.append((name, " ".join(ret.split()), ps))
+    return out
+
+
+def null_args(params):
+    vals = []
+    for p in params:
+        if "*" in p:
+            vals.append(ctypes.c_void_p(None))
+        elif "uint64_t" in p:
+            vals.append(ctypes.c_uint64(0))
+        elif "int64_t" in p:
+            vals.append(ctypes.c_int64(0))
+        elif "int32_t" in p:
+            vals.append(ctypes.c_int32(0))
+        elif "double" in p:
+            vals.append(ctypes.c_double(0.0))
+        elif "float" in p:
+            vals.append(ctypes.c_float(0.0))
+        else:
+            raise AssertionError(f"unmapped parameter type: {p}")
+    return vals
+
+
+def test_every_entry_point_rejects_null_handles_without_touching_the_device(lib):
+    """Every call with null handles, null pointers and zero sizes returns an error code and a message, except the
+    destroy calls, for which null is a no-op; nothing crashes and no device work starts."""
+    lib.dg_last_error.restype = ctypes.c_char_p
+    protos = declared_prototypes()
+    assert len(protos) >= 30
+    for name, ret, params in protos:
+        if name in ("dg_last_error", "dg_penalty_sigma"):
+            continue
+        assert ret.endswith("int"), (name, ret)
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        rc = fn(*null_args(params))
+        if name.endswith("_destroy"):
+            assert rc == 0, name
+        else:
+            assert rc < 0, name
+            assert lib.dg_last_error(), name
