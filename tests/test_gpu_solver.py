@@ -211,3 +211,17 @@ def test_fgmres_basis_passes_off_the_packed_path(dg, case):
             assert st["iterations"] > 30  # the restart cycle grew past 30 rows
         assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-9 * np.max(np.abs(x_ref)), st
     op.close()
+
+
+def test_non_finite_right_hand_side_is_reported(dg):
+    """A NaN in b: both solvers stop at the first residual norm and return DG_ERR_NAN (-6) with the status set."""
+    w = inputs.small_case(n=(2, 2, 2), k=2, seed=21)
+    op = dg.operator_for(w)
+    op.precond_setup()
+    b = torch.ones(w.ndof, dtype=torch.float64, device="cuda")
+    b[3] = float("nan")
+    for mode in (dg.DG_SOLVE_FP64, dg.DG_SOLVE_MIXED):
+        x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+        st = op.solve(x, b=b, mode=mode, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, raise_on_error=False)
+        assert st["rc"] == -6 and st["status"] == -6, (mode, st)
+    op.close()
