@@ -362,7 +362,7 @@ class Operator:
                                  self._precision(x, precision), int(bool(residual)), _stream_ptr(stream)))
         return y
 
-    def precond_setup(self, kind=DG_PRECOND_BLOCK_JACOBI, stream=None):
+    def precond_setup(self, kind=DG_BJ_DENSE, stream=None):
         """Block-Jacobi set-up (dg_precond_setup): DG_BJ_DENSE (default) assembles and inverts the dense per-cell
         blocks and builds the fast-diagonalisation tables; DG_BJ_FAST_DIAG builds only the latter."""
         check(lib.dg_precond_setup(self.h, int(kind), _stream_ptr(stream)))
