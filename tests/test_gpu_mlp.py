@@ -1,6 +1,7 @@
 """GPU tests of the learned preconditioner: feature rows, forward pass and gradients against the FP64
-MLP reference (oracle/mlp.py), training, checkpointing, and what the trained network gains inside
-FGMRES over block-Jacobi alone, with the block-Jacobi fallback."""
+MLP reference (oracle/mlp.py) element by element (bit for bit on a network whose arithmetic is exact,
+within propagated per-element bounds on random ones), training, checkpointing, and what the trained
+network gains inside FGMRES over block-Jacobi alone, with the block-Jacobi fallback."""
 
 import os
 import tempfile
@@ -10,6 +11,7 @@ import pytest
 
 from oracle import mlp as om
 from paper_1711_10885_gb300 import inputs
+from tests import mlp_bounds as mb
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -73,22 +75,96 @@ def test_feature_rows(dg):
     mlp.close()
 
 
-@pytest.mark.parametrize("k,rows", [(4, 300), (2, 77), (7, 65)])
-def test_forward_matches_oracle(dg, k, rows):
+def _pack(mlp, W1, b1, W2, b2, W3, b3):
+    p = np.zeros(mlp.nparam, dtype=np.float32)
+    o = mlp.offsets
+    for off, a in zip(o, (W1, b1, W2, b2, W3, b3)):
+        a = np.asarray(a, dtype=np.float32).ravel()
+        p[off:off + a.size] = a
+    return p
+
+
+# forward kernels: the tcgen05 kernel serves inference for degrees 1..5; the mma.sync kernel (training, and
+# degrees 6..7) is selected for every degree by DG_MLP_NO_TCGEN05
+KERNEL_CASES = [(1, 128, "tcgen05"), (2, 77, "tcgen05"), (4, 300, "tcgen05"), (5, 129, "tcgen05"),
+                (2, 77, "mma"), (4, 300, "mma"), (7, 65, "mma")]
+
+
+def _forward(mlp, X, kernel):
+    if kernel == "mma":
+        os.environ["DG_MLP_NO_TCGEN05"] = "1"
+    try:
+        return mlp.forward(X).cpu().numpy().astype(np.float64)
+    finally:
+        os.environ.pop("DG_MLP_NO_TCGEN05", None)
+
+
+@pytest.mark.parametrize("k,rows,kernel", KERNEL_CASES, ids=lambda c: str(c))
+def test_forward_exact_network_bitwise(dg, k, rows, kernel):
+    """On a network whose every FP32 sum and BF16 hidden activation is exact (tests/mlp_bounds.exact_network,
+    precondition checked here), the forward pass has one correct result: every output element must equal
+    the FP64 reference exactly, padding columns included (zero)."""
+    rng = np.random.default_rng(100 + k)
+    mlp = dg.MLP(k, seed=0)
+    W1, b1, W2, b2, W3, b3, make_rows = mb.exact_network(mlp.kin, mlp.kinp, mlp.nb, mlp.outp, rng)
+    X = make_rows(rows)
+    assert mb.forward_is_exact(X, W1, b1, W2, b2, W3, b3)
+    mlp.set_params(_pack(mlp, W1, b1, W2, b2, W3, b3))
+    y_ref, _, _ = om.forward(X, W1, b1, W2, b2, W3, b3, bf16_hidden=True)
+    Y = _forward(mlp, torch.tensor(X, dtype=torch.bfloat16, device="cuda"), kernel)
+    bad = np.argwhere(Y != y_ref)
+    assert bad.size == 0, (bad[:5], Y[tuple(bad[0])], y_ref[tuple(bad[0])])
+    mlp.close()
+
+
+@pytest.mark.parametrize("k,rows,kernel", KERNEL_CASES, ids=lambda c: str(c))
+def test_forward_random_network_elementwise(dg, k, rows, kernel):
+    """Random weights: every output element within its propagated bound (FP32 accumulation and possible BF16
+    flips of the hidden activations, tests/mlp_bounds.forward_bound), and in every output column
+    max |Y - Y_ref| <= 2^-8 max |Y_ref| (a hidden flip moves one activation by one BF16 step, 2^-7 of it)."""
     rng = np.random.default_rng(k)
     mlp = dg.MLP(k, seed=0)
     p = _random_params(mlp, rng)
     mlp.set_params(p)
     X = _rows(mlp, rng, rows)
-    Y = mlp.forward(torch.tensor(X, dtype=torch.bfloat16, device="cuda")).cpu().numpy()
+    Y = _forward(mlp, torch.tensor(X, dtype=torch.bfloat16, device="cuda"), kernel)
     W = om.unpack(p, mlp.offsets, mlp.kinp, mlp.outp)
-    y_ref, _, _ = om.forward(X, *W, bf16_hidden=True)
-    err = np.linalg.norm(Y[:, :mlp.nb] - y_ref[:, :mlp.nb]) / np.linalg.norm(y_ref[:, :mlp.nb])
-    assert err <= 2e-3, err
+    fb = mb.forward_bound(X, *W)
+    nb = mlp.nb
+    err = np.abs(Y[:, :nb] - fb["y"][:, :nb])
+    assert np.all(err <= fb["dy"][:, :nb]), np.max(err / fb["dy"][:, :nb])
+    colmax = np.max(np.abs(fb["y"][:, :nb]), axis=0)
+    assert np.all(np.max(err, axis=0) <= 2.0 ** -8 * colmax)
+    assert np.all(Y[:, nb:] == fb["y"][:, nb:])  # padding rows of W3 and b3 are zero
     mlp.close()
 
 
-def test_gradient_matches_oracle(dg):
+@pytest.mark.parametrize("k,rows", [(4, 200), (2, 131), (7, 96)])
+def test_gradient_exact_network_elementwise(dg, k, rows):
+    """Loss and every gradient element on the exact network: the forward pass is exact, so each gradient
+    element differs from the FP64 reference only by the FP32 backward arithmetic, bounded element by element
+    by gamma_K times its sum of absolute terms (tests/mlp_bounds.grad_bound)."""
+    rng = np.random.default_rng(200 + k)
+    mlp = dg.MLP(k, seed=0)
+    W1, b1, W2, b2, W3, b3, make_rows = mb.exact_network(mlp.kin, mlp.kinp, mlp.nb, mlp.outp, rng)
+    X = make_rows(rows)
+    assert mb.forward_is_exact(X, W1, b1, W2, b2, W3, b3)
+    T = np.round(rng.standard_normal((rows, mlp.nb)) * 64) / 64
+    mlp.set_params(_pack(mlp, W1, b1, W2, b2, W3, b3))
+    loss = mlp.loss_grad(torch.tensor(X, dtype=torch.bfloat16, device="cuda"),
+                         torch.tensor(T, dtype=torch.float32, device="cuda"))
+    loss_ref, g_ref, bounds = mb.grad_bound(X, T, W1, b1, W2, b2, W3, b3, mlp.nb, exact_forward=True)
+    assert abs(loss - loss_ref) <= 1e-6 * loss_ref
+    g = om.unpack(mlp.grad(), mlp.offsets, mlp.kinp, mlp.outp)
+    for name, a, b, bd in zip(["W1", "b1", "W2", "b2", "W3", "b3"], g, g_ref, bounds):
+        err = np.abs(a - b)
+        assert np.all(err <= bd), (name, np.unravel_index(np.argmax(err - bd), err.shape), np.max(err / (bd + 1e-300)))
+    mlp.close()
+
+
+def test_gradient_random_network_elementwise(dg):
+    """Random weights and inputs: every gradient element within its propagated bound, and per block
+    max |g - g_ref| <= 2^-8 max |g_ref| (a flipped BF16 hidden value changes one factor of a term by 2^-7)."""
     rng = np.random.default_rng(7)
     mlp = dg.MLP(4, seed=0)
     p = _random_params(mlp, rng)
@@ -96,14 +172,14 @@ def test_gradient_matches_oracle(dg):
     X = _rows(mlp, rng, 200)
     T = rng.standard_normal((200, mlp.nb)).astype(np.float32)
     loss = mlp.loss_grad(torch.tensor(X, dtype=torch.bfloat16, device="cuda"), torch.tensor(T, device="cuda"))
-    g = mlp.grad()
     W = om.unpack(p, mlp.offsets, mlp.kinp, mlp.outp)
-    loss_ref, g_ref = om.loss_and_grad(X, T, *W, nb=mlp.nb, bf16_hidden=True)
+    loss_ref, g_ref, bounds = mb.grad_bound(X, T, *W, nb=mlp.nb)
     assert abs(loss - loss_ref) <= 1e-3 * loss_ref
-    gW = om.unpack(g, mlp.offsets, mlp.kinp, mlp.outp)
-    for name, a, b in zip(["W1", "b1", "W2", "b2", "W3", "b3"], gW, g_ref):
-        err = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert err <= 2e-2, (name, err)
+    g = om.unpack(mlp.grad(), mlp.offsets, mlp.kinp, mlp.outp)
+    for name, a, b, bd in zip(["W1", "b1", "W2", "b2", "W3", "b3"], g, g_ref, bounds):
+        err = np.abs(a - b)
+        assert np.all(err <= bd), name
+        assert np.max(err) <= 2.0 ** -8 * np.max(np.abs(b)), (name, np.max(err) / np.max(np.abs(b)))
     mlp.close()
 
 
@@ -196,4 +272,32 @@ def test_tensor_memory_forward_equals_mma_sync_forward(dg, k, rows):
     assert torch.isfinite(y_tc).all()
     err = (torch.linalg.norm(y_tc - y_mma) / torch.linalg.norm(y_mma)).item()
     assert err <= 1e-3, err
+    mlp.close()
+
+
+def test_tcgen05_weight_wait_timeout_gives_nan_rows(dg):
+    """The tcgen05 forward kernel's bounded wait for its weights, made to give up at once
+    (DG_MLP_WEIGHT_WAIT_TRIES=0): the kernel issues no MMA and no further copy, waits for the copy in flight,
+    frees its tensor memory and returns NaN rows; a solve using the network reports DG_ERR_NAN; afterwards the
+    same call gives the normal result (the context is intact)."""
+    rng = np.random.default_rng(61)
+    mlp = dg.MLP(4, seed=0)
+    mlp.set_params(_random_params(mlp, rng))
+    X = torch.tensor(_rows(mlp, rng, 300), dtype=torch.bfloat16, device="cuda")
+    y_ok = mlp.forward(X)
+    os.environ["DG_MLP_WEIGHT_WAIT_TRIES"] = "0"
+    try:
+        y_to = mlp.forward(X)
+        torch.cuda.synchronize()
+        assert torch.isnan(y_to).all()
+        w = inputs.small_case(n=(4, 3, 3), k=4, seed=9)
+        op = dg.operator_for(w)
+        x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+        st = op.solve(x, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_MLP, mlp=mlp, rtol=1e-8,
+                      max_iterations=50, raise_on_error=False)
+        assert st["status"] == dg.DG_ERR_NAN, st
+        op.close()
+    finally:
+        del os.environ["DG_MLP_WEIGHT_WAIT_TRIES"]
+    assert torch.equal(mlp.forward(X), y_ok)
     mlp.close()

@@ -128,6 +128,27 @@ def test_unit_cube_q7_32_sampled_cells(dg):
     op.close()
 
 
+def test_unit_cube_q7_32_full_vector(dg):
+    """32^3 cells, Q_7, log-normal D, in the launch configuration that bench.py times: the WHOLE residual and
+    Jacobian (16.8 M entries) against the matrix-free Kronecker form of the same operator (exact 1D integrals,
+    pinned to the dense form and to the oracle in tests/test_kron_matfree_cpu.py); FP64 and double-float at
+    1e-12, FP32 at 1e-5."""
+    from tests import kron_reference as kr
+    w = inputs.unit_cube_q7_32()
+    sigma = dg.dg_penalty_sigma(w.k, 0)
+    y_ref = kr.apply_matfree(w.n, w.k, w.D, w.b, w.c, sigma, w.u, w.lo, w.hi)
+    r_ref = y_ref.copy()
+    r_ref[::w.nb] -= 1.0 / 32 ** 3  # f = 1, g = 0: F = |T| on mode 0
+    op = dg.operator_for(w)
+    u = torch.tensor(w.u, device="cuda")
+    assert relerr(op.apply_jacobian(u).cpu().numpy(), y_ref) <= TOL64
+    assert relerr(op.apply_residual(u).cpu().numpy(), r_ref) <= TOL64
+    assert relerr(op.apply_residual(u, precision=dg.DG_F64X).cpu().numpy(), r_ref) <= TOL64
+    assert relerr(op.apply_jacobian(u, precision=dg.DG_F64X).cpu().numpy(), y_ref) <= TOL64
+    assert relerr(op.apply_residual(u.float()).cpu().numpy(), r_ref) <= TOL32
+    op.close()
+
+
 def test_sine_source_and_dirichlet_data(dg):
     """Right hand side with a sine-mode f and non-zero Dirichlet g on every side."""
     w = inputs.small_case(n=(3, 4, 2), k=4, seed=5, f_kind="sines")

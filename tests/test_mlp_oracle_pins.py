@@ -63,3 +63,88 @@ def test_padding_outputs_do_not_enter_the_loss():
     l2, g2 = om.loss_and_grad(X, T, *P, nb=9, bf16_hidden=False)
     assert l1 == l2
     assert np.all(g2[4][9:] == 0)
+
+
+# ---- pins of the element-wise bounds that the GPU parity tests use (tests/mlp_bounds.py) ----
+
+def _dims(k):
+    nb = (k + 1) ** 3
+    kin = nb + 7
+    return nb, kin, (kin + 15) // 16 * 16, (nb + 15) // 16 * 16
+
+
+def _random_net(rng, k):
+    from tests import mlp_bounds as mb
+    nb, kin, kinp, outp = _dims(k)
+    W1, b1, W2, b2, W3, b3 = _small_net(rng, kin=kin, kinp=kinp, nb=nb, outp=outp)
+    f = lambda a: a.astype(np.float32).astype(np.float64)
+    X = np.zeros((150, kinp))
+    X[:, :kin] = rng.standard_normal((150, kin))
+    return [f(W1), f(b1), f(W2), f(b2), f(W3), f(b3)], om.bf16_round(X), rng.standard_normal((150, nb))
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5, 7])
+def test_exact_network_is_exact(k):
+    """The exact network's precondition holds, and an FP32 evaluation in two different summation orders
+    reproduces the FP64 reference bit for bit."""
+    from tests import mlp_bounds as mb
+    rng = np.random.default_rng(k)
+    nb, kin, kinp, outp = _dims(k)
+    W1, b1, W2, b2, W3, b3, make_rows = mb.exact_network(kin, kinp, nb, outp, rng)
+    X = make_rows(97)
+    assert mb.forward_is_exact(X, W1, b1, W2, b2, W3, b3)
+    y_ref, _, _ = om.forward(X, W1, b1, W2, b2, W3, b3, bf16_hidden=True)
+    y32, _ = mb.emulate_fp32(X, None, W1, b1, W2, b2, W3, b3, nb)
+    assert np.array_equal(y32.astype(np.float64), y_ref)
+    rev = np.arange(kinp)[::-1]
+    y32r, _ = mb.emulate_fp32(X[:, rev], None, W1[:, rev], b1, W2, b2, W3, b3, nb)
+    assert np.array_equal(y32r.astype(np.float64), y_ref)
+    assert not mb.forward_is_exact(X, W1 * 1.01, b1, W2, b2, W3, b3)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_bounds_hold_for_an_fp32_evaluation(k):
+    """An FP32 evaluation with BF16 hidden roundings (numpy's own summation order) stays inside every
+    per-element bound: forward and gradients, random and exact networks."""
+    from tests import mlp_bounds as mb
+    rng = np.random.default_rng(30 + k)
+    W, X, T = _random_net(rng, k)
+    nb = _dims(k)[0]
+    fb = mb.forward_bound(X, *W)
+    y32, g32 = mb.emulate_fp32(X, T, *W, nb)
+    assert np.all(np.abs(y32[:, :nb] - fb["y"][:, :nb]) <= fb["dy"][:, :nb])
+    _, g_ref, bounds = mb.grad_bound(X, T, *W, nb=nb)
+    for a, b, bd in zip(g32, g_ref, bounds):
+        assert np.all(np.abs(a - b) <= bd)
+    nb, kin, kinp, outp = _dims(k)
+    W1, b1, W2, b2, W3, b3, make_rows = mb.exact_network(kin, kinp, nb, outp, rng)
+    X = make_rows(120)
+    T = np.round(rng.standard_normal((120, nb)) * 64) / 64
+    _, g32 = mb.emulate_fp32(X, T, W1, b1, W2, b2, W3, b3, nb)
+    _, g_ref, bounds = mb.grad_bound(X, T, W1, b1, W2, b2, W3, b3, nb, exact_forward=True)
+    for a, b, bd in zip(g32, g_ref, bounds):
+        assert np.all(np.abs(a - b) <= bd)
+        assert np.max(bd) <= 1e-2 * np.max(np.abs(b))  # the bounds are tight enough to see a wrong element
+
+
+def test_bounds_catch_planted_mistakes():
+    """A swapped pair of output columns, or one gradient row taken from its neighbour, breaks the bounds."""
+    from tests import mlp_bounds as mb
+    rng = np.random.default_rng(5)
+    k = 2
+    nb, kin, kinp, outp = _dims(k)
+    W, X, T = _random_net(rng, k)
+    fb = mb.forward_bound(X, *W)
+    y32, _ = mb.emulate_fp32(X, None, *W, nb)
+    y_bad = y32.copy()
+    y_bad[:, [3, 4]] = y_bad[:, [4, 3]]
+    assert not np.all(np.abs(y_bad[:, :nb] - fb["y"][:, :nb]) <= fb["dy"][:, :nb])
+    W1, b1, W2, b2, W3, b3, make_rows = mb.exact_network(kin, kinp, nb, outp, rng)
+    X = make_rows(64)
+    T = np.round(rng.standard_normal((64, nb)) * 64) / 64
+    _, g32 = mb.emulate_fp32(X, T, W1, b1, W2, b2, W3, b3, nb)
+    _, g_ref, bounds = mb.grad_bound(X, T, W1, b1, W2, b2, W3, b3, nb, exact_forward=True)
+    for blk in (0, 2, 4):  # W1, W2, W3: row 1 replaced by row 0
+        bad = g32[blk].copy()
+        bad[1] = bad[0]
+        assert not np.all(np.abs(bad - g_ref[blk]) <= bounds[blk])
