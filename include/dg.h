@@ -331,8 +331,12 @@ int dg_batch_destroy(dg_batch* b);
  * allocating routine.
  *
  * Its work space (point-space residual, face traces, face coefficients) is a fixed device array
- * of DG_STATIC_SCRATCH_BYTES inside libdg.so.  Every GPU that loads the library holds this array
- * until the process exits.  A problem needs
+ * of DG_STATIC_SCRATCH_BYTES inside libdg.so.  The array is reserved on a device together with
+ * the library's kernel images: with CUDA's lazy module loading (the default of current toolkits)
+ * that happens at the first call of this entry point (or the first kernel launch of the library) on
+ * that device, otherwise when the library is loaded; from then on the device holds it until the
+ * process exits.  Callers that must not allocate after start-up should therefore make one call at
+ * start-up on each device they use.  A problem needs
  *     256-byte-rounded ncells*(k+1)^3*8  +  ncells*12*(k+1)^2*8  +  ncells*18*8  bytes,
  * for example at most about 3200 cells at k = 7 or 15000 cells at k = 3.  Larger problems are
  * rejected with DG_ERR_INVALID_ARG and a message; use dg_setup / dg_apply_jacobian for them.

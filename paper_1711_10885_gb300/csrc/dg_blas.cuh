@@ -7,10 +7,9 @@
 
 namespace dgb {
 
-constexpr int RED_BLOCKS = 152 * 4;   // rows of the partial-sum buffer hold up to this many block sums
+// grids are sized by the caller from the device's SM count: one wave of each kernel's resident CTAs
 constexpr int RED_THREADS = 256;
 constexpr int PASS_MINB = 3;           // resident CTAs per SM of the basis passes (their launch bounds)
-constexpr int PASS_BLOCKS = 152 * PASS_MINB;  // their grid: one wave
 constexpr int PASS_LOADS = 8;          // rows loaded together by the dot and update passes (80 registers or fewer)
 constexpr int MAX_ROWS = 64;          // basis rows per pass (restart lengths up to 60, plus w . w)
 
@@ -79,7 +78,6 @@ basis_dots(const T* __restrict__ V, size_t ld, int nv, const T* __restrict__ w, 
 // V_0 .. V_{nr-2} are final (orthonormal), the last row u = V_{nr-1} is provisional and w is the new vector.
 constexpr int DOTS2_THREADS = 128;
 constexpr int DOTS2_MINB = 6;
-constexpr int DOTS2_BLOCKS = 152 * DOTS2_MINB;
 constexpr int PART_ROWS = 2 * MAX_ROWS + 1;  // rows of block sums a pass can produce
 constexpr int DOTS2_LOADS = 6;
 

@@ -20,6 +20,21 @@ int cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
 }
 
+int sm_count() {
+  static std::atomic<int> cache[64];  // 0 = not queried yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  if (cached) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 // P_j(2x-1) and its x-derivative for j = 0..jmax (three-term recurrence, differentiated term by term)
 static void shifted_legendre(int jmax, double x, double* p, double* dp) {
   const double t = 2.0 * x - 1.0;
@@ -109,7 +124,8 @@ __global__ void cast_f64_to_f32(const double* __restrict__ a, float* __restrict_
 
 static int cast_launch(const double* a, float* b, dgk::dfl* x, int64_t n, cudaStream_t s) {
   const int64_t blocks64 = (n + 255) / 256;
-  const unsigned blocks = (unsigned)(blocks64 > 152 * 32 ? 152 * 32 : (blocks64 > 0 ? blocks64 : 1));
+  const int64_t cap = (int64_t)sm_count() * 32;
+  const unsigned blocks = (unsigned)(blocks64 > cap ? cap : (blocks64 > 0 ? blocks64 : 1));
   cast_f64_to_f32<<<blocks, 256, 0, s>>>(a, b, x, n);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "cast kernel");
@@ -202,6 +218,10 @@ int dg_setup_ex(const dg_mesh* mesh, int32_t k, const dg_coeffs* co, const dg_bc
     if (mesh->n[r] < 1 || !std::isfinite(mesh->lo[r]) || !std::isfinite(mesh->hi[r]) ||
         !(mesh->hi[r] > mesh->lo[r])) {
       set_error("dg_setup: each axis needs n >= 1 and finite lo < hi");
+      return DG_ERR_INVALID_ARG;
+    }
+    if (ncell > ((int64_t)1 << 30) / mesh->n[r]) {
+      set_error("dg_setup: too many cells");
       return DG_ERR_INVALID_ARG;
     }
     ncell *= mesh->n[r];

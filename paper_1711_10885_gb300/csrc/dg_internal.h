@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -95,9 +96,35 @@ struct dg_handle {
 namespace dgi {
 
 void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Streaming multiprocessors of the current device (queried once per device); grids of the memory-bound and
+// persistent kernels are sized from it.
+int sm_count();
+
+// A one-time setting per device and function (cudaFuncSetAttribute acts on the current device only): run(f)
+// calls f on the first use on each device and records success there.  Two threads that first meet a device at
+// once may both call f, which is harmless for the idempotent attribute settings it guards.
+class DeviceOnce {
+ public:
+  template <class F>
+  int run(F&& f) {
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return f();
+    const uint64_t bit = 1ull << dev;
+    if (done_.load(std::memory_order_acquire) & bit) return 0;
+    const int rc = f();
+    if (rc == 0) done_.fetch_or(bit, std::memory_order_acq_rel);
+    return rc;
+  }
+
+ private:
+  std::atomic<uint64_t> done_{0};
+};
 // Gauss-Legendre nodes/weights (M points) and the 1D matrices for N = k+1 modes (host, FP64)
 void build_tables(int N, int M, Tables1D* tb);
-int cuda_fail(cudaError_t e, const char* what);
 
 // mode 0: y = A z, mode 1: y = A z - F; stages: bit 0 cell kernel, bit 1 face kernel (3 = full apply)
 int launch_apply_f64(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s);

@@ -102,7 +102,7 @@ size_t face_smem() {
 }
 
 // cells per CTA of the small-mesh variant of the FP64 kernels: a quarter of the full tile, so that meshes of
-// fewer than 152 full tiles still spread over the 152 SMs (each SM issues only two FP64 FMAs per clock)
+// fewer full tiles than SMs still spread over all SMs (each SM issues only two FP64 FMAs per clock)
 template <int M>
 constexpr int small_cpb() {
   return dgk::Launch<M>::CPB / 4 > 0 ? dgk::Launch<M>::CPB / 4 : 1;
@@ -110,21 +110,21 @@ constexpr int small_cpb() {
 
 template <int N, typename T, typename TV = T, int M = N, bool VB = false, int CPB = dgk::Launch<M>::CPB>
 int set_smem_attrs() {
-  static bool done = false;  // per instantiation; attributes are per function
-  if (done) return 0;
-  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<M, T, CPB>());
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel)");
-  e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, true>(),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T, CPB>());
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
-  if constexpr (!VB) {
-    e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, false>(),
+  static DeviceOnce once;  // per instantiation and device; attributes are per function
+  return once.run([]() -> int {
+    cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, T, false, CPB, TV, M, VB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<M, T, CPB>());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel)");
+    e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, true>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T, CPB>());
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
-  }
-  done = true;
-  return 0;
+    if constexpr (!VB) {
+      e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, TV, M, VB, false>(),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<M, T, CPB>());
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel)");
+    }
+    return 0;
+  });
 }
 
 // face kernel launch: the periodic-aware variant when the mesh has a periodic axis (always for the
@@ -154,16 +154,16 @@ inline const Buffers& buffers_for<dgk::dfl>(const dg_handle* h) { return h->pX; 
 
 template <int N>
 int set_self_smem_attrs() {
-  static bool done = false;
-  if (done) return 0;
-  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, double, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<N, double>());
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel self)");
-  e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, double, true, dgk::Launch<N>::CPB, double, N, false, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<N, double>());
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel self)");
-  done = true;
-  return 0;
+  static DeviceOnce once;
+  return once.run([&]() -> int {
+    cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel<N, double, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem<N, double>());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel self)");
+    e = cudaFuncSetAttribute(dgk::dg_face_kernel<N, double, true, dgk::Launch<N>::CPB, double, N, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_smem<N, double>());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel self)");
+    return 0;
+  });
 }
 
 // geometry of the handle with the velocity field tables of the VB kernels (FP64, or the double-float copies)
@@ -223,7 +223,7 @@ template <int N, typename T, typename TV>
 int apply_sized(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s, const StageArgs* st) {
   if constexpr (std::is_same<T, double>::value && std::is_same<TV, double>::value &&
                 small_cpb<N>() < dgk::Launch<N>::CPB) {
-    if (h->ncell < (int64_t)152 * dgk::Launch<N>::CPB)
+    if (h->ncell < (int64_t)sm_count() * dgk::Launch<N>::CPB)
       return apply_n<N, T, TV, N, false, small_cpb<N>()>(h, z, y, mode, stages, s, st);
   }
   return apply_n<N, T, TV>(h, z, y, mode, stages, s, st);
@@ -352,18 +352,18 @@ namespace dgi {
 // Tensor diffusion / affine geometry kernels (M = N), FP64 (T = double) or double-float (T = dfl) operator.
 template <int N, typename T>
 int set_td_smem_attrs() {
-  static bool done = false;
-  if (done) return 0;
-  constexpr int CPB = dgk::Launch<N>::CPB;
-  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel_td<N, T, CPB, double, N>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * cell_smem<N, T>()));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel_td)");
-  e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, double, N, false, true, true>(),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(face_smem<N, T>() + (size_t)CPB * 4 * N * N * sizeof(T)));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel td)");
-  done = true;
-  return 0;
+  static DeviceOnce once;
+  return once.run([&]() -> int {
+    constexpr int CPB = dgk::Launch<N>::CPB;
+    cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel_td<N, T, CPB, double, N>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * cell_smem<N, T>()));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel_td)");
+    e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, double, N, false, true, true>(),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(face_smem<N, T>() + (size_t)CPB * 4 * N * N * sizeof(T)));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel td)");
+    return 0;
+  });
 }
 
 template <int N, typename T>
@@ -420,18 +420,18 @@ namespace dgi {
 // (q = 2p+4); FP64 (T = double) or double-float (T = dfl) operator, FP64 vectors.
 template <int N, typename T, int M>
 int set_pw_smem_attrs() {
-  static bool done = false;
-  if (done) return 0;
-  constexpr int CPB = dgk::Launch<M>::CPB;
-  cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel_td<N, T, CPB, double, M, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * cell_smem<M, T>()));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel_td pw)");
-  e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, double, M, true, true, true, true>(),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(face_smem<M, T>() + (size_t)CPB * 4 * M * M * sizeof(T)));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel pw)");
-  done = true;
-  return 0;
+  static DeviceOnce once;
+  return once.run([&]() -> int {
+    constexpr int CPB = dgk::Launch<M>::CPB;
+    cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel_td<N, T, CPB, double, M, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * cell_smem<M, T>()));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_cell_kernel_td pw)");
+    e = cudaFuncSetAttribute(dgk::face_kernel_for<N, T, CPB, double, M, true, true, true, true>(),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(face_smem<M, T>() + (size_t)CPB * 4 * M * M * sizeof(T)));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dg_face_kernel pw)");
+    return 0;
+  });
 }
 
 template <int N, typename T, int M>

@@ -256,7 +256,7 @@ int dg_assemble(dg_handle* h, void* stream, dg_matrix** out) {
       DG_TRY(cudaMemcpyAsync(d_tc, tc.data(), tc.size() * sizeof(int), cudaMemcpyHostToDevice, s), "copy targets");
       DG_TRY(cudaMemcpyAsync(d_ts, ts.data(), ts.size() * sizeof(int), cudaMemcpyHostToDevice, s), "copy slots");
       const int nc = (int)cs.size();
-      const unsigned g1 = (unsigned)std::min(152 * 8, (nc + 255) / 256);
+      const unsigned g1 = (unsigned)std::min(dgi::sm_count() * 8, (nc + 255) / 256);
       for (int j = 0; j < nb; ++j) {
         probe_set<<<g1, 256, 0, s>>>(x, d_cells, nc, nb, j, 1.0);
         rc = dgi::launch_apply_f64(h, x, y, 0, 3, s);

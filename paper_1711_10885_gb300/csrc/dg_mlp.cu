@@ -98,6 +98,7 @@ struct FwdArgs {
   const __nv_bfloat16* W1p;
   const __nv_bfloat16* W2p;
   const __nv_bfloat16* W3p;
+  uint32_t w_wait_tries;  // tcgen05 kernel: polls of the weight-arrival wait before it counts as timed out
 };
 
 // Output layer on 8 NT columns starting at c0 for this warp's 16 rows, with the bias and either the
@@ -270,9 +271,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// wait for the mbarrier phase with the given parity; false after TC_WAIT_ITERS unsuccessful tries
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < TC_WAIT_ITERS; ++it) {
+// wait for the mbarrier phase with the given parity; false after `tries` unsuccessful tries
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t tries = TC_WAIT_ITERS) {
+  for (uint32_t it = 0; it < tries; ++it) {
     if (mbar_try_wait(mbar, parity)) return true;
     __nanosleep(128);
   }
@@ -337,23 +338,19 @@ __device__ __forceinline__ void tc_bulk_load(uint32_t dst, const void* src, uint
   }
 }
 
-// one layer: D (tensor memory) = A (128 x K) W^T (W: N x K), issued by thread 0 once the weights have arrived
-// (mbarrier wbar, phase parity wpar) and committed to the mbarrier mbar
-__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_s, uint32_t w_s, int K, int N, uint32_t wbar,
-                                         uint32_t wpar, uint32_t mbar) {
-  if (threadIdx.x == 0) {
-    mbar_wait(wbar, wpar);  // on a timeout the MMAs read stale weights; the caller's wait reports it
-    const uint32_t idesc = tc_idesc(TC_ROWS, N), sbo = (uint32_t)(K >> 3) * 128;
-    for (int kk = 0; kk < (K >> 4); ++kk)
-      tc_mma(tmem, tc_sdesc(a_s + kk * 256, 128, sbo), tc_sdesc(w_s + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
-    tc_commit(mbar);
-  }
+// one layer: D (tensor memory) = A (128 x K) W^T (W: N x K), issued by one thread and committed to the mbarrier
+// mbar
+__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_s, uint32_t w_s, int K, int N, uint32_t mbar) {
+  const uint32_t idesc = tc_idesc(TC_ROWS, N), sbo = (uint32_t)(K >> 3) * 128;
+  for (int kk = 0; kk < (K >> 4); ++kk)
+    tc_mma(tmem, tc_sdesc(a_s + kk * 256, 128, sbo), tc_sdesc(w_s + kk * 256, 128, sbo), idesc, kk > 0 ? 1u : 0u);
+  tc_commit(mbar);
 }
 
 // bias + ReLU of this thread's accumulator row (columns of its half), as BF16, into the next layer's A operand
 // (K = HID); bias in shared memory
 __device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, int row, int c_lo, const float* bias,
-                                                   unsigned char* As, bool ok) {
+                                                   unsigned char* As) {
   for (int cb = c_lo; cb < c_lo + HID / 2; cb += 32) {
     float v[32];
     tmem_ld32(trow + cb, v);
@@ -363,8 +360,8 @@ __device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, int row, int c
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int j = 8 * q + 2 * i;
-        const float x0 = ok ? fmaxf(v[j] + bias[cb + j], 0.f) : __int_as_float(0x7fc00000);
-        const float x1 = ok ? fmaxf(v[j + 1] + bias[cb + j + 1], 0.f) : __int_as_float(0x7fc00000);
+        const float x0 = fmaxf(v[j] + bias[cb + j], 0.f);
+        const float x1 = fmaxf(v[j + 1] + bias[cb + j + 1], 0.f);
         p[i] = pack_bf16(x0, x1);
       }
       *reinterpret_cast<uint4*>(As + core_chunk(row, (cb >> 3) + q, HID)) = make_uint4(p[0], p[1], p[2], p[3]);
@@ -372,6 +369,11 @@ __device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, int row, int c
   }
 }
 
+// Bounded waits: thread 0 alone waits for the weights and keeps count of the asynchronous work in flight (the
+// weight copy into Ws, the committed MMAs); every thread waits for MMA completion before it reads the accumulator.
+// A timed-out wait clears the CTA's status flag (shared memory); from then on no MMA and no copy is issued, the
+// epilogues are skipped, thread 0 waits again (bounded, the full limit) for whatever is still in flight, the rows
+// of this tile are written as NaN straight to global memory, and the tensor memory is freed before returning.
 __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* As = tc_smem;
@@ -379,6 +381,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_ABYTES + TC_WBYTES);  // MMA completion
   uint64_t* wbar = mbar + 1;                                                      // weight arrival
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + TC_ABYTES + TC_WBYTES + 16);
+  volatile uint32_t* status = tslot + 1;  // 1 while every wait has succeeded
   float* bs = reinterpret_cast<float*>(tc_smem + TC_ABYTES + TC_WBYTES + 64);  // b1, b2, b3
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = 32 * (warp & 3) + (tid & 31), half = warp >> 2;  // TMEM lane = row; column half
@@ -391,12 +394,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // thread 0's record of asynchronous work in flight, with the phase parities of the two mbarriers
+  bool w_pending = false, m_pending = false;
+  uint32_t wpar = 0, mpar = 0;
   if (tid == 0) {
+    *status = 1u;
     mbar_init(mb, 1);
     mbar_init(wb, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_async_smem();
     tc_bulk_load(w_s, a.W1p, (uint32_t)(HID * a.kinp * 2), wb);  // W1 streams in while the X tile is staged
+    w_pending = true;
   }
   tc_stage_rows(As, a.X + row0 * a.kinp, here, a.kinp);
   for (int i = tid; i < 3 * HID; i += TC_THREADS) {
@@ -409,61 +417,101 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's 32 lanes = its 32 rows
-  bool ok = true;
-  uint32_t parity = 0;
 #pragma unroll 1
-  for (int layer = 0; layer < 2; ++layer) {
-    tc_layer(tmem, a_s, w_s, layer == 0 ? a.kinp : HID, HID, wb, parity, mb);
-    ok = mbar_wait(mb, parity) && ok;
+  for (int layer = 0; layer < 3; ++layer) {
+    // thread 0: weights arrived -> the layer's MMAs, committed to mb
+    if (tid == 0 && *status == 1u) {
+      if (mbar_wait(wb, wpar, a.w_wait_tries)) {
+        w_pending = false;
+        wpar ^= 1u;
+        tc_layer(tmem, a_s, w_s, layer == 0 ? a.kinp : HID, layer == 2 ? a.outp : HID, mb);
+        m_pending = true;
+      } else {
+        *status = 0u;
+      }
+    }
+    __syncthreads();
+    // every thread: the MMAs have completed (their accumulator is readable, A and W are free again)
+    bool saw = false;
+    if (*status == 1u) {
+      saw = mbar_wait(mb, mpar);
+      if (!saw) *status = 0u;
+    }
     tc_fence_after();
-    // the MMAs have read A and W: the next weights stream in during the epilogue, which overwrites A with the
-    // hidden layer
-    if (tid == 0)
-      tc_bulk_load(w_s, layer == 0 ? a.W2p : a.W3p, (uint32_t)((layer == 0 ? HID : a.outp) * HID * 2), wb);
-    parity ^= 1u;
-    tc_hidden_epilogue(trow, row, half * (HID / 2), bs + layer * HID, As, ok);
+    __syncthreads();
+    const bool ok = *status == 1u;
+    if (tid == 0 && saw) {
+      m_pending = false;
+      mpar ^= 1u;
+      // the next layer's weights stream in during the epilogue, which overwrites A with the hidden layer
+      if (ok && layer < 2) {
+        tc_bulk_load(w_s, layer == 0 ? a.W2p : a.W3p, (uint32_t)((layer == 0 ? HID : a.outp) * HID * 2), wb);
+        w_pending = true;
+      }
+    }
+    if (layer == 2 || !ok) break;
+    tc_hidden_epilogue(trow, row, half * (HID / 2), bs + layer * HID, As);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
   }
-  tc_layer(tmem, a_s, w_s, HID, a.outp, wb, parity, mb);
-  ok = mbar_wait(mb, parity) && ok;
-  tc_fence_after();
-  // output layer: the accumulator rows plus bias go through shared memory (A and W are free now; rows padded by
-  // four floats), then the tile's block of Y (rows x outp) or z (cells x nb, scaled) is written contiguously
-  float* Ys = reinterpret_cast<float*>(tc_smem);
-  const int ys = a.outp + 4;
-  const int ohalf = a.outp >> 1;  // a multiple of 8
-  for (int cb = half * ohalf; cb < (half + 1) * ohalf; cb += 8) {
-    float v[8];
-    tmem_ld8(trow + cb, v);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = ok ? v[i] + bs[2 * HID + cb + i] : __int_as_float(0x7fc00000);
-    *reinterpret_cast<float4*>(Ys + row * ys + cb) = make_float4(v[0], v[1], v[2], v[3]);
-    *reinterpret_cast<float4*>(Ys + row * ys + cb + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  // after a timeout: wait (bounded) for the copy or MMAs still in flight before shared or tensor memory is reused
+  if (tid == 0) {
+    if (m_pending && mbar_wait(mb, mpar)) m_pending = false;
+    if (w_pending && mbar_wait(wb, wpar)) w_pending = false;
   }
   __syncthreads();
-  if (a.Y) {
-    float* dst = a.Y + row0 * a.outp;
-    for (int e = tid; e < here * a.outp; e += TC_THREADS) {
-      const int r = e / a.outp, c = e - r * a.outp;
-      dst[e] = Ys[r * ys + c];
+  if (*status == 1u) {
+    // output layer: the accumulator rows plus bias go through shared memory (A and W are free now; rows padded
+    // by four floats), then the tile's block of Y (rows x outp) or z (cells x nb, scaled) is written
+    // contiguously
+    float* Ys = reinterpret_cast<float*>(tc_smem);
+    const int ys = a.outp + 4;
+    const int ohalf = a.outp >> 1;  // a multiple of 8
+    for (int cb = half * ohalf; cb < (half + 1) * ohalf; cb += 8) {
+      float v[8];
+      tmem_ld8(trow + cb, v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] += bs[2 * HID + cb + i];
+      *reinterpret_cast<float4*>(Ys + row * ys + cb) = make_float4(v[0], v[1], v[2], v[3]);
+      *reinterpret_cast<float4*>(Ys + row * ys + cb + 4) = make_float4(v[4], v[5], v[6], v[7]);
     }
-  }
-  if (a.z) {
-    for (int e = tid; e < here * a.nb; e += TC_THREADS) {
-      const int r = e / a.nb, c = e - r * a.nb;
-      const float zv = a.scale[row0 + r] * Ys[r * ys + c];
-      const size_t zi = (size_t)row0 * a.nb + e;
-      if (a.z_is_f64) {
-        double* zp = static_cast<double*>(a.z) + zi;
-        *zp = a.z_accumulate ? *zp + (double)zv : (double)zv;
-      } else {
-        float* zp = static_cast<float*>(a.z) + zi;
-        *zp = a.z_accumulate ? *zp + zv : zv;
+    __syncthreads();
+    if (a.Y) {
+      float* dst = a.Y + row0 * a.outp;
+      for (int e = tid; e < here * a.outp; e += TC_THREADS) {
+        const int r = e / a.outp, c = e - r * a.outp;
+        dst[e] = Ys[r * ys + c];
       }
     }
+    if (a.z) {
+      for (int e = tid; e < here * a.nb; e += TC_THREADS) {
+        const int r = e / a.nb, c = e - r * a.nb;
+        const float zv = a.scale[row0 + r] * Ys[r * ys + c];
+        const size_t zi = (size_t)row0 * a.nb + e;
+        if (a.z_is_f64) {
+          double* zp = static_cast<double*>(a.z) + zi;
+          *zp = a.z_accumulate ? *zp + (double)zv : (double)zv;
+        } else {
+          float* zp = static_cast<float*>(a.z) + zi;
+          *zp = a.z_accumulate ? *zp + zv : zv;
+        }
+      }
+    }
+  } else {
+    // a wait timed out: NaN rows (a solve that uses them reports a non-finite residual)
+    const float nan = __int_as_float(0x7fc00000);
+    if (a.Y)
+      for (int e = tid; e < here * a.outp; e += TC_THREADS) a.Y[row0 * a.outp + e] = nan;
+    if (a.z)
+      for (int e = tid; e < here * a.nb; e += TC_THREADS) {
+        const size_t zi = (size_t)row0 * a.nb + e;
+        if (a.z_is_f64)
+          static_cast<double*>(a.z)[zi] = (double)nan;
+        else
+          static_cast<float*>(a.z)[zi] = nan;
+      }
   }
   tc_fence_before();
   __syncthreads();
@@ -678,6 +726,17 @@ int ensure_ws(dg_mlp* m, size_t bytes) {
   return 0;
 }
 
+// Polls of the tcgen05 kernel's weight-arrival wait (about a second at the default).  DG_MLP_WEIGHT_WAIT_TRIES
+// lowers it to exercise the timeout path: with 0 the wait gives up at once, the kernel issues nothing more,
+// waits (with the full limit) for the copy still in flight and writes NaN rows.
+uint32_t weight_wait_tries() {
+  const char* v = std::getenv("DG_MLP_WEIGHT_WAIT_TRIES");
+  if (!v || !*v) return dgm::TC_WAIT_ITERS;
+  char* end = nullptr;
+  const unsigned long t = std::strtoul(v, &end, 10);
+  return (end && *end == 0 && t < dgm::TC_WAIT_ITERS) ? (uint32_t)t : dgm::TC_WAIT_ITERS;
+}
+
 dgm::FwdArgs fwd_args(const dg_mlp* m, const __nv_bfloat16* X, int64_t rows) {
   dgm::FwdArgs a{};
   a.X = X;
@@ -691,6 +750,7 @@ dgm::FwdArgs fwd_args(const dg_mlp* m, const __nv_bfloat16* X, int64_t rows) {
   a.kinp = m->d.kinp;
   a.outp = m->d.outp;
   a.nb = m->d.nb;
+  a.w_wait_tries = weight_wait_tries();
   return a;
 }
 
@@ -726,27 +786,24 @@ int launch_forward(const dg_mlp* m, const dgm::FwdArgs& a_in, cudaStream_t s) {
   dgm::FwdArgs a = a_in;
   if (use_tc_forward(m, a)) {
     if (int rc = packed_weights(m, s, a)) return rc;
-    static bool tc_attr = false;
-    if (!tc_attr) {
-      if (int rc = cfail(cudaFuncSetAttribute(dgm::mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)dgm::TC_SMEM),
-                         "MLP tcgen05 forward smem"))
-        return rc;
-      tc_attr = true;
-    }
+    static DeviceOnce tc_attr;
+    if (int rc = tc_attr.run([] {
+          return cfail(cudaFuncSetAttribute(dgm::mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)dgm::TC_SMEM),
+                       "MLP tcgen05 forward smem");
+        }))
+      return rc;
     const unsigned grid = (unsigned)((a.rows + dgm::TC_ROWS - 1) / dgm::TC_ROWS);
     if (grid == 0) return 0;
     dgm::mlp_forward_tc<<<grid, dgm::TC_THREADS, dgm::TC_SMEM, s>>>(a);
     return cfail(cudaGetLastError(), "MLP tcgen05 forward");
   }
-  static bool attr = false;
   const size_t smem = fwd_smem(m->d);
-  if (!attr || smem > 48 * 1024) {
+  if (smem > 48 * 1024) {  // set on every launch above the default: the size depends on the network
     if (int rc = cfail(cudaFuncSetAttribute(dgm::mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)std::max<size_t>(smem, 48 * 1024)),
+                                            (int)smem),
                        "MLP forward smem"))
       return rc;
-    attr = true;
   }
   const unsigned grid = (unsigned)((a.rows + dgm::ROWS - 1) / dgm::ROWS);
   if (grid == 0) return 0;
@@ -959,11 +1016,11 @@ int dg_mlp_features(const dg_mlp* m, const dg_handle* h, const void* r, int32_t 
   const int64_t n = cells ? rows : h->ncell;
   auto* Xb = static_cast<__nv_bfloat16*>(X);
   if (precision == DG_F64)
-    dgm::mlp_features<double><<<152 * 8, 256, 0, s>>>(static_cast<const double*>(r), static_cast<const double*>(h->p64.D),
+    dgm::mlp_features<double><<<sm_count() * 8, 256, 0, s>>>(static_cast<const double*>(r), static_cast<const double*>(h->p64.D),
                                                       h->n[0], h->n[1], h->n[2], cells, n, m->d.nb, m->d.kinp,
                                                       m->t_scale, Xb, scale);
   else
-    dgm::mlp_features<float><<<152 * 8, 256, 0, s>>>(static_cast<const float*>(r), static_cast<const double*>(h->p64.D),
+    dgm::mlp_features<float><<<sm_count() * 8, 256, 0, s>>>(static_cast<const float*>(r), static_cast<const double*>(h->p64.D),
                                                      h->n[0], h->n[1], h->n[2], cells, n, m->d.nb, m->d.kinp,
                                                      m->t_scale, Xb, scale);
   return cfail(cudaGetLastError(), "MLP features");

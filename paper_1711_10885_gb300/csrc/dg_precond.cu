@@ -644,13 +644,15 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
 #define FDMP(NV)                                                                                          \
   case NV: {                                                                                              \
     using P = FdmPlanes<NV>;                                                                              \
-    static bool attr = false;                                                                             \
-    if (!attr && P::SMEM > 48 * 1024) {                                                                   \
-      cudaError_t ea = cudaFuncSetAttribute(fdm_apply_planes<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                            P::SMEM);                                                     \
-      if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply_planes)");             \
+    static DeviceOnce attr;                                                                               \
+    if (P::SMEM > 48 * 1024) {                                                                            \
+      if (int rca = attr.run([] {                                                                         \
+            cudaError_t ea = cudaFuncSetAttribute(fdm_apply_planes<NV>,                                   \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);  \
+            return ea == cudaSuccess ? 0 : cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply_planes)");       \
+          }))                                                                                             \
+        return rca;                                                                                       \
     }                                                                                                     \
-    attr = true;                                                                                          \
     fdm_apply_planes<NV><<<(unsigned)((h->ncell + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>(          \
         tab, r, z, h->ncell);                                                                             \
     break;                                                                                                \
@@ -665,8 +667,11 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
   switch (N) {
 #define FDM(NV)                                                                                           \
   case NV:                                                                                                \
-    if (smem > 48 * 1024)                                                                                 \
-      cudaFuncSetAttribute(fdm_apply<NV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    if (smem > 48 * 1024) {                                                                               \
+      cudaError_t ea = cudaFuncSetAttribute(fdm_apply<NV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                            (int)smem);                                                   \
+      if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply)");                    \
+    }                                                                                                     \
     fdm_apply<NV, R><<<grid, cpb * NN, smem, s>>>(tab, r, z, h->ncell, cpb);                              \
     break;
     FDM(2) FDM(3) FDM(4) FDM(5) FDM(6) FDM(7) FDM(8) FDM(9) FDM(10) FDM(11)
@@ -824,7 +829,7 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      cast_blocks<<<152 * 8, 256, 0, s>>>(static_cast<const double*>(h->bj64), static_cast<float*>(h->bj32), h->ncell,
+      cast_blocks<<<sm_count() * 8, 256, 0, s>>>(static_cast<const double*>(h->bj64), static_cast<float*>(h->bj32), h->ncell,
                                          n, np);
       e = cudaGetLastError();
     }

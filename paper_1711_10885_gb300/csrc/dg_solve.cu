@@ -25,13 +25,21 @@ struct Ctx {
   dg_handle* h;
   cudaStream_t s;
   size_t n;
-  double* part;   // MAX_ROWS rows of RED_BLOCKS block sums
+  double* part;   // PART_ROWS rows of block sums (up to max(dots2_blocks, red_blocks) per row)
   double* hdev;   // 128 results of a dot pass
   double* ydev;   // 64 coefficients of the solution update
   double* cdev;   // 2 MAX_ROWS + 3 coefficients of the second basis pass
   double* hhost;  // pinned, 512: reduction results at 0, solution coefficients at 0, pass coefficients at 256
   int applies64 = 0, applies32 = 0;
   bool f64x = false;  // FP64 vectors with the double-float operator
+  // grids, sized from the device's SM count: the element-wise kernels, the basis passes (one wave at their
+  // resident-CTA bound) and the two-row dot pass
+  int red_blocks = 0, pass_blocks = 0, dots2_blocks = 0;
+  void set_grids(int sms) {
+    red_blocks = sms * 4;
+    pass_blocks = sms * dgb::PASS_MINB;
+    dots2_blocks = sms * dgb::DOTS2_MINB;
+  }
 };
 
 int cuda_check(cudaError_t e, const char* what) { return e == cudaSuccess ? 0 : cuda_fail(e, what); }
@@ -50,15 +58,13 @@ bool packable(size_t n, std::initializer_list<const void*> ptrs) {
 // the 48 KB a launch gets without opting in: opt in once per kernel
 template <typename T, int W>
 int basis_smem_attr() {
-  static bool done = false;
-  if (done) return 0;
-  if (int rc = cuda_check(cudaFuncSetAttribute(dgb::basis_dots<T, W, dgb::PASS_MINB, dgb::PASS_LOADS>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               dgb::MAX_ROWS * dgb::RED_THREADS * (int)sizeof(T)),
-                          "basis pass shared memory"))
-    return rc;
-  done = true;
-  return 0;
+  static DeviceOnce once;
+  return once.run([] {
+    return cuda_check(cudaFuncSetAttribute(dgb::basis_dots<T, W, dgb::PASS_MINB, dgb::PASS_LOADS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           dgb::MAX_ROWS * dgb::RED_THREADS * (int)sizeof(T)),
+                      "basis pass shared memory");
+  });
 }
 
 // dst[q] = V_q . w (q < nv) on the device
@@ -69,13 +75,13 @@ int basis_dots(Ctx& c, const T* V, int nv, const T* w, double* dst) {
     constexpr int W = 16 / sizeof(T);
     if (int rc = basis_smem_attr<T, W>()) return rc;
     dgb::basis_dots<T, W, dgb::PASS_MINB, dgb::PASS_LOADS>
-        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, w, c.n / W, c.part);
+        <<<c.pass_blocks, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, w, c.n / W, c.part);
   } else {
     if (int rc = basis_smem_attr<T, 1>()) return rc;
     dgb::basis_dots<T, 1, dgb::PASS_MINB, dgb::PASS_LOADS>
-        <<<dgb::PASS_BLOCKS, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, w, c.n, c.part);
+        <<<c.pass_blocks, dgb::RED_THREADS, smem, c.s>>>(V, c.n, nv, w, c.n, c.part);
   }
-  dgb::mdot_final<<<nv, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::PASS_BLOCKS, dst);
+  dgb::mdot_final<<<nv, dgb::RED_THREADS, 0, c.s>>>(c.part, c.pass_blocks, dst);
   return cuda_check(cudaGetLastError(), "basis dot kernels");
 }
 
@@ -84,9 +90,9 @@ template <typename T>
 int lincomb_add(Ctx& c, const T* Z, int nv, const double* y, T* x) {
   if (packable<T>(c.n, {Z, x})) {
     constexpr int W = 16 / sizeof(T);
-    dgb::lincomb_add<T, W, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n / W);
+    dgb::lincomb_add<T, W, dgb::PASS_MINB, dgb::PASS_LOADS><<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n / W);
   } else {
-    dgb::lincomb_add<T, 1, dgb::PASS_MINB, dgb::PASS_LOADS><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n);
+    dgb::lincomb_add<T, 1, dgb::PASS_MINB, dgb::PASS_LOADS><<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(Z, c.n, nv, y, x, c.n);
   }
   return cuda_check(cudaGetLastError(), "solution update");
 }
@@ -105,7 +111,7 @@ int dots(Ctx& c, const T* V, int nv, const T* w, double* out_host) {
 
 template <typename T>
 int scale(Ctx& c, T* v, double a) {
-  dgb::scale_copy<T, T><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(v, v, a, c.n);
+  dgb::scale_copy<T, T><<<c.red_blocks, dgb::RED_THREADS, 0, c.s>>>(v, v, a, c.n);
   return cuda_check(cudaGetLastError(), "scale");
 }
 
@@ -135,22 +141,23 @@ template <typename T>
 int basis_dots2(Ctx& c, const T* V, int nr, const T* w, double* dst) {
   const int rows = 2 * nr + 1;
   const size_t smem = (size_t)rows * dgb::DOTS2_THREADS * sizeof(T);
-  static bool attr_packed = false, attr_scalar = false;
+  static DeviceOnce attr_packed, attr_scalar;
   const bool pk = packable<T>(c.n, {V, w});
   constexpr int W = 16 / sizeof(T);
-  bool& attr = pk ? attr_packed : attr_scalar;
-  if (!attr) {
-    const int most = dgb::PART_ROWS * dgb::DOTS2_THREADS * (int)sizeof(T);
-    cudaError_t e = pk ? cudaFuncSetAttribute(dgb::basis_dots2<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)
-                       : cudaFuncSetAttribute(dgb::basis_dots2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    if (int rc = cuda_check(e, "basis pass shared memory")) return rc;
-    attr = true;
-  }
+  const int most = dgb::PART_ROWS * dgb::DOTS2_THREADS * (int)sizeof(T);
+  if (int rc = (pk ? attr_packed : attr_scalar).run([&] {
+        return cuda_check(pk ? cudaFuncSetAttribute(dgb::basis_dots2<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    most)
+                             : cudaFuncSetAttribute(dgb::basis_dots2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    most),
+                          "basis pass shared memory");
+      }))
+    return rc;
   if (pk)
-    dgb::basis_dots2<T, W><<<dgb::DOTS2_BLOCKS, dgb::DOTS2_THREADS, smem, c.s>>>(V, c.n, nr, w, c.n / W, c.part);
+    dgb::basis_dots2<T, W><<<c.dots2_blocks, dgb::DOTS2_THREADS, smem, c.s>>>(V, c.n, nr, w, c.n / W, c.part);
   else
-    dgb::basis_dots2<T, 1><<<dgb::DOTS2_BLOCKS, dgb::DOTS2_THREADS, smem, c.s>>>(V, c.n, nr, w, c.n, c.part);
-  dgb::mdot_final<<<rows, dgb::RED_THREADS, 0, c.s>>>(c.part, dgb::DOTS2_BLOCKS, dst);
+    dgb::basis_dots2<T, 1><<<c.dots2_blocks, dgb::DOTS2_THREADS, smem, c.s>>>(V, c.n, nr, w, c.n, c.part);
+  dgb::mdot_final<<<rows, dgb::RED_THREADS, 0, c.s>>>(c.part, c.dots2_blocks, dst);
   return cuda_check(cudaGetLastError(), "basis dot kernels");
 }
 
@@ -164,10 +171,10 @@ int basis_update2(Ctx& c, T* V, int nr, const double* coef_host, bool write_u, T
     return rc;
   if (packable<T>(c.n, {V, w})) {
     constexpr int W = 16 / sizeof(T);
-    dgb::basis_update2<T, W><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w,
+    dgb::basis_update2<T, W><<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w,
                                                                               c.n / W);
   } else {
-    dgb::basis_update2<T, 1><<<dgb::PASS_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w, c.n);
+    dgb::basis_update2<T, 1><<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w, c.n);
   }
   return cuda_check(cudaGetLastError(), "basis update");
 }
@@ -203,7 +210,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
         return rc;
     } else {
       if (int rc = apply_A<T>(c, x, v0)) return rc;
-      dgb::sub<T><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, c.s>>>(b, v0, v0, n);
+      dgb::sub<T><<<c.red_blocks, dgb::RED_THREADS, 0, c.s>>>(b, v0, v0, n);
     }
     double nrm2;
     if (int rc = dots<T>(c, v0, 1, v0, &nrm2)) return rc;
@@ -451,7 +458,9 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   // workspace: reductions, r/b copy, FP64 basis (V, Z), FP32 basis for the inner solve
   // partial sums (rows x blocks of the widest pass), then the dot results (128), y (128) and the pass
   // coefficients (2 MAX_ROWS + 3 = 131); 400 keeps what follows 16-byte aligned
-  const size_t part_size = (size_t)dgb::PART_ROWS * std::max(dgb::DOTS2_BLOCKS, dgb::RED_BLOCKS);
+  Ctx c;
+  c.set_grids(sm_count());
+  const size_t part_size = (size_t)dgb::PART_ROWS * std::max(c.dots2_blocks, c.red_blocks);
   const size_t small = part_size + 400;
   size_t v64 = 0, v32 = 0;
   if (o->mode == DG_SOLVE_FP64) {
@@ -462,7 +471,6 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   }
   const size_t bytes = (small + n + v64) * sizeof(double) + v32 * sizeof(float) + 256;
   if (int rc = ensure_ws(h, bytes)) return rc;
-  Ctx c;
   c.h = h;
   c.s = s;
   c.n = n;
@@ -536,7 +544,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
         return e2 ? e2 : mlp_apply_impl(mlp, h, r, z, DG_F32, 1, s);
       };
     std::function<int(const double*, double*)> P = [&](const double* v, double* z) -> int {
-      dgb::scale_copy<double, float><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, s>>>(v, rhs32, 1.0, n);
+      dgb::scale_copy<double, float><<<c.red_blocks, dgb::RED_THREADS, 0, s>>>(v, rhs32, 1.0, n);
       cudaMemsetAsync(e32, 0, n * sizeof(float), s);
       Result ri;
       double vn2;
@@ -546,7 +554,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       if (rc2) return rc2;
       maybe_fallback(ri.beta0, ri.res);
       inner_total += ri.iterations;
-      dgb::scale_copy<float, double><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, s>>>(e32, z, 1.0, n);
+      dgb::scale_copy<float, double><<<c.red_blocks, dgb::RED_THREADS, 0, s>>>(e32, z, 1.0, n);
       return cuda_check(cudaGetLastError(), "inner solve casts");
     };
     std::function<int(const double*, double*)> P0;
@@ -571,7 +579,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       c.f64x = false;
       double* r64 = V64;  // the basis is free between calls
       if ((rc = apply_A<double>(c, x_dev, r64))) break;
-      dgb::sub<double><<<dgb::RED_BLOCKS, dgb::RED_THREADS, 0, s>>>(bcopy, r64, r64, n);
+      dgb::sub<double><<<c.red_blocks, dgb::RED_THREADS, 0, s>>>(bcopy, r64, r64, n);
       double rn2;
       if ((rc = dots<double>(c, r64, 1, r64, &rn2))) break;
       res.res = std::sqrt(rn2);

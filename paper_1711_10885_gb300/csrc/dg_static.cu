@@ -1,6 +1,7 @@
 // dg_static.cu -- Jacobian application that allocates nothing: its work buffers (point-space
 // residual, face traces, face coefficients) live in one file-scope device array instead of in
 // memory obtained from cudaMalloc by dg_setup.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -16,8 +17,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 void* g_static_ptr[kMaxDevices] = {};
 
-// Device address of g_static_scratch on the current device, looked up once per device.
-int static_scratch(void** out) {
+// Device address of g_static_scratch on the current device, looked up once per device; *dev_out receives
+// the current device's index.
+int static_scratch(void** out, int* dev_out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return dgi::cuda_fail(e, "dg_apply_jacobian_static: cudaGetDevice");
@@ -33,6 +35,7 @@ int static_scratch(void** out) {
     g_static_ptr[dev] = p;
   }
   *out = g_static_ptr[dev];
+  *dev_out = dev;
   return DG_OK;
 }
 
@@ -92,6 +95,10 @@ int dg_apply_jacobian_static(const dg_mesh* mesh, int32_t k, const double* D_dev
       set_error("dg_apply_jacobian_static: each axis needs n >= 1, finite lo < hi and a finite velocity");
       return DG_ERR_INVALID_ARG;
     }
+    if (ncell > ((int64_t)1 << 30) / mesh->n[r]) {
+      set_error("dg_apply_jacobian_static: more than 2^30 cells");
+      return DG_ERR_INVALID_ARG;
+    }
     ncell *= mesh->n[r];
   }
   if (!std::isfinite(c) || !std::isfinite(sigma) || sigma < 0) {
@@ -109,7 +116,8 @@ int dg_apply_jacobian_static(const dg_mesh* mesh, int32_t k, const double* D_dev
     return DG_ERR_INVALID_ARG;
   }
   void* base = nullptr;
-  if (int rc = static_scratch(&base)) return rc;
+  int dev = 0;
+  if (int rc = static_scratch(&base, &dev)) return rc;
   unsigned char* p = static_cast<unsigned char*>(base);
 
   // A handle on the stack that points into the fixed array; nothing in it is owned or freed.
@@ -132,10 +140,11 @@ int dg_apply_jacobian_static(const dg_mesh* mesh, int32_t k, const double* D_dev
   h.work_tr = p + bytes_V;
   h.p64.fc = p + bytes_V + bytes_tr;
   h.p64.D = const_cast<double*>(D_dev);
-  cudaGetDevice(&h.device);
+  h.device = dev;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  static_face_coeffs<<<152 * 4, 128, 0, s>>>(D_dev, h.n[0], h.n[1], h.n[2], h.h[0], h.h[1], h.h[2], sigma,
+  const unsigned fgrid = (unsigned)std::min<int64_t>((ncell + 127) / 128, (int64_t)sm_count() * 4);
+  static_face_coeffs<<<fgrid, 128, 0, s>>>(D_dev, h.n[0], h.n[1], h.n[2], h.h[0], h.h[1], h.h[2], sigma,
                                             static_cast<double*>(h.p64.fc));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "dg_apply_jacobian_static: face coefficient kernel");

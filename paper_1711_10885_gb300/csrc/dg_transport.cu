@@ -101,8 +101,8 @@ __global__ void to_pairs(const double* __restrict__ a, dgk::dfl* __restrict__ x,
 }
 
 unsigned grid_for(int64_t n) {
-  const int64_t blocks = (n + 255) / 256;
-  return (unsigned)(blocks > 152 * 16 ? 152 * 16 : (blocks > 0 ? blocks : 1));
+  const int64_t blocks = (n + 255) / 256, cap = (int64_t)dgi::sm_count() * 16;
+  return (unsigned)(blocks > cap ? cap : (blocks > 0 ? blocks : 1));
 }
 
 }  // namespace

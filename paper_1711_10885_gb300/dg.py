@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libdg.so")
 
 DG_OK = 0
+DG_ERR_INVALID_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_NOT_CONVERGED, DG_ERR_TIMEOUT, DG_ERR_NAN = -1, -2, -3, -4, -5, -6
 DG_F64 = 0
 DG_F32 = 1
 DG_F64X = 2  # FP64 vectors, double-float arithmetic on the FP32 pipes

@@ -41,7 +41,9 @@ def _call_static(dg, w, D_dev, z, y, sigma):
                                            ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(y.data_ptr()), stream)
 
 
-@pytest.mark.parametrize("n,k", [((6, 5, 4), 4), ((3, 4, 5), 7)])
+# small meshes (the quarter-tile launch variant) and a k = 7 mesh of 2940 cells whose work space fills 30.5 of
+# the 32 MiB (the full-tile variant, and every offset of the array in use)
+@pytest.mark.parametrize("n,k", [((6, 5, 4), 4), ((3, 4, 5), 7), ((14, 14, 15), 7)])
 def test_static_matches_regular_apply_on_two_calls(dg, n, k):
     w = inputs.small_case(n=n, k=k, seed=40 + k, b=(0.6, -0.3, 0.9))
     sigma = dg.dg_penalty_sigma(k, 0)
@@ -56,6 +58,11 @@ def test_static_matches_regular_apply_on_two_calls(dg, n, k):
         torch.cuda.synchronize()
         err = (torch.max(torch.abs(y - y_ref)) / torch.max(torch.abs(y_ref))).item()
         assert err <= TOL64, (call, err)
+    # a third call with the same vectors leaves the device's free memory unchanged: nothing is allocated
+    free_before = torch.cuda.mem_get_info()[0]
+    assert _call_static(dg, w, D_dev, z, y, sigma) == 0, dg.lib.dg_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
     op.close()
 
 
