@@ -423,6 +423,143 @@ def solve_benchmark(rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10, w
     return out
 
 
+def _timed_solve(op, n, clock_dev=0, **kw):
+    """One dg_solve from x = 0 with wall time and the SM clock sampled during it; returns (stats, x)."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    sampler = ClockSampler(clock_dev)
+    sampler.start()
+    t0 = time.perf_counter()
+    st = op.solve(x, raise_on_error=False, **kw)
+    torch.cuda.synchronize()
+    st["wall_s"] = time.perf_counter() - t0
+    st["clocks"] = sampler.stop()
+    st["converged"] = st["status"] == dg.DG_OK
+    return st, x
+
+
+def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
+    """The solve half of the headline metric, in the default line (one GPU):
+
+    q5_48: 48^3 Q5 (23.9 M DOF), log-normal D, 8 sine modes, to 1e-10 relative residual: the mixed-precision
+      solve (FP64 outer FGMRES(10) with the true residual, defect update and orthogonalisation in FP64; FP32
+      inner FGMRES(30) on the FP32 operator with the block inverse by fast diagonalisation) with the FP64 outer
+      operator (the conforming variant) and with the double-float outer operator, against plain FP64
+      FGMRES(30) with the same (exact) block-Jacobi preconditioner in FP64, capped at fp64_cap_s seconds.
+    q4_64: 64^3 Q4 (32.8 M DOF), sigma 1.5, to 1e-8: mixed + block-Jacobi, mixed + block-Jacobi + the learned
+      first direction, the network alone in every inner application (capped), and plain FP64 block-Jacobi
+      (capped at fp64_cap_s_q4 seconds).  The network is trained on the solver's own pairs first (timed)."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, inputs, learned as learned_mod
+    out = {}
+    w = inputs.unit_cube_q5_48(with_u=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op = dg.operator_for(w)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    op.precond_setup(dg.DG_BJ_FAST_DIAG)
+    torch.cuda.synchronize()
+    q5 = {"workload": "unit_cube_q5_48", "dofs": w.ndof, "rtol": 1e-10, "operator_setup_s": t1 - t0,
+          "precond_setup_s": time.perf_counter() - t1,
+          "precond": "block-Jacobi, exact block inverse by fast diagonalisation (FP32 inner, FP64 outer / plain)"}
+    xs = {}
+    for name, outer in (("mixed_fp64_outer", 1), ("mixed_df_outer", 0)):
+        st, xs[name] = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
+                                    rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10,
+                                    outer_precision=outer)
+        q5[name] = st
+    # plain FP64: its iteration rate first, to turn the time cap into an iteration cap
+    st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
+                         rtol=1e-10, max_iterations=60)
+    cap = max(60, int(fp64_cap_s / (st["wall_s"] / max(1, st["iterations"]))))
+    st, xs["fp64"] = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
+                                  rtol=1e-10, max_iterations=cap)
+    st["iteration_cap"] = cap
+    q5["fp64"] = st
+    if st["converged"]:
+        for name in ("mixed_fp64_outer", "mixed_df_outer"):
+            q5[name]["field_diff_vs_fp64"] = float((xs[name] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
+        q5["speedup_mixed_fp64_outer"] = st["wall_s"] / q5["mixed_fp64_outer"]["wall_s"]
+        q5["speedup_mixed_df_outer"] = st["wall_s"] / q5["mixed_df_outer"]["wall_s"]
+    else:
+        q5["speedup_lower_bound_mixed_fp64_outer"] = st["wall_s"] / q5["mixed_fp64_outer"]["wall_s"]
+    op.close()
+    del xs
+    out["q5_48"] = q5
+    if not learned:
+        return out
+
+    train = [inputs.Workload(f"train{s_}", (32, 32, 32), 4, inputs.log_normal_D(32 ** 3, 1.5, s_))
+             for s_ in (10, 11, 12, 13)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mlp, info = learned_mod.train_preconditioner(train, 4, pairs=20000, epochs=60, batch=256, lr=1e-3, seed=0,
+                                                 minus_block_jacobi=False)
+    torch.cuda.synchronize()
+    info["train_s"] = time.perf_counter() - t0
+    ev = inputs.Workload("eval", (64, 64, 64), 4, inputs.log_normal_D(64 ** 3, 1.5, 20))
+    t0 = time.perf_counter()
+    op = dg.operator_for(ev)
+    op.precond_setup(dg.DG_BJ_FAST_DIAG)
+    torch.cuda.synchronize()
+    q4 = {"workload": "64^3 Q4, D log-normal sigma 1.5 (seed 20)", "dofs": ev.ndof, "rtol": 1e-8, "mlp": info,
+          "setup_s": time.perf_counter() - t0}
+    common = dict(rtol=1e-8, inner_rtol=1e-2, mlp=mlp)
+    q4["mixed_bj"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
+                                     preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, **common)
+    q4["mixed_bj_learned"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
+                                             preconditioner=dg.DG_PRECOND_BJ_MLP, mlp_placement=1, **common)
+    q4["mixed_learned_only"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
+                                               preconditioner=dg.DG_PRECOND_MLP, max_iterations=30, **common)
+    st, _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
+                         rtol=1e-8, max_iterations=30)
+    cap = max(30, int(fp64_cap_s_q4 / (st["wall_s"] / max(1, st["iterations"]))))
+    q4["fp64_bj"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
+                                    rtol=1e-8, max_iterations=cap)
+    q4["fp64_bj"]["iteration_cap"] = cap
+    mlp.close()
+    op.close()
+    out["q4_64"] = q4
+    return out
+
+
+def peak_probes():
+    """FP64 FMA, FP64 tensor-core (mma.sync m8n8k4) and FP32 FMA throughput of this GPU (dg_peak_probe), each
+    timed with events on the launching stream after a warm-up launch, best of three, with the SM clock."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.2)
+    for name, kind, iters in (("dfma", dg.DG_PROBE_DFMA, 25000), ("dmma", dg.DG_PROBE_DMMA, 6000),
+                              ("ffma", dg.DG_PROBE_FFMA, 1500000)):
+        dg.peak_probe(kind, iters // 10, sink)
+        best = None
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fl = dg.peak_probe(kind, iters, sink)
+            b.record(stream)
+            b.synchronize()
+            t = fl / (a.elapsed_time(b) * 1e-3) / 1e12
+            best = t if best is None else max(best, t)
+        out[name + "_tflops"] = best
+    out["clocks"] = sampler.stop()
+    out["unit_count_fp64_tflops"] = FP64_PEAK_TFLOPS
+    out["unit_count_fp32_tflops"] = FP32_PEAK_TFLOPS
+    out["dmma_over_dfma"] = out["dmma_tflops"] / out["dfma_tflops"]
+    return out
+
+
 def tensor_benchmark(reps=20):
     """The paper's Problem A coefficients (Sec. 5.1: tensor-valued diffusion, constant per cell) on the
     32^3 Q7 workload: per-cell SPD tensors R diag(l) R^T with log-normal eigenvalues (seed 60), b, c, f
@@ -1139,6 +1276,10 @@ def run_ours(args):
         },
     }
     if ws == 1:
+        line["peaks"] = peak_probes()
+        line["roofline"]["peak_measured_dfma"] = line["peaks"]["dfma_tflops"]
+        line["roofline"]["frac_of_measured_dfma"] = achieved / line["peaks"]["dfma_tflops"]
+    if ws == 1:
         line["small_case_latency"] = small_case_latency()
     if ws == 1:
         line["mlp_forward"] = mlp_forward_benchmark()
@@ -1153,6 +1294,8 @@ def run_ours(args):
     if ws == 1 and not args.no_problem_b:
         line["problem_b"] = problem_b_benchmark()
         line["problem_c"] = problem_c_benchmark()
+    if ws == 1 and not args.no_solve:
+        line["solve"] = solve_section(learned=not args.no_learned)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -1168,6 +1311,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the solve comparisons of the default line")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner part of them")
+    ap.add_argument("--solve-section", action="store_true", help="print only the default line's solve section")
+    ap.add_argument("--peaks", action="store_true", help="print only the arithmetic throughput probes")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--no-transport", action="store_true", help="skip the Taylor-Green transport section")
     ap.add_argument("--no-matrix", action="store_true", help="skip the matrix-based comparison section")
@@ -1232,6 +1379,16 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"transport": transport_benchmark(n=args.transport, steps=args.steps,
                                                            warmup=args.warmup)}), flush=True)
+    elif args.solve_section:
+        import torch
+        torch.cuda.set_device(0)
+        t0 = time.perf_counter()
+        out = solve_section(learned=not args.no_learned)
+        print(json.dumps({"solve": out, "section_s": time.perf_counter() - t0}), flush=True)
+    elif args.peaks:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"peaks": peak_probes()}), flush=True)
     elif args.solve_only:
         import torch
         torch.cuda.set_device(0)

@@ -320,6 +320,17 @@ int dg_batch_tuning(const dg_batch* b, int32_t k, int32_t* cells_per_cta, float*
 int dg_batch_destroy(dg_batch* b);
 
 /* ---------------------------------------------------------------------------------------------
+ * Arithmetic throughput probes: the denominators of the roofline of the cost model (Sec. 3.6), measured
+ * on the device the library runs on.  kind DG_PROBE_DFMA runs chains of FP64 FMAs, DG_PROBE_DMMA FP64
+ * tensor-core products (mma.sync m8n8k4, 512 flops per warp instruction), DG_PROBE_FFMA chains of FP32
+ * FMAs, on every warp slot of every SM, `iterations` rounds each.  *flops (host) receives the floating-point
+ * operations of the launch; the caller times it with events on `stream`.  sink_dev is a device double that
+ * is written only by an impossible outcome (it keeps the work from being removed).  Asynchronous.
+ * --------------------------------------------------------------------------------------------- */
+enum { DG_PROBE_DFMA = 0, DG_PROBE_DMMA = 1, DG_PROBE_FFMA = 2 };
+int dg_peak_probe(int32_t kind, int64_t iterations, double* sink_dev, double* flops, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Allocation-free Jacobian application.  The paper has no counterpart of this entry point.
  *
  * dg_setup obtains its tables, coefficients and work buffers from cudaMalloc.  Some callers cannot

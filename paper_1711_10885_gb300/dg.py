@@ -21,6 +21,7 @@ DG_ERR_INVALID_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_NOT_CONVERGED, DG_ERR_TIMEOU
 DG_F64 = 0
 DG_F32 = 1
 DG_F64X = 2  # FP64 vectors, double-float arithmetic on the FP32 pipes
+DG_PROBE_DFMA, DG_PROBE_DMMA, DG_PROBE_FFMA = 0, 1, 2
 DG_MAX_DEGREE = 10
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -145,6 +146,7 @@ def _load():
                                  ctypes.POINTER(dg_mlp_train_stats), vp]
     lib.dg_mlp_apply.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp]
     lib.dg_mlp_apply_add.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp]
+    lib.dg_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, _dp, vp]
     lib.dg_mlp_save.argtypes = [vp, ctypes.c_char_p]
     lib.dg_mlp_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
     return lib
@@ -160,7 +162,16 @@ EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadra
             "dg_mlp_param_offsets", "dg_mlp_set_target_scale", "dg_mlp_features", "dg_mlp_forward", "dg_mlp_loss_grad",
             "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load",
             "dg_apply_jacobian_static", "dg_setup_ex", "dg_project", "dg_rk_stage", "dg_ssprk2", "dg_assemble",
-            "dg_matrix_info", "dg_matrix_export", "dg_spmv", "dg_matrix_destroy"]
+            "dg_matrix_info", "dg_matrix_export", "dg_spmv", "dg_matrix_destroy", "dg_peak_probe"]
+
+
+def peak_probe(kind, iterations, sink, stream=None):
+    """Launch one arithmetic throughput probe (dg_peak_probe) on the stream; returns its floating-point
+    operation count.  sink: a float64 device tensor of at least one element."""
+    fl = ctypes.c_double()
+    check(lib.dg_peak_probe(int(kind), int(iterations), ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fl),
+                            _stream_ptr(stream)))
+    return fl.value
 
 
 def check(rc):
