@@ -3,6 +3,7 @@
 
 #include "dg_internal.h"
 #include "dg_kernels.cuh"
+#include "dg_kernels_plane.cuh"
 
 namespace dgi {
 
@@ -218,9 +219,65 @@ int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaSt
   return 0;
 }
 
-// FP64 applies: meshes with fewer full tiles than SMs take the small-tile variant
+// FP32 operator with one thread per plane of a cell (dg_kernels_plane.cuh): degrees 1..6, modes 0 and 1.  V is
+// kept in the plane layout between its two kernels.
+template <int N>
+int apply_plane(const dg_handle* h, const float* z, float* y, int mode, int stages, cudaStream_t s) {
+  using C = dgk::PlaneCfg<N>;
+  const size_t smem_cell = (size_t)C::CPB * C::CS * sizeof(float);
+  const size_t smem_face = (size_t)C::CPB * (C::CS + C::GS) * sizeof(float);
+  static DeviceOnce once;
+  if (int rc = once.run([&]() -> int {
+        cudaError_t e = cudaFuncSetAttribute(dgk::dg_cell_kernel_pl<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_cell);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(dgk::dg_face_kernel_pl<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_face);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(dgk::dg_face_kernel_pl<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_face);
+        return e == cudaSuccess ? 0 : cuda_fail(e, "cudaFuncSetAttribute(plane kernels)");
+      }))
+    return rc;
+  const auto tb = make_tab<N, float>(h->tab);
+  dgk::PlaneTab<N> pt;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) pt.A[i][j] = (float)h->tab.A[i][j];
+  const auto geo = make_geo<float>(h);
+  const unsigned grid = (unsigned)((h->ncell + C::CPB - 1) / C::CPB);
+  float* V = static_cast<float*>(h->work_V);
+  float* tr = static_cast<float*>(h->work_tr);
+  if (stages & 1)
+    dgk::dg_cell_kernel_pl<N><<<grid, C::THREADS, smem_cell, s>>>(tb, geo, z, static_cast<const float*>(h->p32.D),
+                                                                   V, tr);
+  if (stages & 2) {
+    dgk::FaceArgs<float, float> fa;
+    fa.V = V;
+    fa.traces = tr;
+    fa.fc = static_cast<const float*>(h->p32.fc);
+    fa.F = mode == 1 ? static_cast<const float*>(h->p32.F) : nullptr;
+    for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
+    fa.y = y;
+    fa.mode = mode;
+    fa.u = z;
+    fa.z0 = nullptr;
+    fa.cz = fa.cu = fa.cr = 0.0;
+    if (h->periodic[0] || h->periodic[1] || h->periodic[2])
+      dgk::dg_face_kernel_pl<N, true><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa);
+    else
+      dgk::dg_face_kernel_pl<N, false><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "FP32 operator kernel launch");
+}
+
+// FP64 applies: meshes with fewer full tiles than SMs take the small-tile variant; FP32 applies of degree <= 6
+// (modes 0, 1) take the plane kernels
 template <int N, typename T, typename TV>
 int apply_sized(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s, const StageArgs* st) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<TV, float>::value && N <= 7) {
+    if (mode == 0 || mode == 1) return apply_plane<N>(h, z, y, mode, stages, s);
+  }
   if constexpr (std::is_same<T, double>::value && std::is_same<TV, double>::value &&
                 small_cpb<N>() < dgk::Launch<N>::CPB) {
     if (h->ncell < (int64_t)sm_count() * dgk::Launch<N>::CPB)
