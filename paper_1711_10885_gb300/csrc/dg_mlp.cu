@@ -1,5 +1,6 @@
 // dg_mlp.cu -- per-element MLP preconditioner: feature gather, fused BF16 tensor-core forward pass,
-// FP32 backward pass, Adam, and the preconditioner application z = M(r) used inside FGMRES.
+// backward pass on the tensor cores (BF16 operands, FP32 accumulation), Adam, and the preconditioner
+// application z = M(r) used inside FGMRES.
 //
 // Network (per cell T): x = [r_T / s, log D_T, log D of the 6 face neighbours (own value where there is
 // no neighbour)], s = ||r_T||_2;  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3 (256 hidden
@@ -348,9 +349,10 @@ __device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_s, uint32_t w
 }
 
 // bias + ReLU of this thread's accumulator row (columns of its half), as BF16, into the next layer's A operand
-// (K = HID); bias in shared memory
+// (K = HID); bias in shared memory.  Hrow (training): the same BF16 values also go to this row of the hidden
+// layer in global memory (row-major [rows][HID]), or nullptr.
 __device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, int row, int c_lo, const float* bias,
-                                                   unsigned char* As) {
+                                                   unsigned char* As, __nv_bfloat16* Hrow) {
   for (int cb = c_lo; cb < c_lo + HID / 2; cb += 32) {
     float v[32];
     tmem_ld32(trow + cb, v);
@@ -364,7 +366,9 @@ __device__ __forceinline__ void tc_hidden_epilogue(uint32_t trow, int row, int c
         const float x1 = fmaxf(v[j + 1] + bias[cb + j + 1], 0.f);
         p[i] = pack_bf16(x0, x1);
       }
-      *reinterpret_cast<uint4*>(As + core_chunk(row, (cb >> 3) + q, HID)) = make_uint4(p[0], p[1], p[2], p[3]);
+      const uint4 v4 = make_uint4(p[0], p[1], p[2], p[3]);
+      *reinterpret_cast<uint4*>(As + core_chunk(row, (cb >> 3) + q, HID)) = v4;
+      if (Hrow) *reinterpret_cast<uint4*>(Hrow + cb + 8 * q) = v4;
     }
   }
 }
@@ -450,7 +454,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
       }
     }
     if (layer == 2 || !ok) break;
-    tc_hidden_epilogue(trow, row, half * (HID / 2), bs + layer * HID, As);
+    __nv_bfloat16* Hg = layer == 0 ? a.H1 : a.H2;
+    tc_hidden_epilogue(trow, row, half * (HID / 2), bs + layer * HID, As,
+                       (Hg && row < here) ? Hg + (row0 + row) * HID : nullptr);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -561,47 +567,74 @@ __global__ void mlp_features(const T* __restrict__ r, const double* __restrict__
   }
 }
 
-// ---- backward pass (FP32 SIMT) ----
+// ---- backward pass: BF16 tensor-core GEMMs with FP32 accumulation ----
 
-// C[M x N] (+)= sum_k A(m,k) B(k,n) with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]
+// C[M x N] = sum_k A(m,k) B(k,n) with A(m,k) = A[m*sam + k*sak] and B(k,n) = B[k*sbk + n] (n contiguous), both
+// rounded to BF16 on the way into shared memory; mma.sync m16n8k16 (BF16 in, FP32 accumulate).  CTA tile 64 x 64,
+// K step 32, four warps of 32 x 32 (2 x 4 MMA tiles).  Shared tiles: As[m][k], Bs[n][k] (B transposed, so that
+// both fragments are 32-bit loads of consecutive k), rows padded to 40 halves.
+constexpr int GB_M = 64, GB_N = 64, GB_K = 32, GB_KP = GB_K + 8, GB_THREADS = 128;
+
 template <typename TA, typename TB>
-__global__ void __launch_bounds__(256) sgemm(int M, int N, int K, const TA* __restrict__ A, int64_t sam,
-                                             int64_t sak, const TB* __restrict__ B, int64_t sbk, int64_t sbn,
-                                             float* __restrict__ C, int ldc, int accumulate) {
-  __shared__ float As[16][64 + 1];
-  __shared__ float Bs[16][64 + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-      const int kk = e / 64, mm = e % 64;
-      const int gm = m0 + mm, gk = k0 + kk, gn = n0 + mm;
-      As[kk][mm] = (gm < M && gk < K) ? (float)A[gm * sam + gk * sak] : 0.f;
-      Bs[kk][mm] = (gn < N && gk < K) ? (float)B[gk * sbk + gn * sbn] : 0.f;
+__global__ void __launch_bounds__(GB_THREADS) gemm_bf16_tc(int M, int N, int K, const TA* __restrict__ A, int64_t sam,
+                                                           int64_t sak, const TB* __restrict__ B, int64_t sbk,
+                                                           float* __restrict__ C, int ldc) {
+  __shared__ __align__(16) __nv_bfloat16 As[GB_M * GB_KP];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GB_N * GB_KP];
+  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  const bool a_m_fast = sam == 1;  // consecutive threads read consecutive m (else consecutive k)
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += GB_K) {
+    for (int e = threadIdx.x; e < GB_M * GB_K; e += GB_THREADS) {
+      const int mm = a_m_fast ? e % GB_M : e / GB_K, kk = a_m_fast ? e / GB_M : e % GB_K;
+      const int gm = m0 + mm, gk = k0 + kk;
+      const float v = (gm < M && gk < K) ? (float)A[gm * sam + gk * sak] : 0.f;
+      As[mm * GB_KP + kk] = __float2bfloat16_rn(v);
+    }
+    for (int e = threadIdx.x; e < GB_N * GB_K; e += GB_THREADS) {
+      const int nn = e % GB_N, kk = e / GB_N;
+      const int gn = n0 + nn, gk = k0 + kk;
+      const float v = (gn < N && gk < K) ? (float)B[gk * sbk + gn] : 0.f;
+      Bs[nn * GB_KP + kk] = __float2bfloat16_rn(v);
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float av[4], bv[4];
+    for (int ks = 0; ks < GB_K; ks += 16) {
+      uint32_t a[2][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < 2; ++i) {
+        const __nv_bfloat16* ap = As + (wm + 16 * i + g) * GB_KP + ks + 2 * tig;
+        a[i][0] = *reinterpret_cast<const uint32_t*>(ap);
+        a[i][1] = *reinterpret_cast<const uint32_t*>(ap + 8 * GB_KP);
+        a[i][2] = *reinterpret_cast<const uint32_t*>(ap + 8);
+        a[i][3] = *reinterpret_cast<const uint32_t*>(ap + 8 * GB_KP + 8);
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat16* bp = Bs + (wn + 8 * j + g) * GB_KP + ks + 2 * tig;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bp);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bp + 8);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], a[i], b0, b1);
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
-      if (gm < M && gn < N) C[(size_t)gm * ldc + gn] = accumulate ? C[(size_t)gm * ldc + gn] + acc[i][j] : acc[i][j];
-    }
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gm = m0 + wm + 16 * i + g + (q >= 2 ? 8 : 0), gn = n0 + wn + 8 * j + 2 * tig + (q & 1);
+        if (gm < M && gn < N) C[(size_t)gm * ldc + gn] = acc[i][j][q];
+      }
 }
 
 // dY = 2 (Y - T) / (rows * nb) on the nb real outputs (zero on the padding); loss partials per block
@@ -754,10 +787,10 @@ dgm::FwdArgs fwd_args(const dg_mlp* m, const __nv_bfloat16* X, int64_t rows) {
   return a;
 }
 
-// the tensor-memory (tcgen05) forward pass serves inference of networks with kinp, outp <= 256 (degrees 1..5);
-// training, which also stores the hidden layers, and larger networks use the mma.sync kernel
-bool use_tc_forward(const dg_mlp* m, const dgm::FwdArgs& a) {
-  return !a.H1 && !a.H2 && m->d.kinp <= dgm::TC_KMAX && m->d.outp <= dgm::HID && !std::getenv("DG_MLP_NO_TCGEN05");
+// the tensor-memory (tcgen05) forward pass serves networks with kinp, outp <= 256 (degrees 1..5), for inference
+// and for training (where it also stores the hidden layers); larger networks use the mma.sync kernel
+bool use_tc_forward(const dg_mlp* m, const dgm::FwdArgs&) {
+  return m->d.kinp <= dgm::TC_KMAX && m->d.outp <= dgm::HID && !std::getenv("DG_MLP_NO_TCGEN05");
 }
 
 // the weights of the tcgen05 kernel in its shared-memory layout, repacked on the stream after every change of
@@ -811,11 +844,16 @@ int launch_forward(const dg_mlp* m, const dgm::FwdArgs& a_in, cudaStream_t s) {
   return cfail(cudaGetLastError(), "MLP forward");
 }
 
+// C = A B on the tensor cores (BF16 operands, FP32 accumulation); B's n index is contiguous (sbn = 1)
 template <typename TA, typename TB>
 int gemm(int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn, float* C,
          int ldc, cudaStream_t s) {
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  dgm::sgemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, 0);
+  if (sbn != 1) {
+    set_error("MLP backward GEMM: B must have its n index contiguous");
+    return DG_ERR_INVALID_ARG;
+  }
+  dim3 grid((N + dgm::GB_N - 1) / dgm::GB_N, (M + dgm::GB_M - 1) / dgm::GB_M);
+  dgm::gemm_bf16_tc<TA, TB><<<grid, dgm::GB_THREADS, 0, s>>>(M, N, K, A, sam, sak, B, sbk, C, ldc);
   return cfail(cudaGetLastError(), "MLP backward GEMM");
 }
 

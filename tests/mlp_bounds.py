@@ -15,7 +15,10 @@ Both are propagated through the layers with absolute values (|W| times the devia
 layer, plus the accumulation term of this layer), which gives a bound for every output element rather
 than a norm of the whole tensor.  The backward pass (FP32 GEMMs on the GPU) is bounded the same way from
 the forward deviations: |a' b' - a b| <= (|a| + da)(|b| + db) - |a||b| term by term, plus gamma_K of the
-absolute sums, with a ReLU mask counted as undecided where the activation's range touches zero.
+absolute sums, with a ReLU mask counted as undecided where the activation's range touches zero.  The backward
+GEMMs run on the tensor cores with BF16 operands: their FP32 left operands (dY, dZ2, dZ1) are rounded to BF16
+(relative error <= 2^-8 each), which enters each product's bound as a deviation of that operand; the bias
+gradients are FP32 column sums of the unrounded operands.
 """
 
 from __future__ import annotations
@@ -25,6 +28,7 @@ import numpy as np
 from oracle import mlp as om
 
 U32 = 2.0 ** -24
+U_BF16 = 2.0 ** -8  # bound on the relative error of rounding to BF16 (half an ulp of an 8-bit significand)
 
 
 def gam(K: int) -> float:
@@ -90,26 +94,28 @@ def grad_bound(X, T, W1, b1, W2, b2, W3, b3, nb, exact_forward=False):
     ddY[:, :nb] = 2.0 / n * (fb["dy"][:, :nb] + 2 * U32 * (np.abs(y[:, :nb]) + np.abs(T) + fb["dy"][:, :nb])) \
         + 2 * U32 * np.abs(dY[:, :nb])
     A = np.abs(dY) + ddY
-    bW3 = _prod_dev(dY, ddY, h2, dh2, rows)
+    bf = lambda a, da: da + U_BF16 * (np.abs(a) + da)  # deviation of a GEMM operand after rounding to BF16
+    bW3 = _prod_dev(dY, bf(dY, ddY), h2, dh2, rows)
     bb3 = ddY.sum(axis=0) + gam(rows) * A.sum(axis=0)
     dH2 = dY @ W3q
-    ddH2 = ddY @ np.abs(W3q) + gam(W3q.shape[0]) * A @ np.abs(W3q)
+    ddH2 = bf(dY, ddY) @ np.abs(W3q) + gam(W3q.shape[0]) * A @ np.abs(W3q)
     dZ2 = dH2 * (h2 > 0)
     ddZ2 = _mask_dev(dH2, ddH2, h2, dh2)
-    bW2 = _prod_dev(dZ2, ddZ2, h1, dh1, rows)
+    bW2 = _prod_dev(dZ2, bf(dZ2, ddZ2), h1, dh1, rows)
     bb2 = ddZ2.sum(axis=0) + gam(rows) * (np.abs(dZ2) + ddZ2).sum(axis=0)
     dH1 = dZ2 @ W2q
-    ddH1 = ddZ2 @ np.abs(W2q) + gam(W2q.shape[0]) * (np.abs(dZ2) + ddZ2) @ np.abs(W2q)
+    ddH1 = bf(dZ2, ddZ2) @ np.abs(W2q) + gam(W2q.shape[0]) * (np.abs(dZ2) + ddZ2) @ np.abs(W2q)
     dZ1 = dH1 * (h1 > 0)
     ddZ1 = _mask_dev(dH1, ddH1, h1, dh1)
-    bW1 = _prod_dev(dZ1, ddZ1, X, np.zeros_like(X), rows)
+    bW1 = _prod_dev(dZ1, bf(dZ1, ddZ1), X, np.zeros_like(X), rows)
     bb1 = ddZ1.sum(axis=0) + gam(rows) * (np.abs(dZ1) + ddZ1).sum(axis=0)
     return loss, g, (bW1, bb1, bW2, bb2, bW3, bb3)
 
 
 def emulate_fp32(X, T, W1, b1, W2, b2, W3, b3, nb):
     """The GPU's arithmetic emulated on the CPU: BF16 weights, FP32 sums (numpy's own summation order), BF16
-    hidden activations, FP32 backward.  Used only to pin the bounds above on the CPU."""
+    hidden activations, backward GEMMs on BF16-rounded operands with FP32 sums.  Used only to pin the bounds above
+    on the CPU."""
     f = np.float32
     X = np.asarray(X, dtype=f)
     W1q, W2q, W3q = (om.bf16_round(W).astype(f) for W in (W1, W2, W3))
@@ -121,13 +127,14 @@ def emulate_fp32(X, T, W1, b1, W2, b2, W3, b3, nb):
     rows = X.shape[0]
     dY = np.zeros_like(y)
     dY[:, :nb] = (y[:, :nb] - np.asarray(T, dtype=f)) * f(2.0 / (rows * nb))
-    gW3 = dY.T @ h2
+    r16 = lambda a: om.bf16_round(a).astype(f)  # the tensor-core GEMMs take BF16 operands
+    gW3 = r16(dY).T @ h2
     gb3 = dY.sum(axis=0, dtype=f)
-    dZ2 = (dY @ W3q) * (h2 > 0)
-    gW2 = dZ2.T @ h1
+    dZ2 = (r16(dY) @ W3q) * (h2 > 0)
+    gW2 = r16(dZ2).T @ h1
     gb2 = dZ2.sum(axis=0, dtype=f)
-    dZ1 = (dZ2 @ W2q) * (h1 > 0)
-    gW1 = dZ1.T @ X
+    dZ1 = (r16(dZ2) @ W2q) * (h1 > 0)
+    gW1 = r16(dZ1).T @ X
     gb1 = dZ1.sum(axis=0, dtype=f)
     return y, (gW1, gb1, gW2, gb2, gW3, gb3)
 

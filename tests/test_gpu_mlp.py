@@ -139,11 +139,13 @@ def test_forward_random_network_elementwise(dg, k, rows, kernel):
     mlp.close()
 
 
-@pytest.mark.parametrize("k,rows", [(4, 200), (2, 131), (7, 96)])
-def test_gradient_exact_network_elementwise(dg, k, rows):
-    """Loss and every gradient element on the exact network: the forward pass is exact, so each gradient
-    element differs from the FP64 reference only by the FP32 backward arithmetic, bounded element by element
-    by gamma_K times its sum of absolute terms (tests/mlp_bounds.grad_bound)."""
+@pytest.mark.parametrize("k,rows,kernel", [(4, 200, "tcgen05"), (4, 200, "mma"), (2, 131, "tcgen05"),
+                                           (7, 96, "mma")])
+def test_gradient_exact_network_elementwise(dg, k, rows, kernel):
+    """Loss and every gradient element on the exact network, with the training forward pass on the tcgen05 or
+    the mma.sync kernel: the forward pass is exact, so each gradient element differs from the FP64 reference
+    only by the backward arithmetic on the tensor cores (BF16 operands, FP32 accumulation), bounded element by
+    element (tests/mlp_bounds.grad_bound)."""
     rng = np.random.default_rng(200 + k)
     mlp = dg.MLP(k, seed=0)
     W1, b1, W2, b2, W3, b3, make_rows = mb.exact_network(mlp.kin, mlp.kinp, mlp.nb, mlp.outp, rng)
@@ -151,8 +153,13 @@ def test_gradient_exact_network_elementwise(dg, k, rows):
     assert mb.forward_is_exact(X, W1, b1, W2, b2, W3, b3)
     T = np.round(rng.standard_normal((rows, mlp.nb)) * 64) / 64
     mlp.set_params(_pack(mlp, W1, b1, W2, b2, W3, b3))
-    loss = mlp.loss_grad(torch.tensor(X, dtype=torch.bfloat16, device="cuda"),
-                         torch.tensor(T, dtype=torch.float32, device="cuda"))
+    if kernel == "mma":
+        os.environ["DG_MLP_NO_TCGEN05"] = "1"
+    try:
+        loss = mlp.loss_grad(torch.tensor(X, dtype=torch.bfloat16, device="cuda"),
+                             torch.tensor(T, dtype=torch.float32, device="cuda"))
+    finally:
+        os.environ.pop("DG_MLP_NO_TCGEN05", None)
     loss_ref, g_ref, bounds = mb.grad_bound(X, T, W1, b1, W2, b2, W3, b3, mlp.nb, exact_forward=True)
     assert abs(loss - loss_ref) <= 1e-6 * loss_ref
     g = om.unpack(mlp.grad(), mlp.offsets, mlp.kinp, mlp.outp)
@@ -164,7 +171,8 @@ def test_gradient_exact_network_elementwise(dg, k, rows):
 
 def test_gradient_random_network_elementwise(dg):
     """Random weights and inputs: every gradient element within its propagated bound, and per block
-    max |g - g_ref| <= 2^-8 max |g_ref| (a flipped BF16 hidden value changes one factor of a term by 2^-7)."""
+    max |g - g_ref| <= 2^-6 max |g_ref| (the BF16 operands of the backward GEMMs and a flipped BF16 hidden
+    value each change one factor of a term by at most 2^-8 and 2^-7 of it)."""
     rng = np.random.default_rng(7)
     mlp = dg.MLP(4, seed=0)
     p = _random_params(mlp, rng)
@@ -179,7 +187,7 @@ def test_gradient_random_network_elementwise(dg):
     for name, a, b, bd in zip(["W1", "b1", "W2", "b2", "W3", "b3"], g, g_ref, bounds):
         err = np.abs(a - b)
         assert np.all(err <= bd), name
-        assert np.max(err) <= 2.0 ** -8 * np.max(np.abs(b)), (name, np.max(err) / np.max(np.abs(b)))
+        assert np.max(err) <= 2.0 ** -6 * np.max(np.abs(b)), (name, np.max(err) / np.max(np.abs(b)))
     mlp.close()
 
 
