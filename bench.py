@@ -959,7 +959,9 @@ def batch_benchmark(reps=20):
     out = {"problems": len(ws), "dofs": dofs, "graph_launch_ms": ms_batch, "standalone_sum_ms": ms_alone,
            "batch_mdofs": dofs / (ms_batch * 1e-3) / 1e6, "standalone_mdofs": dofs / (ms_alone * 1e-3) / 1e6,
            "speedup": ms_alone / ms_batch, "autotune_s": tune_s,
-           "cells_per_cta": {k: batch.tuning(k)["cells_per_cta"] for k in sorted({w.k for w in ws})}}
+           "tuning": {k: batch.tuning(k) for k in sorted({w.k for w in ws})},
+           "candidates": "0: F cells/CTA x 1 line/thread (standalone layout), 1: F/2 x 1, 2: F x 2, 3: 2F x 2; "
+                         "F = floor(256 / (k+1)^2)"}
     batch.close()
     for op in ops:
         op.close()

@@ -313,9 +313,16 @@ int dg_batch_create(dg_handle* const* handles, int32_t count, void* stream, dg_b
 int dg_batch_apply(dg_batch* b, const double* const* in_dev, double* const* out_dev, int32_t residual,
                    void* stream);
 
-/* Autotuner result for degree k: chosen cells per CTA, and the measured time (ms) of the two
- * candidates (full and half cells per CTA) on that degree's problems. */
-int dg_batch_tuning(const dg_batch* b, int32_t k, int32_t* cells_per_cta, float* ms_candidates);
+/* Autotuner result for degree k.  At dg_batch_create every degree present is timed alone (its counter reset,
+ * cell kernel and face kernel over all its problems, best of three after a warm-up) with each of the
+ * DG_BATCH_CANDIDATES thread layouts, with F = floor(256 / (k+1)^2) cells per CTA of the standalone kernels:
+ *   0: F cells per CTA, one line per thread (the standalone layout)   1: F/2 cells, one line per thread
+ *   2: F cells, two lines per thread                                    3: 2F cells, two lines per thread
+ * and the fastest is used.  Outputs (host, may be null): the chosen cells per CTA and lines per thread, and
+ * the time (ms) of every candidate (DG_BATCH_CANDIDATES floats); zeros for a degree not in the batch. */
+#define DG_BATCH_CANDIDATES 4
+int dg_batch_tuning(const dg_batch* b, int32_t k, int32_t* cells_per_cta, int32_t* lines_per_thread,
+                    float* ms_candidates);
 
 int dg_batch_destroy(dg_batch* b);
 

@@ -369,15 +369,16 @@ struct SelfArgs {
 };
 
 // Cell-kernel work on one tile of `here` consecutive cells starting at cell0 (virtual cells in SELF mode),
-// run by all threads of the CTA (blockDim.x >= CPB * M^2; threads beyond that only help with copies).
-template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false>
+// run by all threads of the CTA (blockDim.x >= CPB * ceil(M^2 / LPT); threads beyond that only help with copies).
+// LPT lines per thread: the ceil(M^2 / LPT) threads of a cell take the lines t0, t0 + ceil(M^2 / LPT), ...
+template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false, int LPT = 1>
 __device__ __forceinline__ void cell_tile(const TabNM<N, M, T>& tb, const Geo<T>& g, const TV* __restrict__ z,
                                           const T* __restrict__ Dcell, T* __restrict__ Vout, T* __restrict__ traces,
                                           int cell0, int here, int cell_base, unsigned char* smem_raw) {
-  constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS;
+  constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS, TPC = (NN + LPT - 1) / LPT;
   T* sU = reinterpret_cast<T*>(smem_raw);
   T* sV = sU + CPB * CS;
-  const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
+  const int lc = threadIdx.x / TPC, t0 = threadIdx.x - lc * TPC;
   const bool active = lc < here;
   const int cell = cell0 + lc;                                 // output index (virtual in SELF mode)
   const int rcell = SELF ? cell_base + cell / N3 : cell;       // real cell (coefficients)
@@ -399,45 +400,60 @@ __device__ __forceinline__ void cell_tile(const TabNM<N, M, T>& tb, const Geo<T>
   // Sec. 3.3, eq. evalfe: u at the Gauss points, axis x then y ...
 #pragma unroll
   for (int dir = 0; dir < 2; ++dir) {
-    if (active && (M == N || t < ModalLines<N, M>::count(dir))) {
-      T x[N], y[M];
-      const int bs = ModalLines<N, M>::base(dir, t), st = Lay<M>::stride(dir);
-      load_line<N>(U, bs, st, x);
-      eo_fwd<N, M, T>(tb, x, y);
-      store_line<M>(U, bs, st, y);
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+      const int t = t0 + l * TPC;
+      if (active && t < NN && (M == N || t < ModalLines<N, M>::count(dir))) {
+        T x[N], y[M];
+        const int bs = ModalLines<N, M>::base(dir, t), st = Lay<M>::stride(dir);
+        load_line<N>(U, bs, st, x);
+        eo_fwd<N, M, T>(tb, x, y);
+        store_line<M>(U, bs, st, y);
+      }
     }
     __syncthreads();
   }
 
   const T DT = active ? Dcell[rcell] : T(0);
-  const int a = t % M, b = t / M;
-  const T wperp = tb.w[a] * tb.w[b];
   T* trc = traces + (size_t)cell * 12 * NN;
-  const T* bl = VB ? g.bsc + (size_t)rcell * 3 * M * NN + t : nullptr;
   // ... then z, kept in registers for the z derivative pass (Sec. 3.2, eqs. evalblf / gauss_points):
   // V = c|T| w u + B_z [w (alpha_z D d_z u + beta_z u)], traces on the two z faces
-  if (active) {
-    T x[N], u[M], v[M];
-    const int bs = Lay<M>::base(2, t), st = Lay<M>::stride(2);
-    load_line<N>(U, bs, st, x);
-    eo_fwd<N, M, T>(tb, x, u);
-    store_line<M>(U, bs, st, u);
-    deriv_line<N, M, T, true, VB>(tb, u, v, wperp * (DT * g.alpha[2]), wperp * g.beta[2], wperp * g.creact,
-                                  VB ? bl + 2 * M * NN : nullptr, trc + 8 * NN, NN, t);
-    store_line<M>(V, bs, st, v);
+#pragma unroll
+  for (int l = 0; l < LPT; ++l) {
+    const int t = t0 + l * TPC;
+    if (active && t < NN) {
+      const int a = t % M, b = t / M;
+      const T wperp = tb.w[a] * tb.w[b];
+      const T* bl = VB ? g.bsc + (size_t)rcell * 3 * M * NN + t : nullptr;
+      T x[N], u[M], v[M];
+      const int bs = Lay<M>::base(2, t), st = Lay<M>::stride(2);
+      load_line<N>(U, bs, st, x);
+      eo_fwd<N, M, T>(tb, x, u);
+      store_line<M>(U, bs, st, u);
+      deriv_line<N, M, T, true, VB>(tb, u, v, wperp * (DT * g.alpha[2]), wperp * g.beta[2], wperp * g.creact,
+                                    VB ? bl + 2 * M * NN : nullptr, trc + 8 * NN, NN, t);
+      store_line<M>(V, bs, st, v);
+    }
   }
   __syncthreads();
   // x and y derivative passes accumulate into V
 #pragma unroll
   for (int dir = 0; dir < 2; ++dir) {
-    if (active) {
-      T u[M], v[M];
-      const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
-      load_line<M>(U, bs, st, u);
-      load_line<M>(V, bs, st, v);
-      deriv_line<N, M, T, false, VB>(tb, u, v, wperp * (DT * g.alpha[dir]), wperp * g.beta[dir], T(0),
-                                     VB ? bl + dir * M * NN : nullptr, trc + 4 * dir * NN, NN, t);
-      store_line<M>(V, bs, st, v);
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+      const int t = t0 + l * TPC;
+      if (active && t < NN) {
+        const int a = t % M, b = t / M;
+        const T wperp = tb.w[a] * tb.w[b];
+        const T* bl = VB ? g.bsc + (size_t)rcell * 3 * M * NN + t : nullptr;
+        T u[M], v[M];
+        const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
+        load_line<M>(U, bs, st, u);
+        load_line<M>(V, bs, st, v);
+        deriv_line<N, M, T, false, VB>(tb, u, v, wperp * (DT * g.alpha[dir]), wperp * g.beta[dir], T(0),
+                                       VB ? bl + dir * M * NN : nullptr, trc + 4 * dir * NN, NN, t);
+        store_line<M>(V, bs, st, v);
+      }
     }
     __syncthreads();
   }
@@ -765,15 +781,17 @@ __device__ __forceinline__ void face_weights(const Geo<T>& g, const FaceArgs<T, 
   }
 }
 
-// Face-kernel work on one tile of `here` consecutive cells starting at cell0 (see cell_tile).
+// Face-kernel work on one tile of `here` consecutive cells starting at cell0 (see cell_tile; LPT lines per thread,
+// 1 for the tensor-diffusion path, whose tangential weights pass through shared memory between two barriers).
 template <int N, typename T, bool SELF, int CPB, typename TV = T, int M = N, bool VB = false, bool PER = false,
-          bool TD = false, bool PW = false>
+          bool TD = false, bool PW = false, int LPT = 1>
 __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>& g, const FaceArgs<T, TV>& fa,
                                           int cell0, int here, int cell_base, unsigned char* smem_raw) {
-  constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS;
+  static_assert(LPT == 1 || !TD, "several lines per thread: scalar diffusion only");
+  constexpr int NN = M * M, N3 = N * N * N, CS = Lay<M>::CS, TPC = (NN + LPT - 1) / LPT;
   T* sV = reinterpret_cast<T*>(smem_raw);
   T* sW = sV + CPB * CS;  // TD: tangential weights [CPB][side][2][M^2]
-  const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
+  const int lc = threadIdx.x / TPC, t0 = threadIdx.x - lc * TPC;
   const bool active = lc < here;
   const int vcell = cell0 + lc;                                // output / trace index
   const int cell = SELF ? cell_base + vcell / N3 : vcell;      // real cell
@@ -781,12 +799,18 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
 
   gload_cells<M>(sV, fa.V, cell0, here);
   __syncthreads();
-  const int a = t % M, b = t / M;
   if (fa.mode == 2 && active) {
     // (f, v)_T: scale f by the quadrature weight Delta_T w_i (Sec. 3.1)
-    const T wz = g.vol * tb.w[a] * tb.w[b];
 #pragma unroll
-    for (int l = 0; l < M; ++l) V[Lay<M>::idx(l, a, b)] *= wz * tb.w[l];
+    for (int l = 0; l < LPT; ++l) {
+      const int t = t0 + l * TPC;
+      if (t < NN) {
+        const int a = t % M, b = t / M;
+        const T wz = g.vol * tb.w[a] * tb.w[b];
+#pragma unroll
+        for (int q = 0; q < M; ++q) V[Lay<M>::idx(q, a, b)] *= wz * tb.w[q];
+      }
+    }
   }
   __syncthreads();
 
@@ -794,56 +818,62 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
   ic[0] = cell % g.n[0];
   ic[1] = (cell / g.n[0]) % g.n[1];
   ic[2] = cell / (g.n[0] * g.n[1]);
-  const T wab = tb.w[a] * tb.w[b];
   // lift the face weights onto the normal lines, x then y then z (Sec. 3.4, normal direction last):
   // v_l += l_l(s) Vf + l_l'(s) Wf; the z pass continues with the first transposed contraction
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
-    T Vf[2], Wf[2];
-    if (active) {
-      const T wf = g.area[dir] * wab;
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        T Wt1, Wt2;
-        face_weights<N, T, SELF, TV, M, VB, PER, TD, PW>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf[s], Wf[s], Wt1,
-                                                         Wt2);
-        if (TD) {
-          sW[((lc * 2 + s) * 2 + 0) * NN + t] = Wt1;
-          sW[((lc * 2 + s) * 2 + 1) * NN + t] = Wt2;
-        }
-      }
-    }
-    if (TD) {
-      // tangential derivatives of v at the face points, transposed: the weight Wt at (a2, b) reaches the
-      // value of v at (a, b) through Dc[a2][a] (and likewise along b)
-      __syncthreads();
-      if (active) {
+    for (int l = 0; l < LPT; ++l) {
+      const int t = t0 + l * TPC;
+      const bool line = active && t < NN;
+      const int a = line ? t % M : 0, b = line ? t / M : 0;  // t < NN keeps a, b < M
+      const T wab = tb.w[a] * tb.w[b];
+      T Vf[2], Wf[2];
+      if (line) {
+        const T wf = g.area[dir] * wab;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const T* W1 = sW + ((lc * 2 + s) * 2 + 0) * NN;
-          const T* W2 = sW + ((lc * 2 + s) * 2 + 1) * NN;
-          T e = Vf[s];
-#pragma unroll
-          for (int q = 0; q < M; ++q) e = fma(tb.Dc[q][a], W1[q + M * b], fma(tb.Dc[q][b], W2[a + M * q], e));
-          Vf[s] = e;
+          T Wt1, Wt2;
+          face_weights<N, T, SELF, TV, M, VB, PER, TD, PW>(g, fa, cell, vcell, ic, dir, s, t, wf, Vf[s], Wf[s], Wt1,
+                                                           Wt2);
+          if (TD) {
+            sW[((lc * 2 + s) * 2 + 0) * NN + t] = Wt1;
+            sW[((lc * 2 + s) * 2 + 1) * NN + t] = Wt2;
+          }
         }
       }
-    }
-    if (active) {
-      const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
-      T v[M];
-      load_line<M>(V, bs, st, v);
+      if (TD) {
+        // tangential derivatives of v at the face points, transposed: the weight Wt at (a2, b) reaches the
+        // value of v at (a, b) through Dc[a2][a] (and likewise along b)  (LPT == 1 here)
+        __syncthreads();
+        if (line) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
+          for (int s = 0; s < 2; ++s) {
+            const T* W1 = sW + ((lc * 2 + s) * 2 + 0) * NN;
+            const T* W2 = sW + ((lc * 2 + s) * 2 + 1) * NN;
+            T e = Vf[s];
 #pragma unroll
-        for (int l = 0; l < M; ++l) v[l] = fma(tb.L[s][l], Vf[s], fma(tb.P[s][l], Wf[s], v[l]));
+            for (int q = 0; q < M; ++q) e = fma(tb.Dc[q][a], W1[q + M * b], fma(tb.Dc[q][b], W2[a + M * q], e));
+            Vf[s] = e;
+          }
+        }
       }
-      if (dir == 2) {
-        T y[N];
-        eo_bwd<N, M, T>(tb, v, y);
-        store_line<N>(V, bs, st, y);
-      } else {
-        store_line<M>(V, bs, st, v);
+      if (line) {
+        const int bs = Lay<M>::base(dir, t), st = Lay<M>::stride(dir);
+        T v[M];
+        load_line<M>(V, bs, st, v);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+#pragma unroll
+          for (int q = 0; q < M; ++q) v[q] = fma(tb.L[s][q], Vf[s], fma(tb.P[s][q], Wf[s], v[q]));
+        }
+        if (dir == 2) {
+          T y[N];
+          eo_bwd<N, M, T>(tb, v, y);
+          store_line<N>(V, bs, st, y);
+        } else {
+          store_line<M>(V, bs, st, v);
+        }
       }
     }
     __syncthreads();
@@ -853,12 +883,16 @@ __device__ __forceinline__ void face_tile(const TabNM<N, M, T>& tb, const Geo<T>
 #pragma unroll
   for (int dd = 0; dd < 2; ++dd) {
     const int dir = 1 - dd;
-    if (active && (M == N || t < ModalLines<N, M>::count(dir))) {
-      T x[M], y[N];
-      const int bs = ModalLines<N, M>::base(dir, t), st = Lay<M>::stride(dir);
-      load_line<M>(V, bs, st, x);
-      eo_bwd<N, M, T>(tb, x, y);
-      store_line<N>(V, bs, st, y);
+#pragma unroll
+    for (int l = 0; l < LPT; ++l) {
+      const int t = t0 + l * TPC;
+      if (active && t < NN && (M == N || t < ModalLines<N, M>::count(dir))) {
+        T x[M], y[N];
+        const int bs = ModalLines<N, M>::base(dir, t), st = Lay<M>::stride(dir);
+        load_line<M>(V, bs, st, x);
+        eo_bwd<N, M, T>(tb, x, y);
+        store_line<N>(V, bs, st, y);
+      }
     }
     __syncthreads();
   }

@@ -22,6 +22,7 @@ DG_F64 = 0
 DG_F32 = 1
 DG_F64X = 2  # FP64 vectors, double-float arithmetic on the FP32 pipes
 DG_PROBE_DFMA, DG_PROBE_DMMA, DG_PROBE_FFMA = 0, 1, 2
+DG_BATCH_CANDIDATES = 4
 DG_MAX_DEGREE = 10
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -131,7 +132,8 @@ def _load():
     lib.dg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(dg_solve_opts), ctypes.POINTER(dg_solve_stats), vp]
     lib.dg_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.dg_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, vp]
-    lib.dg_batch_tuning.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
+    lib.dg_batch_tuning.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_float)]
     lib.dg_batch_destroy.argtypes = [vp]
     lib.dg_mlp_create.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(vp)]
     lib.dg_mlp_destroy.argtypes = [vp]
@@ -621,10 +623,12 @@ class Batch:
         return ys
 
     def tuning(self, k):
-        cpb = ctypes.c_int32()
-        ms = (ctypes.c_float * 2)()
-        check(lib.dg_batch_tuning(self.b, int(k), ctypes.byref(cpb), ms))
-        return {"cells_per_cta": cpb.value, "ms_full": ms[0], "ms_half": ms[1]}
+        """Autotuner result for degree k: chosen cells per CTA and lines per thread, and the time (ms) of every
+        candidate layout (see dg_batch_tuning)."""
+        cpb, lpt = ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_float * DG_BATCH_CANDIDATES)()
+        check(lib.dg_batch_tuning(self.b, int(k), ctypes.byref(cpb), ctypes.byref(lpt), ms))
+        return {"cells_per_cta": cpb.value, "lines_per_thread": lpt.value, "ms_candidates": list(ms)}
 
     def close(self):
         if getattr(self, "b", None):

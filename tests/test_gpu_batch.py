@@ -33,7 +33,13 @@ def test_batch_equals_standalone_bitwise(dg):
             assert torch.equal(y, ref)
     for k in sorted({w.k for w in ws}):
         t = batch.tuning(k)
-        assert t["cells_per_cta"] >= 1 and t["ms_full"] > 0 and t["ms_half"] > 0
+        assert t["cells_per_cta"] >= 1 and t["lines_per_thread"] in (1, 2)
+        assert len(t["ms_candidates"]) == dg.DG_BATCH_CANDIDATES and min(t["ms_candidates"]) > 0
+        # the chosen layout is the fastest candidate
+        F = 256 // (k + 1) ** 2
+        shapes = [(F, 1), (max(1, F // 2), 1), (F, 2), (2 * F, 2)]
+        best = min(range(len(shapes)), key=lambda v: t["ms_candidates"][v])
+        assert (t["cells_per_cta"], t["lines_per_thread"]) == shapes[best]
     batch.close()
     for op in ops:
         op.close()
