@@ -139,12 +139,14 @@ basis_dots2(const T* __restrict__ V, size_t ld, int nr, const T* __restrict__ w,
 }
 
 // pass 2 (coef on the device: a[q] at coef[q], d[q] at coef[MAX_ROWS + q] for q < nr - 1, then 1/alpha, e, 1/beta
-// at coef[2 MAX_ROWS + 0, 1, 2]):
+// at coef[2 MAX_ROWS + 0, 1, 2]; nothing is done when *stop is set):
 //   u = V_{nr-1} <- (u - sum_q a[q] V_q) / alpha         (the reorthogonalised final row; only when write_u)
 //   w            <- (w - sum_q d[q] V_q - e u_old) / beta  (the next provisional row)
 template <typename T, int W>
 __global__ void __launch_bounds__(RED_THREADS, PASS_MINB)
-basis_update2(T* V, size_t ld, int nr, const double* __restrict__ coef, int write_u, T* w, size_t npack) {
+basis_update2(T* V, size_t ld, int nr, const double* __restrict__ coef, int write_u, T* w, size_t npack,
+              const int* __restrict__ stop) {
+  if (stop && *stop) return;  // the device-side Arnoldi has ended this cycle: nothing to update
   __shared__ T as[MAX_ROWS], ds[MAX_ROWS];
   __shared__ T sc[3];
   const int t = threadIdx.x, nf = nr - 1;
@@ -250,6 +252,194 @@ __global__ void __launch_bounds__(RED_THREADS)
 sub(const T* __restrict__ a, const T* b, T* out, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = a[i] - b[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device-side bookkeeping of the FGMRES cycle (one thread): the Hessenberg matrix, its Givens rotations, the
+// rotated right-hand side g and the residual estimate |g[col + 1]| live in device memory, so a cycle runs
+// without a host synchronisation per Arnoldi step.  The steps are those of the host loop they replace (see
+// fgmres in dg_solve.cu): the reorthogonalisation of the provisional row u_j gives a and alpha and finalises
+// Hessenberg column j - 1; the coefficients of w on the final rows give column j provisionally and the
+// coefficients of pass 2.  A cycle ends (stop) on convergence, breakdown or a non-finite value; pass 2 and
+// the later steps' bookkeeping then do nothing.
+// ---------------------------------------------------------------------------------------------
+struct ArnState {
+  double res;   // current residual estimate |g[fin]|
+  double btil;  // provisional norm of the last projection
+  double tol;   // absolute stopping tolerance
+  double prov;  // provisional estimate of the residual after the last step's column (H[j+1][j] ~ btil)
+  int m;        // restart length (row length of H)
+  int fin;      // columns 0 .. fin-1 of H are final and rotated into g
+  int jend;     // columns of this cycle (Hessenberg columns computed)
+  int stop;     // the cycle has ended
+  int err;      // 1: a non-finite value was met
+  int pad;
+  double cs[MAX_ROWS], sn[MAX_ROWS], g[MAX_ROWS + 1], cprev[MAX_ROWS + 1], a[MAX_ROWS + 1];
+  double H[(MAX_ROWS + 1) * MAX_ROWS];
+};
+constexpr int ARN_HEAD_BYTES = 56;  // res .. pad: what the host reads back
+
+// The values a step works on, staged by the warp in shared memory before one thread does the scalar work (each
+// global value is read once, in parallel, instead of by a chain of dependent loads).
+struct ArnCache {
+  double d[2 * MAX_ROWS + 1];  // the pass's dot products
+  double cp[MAX_ROWS + 1];     // provisional column (cprev)
+  double cs[MAX_ROWS], sn[MAX_ROWS], g[MAX_ROWS + 1];
+  double h[MAX_ROWS + 1];      // the column being finalised
+};
+
+__device__ inline void arn_stage(ArnCache& k, const ArnState* st, const double* dots, int nd, int j) {
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) k.d[i] = dots[i];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) k.cp[i] = st->cprev[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    k.cs[i] = st->cs[i];
+    k.sn[i] = st->sn[i];
+  }
+  for (int i = threadIdx.x; i <= j + 1 && i <= st->m; i += blockDim.x) k.g[i] = st->g[i];
+  __syncthreads();
+}
+
+// column col of H from the provisional coefficients cp, btil and the next row's reorthogonalisation (ap, alpha),
+// rotated by the previous rotations and a new one annihilating H[col+1][col]; g, fin and the residual estimate
+// follow (thread 0; st in global memory, k the staged copies)
+__device__ inline void arn_finalize(ArnState* st, ArnCache& k, int col, const double* ap, double alpha) {
+  const int m = st->m;
+  double* h = k.h;
+  for (int i = 0; i <= col; ++i) h[i] = k.cp[i] + st->btil * ap[i];
+  h[col + 1] = st->btil * alpha;
+  for (int i = 0; i < col; ++i) {
+    const double p = h[i], q = h[i + 1];
+    h[i] = k.cs[i] * p + k.sn[i] * q;
+    h[i + 1] = -k.sn[i] * p + k.cs[i] * q;
+  }
+  const double p = h[col], q = h[col + 1];
+  const double rr = hypot(p, q);
+  const double c = rr > 0 ? p / rr : 1.0, sn = rr > 0 ? q / rr : 0.0;
+  k.cs[col] = st->cs[col] = c;
+  k.sn[col] = st->sn[col] = sn;
+  h[col] = rr;
+  h[col + 1] = 0.0;
+  for (int i = 0; i <= col + 1; ++i) st->H[i * m + col] = h[i];
+  const double gc = k.g[col];
+  k.g[col + 1] = st->g[col + 1] = -sn * gc;
+  k.g[col] = st->g[col] = c * gc;
+  st->fin = col + 1;
+  st->res = fabs(k.g[col + 1]);
+}
+
+__global__ void arn_init(ArnState* st, int m, double tol, double beta) {
+  st->res = beta;
+  st->btil = 0.0;
+  st->tol = tol;
+  st->prov = beta;
+  st->m = m;
+  st->fin = st->jend = st->stop = st->err = 0;
+  for (int i = 0; i <= m; ++i) st->g[i] = 0.0;
+  st->g[0] = beta;
+}
+
+// step j (one warp): dots = (V_q . u_j, q <= j; V_q . w, q <= j; w . w) from pass 1; writes pass 2's coefficients
+__global__ void arn_step(ArnState* st, const double* __restrict__ dots, int j, double* __restrict__ coef) {
+  __shared__ ArnCache k;
+  if (st->stop) return;  // uniform: every thread reads the same flag before any thread writes it
+  arn_stage(k, st, dots, 2 * j + 3, j);
+  if (threadIdx.x != 0) return;
+  const double* pu = k.d;
+  const double* qw = k.d + j + 1;
+  const double ww = k.d[2 * j + 2];
+  double* a = st->a;
+  double alpha = 1.0;  // u_0 is final
+  if (j > 0) {
+    double s2 = pu[j];
+    for (int i = 0; i < j; ++i) {
+      a[i] = pu[i];
+      s2 -= pu[i] * pu[i];
+    }
+    if (!isfinite(s2)) {
+      st->err = 1;
+      st->stop = 1;
+      return;
+    }
+    alpha = sqrt(fmax(s2, 0.0));
+    if (st->fin < j) arn_finalize(st, k, j - 1, pu, alpha);
+    if (st->res <= st->tol || alpha == 0.0) {  // converged, or u_j in the span of the final rows (breakdown)
+      st->jend = j;
+      st->stop = 1;
+      return;
+    }
+  }
+  // coefficients of w on the final rows 0 .. j; they become the provisional column (cprev)
+  double bt2 = ww, ca = 0.0;
+  for (int i = 0; i < j; ++i) ca += pu[i] * qw[i];
+  const double cj = (qw[j] - ca) / alpha;
+  for (int i = 0; i < j; ++i) {
+    k.cp[i] = st->cprev[i] = qw[i];
+    bt2 -= qw[i] * qw[i];
+  }
+  k.cp[j] = st->cprev[j] = cj;
+  bt2 -= cj * cj;
+  if (!isfinite(bt2)) {
+    st->err = 1;
+    st->stop = 1;
+    return;
+  }
+  st->jend = j + 1;
+  if (bt2 <= 0.0) {  // w in the span of the basis: column j is final with a zero subdiagonal entry
+    st->btil = 0.0;
+    arn_finalize(st, k, j, pu, 0.0);
+    st->stop = 1;
+    return;
+  }
+  const double btil = sqrt(bt2);
+  st->btil = btil;
+  // provisional estimate of the residual after column j: the column rotated by the previous rotations, with
+  // btil as its subdiagonal entry
+  {
+    double* col = k.h;
+    for (int i = 0; i <= j; ++i) col[i] = k.cp[i];
+    for (int i = 0; i < j; ++i) {
+      const double p = col[i], q = col[i + 1];
+      col[i] = k.cs[i] * p + k.sn[i] * q;
+      col[i + 1] = -k.sn[i] * p + k.cs[i] * q;
+    }
+    st->prov = fabs(k.g[j]) * btil / fmax(hypot(col[j], btil), 1e-300);
+  }
+  // pass 2: v_j = (u_j - V_{<j} a) / alpha, u_{j+1} = (w - V_{<j} d - e u_j) / btil
+  const double e = cj / alpha;
+  for (int i = 0; i < j; ++i) {
+    coef[i] = pu[i];
+    coef[MAX_ROWS + i] = qw[i] - e * pu[i];
+  }
+  coef[2 * MAX_ROWS + 0] = 1.0 / alpha;
+  coef[2 * MAX_ROWS + 1] = e;
+  coef[2 * MAX_ROWS + 2] = 1.0 / btil;
+}
+
+// after the last step j of a cycle (one warp): dots = (V_q . u_{j+1}, q <= j + 1) finalise column j
+__global__ void arn_final(ArnState* st, const double* __restrict__ dots, int j) {
+  __shared__ ArnCache k;
+  if (st->stop || st->fin >= st->jend) return;
+  arn_stage(k, st, dots, j + 2, j);
+  if (threadIdx.x != 0) return;
+  double s2 = k.d[j + 1];
+  for (int i = 0; i <= j; ++i) s2 -= k.d[i] * k.d[i];
+  if (!isfinite(s2)) {
+    st->err = 1;
+    st->stop = 1;
+    return;
+  }
+  arn_finalize(st, k, j, k.d, sqrt(fmax(s2, 0.0)));
+}
+
+// y = H^{-1} g over the cycle's jend columns (upper triangular after the rotations), zero beyond (one thread)
+__global__ void arn_solve(const ArnState* st, double* __restrict__ y) {
+  const int m = st->m, n = st->jend;
+  for (int i = m - 1; i >= n; --i) y[i] = 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    double acc = st->g[i];
+    for (int q = i + 1; q < n; ++q) acc -= st->H[i * m + q] * y[q];
+    y[i] = st->H[i * m + i] != 0.0 ? acc / st->H[i * m + i] : 0.0;
+  }
 }
 
 }  // namespace dgb

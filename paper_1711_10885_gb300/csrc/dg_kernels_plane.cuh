@@ -1,5 +1,6 @@
 // dg_kernels_plane.cuh -- FP32 operator kernels with one thread per PLANE of a cell (the FP32 operator of the
-// inner solve, Problem A: per-cell scalar D, constant b, axis-parallel cells, M = N Gauss points).
+// inner solve, Problem A: per-cell scalar D, constant b, axis-parallel cells, M = N Gauss points).  The launcher
+// (dg_launch.cuh) uses them where they beat the line kernels on GB300, which is degree 5 (N = 6).
 //
 // The line kernels of dg_kernels.cuh give each thread one line of the cell tensor, so every 1D pass (eq.
 // sum_fact_kernel) loads and stores the whole tensor through shared memory.  On the FP64 pipe that is hidden;

@@ -219,8 +219,10 @@ int apply_n(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaSt
   return 0;
 }
 
-// FP32 operator with one thread per plane of a cell (dg_kernels_plane.cuh): degrees 1..6, modes 0 and 1.  V is
-// kept in the plane layout between its two kernels.
+// FP32 operator with one thread per plane of a cell (dg_kernels_plane.cuh), modes 0 and 1.  V is kept in the plane
+// layout between its two kernels.  Measured on GB300 at about 24 M DOF (FP32 Jacobian applies), against the line
+// kernels: k = 5 222 us vs 252 us; k = 1, 2, 3, 4, 6: 731, 464, 329, 400, 414 us vs 468, 385, 256, 273, 274 us
+// (odd N and N = 2 leave the plane transposes scalar and short).  So only k = 5 takes it.
 template <int N>
 int apply_plane(const dg_handle* h, const float* z, float* y, int mode, int stages, cudaStream_t s) {
   using C = dgk::PlaneCfg<N>;
@@ -271,11 +273,11 @@ int apply_plane(const dg_handle* h, const float* z, float* y, int mode, int stag
   return e == cudaSuccess ? 0 : cuda_fail(e, "FP32 operator kernel launch");
 }
 
-// FP64 applies: meshes with fewer full tiles than SMs take the small-tile variant; FP32 applies of degree <= 6
+// FP64 applies: meshes with fewer full tiles than SMs take the small-tile variant; FP32 applies of degree 5
 // (modes 0, 1) take the plane kernels
 template <int N, typename T, typename TV>
 int apply_sized(const dg_handle* h, const TV* z, TV* y, int mode, int stages, cudaStream_t s, const StageArgs* st) {
-  if constexpr (std::is_same<T, float>::value && std::is_same<TV, float>::value && N <= 7) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<TV, float>::value && N == 6) {
     if (mode == 0 || mode == 1) return apply_plane<N>(h, z, y, mode, stages, s);
   }
   if constexpr (std::is_same<T, double>::value && std::is_same<TV, double>::value &&

@@ -21,6 +21,10 @@ int mlp_apply_impl(dg_mlp* m, const dg_handle* h, const void* r, void* z, int32_
 
 namespace {
 
+// Arnoldi steps of the inner FP32 solve between two reads of its device-side state (a step costs about a
+// millisecond at the benchmark sizes, a read a few microseconds; steps past a convergence are wasted)
+constexpr int kInnerCheckEvery = 5;
+
 struct Ctx {
   dg_handle* h;
   cudaStream_t s;
@@ -29,7 +33,9 @@ struct Ctx {
   double* hdev;   // 128 results of a dot pass
   double* ydev;   // 64 coefficients of the solution update
   double* cdev;   // 2 MAX_ROWS + 3 coefficients of the second basis pass
-  double* hhost;  // pinned, 512: reduction results at 0, solution coefficients at 0, pass coefficients at 256
+  double* hhost;  // pinned, 512: reduction results at 0, the Arnoldi state's head at 448
+  dgb::ArnState* arn[2] = {nullptr, nullptr};  // device Arnoldi state of the outer (0) and inner (1) FGMRES
+  int depth = 0;                               // nesting level of the running fgmres call
   int applies64 = 0, applies32 = 0;
   bool f64x = false;  // FP64 vectors with the double-float operator
   // grids, sized from the device's SM count: the element-wise kernels, the basis passes (one wave at their
@@ -161,20 +167,16 @@ int basis_dots2(Ctx& c, const T* V, int nr, const T* w, double* dst) {
   return cuda_check(cudaGetLastError(), "basis dot kernels");
 }
 
-// Pass 2: coefficients from the host (staged in the pinned buffer, copied ahead of the kernel on the stream)
+// Pass 2 with the coefficients the device-side Arnoldi step wrote to c.cdev (skipped once the cycle stopped)
 template <typename T>
-int basis_update2(Ctx& c, T* V, int nr, const double* coef_host, bool write_u, T* w) {
-  double* stage = c.hhost + 256;
-  std::memcpy(stage, coef_host, (2 * dgb::MAX_ROWS + 3) * sizeof(double));
-  if (int rc = cuda_check(cudaMemcpyAsync(c.cdev, stage, (2 * dgb::MAX_ROWS + 3) * sizeof(double),
-                                          cudaMemcpyHostToDevice, c.s), "coefficient copy"))
-    return rc;
+int basis_update2(Ctx& c, T* V, int nr, bool write_u, T* w, const int* stop) {
   if (packable<T>(c.n, {V, w})) {
     constexpr int W = 16 / sizeof(T);
     dgb::basis_update2<T, W><<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w,
-                                                                              c.n / W);
+                                                                           c.n / W, stop);
   } else {
-    dgb::basis_update2<T, 1><<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w, c.n);
+    dgb::basis_update2<T, 1><<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w, c.n,
+                                                                           stop);
   }
   return cuda_check(cudaGetLastError(), "basis update");
 }
@@ -191,17 +193,46 @@ int basis_update2(Ctx& c, T* V, int nr, const double* coef_host, bool write_u, T
 // writes v_j and the next provisional row u_{j+1} = (w - V_{<=j} c) / beta (with v_j expressed through u_j).
 // Column j of H follows one step later, from w = V_{<=j} c + beta u_{j+1} and u_{j+1}'s own reorthogonalisation
 // (a', alpha'): H[0..j][j] = c + beta a', H[j+1][j] = beta alpha'.  FGMRES needs only A Z = V H with V
-// orthonormal, and z_j = M(u_j) is such a direction whatever the later correction of u_j.  Convergence is
-// decided on a provisional estimate (H[j+1][j] ~ beta); when it or the restart length stops the cycle, one more
-// dot pass finalises column j.
+// orthonormal, and z_j = M(u_j) is such a direction whatever the later correction of u_j.
+//
+// The scalar work of a step (finalising column j - 1, the Givens rotations, the residual estimate, the stop test,
+// the provisional estimate after column j and the coefficients of pass 2) runs on the device (dgb::arn_step),
+// so the host launches the steps of a cycle without waiting; it reads the state back every check_every steps
+// and at the end of the cycle (one synchronisation each).  When the provisional estimate has met the
+// tolerance, one more dot pass (the reorthogonalisation of u_{j+1}) finalises column j and decides; a cycle
+// that stops between two reads is confirmed by the next step's pass 1, whose operator application is then
+// unused.  The outer solve reads every step (its steps are whole inner solves); the inner one less often.
 template <typename T>
 int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, bool x0_zero, T* V, T* Z, int m,
            double tol_abs, int maxit, int max_cycles, bool true_residual_check, Result* out,
            const std::function<void(double, double)>& cycle_hook = {},
-           const std::function<int(const T*, T*)>& M0 = {}) {
+           const std::function<int(const T*, T*)>& M0 = {}, int check_every = 1) {
   const size_t n = c.n;
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), res(2 * dgb::MAX_ROWS + 2),
-      a(m + 1), cc(m + 1), cprev(m + 1), col(m + 1), coef(2 * dgb::MAX_ROWS + 3);
+  if (c.depth > 1) {
+    set_error("FGMRES: nested deeper than outer and inner solve");
+    return DG_ERR_INVALID_ARG;
+  }
+  dgb::ArnState* st = c.arn[c.depth];
+  ++c.depth;
+  struct DepthGuard {
+    Ctx& c;
+    ~DepthGuard() { --c.depth; }
+  } guard{c};
+  const int* stop = &st->stop;
+  double* head = c.hhost + 448;  // pinned copy of the state's head (ARN_HEAD_BYTES)
+  dgb::ArnState hd;
+  auto read_head = [&]() -> int {
+    if (int rc = cuda_check(cudaMemcpyAsync(head, st, dgb::ARN_HEAD_BYTES, cudaMemcpyDeviceToHost, c.s),
+                            "Arnoldi state copy"))
+      return rc;
+    if (int rc = cuda_check(cudaStreamSynchronize(c.s), "Arnoldi sync")) return rc;
+    std::memcpy(&hd, head, dgb::ARN_HEAD_BYTES);
+    if (hd.err) {
+      set_error("FGMRES: non-finite Arnoldi vector");
+      return DG_ERR_NAN;
+    }
+    return 0;
+  };
   Result r;
   for (int cycle = 0; cycle < max_cycles; ++cycle) {
     T* v0 = V;
@@ -228,36 +259,11 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     if (r.iterations >= maxit) break;
     if (cycle > 0 && !true_residual_check) break;
     if (int rc = scale<T>(c, v0, 1.0 / beta)) return rc;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jend = 0, fin = 0;  // columns 0 .. fin-1 of H are final and rotated into g
-    bool est_conv = false;
-    double btil = 0.0;      // provisional norm of the last projection
-    // rotate column col (previous rotations, then a new one annihilating H[col+1][col]) and update g
-    auto rotate = [&](int col) {
-      for (int i = 0; i < col; ++i) {
-        const double p = H[i * m + col], q = H[(i + 1) * m + col];
-        H[i * m + col] = cs[i] * p + sn[i] * q;
-        H[(i + 1) * m + col] = -sn[i] * p + cs[i] * q;
-      }
-      const double p = H[col * m + col], q = H[(col + 1) * m + col];
-      const double rr = std::hypot(p, q);
-      cs[col] = rr > 0 ? p / rr : 1.0;
-      sn[col] = rr > 0 ? q / rr : 0.0;
-      H[col * m + col] = rr;
-      H[(col + 1) * m + col] = 0.0;
-      g[col + 1] = -sn[col] * g[col];
-      g[col] = cs[col] * g[col];
-      fin = col + 1;
-      r.res = std::fabs(g[col + 1]);
-    };
-    // column col from the provisional coefficients cprev, btil and u_{col+1}'s reorthogonalisation (ap, alpha)
-    auto finalize = [&](int col, const double* ap, double alpha) {
-      for (int i = 0; i <= col; ++i) H[i * m + col] = cprev[i] + btil * ap[i];
-      H[(col + 1) * m + col] = btil * alpha;
-      rotate(col);
-    };
-    for (int j = 0; j < m; ++j) {
+    dgb::arn_init<<<1, 1, 0, c.s>>>(st, m, tol_abs, beta);
+    const int steps = std::min(m, maxit - r.iterations);
+    int last = steps - 1;  // the step after which the cycle's last column is finalised
+    bool finalised = false;
+    for (int j = 0; j < steps; ++j) {
       T* uj = V + (size_t)j * n;
       T* zj = Z + (size_t)j * n;
       T* w = V + (size_t)(j + 1) * n;
@@ -270,109 +276,46 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
           return rc;
       }
       if (int rc = apply_A<T>(c, zj, w)) return rc;
-      // pass 1
-      if (int rc = basis_dots2<T>(c, V, j + 1, w, c.hdev)) return rc;
-      if (int rc = cuda_check(cudaMemcpyAsync(c.hhost, c.hdev, (2 * j + 3) * sizeof(double),
-                                              cudaMemcpyDeviceToHost, c.s), "dot copy"))
-        return rc;
-      if (int rc = cuda_check(cudaStreamSynchronize(c.s), "Arnoldi sync")) return rc;
-      std::memcpy(res.data(), c.hhost, (2 * j + 3) * sizeof(double));
-      const double* pu = res.data();          // V_q . u_j
-      const double* qw = res.data() + j + 1;  // V_q . w
-      const double ww = res[2 * j + 2];
-      double alpha = 1.0;                     // u_0 is final
-      if (j > 0) {
-        double s2 = pu[j];
-        for (int i = 0; i < j; ++i) {
-          a[i] = pu[i];
-          s2 -= a[i] * a[i];
-        }
-        if (!std::isfinite(s2)) {
-          set_error("FGMRES: non-finite Arnoldi vector");
-          return DG_ERR_NAN;
-        }
-        alpha = std::sqrt(std::max(s2, 0.0));
-        if (fin < j) finalize(j - 1, a.data(), alpha);
-        if (r.res <= tol_abs || alpha == 0.0) {  // converged, or u_j in the span of the final rows (breakdown)
-          est_conv = true;
-          jend = j;
-          break;
-        }
-      }
-      // coefficients of w on the final rows 0 .. j
-      double bt2 = ww, ca = 0.0;
-      for (int i = 0; i < j; ++i) {
-        cc[i] = qw[i];
-        ca += a[i] * qw[i];
-      }
-      cc[j] = (qw[j] - ca) / alpha;
-      for (int i = 0; i <= j; ++i) bt2 -= cc[i] * cc[i];
-      if (!std::isfinite(bt2)) {
-        set_error("FGMRES: non-finite Arnoldi vector");
-        return DG_ERR_NAN;
-      }
-      ++r.iterations;
-      jend = j + 1;
-      for (int i = 0; i <= j; ++i) cprev[i] = cc[i];
-      if (bt2 <= 0.0) {  // w in the span of the basis: column j is final with a zero subdiagonal entry
-        btil = 0.0;
-        finalize(j, a.data(), 0.0);
-        est_conv = true;
+      if (int rc = basis_dots2<T>(c, V, j + 1, w, c.hdev)) return rc;  // pass 1
+      dgb::arn_step<<<1, 32, 0, c.s>>>(st, c.hdev, j, c.cdev);
+      if (int rc = basis_update2<T>(c, V, j + 1, j > 0, w, stop)) return rc;  // pass 2
+      if (j == steps - 1 || (j + 1) % check_every != 0) continue;
+      if (int rc = read_head()) return rc;
+      if (hd.stop) {  // converged or broke down at an earlier column: nothing left to finalise
+        last = j;
+        finalised = true;
         break;
       }
-      btil = std::sqrt(bt2);
-      // pass 2: v_j = (u_j - V_{<j} a) / alpha, u_{j+1} = (w - V_{<j} d - e u_j) / btil
-      const double e = cc[j] / alpha;
-      for (int i = 0; i < j; ++i) {
-        coef[i] = a[i];
-        coef[dgb::MAX_ROWS + i] = cc[i] - e * a[i];
-      }
-      coef[2 * dgb::MAX_ROWS + 0] = 1.0 / alpha;
-      coef[2 * dgb::MAX_ROWS + 1] = e;
-      coef[2 * dgb::MAX_ROWS + 2] = 1.0 / btil;
-      if (int rc = basis_update2<T>(c, V, j + 1, coef.data(), j > 0, w)) return rc;
-      // provisional estimate of the residual after column j (H[j+1][j] ~ btil)
-      for (int i = 0; i <= j; ++i) col[i] = cc[i];
-      for (int i = 0; i < j; ++i) {
-        const double p = col[i], q = col[i + 1];
-        col[i] = cs[i] * p + sn[i] * q;
-        col[i + 1] = -sn[i] * p + cs[i] * q;
-      }
-      const double prov = std::fabs(g[j]) * btil / std::max(std::hypot(col[j], btil), 1e-300);
-      const bool last = j == m - 1 || r.iterations >= maxit;
-      if (prov <= tol_abs || last) {
-        // finalise column j: the reorthogonalisation of u_{j+1} against rows 0 .. j
-        if (int rc = dots<T>(c, V, j + 2, w, res.data())) return rc;
-        double s2 = res[j + 1];
-        for (int i = 0; i <= j; ++i) s2 -= res[i] * res[i];
-        if (!std::isfinite(s2)) {
-          set_error("FGMRES: non-finite Arnoldi vector");
-          return DG_ERR_NAN;
-        }
-        finalize(j, res.data(), std::sqrt(std::max(s2, 0.0)));
-        if (r.res <= tol_abs) {
-          est_conv = true;
+      if (hd.prov <= tol_abs) {
+        // finalise column j now: the reorthogonalisation of u_{j+1} against rows 0 .. j
+        if (int rc = basis_dots<T>(c, V, j + 2, w, c.hdev)) return rc;
+        dgb::arn_final<<<1, 32, 0, c.s>>>(st, c.hdev, j);
+        if (int rc = read_head()) return rc;
+        if (hd.res <= tol_abs) {
+          last = j;
+          finalised = true;
           break;
         }
-        if (last) break;
       }
     }
-    if (fin != jend) {
+    // finalise the last column: the reorthogonalisation of u_steps against rows 0 .. steps - 1
+    if (!finalised) {
+      if (int rc = basis_dots<T>(c, V, last + 2, V + (size_t)(last + 1) * n, c.hdev)) return rc;
+      dgb::arn_final<<<1, 32, 0, c.s>>>(st, c.hdev, last);
+    }
+    dgb::arn_solve<<<1, 1, 0, c.s>>>(st, c.ydev);
+    if (int rc = read_head()) return rc;
+    if (hd.fin != hd.jend) {
       set_error("FGMRES: internal error (Hessenberg column not finalised)");
       return DG_ERR_INVALID_ARG;
     }
-    // y = H^{-1} g (upper triangular), x += Z y
-    for (int i = jend - 1; i >= 0; --i) {
-      double acc = g[i];
-      for (int k = i + 1; k < jend; ++k) acc -= H[i * m + k] * y[k];
-      y[i] = H[i * m + i] != 0 ? acc / H[i * m + i] : 0.0;
-    }
-    std::memcpy(c.hhost, y.data(), jend * sizeof(double));
-    if (int rc = cuda_check(cudaMemcpyAsync(c.ydev, c.hhost, jend * sizeof(double), cudaMemcpyHostToDevice, c.s),
-                            "y copy"))
-      return rc;
-    if (int rc = lincomb_add<T>(c, Z, jend, c.ydev, x)) return rc;
-    if (int rc = cuda_check(cudaStreamSynchronize(c.s), "solution update")) return rc;
+    const int jend = hd.jend;
+    r.iterations += jend;
+    r.res = hd.res;
+    const bool est_conv = hd.stop || hd.res <= tol_abs;
+    // x += Z y
+    if (jend > 0)
+      if (int rc = lincomb_add<T>(c, Z, jend, c.ydev, x)) return rc;
     if (cycle_hook) cycle_hook(beta, r.res);
     if (est_conv && !true_residual_check) {
       r.converged = true;
@@ -461,7 +404,8 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   Ctx c;
   c.set_grids(sm_count());
   const size_t part_size = (size_t)dgb::PART_ROWS * std::max(c.dots2_blocks, c.red_blocks);
-  const size_t small = part_size + 400;
+  const size_t arn_words = (sizeof(dgb::ArnState) + 255) / 256 * 32;  // one state, rounded to 256 bytes
+  const size_t small = part_size + 400 + 2 * arn_words;
   size_t v64 = 0, v32 = 0;
   if (o->mode == DG_SOLVE_FP64) {
     v64 = (size_t)(2 * m + 1) * n;  // V and Z (Z = V's provisional rows without a preconditioner)
@@ -479,6 +423,8 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   c.hdev = base + part_size;  // up to 2 * 61 + 1 results of a pass
   c.ydev = c.hdev + 128;
   c.cdev = c.ydev + 128;
+  c.arn[0] = reinterpret_cast<dgb::ArnState*>(base + part_size + 400);
+  c.arn[1] = reinterpret_cast<dgb::ArnState*>(base + part_size + 400 + arn_words);
   double* bcopy = base + small;
   double* V64 = bcopy + n;
   float* f32 = reinterpret_cast<float*>(V64 + v64);
@@ -550,7 +496,8 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       double vn2;
       int rc2 = dots<float>(c, rhs32, 1, rhs32, &vn2);
       if (rc2) return rc2;
-      rc2 = fgmres<float>(c, M32, rhs32, e32, true, V32, Z32, m, o->inner_rtol * std::sqrt(vn2), m, 1, false, &ri);
+      rc2 = fgmres<float>(c, M32, rhs32, e32, true, V32, Z32, m, o->inner_rtol * std::sqrt(vn2), m, 1, false, &ri,
+                          {}, {}, kInnerCheckEvery);
       if (rc2) return rc2;
       maybe_fallback(ri.beta0, ri.res);
       inner_total += ri.iterations;
