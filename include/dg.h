@@ -276,6 +276,19 @@ int dg_mlp_set_target_scale(dg_mlp* m, float t_scale);
  * precision). */
 int dg_mlp_features(const dg_mlp* m, const dg_handle* h, const void* r_dev, int32_t precision,
                     const int32_t* cells_dev, int64_t rows, void* X_dev, float* scale_dev, void* stream);
+/* Training pairs of the learned preconditioner from a solver state of the handle's problem (the method's own
+ * data).  With r = F - A x (x_dev, FP64), for sample i < count with cell = cells_dev[i] and output row
+ * row = rows_dev[i] (int32 device arrays; rows may be any permutation, e.g. to shuffle the set):
+ *   X[row] = the feature row of r on the cell (as dg_mlp_features), BF16 [*][kin_padded];
+ *   E[row][j] = e_j / ||r_cell||_2, e = (xstar - x) on the cell, minus the block-Jacobi correction of r when
+ *   subtract_block_jacobi (needs dg_precond_setup), FP32 [*][(k+1)^3]; zero where r_cell = 0.
+ * Uses the network's device work space for r.  Asynchronous on `stream`. */
+int dg_mlp_pairs(dg_mlp* m, dg_handle* h, const double* x_dev, const double* xstar_dev, const int32_t* cells_dev,
+                 const int32_t* rows_dev, int64_t count, int32_t subtract_block_jacobi, void* X_dev, float* E_dev,
+                 void* stream);
+/* t = RMS of E_dev (rows x (k+1)^3 FP32 targets); E_dev /= t in place and t becomes the network's target scale
+ * (as dg_mlp_set_target_scale).  *t_scale (host, may be null) receives it.  Synchronises `stream`. */
+int dg_mlp_normalize_targets(dg_mlp* m, float* E_dev, int64_t rows, float* t_scale, void* stream);
 /* Y = network(X) for `rows` rows: Y device FP32 [rows][out_padded]. */
 int dg_mlp_forward(const dg_mlp* m, const void* X_dev, int64_t rows, float* Y_dev, void* stream);
 /* Mean squared error of network(X) against T and its gradient (kept in the network). */

@@ -527,44 +527,95 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_forward_tc(const FwdArgs a)
   }
 }
 
-// Feature rows for cells: X[row] = [r_T / s, log D (own, x-, x+, y-, y+, z-, z+), 0 ...] in BF16, and
-// scale[row] = s * t_scale (s = ||r_T||_2; a zero residual gives a zero row and scale 0).
+// One warp writes the feature row of `cell` into xr: [sign r_T / s, log D (own, x-, x+, y-, y+, z-, z+), 0 ...] in
+// BF16, s = ||r_T||_2 (a zero residual gives a zero row); returns s on every lane.
+template <typename T>
+__device__ __forceinline__ float feature_row(const T* __restrict__ rc, float sign, const double* __restrict__ D, int nx,
+                                             int ny, int nz, int64_t cell, int nb, int kinp, __nv_bfloat16* xr) {
+  const int lane = threadIdx.x & 31;
+  float ss = 0.f;
+  for (int j = lane; j < nb; j += 32) {
+    const float v = (float)rc[j];
+    ss = fmaf(v, v, ss);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  const float s = sqrtf(ss);
+  const float inv = s > 0.f ? sign / s : 0.f;
+  for (int j = lane; j < nb; j += 32) xr[j] = __float2bfloat16_rn((float)rc[j] * inv);
+  if (lane < 7) {
+    const int ic[3] = {(int)(cell % nx), (int)((cell / nx) % ny), (int)(cell / ((int64_t)nx * ny))};
+    int64_t c = cell;
+    if (lane > 0) {
+      const int dir = (lane - 1) / 2, up = (lane - 1) & 1;
+      const int n[3] = {nx, ny, nz};
+      const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+      const bool inside = up ? ic[dir] + 1 < n[dir] : ic[dir] > 0;
+      if (inside) c = up ? cell + st[dir] : cell - st[dir];
+    }
+    xr[nb + lane] = __float2bfloat16_rn((float)log(D[c]));
+  }
+  for (int j = nb + 7 + lane; j < kinp; j += 32) xr[j] = __float2bfloat16_rn(0.f);
+  return s;
+}
+
+// Feature rows for cells: X[row] = feature_row(r on cell), scale[row] = s * t_scale.
 template <typename T>
 __global__ void mlp_features(const T* __restrict__ r, const double* __restrict__ D, int nx, int ny, int nz,
                              const int* __restrict__ cells, int64_t nrows, int nb, int kinp, float t_scale,
                              __nv_bfloat16* __restrict__ X, float* __restrict__ scale) {
-  const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = warp0; row < nrows; row += nwarps) {
     const int64_t cell = cells ? cells[row] : row;
-    const T* rc = r + cell * nb;
-    float ss = 0.f;
-    for (int j = lane; j < nb; j += 32) {
-      const float v = (float)rc[j];
-      ss = fmaf(v, v, ss);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const float s = sqrtf(ss);
-    const float inv = s > 0.f ? 1.f / s : 0.f;
-    __nv_bfloat16* xr = X + row * kinp;
-    for (int j = lane; j < nb; j += 32) xr[j] = __float2bfloat16_rn((float)rc[j] * inv);
-    if (lane < 7) {
-      const int ic[3] = {(int)(cell % nx), (int)((cell / nx) % ny), (int)(cell / ((int64_t)nx * ny))};
-      int64_t c = cell;
-      if (lane > 0) {
-        const int dir = (lane - 1) / 2, up = (lane - 1) & 1;
-        const int n[3] = {nx, ny, nz};
-        const int64_t st[3] = {1, nx, (int64_t)nx * ny};
-        const bool inside = up ? ic[dir] + 1 < n[dir] : ic[dir] > 0;
-        if (inside) c = up ? cell + st[dir] : cell - st[dir];
-      }
-      xr[nb + lane] = __float2bfloat16_rn((float)log(D[c]));
-    }
-    for (int j = nb + 7 + lane; j < kinp; j += 32) xr[j] = __float2bfloat16_rn(0.f);
-    if (lane == 0) scale[row] = s * t_scale;
+    const float s = feature_row<T>(r + cell * nb, 1.f, D, nx, ny, nz, cell, nb, kinp, X + row * kinp);
+    if ((threadIdx.x & 31) == 0) scale[row] = s * t_scale;
   }
+}
+
+// Training pairs from a solver state: y = A x - F is the negated residual r = F - A x; for sample i (cell cells[i],
+// output row rows[i]) X[row] = feature_row(r), E[row][j] = (xstar - x - BJ(r))_j / ||r_cell|| on the cell, where
+// bjy = BJ(y) = -BJ(r) is the block-Jacobi correction of y (or null: no subtraction); zero where r_cell = 0.
+__global__ void mlp_pairs(const double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ xstar,
+                          const double* __restrict__ bjy, const double* __restrict__ D, int nx, int ny, int nz,
+                          const int* __restrict__ cells, const int* __restrict__ rows, int64_t count, int nb, int kinp,
+                          __nv_bfloat16* __restrict__ X, float* __restrict__ E) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp0; i < count; i += nwarps) {
+    const int64_t cell = cells[i], row = rows[i];
+    const float s = feature_row<double>(y + cell * nb, -1.f, D, nx, ny, nz, cell, nb, kinp, X + row * kinp);
+    const double inv = s > 0.f ? 1.0 / (double)s : 0.0;
+    const int64_t b = cell * nb;
+    for (int j = lane; j < nb; j += 32) {
+      double e = xstar[b + j] - x[b + j];
+      if (bjy) e += bjy[b + j];
+      E[row * nb + j] = (float)(e * inv);
+    }
+  }
+}
+
+// sum of squares of E in FP64: per-block partial sums
+__global__ void sum_squares(const float* __restrict__ E, int64_t n, double* __restrict__ part) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)E[i] * E[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void scale_in_place(float* __restrict__ E, int64_t n, float a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    E[i] *= a;
 }
 
 // ---- backward pass: BF16 tensor-core GEMMs with FP32 accumulation ----
@@ -1062,6 +1113,63 @@ int dg_mlp_features(const dg_mlp* m, const dg_handle* h, const void* r, int32_t 
                                                      h->n[0], h->n[1], h->n[2], cells, n, m->d.nb, m->d.kinp,
                                                      m->t_scale, Xb, scale);
   return cfail(cudaGetLastError(), "MLP features");
+}
+
+int dg_mlp_pairs(dg_mlp* m, dg_handle* h, const double* x, const double* xstar, const int32_t* cells,
+                 const int32_t* rows, int64_t count, int32_t subtract_block_jacobi, void* X, float* E, void* stream) {
+  if (!m || !h || !x || !xstar || !cells || !rows || !X || !E || count < 0 || h->N * h->N * h->N != m->d.nb ||
+      h->td) {
+    set_error("dg_mlp_pairs: bad arguments, degree mismatch, or a tensor-diffusion handle");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (subtract_block_jacobi && !h->bj64 && !h->fdm64) {
+    set_error("dg_mlp_pairs: subtract_block_jacobi needs dg_precond_setup first");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (count == 0) return DG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t ndof = (size_t)h->ncell * m->d.nb;
+  if (int rc = ensure_ws(m, (subtract_block_jacobi ? 2 : 1) * ndof * sizeof(double))) return rc;
+  double* y = static_cast<double*>(m->ws);
+  double* bjy = subtract_block_jacobi ? y + ndof : nullptr;
+  if (int rc = launch_apply_f64(h, x, y, 1, 3, s)) return rc;  // y = A x - F
+  if (bjy)
+    if (int rc = precond_bj_f64(h, y, bjy, s)) return rc;
+  dgm::mlp_pairs<<<sm_count() * 8, 256, 0, s>>>(y, x, xstar, bjy, static_cast<const double*>(h->p64.D), h->n[0],
+                                                 h->n[1], h->n[2], cells, rows, count, m->d.nb, m->d.kinp,
+                                                 static_cast<__nv_bfloat16*>(X), E);
+  return cfail(cudaGetLastError(), "MLP training pairs");
+}
+
+int dg_mlp_normalize_targets(dg_mlp* m, float* E, int64_t rows, float* t_scale, void* stream) {
+  if (!m || !E || rows < 1) {
+    set_error("dg_mlp_normalize_targets: bad arguments");
+    return DG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  constexpr int B = 256;
+  if (int rc = ensure_ws(m, B * sizeof(double))) return rc;
+  double* part = static_cast<double*>(m->ws);
+  const int64_t n = rows * m->d.nb;
+  dgm::sum_squares<<<B, 256, 0, s>>>(E, n, part);
+  std::vector<double> h(B);
+  if (int rc = cfail(cudaMemcpyAsync(h.data(), part, B * sizeof(double), cudaMemcpyDeviceToHost, s), "RMS copy"))
+    return rc;
+  if (int rc = cfail(cudaStreamSynchronize(s), "RMS sync")) return rc;
+  double tot = 0.0;
+  for (double v : h) tot += v;
+  const double rms = std::sqrt(tot / (double)n);
+  if (!std::isfinite(rms)) {
+    set_error("dg_mlp_normalize_targets: non-finite targets");
+    return DG_ERR_NAN;
+  }
+  if (rms > 0) {
+    dgm::scale_in_place<<<sm_count() * 8, 256, 0, s>>>(E, n, (float)(1.0 / rms));
+    if (int rc = cfail(cudaGetLastError(), "target scaling")) return rc;
+    m->t_scale = (float)rms;
+  }
+  if (t_scale) *t_scale = m->t_scale;
+  return DG_OK;
 }
 
 int dg_mlp_forward(const dg_mlp* m, const void* X, int64_t rows, float* Y, void* stream) {

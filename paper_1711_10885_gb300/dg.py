@@ -143,6 +143,8 @@ def _load():
     lib.dg_mlp_set_target_scale.argtypes = [vp, ctypes.c_float]
     lib.dg_mlp_features.argtypes = [vp, vp, vp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp]
     lib.dg_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.dg_mlp_pairs.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp, vp]
+    lib.dg_mlp_normalize_targets.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_float), vp]
     lib.dg_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp]
     lib.dg_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(dg_mlp_train_opts),
                                  ctypes.POINTER(dg_mlp_train_stats), vp]
@@ -164,7 +166,8 @@ EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadra
             "dg_mlp_param_offsets", "dg_mlp_set_target_scale", "dg_mlp_features", "dg_mlp_forward", "dg_mlp_loss_grad",
             "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load",
             "dg_apply_jacobian_static", "dg_setup_ex", "dg_project", "dg_rk_stage", "dg_ssprk2", "dg_assemble",
-            "dg_matrix_info", "dg_matrix_export", "dg_spmv", "dg_matrix_destroy", "dg_peak_probe"]
+            "dg_matrix_info", "dg_matrix_export", "dg_spmv", "dg_matrix_destroy", "dg_peak_probe", "dg_mlp_pairs",
+            "dg_mlp_normalize_targets"]
 
 
 def peak_probe(kind, iterations, sink, stream=None):
@@ -565,6 +568,21 @@ class MLP:
         check(lib.dg_mlp_features(self.m, op.h, ctypes.c_void_p(r.data_ptr()), _prec(r), cp, rows,
                                   ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(sc.data_ptr()), _stream_ptr(stream)))
         return X, sc
+
+    def pairs(self, op, x, xstar, cells, rows, X, E, subtract_block_jacobi=False, stream=None):
+        """Training pairs from a solver state (dg_mlp_pairs): cells and rows are int32 device tensors; X (BF16
+        [*, kin_padded]) and E (FP32 [*, (k+1)^3]) are written at the given rows."""
+        check(lib.dg_mlp_pairs(self.m, op.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(xstar.data_ptr()),
+                               ctypes.c_void_p(cells.data_ptr()), ctypes.c_void_p(rows.data_ptr()), cells.numel(),
+                               int(bool(subtract_block_jacobi)), ctypes.c_void_p(X.data_ptr()),
+                               ctypes.c_void_p(E.data_ptr()), _stream_ptr(stream)))
+
+    def normalize_targets(self, E, stream=None):
+        """E /= RMS(E) in place; the RMS becomes the network's target scale and is returned."""
+        t = ctypes.c_float()
+        check(lib.dg_mlp_normalize_targets(self.m, ctypes.c_void_p(E.data_ptr()), E.shape[0], ctypes.byref(t),
+                                           _stream_ptr(stream)))
+        return t.value
 
     def forward(self, X, stream=None):
         import torch

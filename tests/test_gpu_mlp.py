@@ -9,6 +9,7 @@ import tempfile
 import numpy as np
 import pytest
 
+import oracle
 from oracle import mlp as om
 from paper_1711_10885_gb300 import inputs
 from tests import mlp_bounds as mb
@@ -308,4 +309,61 @@ def test_tcgen05_weight_wait_timeout_gives_nan_rows(dg):
     finally:
         del os.environ["DG_MLP_WEIGHT_WAIT_TRIES"]
     assert torch.equal(mlp.forward(X), y_ok)
+    mlp.close()
+
+
+@pytest.mark.parametrize("subtract", [False, True])
+def test_training_pairs_match_oracle(dg, subtract):
+    """dg_mlp_pairs: the feature rows of r = F - A x and the targets e_T / ||r_T|| (e = x* - x, minus the exact
+    block inverse of r when subtract) at shuffled rows, against the FP64 oracle (A and F by direct quadrature,
+    the diagonal blocks solved with numpy); dg_mlp_normalize_targets against the RMS of the targets."""
+    w = inputs.small_case(n=(3, 4, 2), k=2, seed=19, sigma_D=1.5)
+    pr = oracle.Problem(w.n, w.k, w.D, b=w.b, c=w.c, lo=w.lo, hi=w.hi)
+    rng = np.random.default_rng(23)
+    x = rng.uniform(-1, 1, w.ndof)
+    xstar = rng.uniform(-1, 1, w.ndof)
+    F = oracle.rhs(pr, np.ones(pr.ncell * pr.m ** 3), None)
+    r = F - oracle.apply(pr, x)
+    e = xstar - x
+    nb = w.nb
+    if subtract:
+        for c in range(w.ncell):
+            sl = slice(c * nb, (c + 1) * nb)
+            B = np.empty((nb, nb))
+            for j in range(nb):
+                ej = np.zeros(w.ndof)
+                ej[c * nb + j] = 1.0
+                B[:, j] = oracle.apply(pr, ej)[sl]
+            e[sl] -= np.linalg.solve(B, r[sl])
+    op = dg.operator_for(w)
+    op.precond_setup()
+    mlp = dg.MLP(2, seed=1)
+    cells = np.array([0, 5, 7, 11, 13, 23], dtype=np.int32)
+    rows = np.array([3, 0, 5, 1, 4, 2], dtype=np.int32)
+    X = torch.zeros((len(cells), mlp.kinp), dtype=torch.bfloat16, device="cuda")
+    E = torch.zeros((len(cells), nb), dtype=torch.float32, device="cuda")
+    mlp.pairs(op, torch.tensor(x, device="cuda"), torch.tensor(xstar, device="cuda"),
+              torch.tensor(cells, device="cuda"), torch.tensor(rows, device="cuda"), X, E,
+              subtract_block_jacobi=subtract)
+    Xh, Eh = X.float().cpu().numpy(), E.cpu().numpy()
+    logD = np.log(w.D)
+    nx, ny, nz = w.n
+    E_ref = np.zeros_like(Eh, dtype=np.float64)
+    for c, row in zip(cells, rows):
+        ic = [c % nx, (c // nx) % ny, c // (nx * ny)]
+        nbr = [c]
+        for d, st, nn in ((0, 1, nx), (1, nx, ny), (2, nx * ny, nz)):
+            nbr.append(c - st if ic[d] > 0 else c)
+            nbr.append(c + st if ic[d] < nn - 1 else c)
+        feat, s = om.features(r[c * nb:(c + 1) * nb], logD[nbr], mlp.kinp)
+        ref = om.bf16_round(feat)
+        assert np.max(np.abs(Xh[row] - ref)) <= 2 ** -7 * np.max(np.abs(ref)), (c, row)
+        E_ref[row] = e[c * nb:(c + 1) * nb] / s
+        assert np.max(np.abs(Eh[row] - E_ref[row])) <= 1e-6 * np.max(np.abs(E_ref[row])), (c, row)
+    t = mlp.normalize_targets(E)
+    rms = np.sqrt(np.mean(E_ref ** 2))
+    assert abs(t - rms) <= 1e-6 * rms
+    assert np.max(np.abs(E.cpu().numpy() - E_ref / rms)) <= 1e-6 * np.max(np.abs(E_ref / rms))
+    assert mlp.params()[1] == pytest.approx(t)
+    op.close()
     mlp.close()
