@@ -38,8 +38,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
 # kernels as they were when profiled, keyed by the sha256 of the kernel source at that time.
 NCU_TRAFFIC = {
-    ("dg_cell_kernel", "5eaf0d8c36ebbee1"): 134589696 + 273854720,  # 134.59 MB read + 273.85 MB write
-    ("dg_face_kernel", "5eaf0d8c36ebbee1"): 474638080 + 112805888,  # 474.64 MB read + 112.81 MB write
+    ("dg_cell_kernel", "f1e344aa4d41ba1e"): 135631360 + 271920128,  # 135.63 MB read + 271.92 MB write
+    ("dg_face_kernel", "f1e344aa4d41ba1e"): 474571776 + 113187328,  # 474.57 MB read + 113.19 MB write
 }
 
 
@@ -256,6 +256,18 @@ def run_profile(args):
             op.apply_residual(u, r, precision=prec)
         torch.cuda.synchronize()
         print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "r_norm": float(r.abs().max())}))
+        op.close()
+        return
+    if args.f32:
+        # the FP32 operator of the mixed solve's inner FGMRES: 48^3 cells, Q5 (23.9 M DOF), W + K Jacobian applies
+        w = inputs.Workload("unit_cube_q5_48", (48, 48, 48), 5, inputs.log_normal_D(48 ** 3, 1.0, 3))
+        op = dg.Operator(w.n, w.k, w.D, b=w.b, c=w.c)
+        u = torch.tensor(inputs.uniform_u(w.ndof, 5), dtype=torch.float32, device="cuda")
+        y = torch.empty_like(u)
+        for _ in range(args.warmup + args.steps):
+            op.apply_jacobian(u, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "applies": args.warmup + args.steps, "y_max": float(y.abs().max())}))
         op.close()
         return
     if args.small:
@@ -557,6 +569,34 @@ def peak_probes():
     out["unit_count_fp64_tflops"] = FP64_PEAK_TFLOPS
     out["unit_count_fp32_tflops"] = FP32_PEAK_TFLOPS
     out["dmma_over_dfma"] = out["dmma_tflops"] / out["dfma_tflops"]
+    return out
+
+
+def f32_degrees(reps=50):
+    """FP32 Jacobian apply (the inner operator of the mixed solve) per degree 1..7 at about 24 M DOF: time per apply
+    (CUDA events, after five warm-ups), GDOF/s and the executed-flop rate against the FP32 unit-count peak."""
+    import torch
+
+    from paper_1711_10885_gb300 import dg, flops, inputs
+    out = {}
+    for k, n in ((1, 144), (2, 96), (3, 72), (4, 58), (5, 48), (6, 42), (7, 36)):
+        w = inputs.Workload("f32", (n, n, n), k, inputs.log_normal_D(n ** 3, 1.0, 1))
+        op = dg.Operator(w.n, w.k, w.D, b=w.b, c=w.c)
+        u = torch.tensor(inputs.uniform_u(w.ndof, 2), dtype=torch.float32, device="cuda")
+        y = torch.empty_like(u)
+        for _ in range(5):
+            op.apply_jacobian(u, y)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            op.apply_jacobian(u, y)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        tf = flops.apply_flops_per_dof(k, w.n, residual=False) * w.ndof / (ms * 1e-3) / 1e12
+        out[k] = {"cells": n ** 3, "dofs": w.ndof, "apply_us": ms * 1e3, "gdofs": w.ndof / ms / 1e6,
+                  "tflops": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS}
+        op.close()
     return out
 
 
@@ -1317,6 +1357,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner part of them")
     ap.add_argument("--solve-section", action="store_true", help="print only the default line's solve section")
     ap.add_argument("--peaks", action="store_true", help="print only the arithmetic throughput probes")
+    ap.add_argument("--f32", action="store_true", help="with --profile: W + K FP32 applies at 48^3 Q5")
+    ap.add_argument("--f32-degrees", action="store_true", help="print only the FP32 apply per degree")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched-apply comparison")
     ap.add_argument("--no-transport", action="store_true", help="skip the Taylor-Green transport section")
     ap.add_argument("--no-matrix", action="store_true", help="skip the matrix-based comparison section")
@@ -1391,6 +1433,10 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"peaks": peak_probes()}), flush=True)
+    elif args.f32_degrees:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"f32_degrees": f32_degrees()}), flush=True)
     elif args.solve_only:
         import torch
         torch.cuda.set_device(0)
