@@ -459,9 +459,11 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     q5_48: 48^3 Q5 (23.9 M DOF), log-normal D, 8 sine modes, to 1e-10 relative residual: the mixed-precision
       solve (FP64 outer FGMRES(10) with the true residual, defect update and orthogonalisation in FP64; FP32
       inner FGMRES(30) on the FP32 operator with the block inverse by fast diagonalisation) with the FP64 outer
-      operator (the conforming variant) and with the double-float outer operator, against plain FP64
-      FGMRES(30) with the same (exact) block-Jacobi preconditioner in FP64, capped at fp64_cap_s seconds.
-    q4_64: 64^3 Q4 (32.8 M DOF), sigma 1.5, to 1e-8: mixed + block-Jacobi, mixed + block-Jacobi + the learned
+      operator (the conforming variant) and with the double-float outer operator, each with the inner Krylov
+      basis stored in FP32 and in scaled FP16, against plain FP64 FGMRES(30) with the same (exact) block-Jacobi
+      preconditioner in FP64, capped at fp64_cap_s seconds.
+    q4_64: 64^3 Q4 (32.8 M DOF), sigma 1.5, to 1e-8: mixed + block-Jacobi (FP32 and FP16 inner basis),
+      mixed + block-Jacobi + the learned
       first direction, the network alone in every inner application (capped), and plain FP64 block-Jacobi
       (capped at fp64_cap_s_q4 seconds).  The network is trained on the solver's own pairs first (timed)."""
     import torch
@@ -480,10 +482,13 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
           "precond_setup_s": time.perf_counter() - t1,
           "precond": "block-Jacobi, exact block inverse by fast diagonalisation (FP32 inner, FP64 outer / plain)"}
     xs = {}
-    for name, outer in (("mixed_fp64_outer", 1), ("mixed_df_outer", 0)):
+    # each outer operator with the inner Krylov basis stored in FP32 (the default) and in scaled FP16
+    mixed = (("mixed_fp64_outer", 1, 0), ("mixed_df_outer", 0, 0), ("mixed_fp64_outer_fp16_basis", 1, 1),
+             ("mixed_df_outer_fp16_basis", 0, 1))
+    for name, outer, basis in mixed:
         st, xs[name] = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
                                     rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=10,
-                                    outer_precision=outer)
+                                    outer_precision=outer, inner_basis_precision=basis)
         q5[name] = st
     # plain FP64: its iteration rate first, to turn the time cap into an iteration cap
     st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
@@ -494,12 +499,12 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     st["iteration_cap"] = cap
     q5["fp64"] = st
     if st["converged"]:
-        for name in ("mixed_fp64_outer", "mixed_df_outer"):
+        for name, _, _ in mixed:
             q5[name]["field_diff_vs_fp64"] = float((xs[name] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
-        q5["speedup_mixed_fp64_outer"] = st["wall_s"] / q5["mixed_fp64_outer"]["wall_s"]
-        q5["speedup_mixed_df_outer"] = st["wall_s"] / q5["mixed_df_outer"]["wall_s"]
+            q5["speedup_" + name] = st["wall_s"] / q5[name]["wall_s"]
     else:
-        q5["speedup_lower_bound_mixed_fp64_outer"] = st["wall_s"] / q5["mixed_fp64_outer"]["wall_s"]
+        for name, _, _ in mixed:
+            q5["speedup_lower_bound_" + name] = st["wall_s"] / q5[name]["wall_s"]
     op.close()
     del xs
     out["q5_48"] = q5
@@ -524,6 +529,9 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     common = dict(rtol=1e-8, inner_rtol=1e-2, mlp=mlp)
     q4["mixed_bj"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
                                      preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, **common)
+    q4["mixed_bj_fp16_basis"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
+                                                preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, inner_basis_precision=1,
+                                                **common)
     q4["mixed_bj_learned"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
                                              preconditioner=dg.DG_PRECOND_BJ_MLP, mlp_placement=1, **common)
     q4["mixed_learned_only"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,

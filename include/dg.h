@@ -191,6 +191,12 @@ typedef struct {
                              (DG_F64X: FP64-level results on the FP32 pipes, about 4x faster on GB300),
                              with the stopping test confirmed by a true FP64 residual and the solve
                              finished in FP64 if that residual is still above rtol; 1 = FP64      */
+  int32_t inner_basis_precision; /* MIXED: storage of the inner FP32 FGMRES's orthonormal basis (its arithmetic
+                             stays FP32): 0 = FP32; 1 = FP16, each entry stored times 2^8 (the rows have unit
+                             length), which halves the bytes of the basis passes; applies when the vector
+                             length is a multiple of 8 (always for odd k), else FP32.  The rounding of the
+                             rows (2^-11 relative) perturbs the inner Arnoldi relation at that level, which
+                             the flexible outer method absorbs like any other inexact preconditioner.  */
 } dg_solve_opts;
 
 typedef struct {
@@ -205,8 +211,8 @@ typedef struct {
 } dg_solve_stats;
 
 /* Kinds of dg_precond_setup.  DG_BJ_DENSE: the dense inverse blocks below (FP64, FP32, FP16) and the
- * fast-diagonalisation tables.  DG_BJ_FAST_DIAG: only the fast-diagonalisation tables (complex FP32 and FP64,
- * 3 (2 (k+1)^2 + k+1) + 1 numbers per cell; any degree): every diagonal block is a Kronecker sum of three
+ * fast-diagonalisation tables.  DG_BJ_FAST_DIAG: only the fast-diagonalisation tables (FP32 and FP64, real or
+ * complex, 3 (2 (k+1)^2 + k+1) + 1 numbers per cell; any degree): every diagonal block is a Kronecker sum of three
  * 1D cell operators A_TT = I (x) I (x) A_x + I (x) A_y (x) I + A_z (x) I (x) I + c |T| I, inverted exactly
  * through their eigen-decompositions (computed on the host).  Both need the scalar axis-parallel kernels. */
 enum { DG_BJ_DENSE = 1, DG_BJ_FAST_DIAG = 2 };
@@ -218,6 +224,15 @@ enum { DG_BJ_DENSE = 1, DG_BJ_FAST_DIAG = 2 };
  * to a multiple of 4).  Memory: about ncells * (k+1)^6 * 12 bytes, owned by the handle.  Requires (k+1)^3 <= 512.  Returns
  * DG_ERR_NAN if a block is singular.  Synchronises `stream`. */
 int dg_precond_setup(dg_handle* h, int32_t kind, void* stream);
+
+/* What dg_precond_setup built, as bits of *info: DG_PRECOND_HAS_DENSE the dense inverse blocks,
+ * DG_PRECOND_HAS_FAST_DIAG the fast-diagonalisation tables, DG_PRECOND_FAST_DIAG_REAL all of them in real
+ * arithmetic.  A cell whose three 1D operators have real eigenvalues and eigenvectors (diffusion-dominated
+ * cells) gets real tables: half the bytes and a quarter of the multiply-adds of the complex form, which the
+ * other cells keep (e.g. convection-dominated ones); *complex_cells (may be NULL) receives their number.
+ * 0 before set-up. */
+enum { DG_PRECOND_HAS_DENSE = 1, DG_PRECOND_HAS_FAST_DIAG = 2, DG_PRECOND_FAST_DIAG_REAL = 4 };
+int dg_precond_info(const dg_handle* h, int32_t* info, int64_t* complex_cells);
 
 /* z = M^{-1} r with the block-Jacobi preconditioner (r, z device vectors of the given precision).  DG_F64
  * applies the dense FP64 inverse blocks (or, after DG_BJ_FAST_DIAG, the fast diagonalisation in complex FP64);

@@ -2,6 +2,7 @@
 // passes are bound by HBM bandwidth: they move 16 bytes per load and keep several rows in flight.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -252,6 +253,221 @@ __global__ void __launch_bounds__(RED_THREADS)
 sub(const T* __restrict__ a, const T* b, T* out, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = a[i] - b[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP16 storage of the inner FP32 FGMRES basis.  The stored rows are unit vectors, or provisional rows of
+// about unit length, so their entries are of magnitude 1 at most (typically n^-1/2, 3e-4 at n = 10^7).  They
+// are stored times HB_SCALE = 2^8: the typical entry then sits in FP16's normal range (down to 2^-14), and a
+// provisional row would have to exceed unit length 256-fold in one entry to overflow (which the Arnoldi step
+// reports as a non-finite dot product).  Entries below 2^-22 become subnormal, an absolute error of 2^-33 at
+// most.  All arithmetic is FP32; a row is read as (float)h * 2^-8 (exact) and written rounded to nearest.
+// Packs of 8 elements: one 16-byte load of the FP16 row, two of an FP32 vector.
+// ---------------------------------------------------------------------------------------------
+constexpr float HB_SCALE = 256.f, HB_INV = 1.f / 256.f;
+
+struct H8 {
+  float v[8];
+};
+// raw 16-byte load of 8 FP16 entries (kept packed while in flight: 4 registers) and its conversion
+__device__ __forceinline__ uint4 ld_raw(const __half* row, size_t p) { return reinterpret_cast<const uint4*>(row)[p]; }
+__device__ __forceinline__ H8 unpack_h8(const uint4& q) {
+  const __half2* h = reinterpret_cast<const __half2*>(&q);
+  H8 r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(h[i]);
+    r.v[2 * i] = f.x * HB_INV;
+    r.v[2 * i + 1] = f.y * HB_INV;
+  }
+  return r;
+}
+__device__ __forceinline__ H8 ld_h8(const __half* row, size_t p) {
+  const uint4 q = reinterpret_cast<const uint4*>(row)[p];
+  const __half2* h = reinterpret_cast<const __half2*>(&q);
+  H8 r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(h[i]);
+    r.v[2 * i] = f.x * HB_INV;
+    r.v[2 * i + 1] = f.y * HB_INV;
+  }
+  return r;
+}
+__device__ __forceinline__ void st_h8(__half* row, size_t p, const H8& x) {
+  uint4 q;
+  __half2* h = reinterpret_cast<__half2*>(&q);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(x.v[2 * i] * HB_SCALE, x.v[2 * i + 1] * HB_SCALE);
+  reinterpret_cast<uint4*>(row)[p] = q;
+}
+__device__ __forceinline__ H8 ld_f8(const float* row, size_t p) {
+  const float4 a = reinterpret_cast<const float4*>(row)[2 * p], b = reinterpret_cast<const float4*>(row)[2 * p + 1];
+  H8 r;
+  r.v[0] = a.x, r.v[1] = a.y, r.v[2] = a.z, r.v[3] = a.w, r.v[4] = b.x, r.v[5] = b.y, r.v[6] = b.z, r.v[7] = b.w;
+  return r;
+}
+__device__ __forceinline__ void st_f8(float* row, size_t p, const H8& x) {
+  reinterpret_cast<float4*>(row)[2 * p] = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+  reinterpret_cast<float4*>(row)[2 * p + 1] = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+
+// row conversions: dst (FP16, scaled) = a * src (FP32); dst (FP32) = src (FP16, unscaled)
+__global__ void __launch_bounds__(RED_THREADS) h_store_scaled(const float* __restrict__ src, float a,
+                                                              __half* __restrict__ dst, size_t npack) {
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npack; p += (size_t)gridDim.x * blockDim.x) {
+    H8 x = ld_f8(src, p);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x.v[e] *= a;
+    st_h8(dst, p, x);
+  }
+}
+__global__ void __launch_bounds__(RED_THREADS) h_load(const __half* __restrict__ src, float* __restrict__ dst,
+                                                      size_t npack) {
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npack; p += (size_t)gridDim.x * blockDim.x)
+    st_f8(dst, p, ld_h8(src, p));
+}
+
+// pass 1 with an FP16 basis (rows V_0 .. V_{nr-1}, u = V_{nr-1}) and an FP32 w; rows of `part` as basis_dots2
+__global__ void __launch_bounds__(DOTS2_THREADS, DOTS2_MINB)
+basis_dots2_h(const __half* __restrict__ V, size_t ld, int nr, const float* __restrict__ w, size_t npack,
+              double* __restrict__ part) {
+  extern __shared__ unsigned char basis_smem[];
+  float* acc = reinterpret_cast<float*>(basis_smem);
+  const int t = threadIdx.x;
+  const int nrow = 2 * nr + 1, nf = nr - 1;
+  for (int q = 0; q < nrow; ++q) acc[q * DOTS2_THREADS + t] = 0.f;
+  __syncthreads();
+  const __half* u = V + (size_t)nf * ld;
+  for (size_t p = (size_t)blockIdx.x * DOTS2_THREADS + t; p < npack; p += (size_t)gridDim.x * DOTS2_THREADS) {
+    const H8 wp = ld_f8(w, p), up = ld_h8(u, p);
+    for (int v0 = 0; v0 < nf; v0 += DOTS2_LOADS) {
+      uint4 a[DOTS2_LOADS];
+#pragma unroll
+      for (int q = 0; q < DOTS2_LOADS; ++q)
+        if (v0 + q < nf) a[q] = ld_raw(V + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < DOTS2_LOADS; ++q)
+        if (v0 + q < nf) {
+          const H8 aq = unpack_h8(a[q]);
+          float su = 0.f, sw = 0.f;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            su = fmaf(aq.v[e], up.v[e], su);
+            sw = fmaf(aq.v[e], wp.v[e], sw);
+          }
+          acc[(v0 + q) * DOTS2_THREADS + t] += su;
+          acc[(nr + v0 + q) * DOTS2_THREADS + t] += sw;
+        }
+    }
+    float uu = 0.f, uw = 0.f, ww = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      uu = fmaf(up.v[e], up.v[e], uu);
+      uw = fmaf(up.v[e], wp.v[e], uw);
+      ww = fmaf(wp.v[e], wp.v[e], ww);
+    }
+    acc[nf * DOTS2_THREADS + t] += uu;
+    acc[(nr + nf) * DOTS2_THREADS + t] += uw;
+    acc[2 * nr * DOTS2_THREADS + t] += ww;
+  }
+  __syncthreads();
+  const int lane = t & 31, wid = t >> 5;
+  for (int q = wid; q < nrow; q += DOTS2_THREADS / 32) {
+    double s = 0.0;
+    for (int k = lane; k < DOTS2_THREADS; k += 32) s += (double)acc[q * DOTS2_THREADS + k];
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)q * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// pass 2 with an FP16 basis: u = V_{nr-1} <- (u - V a) / alpha (when write_u), V_nr <- (w - V d - e u_old) / beta
+// (w FP32, the new row written to the basis); nothing when *stop
+__global__ void __launch_bounds__(RED_THREADS, PASS_MINB)
+basis_update2_h(__half* V, size_t ld, int nr, const double* __restrict__ coef, int write_u, const float* w,
+                size_t npack, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ float as[MAX_ROWS], ds[MAX_ROWS];
+  __shared__ float sc[3];
+  const int t = threadIdx.x, nf = nr - 1;
+  if (t < nf) {
+    as[t] = (float)coef[t];
+    ds[t] = (float)coef[MAX_ROWS + t];
+  }
+  if (t < 3) sc[t] = (float)coef[2 * MAX_ROWS + t];
+  __syncthreads();
+  const float ia = sc[0], e = sc[1], ib = sc[2];
+  __half* u = V + (size_t)nf * ld;
+  __half* out = V + (size_t)nr * ld;
+  for (size_t p = (size_t)blockIdx.x * RED_THREADS + t; p < npack; p += (size_t)gridDim.x * RED_THREADS) {
+    const H8 up = ld_h8(u, p), wp = ld_f8(w, p);
+    H8 tu, tw;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      tu.v[k] = up.v[k];
+      tw.v[k] = fmaf(-e, up.v[k], wp.v[k]);
+    }
+    for (int v0 = 0; v0 < nf; v0 += PASS_LOADS) {
+      uint4 a[PASS_LOADS];
+#pragma unroll
+      for (int q = 0; q < PASS_LOADS; ++q)
+        if (v0 + q < nf) a[q] = ld_raw(V + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < PASS_LOADS; ++q)
+        if (v0 + q < nf) {
+          const H8 aq = unpack_h8(a[q]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            tu.v[k] = fmaf(-as[v0 + q], aq.v[k], tu.v[k]);
+            tw.v[k] = fmaf(-ds[v0 + q], aq.v[k], tw.v[k]);
+          }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      tu.v[k] *= ia;
+      tw.v[k] *= ib;
+    }
+    if (write_u) st_h8(u, p, tu);
+    st_h8(out, p, tw);
+  }
+}
+
+// part[q * gridDim.x + b] = this block's share of V_q . x (q < nv), FP16 rows and FP16 x
+__global__ void __launch_bounds__(RED_THREADS, PASS_MINB)
+basis_dots_h(const __half* __restrict__ V, size_t ld, int nv, const __half* __restrict__ x, size_t npack,
+             double* __restrict__ part) {
+  extern __shared__ unsigned char basis_smem[];
+  float* acc = reinterpret_cast<float*>(basis_smem);
+  const int t = threadIdx.x;
+  for (int q = 0; q < nv; ++q) acc[q * RED_THREADS + t] = 0.f;
+  __syncthreads();
+  for (size_t p = (size_t)blockIdx.x * RED_THREADS + t; p < npack; p += (size_t)gridDim.x * RED_THREADS) {
+    const H8 xp = ld_h8(x, p);
+    for (int v0 = 0; v0 < nv; v0 += PASS_LOADS) {
+      uint4 a[PASS_LOADS];
+#pragma unroll
+      for (int q = 0; q < PASS_LOADS; ++q)
+        if (v0 + q < nv) a[q] = ld_raw(V + (size_t)(v0 + q) * ld, p);
+#pragma unroll
+      for (int q = 0; q < PASS_LOADS; ++q)
+        if (v0 + q < nv) {
+          const H8 aq = unpack_h8(a[q]);
+          float s = 0.f;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) s = fmaf(aq.v[e], xp.v[e], s);
+          acc[(v0 + q) * RED_THREADS + t] += s;
+        }
+    }
+  }
+  __syncthreads();
+  const int lane = t & 31, wid = t >> 5;
+  for (int q = wid; q < nv; q += RED_THREADS / 32) {
+    double s = 0.0;
+    for (int k = lane; k < RED_THREADS; k += 32) s += (double)acc[q * RED_THREADS + k];
+    s = warp_sum(s);
+    if (lane == 0) part[(size_t)q * gridDim.x + blockIdx.x] = s;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------

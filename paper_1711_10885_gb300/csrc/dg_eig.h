@@ -7,12 +7,14 @@
 // Method: Householder reduction to upper Hessenberg form, then complex single-shift QR iterations with
 // Wilkinson shifts (Givens rotations on the active block, deflation on negligible subdiagonal entries) to the
 // Schur form A = Q T Q^H; the eigenvectors of the triangular T by back substitution, mapped back with Q; and
-// V^{-1} by Gauss-Jordan elimination with partial pivoting.  Plain C++ (no CUDA), so that a host test can
-// check it against a library eigen-solver.
+// V^{-1} by Gauss-Jordan elimination with partial pivoting; when every eigenvalue is real, the same
+// decomposition in real arithmetic (real_decomposition).  Plain C++ (no CUDA), so that a host test can check it
+// against a library eigen-solver.
 #pragma once
 
 #include <cmath>
 #include <complex>
+#include <utility>
 
 namespace dge {
 
@@ -196,6 +198,67 @@ inline bool eig_general(int n, const double* A, cd* V, cd* Vinv, cd* lam) {
       vinv_max = std::fmax(vinv_max, std::abs(M[i][j + n]));
     }
   return vinv_max < 1e12;
+}
+
+// Real form of a decomposition from eig_general when every eigenvalue is real (|Im lambda| <= 1e-13 max |lambda|):
+// each eigenvector column is rotated by the conjugate phase of its largest entry (a real simple eigenvalue has a
+// real eigenvector up to a complex factor), which must leave imaginary parts below 1e-9 of the column's norm; the
+// real parts, renormalised to unit 2-norm, give Vr, and Wr = Vr^{-1} by Gauss-Jordan with partial pivoting.
+// Returns false (outputs unspecified) when an eigenvalue is complex, a column does not become real (a defective
+// or repeated eigenvalue with a complex basis of its eigenspace), or Vr is numerically singular.
+inline bool real_decomposition(int n, const cd* V, const cd* lam, double* Vr, double* Wr, double* lr) {
+  constexpr int NMAX = 16;
+  if (n < 1 || n > NMAX) return false;
+  double lmax = 0.0;
+  for (int k = 0; k < n; ++k) lmax = std::fmax(lmax, std::abs(lam[k]));
+  for (int k = 0; k < n; ++k) {
+    if (std::fabs(lam[k].imag()) > 1e-13 * lmax) return false;
+    lr[k] = lam[k].real();
+  }
+  for (int k = 0; k < n; ++k) {
+    int big = 0;
+    for (int i = 1; i < n; ++i)
+      if (std::abs(V[i * n + k]) > std::abs(V[big * n + k])) big = i;
+    const double vb = std::abs(V[big * n + k]);
+    if (!(vb > 0.0)) return false;
+    const cd rot = std::conj(V[big * n + k]) / vb;
+    double nrm = 0.0, imax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const cd v = V[i * n + k] * rot;
+      Vr[i * n + k] = v.real();
+      nrm += v.real() * v.real();
+      imax = std::fmax(imax, std::fabs(v.imag()));
+    }
+    nrm = std::sqrt(nrm);
+    if (imax > 1e-9 * nrm) return false;
+    for (int i = 0; i < n; ++i) Vr[i * n + k] /= nrm;
+  }
+  double M[NMAX][2 * NMAX];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) M[i][j] = j < n ? Vr[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int p = 0; p < n; ++p) {
+    int piv = p;
+    for (int i = p + 1; i < n; ++i)
+      if (std::fabs(M[i][p]) > std::fabs(M[piv][p])) piv = i;
+    if (!(std::fabs(M[piv][p]) > 1e-13)) return false;
+    if (piv != p)
+      for (int j = 0; j < 2 * n; ++j) std::swap(M[p][j], M[piv][j]);
+    const double d = M[p][p];
+    for (int j = 0; j < 2 * n; ++j) M[p][j] /= d;
+    for (int i = 0; i < n; ++i) {
+      if (i == p) continue;
+      const double f = M[i][p];
+      if (f == 0.0) continue;
+      for (int j = 0; j < 2 * n; ++j) M[i][j] -= f * M[p][j];
+    }
+  }
+  double wmax = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      Wr[i * n + j] = M[i][j + n];
+      wmax = std::fmax(wmax, std::fabs(M[i][j + n]));
+    }
+  return wmax < 1e12;
 }
 
 }  // namespace dge

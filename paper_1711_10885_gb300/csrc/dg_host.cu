@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -164,8 +165,8 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->bj32);
   cudaFree(h->bj16);
   cudaFree(h->bj16s);
-  cudaFree(h->fdm);
-  cudaFree(h->fdm64);
+  for (void* q : {h->fdm.re32, h->fdm.re64, h->fdm.cx32, h->fdm.cx64, (void*)h->fdm.re_cells, (void*)h->fdm.cx_cells})
+    cudaFree(q);
   cudaFree(h->bsc);
   cudaFree(h->bface);
   cudaFree(h->bscX);

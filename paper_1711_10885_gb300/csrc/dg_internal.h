@@ -32,6 +32,20 @@ struct Buffers {
 
 }  // namespace dgi
 
+// Tables of the fast-diagonalisation block inverse.  A cell whose three 1D operators have real eigenvalues and
+// eigenvectors gets real tables, the others complex ones (3 (2 n^2 + n) + 1 entries per cell either way, in the
+// order of their group); each group lists its cells in ascending order (null list: the group is every cell).
+struct FdmTables {
+  bool built = false;
+  int64_t nre = 0, ncx = 0;
+  void* re32 = nullptr;  // [nre][TS] float
+  void* re64 = nullptr;  // [nre][TS] double
+  void* cx32 = nullptr;  // [ncx][TS] float2
+  void* cx64 = nullptr;  // [ncx][TS] double2
+  int64_t* re_cells = nullptr;
+  int64_t* cx_cells = nullptr;
+};
+
 struct dg_handle {
   int k = 0, N = 0;
   int M = 0;                 // Gauss points per direction (N or N + 2)
@@ -84,9 +98,8 @@ struct dg_handle {
   // used by the FP32 inner solves of DG_SOLVE_MIXED
   void* bj16 = nullptr;
   void* bj16s = nullptr;
-  // exact block inverse by fast diagonalisation (complex FP32 tables, see dg_precond.cu); null if not built
-  void* fdm = nullptr;
-  void* fdm64 = nullptr;  // the same tables in complex FP64
+  // exact block inverse by fast diagonalisation (tables built on the host, see dg_precond.cu)
+  FdmTables fdm;
   // Krylov workspace (grown on demand, freed by dg_destroy)
   void* ws = nullptr;
   size_t ws_bytes = 0;

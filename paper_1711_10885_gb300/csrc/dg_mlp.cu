@@ -1122,7 +1122,7 @@ int dg_mlp_pairs(dg_mlp* m, dg_handle* h, const double* x, const double* xstar, 
     set_error("dg_mlp_pairs: bad arguments, degree mismatch, or a tensor-diffusion handle");
     return DG_ERR_INVALID_ARG;
   }
-  if (subtract_block_jacobi && !h->bj64 && !h->fdm64) {
+  if (subtract_block_jacobi && !h->bj64 && !h->fdm.built) {
     set_error("dg_mlp_pairs: subtract_block_jacobi needs dg_precond_setup first");
     return DG_ERR_INVALID_ARG;
   }

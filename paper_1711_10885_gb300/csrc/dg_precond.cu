@@ -306,21 +306,32 @@ struct Cx<double> {
   using type = double2;
 };
 
+// cell indices of the group positions q0 .. q0 + here - 1 (cells null: position = cell), into shared memory
+__device__ __forceinline__ void load_cells(int64_t* s_cell, const int64_t* __restrict__ cells, int64_t q0, int here) {
+  for (int i = threadIdx.x; i < here; i += blockDim.x) s_cell[i] = cells ? cells[q0 + i] : q0 + i;
+}
+
+// kernels over one group of cells: positions 0 .. count - 1 of the group, tables in group order
 template <int N, typename R>
 __global__ void __launch_bounds__(256) fdm_apply(const typename Cx<R>::type* __restrict__ tab, const R* __restrict__ r,
-                                                 R* __restrict__ z, int64_t ncell, int cpb) {
+                                                 R* __restrict__ z, int64_t count, const int64_t* __restrict__ cells,
+                                                 int cpb) {
   using C = typename Cx<R>::type;
   constexpr int NN = N * N, N3 = NN * N, TS = 3 * (2 * NN + N) + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_cell[64];
   C* U = reinterpret_cast<C*>(smem_raw);  // [cpb][N3]
   C* T = U + (size_t)cpb * N3;             // [cpb][TS]
   const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
-  const int64_t cell0 = (int64_t)blockIdx.x * cpb;
-  const int here = (int)min((int64_t)cpb, ncell - cell0);
-  for (int e = threadIdx.x; e < here * TS; e += blockDim.x) T[e] = tab[cell0 * TS + e];
+  const int64_t q0 = (int64_t)blockIdx.x * cpb;
+  const int here = (int)min((int64_t)cpb, count - q0);
+  load_cells(s_cell, cells, q0, here);
+  for (int e = threadIdx.x; e < here * TS; e += blockDim.x) T[e] = tab[q0 * TS + e];
+  __syncthreads();
   for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3;
     C v;
-    v.x = r[cell0 * N3 + e];
+    v.x = r[s_cell[l] * N3 + (e - l * N3)];
     v.y = R(0);
     U[e] = v;
   }
@@ -375,7 +386,10 @@ __global__ void __launch_bounds__(256) fdm_apply(const typename Cx<R>::type* __r
   }
   __syncthreads();
   for (int d = 0; d < 3; ++d) pass(d, tb + d * (2 * NN + N) + NN);  // V_d
-  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) z[cell0 * N3 + e] = U[e].x;
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3;
+    z[s_cell[l] * N3 + (e - l * N3)] = U[e].x;
+  }
 }
 
 // FP32 variant for n <= 6 with fewer shared-memory transactions: n threads per cell.  Thread p owns the plane
@@ -438,22 +452,26 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <int N>
 __global__ void __launch_bounds__(128, 4) fdm_apply_planes(const float2* __restrict__ tab, const float* __restrict__ r,
-                                                          float* __restrict__ z, int64_t ncell) {
+                                                          float* __restrict__ z, int64_t count,
+                                                          const int64_t* __restrict__ cells) {
   using P = FdmPlanes<N>;
   constexpr int NN = P::NN, N3 = P::N3, PP = P::PP, CP = P::CP, TS = P::TS, TSP = P::TSP, AX = 2 * NN + N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_cell[P::CB];
   float2* U = reinterpret_cast<float2*>(smem_raw);  // [CB][CP]: U[cell][c * PP + a + N b]
   float2* T = U + P::CB * CP;                        // [CB][TSP]
-  const int64_t cell0 = (int64_t)blockIdx.x * P::CB;
-  const int here = (int)min((int64_t)P::CB, ncell - cell0);
-  // the real input of plane c sits in the upper half of its complex slot: floats PP .. PP + NN - 1 of the plane
+  const int64_t q0 = (int64_t)blockIdx.x * P::CB;
+  const int here = (int)min((int64_t)P::CB, count - q0);
+  load_cells(s_cell, cells, q0, here);
   for (int e = threadIdx.x; e < here * TS; e += blockDim.x) {
     const int l = e / TS;
-    cp_async(T + l * TSP + (e - l * TS), tab + cell0 * TS + e, 1);
+    cp_async(T + l * TSP + (e - l * TS), tab + q0 * TS + e, 1);
   }
+  __syncthreads();
+  // the real input of plane c sits in the upper half of its complex slot: floats PP .. PP + NN - 1 of the plane
   for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
     const int l = e / N3, rem = e - l * N3, c = rem / NN;
-    cp_async(reinterpret_cast<float*>(U + l * CP + c * PP) + PP + (rem - c * NN), r + cell0 * N3 + e, 0);
+    cp_async(reinterpret_cast<float*>(U + l * CP + c * PP) + PP + (rem - c * NN), r + s_cell[l] * N3 + rem, 0);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -515,7 +533,171 @@ __global__ void __launch_bounds__(128, 4) fdm_apply_planes(const float2* __restr
   __syncthreads();
   for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
     const int l = e / N3, rem = e - l * N3, c = rem / NN;
-    z[cell0 * N3 + e] = U[l * CP + c * PP + (rem - c * NN)].x;
+    z[s_cell[l] * N3 + rem] = U[l * CP + c * PP + (rem - c * NN)].x;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same inverse with real tables: when every 1D cell operator has real eigenvalues (diffusion-dominated
+// cells, the usual case: the convection term is a small skew perturbation of the symmetric stiffness and
+// penalty terms) V_r, W_r and lambda_r are real, the table per cell holds 3 (2 n^2 + n) + 1 reals in the layout
+// above, and each 1D contraction is a real n x n product (a quarter of the complex one's FMAs).
+// ---------------------------------------------------------------------------------------------
+
+// FP32, n <= 8: n threads per cell owning planes (as fdm_apply_planes), the pass matrix in registers (n^2 floats).
+template <int N>
+struct FdmPlanesR {
+  static constexpr int NN = N * N, N3 = NN * N;
+  static constexpr int PP = NN | 1;                 // pitch of a plane c (words; odd)
+  static constexpr int CP = N * PP;                 // pitch of a cell's data
+  static constexpr int TS = 3 * (2 * NN + N) + 1;   // table entries per cell
+  static constexpr int TSP = TS | 1;                // their pitch in shared memory
+  static constexpr int CB = 128 / N;                // cells per CTA
+  static constexpr int SMEM = CB * (CP + TSP) * 4;
+};
+
+template <int N>
+__device__ __forceinline__ void fdm_matrix_r(float (&m)[N][N], const float* M) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int l = 0; l < N; ++l) m[i][l] = M[i * N + l];
+}
+
+// u[base + i * stride] <- sum_l m[i][l] u[base + l * stride]
+template <int N>
+__device__ __forceinline__ void fdm_line_r(const float (&m)[N][N], float* u, int base, int stride) {
+  float x[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) x[l] = u[base + l * stride];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float y = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) y = fmaf(m[i][l], x[l], y);
+    u[base + i * stride] = y;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(const float* __restrict__ tab,
+                                                                               const float* __restrict__ r,
+                                                                               float* __restrict__ z, int64_t count,
+                                                                               const int64_t* __restrict__ cells) {
+  using P = FdmPlanesR<N>;
+  constexpr int NN = P::NN, N3 = P::N3, PP = P::PP, CP = P::CP, TS = P::TS, TSP = P::TSP, AX = 2 * NN + N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_cell[P::CB];
+  float* U = reinterpret_cast<float*>(smem_raw);  // [CB][CP]: U[cell][c * PP + a + N b]
+  float* T = U + P::CB * CP;                       // [CB][TSP]
+  const int64_t q0 = (int64_t)blockIdx.x * P::CB;
+  const int here = (int)min((int64_t)P::CB, count - q0);
+  load_cells(s_cell, cells, q0, here);
+  for (int e = threadIdx.x; e < here * TS; e += blockDim.x) {
+    const int l = e / TS;
+    cp_async(T + l * TSP + (e - l * TS), tab + q0 * TS + e, 0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3, rem = e - l * N3, c = rem / NN;
+    cp_async(U + l * CP + c * PP + (rem - c * NN), r + s_cell[l] * N3 + rem, 0);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int lc = threadIdx.x / N, p = threadIdx.x - lc * N;
+  const bool active = lc < here;
+  float* u = U + lc * CP;
+  const float* tb = T + lc * TSP;
+  float m[N][N];
+  if (active) {  // W_x on the x-lines (b, c = p), W_y on the y-lines (a, c = p)
+    fdm_matrix_r<N>(m, tb);
+    for (int b = 0; b < N; ++b) fdm_line_r<N>(m, u, p * PP + N * b, 1);
+    fdm_matrix_r<N>(m, tb + AX);
+    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, p * PP + a, N);
+  }
+  __syncthreads();
+  if (active) {  // W_z on the z-lines (a, b = p); divide by lambda_x(a) + lambda_y(p) + lambda_z(c) + c |T|; V_z
+    fdm_matrix_r<N>(m, tb + 2 * AX);
+    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, a + N * p, PP);
+    const float* lx = tb + 2 * NN;
+    const float lyc = tb[AX + 2 * NN + p] + tb[TS - 1];
+    const float* lz = tb + 2 * AX + 2 * NN;
+    for (int a = 0; a < N; ++a) {
+      const float la = lx[a] + lyc;
+#pragma unroll
+      for (int c = 0; c < N; ++c) u[a + N * p + PP * c] /= la + lz[c];
+    }
+    fdm_matrix_r<N>(m, tb + 2 * AX + NN);
+    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, a + N * p, PP);
+  }
+  __syncthreads();
+  if (active) {  // V_y on the y-lines, V_x on the x-lines
+    fdm_matrix_r<N>(m, tb + AX + NN);
+    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, p * PP + a, N);
+    fdm_matrix_r<N>(m, tb + NN);
+    for (int b = 0; b < N; ++b) fdm_line_r<N>(m, u, p * PP + N * b, 1);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3, rem = e - l * N3, c = rem / NN;
+    z[s_cell[l] * N3 + rem] = U[l * CP + c * PP + (rem - c * NN)];
+  }
+}
+
+// any n and precision: one thread per line (n^2 threads per cell), the pass matrices read from shared memory
+template <int N, typename R>
+__global__ void __launch_bounds__(256) fdm_apply_real(const R* __restrict__ tab, const R* __restrict__ r,
+                                                      R* __restrict__ z, int64_t count,
+                                                      const int64_t* __restrict__ cells, int cpb) {
+  constexpr int NN = N * N, N3 = NN * N, TS = 3 * (2 * NN + N) + 1, AX = 2 * NN + N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_cell[64];
+  R* U = reinterpret_cast<R*>(smem_raw);  // [cpb][N3]
+  R* T = U + (size_t)cpb * N3;             // [cpb][TS]
+  const int lc = threadIdx.x / NN, t = threadIdx.x - lc * NN;
+  const int64_t q0 = (int64_t)blockIdx.x * cpb;
+  const int here = (int)min((int64_t)cpb, count - q0);
+  load_cells(s_cell, cells, q0, here);
+  for (int e = threadIdx.x; e < here * TS; e += blockDim.x) T[e] = tab[q0 * TS + e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3;
+    U[e] = r[s_cell[l] * N3 + (e - l * N3)];
+  }
+  __syncthreads();
+  const bool active = lc < here;
+  R* u = U + lc * N3;
+  const R* tb = T + lc * TS;
+  auto base = [&](int d) { return d == 0 ? N * t : (d == 1 ? (t % N) + NN * (t / N) : t); };
+  auto stride = [](int d) { return d == 0 ? 1 : (d == 1 ? N : NN); };
+  auto pass = [&](int d, const R* Mx) {
+    if (active) {
+      const int bs = base(d), st = stride(d);
+      R x[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) x[l] = u[bs + l * st];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        R y = R(0);
+#pragma unroll
+        for (int l = 0; l < N; ++l) y = fma(Mx[i * N + l], x[l], y);
+        u[bs + i * st] = y;
+      }
+    }
+    __syncthreads();
+  };
+  for (int d = 0; d < 3; ++d) pass(d, tb + d * AX);  // W_d
+  if (active) {
+    const int a = t % N, b = t / N;
+    const R lab = tb[2 * NN + a] + tb[AX + 2 * NN + b] + tb[TS - 1];
+#pragma unroll
+    for (int c = 0; c < N; ++c) u[a + N * b + NN * c] /= lab + tb[2 * AX + 2 * NN + c];
+  }
+  __syncthreads();
+  for (int d = 0; d < 3; ++d) pass(d, tb + d * AX + NN);  // V_d
+  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+    const int l = e / N3;
+    z[s_cell[l] * N3 + (e - l * N3)] = U[e];
   }
 }
 
@@ -564,8 +746,11 @@ void cell_operator_1d(const dg_handle* h, const std::vector<double>& D, int64_t 
 }  // namespace
 
 // the fast-diagonalisation tables of every cell (host, threads over cells); false if a 1D operator could not be
-// diagonalised (the preconditioner then keeps the dense blocks)
-bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<double2>& tab) {
+// diagonalised (the preconditioner then keeps the dense blocks).  Cells whose three 1D operators have real
+// eigenvalues and real eigenvectors get is_real = 1 and the same tables in real arithmetic in `real` (same
+// layout, one double per entry).
+bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<double2>& tab, std::vector<double>& real,
+               std::vector<uint8_t>& is_real) {
   const int n = h->N, M = h->M, NN = n * n, TS = 3 * (2 * NN + n) + 1;
   const Tables1D& t = h->tab;
   // theta_j and theta_j' at the points and at the ends, from the Lagrange tables (exact: degree <= k < M)
@@ -594,6 +779,8 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<dou
         C[i * n + j] += t.w[q] * dth[q * n + i] * th[q * n + j];
       }
   tab.assign((size_t)h->ncell * TS, make_double2(0.0, 0.0));
+  real.assign((size_t)h->ncell * TS, 0.0);
+  is_real.assign(h->ncell, 1);
   const double cvol = h->c * h->h[0] * h->h[1] * h->h[2];
   const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::vector<int> ok(nth, 1);
@@ -602,6 +789,7 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<dou
     std::vector<dge::cd> V(NN), W(NN), lam(n);
     for (int64_t cell = w; cell < h->ncell && ok[w]; cell += nth) {
       double2* o = &tab[(size_t)cell * TS];
+      double* orl = &real[(size_t)cell * TS];
       for (int r = 0; r < 3; ++r) {
         cell_operator_1d(h, D, cell, r, S, C, e0, e1, d0, d1, A.data());
         if (!dge::eig_general(n, A.data(), V.data(), W.data(), lam.data())) {
@@ -614,8 +802,12 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<dou
           b[NN + e] = make_double2(V[e].real(), V[e].imag());
         }
         for (int e = 0; e < n; ++e) b[2 * NN + e] = make_double2(lam[e].real(), lam[e].imag());
+        double* br = orl + r * (2 * NN + n);
+        if (is_real[cell] && !dge::real_decomposition(n, V.data(), lam.data(), br + NN, br, br + 2 * NN))
+          is_real[cell] = 0;
       }
       o[TS - 1] = make_double2(cvol, 0.0);
+      orl[TS - 1] = cvol;
     }
   };
   std::vector<std::thread> pool;
@@ -627,17 +819,69 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<dou
   return true;
 }
 
+// one group of cells with real tables: the plane kernel in FP32 up to n = 8, else one thread per line
 template <typename R>
-int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
+int fdm_group_real(const dg_handle* h, const R* tab, const int64_t* cells, int64_t count, const R* r, R* z,
+                   cudaStream_t s) {
+  const int N = h->N, NN = N * N, cpb = std::max(1, 256 / NN), TS = 3 * (2 * NN + N) + 1;
+  if constexpr (sizeof(R) == 4) {
+    if (N <= 8) {
+      switch (N) {
+#define FDMR(NV)                                                                                          \
+  case NV: {                                                                                              \
+    using P = FdmPlanesR<NV>;                                                                             \
+    static DeviceOnce attr;                                                                               \
+    if (P::SMEM > 48 * 1024) {                                                                            \
+      if (int rca = attr.run([] {                                                                         \
+            cudaError_t ea = cudaFuncSetAttribute(fdm_apply_planes_real<NV>,                              \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);  \
+            return ea == cudaSuccess ? 0 : cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply_planes_real)");  \
+          }))                                                                                             \
+        return rca;                                                                                       \
+    }                                                                                                     \
+    fdm_apply_planes_real<NV><<<(unsigned)((count + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>(       \
+        tab, r, z, count, cells);                                                                         \
+    break;                                                                                                \
+  }
+        FDMR(2) FDMR(3) FDMR(4) FDMR(5) FDMR(6) FDMR(7) FDMR(8)
+#undef FDMR
+      }
+      cudaError_t e = cudaGetLastError();
+      return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation, real)");
+    }
+  }
+  const size_t smem = (size_t)cpb * (N * NN + TS) * sizeof(R);
+  const unsigned grid = (unsigned)((count + cpb - 1) / cpb);
+  switch (N) {
+#define FDMG(NV)                                                                                          \
+  case NV:                                                                                                \
+    if (smem > 48 * 1024) {                                                                               \
+      static DeviceOnce attr;                                                                             \
+      if (int rca = attr.run([&] {                                                                        \
+            cudaError_t ea = cudaFuncSetAttribute(fdm_apply_real<NV, R>,                                  \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            return ea == cudaSuccess ? 0 : cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply_real)");         \
+          }))                                                                                             \
+        return rca;                                                                                       \
+    }                                                                                                     \
+    fdm_apply_real<NV, R><<<grid, cpb * NN, smem, s>>>(tab, r, z, count, cells, cpb);                     \
+    break;
+    FDMG(2) FDMG(3) FDMG(4) FDMG(5) FDMG(6) FDMG(7) FDMG(8) FDMG(9) FDMG(10) FDMG(11)
+#undef FDMG
+    default:
+      set_error("fast diagonalisation: unsupported degree");
+      return DG_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation, real)");
+}
+
+// one group of cells with complex tables: the plane kernel in FP32 up to n = 6, else one thread per line
+template <typename R>
+int fdm_group_complex(const dg_handle* h, const typename Cx<R>::type* tab, const int64_t* cells, int64_t count,
+                      const R* r, R* z, cudaStream_t s) {
   using C = typename Cx<R>::type;
   const int N = h->N, NN = N * N, cpb = std::max(1, 256 / NN), TS = 3 * (2 * NN + N) + 1;
-  const size_t smem = (size_t)cpb * (N * NN + TS) * sizeof(C);
-  const unsigned grid = (unsigned)((h->ncell + cpb - 1) / cpb);
-  const C* tab = static_cast<const C*>(sizeof(R) == 4 ? h->fdm : h->fdm64);
-  if (!tab) {
-    set_error("block-Jacobi: the fast diagonalisation was not set up");
-    return DG_ERR_INVALID_ARG;
-  }
   if constexpr (sizeof(R) == 4) {
     if (N <= 6) {
       switch (N) {
@@ -653,8 +897,8 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
           }))                                                                                             \
         return rca;                                                                                       \
     }                                                                                                     \
-    fdm_apply_planes<NV><<<(unsigned)((h->ncell + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>(          \
-        tab, r, z, h->ncell);                                                                             \
+    fdm_apply_planes<NV><<<(unsigned)((count + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>(tab, r, z,  \
+                                                                                           count, cells); \
     break;                                                                                                \
   }
         FDMP(2) FDMP(3) FDMP(4) FDMP(5) FDMP(6)
@@ -664,15 +908,21 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
       return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation)");
     }
   }
+  const size_t smem = (size_t)cpb * (N * NN + TS) * sizeof(C);
+  const unsigned grid = (unsigned)((count + cpb - 1) / cpb);
   switch (N) {
 #define FDM(NV)                                                                                           \
   case NV:                                                                                                \
     if (smem > 48 * 1024) {                                                                               \
-      cudaError_t ea = cudaFuncSetAttribute(fdm_apply<NV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                            (int)smem);                                                   \
-      if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply)");                    \
+      static DeviceOnce attr;                                                                             \
+      if (int rca = attr.run([&] {                                                                        \
+            cudaError_t ea = cudaFuncSetAttribute(fdm_apply<NV, R>,                                       \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            return ea == cudaSuccess ? 0 : cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply)");              \
+          }))                                                                                             \
+        return rca;                                                                                       \
     }                                                                                                     \
-    fdm_apply<NV, R><<<grid, cpb * NN, smem, s>>>(tab, r, z, h->ncell, cpb);                              \
+    fdm_apply<NV, R><<<grid, cpb * NN, smem, s>>>(tab, r, z, count, cells, cpb);                          \
     break;
     FDM(2) FDM(3) FDM(4) FDM(5) FDM(6) FDM(7) FDM(8) FDM(9) FDM(10) FDM(11)
 #undef FDM
@@ -682,6 +932,26 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation)");
+}
+
+// z = A_TT^{-1} r on every cell: the real group, then the complex group (disjoint cells)
+template <typename R>
+int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
+  using C = typename Cx<R>::type;
+  const FdmTables& f = h->fdm;
+  if (!f.built) {
+    set_error("block-Jacobi: the fast diagonalisation was not set up");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (f.nre > 0)
+    if (int rc = fdm_group_real<R>(h, static_cast<const R*>(sizeof(R) == 4 ? f.re32 : f.re64), f.re_cells, f.nre, r,
+                                   z, s))
+      return rc;
+  if (f.ncx > 0)
+    if (int rc = fdm_group_complex<R>(h, static_cast<const C*>(sizeof(R) == 4 ? f.cx32 : f.cx64), f.cx_cells, f.ncx,
+                                      r, z, s))
+      return rc;
+  return 0;
 }
 
 int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) { return precond_fdm(h, r, z, s); }
@@ -729,30 +999,63 @@ using namespace dgi;
 extern "C" {
 
 namespace {
-// the fast-diagonalisation tables (complex FP32 and FP64) of every cell; DG_ERR_NAN if a 1D cell operator
-// could not be diagonalised
+// the fast-diagonalisation tables of every cell (FP32 and FP64; real for the cells that allow it, complex for the
+// others, each group with its list of cells); DG_ERR_NAN if a 1D cell operator could not be diagonalised
 int setup_fdm(dg_handle* h) {
-  if (h->fdm && h->fdm64) return DG_OK;
+  if (h->fdm.built) return DG_OK;
   std::vector<double> Dh(h->ncell);
   cudaError_t e = cudaMemcpy(Dh.data(), h->p64.D, h->ncell * sizeof(double), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "fast diagonalisation: D");
   std::vector<double2> tab;
-  if (!build_fdm(h, Dh, tab)) {
+  std::vector<double> real;
+  std::vector<uint8_t> is_real;
+  if (!build_fdm(h, Dh, tab, real, is_real)) {
     set_error("dg_precond_setup: a 1D cell operator could not be diagonalised");
     return DG_ERR_NAN;
   }
-  std::vector<float2> tab32(tab.size());
-  for (size_t i = 0; i < tab.size(); ++i) tab32[i] = make_float2((float)tab[i].x, (float)tab[i].y);
-  e = cudaMalloc(&h->fdm64, tab.size() * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc(&h->fdm, tab.size() * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMemcpy(h->fdm64, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->fdm, tab32.data(), tab32.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  const int N = h->N, TS = 3 * (2 * N * N + N) + 1;
+  std::vector<int64_t> re_cells, cx_cells;
+  for (int64_t c = 0; c < h->ncell; ++c) (is_real[c] ? re_cells : cx_cells).push_back(c);
+  const int64_t nre = (int64_t)re_cells.size(), ncx = (int64_t)cx_cells.size();
+  // group tables in group order
+  std::vector<double> re64((size_t)nre * TS);
+  std::vector<float> re32((size_t)nre * TS);
+  std::vector<double2> cx64((size_t)ncx * TS);
+  std::vector<float2> cx32((size_t)ncx * TS);
+  for (int64_t q = 0; q < nre; ++q)
+    for (int i = 0; i < TS; ++i) {
+      re64[(size_t)q * TS + i] = real[(size_t)re_cells[q] * TS + i];
+      re32[(size_t)q * TS + i] = (float)real[(size_t)re_cells[q] * TS + i];
+    }
+  for (int64_t q = 0; q < ncx; ++q)
+    for (int i = 0; i < TS; ++i) {
+      const double2 v = tab[(size_t)cx_cells[q] * TS + i];
+      cx64[(size_t)q * TS + i] = v;
+      cx32[(size_t)q * TS + i] = make_float2((float)v.x, (float)v.y);
+    }
+  FdmTables f;
+  f.nre = nre;
+  f.ncx = ncx;
+  auto up = [&](void** dst, const void* src, size_t bytes) {
+    if (e != cudaSuccess || bytes == 0) return;
+    e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up(&f.re32, re32.data(), re32.size() * sizeof(float));
+  up(&f.re64, re64.data(), re64.size() * sizeof(double));
+  up(&f.cx32, cx32.data(), cx32.size() * sizeof(float2));
+  up(&f.cx64, cx64.data(), cx64.size() * sizeof(double2));
+  // a group that is every cell needs no list
+  if (ncx > 0) {
+    up(reinterpret_cast<void**>(&f.cx_cells), cx_cells.data(), cx_cells.size() * sizeof(int64_t));
+    if (nre > 0) up(reinterpret_cast<void**>(&f.re_cells), re_cells.data(), re_cells.size() * sizeof(int64_t));
+  }
   if (e != cudaSuccess) {
-    cudaFree(h->fdm);
-    cudaFree(h->fdm64);
-    h->fdm = h->fdm64 = nullptr;
+    for (void* q : {f.re32, f.re64, f.cx32, f.cx64, (void*)f.re_cells, (void*)f.cx_cells}) cudaFree(q);
     return cuda_fail(e, "fast diagonalisation tables");
   }
+  f.built = true;
+  h->fdm = f;
   return DG_OK;
 }
 }  // namespace
@@ -865,19 +1168,30 @@ int dg_precond_setup(dg_handle* h, int32_t kind, void* stream) {
   return rc;
 }
 
+int dg_precond_info(const dg_handle* h, int32_t* info, int64_t* complex_cells) {
+  if (!h || !info) {
+    set_error("dg_precond_info: null handle or output");
+    return DG_ERR_INVALID_ARG;
+  }
+  *info = (h->bj64 ? DG_PRECOND_HAS_DENSE : 0) | (h->fdm.built ? DG_PRECOND_HAS_FAST_DIAG : 0) |
+          (h->fdm.built && h->fdm.ncx == 0 ? DG_PRECOND_FAST_DIAG_REAL : 0);
+  if (complex_cells) *complex_cells = h->fdm.built ? h->fdm.ncx : 0;
+  return DG_OK;
+}
+
 int dg_precond_apply(dg_handle* h, const void* r, void* z, int32_t precision, void* stream) {
   if (!h || !r || !z || r == z || (precision != DG_F64 && precision != DG_F32)) {
     set_error("dg_precond_apply: bad arguments");
     return DG_ERR_INVALID_ARG;
   }
-  if (!h->bj64 && !h->fdm64) {
+  if (!h->bj64 && !h->fdm.built) {
     set_error("dg_precond_apply: call dg_precond_setup first");
     return DG_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == DG_F64) return precond_bj_f64(h, static_cast<const double*>(r), static_cast<double*>(z), s);
   // FP32: the exact block inverse by fast diagonalisation when it was built, else the FP32 dense blocks
-  if (h->fdm) return precond_fdm_f32(h, static_cast<const float*>(r), static_cast<float*>(z), s);
+  if (h->fdm.built) return precond_fdm_f32(h, static_cast<const float*>(r), static_cast<float*>(z), s);
   return precond_bj_f32(h, static_cast<const float*>(r), static_cast<float*>(z), s);
 }
 

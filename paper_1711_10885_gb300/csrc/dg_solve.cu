@@ -8,6 +8,7 @@
 #include <functional>
 #include <initializer_list>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "dg_blas.cuh"
@@ -181,6 +182,42 @@ int basis_update2(Ctx& c, T* V, int nr, bool write_u, T* w, const int* stop) {
   return cuda_check(cudaGetLastError(), "basis update");
 }
 
+// The same three passes over an FP16 basis (rows scaled by dgb::HB_SCALE) of the FP32 inner solve; w is an FP32
+// vector of its own.  The caller guarantees n % 8 == 0 and 16-byte aligned rows.
+int basis_dots2(Ctx& c, const __half* V, int nr, const float* w, double* dst) {
+  const int rows = 2 * nr + 1;
+  static DeviceOnce attr;
+  if (int rc = attr.run([] {
+        return cuda_check(cudaFuncSetAttribute(dgb::basis_dots2_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               dgb::PART_ROWS * dgb::DOTS2_THREADS * (int)sizeof(float)),
+                          "basis pass shared memory");
+      }))
+    return rc;
+  dgb::basis_dots2_h<<<c.dots2_blocks, dgb::DOTS2_THREADS, (size_t)rows * dgb::DOTS2_THREADS * sizeof(float), c.s>>>(
+      V, c.n, nr, w, c.n / 8, c.part);
+  dgb::mdot_final<<<rows, dgb::RED_THREADS, 0, c.s>>>(c.part, c.dots2_blocks, dst);
+  return cuda_check(cudaGetLastError(), "basis dot kernels");
+}
+
+int basis_update2(Ctx& c, __half* V, int nr, bool write_u, const float* w, const int* stop) {
+  dgb::basis_update2_h<<<c.pass_blocks, dgb::RED_THREADS, 0, c.s>>>(V, c.n, nr, c.cdev, write_u, w, c.n / 8, stop);
+  return cuda_check(cudaGetLastError(), "basis update");
+}
+
+int basis_dots(Ctx& c, const __half* V, int nv, const __half* x, double* dst) {
+  static DeviceOnce attr;
+  if (int rc = attr.run([] {
+        return cuda_check(cudaFuncSetAttribute(dgb::basis_dots_h, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               dgb::MAX_ROWS * dgb::RED_THREADS * (int)sizeof(float)),
+                          "basis pass shared memory");
+      }))
+    return rc;
+  dgb::basis_dots_h<<<c.pass_blocks, dgb::RED_THREADS, (size_t)nv * dgb::RED_THREADS * sizeof(float), c.s>>>(
+      V, c.n, nv, x, c.n / 8, c.part);
+  dgb::mdot_final<<<nv, dgb::RED_THREADS, 0, c.s>>>(c.part, c.pass_blocks, dst);
+  return cuda_check(cudaGetLastError(), "basis dot kernels");
+}
+
 // Flexible GMRES(m) on A x = b in precision T with right preconditioner M (nullptr: none, z_j = v_j).
 // V: (m+1) n, Z: m n.  x holds the initial guess unless x0_zero.
 //
@@ -202,11 +239,17 @@ int basis_update2(Ctx& c, T* V, int nr, bool write_u, T* w, const int* stop) {
 // tolerance, one more dot pass (the reorthogonalisation of u_{j+1}) finalises column j and decides; a cycle
 // that stops between two reads is confirmed by the next step's pass 1, whose operator application is then
 // unused.  The outer solve reads every step (its steps are whole inner solves); the inner one less often.
-template <typename T>
-int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, bool x0_zero, T* V, T* Z, int m,
+//
+// B = __half (T = float only): the basis V is stored in scaled FP16 and `tmp` holds two FP32 vectors, the new
+// operator product w and the FP32 copy of u_j that the preconditioner reads.
+template <typename T, typename B = T>
+int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, bool x0_zero, B* V, T* Z, int m,
            double tol_abs, int maxit, int max_cycles, bool true_residual_check, Result* out,
            const std::function<void(double, double)>& cycle_hook = {},
-           const std::function<int(const T*, T*)>& M0 = {}, int check_every = 1) {
+           const std::function<int(const T*, T*)>& M0 = {}, int check_every = 1, T* tmp = nullptr) {
+  constexpr bool half_basis = !std::is_same<T, B>::value;
+  static_assert(!half_basis || (std::is_same<T, float>::value && std::is_same<B, __half>::value),
+                "FP16 basis storage is for the FP32 solve");
   const size_t n = c.n;
   if (c.depth > 1) {
     set_error("FGMRES: nested deeper than outer and inner solve");
@@ -235,7 +278,9 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
   };
   Result r;
   for (int cycle = 0; cycle < max_cycles; ++cycle) {
-    T* v0 = V;
+    T* v0;  // the residual, normalised in place (or, with an FP16 basis, stored scaled into row 0)
+    if constexpr (half_basis) v0 = tmp;
+    else v0 = V;
     if (x0_zero && cycle == 0) {
       if (int rc = cuda_check(cudaMemcpyAsync(v0, b, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s), "copy b"))
         return rc;
@@ -258,15 +303,29 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     }
     if (r.iterations >= maxit) break;
     if (cycle > 0 && !true_residual_check) break;
-    if (int rc = scale<T>(c, v0, 1.0 / beta)) return rc;
+    if constexpr (half_basis) {
+      dgb::h_store_scaled<<<c.red_blocks, dgb::RED_THREADS, 0, c.s>>>(v0, (float)(1.0 / beta), V, n / 8);
+      if (int rc = cuda_check(cudaGetLastError(), "basis row store")) return rc;
+    } else if (int rc = scale<T>(c, v0, 1.0 / beta)) {
+      return rc;
+    }
     dgb::arn_init<<<1, 1, 0, c.s>>>(st, m, tol_abs, beta);
     const int steps = std::min(m, maxit - r.iterations);
     int last = steps - 1;  // the step after which the cycle's last column is finalised
     bool finalised = false;
     for (int j = 0; j < steps; ++j) {
-      T* uj = V + (size_t)j * n;
+      const T* uj;
+      T* w;
       T* zj = Z + (size_t)j * n;
-      T* w = V + (size_t)(j + 1) * n;
+      if constexpr (half_basis) {
+        dgb::h_load<<<c.red_blocks, dgb::RED_THREADS, 0, c.s>>>(V + (size_t)j * n, tmp + n, n / 8);
+        if (int rc = cuda_check(cudaGetLastError(), "basis row load")) return rc;
+        uj = tmp + n;
+        w = tmp;
+      } else {
+        uj = V + (size_t)j * n;
+        w = V + (size_t)(j + 1) * n;
+      }
       if (j == 0 && M0) {
         if (int rc = M0(uj, zj)) return rc;
       } else if (M) {
@@ -276,9 +335,9 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
           return rc;
       }
       if (int rc = apply_A<T>(c, zj, w)) return rc;
-      if (int rc = basis_dots2<T>(c, V, j + 1, w, c.hdev)) return rc;  // pass 1
+      if (int rc = basis_dots2(c, V, j + 1, w, c.hdev)) return rc;  // pass 1
       dgb::arn_step<<<1, 32, 0, c.s>>>(st, c.hdev, j, c.cdev);
-      if (int rc = basis_update2<T>(c, V, j + 1, j > 0, w, stop)) return rc;  // pass 2
+      if (int rc = basis_update2(c, V, j + 1, j > 0, w, stop)) return rc;  // pass 2
       if (j == steps - 1 || (j + 1) % check_every != 0) continue;
       if (int rc = read_head()) return rc;
       if (hd.stop) {  // converged or broke down at an earlier column: nothing left to finalise
@@ -288,7 +347,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
       }
       if (hd.prov <= tol_abs) {
         // finalise column j now: the reorthogonalisation of u_{j+1} against rows 0 .. j
-        if (int rc = basis_dots<T>(c, V, j + 2, w, c.hdev)) return rc;
+        if (int rc = basis_dots(c, V, j + 2, V + (size_t)(j + 1) * n, c.hdev)) return rc;
         dgb::arn_final<<<1, 32, 0, c.s>>>(st, c.hdev, j);
         if (int rc = read_head()) return rc;
         if (hd.res <= tol_abs) {
@@ -300,7 +359,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     }
     // finalise the last column: the reorthogonalisation of u_steps against rows 0 .. steps - 1
     if (!finalised) {
-      if (int rc = basis_dots<T>(c, V, last + 2, V + (size_t)(last + 1) * n, c.hdev)) return rc;
+      if (int rc = basis_dots(c, V, last + 2, V + (size_t)(last + 1) * n, c.hdev)) return rc;
       dgb::arn_final<<<1, 32, 0, c.s>>>(st, c.hdev, last);
     }
     dgb::arn_solve<<<1, 1, 0, c.s>>>(st, c.ydev);
@@ -360,6 +419,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   if (m > 60 || mo > 60 || (o->mode != DG_SOLVE_FP64 && o->mode != DG_SOLVE_MIXED) ||
       (o->inner_block_precision < 0 || o->inner_block_precision > 2) ||
       (o->outer_precision < 0 || o->outer_precision > 1) ||
+      (o->inner_basis_precision < 0 || o->inner_basis_precision > 1) ||
       (o->preconditioner != DG_PRECOND_NONE && o->preconditioner != DG_PRECOND_BLOCK_JACOBI &&
        o->preconditioner != DG_PRECOND_MLP && o->preconditioner != DG_PRECOND_BJ_MLP) ||
       !(o->rtol > 0) || (o->mode == DG_SOLVE_MIXED && !(o->inner_rtol > 0 && o->inner_rtol < 1))) {
@@ -372,7 +432,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     return DG_ERR_INVALID_ARG;
   }
   if ((o->preconditioner == DG_PRECOND_BLOCK_JACOBI || o->preconditioner == DG_PRECOND_BJ_MLP) && !h->bj64 &&
-      !h->fdm64) {
+      !h->fdm.built) {
     set_error("dg_solve: block-Jacobi requested but dg_precond_setup was not called");
     return DG_ERR_INVALID_ARG;
   }
@@ -393,7 +453,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   int fallback = 0;
   dg_mlp* mlp = const_cast<dg_mlp*>(o->mlp);
   auto maybe_fallback = [&](double start, double end) {
-    if (use_mlp && o->fallback_ratio > 0 && (h->bj64 || h->fdm64) && start > 0 && end > o->fallback_ratio * start) {
+    if (use_mlp && o->fallback_ratio > 0 && (h->bj64 || h->fdm.built) && start > 0 && end > o->fallback_ratio * start) {
       use_mlp = false;
       fallback = 1;
     }
@@ -406,12 +466,14 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   const size_t part_size = (size_t)dgb::PART_ROWS * std::max(c.dots2_blocks, c.red_blocks);
   const size_t arn_words = (sizeof(dgb::ArnState) + 255) / 256 * 32;  // one state, rounded to 256 bytes
   const size_t small = part_size + 400 + 2 * arn_words;
+  // FP16 storage of the inner basis: FP32 Z, rhs, e, w and u (m + 4 vectors), then the m + 1 FP16 rows
+  const bool half_basis = o->mode == DG_SOLVE_MIXED && o->inner_basis_precision == 1 && n % 8 == 0;
   size_t v64 = 0, v32 = 0;
   if (o->mode == DG_SOLVE_FP64) {
     v64 = (size_t)(2 * m + 1) * n;  // V and Z (Z = V's provisional rows without a preconditioner)
   } else {
     v64 = (size_t)(2 * mo + 1) * n;
-    v32 = (size_t)(2 * m + 1 + 2) * n;
+    v32 = half_basis ? (size_t)(m + 4) * n + (size_t)(m + 1) * n / 2 : (size_t)(2 * m + 1 + 2) * n;
   }
   const size_t bytes = (small + n + v64) * sizeof(double) + v32 * sizeof(float) + 256;
   if (int rc = ensure_ws(h, bytes)) return rc;
@@ -427,7 +489,8 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   c.arn[1] = reinterpret_cast<dgb::ArnState*>(base + part_size + 400 + arn_words);
   double* bcopy = base + small;
   double* V64 = bcopy + n;
-  float* f32 = reinterpret_cast<float*>(V64 + v64);
+  // the FP32 / FP16 vectors start on a 256-byte boundary (the 256 spare bytes of the workspace)
+  float* f32 = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(V64 + v64) + 255) / 256 * 256);
   c.hhost = h->ws_host;
 
   int rc = 0;
@@ -467,16 +530,27 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     inner_total = res.iterations;
   } else {
     // inner FP32 FGMRES(m) on the FP32 operator, x0 = 0, one cycle or until inner_rtol: z = P(v)
-    float* V32 = f32;
-    float* Z32 = V32 + (size_t)(m + 1) * n;
-    float* rhs32 = Z32 + (size_t)m * n;
-    float* e32 = rhs32 + n;
+    float *V32, *Z32, *rhs32, *e32, *tmp32 = nullptr;
+    __half* V16 = nullptr;
+    if (half_basis) {
+      Z32 = f32;
+      rhs32 = Z32 + (size_t)m * n;
+      e32 = rhs32 + n;
+      tmp32 = e32 + n;
+      V16 = reinterpret_cast<__half*>(tmp32 + 2 * n);
+      V32 = nullptr;
+    } else {
+      V32 = f32;
+      Z32 = V32 + (size_t)(m + 1) * n;
+      rhs32 = Z32 + (size_t)m * n;
+      e32 = rhs32 + n;
+    }
     std::function<int(const float*, float*)> M32;
     // block-Jacobi inside the FP32 inner solve: the FP16 blocks (half the bytes of this HBM-bound product) unless
     // the caller asked for the FP32 ones
     auto bj_inner = [&](const float* r, float* z) {
       if (o->inner_block_precision == 1) return precond_bj_f32(h, r, z, s);
-      if (o->inner_block_precision == 0 && h->fdm) return precond_fdm_f32(h, r, z, s);
+      if (o->inner_block_precision == 0 && h->fdm.built) return precond_fdm_f32(h, r, z, s);
       return precond_bj_f16(h, r, z, s);
     };
     if (pc)
@@ -496,8 +570,11 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       double vn2;
       int rc2 = dots<float>(c, rhs32, 1, rhs32, &vn2);
       if (rc2) return rc2;
-      rc2 = fgmres<float>(c, M32, rhs32, e32, true, V32, Z32, m, o->inner_rtol * std::sqrt(vn2), m, 1, false, &ri,
-                          {}, {}, kInnerCheckEvery);
+      const double itol = o->inner_rtol * std::sqrt(vn2);
+      rc2 = half_basis ? fgmres<float, __half>(c, M32, rhs32, e32, true, V16, Z32, m, itol, m, 1, false, &ri, {}, {},
+                                               kInnerCheckEvery, tmp32)
+                       : fgmres<float>(c, M32, rhs32, e32, true, V32, Z32, m, itol, m, 1, false, &ri, {}, {},
+                                       kInnerCheckEvery);
       if (rc2) return rc2;
       maybe_fallback(ri.beta0, ri.res);
       inner_total += ri.iterations;

@@ -70,6 +70,9 @@ DG_PRECOND_MLP = 2
 DG_PRECOND_BJ_MLP = 3
 DG_BJ_DENSE = 1
 DG_BJ_FAST_DIAG = 2
+DG_PRECOND_HAS_DENSE = 1
+DG_PRECOND_HAS_FAST_DIAG = 2
+DG_PRECOND_FAST_DIAG_REAL = 4
 
 
 class dg_solve_opts(ctypes.Structure):
@@ -77,7 +80,7 @@ class dg_solve_opts(ctypes.Structure):
                 ("outer_restart", ctypes.c_int32), ("max_iterations", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("inner_rtol", ctypes.c_double), ("mlp", ctypes.c_void_p), ("mlp_placement", ctypes.c_int32),
                 ("fallback_ratio", ctypes.c_double), ("inner_block_precision", ctypes.c_int32),
-                ("outer_precision", ctypes.c_int32)]
+                ("outer_precision", ctypes.c_int32), ("inner_basis_precision", ctypes.c_int32)]
 
 
 class dg_mlp_train_opts(ctypes.Structure):
@@ -129,6 +132,7 @@ def _load():
     lib.dg_apply_stage.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32, ctypes.c_int32, vp]
     lib.dg_precond_setup.argtypes = [vp, ctypes.c_int32, vp]
     lib.dg_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.dg_precond_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
     lib.dg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(dg_solve_opts), ctypes.POINTER(dg_solve_stats), vp]
     lib.dg_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.dg_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, vp]
@@ -161,7 +165,7 @@ lib = _load()
 # C-ABI symbols declared in include/dg.h (checked by the CPU test suite)
 EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadrature_points", "dg_apply_jacobian",
             "dg_apply_residual", "dg_rhs", "dg_last_error", "dg_apply_stage", "dg_precond_setup",
-            "dg_precond_apply", "dg_solve", "dg_batch_create", "dg_batch_apply", "dg_batch_tuning",
+            "dg_precond_apply", "dg_precond_info", "dg_solve", "dg_batch_create", "dg_batch_apply", "dg_batch_tuning",
             "dg_batch_destroy", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_dims", "dg_mlp_params",
             "dg_mlp_param_offsets", "dg_mlp_set_target_scale", "dg_mlp_features", "dg_mlp_forward", "dg_mlp_loss_grad",
             "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load",
@@ -384,6 +388,13 @@ class Operator:
         blocks and builds the fast-diagonalisation tables; DG_BJ_FAST_DIAG builds only the latter."""
         check(lib.dg_precond_setup(self.h, int(kind), _stream_ptr(stream)))
 
+    def precond_info(self):
+        """(bits of what dg_precond_setup built: DG_PRECOND_HAS_DENSE, _HAS_FAST_DIAG, _FAST_DIAG_REAL; the
+        number of cells with complex fast-diagonalisation tables)."""
+        v, n = ctypes.c_int32(), ctypes.c_int64()
+        check(lib.dg_precond_info(self.h, ctypes.byref(v), ctypes.byref(n)))
+        return v.value, n.value
+
     def precond_apply(self, r, z=None, stream=None):
         """z = M^{-1} r with the block-Jacobi preconditioner (dg_precond_apply)."""
         import torch
@@ -396,12 +407,14 @@ class Operator:
 
     def solve(self, x, b=None, mode=DG_SOLVE_FP64, preconditioner=DG_PRECOND_BLOCK_JACOBI, restart=30,
               outer_restart=10, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True,
-              mlp=None, fallback_ratio=0.0, mlp_placement=0, inner_block_precision=0, outer_precision=0):
+              mlp=None, fallback_ratio=0.0, mlp_placement=0, inner_block_precision=0, outer_precision=0,
+              inner_basis_precision=0):
         """Solve A x = b (b = F when None) in place on the FP64 tensor x (dg_solve); returns the stats dict.
 
         DG_SOLVE_MIXED: inner_block_precision picks the inner FP32 solve's block inverse (0 fast
         diagonalisation, 1 FP32 dense blocks, 2 scaled FP16 blocks); outer_precision picks the outer operator
-        (0 double-float with an FP64-confirmed stop, 1 FP64)."""
+        (0 double-float with an FP64-confirmed stop, 1 FP64); inner_basis_precision the storage of the inner
+        Krylov basis (0 FP32, 1 scaled FP16)."""
         import torch
         if x.dtype != torch.float64:
             raise TypeError("x must be float64")
@@ -410,7 +423,7 @@ class Operator:
             self._vec_check(b)
         o = dg_solve_opts(mode, preconditioner, restart, outer_restart, max_iterations, rtol, inner_rtol,
                           mlp.m.value if mlp is not None else None, int(mlp_placement), fallback_ratio,
-                          int(inner_block_precision), int(outer_precision))
+                          int(inner_block_precision), int(outer_precision), int(inner_basis_precision))
         st = dg_solve_stats()
         rc = lib.dg_solve(self.h, ctypes.c_void_p(b.data_ptr()) if b is not None else None,
                           ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream))

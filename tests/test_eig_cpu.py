@@ -28,10 +28,15 @@ int main() {
     for (auto& a : A) if (std::scanf("%lf", &a) != 1) return 2;
     std::vector<dge::cd> V(n * n), W(n * n), lam(n);
     const bool ok = dge::eig_general(n, A.data(), V.data(), W.data(), lam.data());
-    std::printf("%d\n", ok ? 1 : 0);
+    std::vector<double> Vr(n * n), Wr(n * n), lr(n);
+    const bool real = ok && dge::real_decomposition(n, V.data(), lam.data(), Vr.data(), Wr.data(), lr.data());
+    std::printf("%d %d\n", ok ? 1 : 0, real ? 1 : 0);
     for (int i = 0; i < n; ++i) std::printf("%.17g %.17g\n", lam[i].real(), lam[i].imag());
     for (int i = 0; i < n * n; ++i) std::printf("%.17g %.17g\n", V[i].real(), V[i].imag());
     for (int i = 0; i < n * n; ++i) std::printf("%.17g %.17g\n", W[i].real(), W[i].imag());
+    for (int i = 0; i < n; ++i) std::printf("%.17g\n", real ? lr[i] : 0.0);
+    for (int i = 0; i < n * n; ++i) std::printf("%.17g\n", real ? Vr[i] : 0.0);
+    for (int i = 0; i < n * n; ++i) std::printf("%.17g\n", real ? Wr[i] : 0.0);
   }
   return 0;
 }
@@ -68,16 +73,19 @@ def run(driver, mats):
         inp.append(str(A.shape[0]))
         inp.append(" ".join(repr(float(v)) for v in A.ravel()))
     out = subprocess.run([driver], input="\n".join(inp), capture_output=True, text=True, check=True).stdout.split()
-    pos, res = 0, []
+    pos, res, reals = 0, [], []
     for A in mats:
         n = A.shape[0]
-        ok = int(out[pos])
-        pos += 1
+        ok, real = int(out[pos]), int(out[pos + 1])
+        pos += 2
         vals = np.array([float(x) for x in out[pos:pos + 2 * (n + 2 * n * n)]])
         pos += 2 * (n + 2 * n * n)
         c = vals[0::2] + 1j * vals[1::2]
         res.append((ok, c[:n], c[n:n + n * n].reshape(n, n), c[n + n * n:].reshape(n, n)))
-    return res
+        r = np.array([float(x) for x in out[pos:pos + n + 2 * n * n]])
+        pos += n + 2 * n * n
+        reals.append((real, r[:n], r[n:n + n * n].reshape(n, n), r[n + n * n:].reshape(n, n)))
+    return res, reals
 
 
 def test_eigen_decomposition_matches_lapack(driver):
@@ -86,7 +94,7 @@ def test_eigen_decomposition_matches_lapack(driver):
     mats += [dg_1d_operator(k, rng) for k in (1, 2, 4, 7, 10)]
     S = rng.standard_normal((9, 9))
     mats.append(S + S.T + 1e-3 * rng.standard_normal((9, 9)))  # nearly symmetric, real spectrum
-    for A, (ok, lam, V, W) in zip(mats, run(driver, mats)):
+    for A, (ok, lam, V, W) in zip(mats, run(driver, mats)[0]):
         n = A.shape[0]
         assert ok, n
         ref = np.linalg.eigvals(A)
@@ -99,3 +107,36 @@ def test_eigen_decomposition_matches_lapack(driver):
             left.pop(j)
         assert np.max(np.abs(A @ V - V * lam[None, :])) <= 1e-11 * scale * np.max(np.abs(V))
         assert np.max(np.abs(V @ W - np.eye(n))) <= 1e-9
+
+
+def test_real_decomposition_of_real_spectra(driver):
+    """The real form of the decomposition: produced exactly when the spectrum is real (diffusion-dominated 1D DG
+    operators, symmetric matrices), with A Vr = Vr diag(lr) and Vr Wr = I to round-off; refused for matrices
+    with complex pairs (a rotation, a convection-dominated operator)."""
+    rng = np.random.default_rng(4)
+    real_mats = [dg_1d_operator(k, rng) for k in (1, 3, 5, 7)]
+    S = rng.standard_normal((6, 6))
+    real_mats.append(S + S.T)
+    T = np.triu(rng.standard_normal((5, 5)), 1) + np.diag([1.0, 2.0, 3.0, 4.0, 5.0])
+    real_mats.append(T)  # distinct real eigenvalues, non-normal
+    rot = np.array([[0.0, -1.0], [1.0, 0.0]])
+    from tests import kron_reference as kr
+    mt = kr.matrices_1d(5)
+    conv = 1.0 * mt["S"] - 400.0 * mt["C"] + 50.0 * np.outer(mt["e1"], mt["e1"])  # convection-dominated
+    skew = np.eye(7) + np.diag(np.ones(6), 1) - np.diag(np.ones(6), -1)  # I + skew-symmetric: 1 +- i t pairs
+    complex_mats = [rot, skew, conv]
+    mats = real_mats + complex_mats
+    res, reals = run(driver, mats)
+    for i, A in enumerate(mats):
+        ok, lam = res[i][0], res[i][1]
+        real, lr, Vr, Wr = reals[i]
+        assert ok
+        has_complex = np.max(np.abs(lam.imag)) > 1e-13 * np.max(np.abs(lam))
+        assert real == (0 if has_complex else 1), (i, lam)
+        if real:
+            scale = np.max(np.abs(lr))
+            assert np.max(np.abs(A @ Vr - Vr * lr[None, :])) <= 1e-11 * scale * np.max(np.abs(Vr))
+            assert np.max(np.abs(Vr @ Wr - np.eye(A.shape[0]))) <= 1e-9
+            assert np.allclose(np.linalg.norm(Vr, axis=0), 1.0, atol=1e-14)
+            assert np.allclose(np.sort(lr), np.sort(np.linalg.eigvals(A).real), rtol=1e-9, atol=1e-9 * scale)
+    assert sum(r[0] for r in reals) == len(real_mats)

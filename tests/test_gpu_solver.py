@@ -91,7 +91,31 @@ def test_fgmres_solution_matches_dense_solve(dg, mode):
     op.close()
 
 
-def test_mixed_and_fp64_solutions_agree(dg):
+@pytest.mark.parametrize("n,k,basis", [((3, 2, 2), 3, 1), ((3, 2, 2), 2, 1)])
+def test_fp16_inner_basis_solution_matches_dense_solve(dg, n, k, basis):
+    """The inner Krylov basis stored in scaled FP16 (768 unknowns, a multiple of 8); with 324 unknowns the
+    option falls back to the FP32 basis.  Same bounds as the FP32-basis solves."""
+    w = inputs.small_case(n=n, k=k, seed=18, b=(1.0, 0.5, 0.25), f_kind="sines")
+    w.f_params = inputs.sine_modes(10)
+    pr = oracle_problem(w)
+    A = oracle_matrix(pr)
+    F = oracle.rhs(pr, inputs.f_at(w, oracle.volume_points(pr)), None)
+    x_ref = np.linalg.solve(A, F)
+    op = dg.operator_for(w)
+    op.precond_setup()
+    for outer in (0, 1):
+        x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+        st = op.solve(x, mode=dg.DG_SOLVE_MIXED, rtol=1e-12, restart=20, outer_restart=8, inner_rtol=1e-2,
+                      outer_precision=outer, inner_basis_precision=basis)
+        assert st["rc"] == 0 and st["rel_residual"] <= 1e-12
+        xs = x.cpu().numpy()
+        assert np.max(np.abs(xs - x_ref)) <= 1e-9 * np.max(np.abs(x_ref)), st
+        assert np.linalg.norm(A @ xs - F) <= 1e-11 * np.linalg.norm(F)
+    op.close()
+
+
+@pytest.mark.parametrize("basis", [0, 1])
+def test_mixed_and_fp64_solutions_agree(dg, basis):
     w = inputs.small_case(n=(4, 4, 4), k=3, seed=12, f_kind="sines")
     w.f_params = inputs.sine_modes(13)
     op = dg.operator_for(w)
@@ -99,7 +123,7 @@ def test_mixed_and_fp64_solutions_agree(dg):
     x64 = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
     xmx = torch.zeros_like(x64)
     s1 = op.solve(x64, mode=dg.DG_SOLVE_FP64, rtol=1e-13)
-    s2 = op.solve(xmx, mode=dg.DG_SOLVE_MIXED, rtol=1e-13, inner_rtol=1e-3)
+    s2 = op.solve(xmx, mode=dg.DG_SOLVE_MIXED, rtol=1e-13, inner_rtol=1e-3, inner_basis_precision=basis)
     diff = (torch.max(torch.abs(x64 - xmx)) / torch.max(torch.abs(x64))).item()
     assert diff <= 1e-10, (diff, s1, s2)
     op.close()
@@ -115,6 +139,8 @@ def test_solver_errors(dg):
         op.solve(x, preconditioner=dg.DG_PRECOND_NONE, restart=100)
     with pytest.raises(dg.DGError):  # outer operator precision is 0 (double-float) or 1 (FP64)
         op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_NONE, outer_precision=2)
+    with pytest.raises(dg.DGError):  # inner basis storage is 0 (FP32) or 1 (FP16)
+        op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_NONE, inner_basis_precision=2)
     st = op.solve(x, preconditioner=dg.DG_PRECOND_NONE, max_iterations=2, rtol=1e-14, raise_on_error=False)
     assert st["rc"] == -4 and st["status"] == -4  # DG_ERR_NOT_CONVERGED
     op.close()
@@ -149,6 +175,49 @@ def test_fast_diagonalisation_equals_dense_block_inverse(dg, case):
     op2.precond_setup(dg.DG_BJ_FAST_DIAG)
     z64f = op2.precond_apply(r).cpu().numpy()
     assert np.max(np.abs(z64f - z64)) <= 1e-10 * np.max(np.abs(z64))
+    op.close()
+    op2.close()
+
+
+@pytest.mark.parametrize("regime,k", [("diffusion", 5), ("diffusion", 7), ("diffusion", 2), ("convection", 5),
+                                      ("convection", 3), ("mixed", 5), ("mixed", 3), ("mixed", 7)])
+def test_fast_diagonalisation_real_and_complex_tables(dg, regime, k):
+    """Diffusion-dominated cells have real 1D spectra: their tables are real (the real plane kernel at n <= 8 in
+    FP32, one thread per line otherwise and in FP64).  Strong convection (|b| h / D of order 1000) gives complex
+    pairs: complex tables.  "mixed" alternates D = 100 and D = 0.01 between cells, so both groups run, each through
+    its list of cells.  Either way the application equals the dense FP64 block inverse."""
+    conv = regime != "diffusion"
+    w = inputs.small_case(n=(3, 2, 2), k=k, seed=90 + k, b=(40.0, -30.0, 20.0) if conv else (1.0, 0.5, 0.25), c=0.5)
+    if regime == "mixed":
+        D = np.where(np.arange(w.ncell) % 2 == 0, 100.0, 0.01)
+    else:
+        D = w.D * (0.02 if conv else 1.0)
+    op = dg.Operator(w.n, w.k, D, b=w.b, c=w.c)
+    op.precond_setup()
+    info, ncx = op.precond_info()
+    assert info & dg.DG_PRECOND_HAS_DENSE and info & dg.DG_PRECOND_HAS_FAST_DIAG
+    assert bool(info & dg.DG_PRECOND_FAST_DIAG_REAL) == (not conv), info
+    assert (ncx > 0) == conv and ncx <= w.ncell
+    if regime == "mixed":
+        assert 0 < ncx < w.ncell, ncx
+    r = torch.tensor(np.random.default_rng(91 + k).uniform(-1, 1, w.ndof), device="cuda")
+    z64 = op.precond_apply(r).cpu().numpy()
+    z32 = op.precond_apply(r.float()).cpu().numpy()
+    # FP32 rounding is amplified by the conditioning of the eigenvector matrices, which grows with the
+    # non-normality of convection-dominated 1D operators: 1e-4 of the cell group's largest entry for real cells,
+    # 1e-2 for complex ones (a flexible outer method absorbs it like any inexact preconditioner)
+    nb = w.nb
+    cells = np.arange(w.ncell)
+    groups = [(cells % 2 == 0, 1e-4), (cells % 2 == 1, 1e-2)] if regime == "mixed" else \
+        [(cells >= 0, 1e-2 if conv else 1e-4)]
+    for sel, tol in groups:
+        m = np.repeat(sel, nb)
+        assert np.max(np.abs(z32[m] - z64[m])) <= tol * np.max(np.abs(z64[m])), (regime, tol)
+    op2 = dg.Operator(w.n, w.k, D, b=w.b, c=w.c)
+    op2.precond_setup(dg.DG_BJ_FAST_DIAG)
+    assert op2.precond_info() == (info & ~dg.DG_PRECOND_HAS_DENSE, ncx)
+    z64f = op2.precond_apply(r).cpu().numpy()
+    assert np.max(np.abs(z64f - z64)) <= (1e-9 if conv else 1e-10) * np.max(np.abs(z64))
     op.close()
     op2.close()
 
