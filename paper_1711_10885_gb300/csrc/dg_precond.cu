@@ -538,44 +538,96 @@ __global__ void __launch_bounds__(128, 4) fdm_apply_planes(const float2* __restr
 }
 
 // ---------------------------------------------------------------------------------------------
-// The same inverse with real tables: when every 1D cell operator has real eigenvalues (diffusion-dominated
+// The same inverse with real tables: when a cell's 1D operators have real eigenvalues (diffusion-dominated
 // cells, the usual case: the convection term is a small skew perturbation of the symmetric stiffness and
-// penalty terms) V_r, W_r and lambda_r are real, the table per cell holds 3 (2 n^2 + n) + 1 reals in the layout
-// above, and each 1D contraction is a real n x n product (a quarter of the complex one's FMAs).
+// penalty terms) V_r, W_r and lambda_r are real, and each 1D contraction is a real n x n product (a quarter of
+// the complex one's FMAs).  Table per cell (RealLay): for r = 0..2 at r * AXP: W_r [n][n], V_r [n][n],
+// lambda_r [n], zero padding to a multiple of 4 entries; c |T| at 3 AXP; TP entries in all (a multiple of 4, so
+// every cell's table, and for even n every matrix, starts on a 16-byte boundary in FP32).
 // ---------------------------------------------------------------------------------------------
+template <int N>
+struct RealLay {
+  static constexpr int NN = N * N;
+  static constexpr int AXP = (2 * NN + N + 3) / 4 * 4;
+  static constexpr int TP = 3 * AXP + 4;
+};
 
-// FP32, n <= 8: n threads per cell owning planes (as fdm_apply_planes), the pass matrix in registers (n^2 floats).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// FP32, n <= 8: n threads per cell.  Thread p holds plane c = p in registers for the x and y passes and the
+// z-lines (a, b = p) for the z pass, so the data crosses shared memory once per phase (three phases, two
+// barriers), and each pass matrix is read once per thread (float4 rows for even n).  Cell data pitch UP and
+// table pitch TP are multiples of 4 words: the 16-byte plane loads of the n threads of a cell and of
+// neighbouring cells fall on distinct bank groups.
 template <int N>
 struct FdmPlanesR {
   static constexpr int NN = N * N, N3 = NN * N;
-  static constexpr int PP = NN | 1;                 // pitch of a plane c (words; odd)
-  static constexpr int CP = N * PP;                 // pitch of a cell's data
-  static constexpr int TS = 3 * (2 * NN + N) + 1;   // table entries per cell
-  static constexpr int TSP = TS | 1;                // their pitch in shared memory
-  static constexpr int CB = 128 / N;                // cells per CTA
-  static constexpr int SMEM = CB * (CP + TSP) * 4;
+  static constexpr bool V4 = NN % 4 == 0;  // planes and matrices in 16-byte rows (even n)
+  // cell pitch: a multiple of 4 words for the 16-byte rows, else odd (scalar accesses of neighbouring cells on
+  // distinct banks)
+  static constexpr int UP = V4 ? (N3 + 3) / 4 * 4 : (N3 | 1);
+  static constexpr int TP = RealLay<N>::TP;
+  static constexpr int CB = 128 / N;                  // cells per CTA
+  static constexpr int TOFF = (CB * UP + 3) / 4 * 4;  // the tables start on a 16-byte boundary
+  static constexpr int SMEM = (TOFF + CB * TP) * 4;
 };
 
-template <int N>
-__device__ __forceinline__ void fdm_matrix_r(float (&m)[N][N], const float* M) {
+// n x n matrix (row-major) from shared memory into registers
+template <int N, bool V4>
+__device__ __forceinline__ void fdm_load_r(float* m, const float* M) {
+  if constexpr (V4) {
 #pragma unroll
-  for (int i = 0; i < N; ++i)
+    for (int q = 0; q < N * N / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(M)[q];
+      m[4 * q] = v.x, m[4 * q + 1] = v.y, m[4 * q + 2] = v.z, m[4 * q + 3] = v.w;
+    }
+  } else {
 #pragma unroll
-    for (int l = 0; l < N; ++l) m[i][l] = M[i * N + l];
+    for (int q = 0; q < N * N; ++q) m[q] = M[q];
+  }
 }
 
-// u[base + i * stride] <- sum_l m[i][l] u[base + l * stride]
+// v[o + s i] <- sum_l m[i][l] v[o + s l], i < n (registers: o and s are compile-time after unrolling)
 template <int N>
-__device__ __forceinline__ void fdm_line_r(const float (&m)[N][N], float* u, int base, int stride) {
+__device__ __forceinline__ void fdm_reg_line(const float* m, float* v, int o, int s) {
   float x[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) x[l] = u[base + l * stride];
+  for (int l = 0; l < N; ++l) x[l] = v[o + s * l];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     float y = 0.f;
 #pragma unroll
-    for (int l = 0; l < N; ++l) y = fmaf(m[i][l], x[l], y);
-    u[base + i * stride] = y;
+    for (int l = 0; l < N; ++l) y = fmaf(m[i * N + l], x[l], y);
+    v[o + s * i] = y;
+  }
+}
+
+// plane c of a cell (u[a + n b] at c n^2) into / out of registers pl[a + n b]
+template <int N, bool V4>
+__device__ __forceinline__ void plane_in(float* pl, const float* u) {
+  if constexpr (V4) {
+#pragma unroll
+    for (int q = 0; q < N * N / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(u)[q];
+      pl[4 * q] = v.x, pl[4 * q + 1] = v.y, pl[4 * q + 2] = v.z, pl[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) pl[q] = u[q];
+  }
+}
+template <int N, bool V4>
+__device__ __forceinline__ void plane_out(const float* pl, float* u) {
+  if constexpr (V4) {
+#pragma unroll
+    for (int q = 0; q < N * N / 4; ++q)
+      reinterpret_cast<float4*>(u)[q] = make_float4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N * N; ++q) u[q] = pl[q];
   }
 }
 
@@ -585,62 +637,92 @@ __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(c
                                                                                float* __restrict__ z, int64_t count,
                                                                                const int64_t* __restrict__ cells) {
   using P = FdmPlanesR<N>;
-  constexpr int NN = P::NN, N3 = P::N3, PP = P::PP, CP = P::CP, TS = P::TS, TSP = P::TSP, AX = 2 * NN + N;
+  constexpr int NN = P::NN, N3 = P::N3, UP = P::UP, TP = P::TP, AXP = RealLay<N>::AXP;
+  constexpr bool V4 = P::V4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int64_t s_cell[P::CB];
-  float* U = reinterpret_cast<float*>(smem_raw);  // [CB][CP]: U[cell][c * PP + a + N b]
-  float* T = U + P::CB * CP;                       // [CB][TSP]
+  float* U = reinterpret_cast<float*>(smem_raw);  // [CB][UP]: U[cell][a + n b + n^2 c]
+  float* T = U + P::TOFF;                          // [CB][TP]
   const int64_t q0 = (int64_t)blockIdx.x * P::CB;
   const int here = (int)min((int64_t)P::CB, count - q0);
   load_cells(s_cell, cells, q0, here);
-  for (int e = threadIdx.x; e < here * TS; e += blockDim.x) {
-    const int l = e / TS;
-    cp_async(T + l * TSP + (e - l * TS), tab + q0 * TS + e, 0);
-  }
+  for (int e = threadIdx.x; e < here * (TP / 4); e += blockDim.x)  // tables: contiguous in group order
+    cp_async16(T + 4 * e, tab + q0 * TP + 4 * e);
   __syncthreads();
-  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
-    const int l = e / N3, rem = e - l * N3, c = rem / NN;
-    cp_async(U + l * CP + c * PP + (rem - c * NN), r + s_cell[l] * N3 + rem, 0);
+  if constexpr (N3 % 4 == 0) {
+    for (int e = threadIdx.x; e < here * (N3 / 4); e += blockDim.x) {
+      const int l = e / (N3 / 4), q = e - l * (N3 / 4);
+      cp_async16(U + l * UP + 4 * q, r + s_cell[l] * N3 + 4 * q);
+    }
+  } else {
+    for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+      const int l = e / N3, q = e - l * N3;
+      cp_async(U + l * UP + q, r + s_cell[l] * N3 + q, 0);
+    }
   }
   cp_async_wait_all();
   __syncthreads();
   const int lc = threadIdx.x / N, p = threadIdx.x - lc * N;
   const bool active = lc < here;
-  float* u = U + lc * CP;
-  const float* tb = T + lc * TSP;
-  float m[N][N];
-  if (active) {  // W_x on the x-lines (b, c = p), W_y on the y-lines (a, c = p)
-    fdm_matrix_r<N>(m, tb);
-    for (int b = 0; b < N; ++b) fdm_line_r<N>(m, u, p * PP + N * b, 1);
-    fdm_matrix_r<N>(m, tb + AX);
-    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, p * PP + a, N);
-  }
-  __syncthreads();
-  if (active) {  // W_z on the z-lines (a, b = p); divide by lambda_x(a) + lambda_y(p) + lambda_z(c) + c |T|; V_z
-    fdm_matrix_r<N>(m, tb + 2 * AX);
-    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, a + N * p, PP);
-    const float* lx = tb + 2 * NN;
-    const float lyc = tb[AX + 2 * NN + p] + tb[TS - 1];
-    const float* lz = tb + 2 * AX + 2 * NN;
-    for (int a = 0; a < N; ++a) {
-      const float la = lx[a] + lyc;
+  float* u = U + lc * UP;
+  const float* tb = T + lc * TP;
+  float m[NN], v[NN];
+  if (active) {  // plane c = p: W_x on its x-lines, W_y on its y-lines
+    plane_in<N, V4>(v, u + p * NN);
+    fdm_load_r<N, V4>(m, tb);
 #pragma unroll
-      for (int c = 0; c < N; ++c) u[a + N * p + PP * c] /= la + lz[c];
+    for (int b = 0; b < N; ++b) fdm_reg_line<N>(m, v, N * b, 1);
+    fdm_load_r<N, V4>(m, tb + AXP);
+#pragma unroll
+    for (int a = 0; a < N; ++a) fdm_reg_line<N>(m, v, a, N);
+    plane_out<N, V4>(v, u + p * NN);
+  }
+  __syncthreads();
+  if (active) {  // z-lines (a, b = p): W_z, divide by lambda_x(a) + lambda_y(p) + lambda_z(c) + c |T|, V_z
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a + N * c] = u[a + N * p + NN * c];
+    fdm_load_r<N, V4>(m, tb + 2 * AXP);
+#pragma unroll
+    for (int a = 0; a < N; ++a) fdm_reg_line<N>(m, v, a, N);
+    const float lyc = tb[AXP + 2 * NN + p] + tb[3 * AXP];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      const float lzc = tb[2 * AXP + 2 * NN + c] + lyc;
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a + N * c] /= tb[2 * NN + a] + lzc;
     }
-    fdm_matrix_r<N>(m, tb + 2 * AX + NN);
-    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, a + N * p, PP);
+    fdm_load_r<N, V4>(m, tb + 2 * AXP + NN);
+#pragma unroll
+    for (int a = 0; a < N; ++a) fdm_reg_line<N>(m, v, a, N);
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+      for (int a = 0; a < N; ++a) u[a + N * p + NN * c] = v[a + N * c];
   }
   __syncthreads();
-  if (active) {  // V_y on the y-lines, V_x on the x-lines
-    fdm_matrix_r<N>(m, tb + AX + NN);
-    for (int a = 0; a < N; ++a) fdm_line_r<N>(m, u, p * PP + a, N);
-    fdm_matrix_r<N>(m, tb + NN);
-    for (int b = 0; b < N; ++b) fdm_line_r<N>(m, u, p * PP + N * b, 1);
+  if (active) {  // plane c = p: V_y, V_x
+    plane_in<N, V4>(v, u + p * NN);
+    fdm_load_r<N, V4>(m, tb + AXP + NN);
+#pragma unroll
+    for (int a = 0; a < N; ++a) fdm_reg_line<N>(m, v, a, N);
+    fdm_load_r<N, V4>(m, tb + NN);
+#pragma unroll
+    for (int b = 0; b < N; ++b) fdm_reg_line<N>(m, v, N * b, 1);
+    plane_out<N, V4>(v, u + p * NN);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
-    const int l = e / N3, rem = e - l * N3, c = rem / NN;
-    z[s_cell[l] * N3 + rem] = U[l * CP + c * PP + (rem - c * NN)];
+  if constexpr (N3 % 4 == 0) {
+    for (int e = threadIdx.x; e < here * (N3 / 4); e += blockDim.x) {
+      const int l = e / (N3 / 4), q = e - l * (N3 / 4);
+      reinterpret_cast<float4*>(z + s_cell[l] * N3)[q] = reinterpret_cast<const float4*>(U + l * UP)[q];
+    }
+  } else {
+    for (int e = threadIdx.x; e < here * N3; e += blockDim.x) {
+      const int l = e / N3, q = e - l * N3;
+      z[s_cell[l] * N3 + q] = U[l * UP + q];
+    }
   }
 }
 
@@ -649,7 +731,7 @@ template <int N, typename R>
 __global__ void __launch_bounds__(256) fdm_apply_real(const R* __restrict__ tab, const R* __restrict__ r,
                                                       R* __restrict__ z, int64_t count,
                                                       const int64_t* __restrict__ cells, int cpb) {
-  constexpr int NN = N * N, N3 = NN * N, TS = 3 * (2 * NN + N) + 1, AX = 2 * NN + N;
+  constexpr int NN = N * N, N3 = NN * N, TS = RealLay<N>::TP, AX = RealLay<N>::AXP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int64_t s_cell[64];
   R* U = reinterpret_cast<R*>(smem_raw);  // [cpb][N3]
@@ -689,7 +771,7 @@ __global__ void __launch_bounds__(256) fdm_apply_real(const R* __restrict__ tab,
   for (int d = 0; d < 3; ++d) pass(d, tb + d * AX);  // W_d
   if (active) {
     const int a = t % N, b = t / N;
-    const R lab = tb[2 * NN + a] + tb[AX + 2 * NN + b] + tb[TS - 1];
+    const R lab = tb[2 * NN + a] + tb[AX + 2 * NN + b] + tb[3 * AX];
 #pragma unroll
     for (int c = 0; c < N; ++c) u[a + N * b + NN * c] /= lab + tb[2 * AX + 2 * NN + c];
   }
@@ -823,9 +905,11 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<dou
 template <typename R>
 int fdm_group_real(const dg_handle* h, const R* tab, const int64_t* cells, int64_t count, const R* r, R* z,
                    cudaStream_t s) {
-  const int N = h->N, NN = N * N, cpb = std::max(1, 256 / NN), TS = 3 * (2 * NN + N) + 1;
+  const int N = h->N, NN = N * N, cpb = std::max(1, 256 / NN), TS = 3 * ((2 * NN + N + 3) / 4 * 4) + 4;
+  // the plane kernel moves r and z in 16-byte pieces for even n: other vectors take the line kernel
+  const bool aligned = N % 2 == 1 || (reinterpret_cast<uintptr_t>(r) % 16 == 0 && reinterpret_cast<uintptr_t>(z) % 16 == 0);
   if constexpr (sizeof(R) == 4) {
-    if (N <= 8) {
+    if (N <= 8 && aligned) {
       switch (N) {
 #define FDMR(NV)                                                                                          \
   case NV: {                                                                                              \
@@ -1013,20 +1097,24 @@ int setup_fdm(dg_handle* h) {
     set_error("dg_precond_setup: a 1D cell operator could not be diagonalised");
     return DG_ERR_NAN;
   }
-  const int N = h->N, TS = 3 * (2 * N * N + N) + 1;
+  const int N = h->N, NN = N * N, AX = 2 * NN + N, TS = 3 * AX + 1;
+  const int AXP = (AX + 3) / 4 * 4, TP = 3 * AXP + 4;  // the padded layout of the real kernels
   std::vector<int64_t> re_cells, cx_cells;
   for (int64_t c = 0; c < h->ncell; ++c) (is_real[c] ? re_cells : cx_cells).push_back(c);
   const int64_t nre = (int64_t)re_cells.size(), ncx = (int64_t)cx_cells.size();
-  // group tables in group order
-  std::vector<double> re64((size_t)nre * TS);
-  std::vector<float> re32((size_t)nre * TS);
+  // group tables in group order; real ones with each axis block (W, V, lambda) padded to AXP entries
+  std::vector<double> re64((size_t)nre * TP, 0.0);
+  std::vector<float> re32((size_t)nre * TP, 0.f);
+  for (int64_t q = 0; q < nre; ++q) {
+    const double* src = &real[(size_t)re_cells[q] * TS];
+    double* dst = &re64[(size_t)q * TP];
+    for (int ax = 0; ax < 3; ++ax)
+      for (int i = 0; i < AX; ++i) dst[ax * AXP + i] = src[ax * AX + i];
+    dst[3 * AXP] = src[TS - 1];
+    for (int i = 0; i < TP; ++i) re32[(size_t)q * TP + i] = (float)dst[i];
+  }
   std::vector<double2> cx64((size_t)ncx * TS);
   std::vector<float2> cx32((size_t)ncx * TS);
-  for (int64_t q = 0; q < nre; ++q)
-    for (int i = 0; i < TS; ++i) {
-      re64[(size_t)q * TS + i] = real[(size_t)re_cells[q] * TS + i];
-      re32[(size_t)q * TS + i] = (float)real[(size_t)re_cells[q] * TS + i];
-    }
   for (int64_t q = 0; q < ncx; ++q)
     for (int i = 0; i < TS; ++i) {
       const double2 v = tab[(size_t)cx_cells[q] * TS + i];
