@@ -167,7 +167,7 @@ typedef struct {
   int32_t preconditioner; /* DG_PRECOND_NONE or DG_PRECOND_BLOCK_JACOBI (FP64 blocks in FP64 mode, FP32
                              blocks inside the FP32 inner solve); needs dg_precond_setup first        */
   int32_t restart;        /* FGMRES restart length (inner length in MIXED mode), 1..60, 0 = 30        */
-  int32_t outer_restart;  /* MIXED: outer restart length, 1..60, 0 = 10                               */
+  int32_t outer_restart;  /* MIXED: outer restart length, 1..60, 0 = 20                               */
   int32_t max_iterations; /* cap on (outer) iterations, 0 = 10000                                      */
   double rtol;            /* stop when ||b - A x||_2 <= rtol ||b||_2, checked on the FP64 residual     */
   double inner_rtol;      /* MIXED: relative residual reduction of each inner solve, in (0, 1)         */

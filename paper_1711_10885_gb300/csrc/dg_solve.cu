@@ -415,7 +415,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     return DG_ERR_INVALID_ARG;
   }
   const int m = o->restart > 0 ? o->restart : 30;
-  const int mo = o->outer_restart > 0 ? o->outer_restart : 10;
+  const int mo = o->outer_restart > 0 ? o->outer_restart : 20;
   if (m > 60 || mo > 60 || (o->mode != DG_SOLVE_FP64 && o->mode != DG_SOLVE_MIXED) ||
       (o->inner_block_precision < 0 || o->inner_block_precision > 2) ||
       (o->outer_precision < 0 || o->outer_precision > 1) ||

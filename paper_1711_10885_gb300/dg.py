@@ -406,7 +406,7 @@ class Operator:
         return z
 
     def solve(self, x, b=None, mode=DG_SOLVE_FP64, preconditioner=DG_PRECOND_BLOCK_JACOBI, restart=30,
-              outer_restart=10, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True,
+              outer_restart=20, max_iterations=0, rtol=1e-10, inner_rtol=1e-3, stream=None, raise_on_error=True,
               mlp=None, fallback_ratio=0.0, mlp_placement=0, inner_block_precision=0, outer_precision=0,
               inner_basis_precision=0):
         """Solve A x = b (b = F when None) in place on the FP64 tensor x (dg_solve); returns the stats dict.
