@@ -192,7 +192,7 @@ def run_profile_solver(args):
     """Minimal launch sequence for profilers of the solver kernels: at 48^3 Q5 (fast diagonalisation only, under
     1 GB on the device) W + K FP32 and FP64 block-Jacobi applications and learned-preconditioner applications
     (untrained network); then one outer iteration of the mixed solve (one inner FGMRES(30) cycle) at 32^3 Q5 for
-    the basis passes (about 3 GB)."""
+    the basis passes (about 3 GB), and one inner FGMRES(20) cycle with the FP16 basis at 48^3 Q5 (about 4 GB)."""
     import torch
 
     from paper_1711_10885_gb300 import dg, inputs
@@ -231,8 +231,17 @@ def run_profile_solver(args):
     st = ops.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=1e-10, restart=30,
                    outer_restart=20, inner_rtol=1e-3, max_iterations=1, raise_on_error=False)
     ops.close()
+    del x
+    # one inner FGMRES(20) cycle with the FP16 basis at 48^3 Q5 (outer restart 1: about 4 GB on the device)
+    op = dg.operator_for(w)
+    op.precond_setup(dg.DG_BJ_FAST_DIAG)
+    x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    st48 = op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=1e-10, restart=20,
+                    outer_restart=1, inner_rtol=1e-3, max_iterations=1, inner_basis_precision=1, raise_on_error=False)
+    op.close()
     print(json.dumps({"profile": "solver", "mlp_apply_ms": ms, "mlp_tflops": flops / (ms * 1e-3) / 1e12,
-                      "cells": w.ncell, "solve_32": {k: st[k] for k in ("iterations", "inner_iterations")}}))
+                      "cells": w.ncell, "solve_32": {k: st[k] for k in ("iterations", "inner_iterations")},
+                      "solve_48_fp16_basis": {k: st48[k] for k in ("iterations", "inner_iterations")}}))
 
 
 def run_profile(args):
@@ -453,6 +462,28 @@ def _timed_solve(op, n, clock_dev=0, **kw):
     return st, x
 
 
+def _precond_timing(op, n, reps=20):
+    """The block inverse of a set-up handle: what was built (dg_precond_info) and the FP32 and FP64 application
+    times (CUDA events on the current stream, after three warm-ups)."""
+    import torch
+
+    info, ncx = op.precond_info()
+    out = {"info": info, "complex_cells": ncx}
+    r = torch.rand(n, dtype=torch.float32, device="cuda") - 0.5
+    for name, v in (("fp32_us", r), ("fp64_us", r.double())):
+        z = torch.empty_like(v)
+        for _ in range(3):
+            op.precond_apply(v, z)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            op.precond_apply(v, z)
+        b.record()
+        b.synchronize()
+        out[name] = a.elapsed_time(b) / reps * 1e3
+    return out
+
+
 def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     """The solve half of the headline metric, in the default line (one GPU):
 
@@ -480,7 +511,8 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     torch.cuda.synchronize()
     q5 = {"workload": "unit_cube_q5_48", "dofs": w.ndof, "rtol": 1e-10, "operator_setup_s": t1 - t0,
           "precond_setup_s": time.perf_counter() - t1,
-          "precond": "block-Jacobi, exact block inverse by fast diagonalisation (FP32 inner, FP64 outer / plain)"}
+          "precond": "block-Jacobi, exact block inverse by fast diagonalisation (FP32 inner, FP64 outer / plain)",
+          "block_inverse": _precond_timing(op, w.ndof)}
     xs = {}
     # each outer operator with the inner Krylov basis stored in FP32 (the default) and in scaled FP16
     mixed = (("mixed_fp64_outer", 1, 0), ("mixed_df_outer", 0, 0), ("mixed_fp64_outer_fp16_basis", 1, 1),
@@ -525,7 +557,7 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     op.precond_setup(dg.DG_BJ_FAST_DIAG)
     torch.cuda.synchronize()
     q4 = {"workload": "64^3 Q4, D log-normal sigma 1.5 (seed 20)", "dofs": ev.ndof, "rtol": 1e-8, "mlp": info,
-          "setup_s": time.perf_counter() - t0}
+          "setup_s": time.perf_counter() - t0, "block_inverse": _precond_timing(op, ev.ndof)}
     common = dict(rtol=1e-8, inner_rtol=1e-2, mlp=mlp)
     q4["mixed_bj"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
                                      preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, **common)
@@ -545,6 +577,33 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     mlp.close()
     op.close()
     out["q4_64"] = q4
+    return out
+
+
+def restart_sweep():
+    """Outer restart length of the mixed solve (double-float outer operator, inner FGMRES(30) with the FP16 basis):
+    48^3 Q5 to 1e-10 for 10, 20, 30, 60 and 64^3 Q4 (sigma 1.5) to 1e-8 for 10, 20, 30; and the plain FP64
+    FGMRES(60) at 48^3 Q5 (the reference solve of the bench uses FGMRES(30))."""
+    from paper_1711_10885_gb300 import dg, inputs
+    out = {}
+    cases = (("q5_48", inputs.unit_cube_q5_48(with_u=False), 1e-10, 1e-3, (10, 20, 30, 60)),
+             ("q4_64", inputs.Workload("eval", (64, 64, 64), 4, inputs.log_normal_D(64 ** 3, 1.5, 20)), 1e-8, 1e-2,
+              (10, 20, 30)))
+    for name, w, rtol, itol, restarts in cases:
+        op = dg.operator_for(w)
+        op.precond_setup(dg.DG_BJ_FAST_DIAG)
+        out[name] = {}
+        for mo in restarts:
+            st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
+                                 rtol=rtol, inner_rtol=itol, restart=30, outer_restart=mo, inner_basis_precision=1)
+            out[name][str(mo)] = {k: st[k] for k in ("iterations", "inner_iterations", "rel_residual", "wall_s",
+                                                     "converged")}
+            out[name][str(mo)]["sm_mhz"] = st["clocks"].get("sm_mhz")
+        if name == "q5_48":  # the plain FP64 reference with a restart of 60 instead of 30
+            st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
+                                 rtol=rtol, restart=60, max_iterations=6000)
+            out[name]["fp64_restart_60"] = {k: st[k] for k in ("iterations", "rel_residual", "wall_s", "converged")}
+        op.close()
     return out
 
 
@@ -1364,6 +1423,9 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the solve comparisons of the default line")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner part of them")
     ap.add_argument("--solve-section", action="store_true", help="print only the default line's solve section")
+    ap.add_argument("--restart-sweep", action="store_true",
+                    help="print only the mixed solves (double-float outer operator, FP16 inner basis) at 48^3 Q5 and "
+                         "64^3 Q4 for several outer restart lengths")
     ap.add_argument("--peaks", action="store_true", help="print only the arithmetic throughput probes")
     ap.add_argument("--f32", action="store_true", help="with --profile: W + K FP32 applies at 48^3 Q5")
     ap.add_argument("--f32-degrees", action="store_true", help="print only the FP32 apply per degree")
@@ -1431,6 +1493,10 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"transport": transport_benchmark(n=args.transport, steps=args.steps,
                                                            warmup=args.warmup)}), flush=True)
+    elif args.restart_sweep:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"restart_sweep": restart_sweep()}), flush=True)
     elif args.solve_section:
         import torch
         torch.cuda.set_device(0)
