@@ -259,8 +259,9 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
  * two ReLU layers of 256 units, and an output layer of (k+1)^3 units; the correction is
  *   z_T = s * t_scale * y(x),
  * which makes the preconditioner positively homogeneous in r.  Weights are FP32 masters rounded to
- * BF16 for the forward GEMMs (tensor cores, FP32 accumulation); the backward pass and Adam run in
- * FP32.  Rows of X are BF16 [rows][kin_padded]; targets T are FP32 [rows][(k+1)^3].
+ * BF16 for the GEMMs of the forward and the backward pass (tensor cores, FP32 accumulation); bias
+ * gradients and Adam run in FP32.  Rows of X are BF16 [rows][kin_padded]; targets T are FP32
+ * [rows][(k+1)^3].
  * --------------------------------------------------------------------------------------------- */
 typedef struct {
   int32_t epochs;   /* passes over the rows                    */
