@@ -1,6 +1,7 @@
 // dg_internal.h -- host-side state of a dg_handle and the per-precision launchers.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -151,6 +152,8 @@ int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t 
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
+// z = block inverse of (scale * r) for a scaled FP16 r; tmp: n FP32 values of scratch, 16-byte aligned
+int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* tmp, cudaStream_t s);
 // F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null);
 // with vol = 1 instead of |T| and no g this is the L2 projection z_i = (f, phi_i)_T / |T|
 int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,

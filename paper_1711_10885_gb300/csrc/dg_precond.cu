@@ -4,6 +4,7 @@
 #include <cmath>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -573,6 +574,7 @@ struct FdmPlanesR {
   static constexpr int CB = 128 / N;                  // cells per CTA
   static constexpr int TOFF = (CB * UP + 3) / 4 * 4;  // the tables start on a 16-byte boundary
   static constexpr int SMEM = (TOFF + CB * TP) * 4;
+  static constexpr int SMEM_H = SMEM + CB * N3 * 2;    // plus the FP16 input staging
 };
 
 // n x n matrix (row-major) from shared memory into registers
@@ -631,25 +633,36 @@ __device__ __forceinline__ void plane_out(const float* pl, float* u) {
   }
 }
 
-template <int N>
+// TIn = __half (even n only): r is a scaled FP16 vector (r_i = in_scale * h_i), the FGMRES basis row of the FP32
+// inner solve; its cells arrive by 16-byte cp.async in a staging area RH [CB][n^3] after the tables and are
+// converted as the first phase loads its planes.
+template <int N, typename TIn>
 __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(const float* __restrict__ tab,
-                                                                               const float* __restrict__ r,
+                                                                               const TIn* __restrict__ r,
+                                                                               float in_scale,
                                                                                float* __restrict__ z, int64_t count,
                                                                                const int64_t* __restrict__ cells) {
   using P = FdmPlanesR<N>;
   constexpr int NN = P::NN, N3 = P::N3, UP = P::UP, TP = P::TP, AXP = RealLay<N>::AXP;
-  constexpr bool V4 = P::V4;
+  constexpr bool V4 = P::V4, HIN = std::is_same<TIn, __half>::value;
+  static_assert(!HIN || (N3 % 8 == 0 && NN % 4 == 0), "FP16 input: even n");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int64_t s_cell[P::CB];
   float* U = reinterpret_cast<float*>(smem_raw);  // [CB][UP]: U[cell][a + n b + n^2 c]
   float* T = U + P::TOFF;                          // [CB][TP]
+  __half* RH = reinterpret_cast<__half*>(T + P::CB * TP);  // FP16 input: [CB][N3]
   const int64_t q0 = (int64_t)blockIdx.x * P::CB;
   const int here = (int)min((int64_t)P::CB, count - q0);
   load_cells(s_cell, cells, q0, here);
   for (int e = threadIdx.x; e < here * (TP / 4); e += blockDim.x)  // tables: contiguous in group order
     cp_async16(T + 4 * e, tab + q0 * TP + 4 * e);
   __syncthreads();
-  if constexpr (N3 % 4 == 0) {
+  if constexpr (HIN) {
+    for (int e = threadIdx.x; e < here * (N3 / 8); e += blockDim.x) {
+      const int l = e / (N3 / 8), q = e - l * (N3 / 8);
+      cp_async16(RH + l * N3 + 8 * q, r + s_cell[l] * N3 + 8 * q);
+    }
+  } else if constexpr (N3 % 4 == 0) {
     for (int e = threadIdx.x; e < here * (N3 / 4); e += blockDim.x) {
       const int l = e / (N3 / 4), q = e - l * (N3 / 4);
       cp_async16(U + l * UP + 4 * q, r + s_cell[l] * N3 + 4 * q);
@@ -668,7 +681,19 @@ __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(c
   const float* tb = T + lc * TP;
   float m[NN], v[NN];
   if (active) {  // plane c = p: W_x on its x-lines, W_y on its y-lines
-    plane_in<N, V4>(v, u + p * NN);
+    if constexpr (HIN) {
+      const uint2* src = reinterpret_cast<const uint2*>(RH + lc * N3 + p * NN);  // 4 halves per 8-byte load
+#pragma unroll
+      for (int q = 0; q < NN / 4; ++q) {
+        const uint2 w = src[q];
+        const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+        const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+        v[4 * q] = f0.x * in_scale, v[4 * q + 1] = f0.y * in_scale;
+        v[4 * q + 2] = f1.x * in_scale, v[4 * q + 3] = f1.y * in_scale;
+      }
+    } else {
+      plane_in<N, V4>(v, u + p * NN);
+    }
     fdm_load_r<N, V4>(m, tb);
 #pragma unroll
     for (int b = 0; b < N; ++b) fdm_reg_line<N>(m, v, N * b, 1);
@@ -917,14 +942,14 @@ int fdm_group_real(const dg_handle* h, const R* tab, const int64_t* cells, int64
     static DeviceOnce attr;                                                                               \
     if (P::SMEM > 48 * 1024) {                                                                            \
       if (int rca = attr.run([] {                                                                         \
-            cudaError_t ea = cudaFuncSetAttribute(fdm_apply_planes_real<NV>,                              \
+            cudaError_t ea = cudaFuncSetAttribute(fdm_apply_planes_real<NV, float>,                       \
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);  \
             return ea == cudaSuccess ? 0 : cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply_planes_real)");  \
           }))                                                                                             \
         return rca;                                                                                       \
     }                                                                                                     \
-    fdm_apply_planes_real<NV><<<(unsigned)((count + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>(       \
-        tab, r, z, count, cells);                                                                         \
+    fdm_apply_planes_real<NV, float><<<(unsigned)((count + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>( \
+        tab, r, 1.f, z, count, cells);                                                                    \
     break;                                                                                                \
   }
         FDMR(2) FDMR(3) FDMR(4) FDMR(5) FDMR(6) FDMR(7) FDMR(8)
@@ -1039,6 +1064,74 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
 }
 
 int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) { return precond_fdm(h, r, z, s); }
+
+namespace {
+// dst[c n^3 + i] = scale * src[c n^3 + i] for the listed cells (FP16 -> FP32)
+__global__ void half_cells_to_float(const __half* __restrict__ src, float scale, const int64_t* __restrict__ cells,
+                                    int64_t count, int n3, float* __restrict__ dst) {
+  const int64_t total = count * n3;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / n3, i = e - q * n3, c = cells ? cells[q] : q;
+    dst[c * n3 + i] = __half2float(src[c * n3 + i]) * scale;
+  }
+}
+
+template <int N>
+int fdm_real_half(const dg_handle* h, const float* tab, const int64_t* cells, int64_t count, const __half* r,
+                  float scale, float* z, cudaStream_t s) {
+  using P = FdmPlanesR<N>;
+  static DeviceOnce attr;
+  if (P::SMEM_H > 48 * 1024)
+    if (int rca = attr.run([] {
+          cudaError_t ea = cudaFuncSetAttribute(fdm_apply_planes_real<N, __half>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM_H);
+          return ea == cudaSuccess ? 0 : cuda_fail(ea, "cudaFuncSetAttribute(fdm_apply_planes_real, FP16 input)");
+        }))
+      return rca;
+  fdm_apply_planes_real<N, __half><<<(unsigned)((count + P::CB - 1) / P::CB), P::CB * N, P::SMEM_H, s>>>(
+      tab, r, scale, z, count, cells);
+  return 0;
+}
+}  // namespace
+
+// z = A_TT^{-1} (scale * r) for a scaled FP16 vector r (the FP16 basis rows of the inner solve).  The real group
+// reads r directly (even n <= 8, 16-byte aligned r and z); the complex group and every other case first convert
+// their entries into tmp (n FP32 values, 16-byte aligned) and take the FP32 path.
+int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* tmp, cudaStream_t s) {
+  const FdmTables& f = h->fdm;
+  if (!f.built) {
+    set_error("block-Jacobi: the fast diagonalisation was not set up");
+    return DG_ERR_INVALID_ARG;
+  }
+  const int N = h->N, N3 = N * N * N;
+  const bool direct = N % 2 == 0 && N <= 8 && reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(z) % 16 == 0;
+  if (!direct) {
+    half_cells_to_float<<<sm_count() * 4, 256, 0, s>>>(r, scale, nullptr, h->ncell, N3, tmp);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "FP16 row conversion");
+    return precond_fdm(h, static_cast<const float*>(tmp), z, s);
+  }
+  if (f.nre > 0) {
+    const float* tab = static_cast<const float*>(f.re32);
+    int rc = 0;
+    switch (N) {
+      case 2: rc = fdm_real_half<2>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
+      case 4: rc = fdm_real_half<4>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
+      case 6: rc = fdm_real_half<6>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
+      default: rc = fdm_real_half<8>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
+    }
+    if (rc) return rc;
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess)
+      return cuda_fail(e, "block-Jacobi apply (fast diagonalisation, FP16 input)");
+  }
+  if (f.ncx > 0) {
+    half_cells_to_float<<<sm_count() * 4, 256, 0, s>>>(r, scale, f.cx_cells, f.ncx, N3, tmp);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "FP16 row conversion");
+    if (int rc = fdm_group_complex<float>(h, static_cast<const float2*>(f.cx32), f.cx_cells, f.ncx, tmp, z, s))
+      return rc;
+  }
+  return 0;
+}
 
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
   if (!h->bj16) return precond_fdm(h, r, z, s);

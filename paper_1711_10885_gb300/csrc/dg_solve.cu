@@ -241,12 +241,14 @@ int basis_dots(Ctx& c, const __half* V, int nv, const __half* x, double* dst) {
 // unused.  The outer solve reads every step (its steps are whole inner solves); the inner one less often.
 //
 // B = __half (T = float only): the basis V is stored in scaled FP16 and `tmp` holds two FP32 vectors, the new
-// operator product w and the FP32 copy of u_j that the preconditioner reads.
+// operator product w and the FP32 copy of u_j that the preconditioner reads; a preconditioner MB that reads
+// the FP16 row itself takes the place of that copy and of M.
 template <typename T, typename B = T>
 int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, bool x0_zero, B* V, T* Z, int m,
            double tol_abs, int maxit, int max_cycles, bool true_residual_check, Result* out,
            const std::function<void(double, double)>& cycle_hook = {},
-           const std::function<int(const T*, T*)>& M0 = {}, int check_every = 1, T* tmp = nullptr) {
+           const std::function<int(const T*, T*)>& M0 = {}, int check_every = 1, T* tmp = nullptr,
+           const std::function<int(const B*, T*)>& MB = {}) {
   constexpr bool half_basis = !std::is_same<T, B>::value;
   static_assert(!half_basis || (std::is_same<T, float>::value && std::is_same<B, __half>::value),
                 "FP16 basis storage is for the FP32 solve");
@@ -314,19 +316,26 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
     int last = steps - 1;  // the step after which the cycle's last column is finalised
     bool finalised = false;
     for (int j = 0; j < steps; ++j) {
-      const T* uj;
+      const T* uj = nullptr;
       T* w;
       T* zj = Z + (size_t)j * n;
+      bool applied = false;  // z_j formed straight from the FP16 row
       if constexpr (half_basis) {
-        dgb::h_load<<<c.red_blocks, dgb::RED_THREADS, 0, c.s>>>(V + (size_t)j * n, tmp + n, n / 8);
-        if (int rc = cuda_check(cudaGetLastError(), "basis row load")) return rc;
-        uj = tmp + n;
         w = tmp;
+        if (MB && !(j == 0 && M0)) {
+          if (int rc = MB(V + (size_t)j * n, zj)) return rc;
+          applied = true;
+        } else {
+          dgb::h_load<<<c.red_blocks, dgb::RED_THREADS, 0, c.s>>>(V + (size_t)j * n, tmp + n, n / 8);
+          if (int rc = cuda_check(cudaGetLastError(), "basis row load")) return rc;
+          uj = tmp + n;
+        }
       } else {
         uj = V + (size_t)j * n;
         w = V + (size_t)(j + 1) * n;
       }
-      if (j == 0 && M0) {
+      if (applied) {
+      } else if (j == 0 && M0) {
         if (int rc = M0(uj, zj)) return rc;
       } else if (M) {
         if (int rc = M(uj, zj)) return rc;
@@ -563,6 +572,13 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
         int e2 = bj_inner(r, z);
         return e2 ? e2 : mlp_apply_impl(mlp, h, r, z, DG_F32, 1, s);
       };
+    // with the FP16 basis and the fast-diagonalisation block inverse alone (no network), the block inverse reads
+    // the basis rows itself (the FP32 copy of u_j goes away)
+    std::function<int(const __half*, float*)> M16;
+    if (half_basis && pc && !use_mlp && o->inner_block_precision == 0 && h->fdm.built)
+      M16 = [&](const __half* r, float* z) {
+        return precond_fdm_f32_half(h, r, dgb::HB_INV, z, tmp32 + n, s);
+      };
     std::function<int(const double*, double*)> P = [&](const double* v, double* z) -> int {
       dgb::scale_copy<double, float><<<c.red_blocks, dgb::RED_THREADS, 0, s>>>(v, rhs32, 1.0, n);
       cudaMemsetAsync(e32, 0, n * sizeof(float), s);
@@ -572,7 +588,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       if (rc2) return rc2;
       const double itol = o->inner_rtol * std::sqrt(vn2);
       rc2 = half_basis ? fgmres<float, __half>(c, M32, rhs32, e32, true, V16, Z32, m, itol, m, 1, false, &ri, {}, {},
-                                               kInnerCheckEvery, tmp32)
+                                               kInnerCheckEvery, tmp32, M16)
                        : fgmres<float>(c, M32, rhs32, e32, true, V32, Z32, m, itol, m, 1, false, &ri, {}, {},
                                        kInnerCheckEvery);
       if (rc2) return rc2;

@@ -91,11 +91,18 @@ def test_fgmres_solution_matches_dense_solve(dg, mode):
     op.close()
 
 
-@pytest.mark.parametrize("n,k,basis", [((3, 2, 2), 3, 1), ((3, 2, 2), 2, 1)])
-def test_fp16_inner_basis_solution_matches_dense_solve(dg, n, k, basis):
-    """The inner Krylov basis stored in scaled FP16 (768 unknowns, a multiple of 8); with 324 unknowns the
-    option falls back to the FP32 basis.  Same bounds as the FP32-basis solves."""
-    w = inputs.small_case(n=n, k=k, seed=18, b=(1.0, 0.5, 0.25), f_kind="sines")
+@pytest.mark.parametrize("n,k,basis,mixed_cells", [((3, 2, 2), 3, 1, False), ((3, 2, 2), 2, 1, False),
+                                                   ((4, 2, 2), 2, 1, False), ((3, 2, 2), 3, 1, True)])
+def test_fp16_inner_basis_solution_matches_dense_solve(dg, n, k, basis, mixed_cells):
+    """The inner Krylov basis stored in scaled FP16: 768 unknowns (k = 3, the block inverse reads the FP16 rows
+    itself), 432 unknowns (k = 2: odd n, the rows are converted to FP32 first); with 324 unknowns (not a multiple
+    of 8) the option falls back to the FP32 basis.  mixed_cells: D alternating 100 / 0.01 with strong convection,
+    so the block inverse has real and complex cells (the complex ones converted from FP16 first).  Same bounds as
+    the FP32-basis solves."""
+    w = inputs.small_case(n=n, k=k, seed=18, b=(40.0, -30.0, 20.0) if mixed_cells else (1.0, 0.5, 0.25),
+                          f_kind="sines")
+    if mixed_cells:
+        w.D = np.where(np.arange(w.ncell) % 2 == 0, 100.0, 0.01)
     w.f_params = inputs.sine_modes(10)
     pr = oracle_problem(w)
     A = oracle_matrix(pr)
@@ -103,6 +110,8 @@ def test_fp16_inner_basis_solution_matches_dense_solve(dg, n, k, basis):
     x_ref = np.linalg.solve(A, F)
     op = dg.operator_for(w)
     op.precond_setup()
+    if mixed_cells:
+        assert 0 < op.precond_info()[1] < w.ncell
     for outer in (0, 1):
         x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
         st = op.solve(x, mode=dg.DG_SOLVE_MIXED, rtol=1e-12, restart=20, outer_restart=8, inner_rtol=1e-2,
