@@ -31,9 +31,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# FP64 peak of one GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz (unit counts and max clock)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Unit-count peaks: SMs x FMA per clock per SM (2 FP64, 128 FP32) x 2 flop x maximum SM clock.  The values below
+# are those of a GB300 (152 SMs, 2070 MHz); set_unit_peaks() replaces them with the running device's SM count and
+# the maximum SM clock nvidia-smi reports, before anything is measured.
+UNIT_SMS, UNIT_MHZ = 152, 2070.0
+FP64_PEAK_TFLOPS = UNIT_SMS * 2 * 2 * UNIT_MHZ * 1e6 / 1e12
+FP32_PEAK_TFLOPS = UNIT_SMS * 128 * 2 * UNIT_MHZ * 1e6 / 1e12
+
+
+def set_unit_peaks(device_index=0):
+    """The unit-count peaks of the device in use (SM count from CUDA, maximum SM clock from nvidia-smi)."""
+    global UNIT_SMS, UNIT_MHZ, FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS
+    import torch
+    if not torch.cuda.is_available():
+        return
+    UNIT_SMS = torch.cuda.get_device_properties(device_index).multi_processor_count
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={device_index}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        UNIT_MHZ = float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        pass
+    FP64_PEAK_TFLOPS = UNIT_SMS * 2 * 2 * UNIT_MHZ * 1e6 / 1e12
+    FP32_PEAK_TFLOPS = UNIT_SMS * 128 * 2 * UNIT_MHZ * 1e6 / 1e12
 
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the
 # kernels as they were when profiled, keyed by the sha256 of the kernel source at that time.
@@ -484,6 +504,27 @@ def _precond_timing(op, n, reps=20):
     return out
 
 
+def _f32_apply_timing(op, w, reps=20):
+    """The FP32 Jacobian apply of the inner solve on this mesh: time per apply (CUDA events, after five warm-ups),
+    MDOF/s and the executed-flop rate against the FP32 unit-count peak."""
+    import torch
+
+    from paper_1711_10885_gb300 import flops, inputs
+    u = torch.tensor(inputs.uniform_u(w.ndof, 2), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(u)
+    for _ in range(5):
+        op.apply_jacobian(u, y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        op.apply_jacobian(u, y)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    tf = flops.apply_flops_per_dof(w.k, w.n, residual=False) * w.ndof / (ms * 1e-3) / 1e12
+    return {"apply_us": ms * 1e3, "mdofs": w.ndof / ms / 1e3, "tflops": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS}
+
+
 def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     """The solve half of the headline metric, in the default line (one GPU):
 
@@ -512,7 +553,7 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     q5 = {"workload": "unit_cube_q5_48", "dofs": w.ndof, "rtol": 1e-10, "operator_setup_s": t1 - t0,
           "precond_setup_s": time.perf_counter() - t1,
           "precond": "block-Jacobi, exact block inverse by fast diagonalisation (FP32 inner, FP64 outer / plain)",
-          "block_inverse": _precond_timing(op, w.ndof)}
+          "block_inverse": _precond_timing(op, w.ndof), "fp32_apply": _f32_apply_timing(op, w)}
     xs = {}
     # each outer operator with the inner Krylov basis stored in FP32 (the default) and in scaled FP16
     mixed = (("mixed_fp64_outer", 1, 0), ("mixed_df_outer", 0, 0), ("mixed_fp64_outer_fp16_basis", 1, 1),
@@ -557,7 +598,8 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     op.precond_setup(dg.DG_BJ_FAST_DIAG)
     torch.cuda.synchronize()
     q4 = {"workload": "64^3 Q4, D log-normal sigma 1.5 (seed 20)", "dofs": ev.ndof, "rtol": 1e-8, "mlp": info,
-          "setup_s": time.perf_counter() - t0, "block_inverse": _precond_timing(op, ev.ndof)}
+          "setup_s": time.perf_counter() - t0, "block_inverse": _precond_timing(op, ev.ndof),
+          "fp32_apply": _f32_apply_timing(op, ev)}
     common = dict(rtol=1e-8, inner_rtol=1e-2, mlp=mlp)
     q4["mixed_bj"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
                                      preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, **common)
@@ -1359,7 +1401,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "kernel": dominant[0], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz (unit counts and max clock)",
+                     "peak_source": f"{UNIT_SMS} SMs x 2 FP64 FMA/clk x 2 x {UNIT_MHZ:.0f} MHz (unit counts and "
+                                    "max clock)",
                      "flops_per_launch": dominant[1]},
         "kernels_ms": {"dg_cell_kernel": cell_ms, "dg_face_kernel": face_ms},
         "executed_flops_per_dof": (cell_fl + face_fl) / w.ndof,
@@ -1464,6 +1507,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.impl != "reference":
+        set_unit_peaks(int(os.environ.get("LOCAL_RANK", "0")))
     if args.impl == "reference":
         run_reference(args)
     elif args.profile:
