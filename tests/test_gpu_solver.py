@@ -299,6 +299,25 @@ def test_fgmres_basis_passes_off_the_packed_path(dg, case):
     op.close()
 
 
+def test_fp16_basis_with_restart_60_and_no_preconditioner(dg):
+    """The FP16 basis passes at their largest size: an inner FGMRES(60) without a preconditioner takes up to 61
+    FP16 rows (the dot pass's 123 rows of per-thread partial sums need more than 48 KB of shared memory) and the
+    identity preconditioner copies the converted row; the solution matches a dense LU solve."""
+    w = inputs.small_case(n=(4, 2, 2), k=2, seed=8, b=(1.0, 0.5, 0.25), f_kind="sines")
+    w.f_params = inputs.sine_modes(9)
+    pr = oracle_problem(w)
+    A = oracle_matrix(pr)
+    F = oracle.rhs(pr, inputs.f_at(w, oracle.volume_points(pr)), None)
+    x_ref = np.linalg.solve(A, F)
+    op = dg.operator_for(w)
+    x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
+    st = op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_NONE, rtol=1e-12, restart=60,
+                  outer_restart=8, inner_rtol=1e-9, inner_basis_precision=1)
+    assert st["rc"] == 0 and st["inner_iterations"] >= 60  # inner cycles of the full 60 steps
+    assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-9 * np.max(np.abs(x_ref))
+    op.close()
+
+
 def test_non_finite_right_hand_side_is_reported(dg):
     """A NaN in b: both solvers stop at the first residual norm and return DG_ERR_NAN (-6) with the status set."""
     w = inputs.small_case(n=(2, 2, 2), k=2, seed=21)
@@ -306,8 +325,9 @@ def test_non_finite_right_hand_side_is_reported(dg):
     op.precond_setup()
     b = torch.ones(w.ndof, dtype=torch.float64, device="cuda")
     b[3] = float("nan")
-    for mode in (dg.DG_SOLVE_FP64, dg.DG_SOLVE_MIXED):
+    for mode, basis in ((dg.DG_SOLVE_FP64, 0), (dg.DG_SOLVE_MIXED, 0), (dg.DG_SOLVE_MIXED, 1)):
         x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
-        st = op.solve(x, b=b, mode=mode, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, raise_on_error=False)
-        assert st["rc"] == -6 and st["status"] == -6, (mode, st)
+        st = op.solve(x, b=b, mode=mode, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, raise_on_error=False,
+                      inner_basis_precision=basis)
+        assert st["rc"] == -6 and st["status"] == -6, (mode, basis, st)
     op.close()
