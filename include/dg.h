@@ -154,8 +154,11 @@ int dg_rhs(dg_handle* h, void* F_dev, int32_t precision, void* stream);
 
 enum { DG_SOLVE_FP64 = 0, DG_SOLVE_MIXED = 1 };
 /* DG_PRECOND_MLP: z = network(r); DG_PRECOND_BJ_MLP: z = block-Jacobi(r) + network(r), the network
- * trained on the part of the error that block-Jacobi misses (needs dg_precond_setup). */
-enum { DG_PRECOND_NONE = 0, DG_PRECOND_BLOCK_JACOBI = 1, DG_PRECOND_MLP = 2, DG_PRECOND_BJ_MLP = 3 };
+ * trained on the part of the error that block-Jacobi misses (needs dg_precond_setup).  DG_PRECOND_RB_GS:
+ * red-black block Gauss-Seidel (dg_precond_apply_rbgs; needs dg_precond_setup): one operator application more
+ * per preconditioner application than block-Jacobi, about half the Krylov iterations. */
+enum { DG_PRECOND_NONE = 0, DG_PRECOND_BLOCK_JACOBI = 1, DG_PRECOND_MLP = 2, DG_PRECOND_BJ_MLP = 3,
+       DG_PRECOND_RB_GS = 4 };
 
 typedef struct dg_mlp dg_mlp; /* learned per-element preconditioner, see below */
 
@@ -164,8 +167,9 @@ typedef struct {
                              DG_SOLVE_MIXED: FGMRES(outer_restart) in FP64 (true residual, defect update
                              and orthogonalisation in FP64) whose preconditioner is one cycle of an FP32
                              FGMRES(restart) on the FP32 operator, stopped at inner_rtol.             */
-  int32_t preconditioner; /* DG_PRECOND_NONE or DG_PRECOND_BLOCK_JACOBI (FP64 blocks in FP64 mode, FP32
-                             blocks inside the FP32 inner solve); needs dg_precond_setup first        */
+  int32_t preconditioner; /* DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI (FP64 blocks in FP64 mode, FP32
+                             blocks inside the FP32 inner solve), DG_PRECOND_RB_GS (in the precision of the
+                             solve it preconditions) or an MLP mode; needs dg_precond_setup first      */
   int32_t restart;        /* FGMRES restart length (inner length in MIXED mode), 1..60, 0 = 30        */
   int32_t outer_restart;  /* MIXED: outer restart length, 1..60, 0 = 20                               */
   int32_t max_iterations; /* cap on (outer) iterations, 0 = 10000                                      */
@@ -239,6 +243,17 @@ int dg_precond_info(const dg_handle* h, int32_t* info, int64_t* complex_cells);
  * DG_F32 the exact block inverse by fast diagonalisation with complex FP32 contractions, or the FP32 dense
  * blocks where the 1D operators could not be diagonalised. */
 int dg_precond_apply(dg_handle* h, const void* r_dev, void* z_dev, int32_t precision, void* stream);
+
+/* z = M^{-1} r with red-black block Gauss-Seidel.  The cells are coloured by the parity of ix + iy + iz, so the
+ * face neighbours of a red cell are black (on a periodic axis with an odd number of cells the two cells across
+ * the wrap share a colour; their coupling is then left out as in block-Jacobi).  M is the block lower-triangular
+ * part of A in red-before-black order:
+ *   z_red = A_rr^{-1} r_red,   z_black = A_bb^{-1} (r - A z_red)_black,
+ * the diagonal blocks inverted by fast diagonalisation (any degree; dg_precond_setup first) and A z_red the
+ * operator applied to z_red (zero on the black cells).  r, z and work are distinct device vectors of the given
+ * precision (DG_F64 or DG_F32), work is scratch; asynchronous on `stream`. */
+int dg_precond_apply_rbgs(dg_handle* h, const void* r_dev, void* z_dev, void* work_dev, int32_t precision,
+                          void* stream);
 
 /* Solve A x = b (b_dev NULL: b = F, the right hand side of dg_setup) with FGMRES; x_dev holds the
  * initial guess and receives the solution (FP64, device).  Fills *stats (may be NULL).  Returns

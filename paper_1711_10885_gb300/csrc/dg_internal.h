@@ -35,10 +35,12 @@ struct Buffers {
 
 // Tables of the fast-diagonalisation block inverse.  A cell whose three 1D operators have real eigenvalues and
 // eigenvectors gets real tables, the others complex ones (3 (2 n^2 + n) + 1 entries per cell either way, in the
-// order of their group); each group lists its cells in ascending order (null list: the group is every cell).
+// order of their group); each group lists its cells, red before black, each colour in ascending order.
 struct FdmTables {
   bool built = false;
   int64_t nre = 0, ncx = 0;
+  // each group lists its red cells (ix + iy + iz even) first, then its black ones: nre_red / ncx_red red cells
+  int64_t nre_red = 0, ncx_red = 0;
   void* re32 = nullptr;  // [nre][TS] float
   void* re64 = nullptr;  // [nre][TS] double
   void* cx32 = nullptr;  // [ncx][TS] float2
@@ -152,8 +154,17 @@ int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t 
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
+// the block inverse on one colour of cells only (0 red, 1 black; -1 every cell); z untouched on the others
+int precond_fdm_color_f32(const dg_handle* h, const float* r, float* z, int color, cudaStream_t s);
+int precond_fdm_color_f64(const dg_handle* h, const double* r, double* z, int color, cudaStream_t s);
 // z = block inverse of (scale * r) for a scaled FP16 r; tmp: n FP32 values of scratch, 16-byte aligned
-int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* tmp, cudaStream_t s);
+int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* tmp, cudaStream_t s,
+                         int color = -1);
+// red-black block Gauss-Seidel (t: n values of scratch; tmp as for precond_fdm_f32_half)
+int precond_rbgs_f32(const dg_handle* h, const float* r, float* z, float* t, cudaStream_t s);
+int precond_rbgs_f64(const dg_handle* h, const double* r, double* z, double* t, cudaStream_t s);
+int precond_rbgs_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* t, float* tmp,
+                          cudaStream_t s);
 // F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null);
 // with vol = 1 instead of |T| and no g this is the L2 projection z_i = (f, phi_i)_T / |T|
 int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,

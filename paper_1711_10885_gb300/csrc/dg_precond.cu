@@ -636,12 +636,15 @@ __device__ __forceinline__ void plane_out(const float* pl, float* u) {
 // TIn = __half (even n only): r is a scaled FP16 vector (r_i = in_scale * h_i), the FGMRES basis row of the FP32
 // inner solve; its cells arrive by 16-byte cp.async in a staging area RH [CB][n^3] after the tables and are
 // converted as the first phase loads its planes.
+// sub (may be null): the input is r - sub (the defect of a Gauss-Seidel sweep), sub an FP32 vector read as the
+// planes are loaded (even n: 16-byte loads).
 template <int N, typename TIn>
 __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(const float* __restrict__ tab,
                                                                                const TIn* __restrict__ r,
                                                                                float in_scale,
                                                                                float* __restrict__ z, int64_t count,
-                                                                               const int64_t* __restrict__ cells) {
+                                                                               const int64_t* __restrict__ cells,
+                                                                               const float* __restrict__ sub) {
   using P = FdmPlanesR<N>;
   constexpr int NN = P::NN, N3 = P::N3, UP = P::UP, TP = P::TP, AXP = RealLay<N>::AXP;
   constexpr bool V4 = P::V4, HIN = std::is_same<TIn, __half>::value;
@@ -693,6 +696,12 @@ __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(c
       }
     } else {
       plane_in<N, V4>(v, u + p * NN);
+    }
+    if (sub) {
+      float w[NN];
+      plane_in<N, V4>(w, sub + s_cell[lc] * N3 + p * NN);
+#pragma unroll
+      for (int q = 0; q < NN; ++q) v[q] -= w[q];
     }
     fdm_load_r<N, V4>(m, tb);
 #pragma unroll
@@ -927,12 +936,19 @@ bool build_fdm(const dg_handle* h, const std::vector<double>& D, std::vector<dou
 }
 
 // one group of cells with real tables: the plane kernel in FP32 up to n = 8, else one thread per line
+// sub (FP32, may be null): the plane kernel takes r - sub as its input (the caller guarantees even n <= 8 and
+// 16-byte aligned vectors when it passes one)
 template <typename R>
 int fdm_group_real(const dg_handle* h, const R* tab, const int64_t* cells, int64_t count, const R* r, R* z,
-                   cudaStream_t s) {
+                   cudaStream_t s, const float* sub = nullptr) {
   const int N = h->N, NN = N * N, cpb = std::max(1, 256 / NN), TS = 3 * ((2 * NN + N + 3) / 4 * 4) + 4;
   // the plane kernel moves r and z in 16-byte pieces for even n: other vectors take the line kernel
-  const bool aligned = N % 2 == 1 || (reinterpret_cast<uintptr_t>(r) % 16 == 0 && reinterpret_cast<uintptr_t>(z) % 16 == 0);
+  const bool aligned = N % 2 == 1 || (reinterpret_cast<uintptr_t>(r) % 16 == 0 && reinterpret_cast<uintptr_t>(z) % 16 == 0 &&
+                                      reinterpret_cast<uintptr_t>(sub) % 16 == 0);
+  if (sub && !(sizeof(R) == 4 && N <= 8 && aligned)) {
+    set_error("fast diagonalisation: a subtracted input needs the FP32 plane kernel");
+    return DG_ERR_INVALID_ARG;
+  }
   if constexpr (sizeof(R) == 4) {
     if (N <= 8 && aligned) {
       switch (N) {
@@ -949,7 +965,7 @@ int fdm_group_real(const dg_handle* h, const R* tab, const int64_t* cells, int64
         return rca;                                                                                       \
     }                                                                                                     \
     fdm_apply_planes_real<NV, float><<<(unsigned)((count + P::CB - 1) / P::CB), P::CB * NV, P::SMEM, s>>>( \
-        tab, r, 1.f, z, count, cells);                                                                    \
+        tab, r, 1.f, z, count, cells, sub);                                                               \
     break;                                                                                                \
   }
         FDMR(2) FDMR(3) FDMR(4) FDMR(5) FDMR(6) FDMR(7) FDMR(8)
@@ -1043,27 +1059,45 @@ int fdm_group_complex(const dg_handle* h, const typename Cx<R>::type* tab, const
   return e == cudaSuccess ? 0 : cuda_fail(e, "block-Jacobi apply (fast diagonalisation)");
 }
 
-// z = A_TT^{-1} r on every cell: the real group, then the complex group (disjoint cells)
+// positions [lo, hi) of a group's cells for a colour (-1: all, 0: red, 1: black)
+inline void color_range(int64_t n, int64_t nred, int color, int64_t* lo, int64_t* hi) {
+  *lo = color == 1 ? nred : 0;
+  *hi = color == 0 ? nred : n;
+}
+
+// z = A_TT^{-1} r on every cell of a colour (-1: every cell): the real group, then the complex group (disjoint
+// cells); z is not written on the other cells
 template <typename R>
-int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s) {
+int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s, int color = -1) {
   using C = typename Cx<R>::type;
   const FdmTables& f = h->fdm;
   if (!f.built) {
     set_error("block-Jacobi: the fast diagonalisation was not set up");
     return DG_ERR_INVALID_ARG;
   }
-  if (f.nre > 0)
-    if (int rc = fdm_group_real<R>(h, static_cast<const R*>(sizeof(R) == 4 ? f.re32 : f.re64), f.re_cells, f.nre, r,
-                                   z, s))
+  const int N = h->N, NN = N * N;
+  const int64_t TPR = 3 * ((2 * NN + N + 3) / 4 * 4) + 4, TS = 3 * (2 * NN + N) + 1;
+  int64_t lo, hi;
+  color_range(f.nre, f.nre_red, color, &lo, &hi);
+  if (hi > lo)
+    if (int rc = fdm_group_real<R>(h, static_cast<const R*>(sizeof(R) == 4 ? f.re32 : f.re64) + lo * TPR,
+                                   f.re_cells + lo, hi - lo, r, z, s))
       return rc;
-  if (f.ncx > 0)
-    if (int rc = fdm_group_complex<R>(h, static_cast<const C*>(sizeof(R) == 4 ? f.cx32 : f.cx64), f.cx_cells, f.ncx,
-                                      r, z, s))
+  color_range(f.ncx, f.ncx_red, color, &lo, &hi);
+  if (hi > lo)
+    if (int rc = fdm_group_complex<R>(h, static_cast<const C*>(sizeof(R) == 4 ? f.cx32 : f.cx64) + lo * TS,
+                                      f.cx_cells + lo, hi - lo, r, z, s))
       return rc;
   return 0;
 }
 
 int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) { return precond_fdm(h, r, z, s); }
+int precond_fdm_color_f32(const dg_handle* h, const float* r, float* z, int color, cudaStream_t s) {
+  return precond_fdm(h, r, z, s, color);
+}
+int precond_fdm_color_f64(const dg_handle* h, const double* r, double* z, int color, cudaStream_t s) {
+  return precond_fdm(h, r, z, s, color);
+}
 
 namespace {
 // dst[c n^3 + i] = scale * src[c n^3 + i] for the listed cells (FP16 -> FP32)
@@ -1078,7 +1112,7 @@ __global__ void half_cells_to_float(const __half* __restrict__ src, float scale,
 
 template <int N>
 int fdm_real_half(const dg_handle* h, const float* tab, const int64_t* cells, int64_t count, const __half* r,
-                  float scale, float* z, cudaStream_t s) {
+                  float scale, float* z, cudaStream_t s, const float* sub = nullptr) {
   using P = FdmPlanesR<N>;
   static DeviceOnce attr;
   if (P::SMEM_H > 48 * 1024)
@@ -1089,7 +1123,7 @@ int fdm_real_half(const dg_handle* h, const float* tab, const int64_t* cells, in
         }))
       return rca;
   fdm_apply_planes_real<N, __half><<<(unsigned)((count + P::CB - 1) / P::CB), P::CB * N, P::SMEM_H, s>>>(
-      tab, r, scale, z, count, cells);
+      tab, r, scale, z, count, cells, sub);
   return 0;
 }
 }  // namespace
@@ -1097,40 +1131,178 @@ int fdm_real_half(const dg_handle* h, const float* tab, const int64_t* cells, in
 // z = A_TT^{-1} (scale * r) for a scaled FP16 vector r (the FP16 basis rows of the inner solve).  The real group
 // reads r directly (even n <= 8, 16-byte aligned r and z); the complex group and every other case first convert
 // their entries into tmp (n FP32 values, 16-byte aligned) and take the FP32 path.
-int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* tmp, cudaStream_t s) {
+int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* tmp, cudaStream_t s,
+                         int color) {
   const FdmTables& f = h->fdm;
   if (!f.built) {
     set_error("block-Jacobi: the fast diagonalisation was not set up");
     return DG_ERR_INVALID_ARG;
   }
-  const int N = h->N, N3 = N * N * N;
+  const int N = h->N, N3 = N * N * N, NN = N * N;
+  const int64_t TPR = 3 * ((2 * NN + N + 3) / 4 * 4) + 4, TS = 3 * (2 * NN + N) + 1;
   const bool direct = N % 2 == 0 && N <= 8 && reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
                       reinterpret_cast<uintptr_t>(z) % 16 == 0;
   if (!direct) {
     half_cells_to_float<<<sm_count() * 4, 256, 0, s>>>(r, scale, nullptr, h->ncell, N3, tmp);
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "FP16 row conversion");
-    return precond_fdm(h, static_cast<const float*>(tmp), z, s);
+    return precond_fdm(h, static_cast<const float*>(tmp), z, s, color);
   }
-  if (f.nre > 0) {
-    const float* tab = static_cast<const float*>(f.re32);
+  int64_t lo, hi;
+  color_range(f.nre, f.nre_red, color, &lo, &hi);
+  if (hi > lo) {
+    const float* tab = static_cast<const float*>(f.re32) + lo * TPR;
+    const int64_t* cells = f.re_cells + lo;
     int rc = 0;
     switch (N) {
-      case 2: rc = fdm_real_half<2>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
-      case 4: rc = fdm_real_half<4>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
-      case 6: rc = fdm_real_half<6>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
-      default: rc = fdm_real_half<8>(h, tab, f.re_cells, f.nre, r, scale, z, s); break;
+      case 2: rc = fdm_real_half<2>(h, tab, cells, hi - lo, r, scale, z, s); break;
+      case 4: rc = fdm_real_half<4>(h, tab, cells, hi - lo, r, scale, z, s); break;
+      case 6: rc = fdm_real_half<6>(h, tab, cells, hi - lo, r, scale, z, s); break;
+      default: rc = fdm_real_half<8>(h, tab, cells, hi - lo, r, scale, z, s); break;
     }
     if (rc) return rc;
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess)
       return cuda_fail(e, "block-Jacobi apply (fast diagonalisation, FP16 input)");
   }
-  if (f.ncx > 0) {
-    half_cells_to_float<<<sm_count() * 4, 256, 0, s>>>(r, scale, f.cx_cells, f.ncx, N3, tmp);
+  color_range(f.ncx, f.ncx_red, color, &lo, &hi);
+  if (hi > lo) {
+    half_cells_to_float<<<sm_count() * 4, 256, 0, s>>>(r, scale, f.cx_cells + lo, hi - lo, N3, tmp);
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "FP16 row conversion");
-    if (int rc = fdm_group_complex<float>(h, static_cast<const float2*>(f.cx32), f.cx_cells, f.ncx, tmp, z, s))
+    if (int rc = fdm_group_complex<float>(h, static_cast<const float2*>(f.cx32) + lo * TS, f.cx_cells + lo, hi - lo,
+                                          tmp, z, s))
       return rc;
   }
   return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Red-black block Gauss-Seidel: with the cells coloured by the parity of ix + iy + iz, the face neighbours of a
+// red cell are black and vice versa (on a periodic axis with an odd cell count the two cells across the wrap
+// share a colour, and their coupling is then treated as in block-Jacobi).  One application is the exact solve
+// with the block lower-triangular part of A in red-before-black order:
+//   z_red = A_rr^{-1} r_red,   z_black = A_bb^{-1} (r - A z_red)_black,
+// with the diagonal blocks inverted by fast diagonalisation and A z_red the operator itself applied to z (zero on
+// the black cells).  t: scratch vector of n values.  In FP32 with even n <= 8 and 16-byte aligned vectors the
+// black cells' defect r - A z_red is formed inside the block-inverse kernel as it loads its planes (real cells)
+// or for the listed cells only (complex cells); otherwise by a separate pass over the vector.
+// ---------------------------------------------------------------------------------------------
+namespace {
+template <typename R>
+__global__ void __launch_bounds__(256) rbgs_defect(const R* __restrict__ r, R* __restrict__ t, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    t[i] = r[i] - t[i];
+}
+__global__ void __launch_bounds__(256) rbgs_defect_half(const __half* __restrict__ r, float scale,
+                                                        float* __restrict__ t, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    t[i] = __half2float(r[i]) * scale - t[i];
+}
+// t = scale * r - t on the listed cells only
+template <typename TIn>
+__global__ void __launch_bounds__(256) rbgs_defect_cells(const TIn* __restrict__ r, float scale,
+                                                         const int64_t* __restrict__ cells, int64_t count, int n3,
+                                                         float* __restrict__ t) {
+  const int64_t total = count * n3;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / n3, i = cells[q] * n3 + (e - q * n3);
+    t[i] = (float)r[i] * scale - t[i];
+  }
+}
+
+template <typename R>
+int rbgs_apply_A(const dg_handle* h, const R* z, R* t, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4)
+    return launch_apply_f32(h, z, t, 0, 3, s);
+  else
+    return launch_apply_f64(h, z, t, 0, 3, s);
+}
+
+inline bool al16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
+// black cells from r - t (t = A z_red on entry; overwritten) with the defect fused (FP32, even n <= 8, aligned;
+// r FP32 or scaled FP16)
+template <typename TIn>
+int rbgs_black_fused(const dg_handle* h, const TIn* r, float scale, float* z, float* t, cudaStream_t s) {
+  const FdmTables& f = h->fdm;
+  const int N = h->N, NN = N * N, N3 = NN * N;
+  const int64_t TPR = 3 * ((2 * NN + N + 3) / 4 * 4) + 4, TS = 3 * (2 * NN + N) + 1;
+  if (f.nre > f.nre_red) {
+    const float* tab = static_cast<const float*>(f.re32) + f.nre_red * TPR;
+    const int64_t* cells = f.re_cells + f.nre_red;
+    const int64_t cnt = f.nre - f.nre_red;
+    int rc = 0;
+    if constexpr (std::is_same<TIn, __half>::value) {
+      switch (N) {
+        case 2: rc = fdm_real_half<2>(h, tab, cells, cnt, r, scale, z, s, t); break;
+        case 4: rc = fdm_real_half<4>(h, tab, cells, cnt, r, scale, z, s, t); break;
+        case 6: rc = fdm_real_half<6>(h, tab, cells, cnt, r, scale, z, s, t); break;
+        default: rc = fdm_real_half<8>(h, tab, cells, cnt, r, scale, z, s, t); break;
+      }
+      if (!rc)
+        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) rc = cuda_fail(e, "red-black Gauss-Seidel (black)");
+    } else {
+      rc = fdm_group_real<float>(h, tab, cells, cnt, r, z, s, t);
+    }
+    if (rc) return rc;
+  }
+  if (f.ncx > f.ncx_red) {
+    const int64_t* cells = f.cx_cells + f.ncx_red;
+    const int64_t cnt = f.ncx - f.ncx_red;
+    rbgs_defect_cells<TIn><<<sm_count() * 4, 256, 0, s>>>(r, scale, cells, cnt, N3, t);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "red-black Gauss-Seidel (defect)");
+    if (int rc = fdm_group_complex<float>(h, static_cast<const float2*>(f.cx32) + f.ncx_red * TS, cells, cnt, t, z, s))
+      return rc;
+  }
+  return 0;
+}
+
+template <typename R, typename First, typename Defect>
+int rbgs_sweep(const dg_handle* h, R* z, R* t, cudaStream_t s, First first, Defect defect_then_black) {
+  if (!h->fdm.built) {
+    set_error("red-black Gauss-Seidel: dg_precond_setup was not called");
+    return DG_ERR_INVALID_ARG;
+  }
+  const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
+  cudaError_t e = cudaMemsetAsync(z, 0, n * sizeof(R), s);
+  if (e != cudaSuccess) return cuda_fail(e, "red-black Gauss-Seidel: clear z");
+  if (int rc = first()) return rc;
+  if (int rc = rbgs_apply_A<R>(h, z, t, s)) return rc;
+  return defect_then_black(n);
+}
+}  // namespace
+
+int precond_rbgs_f32(const dg_handle* h, const float* r, float* z, float* t, cudaStream_t s) {
+  const int N = h->N;
+  const bool fused = N <= 8 && (N % 2 == 1 || (al16(r) && al16(z) && al16(t)));
+  return rbgs_sweep<float>(
+      h, z, t, s, [&] { return precond_fdm<float>(h, r, z, s, 0); },
+      [&](size_t n) -> int {
+        if (fused) return rbgs_black_fused<float>(h, r, 1.f, z, t, s);
+        rbgs_defect<float><<<sm_count() * 4, 256, 0, s>>>(r, t, n);
+        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "red-black Gauss-Seidel");
+        return precond_fdm<float>(h, t, z, s, 1);
+      });
+}
+int precond_rbgs_f64(const dg_handle* h, const double* r, double* z, double* t, cudaStream_t s) {
+  return rbgs_sweep<double>(
+      h, z, t, s, [&] { return precond_fdm<double>(h, r, z, s, 0); },
+      [&](size_t n) -> int {
+        rbgs_defect<double><<<sm_count() * 4, 256, 0, s>>>(r, t, n);
+        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "red-black Gauss-Seidel");
+        return precond_fdm<double>(h, t, z, s, 1);
+      });
+}
+int precond_rbgs_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* t, float* tmp,
+                          cudaStream_t s) {
+  const int N = h->N;
+  const bool fused = N % 2 == 0 && N <= 8 && al16(r) && al16(z) && al16(t);
+  return rbgs_sweep<float>(
+      h, z, t, s, [&] { return precond_fdm_f32_half(h, r, scale, z, tmp, s, 0); },
+      [&](size_t n) -> int {
+        if (fused) return rbgs_black_fused<__half>(h, r, scale, z, t, s);
+        rbgs_defect_half<<<sm_count() * 4, 256, 0, s>>>(r, scale, t, n);
+        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "red-black Gauss-Seidel");
+        return precond_fdm<float>(h, t, z, s, 1);
+      });
 }
 
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
@@ -1192,8 +1364,20 @@ int setup_fdm(dg_handle* h) {
   }
   const int N = h->N, NN = N * N, AX = 2 * NN + N, TS = 3 * AX + 1;
   const int AXP = (AX + 3) / 4 * 4, TP = 3 * AXP + 4;  // the padded layout of the real kernels
+  // groups: real / complex cells, each red (ix + iy + iz even) first, then black, ascending within a colour
   std::vector<int64_t> re_cells, cx_cells;
-  for (int64_t c = 0; c < h->ncell; ++c) (is_real[c] ? re_cells : cx_cells).push_back(c);
+  int64_t nre_red = 0, ncx_red = 0;
+  for (int color = 0; color < 2; ++color) {
+    for (int64_t c = 0; c < h->ncell; ++c) {
+      const int64_t ix = c % h->n[0], iy = (c / h->n[0]) % h->n[1], iz = c / ((int64_t)h->n[0] * h->n[1]);
+      if ((int)((ix + iy + iz) & 1) != color) continue;
+      (is_real[c] ? re_cells : cx_cells).push_back(c);
+    }
+    if (color == 0) {
+      nre_red = (int64_t)re_cells.size();
+      ncx_red = (int64_t)cx_cells.size();
+    }
+  }
   const int64_t nre = (int64_t)re_cells.size(), ncx = (int64_t)cx_cells.size();
   // group tables in group order; real ones with each axis block (W, V, lambda) padded to AXP entries
   std::vector<double> re64((size_t)nre * TP, 0.0);
@@ -1217,6 +1401,8 @@ int setup_fdm(dg_handle* h) {
   FdmTables f;
   f.nre = nre;
   f.ncx = ncx;
+  f.nre_red = nre_red;
+  f.ncx_red = ncx_red;
   auto up = [&](void** dst, const void* src, size_t bytes) {
     if (e != cudaSuccess || bytes == 0) return;
     e = cudaMalloc(dst, bytes);
@@ -1226,11 +1412,8 @@ int setup_fdm(dg_handle* h) {
   up(&f.re64, re64.data(), re64.size() * sizeof(double));
   up(&f.cx32, cx32.data(), cx32.size() * sizeof(float2));
   up(&f.cx64, cx64.data(), cx64.size() * sizeof(double2));
-  // a group that is every cell needs no list
-  if (ncx > 0) {
-    up(reinterpret_cast<void**>(&f.cx_cells), cx_cells.data(), cx_cells.size() * sizeof(int64_t));
-    if (nre > 0) up(reinterpret_cast<void**>(&f.re_cells), re_cells.data(), re_cells.size() * sizeof(int64_t));
-  }
+  up(reinterpret_cast<void**>(&f.re_cells), re_cells.data(), re_cells.size() * sizeof(int64_t));
+  up(reinterpret_cast<void**>(&f.cx_cells), cx_cells.data(), cx_cells.size() * sizeof(int64_t));
   if (e != cudaSuccess) {
     for (void* q : {f.re32, f.re64, f.cx32, f.cx64, (void*)f.re_cells, (void*)f.cx_cells}) cudaFree(q);
     return cuda_fail(e, "fast diagonalisation tables");
@@ -1358,6 +1541,21 @@ int dg_precond_info(const dg_handle* h, int32_t* info, int64_t* complex_cells) {
           (h->fdm.built && h->fdm.ncx == 0 ? DG_PRECOND_FAST_DIAG_REAL : 0);
   if (complex_cells) *complex_cells = h->fdm.built ? h->fdm.ncx : 0;
   return DG_OK;
+}
+
+int dg_precond_apply_rbgs(dg_handle* h, const void* r, void* z, void* work, int32_t precision, void* stream) {
+  if (!h || !r || !z || !work || r == z || r == work || z == work || (precision != DG_F64 && precision != DG_F32)) {
+    set_error("dg_precond_apply_rbgs: bad arguments (r, z, work distinct device vectors; DG_F64 or DG_F32)");
+    return DG_ERR_INVALID_ARG;
+  }
+  if (!h->fdm.built) {
+    set_error("dg_precond_apply_rbgs: call dg_precond_setup first");
+    return DG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == DG_F64)
+    return precond_rbgs_f64(h, static_cast<const double*>(r), static_cast<double*>(z), static_cast<double*>(work), s);
+  return precond_rbgs_f32(h, static_cast<const float*>(r), static_cast<float*>(z), static_cast<float*>(work), s);
 }
 
 int dg_precond_apply(dg_handle* h, const void* r, void* z, int32_t precision, void* stream) {

@@ -430,7 +430,8 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       (o->outer_precision < 0 || o->outer_precision > 1) ||
       (o->inner_basis_precision < 0 || o->inner_basis_precision > 1) ||
       (o->preconditioner != DG_PRECOND_NONE && o->preconditioner != DG_PRECOND_BLOCK_JACOBI &&
-       o->preconditioner != DG_PRECOND_MLP && o->preconditioner != DG_PRECOND_BJ_MLP) ||
+       o->preconditioner != DG_PRECOND_MLP && o->preconditioner != DG_PRECOND_BJ_MLP &&
+       o->preconditioner != DG_PRECOND_RB_GS) ||
       !(o->rtol > 0) || (o->mode == DG_SOLVE_MIXED && !(o->inner_rtol > 0 && o->inner_rtol < 1))) {
     set_error("dg_solve: bad options (restart <= 60, mode, preconditioner, rtol > 0, 0 < inner_rtol < 1)");
     return DG_ERR_INVALID_ARG;
@@ -445,6 +446,10 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     set_error("dg_solve: block-Jacobi requested but dg_precond_setup was not called");
     return DG_ERR_INVALID_ARG;
   }
+  if (o->preconditioner == DG_PRECOND_RB_GS && !h->fdm.built) {
+    set_error("dg_solve: red-black Gauss-Seidel requested but dg_precond_setup was not called");
+    return DG_ERR_INVALID_ARG;
+  }
   if ((o->preconditioner == DG_PRECOND_MLP || o->preconditioner == DG_PRECOND_BJ_MLP) && !mlp_matches(o->mlp, h)) {
     set_error("dg_solve: DG_PRECOND_MLP / DG_PRECOND_BJ_MLP need opts->mlp for the handle's degree");
     return DG_ERR_INVALID_ARG;
@@ -453,6 +458,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
   const bool pc = o->preconditioner != DG_PRECOND_NONE;
+  const bool rbgs = o->preconditioner == DG_PRECOND_RB_GS;  // one more vector: the sweep's A z_red
   // MLP preconditioner, with a switch to block-Jacobi when a cycle stagnates (if blocks exist)
   bool use_mlp = o->preconditioner == DG_PRECOND_MLP || o->preconditioner == DG_PRECOND_BJ_MLP;
   const bool with_bj = o->preconditioner == DG_PRECOND_BJ_MLP;
@@ -479,10 +485,11 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   const bool half_basis = o->mode == DG_SOLVE_MIXED && o->inner_basis_precision == 1 && n % 8 == 0;
   size_t v64 = 0, v32 = 0;
   if (o->mode == DG_SOLVE_FP64) {
-    v64 = (size_t)(2 * m + 1) * n;  // V and Z (Z = V's provisional rows without a preconditioner)
+    v64 = (size_t)(2 * m + 1 + (rbgs ? 1 : 0)) * n;  // V and Z (Z = V's provisional rows without a preconditioner)
   } else {
     v64 = (size_t)(2 * mo + 1) * n;
     v32 = half_basis ? (size_t)(m + 4) * n + (size_t)(m + 1) * n / 2 : (size_t)(2 * m + 1 + 2) * n;
+    if (rbgs) v32 += n;
   }
   const size_t bytes = (small + n + v64) * sizeof(double) + v32 * sizeof(float) + 256;
   if (int rc = ensure_ws(h, bytes)) return rc;
@@ -517,7 +524,13 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
   int inner_total = 0;
   if (o->mode == DG_SOLVE_FP64) {
     std::function<int(const double*, double*)> M, M0;
-    if (pc && !first_only)
+    double* gs64 = V64 + (size_t)(2 * m + 1) * n;  // scratch of the Gauss-Seidel sweep
+    if (rbgs)
+      M = [&](const double* r, double* z) {
+        ++c.applies64;
+        return precond_rbgs_f64(h, r, z, gs64, s);
+      };
+    else if (pc && !first_only)
       M = [&](const double* r, double* z) {
         if (!use_mlp) return precond_bj_f64(h, r, z, s);
         if (!with_bj) return mlp_apply_impl(mlp, h, r, z, DG_F64, 0, s);
@@ -554,6 +567,7 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       rhs32 = Z32 + (size_t)m * n;
       e32 = rhs32 + n;
     }
+    float* gs32 = f32 + v32 - n;  // scratch of the Gauss-Seidel sweep (the last FP32 vector)
     std::function<int(const float*, float*)> M32;
     // block-Jacobi inside the FP32 inner solve: the FP16 blocks (half the bytes of this HBM-bound product) unless
     // the caller asked for the FP32 ones
@@ -562,7 +576,12 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       if (o->inner_block_precision == 0 && h->fdm.built) return precond_fdm_f32(h, r, z, s);
       return precond_bj_f16(h, r, z, s);
     };
-    if (pc)
+    if (rbgs)
+      M32 = [&](const float* r, float* z) {
+        ++c.applies32;
+        return precond_rbgs_f32(h, r, z, gs32, s);
+      };
+    else if (pc)
       M32 = [&](const float* r, float* z) {
         if (!use_mlp || first_only) return with_bj || !use_mlp ? bj_inner(r, z)
                                                              : cuda_check(cudaMemcpyAsync(z, r, n * sizeof(float),
@@ -575,7 +594,12 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
     // with the FP16 basis and the fast-diagonalisation block inverse alone (no network), the block inverse reads
     // the basis rows itself (the FP32 copy of u_j goes away)
     std::function<int(const __half*, float*)> M16;
-    if (half_basis && pc && !use_mlp && o->inner_block_precision == 0 && h->fdm.built)
+    if (half_basis && rbgs)
+      M16 = [&](const __half* r, float* z) {
+        ++c.applies32;
+        return precond_rbgs_f32_half(h, r, dgb::HB_INV, z, gs32, tmp32 + n, s);
+      };
+    else if (half_basis && pc && !use_mlp && o->inner_block_precision == 0 && h->fdm.built)
       M16 = [&](const __half* r, float* z) {
         return precond_fdm_f32_half(h, r, dgb::HB_INV, z, tmp32 + n, s);
       };

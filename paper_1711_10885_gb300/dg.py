@@ -68,6 +68,7 @@ DG_PRECOND_NONE = 0
 DG_PRECOND_BLOCK_JACOBI = 1
 DG_PRECOND_MLP = 2
 DG_PRECOND_BJ_MLP = 3
+DG_PRECOND_RB_GS = 4
 DG_BJ_DENSE = 1
 DG_BJ_FAST_DIAG = 2
 DG_PRECOND_HAS_DENSE = 1
@@ -133,6 +134,7 @@ def _load():
     lib.dg_precond_setup.argtypes = [vp, ctypes.c_int32, vp]
     lib.dg_precond_apply.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
     lib.dg_precond_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+    lib.dg_precond_apply_rbgs.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp]
     lib.dg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(dg_solve_opts), ctypes.POINTER(dg_solve_stats), vp]
     lib.dg_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.dg_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, vp]
@@ -165,7 +167,7 @@ lib = _load()
 # C-ABI symbols declared in include/dg.h (checked by the CPU test suite)
 EXPORTED = ["dg_penalty_sigma", "dg_setup", "dg_destroy", "dg_sizes", "dg_quadrature_points", "dg_apply_jacobian",
             "dg_apply_residual", "dg_rhs", "dg_last_error", "dg_apply_stage", "dg_precond_setup",
-            "dg_precond_apply", "dg_precond_info", "dg_solve", "dg_batch_create", "dg_batch_apply", "dg_batch_tuning",
+            "dg_precond_apply", "dg_precond_info", "dg_precond_apply_rbgs", "dg_solve", "dg_batch_create", "dg_batch_apply", "dg_batch_tuning",
             "dg_batch_destroy", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_dims", "dg_mlp_params",
             "dg_mlp_param_offsets", "dg_mlp_set_target_scale", "dg_mlp_features", "dg_mlp_forward", "dg_mlp_loss_grad",
             "dg_mlp_train", "dg_mlp_apply", "dg_mlp_apply_add", "dg_mlp_save", "dg_mlp_load",
@@ -394,6 +396,18 @@ class Operator:
         v, n = ctypes.c_int32(), ctypes.c_int64()
         check(lib.dg_precond_info(self.h, ctypes.byref(v), ctypes.byref(n)))
         return v.value, n.value
+
+    def precond_apply_rbgs(self, r, z=None, work=None, stream=None):
+        """z = M^{-1} r with red-black block Gauss-Seidel (dg_precond_apply_rbgs); work: scratch like r."""
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        if work is None:
+            work = torch.empty_like(r)
+        self._vec_check(r, z, work)
+        check(lib.dg_precond_apply_rbgs(self.h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                        ctypes.c_void_p(work.data_ptr()), _prec(r), _stream_ptr(stream)))
+        return z
 
     def precond_apply(self, r, z=None, stream=None):
         """z = M^{-1} r with the block-Jacobi preconditioner (dg_precond_apply)."""
