@@ -530,14 +530,14 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
 
     q5_48: 48^3 Q5 (23.9 M DOF), log-normal D, 8 sine modes, to 1e-10 relative residual: the mixed-precision
       solve (FP64 outer FGMRES(20) with the true residual, defect update and orthogonalisation in FP64; FP32
-      inner FGMRES(30) on the FP32 operator with the block inverse by fast diagonalisation) with the FP64 outer
-      operator (the conforming variant) and with the double-float outer operator, each with the inner Krylov
-      basis stored in FP32 and in scaled FP16, against plain FP64 FGMRES(30) with the same (exact) block-Jacobi
-      preconditioner in FP64, capped at fp64_cap_s seconds.
-    q4_64: 64^3 Q4 (32.8 M DOF), sigma 1.5, to 1e-8: mixed + block-Jacobi (FP32 and FP16 inner basis),
-      mixed + block-Jacobi + the learned
-      first direction, the network alone in every inner application (capped), and plain FP64 block-Jacobi
-      (capped at fp64_cap_s_q4 seconds).  The network is trained on the solver's own pairs first (timed)."""
+      inner FGMRES(30) on the FP32 operator) with the FP64 outer operator (the conforming variant) and with the
+      double-float outer operator, each with the inner Krylov basis stored in FP32 and in scaled FP16, each with
+      block-Jacobi (exact block inverse by fast diagonalisation) and with red-black block Gauss-Seidel; against
+      plain FP64 FGMRES(30) with the same preconditioner in FP64, each capped at fp64_cap_s seconds.
+    q4_64: 64^3 Q4 (32.8 M DOF), sigma 1.5, to 1e-8: mixed + block-Jacobi and mixed + red-black Gauss-Seidel
+      (FP32 and FP16 inner basis), mixed + block-Jacobi + the learned first direction, the network alone in every
+      inner application (capped), and plain FP64 with either preconditioner (capped at fp64_cap_s_q4 seconds).
+      The network is trained on the solver's own pairs first (timed)."""
     import torch
 
     from paper_1711_10885_gb300 import dg, inputs, learned as learned_mod
@@ -552,32 +552,39 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
     torch.cuda.synchronize()
     q5 = {"workload": "unit_cube_q5_48", "dofs": w.ndof, "rtol": 1e-10, "operator_setup_s": t1 - t0,
           "precond_setup_s": time.perf_counter() - t1,
-          "precond": "block-Jacobi, exact block inverse by fast diagonalisation (FP32 inner, FP64 outer / plain)",
+          "precond": "block-Jacobi (exact block inverse by fast diagonalisation) or red-black block Gauss-Seidel "
+                     "(suffix _rbgs); FP32 in the inner solve, FP64 in the plain solve",
           "block_inverse": _precond_timing(op, w.ndof), "fp32_apply": _f32_apply_timing(op, w)}
     xs = {}
     # each outer operator with the inner Krylov basis stored in FP32 (the default) and in scaled FP16
-    mixed = (("mixed_fp64_outer", 1, 0), ("mixed_df_outer", 0, 0), ("mixed_fp64_outer_fp16_basis", 1, 1),
-             ("mixed_df_outer_fp16_basis", 0, 1))
-    for name, outer, basis in mixed:
-        st, xs[name] = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
-                                    rtol=1e-10, inner_rtol=1e-3, restart=30, outer_restart=20,
-                                    outer_precision=outer, inner_basis_precision=basis)
-        q5[name] = st
-    # plain FP64: its iteration rate first, to turn the time cap into an iteration cap
-    st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
-                         rtol=1e-10, max_iterations=60)
-    cap = max(60, int(fp64_cap_s / (st["wall_s"] / max(1, st["iterations"]))))
-    st, xs["fp64"] = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
-                                  rtol=1e-10, max_iterations=cap)
-    st["iteration_cap"] = cap
-    q5["fp64"] = st
-    if st["converged"]:
-        for name, _, _ in mixed:
-            q5[name]["field_diff_vs_fp64"] = float((xs[name] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
-            q5["speedup_" + name] = st["wall_s"] / q5[name]["wall_s"]
-    else:
-        for name, _, _ in mixed:
-            q5["speedup_lower_bound_" + name] = st["wall_s"] / q5[name]["wall_s"]
+    variants = (("mixed_fp64_outer", 1, 0), ("mixed_df_outer", 0, 0), ("mixed_fp64_outer_fp16_basis", 1, 1),
+                ("mixed_df_outer_fp16_basis", 0, 1))
+    pcs = (("", dg.DG_PRECOND_BLOCK_JACOBI), ("_rbgs", dg.DG_PRECOND_RB_GS))
+    for sfx, pc in pcs:
+        for name, outer, basis in variants:
+            st, xs[name + sfx] = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=pc, rtol=1e-10,
+                                              inner_rtol=1e-3, restart=30, outer_restart=20, outer_precision=outer,
+                                              inner_basis_precision=basis)
+            q5[name + sfx] = st
+        # plain FP64: its iteration rate first, to turn the time cap into an iteration cap
+        st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=pc, rtol=1e-10, max_iterations=60)
+        cap = max(60, int(fp64_cap_s / (st["wall_s"] / max(1, st["iterations"]))))
+        st, xs["fp64" + sfx] = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=pc, rtol=1e-10,
+                                            max_iterations=cap)
+        st["iteration_cap"] = cap
+        q5["fp64" + sfx] = st
+        ref = xs["fp64" + sfx]
+        for name, _, _ in variants:
+            if st["converged"]:
+                q5[name + sfx]["field_diff_vs_fp64"] = float((xs[name + sfx] - ref).abs().max() / ref.abs().max())
+                q5["speedup_" + name + sfx] = st["wall_s"] / q5[name + sfx]["wall_s"]
+            else:
+                q5["speedup_lower_bound_" + name + sfx] = st["wall_s"] / q5[name + sfx]["wall_s"]
+    conv = [q5["fp64" + sfx]["wall_s"] for sfx, _ in pcs if q5["fp64" + sfx]["converged"]]
+    best_mixed = min((q5[name + sfx]["wall_s"], name + sfx) for sfx, _ in pcs for name, _, _ in variants)
+    q5["fastest_mixed"] = best_mixed[1]
+    if conv:
+        q5["speedup_fastest_mixed_vs_fastest_fp64"] = min(conv) / best_mixed[0]
     op.close()
     del xs
     out["q5_48"] = q5
@@ -601,21 +608,20 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
           "setup_s": time.perf_counter() - t0, "block_inverse": _precond_timing(op, ev.ndof),
           "fp32_apply": _f32_apply_timing(op, ev)}
     common = dict(rtol=1e-8, inner_rtol=1e-2, mlp=mlp)
-    q4["mixed_bj"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
-                                     preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, **common)
-    q4["mixed_bj_fp16_basis"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
-                                                preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, inner_basis_precision=1,
-                                                **common)
+    for sfx, pc in (("bj", dg.DG_PRECOND_BLOCK_JACOBI), ("rbgs", dg.DG_PRECOND_RB_GS)):
+        q4["mixed_" + sfx], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=pc, **common)
+        q4["mixed_" + sfx + "_fp16_basis"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=pc,
+                                                             inner_basis_precision=1, **common)
     q4["mixed_bj_learned"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
                                              preconditioner=dg.DG_PRECOND_BJ_MLP, mlp_placement=1, **common)
     q4["mixed_learned_only"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_MIXED,
                                                preconditioner=dg.DG_PRECOND_MLP, max_iterations=30, **common)
-    st, _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
-                         rtol=1e-8, max_iterations=30)
-    cap = max(30, int(fp64_cap_s_q4 / (st["wall_s"] / max(1, st["iterations"]))))
-    q4["fp64_bj"], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
-                                    rtol=1e-8, max_iterations=cap)
-    q4["fp64_bj"]["iteration_cap"] = cap
+    for sfx, pc in (("bj", dg.DG_PRECOND_BLOCK_JACOBI), ("rbgs", dg.DG_PRECOND_RB_GS)):
+        st, _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=pc, rtol=1e-8, max_iterations=30)
+        cap = max(30, int(fp64_cap_s_q4 / (st["wall_s"] / max(1, st["iterations"]))))
+        q4["fp64_" + sfx], _ = _timed_solve(op, ev.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=pc, rtol=1e-8,
+                                            max_iterations=cap)
+        q4["fp64_" + sfx]["iteration_cap"] = cap
     mlp.close()
     op.close()
     out["q4_64"] = q4
@@ -623,9 +629,10 @@ def solve_section(fp64_cap_s=100.0, fp64_cap_s_q4=20.0, learned=True):
 
 
 def restart_sweep():
-    """Outer restart length of the mixed solve (double-float outer operator, inner FGMRES(30) with the FP16 basis):
-    48^3 Q5 to 1e-10 for 10, 20, 30, 60 and 64^3 Q4 (sigma 1.5) to 1e-8 for 10, 20, 30; and the plain FP64
-    FGMRES(60) at 48^3 Q5 (the reference solve of the bench uses FGMRES(30))."""
+    """Outer restart length of the mixed solve (double-float outer operator, inner FGMRES(30) with the FP16 basis;
+    block-Jacobi and red-black Gauss-Seidel, suffix _rbgs): 48^3 Q5 to 1e-10 for 10, 20, 30, 60 and 64^3 Q4
+    (sigma 1.5) to 1e-8 for 10, 20, 30; and the plain FP64 FGMRES(60) with block-Jacobi at 48^3 Q5 (the reference
+    solve of the bench uses FGMRES(30))."""
     from paper_1711_10885_gb300 import dg, inputs
     out = {}
     cases = (("q5_48", inputs.unit_cube_q5_48(with_u=False), 1e-10, 1e-3, (10, 20, 30, 60)),
@@ -635,12 +642,14 @@ def restart_sweep():
         op = dg.operator_for(w)
         op.precond_setup(dg.DG_BJ_FAST_DIAG)
         out[name] = {}
-        for mo in restarts:
-            st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
-                                 rtol=rtol, inner_rtol=itol, restart=30, outer_restart=mo, inner_basis_precision=1)
-            out[name][str(mo)] = {k: st[k] for k in ("iterations", "inner_iterations", "rel_residual", "wall_s",
+        for sfx, pc in (("", dg.DG_PRECOND_BLOCK_JACOBI), ("_rbgs", dg.DG_PRECOND_RB_GS)):
+            for mo in restarts:
+                st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_MIXED, preconditioner=pc, rtol=rtol,
+                                     inner_rtol=itol, restart=30, outer_restart=mo, inner_basis_precision=1)
+                key = str(mo) + sfx
+                out[name][key] = {k: st[k] for k in ("iterations", "inner_iterations", "rel_residual", "wall_s",
                                                      "converged")}
-            out[name][str(mo)]["sm_mhz"] = st["clocks"].get("sm_mhz")
+                out[name][key]["sm_mhz"] = st["clocks"].get("sm_mhz")
         if name == "q5_48":  # the plain FP64 reference with a restart of 60 instead of 30
             st, _ = _timed_solve(op, w.ndof, mode=dg.DG_SOLVE_FP64, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI,
                                  rtol=rtol, restart=60, max_iterations=6000)
