@@ -165,7 +165,8 @@ int dg_destroy(dg_handle* h) {
   cudaFree(h->bj32);
   cudaFree(h->bj16);
   cudaFree(h->bj16s);
-  for (void* q : {h->fdm.re32, h->fdm.re64, h->fdm.cx32, h->fdm.cx64, (void*)h->fdm.re_cells, (void*)h->fdm.cx_cells})
+  for (void* q : {h->fdm.re32, h->fdm.re64, h->fdm.cx32, h->fdm.cx64, (void*)h->fdm.re_cells, (void*)h->fdm.cx_cells,
+                  (void*)h->fdm.red32, (void*)h->fdm.black32})
     cudaFree(q);
   cudaFree(h->bsc);
   cudaFree(h->bface);

@@ -47,6 +47,10 @@ struct FdmTables {
   void* cx64 = nullptr;  // [ncx][TS] double2
   int64_t* re_cells = nullptr;
   int64_t* cx_cells = nullptr;
+  // every red and every black cell (int32, ascending), for the operator restricted to one colour
+  int* red32 = nullptr;
+  int* black32 = nullptr;
+  int64_t nred = 0, nblack = 0;
 };
 
 struct dg_handle {
@@ -145,6 +149,11 @@ void build_tables(int N, int M, Tables1D* tb);
 // mode 0: y = A z, mode 1: y = A z - F; stages: bit 0 cell kernel, bit 1 face kernel (3 = full apply)
 int launch_apply_f64(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s);
 int launch_apply_f32(const dg_handle* h, const float* z, float* y, int mode, int stages, cudaStream_t s);
+// t = (A z)_to for z vanishing outside the cells `from` (two colours of the red-black colouring); t written on
+// `to` only.  Available where has_offdiag_f32 (degree 5, axis-parallel scalar coefficients)
+bool has_offdiag_f32(const dg_handle* h);
+int launch_offdiag_f32(const dg_handle* h, const float* z, float* t, const int* from, int64_t nfrom, const int* to,
+                       int64_t nto, cudaStream_t s);
 // FP64 vectors, operator evaluated in double-float arithmetic (pairs of FP32)
 int launch_apply_f64x(const dg_handle* h, const double* z, double* y, int mode, int stages, cudaStream_t s);
 int launch_diag_blocks_f64(const dg_handle* h, double* out, int cell_base, int ncells, double* V, double* tr,

@@ -198,13 +198,15 @@ template <int N>
 __global__ void __launch_bounds__(PlaneCfg<N>::THREADS)
 dg_cell_kernel_pl(const __grid_constant__ TabNM<N, N, float> tb, const __grid_constant__ Geo<float> g,
                   const float* __restrict__ z, const float* __restrict__ Dcell, float* __restrict__ Vout,
-                  float* __restrict__ traces) {
+                  float* __restrict__ traces, const int* __restrict__ cells, int count) {
   using C = PlaneCfg<N>;
   constexpr int NN = N * N, PS = C::PS;
   extern __shared__ __align__(16) float smp[];
   const int lc = threadIdx.x / N, p = threadIdx.x - lc * N;
-  const int cell = blockIdx.x * C::CPB + lc;
-  const bool active = cell < g.ncell;
+  // the cells of this CTA: positions blockIdx.x * CPB + lc of the list `cells` (null: every cell, count = ncell)
+  const int pos = blockIdx.x * C::CPB + lc;
+  const bool active = pos < count;
+  const int cell = cells ? (active ? cells[pos] : 0) : pos;
   float* rows = smp + lc * C::CS;  // this cell's N rows of PS floats
   float U[NN], V[NN];
 
@@ -341,23 +343,27 @@ __device__ __forceinline__ int neighbour_pl(const Geo<float>& g, int cell, const
 
 // Face weights of the N points (plane p, line k = 0 .. N-1) of face (dir, s) that this thread handles, stored at
 // p + N k, with wf_k = area * w * w of the point given by the caller in wf[].
+//
+// own_zero: the cell's own traces are taken as zero (the operator applied to a vector that vanishes on this cell's
+// colour); so is a neighbour across a periodic wrap of odd length, which has the cell's own colour.
 template <int N, bool PER>
 __device__ __forceinline__ void face_row_pl(const Geo<float>& g, const FaceArgs<float, float>& fa, int cell,
                                             const int (&ic)[3], int dir, int s, int p, const float (&wf)[N],
-                                            float (&Vf)[N], float (&Wf)[N]) {
+                                            float (&Vf)[N], float (&Wf)[N], bool own_zero = false) {
   constexpr int NN = N * N;
   const int face = 2 * dir + s;
   const bool at_end = s ? (ic[dir] == g.n[dir] - 1) : (ic[dir] == 0);
   const bool boundary = at_end && !(PER && g.periodic[dir]);
+  const bool nb_zero = own_zero && at_end && (g.n[dir] & 1);
   const float* c3 = fa.fc + ((size_t)cell * 6 + face) * 3;
   const float* tro = fa.traces + ((size_t)cell * 6 + face) * 2 * NN + p;
   float uo[N], dO[N], un[N], dn[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    uo[k] = tro[N * k];
-    dO[k] = tro[NN + N * k];
+    uo[k] = own_zero ? 0.f : tro[N * k];
+    dO[k] = own_zero ? 0.f : tro[NN + N * k];
   }
-  if (!boundary) {
+  if (!boundary && !nb_zero) {
     const int nb = neighbour_pl<PER>(g, cell, ic, dir, s, at_end);
     const float* trn = fa.traces + ((size_t)nb * 6 + (2 * dir + 1 - s)) * 2 * NN + p;
 #pragma unroll
@@ -381,14 +387,17 @@ __device__ __forceinline__ void face_row_pl(const Geo<float>& g, const FaceArgs<
 template <int N, bool PER>
 __global__ void __launch_bounds__(PlaneCfg<N>::THREADS)
 dg_face_kernel_pl(const __grid_constant__ TabNM<N, N, float> tb, const __grid_constant__ PlaneTab<N> pt,
-                  const __grid_constant__ Geo<float> g, const __grid_constant__ FaceArgs<float, float> fa) {
+                  const __grid_constant__ Geo<float> g, const __grid_constant__ FaceArgs<float, float> fa,
+                  const int* __restrict__ cells, int count, int own_zero) {
   using C = PlaneCfg<N>;
   constexpr int NN = N * N, PS = C::PS;
   extern __shared__ __align__(16) float smp[];
   const int lc = threadIdx.x / N, p = threadIdx.x - lc * N;
-  const int cell0 = blockIdx.x * C::CPB + lc;
-  const bool active = cell0 < g.ncell;
-  const int cell = active ? cell0 : 0;  // inactive threads work on cell 0 and store nothing
+  // positions of the list `cells` (null: every cell); own_zero (mode 0 only): the cell's own V and traces are
+  // taken as zero, so y on the listed cells is the coupling to the other colour (the off-diagonal blocks)
+  const int pos = blockIdx.x * C::CPB + lc;
+  const bool active = pos < count;
+  const int cell = active ? (cells ? cells[pos] : pos) : 0;  // inactive threads work on cell 0 and store nothing
   float* rows = smp + lc * C::CS;
   float* Gs = smp + C::CPB * C::CS + lc * C::GS;  // y-face weights [s * 2 + {V, W}][i3][j1]
   int ic[3];
@@ -397,14 +406,19 @@ dg_face_kernel_pl(const __grid_constant__ TabNM<N, N, float> tb, const __grid_co
   ic[2] = cell / (g.n[0] * g.n[1]);
   float X[NN];
   // plane i2 = p of V: X[i3 * N + i1]
-  rowvec_load<N>(fa.V + ((size_t)cell * N + p) * NN, X);
+  if (own_zero) {
+#pragma unroll
+    for (int q = 0; q < NN; ++q) X[q] = 0.f;
+  } else {
+    rowvec_load<N>(fa.V + ((size_t)cell * N + p) * NN, X);
+  }
   // x faces (points (i2, i3) = (p, b)) lifted onto the x-lines (rows b = i3)
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     float wf[N], Vf[N], Wf[N];
 #pragma unroll
     for (int b = 0; b < N; ++b) wf[b] = g.area[0] * tb.w[p] * tb.w[b];
-    face_row_pl<N, PER>(g, fa, cell, ic, 0, s, p, wf, Vf, Wf);
+    face_row_pl<N, PER>(g, fa, cell, ic, 0, s, p, wf, Vf, Wf, own_zero);
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
@@ -416,7 +430,7 @@ dg_face_kernel_pl(const __grid_constant__ TabNM<N, N, float> tb, const __grid_co
     float wf[N], Vf[N], Wf[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) wf[a] = g.area[2] * tb.w[a] * tb.w[p];
-    face_row_pl<N, PER>(g, fa, cell, ic, 2, s, p, wf, Vf, Wf);
+    face_row_pl<N, PER>(g, fa, cell, ic, 2, s, p, wf, Vf, Wf, own_zero);
 #pragma unroll
     for (int a = 0; a < N; ++a)
 #pragma unroll
@@ -428,7 +442,7 @@ dg_face_kernel_pl(const __grid_constant__ TabNM<N, N, float> tb, const __grid_co
     float wf[N], Vf[N], Wf[N], gv[N], gw[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) wf[a] = g.area[1] * tb.w[a] * tb.w[p];
-    face_row_pl<N, PER>(g, fa, cell, ic, 1, s, p, wf, Vf, Wf);
+    face_row_pl<N, PER>(g, fa, cell, ic, 1, s, p, wf, Vf, Wf, own_zero);
     eo_bwd<N, N, float>(tb, Vf, gv);
     eo_bwd<N, N, float>(tb, Wf, gw);
     chunk_store<N>(Gs + ((2 * s) * N + p) * N, gv);

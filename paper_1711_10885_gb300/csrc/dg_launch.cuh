@@ -249,9 +249,10 @@ int apply_plane(const dg_handle* h, const float* z, float* y, int mode, int stag
   const unsigned grid = (unsigned)((h->ncell + C::CPB - 1) / C::CPB);
   float* V = static_cast<float*>(h->work_V);
   float* tr = static_cast<float*>(h->work_tr);
+  const int ncell = (int)h->ncell;
   if (stages & 1)
     dgk::dg_cell_kernel_pl<N><<<grid, C::THREADS, smem_cell, s>>>(tb, geo, z, static_cast<const float*>(h->p32.D),
-                                                                   V, tr);
+                                                                   V, tr, nullptr, ncell);
   if (stages & 2) {
     dgk::FaceArgs<float, float> fa;
     fa.V = V;
@@ -265,12 +266,55 @@ int apply_plane(const dg_handle* h, const float* z, float* y, int mode, int stag
     fa.z0 = nullptr;
     fa.cz = fa.cu = fa.cr = 0.0;
     if (h->periodic[0] || h->periodic[1] || h->periodic[2])
-      dgk::dg_face_kernel_pl<N, true><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa);
+      dgk::dg_face_kernel_pl<N, true><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa, nullptr, ncell, 0);
     else
-      dgk::dg_face_kernel_pl<N, false><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa);
+      dgk::dg_face_kernel_pl<N, false><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa, nullptr, ncell, 0);
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "FP32 operator kernel launch");
+}
+
+// t = (A z)_to for a z that vanishes outside the cells `from` (the plane kernels: the cell kernel on `from` only,
+// the face kernel on `to` only with the listed cells' own volume and traces taken as zero), i.e. the coupling of
+// the cells `to` to the cells `from`; `from` and `to` are two colours of a red-black colouring.  t is written on
+// the cells `to` only; z is read on the cells `from` only.
+template <int N>
+int apply_plane_offdiag(const dg_handle* h, const float* z, float* t, const int* from, int nfrom, const int* to,
+                        int nto, cudaStream_t s) {
+  using C = dgk::PlaneCfg<N>;
+  if (int rc = apply_plane<N>(h, z, t, 0, 0, s)) return rc;  // the shared-memory attributes (no launch)
+  const size_t smem_cell = (size_t)C::CPB * C::CS * sizeof(float);
+  const size_t smem_face = (size_t)C::CPB * (C::CS + C::GS) * sizeof(float);
+  const auto tb = make_tab<N, float>(h->tab);
+  dgk::PlaneTab<N> pt;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) pt.A[i][j] = (float)h->tab.A[i][j];
+  const auto geo = make_geo<float>(h);
+  float* V = static_cast<float*>(h->work_V);
+  float* tr = static_cast<float*>(h->work_tr);
+  if (nfrom > 0)
+    dgk::dg_cell_kernel_pl<N><<<(unsigned)((nfrom + C::CPB - 1) / C::CPB), C::THREADS, smem_cell, s>>>(
+        tb, geo, z, static_cast<const float*>(h->p32.D), V, tr, from, nfrom);
+  if (nto > 0) {
+    dgk::FaceArgs<float, float> fa;
+    fa.V = V;
+    fa.traces = tr;
+    fa.fc = static_cast<const float*>(h->p32.fc);
+    fa.F = nullptr;
+    for (int i = 0; i < 6; ++i) fa.g[i] = nullptr;
+    fa.y = t;
+    fa.mode = 0;
+    fa.u = z;
+    fa.z0 = nullptr;
+    fa.cz = fa.cu = fa.cr = 0.0;
+    const unsigned grid = (unsigned)((nto + C::CPB - 1) / C::CPB);
+    if (h->periodic[0] || h->periodic[1] || h->periodic[2])
+      dgk::dg_face_kernel_pl<N, true><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa, to, nto, 1);
+    else
+      dgk::dg_face_kernel_pl<N, false><<<grid, C::THREADS, smem_face, s>>>(tb, pt, geo, fa, to, nto, 1);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "FP32 off-diagonal operator launch");
 }
 
 // FP64 applies: meshes with fewer full tiles than SMs take the small-tile variant; FP32 applies of degree 5

@@ -1255,16 +1255,28 @@ int rbgs_black_fused(const dg_handle* h, const TIn* r, float scale, float* z, fl
   return 0;
 }
 
+// In FP32 at degree 5 the operator runs on the red cells and writes the black ones only (launch_offdiag_f32), so
+// z needs no clearing; otherwise z is cleared and the whole operator applied.
 template <typename R, typename First, typename Defect>
 int rbgs_sweep(const dg_handle* h, R* z, R* t, cudaStream_t s, First first, Defect defect_then_black) {
-  if (!h->fdm.built) {
+  const FdmTables& f = h->fdm;
+  if (!f.built) {
     set_error("red-black Gauss-Seidel: dg_precond_setup was not called");
     return DG_ERR_INVALID_ARG;
   }
   const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
-  cudaError_t e = cudaMemsetAsync(z, 0, n * sizeof(R), s);
-  if (e != cudaSuccess) return cuda_fail(e, "red-black Gauss-Seidel: clear z");
+  const bool offdiag = sizeof(R) == 4 && has_offdiag_f32(h);
+  if (!offdiag) {
+    cudaError_t e = cudaMemsetAsync(z, 0, n * sizeof(R), s);
+    if (e != cudaSuccess) return cuda_fail(e, "red-black Gauss-Seidel: clear z");
+  }
   if (int rc = first()) return rc;
+  if constexpr (sizeof(R) == 4) {
+    if (offdiag) {
+      if (int rc = launch_offdiag_f32(h, z, t, f.red32, f.nred, f.black32, f.nblack, s)) return rc;
+      return defect_then_black(n);
+    }
+  }
   if (int rc = rbgs_apply_A<R>(h, z, t, s)) return rc;
   return defect_then_black(n);
 }
@@ -1414,8 +1426,19 @@ int setup_fdm(dg_handle* h) {
   up(&f.cx64, cx64.data(), cx64.size() * sizeof(double2));
   up(reinterpret_cast<void**>(&f.re_cells), re_cells.data(), re_cells.size() * sizeof(int64_t));
   up(reinterpret_cast<void**>(&f.cx_cells), cx_cells.data(), cx_cells.size() * sizeof(int64_t));
+  std::vector<int> reds, blacks;
+  for (int64_t c = 0; c < h->ncell; ++c) {
+    const int64_t ix = c % h->n[0], iy = (c / h->n[0]) % h->n[1], iz = c / ((int64_t)h->n[0] * h->n[1]);
+    ((ix + iy + iz) & 1 ? blacks : reds).push_back((int)c);
+  }
+  f.nred = (int64_t)reds.size();
+  f.nblack = (int64_t)blacks.size();
+  up(reinterpret_cast<void**>(&f.red32), reds.data(), reds.size() * sizeof(int));
+  up(reinterpret_cast<void**>(&f.black32), blacks.data(), blacks.size() * sizeof(int));
   if (e != cudaSuccess) {
-    for (void* q : {f.re32, f.re64, f.cx32, f.cx64, (void*)f.re_cells, (void*)f.cx_cells}) cudaFree(q);
+    for (void* q : {f.re32, f.re64, f.cx32, f.cx64, (void*)f.re_cells, (void*)f.cx_cells, (void*)f.red32,
+                    (void*)f.black32})
+      cudaFree(q);
     return cuda_fail(e, "fast diagonalisation tables");
   }
   f.built = true;

@@ -352,10 +352,13 @@ def _rbgs_reference(pr, w, A, r):
 
 
 @pytest.mark.parametrize("n,k,per", [((3, 2, 2), 2, (0, 0, 0)), ((2, 3, 2), 3, (0, 0, 0)), ((3, 2, 2), 3, (1, 0, 0)),
-                                     ((4, 2, 3), 1, (0, 1, 1))])
+                                     ((4, 2, 3), 1, (0, 1, 1)), ((3, 2, 2), 5, (0, 0, 0)), ((3, 2, 2), 5, (1, 1, 0)),
+                                     ((3, 3, 1), 5, (1, 1, 0))])
 def test_red_black_gauss_seidel_matches_dense_reference(dg, n, k, per):
     """dg_precond_apply_rbgs in FP64 and FP32 against the sweep written out with the oracle matrix's blocks,
-    including a periodic axis of three cells (the two cells across the wrap share a colour) and even ones."""
+    including periodic axes of three cells (the two cells across the wrap share a colour) and even ones.  At
+    k = 5 the FP32 sweep applies the operator on the red cells only and writes the black ones only (plane
+    kernels with a cell list, the listed cells' own terms taken as zero)."""
     w = inputs.small_case(n=n, k=k, seed=40 + k, b=(0.9, -0.5, 0.3), c=0.7)
     pr = oracle.Problem(w.n, w.k, w.D, b=w.b, c=w.c, periodic=per)
     A = oracle_matrix(pr)
@@ -371,11 +374,12 @@ def test_red_black_gauss_seidel_matches_dense_reference(dg, n, k, per):
     op.close()
 
 
-@pytest.mark.parametrize("mode,basis", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
-def test_red_black_gauss_seidel_solves(dg, mode, basis):
+@pytest.mark.parametrize("mode,basis,k", [("fp64", 0, 3), ("mixed", 0, 3), ("mixed", 1, 3), ("mixed", 1, 5)])
+def test_red_black_gauss_seidel_solves(dg, mode, basis, k):
     """FGMRES with red-black block Gauss-Seidel reaches the dense LU solution, in fewer iterations than with
-    block-Jacobi (plain FP64: inner iterations; mixed: with the FP32 and the FP16 inner basis)."""
-    w = inputs.small_case(n=(4, 4, 3), k=3, seed=19, b=(1.0, 0.5, 0.25), f_kind="sines")
+    block-Jacobi (plain FP64: inner iterations; mixed: with the FP32 and the FP16 inner basis; k = 5: the
+    operator restricted to one colour)."""
+    w = inputs.small_case(n=(4, 4, 3) if k == 3 else (3, 2, 2), k=k, seed=19, b=(1.0, 0.5, 0.25), f_kind="sines")
     w.f_params = inputs.sine_modes(11)
     pr = oracle_problem(w)
     A = oracle_matrix(pr)
