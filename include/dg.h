@@ -249,8 +249,9 @@ int dg_precond_apply(dg_handle* h, const void* r_dev, void* z_dev, int32_t preci
  * the wrap share a colour; their coupling is then left out as in block-Jacobi).  M is the block lower-triangular
  * part of A in red-before-black order:
  *   z_red = A_rr^{-1} r_red,   z_black = A_bb^{-1} (r - A z_red)_black,
- * the diagonal blocks inverted by fast diagonalisation (any degree; dg_precond_setup first) and A z_red the
- * operator applied to z_red (zero on the black cells).  r, z and work are distinct device vectors of the given
+ * the diagonal blocks inverted by fast diagonalisation (any degree; dg_precond_setup first; in dg_solve
+ * whatever dg_solve_opts.inner_block_precision says) and A z_red the operator applied to z_red (zero on the
+ * black cells).  r, z and work are distinct device vectors of the given
  * precision (DG_F64 or DG_F32), work is scratch; asynchronous on `stream`. */
 int dg_precond_apply_rbgs(dg_handle* h, const void* r_dev, void* z_dev, void* work_dev, int32_t precision,
                           void* stream);
