@@ -353,11 +353,11 @@ def _rbgs_reference(pr, w, A, r):
 
 @pytest.mark.parametrize("n,k,per", [((3, 2, 2), 2, (0, 0, 0)), ((2, 3, 2), 3, (0, 0, 0)), ((3, 2, 2), 3, (1, 0, 0)),
                                      ((4, 2, 3), 1, (0, 1, 1)), ((3, 2, 2), 5, (0, 0, 0)), ((3, 2, 2), 5, (1, 1, 0)),
-                                     ((3, 3, 1), 5, (1, 1, 0))])
+                                     ((3, 3, 1), 5, (1, 1, 0)), ((3, 2, 2), 4, (1, 0, 0)), ((2, 3, 2), 4, (0, 0, 0))])
 def test_red_black_gauss_seidel_matches_dense_reference(dg, n, k, per):
     """dg_precond_apply_rbgs in FP64 and FP32 against the sweep written out with the oracle matrix's blocks,
     including periodic axes of three cells (the two cells across the wrap share a colour) and even ones.  At
-    k = 5 the FP32 sweep applies the operator on the red cells only and writes the black ones only (plane
+    k = 4 and 5 the FP32 sweep applies the operator on the red cells only and writes the black ones only (plane
     kernels with a cell list, the listed cells' own terms taken as zero)."""
     w = inputs.small_case(n=n, k=k, seed=40 + k, b=(0.9, -0.5, 0.3), c=0.7)
     pr = oracle.Problem(w.n, w.k, w.D, b=w.b, c=w.c, periodic=per)
