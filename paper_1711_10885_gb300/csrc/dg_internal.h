@@ -51,6 +51,7 @@ struct FdmTables {
   int* red32 = nullptr;
   int* black32 = nullptr;
   int64_t nred = 0, nblack = 0;
+  bool two_cyclic = false;  // no face joins two cells of one colour (no periodic axis of odd length)
 };
 
 struct dg_handle {
@@ -174,6 +175,12 @@ int precond_rbgs_f32(const dg_handle* h, const float* r, float* z, float* t, cud
 int precond_rbgs_f64(const dg_handle* h, const double* r, double* z, double* t, cudaStream_t s);
 int precond_rbgs_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* t, float* tmp,
                           cudaStream_t s);
+// z = M^{-1} u with red-black Gauss-Seidel and w = A z = u + U z together (FP32, two-cyclic colouring, a
+// one-colour operator available): u FP32 or a scaled FP16 row
+bool has_rbgs_eisenstat(const dg_handle* h);
+int precond_rbgs_eisenstat_f32(const dg_handle* h, const float* u, float* z, float* w, float* t, cudaStream_t s);
+int precond_rbgs_eisenstat_f32_half(const dg_handle* h, const __half* u, float scale, float* z, float* w, float* t,
+                                    float* tmp, cudaStream_t s);
 // F = l_h(phi_i) from f at the volume points (device, may not be null) and g per side (device or null);
 // with vol = 1 instead of |T| and no g this is the L2 projection z_i = (f, phi_i)_T / |T|
 int launch_rhs_f64(const dg_handle* h, const double* f, const double* const g[6], double* F, cudaStream_t s,

@@ -1317,6 +1317,75 @@ int precond_rbgs_f32_half(const dg_handle* h, const __half* r, float scale, floa
       });
 }
 
+// ---------------------------------------------------------------------------------------------
+// Gauss-Seidel sweep and operator together (Eisenstat's form).  With the blocks ordered red before black and a
+// two-cyclic colouring, A = D + L + U where D is block diagonal, L = A_br (black rows, red columns) and U = A_rb;
+// the sweep is M = D + L, so for z = M^{-1} u:
+//   A z = (M + U) z = u + U z,
+// and U z is the operator restricted to the red rows and the black columns (launch_offdiag_f32 from the black
+// cells to the red ones).  So the Krylov step's operator application costs half an operator.  The block
+// inverses are exact up to FP32 rounding, so the identity holds to that level; the flexible outer method
+// absorbs it like any other inexactness of the inner solve.
+// ---------------------------------------------------------------------------------------------
+namespace {
+// w = scale * u + (red cell ? w : 0), w holding (U z) on the red cells on entry.  One warp per cell (its colour
+// computed once), packs of 4 values (n^3 a multiple of 4, 16-byte aligned vectors)
+template <typename TU>
+__global__ void __launch_bounds__(256) eisenstat_combine(const TU* __restrict__ u, float scale, float* __restrict__ w,
+                                                         int64_t ncell, int n3, int nx, int ny) {
+  const int lane = threadIdx.x & 31, np = n3 >> 2;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncell;
+       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t ix = c % nx, iy = (c / nx) % ny, iz = c / ((int64_t)nx * ny);
+    const bool red = ((ix + iy + iz) & 1) == 0;
+    float4* wc = reinterpret_cast<float4*>(w + c * n3);
+    for (int q = lane; q < np; q += 32) {
+      float4 uv;
+      if constexpr (std::is_same<TU, __half>::value) {
+        const uint2 raw = reinterpret_cast<const uint2*>(u + c * n3)[q];
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+        uv = make_float4(a.x, a.y, b.x, b.y);
+      } else {
+        uv = reinterpret_cast<const float4*>(u + c * n3)[q];
+      }
+      float4 r = red ? wc[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      r.x = fmaf(uv.x, scale, r.x);
+      r.y = fmaf(uv.y, scale, r.y);
+      r.z = fmaf(uv.z, scale, r.z);
+      r.w = fmaf(uv.w, scale, r.w);
+      wc[q] = r;
+    }
+  }
+}
+}  // namespace
+
+bool has_rbgs_eisenstat(const dg_handle* h) {
+  return h->fdm.built && h->fdm.two_cyclic && has_offdiag_f32(h) && (h->N * h->N * h->N) % 4 == 0;
+}
+
+int precond_rbgs_eisenstat_f32(const dg_handle* h, const float* u, float* z, float* w, float* t, cudaStream_t s) {
+  if (int rc = precond_rbgs_f32(h, u, z, t, s)) return rc;
+  const FdmTables& f = h->fdm;
+  if (int rc = launch_offdiag_f32(h, z, w, f.black32, f.nblack, f.red32, f.nred, s)) return rc;
+  const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
+  eisenstat_combine<float><<<sm_count() * 8, 256, 0, s>>>(u, 1.f, w, h->ncell, (int)(n / h->ncell), h->n[0], h->n[1]);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "Gauss-Seidel operator combination");
+}
+
+int precond_rbgs_eisenstat_f32_half(const dg_handle* h, const __half* u, float scale, float* z, float* w, float* t,
+                                    float* tmp, cudaStream_t s) {
+  if (int rc = precond_rbgs_f32_half(h, u, scale, z, t, tmp, s)) return rc;
+  const FdmTables& f = h->fdm;
+  if (int rc = launch_offdiag_f32(h, z, w, f.black32, f.nblack, f.red32, f.nred, s)) return rc;
+  const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
+  eisenstat_combine<__half><<<sm_count() * 8, 256, 0, s>>>(u, scale, w, h->ncell, (int)(n / h->ncell), h->n[0],
+                                                            h->n[1]);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : cuda_fail(e, "Gauss-Seidel operator combination");
+}
+
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s) {
   if (!h->bj16) return precond_fdm(h, r, z, s);
   const int n = h->N * h->N * h->N, np8 = (n + 7) / 8 * 8, ct = np8 / 8;
@@ -1433,6 +1502,9 @@ int setup_fdm(dg_handle* h) {
   }
   f.nred = (int64_t)reds.size();
   f.nblack = (int64_t)blacks.size();
+  f.two_cyclic = true;
+  for (int r = 0; r < 3; ++r)
+    if (h->periodic[r] && (h->n[r] & 1)) f.two_cyclic = false;
   up(reinterpret_cast<void**>(&f.red32), reds.data(), reds.size() * sizeof(int));
   up(reinterpret_cast<void**>(&f.black32), blacks.data(), blacks.size() * sizeof(int));
   if (e != cudaSuccess) {

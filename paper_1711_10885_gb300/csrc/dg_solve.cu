@@ -248,7 +248,7 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
            double tol_abs, int maxit, int max_cycles, bool true_residual_check, Result* out,
            const std::function<void(double, double)>& cycle_hook = {},
            const std::function<int(const T*, T*)>& M0 = {}, int check_every = 1, T* tmp = nullptr,
-           const std::function<int(const B*, T*)>& MB = {}) {
+           const std::function<int(const B*, T*)>& MB = {}, const std::function<int(const B*, T*, T*)>& MA = {}) {
   constexpr bool half_basis = !std::is_same<T, B>::value;
   static_assert(!half_basis || (std::is_same<T, float>::value && std::is_same<B, __half>::value),
                 "FP16 basis storage is for the FP32 solve");
@@ -320,7 +320,13 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
       T* w;
       T* zj = Z + (size_t)j * n;
       bool applied = false;  // z_j formed straight from the FP16 row
-      if constexpr (half_basis) {
+      bool have_w = false;   // z_j and w = A z_j formed together (MA)
+      if (MA && !(j == 0 && M0)) {
+        if constexpr (half_basis) w = tmp;
+        else w = V + (size_t)(j + 1) * n;
+        if (int rc = MA(V + (size_t)j * n, zj, w)) return rc;
+        applied = have_w = true;
+      } else if constexpr (half_basis) {
         w = tmp;
         if (MB && !(j == 0 && M0)) {
           if (int rc = MB(V + (size_t)j * n, zj)) return rc;
@@ -343,7 +349,8 @@ int fgmres(Ctx& c, const std::function<int(const T*, T*)>& M, const T* b, T* x, 
         if (int rc = cuda_check(cudaMemcpyAsync(zj, uj, n * sizeof(T), cudaMemcpyDeviceToDevice, c.s), "copy v"))
           return rc;
       }
-      if (int rc = apply_A<T>(c, zj, w)) return rc;
+      if (!have_w)
+        if (int rc = apply_A<T>(c, zj, w)) return rc;
       if (int rc = basis_dots2(c, V, j + 1, w, c.hdev)) return rc;  // pass 1
       dgb::arn_step<<<1, 32, 0, c.s>>>(st, c.hdev, j, c.cdev);
       if (int rc = basis_update2(c, V, j + 1, j > 0, w, stop)) return rc;  // pass 2
@@ -603,6 +610,20 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       M16 = [&](const __half* r, float* z) {
         return precond_fdm_f32_half(h, r, dgb::HB_INV, z, tmp32 + n, s);
       };
+    // red-black Gauss-Seidel with a two-cyclic colouring: the sweep and the Krylov step's operator together,
+    // A z = u + U z (half an operator instead of a whole one)
+    std::function<int(const float*, float*, float*)> MA32;
+    std::function<int(const __half*, float*, float*)> MA16;
+    if (rbgs && has_rbgs_eisenstat(h)) {
+      MA32 = [&](const float* u, float* z, float* w) {
+        c.applies32 += 2;
+        return precond_rbgs_eisenstat_f32(h, u, z, w, gs32, s);
+      };
+      MA16 = [&](const __half* u, float* z, float* w) {
+        c.applies32 += 2;
+        return precond_rbgs_eisenstat_f32_half(h, u, dgb::HB_INV, z, w, gs32, tmp32 + n, s);
+      };
+    }
     std::function<int(const double*, double*)> P = [&](const double* v, double* z) -> int {
       dgb::scale_copy<double, float><<<c.red_blocks, dgb::RED_THREADS, 0, s>>>(v, rhs32, 1.0, n);
       cudaMemsetAsync(e32, 0, n * sizeof(float), s);
@@ -612,9 +633,9 @@ int dg_solve(dg_handle* h, const double* b_dev, double* x_dev, const dg_solve_op
       if (rc2) return rc2;
       const double itol = o->inner_rtol * std::sqrt(vn2);
       rc2 = half_basis ? fgmres<float, __half>(c, M32, rhs32, e32, true, V16, Z32, m, itol, m, 1, false, &ri, {}, {},
-                                               kInnerCheckEvery, tmp32, M16)
+                                               kInnerCheckEvery, tmp32, M16, MA16)
                        : fgmres<float>(c, M32, rhs32, e32, true, V32, Z32, m, itol, m, 1, false, &ri, {}, {},
-                                       kInnerCheckEvery);
+                                       kInnerCheckEvery, nullptr, {}, MA32);
       if (rc2) return rc2;
       maybe_fallback(ri.beta0, ri.res);
       inner_total += ri.iterations;
