@@ -483,21 +483,25 @@ def _timed_solve(op, n, clock_dev=0, **kw):
 
 
 def _precond_timing(op, n, reps=20):
-    """The block inverse of a set-up handle: what was built (dg_precond_info) and the FP32 and FP64 application
-    times (CUDA events on the current stream, after three warm-ups)."""
+    """The block inverse of a set-up handle: what was built (dg_precond_info), the FP32 and FP64 application times
+    and the FP32 red-black Gauss-Seidel application time (CUDA events on the current stream, after three
+    warm-ups)."""
     import torch
 
     info, ncx = op.precond_info()
     out = {"info": info, "complex_cells": ncx}
     r = torch.rand(n, dtype=torch.float32, device="cuda") - 0.5
-    for name, v in (("fp32_us", r), ("fp64_us", r.double())):
+    work = torch.empty_like(r)
+    cases = (("fp32_us", r, op.precond_apply), ("fp64_us", r.double(), op.precond_apply),
+             ("rbgs_fp32_us", r, lambda v, z: op.precond_apply_rbgs(v, z, work)))
+    for name, v, fn in cases:
         z = torch.empty_like(v)
         for _ in range(3):
-            op.precond_apply(v, z)
+            fn(v, z)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(reps):
-            op.precond_apply(v, z)
+            fn(v, z)
         b.record()
         b.synchronize()
         out[name] = a.elapsed_time(b) / reps * 1e3
