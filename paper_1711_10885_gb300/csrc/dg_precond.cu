@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(c
   using P = FdmPlanesR<N>;
   constexpr int NN = P::NN, N3 = P::N3, UP = P::UP, TP = P::TP, AXP = RealLay<N>::AXP;
   constexpr bool V4 = P::V4, HIN = std::is_same<TIn, __half>::value;
-  static_assert(!HIN || (N3 % 8 == 0 && NN % 4 == 0), "FP16 input: even n");
+  constexpr bool HSTAGE = HIN && N3 % 8 == 0 && NN % 4 == 0;  // FP16 input staged by 16-byte copies (even n)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int64_t s_cell[P::CB];
   float* U = reinterpret_cast<float*>(smem_raw);  // [CB][UP]: U[cell][a + n b + n^2 c]
@@ -660,11 +660,13 @@ __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(c
   for (int e = threadIdx.x; e < here * (TP / 4); e += blockDim.x)  // tables: contiguous in group order
     cp_async16(T + 4 * e, tab + q0 * TP + 4 * e);
   __syncthreads();
-  if constexpr (HIN) {
+  if constexpr (HSTAGE) {
     for (int e = threadIdx.x; e < here * (N3 / 8); e += blockDim.x) {
       const int l = e / (N3 / 8), q = e - l * (N3 / 8);
       cp_async16(RH + l * N3 + 8 * q, r + s_cell[l] * N3 + 8 * q);
     }
+  } else if constexpr (HIN) {
+    // odd n: the planes are read straight from global memory in the first phase
   } else if constexpr (N3 % 4 == 0) {
     for (int e = threadIdx.x; e < here * (N3 / 4); e += blockDim.x) {
       const int l = e / (N3 / 4), q = e - l * (N3 / 4);
@@ -684,7 +686,11 @@ __global__ void __launch_bounds__(FdmPlanesR<N>::CB * N) fdm_apply_planes_real(c
   const float* tb = T + lc * TP;
   float m[NN], v[NN];
   if (active) {  // plane c = p: W_x on its x-lines, W_y on its y-lines
-    if constexpr (HIN) {
+    if constexpr (HIN && !HSTAGE) {
+      const TIn* src = r + s_cell[lc] * N3 + p * NN;
+#pragma unroll
+      for (int q = 0; q < NN; ++q) v[q] = __half2float(src[q]) * in_scale;
+    } else if constexpr (HIN) {
       const uint2* src = reinterpret_cast<const uint2*>(RH + lc * N3 + p * NN);  // 4 halves per 8-byte load
 #pragma unroll
       for (int q = 0; q < NN / 4; ++q) {
@@ -1140,8 +1146,8 @@ int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float
   }
   const int N = h->N, N3 = N * N * N, NN = N * N;
   const int64_t TPR = 3 * ((2 * NN + N + 3) / 4 * 4) + 4, TS = 3 * (2 * NN + N) + 1;
-  const bool direct = N % 2 == 0 && N <= 8 && reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
-                      reinterpret_cast<uintptr_t>(z) % 16 == 0;
+  const bool direct = N <= 8 && (N % 2 == 1 || (reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
+                                                reinterpret_cast<uintptr_t>(z) % 16 == 0));
   if (!direct) {
     half_cells_to_float<<<sm_count() * 4, 256, 0, s>>>(r, scale, nullptr, h->ncell, N3, tmp);
     if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(e, "FP16 row conversion");
@@ -1155,8 +1161,11 @@ int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float
     int rc = 0;
     switch (N) {
       case 2: rc = fdm_real_half<2>(h, tab, cells, hi - lo, r, scale, z, s); break;
+      case 3: rc = fdm_real_half<3>(h, tab, cells, hi - lo, r, scale, z, s); break;
       case 4: rc = fdm_real_half<4>(h, tab, cells, hi - lo, r, scale, z, s); break;
+      case 5: rc = fdm_real_half<5>(h, tab, cells, hi - lo, r, scale, z, s); break;
       case 6: rc = fdm_real_half<6>(h, tab, cells, hi - lo, r, scale, z, s); break;
+      case 7: rc = fdm_real_half<7>(h, tab, cells, hi - lo, r, scale, z, s); break;
       default: rc = fdm_real_half<8>(h, tab, cells, hi - lo, r, scale, z, s); break;
     }
     if (rc) return rc;
@@ -1233,8 +1242,11 @@ int rbgs_black_fused(const dg_handle* h, const TIn* r, float scale, float* z, fl
     if constexpr (std::is_same<TIn, __half>::value) {
       switch (N) {
         case 2: rc = fdm_real_half<2>(h, tab, cells, cnt, r, scale, z, s, t); break;
+        case 3: rc = fdm_real_half<3>(h, tab, cells, cnt, r, scale, z, s, t); break;
         case 4: rc = fdm_real_half<4>(h, tab, cells, cnt, r, scale, z, s, t); break;
+        case 5: rc = fdm_real_half<5>(h, tab, cells, cnt, r, scale, z, s, t); break;
         case 6: rc = fdm_real_half<6>(h, tab, cells, cnt, r, scale, z, s, t); break;
+        case 7: rc = fdm_real_half<7>(h, tab, cells, cnt, r, scale, z, s, t); break;
         default: rc = fdm_real_half<8>(h, tab, cells, cnt, r, scale, z, s, t); break;
       }
       if (!rc)
@@ -1306,7 +1318,7 @@ int precond_rbgs_f64(const dg_handle* h, const double* r, double* z, double* t, 
 int precond_rbgs_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* t, float* tmp,
                           cudaStream_t s) {
   const int N = h->N;
-  const bool fused = N % 2 == 0 && N <= 8 && al16(r) && al16(z) && al16(t);
+  const bool fused = N <= 8 && (N % 2 == 1 || (al16(r) && al16(z) && al16(t)));
   return rbgs_sweep<float>(
       h, z, t, s, [&] { return precond_fdm_f32_half(h, r, scale, z, tmp, s, 0); },
       [&](size_t n) -> int {
@@ -1330,7 +1342,7 @@ int precond_rbgs_f32_half(const dg_handle* h, const __half* r, float scale, floa
 namespace {
 // w = scale * u + (red cell ? w : 0), w holding (U z) on the red cells on entry.  One warp per cell (its colour
 // computed once), packs of 4 values (n^3 a multiple of 4, 16-byte aligned vectors)
-template <typename TU>
+template <typename TU, bool VEC>
 __global__ void __launch_bounds__(256) eisenstat_combine(const TU* __restrict__ u, float scale, float* __restrict__ w,
                                                          int64_t ncell, int n3, int nx, int ny) {
   const int lane = threadIdx.x & 31, np = n3 >> 2;
@@ -1338,6 +1350,13 @@ __global__ void __launch_bounds__(256) eisenstat_combine(const TU* __restrict__ 
        c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t ix = c % nx, iy = (c / nx) % ny, iz = c / ((int64_t)nx * ny);
     const bool red = ((ix + iy + iz) & 1) == 0;
+    if constexpr (!VEC) {  // n^3 not a multiple of 4: one value per lane and step
+      for (int q = lane; q < n3; q += 32) {
+        const int64_t i = c * n3 + q;
+        w[i] = fmaf((float)u[i], scale, red ? w[i] : 0.f);
+      }
+      continue;
+    }
     float4* wc = reinterpret_cast<float4*>(w + c * n3);
     for (int q = lane; q < np; q += 32) {
       float4 uv;
@@ -1360,16 +1379,21 @@ __global__ void __launch_bounds__(256) eisenstat_combine(const TU* __restrict__ 
 }
 }  // namespace
 
-bool has_rbgs_eisenstat(const dg_handle* h) {
-  return h->fdm.built && h->fdm.two_cyclic && has_offdiag_f32(h) && (h->N * h->N * h->N) % 4 == 0;
-}
+// degree 5 only: there the plane kernels are the faster FP32 operator, so half of one beats a whole apply; at
+// degree 4 a one-colour plane apply plus the addition pass cost as much as the whole line-kernel apply (measured:
+// the 64^3 Q4 solve with the FP32 basis took 1.91 s with it, 1.85 s without)
+bool has_rbgs_eisenstat(const dg_handle* h) { return h->fdm.built && h->fdm.two_cyclic && h->N == 6 && has_offdiag_f32(h); }
 
 int precond_rbgs_eisenstat_f32(const dg_handle* h, const float* u, float* z, float* w, float* t, cudaStream_t s) {
   if (int rc = precond_rbgs_f32(h, u, z, t, s)) return rc;
   const FdmTables& f = h->fdm;
   if (int rc = launch_offdiag_f32(h, z, w, f.black32, f.nblack, f.red32, f.nred, s)) return rc;
   const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
-  eisenstat_combine<float><<<sm_count() * 8, 256, 0, s>>>(u, 1.f, w, h->ncell, (int)(n / h->ncell), h->n[0], h->n[1]);
+  const int n3 = (int)(n / h->ncell);
+  if (n3 % 4 == 0 && al16(u) && al16(w))
+    eisenstat_combine<float, true><<<sm_count() * 8, 256, 0, s>>>(u, 1.f, w, h->ncell, n3, h->n[0], h->n[1]);
+  else
+    eisenstat_combine<float, false><<<sm_count() * 8, 256, 0, s>>>(u, 1.f, w, h->ncell, n3, h->n[0], h->n[1]);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "Gauss-Seidel operator combination");
 }
@@ -1380,8 +1404,11 @@ int precond_rbgs_eisenstat_f32_half(const dg_handle* h, const __half* u, float s
   const FdmTables& f = h->fdm;
   if (int rc = launch_offdiag_f32(h, z, w, f.black32, f.nblack, f.red32, f.nred, s)) return rc;
   const size_t n = (size_t)h->ncell * h->N * h->N * h->N;
-  eisenstat_combine<__half><<<sm_count() * 8, 256, 0, s>>>(u, scale, w, h->ncell, (int)(n / h->ncell), h->n[0],
-                                                            h->n[1]);
+  const int n3 = (int)(n / h->ncell);
+  if (n3 % 4 == 0 && reinterpret_cast<uintptr_t>(u) % 8 == 0 && al16(w))
+    eisenstat_combine<__half, true><<<sm_count() * 8, 256, 0, s>>>(u, scale, w, h->ncell, n3, h->n[0], h->n[1]);
+  else
+    eisenstat_combine<__half, false><<<sm_count() * 8, 256, 0, s>>>(u, scale, w, h->ncell, n3, h->n[0], h->n[1]);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : cuda_fail(e, "Gauss-Seidel operator combination");
 }
