@@ -164,9 +164,6 @@ int precond_bj_f64(const dg_handle* h, const double* r, double* z, cudaStream_t 
 int precond_bj_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 int precond_bj_f16(const dg_handle* h, const float* r, float* z, cudaStream_t s);
 int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s);
-// the block inverse on one colour of cells only (0 red, 1 black; -1 every cell); z untouched on the others
-int precond_fdm_color_f32(const dg_handle* h, const float* r, float* z, int color, cudaStream_t s);
-int precond_fdm_color_f64(const dg_handle* h, const double* r, double* z, int color, cudaStream_t s);
 // z = block inverse of (scale * r) for a scaled FP16 r; tmp: n FP32 values of scratch, 16-byte aligned
 int precond_fdm_f32_half(const dg_handle* h, const __half* r, float scale, float* z, float* tmp, cudaStream_t s,
                          int color = -1);

@@ -1098,12 +1098,7 @@ int precond_fdm(const dg_handle* h, const R* r, R* z, cudaStream_t s, int color 
 }
 
 int precond_fdm_f32(const dg_handle* h, const float* r, float* z, cudaStream_t s) { return precond_fdm(h, r, z, s); }
-int precond_fdm_color_f32(const dg_handle* h, const float* r, float* z, int color, cudaStream_t s) {
-  return precond_fdm(h, r, z, s, color);
-}
-int precond_fdm_color_f64(const dg_handle* h, const double* r, double* z, int color, cudaStream_t s) {
-  return precond_fdm(h, r, z, s, color);
-}
+
 
 namespace {
 // dst[c n^3 + i] = scale * src[c n^3 + i] for the listed cells (FP16 -> FP32)
