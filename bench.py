@@ -205,7 +205,32 @@ def cpu_baseline(w, seconds=15.0):
     oracle.apply(pr, w.u, cells=cells)
     dt = time.perf_counter() - t0
     return {"value": count * w.nb / dt / 1e6, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"A u on {count} random cells of the 32^3 Q7 workload ({dt:.1f} s, one thread)"}
+            "sample": f"A u on {count} random cells of the 32^3 Q7 workload ({dt:.1f} s, one thread)",
+            "host": host_cpu()}
+
+
+def host_cpu():
+    """The host the oracle ran on: logical CPUs and the CPU model (from /proc/cpuinfo or lscpu, where present)."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu": model or platform.processor() or platform.machine()}
 
 
 def run_profile_solver(args):
