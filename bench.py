@@ -237,7 +237,8 @@ def run_profile_solver(args):
     """Minimal launch sequence for profilers of the solver kernels: at 48^3 Q5 (fast diagonalisation only, under
     1 GB on the device) W + K FP32 and FP64 block-Jacobi applications and learned-preconditioner applications
     (untrained network); then one outer iteration of the mixed solve (one inner FGMRES(30) cycle) at 32^3 Q5 for
-    the basis passes (about 3 GB), and one inner FGMRES(20) cycle with the FP16 basis at 48^3 Q5 (about 4 GB)."""
+    the basis passes (about 3 GB), and one inner FGMRES(20) cycle with the FP16 basis at 48^3 Q5 (about 4 GB), with
+    block-Jacobi and with red-black Gauss-Seidel."""
     import torch
 
     from paper_1711_10885_gb300 import dg, inputs
@@ -283,10 +284,15 @@ def run_profile_solver(args):
     x = torch.zeros(w.ndof, dtype=torch.float64, device="cuda")
     st48 = op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_BLOCK_JACOBI, rtol=1e-10, restart=20,
                     outer_restart=1, inner_rtol=1e-3, max_iterations=1, inner_basis_precision=1, raise_on_error=False)
+    # the same cycle with red-black Gauss-Seidel (one-colour operator, Krylov step in Eisenstat's form)
+    x.zero_()
+    st48g = op.solve(x, mode=dg.DG_SOLVE_MIXED, preconditioner=dg.DG_PRECOND_RB_GS, rtol=1e-10, restart=20,
+                     outer_restart=1, inner_rtol=1e-3, max_iterations=1, inner_basis_precision=1, raise_on_error=False)
     op.close()
     print(json.dumps({"profile": "solver", "mlp_apply_ms": ms, "mlp_tflops": flops / (ms * 1e-3) / 1e12,
                       "cells": w.ncell, "solve_32": {k: st[k] for k in ("iterations", "inner_iterations")},
-                      "solve_48_fp16_basis": {k: st48[k] for k in ("iterations", "inner_iterations")}}))
+                      "solve_48_fp16_basis": {k: st48[k] for k in ("iterations", "inner_iterations")},
+                      "solve_48_fp16_basis_rbgs": {k: st48g[k] for k in ("iterations", "inner_iterations")}}))
 
 
 def run_profile(args):
